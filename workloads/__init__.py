@@ -1,0 +1,71 @@
+"""Seeded synthetic inputs for the tet-FEM indentation path.
+
+The only module shared by the CPU oracle and the CUDA path: it builds meshes and
+indenter poses and holds none of the method's arithmetic. Seeds follow
+``numpy.random.Generator(PCG64(1000 + workload index))``.
+
+Workloads (sizes from the indentation problem of Sec. III-A of the paper, on
+synthetic geometry):
+  * ``cube_sphere``        unit cube 8x8x8 hexes x 6 tets (3072 tets, 729 nodes),
+                           E=1e6, nu=0.3, bottom fixed; sphere r=0.3 pressed 0.05
+                           deep in 10 load steps.
+  * ``fingertip_sphere``   two-layer half-capsule fingertip (R=7 mm, L=40 mm, 1 mm
+                           skin E=1.5 MPa nu=0.45 over 2 mm inner E=0.2 MPa
+                           nu=0.48, core surface fixed; ~39k tets / ~8.7k nodes);
+                           sphere r=4 mm pressed 2 mm normal to a seeded skin point
+                           in 20 load steps.
+  * ``fingertip_draws``    random sphere / cylinder / box-edge indentations of the
+                           same fingertip.
+  * ``uneven_fingertips``  fingertips with R~U[5,10] and a log-uniform tet count.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from .indenters import (BOX, CYLINDER, PLANE, SHAPE_NAMES, SPHERE, Indenter,  # noqa: F401
+                        cube_sphere_indenter, draw_indentations, entry_times,
+                        fingertip_sphere_indentation, linear_schedule,
+                        place_at_contact, plane_indenter)
+from .meshgen import (INNER, SKIN, Mesh, cube_mesh, fingertip_for_tets,  # noqa: F401
+                      fingertip_mesh, fingertip_tet_count)
+
+SEED_BASE = 1000
+
+
+def cube_sphere():
+    """Unit cube with a sphere pressed into the top face."""
+    return cube_mesh(8), cube_sphere_indenter()
+
+
+def fingertip_sphere(seed: int = SEED_BASE + 1):
+    """The single-fingertip sphere indentation."""
+    mesh = fingertip_mesh()
+    return mesh, fingertip_sphere_indentation(mesh, seed=seed)
+
+
+def fingertip_draws(n: int = 256, seed: int = SEED_BASE + 2, n_steps: int = 20):
+    """n random indentations of the fingertip."""
+    mesh = fingertip_mesh()
+    return mesh, draw_indentations(mesh, n, seed, n_steps)
+
+
+def uneven_fingertips(n: int = 64, seed: int = SEED_BASE + 3, tet_min: float = 5e3,
+                      tet_max: float = 2e5, build: bool = True):
+    """n fingertip meshes with R~U[5,10] and tets log-uniform in [tet_min, tet_max],
+    each with one random indentation."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(n):
+        R = rng.uniform(5.0, 10.0)
+        target = math.exp(rng.uniform(math.log(tet_min), math.log(tet_max)))
+        h = fingertip_for_tets(target, R)
+        sub = int(rng.integers(0, 2**31 - 1))
+        if build:
+            mesh = fingertip_mesh(R=R, h=h)
+            ind = draw_indentations(mesh, 1, sub)[0]
+            out.append((mesh, ind))
+        else:
+            out.append((R, h, fingertip_tet_count(R, 40.0, h), sub))
+    return out
