@@ -1,0 +1,322 @@
+"""Benchmark of the quasi-static tet-FEM indentation solve on B300.
+
+One step = one complete indentation solve (all 20 load steps: FP64 residual,
+FP32 projected tangent, pipelined PCG, line search) of the single-fingertip
+sphere workload: a two-layer half-capsule fingertip (R = 7 mm, L = 40 mm,
+38,880 tets / 8,740 nodes) pressed 2 mm by a sphere of radius 4 mm in 20 load
+steps, to a relative residual of 1e-6. The mesh is resident on the device when
+the timed region starts; outputs go to device buffers. The end-to-end figure
+goes through the same public C ABI from host arrays (mesh upload, indenter,
+solve, host outputs, release) every step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference]
+
+Multi-GPU runs (torchrun) are independent replicas: every rank solves its own
+indentation, no collectives on the data path (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "indentation solves/s at residual 1e-6; kernel HBM GB/s vs peak; p50/p99 latency"
+UNIT = "solves/s"
+TOL = 1e-6
+WORKLOAD = ("fingertip_sphere: two-layer half-capsule fingertip R=7 mm L=40 mm (1 mm skin "
+            "E=1.5 MPa nu=0.45 over 2 mm inner E=0.2 MPa nu=0.48, core fixed), 38880 tets / "
+            "8740 nodes; sphere r=4 mm pressed 2 mm normal to a seeded skin point in 20 load steps")
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def algorithmic_bytes(n_tets, n_nodes, cg_iters, newton_iters, evals):
+    """Per-launch algorithmic bytes of the solve kernel.
+
+    Stored-tangent accounting of the indentation problem (FP32 = 4 B):
+    per PCG iteration 264 B/tet + 160 B/node (tangent 45 floats + Dm^-1 9 floats,
+    tet ids, CSR, p read / y write, fused PCG vectors); per Newton iteration
+    464 B/tet + 48 B/node extra (u read, tangent write, FP64 forces, CSR); per
+    line-search energy pass 60 B/tet."""
+    return (cg_iters * (264 * n_tets + 160 * n_nodes) + newton_iters * (464 * n_tets + 48 * n_nodes)
+            + evals * 60 * n_tets)
+
+
+def compact_bytes(n_tets, n_nodes, cg_iters, newton_iters, evals):
+    """The same, for this library's compressed tangent (30 floats + ushort4 local
+    ids per tet, node vectors in shared memory): per PCG iteration 128 B/tet read
+    + 32 B/node published/loaded; per Newton iteration the FP64 pass (Dm^-1 72 B,
+    V 8 B, ids 8 B, info 4 B) + tangent write 128 B; per energy pass 92 B/tet."""
+    return (cg_iters * (128 * n_tets + 32 * n_nodes) + newton_iters * (220 * n_tets + 48 * n_nodes)
+            + evals * 92 * n_tets)
+
+
+def cpu_oracle_rate(mesh, ind, n_load_steps):
+    """Time the oracle (as it stands) on the first n_load_steps of the same
+    solve and extrapolate to a full solve by Newton iterations, using the
+    oracle's Newton count for the full solve stored in tests/golden."""
+    from threadpoolctl import threadpool_info
+    from oracle import Problem
+    p = Problem(mesh, ind)
+    t0 = time.perf_counter()
+    r = p.solve(tol=1e-10, load_steps=n_load_steps)
+    dt = time.perf_counter() - t0
+    its = int(np.sum(r.newton_iters[:n_load_steps]))
+    full_its = None
+    g = os.path.join(ROOT, "tests", "golden", "fingertip_sphere_oracle.npz")
+    if os.path.exists(g):
+        full_its = int(np.sum(np.load(g)["newton_iters"]))
+    per_it = dt / max(its, 1)
+    est = per_it * (full_its if full_its else its * ind.n_steps / n_load_steps)
+    threads = max([t.get("num_threads", 1) for t in threadpool_info()] or [1])
+    return {"value": 1.0 / est, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": (f"load steps 1-{n_load_steps} of 20 of the same solve ({its} Newton iterations, "
+                       f"{dt:.1f} s), extrapolated by the oracle's {full_its} Newton iterations for the "
+                       f"full solve; scipy SuperLU is single-threaded, BLAS pool {threads} threads, "
+                       f"nproc {os.cpu_count()}"),
+            "seconds": dt}
+
+
+def run_reference(args, rank, world):
+    """The oracle as it stands on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    import workloads as W
+    mesh, ind = W.fingertip_sphere()
+    for _ in range(args.warmup):
+        cpu_oracle_rate(mesh, ind, 1)
+    times, rates = [], []
+    cores = 1
+    for _ in range(args.steps):
+        r = cpu_oracle_rate(mesh, ind, 1)
+        times.append(r["seconds"])
+        rates.append(r["value"])
+        cores = r["cores"]
+    value = float(args.steps / sum(1.0 / v for v in rates))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "tol": TOL},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "each step: load step 1 of 20 of the solve, extrapolated by "
+                                       "Newton iterations to a full solve"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_cuda(args, rank, world, local):
+    import torch
+    import workloads as W
+    import paper_2103_16747_b300 as F
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    seed = 1001 + rank                       # each replica: its own seeded skin point
+    mesh, ind = W.fingertip_sphere(seed=seed)
+    stream = torch.cuda.Stream(device=dev)
+    solver = F.IndentationSolver(mesh, cuda_stream=stream)
+    solver.set_indenter(ind)
+    info = solver.info()
+    opt = F.fem_default_options()
+    n = mesh.n_nodes
+    d_u = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+    d_f = torch.zeros((ind.n_steps, 3), dtype=torch.float64, device=dev)
+    d_fc = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 126 MB L2
+
+    def solve_once():
+        return F.fem_solve(solver.handle, ind.n_steps, TOL, opt, d_u, d_f, d_fc)[1]
+
+    for _ in range(max(args.warmup, 0)):
+        st = solve_once()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    kernel_ms, stats = [], []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k))                 # evict L2 between timed steps
+            ev[k][0].record(stream)
+            st = solve_once()
+            ev[k][1].record(stream)
+            kernel_ms.append(st.kernel_ms)
+            stats.append(st)
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    local_total = sum(step_ms) / 1000.0
+    total = local_total
+    if world > 1:
+        t = torch.tensor([local_total], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total = float(t.item())
+    value = world * args.steps / total
+
+    # end to end through the public API from host arrays, every step
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()   # noqa: E731
+    h_nodes, h_tets = pin(mesh.nodes), pin(mesh.tets.astype(np.int32))
+    h_mat, h_fixed = pin(mesh.tet_material.astype(np.int32)), pin(mesh.fixed_nodes.astype(np.int32))
+    h_u = torch.zeros((n, 3), dtype=torch.float64).pin_memory()
+    h_f = torch.zeros((ind.n_steps, 3), dtype=torch.float64).pin_memory()
+    h_fc = torch.zeros((n, 3), dtype=torch.float64).pin_memory()
+    h2d = (h_nodes.numel() * 8 + h_tets.numel() * 4 + h_mat.numel() * 4 + h_fixed.numel() * 4
+           + mesh.materials.size * 8 + (12 + 3 + 3 + ind.n_steps) * 8)
+    d2h = (h_u.numel() + h_f.numel() + h_fc.numel()) * 8
+    e2e_times = []
+    for k in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hd = F.fem_create_mesh(h_nodes, h_tets, h_mat, mesh.materials, h_fixed, None, stream)
+        F.fem_set_indenter(hd, ind.shape, ind.pose, np.asarray(ind.params), ind.direction, ind.depth_schedule)
+        F.fem_solve(hd, ind.n_steps, TOL, opt, h_u, h_f, h_fc)
+        F.fem_destroy_mesh(hd)
+        t1 = time.perf_counter()
+        if k >= args.warmup:
+            e2e_times.append(t1 - t0)
+    e2e_local = sum(e2e_times)
+    e2e_total = e2e_local
+    if world > 1:
+        t = torch.tensor([e2e_local], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_total = float(t.item())
+
+    # roofline of the dominant kernel (the persistent solve kernel)
+    s0 = stats[-1]
+    evals = s0.newton_iters + s0.backtracks + ind.n_steps
+    kms = statistics.mean(kernel_ms)
+    alg = algorithmic_bytes(mesh.n_tets, n, s0.cg_iters, s0.newton_iters, evals)
+    cmp_b = compact_bytes(mesh.n_tets, n, s0.cg_iters, s0.newton_iters, evals)
+    peak, peak_kind = peaks()
+    achieved = alg / (kms / 1000.0) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        try:
+            traffic = json.load(open(tpath)).get("solve_kernel_fingertip_sphere_bytes")
+        except Exception:
+            traffic = None
+    lat = sorted(step_ms)
+    p = lambda q: lat[min(len(lat) - 1, int(math.ceil(q * len(lat))) - 1)]   # noqa: E731
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total * 1000.0 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (tangent, PCG vectors) + f64 (residual, "
+            "energy, reductions, displacement)", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "tol": TOL, "n_parts": info.n_parts,
+                       "l2": "flushed between timed steps (256 MiB write, L2 is 126 MB)",
+                       "replicas": world, "newton_iters": s0.newton_iters, "cg_iters": s0.cg_iters,
+                       "backtracks": s0.backtracks},
+            "latency_ms": {"p50": p(0.5), "p99": p(0.99)},
+            "e2e": {"value": world * args.steps / e2e_total, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": 3 * args.steps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "kernel": "solve_kernel",
+                         "kernel_ms": kms, "algorithmic_bytes": alg, "peak_kind": peak_kind,
+                         "compact_accounting_GBs": cmp_b / (kms / 1000.0) / 1e9},
+            "clocks": clk.summary()}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = {k: v for k, v in cpu_oracle_rate(mesh, ind, 2).items() if k != "seconds"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_cuda(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

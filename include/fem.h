@@ -1,0 +1,246 @@
+/*
+ * fem.h -- C ABI of the B300 quasi-static tet-FEM indentation solver.
+ *
+ * The operation (Sec. III-A of Narang et al., "Sim-to-Real for Robotic Tactile
+ * Sensing via Physics-Based Simulation and Learned Latent Projections"): a
+ * volumetric tetrahedral mesh of a soft body with a per-element hyperelastic
+ * law, fixed boundary conditions on some nodes, and a rigid indenter driven
+ * into it; the simulator returns nodal displacements (positions) and nodal
+ * contact forces, from which resultant forces are formed. Here the problem is
+ * solved quasi-statically over prescribed load steps: at step k the indenter
+ * sits at origin + d_k * a and the displacement is a minimiser of
+ *
+ *   Pi(u) = sum_e V_e Psi(F_e) + sum_i k_i/2 min(0, phi(X_i + u_i))^2,
+ *   Psi(F) = mu/2 (tr F^T F - 3) - mu ln J + lam/2 (ln J)^2   (neo-Hookean),
+ *   k_i = c_kappa * E_max,i * A_i / h_bar  (boundary node i, not fully fixed),
+ *
+ * with u = prescribed values on fixed DOFs. Convergence of a load step:
+ * ||R_free||_2 <= tol * max(||f_c||_2, E_max * h_bar^2 * 1e-3), where R is the
+ * FP64 gradient of Pi and f_c the nodal contact forces.
+ *
+ * Conventions for every entry point:
+ *   - Return 0 (FEM_OK) on success, a negative FEM_ERR_* code on failure;
+ *     fem_last_error() then holds a thread-local message.
+ *   - The caller owns every array it passes. Inputs are copied; outputs are
+ *     written into caller-allocated arrays. Output pointers may point to host
+ *     memory (pageable or pinned) or to device memory of the current device;
+ *     the library copies with cudaMemcpyDefault.
+ *   - Units are the caller's (the library is unit-agnostic); the workloads use
+ *     mm, N, MPa.
+ *   - Node and tet indices are 0-based int32. Arrays are row-major.
+ *   - Nothing here falls back to the CPU: without a CUDA device every entry
+ *     point that touches the device returns FEM_ERR_CUDA.
+ */
+#ifndef FEM_B300_FEM_H
+#define FEM_B300_FEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define FEM_OK                  0
+#define FEM_ERR_ARG            -1   /* bad pointer, size, index or option */
+#define FEM_ERR_DEGENERATE_TET -2   /* tet volume <= 1e-12 * (longest edge)^3, or inverted */
+#define FEM_ERR_NONFINITE      -3   /* NaN/Inf in an input or in the FP64 residual */
+#define FEM_ERR_OOM            -4   /* device allocation failed */
+#define FEM_ERR_NOT_CONVERGED  -5   /* a load step hit max_newton or the line search failed;
+                                       outputs hold the last iterate, stats are filled */
+#define FEM_ERR_TIMEOUT        -6   /* a bounded device wait (grid barrier) expired */
+#define FEM_ERR_CUDA           -7   /* a CUDA runtime call failed / no device */
+#define FEM_ERR_TOO_LARGE      -8   /* mesh does not fit the single-solve kernel */
+
+/* ---------------------------------------------------------------- shapes */
+#define FEM_SPHERE   0   /* params[0] = radius; centre = pose origin                  */
+#define FEM_CYLINDER 1   /* params[0] = radius; infinite, axis = third pose column    */
+#define FEM_BOX      2   /* params[0..2] = half extents in the pose's local frame      */
+#define FEM_PLANE    3   /* solid half-space behind the face through the origin whose  */
+                         /* outward normal is the third pose column; no params         */
+
+#define FEM_MAX_STEPS 256
+
+/* tangent used inside the PCG */
+#define FEM_TANGENT_PROJECTED 0  /* per-tet dP/dF eigenvalues clamped at 0               */
+#define FEM_TANGENT_EXACT     1  /* exact dP/dF; PCG stops at negative curvature        */
+#define FEM_TANGENT_ADAPTIVE  2  /* projected until the step's residual fell 100x, then */
+                                 /* exact; back to projected on negative curvature or a */
+                                 /* shortened line-search step (default)                */
+#define FEM_TANGENT_ABS       3  /* negative eigenvalues replaced by their magnitude    */
+/* The block-Jacobi preconditioner always uses the projected (PSD) blocks. */
+
+typedef struct fem_mesh fem_mesh;           /* opaque; owns its device memory */
+
+typedef struct { double E, nu; } fem_material;   /* Young's modulus, Poisson's ratio */
+
+typedef struct {
+    double  c_kappa;          /* penalty factor (default 100)                         */
+    int32_t max_newton;       /* Newton iterations per load step (default 60)         */
+    int32_t max_cg;           /* PCG iterations per Newton iteration (default 2000)   */
+    double  cg_rtol_max;      /* forcing term eta upper bound (default 0.1)           */
+    double  cg_rtol_min;      /* forcing term eta lower bound (default 1e-4)          */
+    int32_t max_backtracks;   /* Armijo halvings per Newton iteration (default 30)    */
+    int32_t tangent;          /* FEM_TANGENT_* (default ADAPTIVE)                     */
+    double  barrier_timeout_s;/* bound on every device-side wait (default 5 s)        */
+} fem_options;
+
+typedef struct {
+    int32_t status;                         /* FEM_OK or the FEM_ERR_* of fem_solve    */
+    int32_t steps_done;                     /* load steps that converged               */
+    int32_t newton_iters;                   /* total Newton iterations                 */
+    int32_t cg_iters;                       /* total PCG iterations                    */
+    int32_t backtracks;                     /* total line-search halvings              */
+    int32_t active_contacts;                /* nodes with phi < 0 at the last step     */
+    double  residual;                       /* final ||R_free||_2                      */
+    double  scale;                          /* final convergence scale                 */
+    double  energy;                         /* final total energy Pi                   */
+    double  kernel_ms;                      /* device time of the solve kernel          */
+    int32_t exact_newton_iters;             /* Newton iterations on the exact tangent   */
+    double  phase_ms[8];                    /* kernel time split (CTA 0 clock shares):
+                                               eval, tangent, pcg init, pcg reduce+halo,
+                                               pcg tangent product, pcg vector update,
+                                               pcg grid barrier, total                 */
+    int32_t newton_per_step[FEM_MAX_STEPS];
+    int32_t cg_per_step[FEM_MAX_STEPS];
+    double  residual_per_step[FEM_MAX_STEPS];
+} fem_stats;
+
+typedef struct {
+    int64_t n_nodes, n_tets;
+    int32_t n_parts;            /* mesh partitions = CTAs of the solve kernel             */
+    int64_t part_tets;          /* tets over all partitions (halo tets counted per part)  */
+    int32_t max_owned_nodes, max_local_nodes, max_part_tets;
+    int32_t smem_bytes;         /* dynamic shared memory per CTA                          */
+    int32_t resident;           /* 1: part tangent and connectivity kept in shared memory */
+    double  h_bar;              /* mean unique-edge length                                 */
+    double  scale_floor;        /* E_max * h_bar^2 * 1e-3                                  */
+    int64_t n_candidates;       /* contact candidate nodes                                 */
+    int64_t device_bytes;       /* device memory owned by the mesh                         */
+} fem_mesh_info;
+
+/* Fill *opt with the defaults listed above. */
+void fem_default_options(fem_options* opt);
+
+/*
+ * Upload a mesh (Sec. III-A: volumetric tet mesh, materials, fixed BCs).
+ *   nodes        [n_nodes*3] reference coordinates.
+ *   tets         [n_tets*4] node indices, positively oriented (V > 0).
+ *   tet_material [n_tets] index into materials (NULL: all 0).
+ *   materials    [n_materials] (E > 0, -1 < nu < 0.5).
+ *   fixed_nodes  [n_fixed] nodes with prescribed displacement (default 0).
+ *   fixed_mask   [n_fixed] bit0=x bit1=y bit2=z prescribed, or NULL for xyz.
+ *   cuda_stream  cudaStream_t for every copy and launch on this mesh (NULL =
+ *                the legacy default stream).
+ *   out          receives the handle; destroy it with fem_destroy_mesh.
+ * Errors: FEM_ERR_ARG (bad sizes/indices), FEM_ERR_NONFINITE (coordinates or
+ * material), FEM_ERR_DEGENERATE_TET, FEM_ERR_TOO_LARGE, FEM_ERR_OOM, FEM_ERR_CUDA.
+ * Validation happens on the host before any CUDA call.
+ */
+int fem_create_mesh(const double* nodes, int64_t n_nodes,
+                    const int32_t* tets, int64_t n_tets,
+                    const int32_t* tet_material, const fem_material* materials,
+                    int32_t n_materials,
+                    const int32_t* fixed_nodes, int64_t n_fixed,
+                    const uint8_t* fixed_mask,
+                    void* cuda_stream, fem_mesh** out);
+
+/*
+ * Set the rigid indenter (Sec. III-A: rigid objects driven into the sensor).
+ *   shape          FEM_SPHERE / FEM_CYLINDER / FEM_BOX / FEM_PLANE.
+ *   pose           [12] origin(3) followed by a 3x3 rotation, row-major, whose
+ *                  columns are the indenter's local axes (orthonormal, det +1).
+ *   params         [3] shape parameters (see FEM_* above); may be NULL for PLANE.
+ *   dir            [3] unit approach direction a.
+ *   depth_schedule [n_steps] depths d_k along a, measured from the pose (the
+ *                  pose is the position of initial contact); 1 <= n_steps <=
+ *                  FEM_MAX_STEPS.
+ * Errors: FEM_ERR_ARG, FEM_ERR_NONFINITE.
+ */
+int fem_set_indenter(fem_mesh* mesh, int shape, const double pose[12],
+                     const double* params, const double dir[3],
+                     const double* depth_schedule, int32_t n_steps);
+
+/*
+ * Prescribed displacements on the fixed DOFs (default: zero). values has
+ * [n_fixed*3] entries in fixed_nodes order; components not flagged by the
+ * node's fixed_mask are ignored. The values are ramped over the load steps:
+ * at step k the fixed DOFs hold values * k / K. NULL resets to zero.
+ */
+int fem_set_dirichlet_values(fem_mesh* mesh, const double* values);
+
+/*
+ * Solve the load steps (the hot path: FP64 residual and energy, FP32
+ * PSD-projected element tangent, block-Jacobi pipelined PCG with FP64
+ * reductions, Armijo line search with a J > 0 guard, FP64 displacement update),
+ * all inside one cooperative persistent kernel launched on the mesh's stream.
+ *   load_steps         must equal the schedule length, or 0 for all of it.
+ *   tol                relative residual tolerance (e.g. 1e-6).
+ *   opt                NULL for defaults.
+ *   out_disp           [n_nodes*3] displacement after the last solved step.
+ *   out_contact_force  [load_steps*3] resultant contact force on the body per
+ *                      step, or NULL.
+ *   out_nodal_contact  [n_nodes*3] nodal contact forces at the last step, or NULL.
+ *   stats              filled when non-NULL.
+ * Synchronises the mesh's stream before returning.
+ * Errors: FEM_ERR_ARG, FEM_ERR_NOT_CONVERGED (outputs = last iterate),
+ * FEM_ERR_NONFINITE, FEM_ERR_TIMEOUT, FEM_ERR_CUDA.
+ */
+int fem_solve(fem_mesh* mesh, int32_t load_steps, double tol, const fem_options* opt,
+              double* out_disp, double* out_contact_force, double* out_nodal_contact,
+              fem_stats* stats);
+
+/* Release the mesh and its device memory (NULL is ignored). */
+void fem_destroy_mesh(fem_mesh* mesh);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* fem_last_error(void);
+
+/* Sizes and derived constants of a mesh (partitioning, shared memory, h_bar). */
+int fem_mesh_info_get(const fem_mesh* mesh, fem_mesh_info* info);
+
+/*
+ * Re-cut the mesh into n_parts partitions (one CTA of the solve kernel each;
+ * the default is min(#SMs, n_nodes/48)). Used by the tile autotuner. Errors:
+ * FEM_ERR_ARG, FEM_ERR_TOO_LARGE (more parts than co-resident CTAs, or a part
+ * that does not fit in shared memory), FEM_ERR_OOM, FEM_ERR_CUDA.
+ */
+int fem_repartition(fem_mesh* mesh, int32_t n_parts);
+
+/* ------------------------------------------------------- diagnostics
+ * Single passes of the hot-path kernels, for parity tests. They run the same
+ * device code as fem_solve (same kernel, one phase) on a caller-supplied
+ * displacement. */
+
+/*
+ * FP64 residual at displacement u and load step `step` (1-based; 0 = the pose
+ * itself): out_R [n_nodes*3] = dPi/du (fixed DOFs included, not zeroed),
+ * out_fc [n_nodes*3] nodal contact forces on the body (may be NULL),
+ * out_energy [2] = (elastic energy, contact energy) (may be NULL).
+ * c_kappa from opt (NULL = default). Host or device pointers.
+ */
+int fem_eval_residual(fem_mesh* mesh, const double* u, int32_t step, const fem_options* opt,
+                      double* out_R, double* out_fc, double* out_energy);
+
+/*
+ * FP32 tangent product y = K(u) p at displacement u and step `step`: element
+ * part from the stored per-tet tangent (projected or exact per opt->tangent)
+ * plus the Gauss-Newton contact term, rows and columns of fixed DOFs zeroed.
+ * p and out_y are [n_nodes*3] FP64 (p is rounded to FP32 on the device).
+ */
+int fem_apply_tangent(fem_mesh* mesh, const double* u, int32_t step, const fem_options* opt,
+                      const double* p, double* out_y);
+
+/*
+ * Failure-detection check: launch the solve kernel's grid barrier with one CTA
+ * that never arrives, bounded by timeout_s (e.g. 0.05). The waiting CTAs give
+ * up, set the device error word and return; the call returns FEM_ERR_TIMEOUT
+ * and the CUDA context stays usable. Returns FEM_OK only if the barrier
+ * (wrongly) completed.
+ */
+int fem_debug_barrier_timeout(double timeout_s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FEM_B300_FEM_H */

@@ -1,0 +1,234 @@
+"""ctypes binding of the C ABI in include/fem.h (argument marshalling only).
+
+Every function keeps the C name and order of arguments. Arrays may be NumPy
+arrays (host) or torch tensors (host or CUDA); they are passed as raw pointers
+after a dtype/contiguity check. Nothing here computes any part of the solve and
+there is no CPU fallback: if the CUDA library is missing, importing this module
+raises ImportError.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfem_b300.so")
+
+FEM_OK = 0
+FEM_ERR_ARG = -1
+FEM_ERR_DEGENERATE_TET = -2
+FEM_ERR_NONFINITE = -3
+FEM_ERR_OOM = -4
+FEM_ERR_NOT_CONVERGED = -5
+FEM_ERR_TIMEOUT = -6
+FEM_ERR_CUDA = -7
+FEM_ERR_TOO_LARGE = -8
+ERR_NAMES = {0: "FEM_OK", -1: "FEM_ERR_ARG", -2: "FEM_ERR_DEGENERATE_TET", -3: "FEM_ERR_NONFINITE",
+             -4: "FEM_ERR_OOM", -5: "FEM_ERR_NOT_CONVERGED", -6: "FEM_ERR_TIMEOUT", -7: "FEM_ERR_CUDA",
+             -8: "FEM_ERR_TOO_LARGE"}
+
+FEM_SPHERE, FEM_CYLINDER, FEM_BOX, FEM_PLANE = 0, 1, 2, 3
+FEM_MAX_STEPS = 256
+FEM_TANGENT_PROJECTED, FEM_TANGENT_EXACT, FEM_TANGENT_ADAPTIVE, FEM_TANGENT_ABS = 0, 1, 2, 3
+PHASES = ("eval", "tangent", "pcg_init", "pcg_reduce", "pcg_matvec", "pcg_update", "pcg_barrier", "total")
+
+# Every symbol include/fem.h declares.
+EXPORTS = ("fem_default_options", "fem_create_mesh", "fem_set_indenter", "fem_set_dirichlet_values",
+           "fem_solve", "fem_destroy_mesh", "fem_last_error", "fem_mesh_info_get", "fem_repartition",
+           "fem_eval_residual", "fem_apply_tangent", "fem_debug_barrier_timeout")
+
+
+class fem_material(C.Structure):
+    _fields_ = [("E", C.c_double), ("nu", C.c_double)]
+
+
+class fem_options(C.Structure):
+    _fields_ = [("c_kappa", C.c_double), ("max_newton", C.c_int32), ("max_cg", C.c_int32),
+                ("cg_rtol_max", C.c_double), ("cg_rtol_min", C.c_double),
+                ("max_backtracks", C.c_int32), ("tangent", C.c_int32),
+                ("barrier_timeout_s", C.c_double)]
+
+
+class fem_stats(C.Structure):
+    _fields_ = [("status", C.c_int32), ("steps_done", C.c_int32), ("newton_iters", C.c_int32),
+                ("cg_iters", C.c_int32), ("backtracks", C.c_int32), ("active_contacts", C.c_int32),
+                ("residual", C.c_double), ("scale", C.c_double), ("energy", C.c_double),
+                ("kernel_ms", C.c_double), ("exact_newton_iters", C.c_int32),
+                ("phase_ms", C.c_double * 8),
+                ("newton_per_step", C.c_int32 * FEM_MAX_STEPS),
+                ("cg_per_step", C.c_int32 * FEM_MAX_STEPS),
+                ("residual_per_step", C.c_double * FEM_MAX_STEPS)]
+
+
+class fem_mesh_info(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("n_tets", C.c_int64), ("n_parts", C.c_int32),
+                ("part_tets", C.c_int64), ("max_owned_nodes", C.c_int32),
+                ("max_local_nodes", C.c_int32), ("max_part_tets", C.c_int32),
+                ("smem_bytes", C.c_int32), ("resident", C.c_int32), ("h_bar", C.c_double), ("scale_floor", C.c_double),
+                ("n_candidates", C.c_int64), ("device_bytes", C.c_int64)]
+
+
+class FemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing; build it with `python -m paper_2103_16747_b300.build`")
+    lib = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    sig = {
+        "fem_default_options": (None, [C.POINTER(fem_options)]),
+        "fem_create_mesh": (C.c_int, [P, C.c_int64, P, C.c_int64, P, P, C.c_int32, P, C.c_int64, P, P,
+                                      C.POINTER(P)]),
+        "fem_set_indenter": (C.c_int, [P, C.c_int, P, P, P, P, C.c_int32]),
+        "fem_set_dirichlet_values": (C.c_int, [P, P]),
+        "fem_solve": (C.c_int, [P, C.c_int32, C.c_double, C.POINTER(fem_options), P, P, P,
+                                C.POINTER(fem_stats)]),
+        "fem_destroy_mesh": (None, [P]),
+        "fem_last_error": (C.c_char_p, []),
+        "fem_mesh_info_get": (C.c_int, [P, C.POINTER(fem_mesh_info)]),
+        "fem_repartition": (C.c_int, [P, C.c_int32]),
+        "fem_eval_residual": (C.c_int, [P, P, C.c_int32, C.POINTER(fem_options), P, P, P]),
+        "fem_apply_tangent": (C.c_int, [P, P, C.c_int32, C.POINTER(fem_options), P, P]),
+        "fem_debug_barrier_timeout": (C.c_int, [C.c_double]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def fem_last_error() -> str:
+    return lib.fem_last_error().decode()
+
+
+def _check(rc):
+    if rc != FEM_OK:
+        raise FemError(rc, fem_last_error())
+    return rc
+
+
+def _ptr(x, dtype, keep):
+    """Raw pointer of a contiguous array of the given numpy dtype (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):                       # torch tensor, host or device
+        import torch
+        want = {np.float64: torch.float64, np.int32: torch.int32, np.uint8: torch.uint8}[dtype]
+        if x.dtype != want or not x.is_contiguous():
+            raise TypeError(f"tensor must be contiguous {want}")
+        keep.append(x)
+        return C.c_void_p(x.data_ptr())
+    a = np.ascontiguousarray(x, dtype=dtype)
+    keep.append(a)
+    return C.c_void_p(a.ctypes.data)
+
+
+def _out_ptr(x, dtype, keep):
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return _ptr(x, dtype, keep)
+    if not (isinstance(x, np.ndarray) and x.dtype == dtype and x.flags.c_contiguous and x.flags.writeable):
+        raise TypeError("output arrays must be writeable C-contiguous numpy arrays of the right dtype")
+    keep.append(x)
+    return C.c_void_p(x.ctypes.data)
+
+
+def fem_default_options() -> fem_options:
+    o = fem_options()
+    lib.fem_default_options(C.byref(o))
+    return o
+
+
+def fem_create_mesh(nodes, tets, tet_material, materials, fixed_nodes, fixed_mask=None,
+                    cuda_stream=None):
+    """Returns an opaque handle (c_void_p). ``materials``: (M, 2) array of (E, nu).
+    ``cuda_stream``: a torch.cuda.Stream, a raw cudaStream_t int, or None."""
+    keep = []
+    nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+    tets = np.ascontiguousarray(tets, dtype=np.int32)
+    mats = np.ascontiguousarray(materials, dtype=np.float64).reshape(-1, 2)
+    mat_arr = (fem_material * len(mats))(*[fem_material(float(e), float(n)) for e, n in mats])
+    fixed = np.ascontiguousarray(fixed_nodes if fixed_nodes is not None else [], dtype=np.int32)
+    stream = getattr(cuda_stream, "cuda_stream", cuda_stream)
+    out = C.c_void_p()
+    rc = lib.fem_create_mesh(_ptr(nodes, np.float64, keep), nodes.shape[0],
+                             _ptr(tets, np.int32, keep), tets.shape[0],
+                             _ptr(tet_material, np.int32, keep), C.cast(mat_arr, C.c_void_p), len(mats),
+                             _ptr(fixed, np.int32, keep) if len(fixed) else None, len(fixed),
+                             _ptr(fixed_mask, np.uint8, keep),
+                             C.c_void_p(stream) if stream else None, C.byref(out))
+    _check(rc)
+    return out
+
+
+def fem_set_indenter(mesh, shape, pose, params, direction, depth_schedule):
+    keep = []
+    d = np.ascontiguousarray(depth_schedule, dtype=np.float64)
+    return _check(lib.fem_set_indenter(mesh, int(shape), _ptr(pose, np.float64, keep),
+                                       _ptr(params, np.float64, keep), _ptr(direction, np.float64, keep),
+                                       _ptr(d, np.float64, keep), len(d)))
+
+
+def fem_set_dirichlet_values(mesh, values):
+    keep = []
+    return _check(lib.fem_set_dirichlet_values(mesh, _ptr(values, np.float64, keep)))
+
+
+def fem_solve(mesh, load_steps, tol, opt=None, out_disp=None, out_contact_force=None,
+              out_nodal_contact=None, check=True):
+    """Runs the solve; outputs are written into the given arrays (numpy or torch,
+    host or device). Returns (rc, fem_stats)."""
+    keep = []
+    st = fem_stats()
+    rc = lib.fem_solve(mesh, int(load_steps), float(tol), C.byref(opt) if opt is not None else None,
+                       _out_ptr(out_disp, np.float64, keep), _out_ptr(out_contact_force, np.float64, keep),
+                       _out_ptr(out_nodal_contact, np.float64, keep), C.byref(st))
+    if check:
+        _check(rc)
+    return rc, st
+
+
+def fem_destroy_mesh(mesh):
+    lib.fem_destroy_mesh(mesh)
+
+
+def fem_mesh_info_get(mesh) -> fem_mesh_info:
+    info = fem_mesh_info()
+    _check(lib.fem_mesh_info_get(mesh, C.byref(info)))
+    return info
+
+
+def fem_repartition(mesh, n_parts):
+    return _check(lib.fem_repartition(mesh, int(n_parts)))
+
+
+def fem_eval_residual(mesh, u, step, opt=None, out_R=None, out_fc=None):
+    keep = []
+    e = (C.c_double * 2)()
+    rc = lib.fem_eval_residual(mesh, _ptr(u, np.float64, keep), int(step),
+                               C.byref(opt) if opt is not None else None,
+                               _out_ptr(out_R, np.float64, keep), _out_ptr(out_fc, np.float64, keep), e)
+    _check(rc)
+    return float(e[0]), float(e[1])
+
+
+def fem_apply_tangent(mesh, u, step, p, out_y, opt=None):
+    keep = []
+    return _check(lib.fem_apply_tangent(mesh, _ptr(u, np.float64, keep), int(step),
+                                        C.byref(opt) if opt is not None else None,
+                                        _ptr(p, np.float64, keep), _out_ptr(out_y, np.float64, keep)))
+
+
+def fem_debug_barrier_timeout(timeout_s):
+    return lib.fem_debug_barrier_timeout(float(timeout_s))

@@ -1,0 +1,867 @@
+// Host runtime and C ABI of the tet-FEM indentation solver (include/fem.h).
+//
+// fem_create_mesh validates the inputs on the host (before any CUDA call),
+// precomputes the per-tet reference data (Dm^-1, V), the boundary faces and
+// lumped nodal areas, the mean edge length and the penalty base per node,
+// renumbers nodes along a Morton curve, cuts the node range into one part per
+// CTA of the solve kernel and uploads everything once. fem_solve then runs the
+// whole solve in one cooperative kernel launch and copies the outputs out.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/fem.h"
+#include "fem_internal.h"
+
+using namespace fem;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation)
+    return fail(FEM_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  return fail(FEM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(call, what)                       \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+uint64_t spread_bits(uint64_t v) {
+  v &= 0x1fffff;
+  v = (v | v << 32) & 0x1f00000000ffffull;
+  v = (v | v << 16) & 0x1f0000ff0000ffull;
+  v = (v | v << 8) & 0x100f00f00f00f00full;
+  v = (v | v << 4) & 0x10c30c30c30c30c3ull;
+  v = (v | v << 2) & 0x1249249249249249ull;
+  return v;
+}
+
+template <typename T>
+cudaError_t upload(T** dptr, const std::vector<T>& h, cudaStream_t s, std::vector<void*>& owned,
+                   size_t& bytes) {
+  const size_t n = std::max<size_t>(h.size(), 1) * sizeof(T);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dptr), n);
+  if (e != cudaSuccess) return e;
+  owned.push_back(*dptr);
+  bytes += n;
+  if (!h.empty()) e = cudaMemcpyAsync(*dptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+  return e;
+}
+
+template <typename T>
+cudaError_t alloc(T** dptr, size_t count, std::vector<void*>& owned, size_t& bytes) {
+  const size_t n = std::max<size_t>(count, 1) * sizeof(T);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dptr), n);
+  if (e != cudaSuccess) return e;
+  owned.push_back(*dptr);
+  bytes += n;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+struct fem_mesh {
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int64_t n_nodes = 0, n_tets = 0, n_fixed = 0;
+  std::vector<int> perm;        // new node -> caller node
+  std::vector<int> fixed_nodes; // caller ids
+  std::vector<unsigned char> fixed_bits;  // per fixed entry
+  std::vector<unsigned char> node_mask;   // per new node
+  // host copies needed to re-partition
+  std::vector<int> tets_new;    // 4 per sorted tet
+  std::vector<double> dminv;    // 9 per sorted tet
+  std::vector<double> vol;
+  std::vector<int> mat;
+  std::vector<int> csr_ptr, csr_ent;   // node -> (tet << 2 | corner), new numbering
+  double h_bar = 0, scale_floor = 0;
+  int64_t n_candidates = 0;
+  MeshDev dev{};
+  WorkDev work{};
+  int smem_bytes = 0;
+  std::vector<void*> owned;     // every device allocation of the mesh
+  std::vector<void*> part_owned;
+  size_t bytes = 0, part_bytes = 0;
+  // indenter
+  bool has_indenter = false;
+  int shape = 0;
+  double origin[3]{}, R[9]{}, iparams[3]{}, dir[3]{};
+  int n_steps = 0;
+  double* d_depths = nullptr;
+  bool has_presc = false;
+  double* d_presc = nullptr;
+  double* d_stage = nullptr;     // 3*n_nodes staging in caller order
+  int* d_perm = nullptr;         // new -> caller
+};
+
+namespace fem {
+cudaError_t launch_permute(const double* src, double* dst, const int* perm, int n, bool to_caller,
+                           cudaStream_t s);
+}
+
+namespace {
+
+int build_partitions(fem_mesh* m, int n_parts) {
+  const int Nn = (int)m->n_nodes, Nt = (int)m->n_tets;
+  // contiguous node ranges balanced by incident-tet count
+  std::vector<int> nb(n_parts + 1, 0);
+  const double total = (double)m->csr_ptr[Nn];
+  int c = 1;
+  for (int i = 0; i < Nn && c < n_parts; ++i) {
+    if ((double)m->csr_ptr[i + 1] >= total * c / n_parts) nb[c++] = i + 1;
+  }
+  for (; c < n_parts; ++c) nb[c] = std::min(Nn, nb[c - 1] + 1);
+  nb[n_parts] = Nn;
+  for (int p = 1; p <= n_parts; ++p)
+    if (nb[p] <= nb[p - 1]) return fail(FEM_ERR_TOO_LARGE, "cannot cut %d nodes into %d parts", Nn, n_parts);
+  std::vector<int> part_of(Nn);
+  for (int p = 0; p < n_parts; ++p)
+    for (int i = nb[p]; i < nb[p + 1]; ++i) part_of[i] = p;
+
+  std::vector<int> tb(n_parts + 1, 0), hb(n_parts + 1, 0), halo;
+  std::vector<ushort4> pt_nodes;
+  std::vector<double> pt_dminv_aos, pt_vol;
+  std::vector<int> pt_info, pt_tet;
+  std::vector<int> lcsr_ptr(Nn + 1, 0);
+  std::vector<unsigned> lcsr;
+  std::vector<int> local_of_tet(Nt, -1);
+  std::vector<int> local_of_node(Nn, -1);
+  int max_own = 0, max_loc = 0, max_pt = 0;
+  std::vector<int> tl;
+  for (int p = 0; p < n_parts; ++p) {
+    tl.clear();
+    for (int i = nb[p]; i < nb[p + 1]; ++i)
+      for (int j = m->csr_ptr[i]; j < m->csr_ptr[i + 1]; ++j) tl.push_back(m->csr_ent[j] >> 2);
+    std::sort(tl.begin(), tl.end());
+    tl.erase(std::unique(tl.begin(), tl.end()), tl.end());
+    const int n_own = nb[p + 1] - nb[p];
+    for (int i = nb[p]; i < nb[p + 1]; ++i) local_of_node[i] = i - nb[p];
+    std::vector<int> hl;
+    for (int t : tl)
+      for (int a = 0; a < 4; ++a) {
+        const int g = m->tets_new[4 * t + a];
+        if (g < nb[p] || g >= nb[p + 1]) hl.push_back(g);
+      }
+    std::sort(hl.begin(), hl.end());
+    hl.erase(std::unique(hl.begin(), hl.end()), hl.end());
+    for (size_t j = 0; j < hl.size(); ++j) local_of_node[hl[j]] = n_own + (int)j;
+    const int n_loc = n_own + (int)hl.size();
+    if (n_loc >= 65535) return fail(FEM_ERR_TOO_LARGE, "part %d has %d local nodes (max 65534)", p, n_loc);
+    for (size_t k = 0; k < tl.size(); ++k) {
+      const int t = tl[k];
+      local_of_tet[t] = (int)k;
+      int ln[4];
+      int mn = Nn;
+      for (int a = 0; a < 4; ++a) {
+        ln[a] = local_of_node[m->tets_new[4 * t + a]];
+        mn = std::min(mn, m->tets_new[4 * t + a]);
+      }
+      pt_nodes.push_back(make_ushort4((unsigned short)ln[0], (unsigned short)ln[1], (unsigned short)ln[2],
+                                      (unsigned short)ln[3]));
+      for (int k9 = 0; k9 < 9; ++k9) pt_dminv_aos.push_back(m->dminv[9 * (size_t)t + k9]);
+      pt_vol.push_back(m->vol[t]);
+      const int owner = part_of[mn] == p ? 1 : 0;
+      pt_info.push_back(m->mat[t] | (owner << 16));
+      pt_tet.push_back(t);
+    }
+    for (int i = nb[p]; i < nb[p + 1]; ++i) {
+      lcsr_ptr[i] = (int)lcsr.size();
+      for (int j = m->csr_ptr[i]; j < m->csr_ptr[i + 1]; ++j) {
+        const int t = m->csr_ent[j] >> 2, corner = m->csr_ent[j] & 3;
+        lcsr.push_back(((unsigned)local_of_tet[t] << 2) | (unsigned)corner);
+      }
+    }
+    for (int t : tl) local_of_tet[t] = -1;
+    for (int g : hl) local_of_node[g] = -1;
+    for (int i = nb[p]; i < nb[p + 1]; ++i) local_of_node[i] = -1;
+    halo.insert(halo.end(), hl.begin(), hl.end());
+    tb[p + 1] = (int)pt_nodes.size();
+    hb[p + 1] = (int)halo.size();
+    max_own = std::max(max_own, n_own);
+    max_loc = std::max(max_loc, n_loc);
+    max_pt = std::max(max_pt, (int)tl.size());
+  }
+  lcsr_ptr[Nn] = (int)lcsr.size();
+  const int total_pt = (int)pt_nodes.size();
+  std::vector<double> pt_dminv((size_t)9 * total_pt);
+  for (int e = 0; e < total_pt; ++e)
+    for (int k = 0; k < 9; ++k) pt_dminv[(size_t)k * total_pt + e] = pt_dminv_aos[(size_t)9 * e + k];
+
+  int max_lcsr = 0;
+  for (int p = 0; p < n_parts; ++p) max_lcsr = std::max(max_lcsr, lcsr_ptr[nb[p + 1]] - lcsr_ptr[nb[p]]);
+  int dev_smem = 0;
+  CUDA_TRY(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device), "smem attr");
+  const int static_smem = 8 * kRed + 64;
+  // resident: the whole part in one chunk with its tangent and local CSR in
+  // shared memory; otherwise stream them from global memory in chunks
+  int resident = 1, chunk = max_pt;
+  SmemLayout L = smem_layout(max_own, max_loc, chunk, max_pt, max_lcsr);
+  if (L.total + static_smem > dev_smem) {
+    resident = 0;
+    chunk = std::min(kChunk, max_pt);
+    L = smem_layout(max_own, max_loc, chunk, 0, 0);
+  }
+  if (L.total + static_smem > dev_smem)
+    return fail(FEM_ERR_TOO_LARGE, "part needs %d B shared memory, device allows %d", L.total + static_smem,
+                dev_smem);
+  int per_sm = 0, n_sm = 0;
+  CUDA_TRY(solve_kernel_occupancy(L.total, &per_sm), "occupancy");
+  CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, m->device), "sm count");
+  if (per_sm * n_sm < n_parts)
+    return fail(FEM_ERR_TOO_LARGE, "%d parts exceed the %d co-resident CTAs", n_parts, per_sm * n_sm);
+
+  for (void* q : m->part_owned) cudaFree(q);
+  m->part_owned.clear();
+  m->bytes -= m->part_bytes;
+  m->part_bytes = 0;
+  auto& o = m->part_owned;
+  size_t& by = m->part_bytes;
+  cudaStream_t s = m->stream;
+  int *d_nb, *d_tb, *d_hb, *d_halo, *d_info, *d_lcsr_ptr;
+  ushort4* d_ptn;
+  double *d_dminv, *d_vol;
+  unsigned* d_lcsr;
+  CUDA_TRY(upload(&d_nb, nb, s, o, by), "upload");
+  CUDA_TRY(upload(&d_tb, tb, s, o, by), "upload");
+  CUDA_TRY(upload(&d_hb, hb, s, o, by), "upload");
+  CUDA_TRY(upload(&d_halo, halo, s, o, by), "upload");
+  CUDA_TRY(upload(&d_ptn, pt_nodes, s, o, by), "upload");
+  CUDA_TRY(upload(&d_dminv, pt_dminv, s, o, by), "upload");
+  CUDA_TRY(upload(&d_vol, pt_vol, s, o, by), "upload");
+  CUDA_TRY(upload(&d_info, pt_info, s, o, by), "upload");
+  CUDA_TRY(upload(&d_lcsr_ptr, lcsr_ptr, s, o, by), "upload");
+  CUDA_TRY(upload(&d_lcsr, lcsr, s, o, by), "upload");
+  float4* d_tan;
+  double* d_part;
+  CUDA_TRY(alloc(&d_tan, (size_t)kTanVec * total_pt, o, by), "alloc tangent");
+  CUDA_TRY(alloc(&d_part, (size_t)2 * n_parts * kRed, o, by), "alloc partials");
+  m->bytes += by;
+  MeshDev& D = m->dev;
+  D.n_parts = n_parts;
+  D.total_pt = total_pt;
+  D.max_own = max_own;
+  D.max_loc = max_loc;
+  D.max_pt = max_pt;
+  D.max_lcsr = max_lcsr;
+  D.chunk = chunk;
+  D.resident = resident;
+  D.part_node_begin = d_nb;
+  D.part_tet_begin = d_tb;
+  D.part_halo_begin = d_hb;
+  D.halo_nodes = d_halo;
+  D.pt_nodes = d_ptn;
+  D.pt_dminv = d_dminv;
+  D.pt_vol = d_vol;
+  D.pt_info = d_info;
+  D.lcsr_ptr = d_lcsr_ptr;
+  D.lcsr = d_lcsr;
+  m->work.tangent = d_tan;
+  m->work.partials = d_part;
+  m->smem_bytes = L.total;
+  CUDA_TRY(cudaStreamSynchronize(s), "partition upload");
+  return FEM_OK;
+}
+
+int default_parts(const fem_mesh* m) {
+  int n_sm = 1;
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, m->device);
+  const int64_t by_nodes = std::max<int64_t>(1, m->n_nodes / 48);
+  return (int)std::min<int64_t>(n_sm, by_nodes);
+}
+
+}  // namespace
+
+extern "C" {
+
+void fem_default_options(fem_options* opt) {
+  if (!opt) return;
+  opt->c_kappa = 100.0;
+  opt->max_newton = 60;
+  opt->max_cg = 2000;
+  opt->cg_rtol_max = 0.1;
+  opt->cg_rtol_min = 1e-4;
+  opt->max_backtracks = 30;
+  opt->tangent = FEM_TANGENT_ADAPTIVE;
+  opt->barrier_timeout_s = 5.0;
+}
+
+const char* fem_last_error(void) { return g_err.c_str(); }
+
+void fem_destroy_mesh(fem_mesh* m) {
+  if (!m) return;
+  for (void* q : m->part_owned) cudaFree(q);
+  for (void* q : m->owned) cudaFree(q);
+  delete m;
+}
+
+int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
+                    const int32_t* tet_material, const fem_material* materials, int32_t n_materials,
+                    const int32_t* fixed_nodes, int64_t n_fixed, const uint8_t* fixed_mask,
+                    void* cuda_stream, fem_mesh** out) {
+  g_err.clear();
+  if (!out) return fail(FEM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!nodes || !tets || !materials) return fail(FEM_ERR_ARG, "nodes, tets and materials must be non-NULL");
+  if (n_nodes < 4 || n_nodes > (1 << 30)) return fail(FEM_ERR_ARG, "n_nodes=%lld out of range", (long long)n_nodes);
+  if (n_tets < 1 || n_tets > (1 << 28)) return fail(FEM_ERR_ARG, "n_tets=%lld out of range", (long long)n_tets);
+  if (n_materials < 1 || n_materials > 65535) return fail(FEM_ERR_ARG, "n_materials=%d out of range", n_materials);
+  if (n_fixed < 0 || (n_fixed > 0 && !fixed_nodes)) return fail(FEM_ERR_ARG, "fixed_nodes is NULL");
+  const int Nn = (int)n_nodes, Nt = (int)n_tets;
+  for (int64_t i = 0; i < 3 * n_nodes; ++i)
+    if (!std::isfinite(nodes[i])) return fail(FEM_ERR_NONFINITE, "node coordinate %lld is not finite", (long long)(i / 3));
+  for (int k = 0; k < n_materials; ++k) {
+    const double E = materials[k].E, nu = materials[k].nu;
+    if (!std::isfinite(E) || !std::isfinite(nu)) return fail(FEM_ERR_NONFINITE, "material %d not finite", k);
+    if (!(E > 0) || !(nu > -1.0 && nu < 0.5)) return fail(FEM_ERR_ARG, "material %d: need E>0, -1<nu<0.5", k);
+  }
+  for (int t = 0; t < Nt; ++t) {
+    for (int a = 0; a < 4; ++a) {
+      const int v = tets[4 * t + a];
+      if (v < 0 || v >= Nn) return fail(FEM_ERR_ARG, "tet %d references node %d", t, v);
+      for (int b = 0; b < a; ++b)
+        if (tets[4 * t + b] == v) return fail(FEM_ERR_DEGENERATE_TET, "tet %d repeats node %d", t, v);
+    }
+    if (tet_material && (tet_material[t] < 0 || tet_material[t] >= n_materials))
+      return fail(FEM_ERR_ARG, "tet %d has material %d", t, tet_material[t]);
+  }
+  std::vector<unsigned char> mask_old(Nn, 0);
+  for (int64_t j = 0; j < n_fixed; ++j) {
+    const int v = fixed_nodes[j];
+    if (v < 0 || v >= Nn) return fail(FEM_ERR_ARG, "fixed node %d out of range", v);
+    const unsigned bits = fixed_mask ? fixed_mask[j] : 7u;
+    if (bits > 7u) return fail(FEM_ERR_ARG, "fixed_mask[%lld]=%u (bits 0-2 only)", (long long)j, bits);
+    mask_old[v] |= (unsigned char)bits;
+  }
+  // reference shape matrices, volumes (caller order)
+  std::vector<double> dminv_old((size_t)9 * Nt), vol_old(Nt);
+  for (int t = 0; t < Nt; ++t) {
+    const double* x0 = nodes + 3 * (size_t)tets[4 * t];
+    double Dm[9];
+    double lmax = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      const double* xc = nodes + 3 * (size_t)tets[4 * t + c + 1];
+      for (int i = 0; i < 3; ++i) Dm[3 * i + c] = xc[i] - x0[i];
+    }
+    for (int a = 0; a < 4; ++a)
+      for (int b = a + 1; b < 4; ++b) {
+        const double* xa = nodes + 3 * (size_t)tets[4 * t + a];
+        const double* xb = nodes + 3 * (size_t)tets[4 * t + b];
+        const double l = std::sqrt((xa[0] - xb[0]) * (xa[0] - xb[0]) + (xa[1] - xb[1]) * (xa[1] - xb[1]) +
+                                   (xa[2] - xb[2]) * (xa[2] - xb[2]));
+        lmax = std::max(lmax, l);
+      }
+    const double c00 = Dm[4] * Dm[8] - Dm[5] * Dm[7], c01 = Dm[5] * Dm[6] - Dm[3] * Dm[8],
+                 c02 = Dm[3] * Dm[7] - Dm[4] * Dm[6];
+    const double det = Dm[0] * c00 + Dm[1] * c01 + Dm[2] * c02;
+    const double V = det / 6.0;
+    if (!(V > 1e-12 * lmax * lmax * lmax))
+      return fail(FEM_ERR_DEGENERATE_TET, "tet %d has volume %.3e (%s)", t, V, V < 0 ? "inverted" : "degenerate");
+    const double id = 1.0 / det;
+    double* o = dminv_old.data() + 9 * (size_t)t;
+    o[0] = c00 * id;
+    o[1] = (Dm[2] * Dm[7] - Dm[1] * Dm[8]) * id;
+    o[2] = (Dm[1] * Dm[5] - Dm[2] * Dm[4]) * id;
+    o[3] = c01 * id;
+    o[4] = (Dm[0] * Dm[8] - Dm[2] * Dm[6]) * id;
+    o[5] = (Dm[2] * Dm[3] - Dm[0] * Dm[5]) * id;
+    o[6] = c02 * id;
+    o[7] = (Dm[1] * Dm[6] - Dm[0] * Dm[7]) * id;
+    o[8] = (Dm[0] * Dm[4] - Dm[1] * Dm[3]) * id;
+    vol_old[t] = V;
+  }
+  // ---------------------------------------------------------------- device
+  int device = 0;
+  {
+    cudaError_t e = cudaGetDevice(&device);
+    if (e != cudaSuccess) return cuda_fail(e, "no CUDA device");
+  }
+  fem_mesh* m = new fem_mesh();
+  m->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  m->device = device;
+  m->n_nodes = n_nodes;
+  m->n_tets = n_tets;
+  m->n_fixed = n_fixed;
+  m->fixed_nodes.assign(fixed_nodes, fixed_nodes + n_fixed);
+  m->fixed_bits.resize(n_fixed);
+  for (int64_t j = 0; j < n_fixed; ++j) m->fixed_bits[j] = fixed_mask ? fixed_mask[j] : 7;
+  auto bail = [&](int code) {
+    fem_destroy_mesh(m);
+    return code;
+  };
+  // Morton renumbering of nodes
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int i = 0; i < Nn; ++i)
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = std::min(lo[k], nodes[3 * i + k]);
+      hi[k] = std::max(hi[k], nodes[3 * i + k]);
+    }
+  const double ext = std::max({hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2], 1e-300});
+  std::vector<std::pair<uint64_t, int>> key(Nn);
+  for (int i = 0; i < Nn; ++i) {
+    uint64_t code = 0;
+    for (int k = 0; k < 3; ++k) {
+      const uint64_t q = (uint64_t)std::min(2097151.0, std::floor((nodes[3 * i + k] - lo[k]) / ext * 2097151.0));
+      code |= spread_bits(q) << k;
+    }
+    key[i] = {code, i};
+  }
+  std::sort(key.begin(), key.end());
+  m->perm.resize(Nn);
+  std::vector<int> iperm(Nn);
+  for (int i = 0; i < Nn; ++i) {
+    m->perm[i] = key[i].second;
+    iperm[key[i].second] = i;
+  }
+  // tets in new numbering, sorted by smallest node
+  std::vector<std::pair<int, int>> tkey(Nt);
+  for (int t = 0; t < Nt; ++t) {
+    int mn = Nn;
+    for (int a = 0; a < 4; ++a) mn = std::min(mn, iperm[tets[4 * t + a]]);
+    tkey[t] = {mn, t};
+  }
+  std::sort(tkey.begin(), tkey.end());
+  m->tets_new.resize(4 * (size_t)Nt);
+  m->dminv.resize(9 * (size_t)Nt);
+  m->vol.resize(Nt);
+  m->mat.resize(Nt);
+  for (int t = 0; t < Nt; ++t) {
+    const int to = tkey[t].second;
+    for (int a = 0; a < 4; ++a) m->tets_new[4 * (size_t)t + a] = iperm[tets[4 * to + a]];
+    for (int k = 0; k < 9; ++k) m->dminv[9 * (size_t)t + k] = dminv_old[9 * (size_t)to + k];
+    m->vol[t] = vol_old[to];
+    m->mat[t] = tet_material ? tet_material[to] : 0;
+  }
+  // node -> (tet, corner) CSR, ordered by tet
+  m->csr_ptr.assign(Nn + 1, 0);
+  for (int t = 0; t < Nt; ++t)
+    for (int a = 0; a < 4; ++a) m->csr_ptr[m->tets_new[4 * (size_t)t + a] + 1]++;
+  for (int i = 0; i < Nn; ++i) m->csr_ptr[i + 1] += m->csr_ptr[i];
+  m->csr_ent.resize(4 * (size_t)Nt);
+  {
+    std::vector<int> fill(m->csr_ptr.begin(), m->csr_ptr.end() - 1);
+    for (int t = 0; t < Nt; ++t)
+      for (int a = 0; a < 4; ++a) m->csr_ent[fill[m->tets_new[4 * (size_t)t + a]]++] = (t << 2) | a;
+  }
+  // X, mask in new order
+  std::vector<double> X(3 * (size_t)Nn);
+  m->node_mask.resize(Nn);
+  for (int i = 0; i < Nn; ++i) {
+    for (int k = 0; k < 3; ++k) X[3 * (size_t)i + k] = nodes[3 * (size_t)m->perm[i] + k];
+    m->node_mask[i] = mask_old[m->perm[i]];
+  }
+  // boundary faces (seen once) -> lumped areas; unique edges -> h_bar
+  std::vector<std::array<int, 3>> faces;
+  faces.reserve(4 * (size_t)Nt);
+  static const int fidx[4][3] = {{0, 1, 2}, {0, 1, 3}, {0, 2, 3}, {1, 2, 3}};
+  for (int t = 0; t < Nt; ++t)
+    for (int f = 0; f < 4; ++f) {
+      std::array<int, 3> v = {m->tets_new[4 * (size_t)t + fidx[f][0]], m->tets_new[4 * (size_t)t + fidx[f][1]],
+                              m->tets_new[4 * (size_t)t + fidx[f][2]]};
+      std::sort(v.begin(), v.end());
+      faces.push_back(v);
+    }
+  std::sort(faces.begin(), faces.end());
+  std::vector<double> area(Nn, 0.0);
+  std::vector<char> on_boundary(Nn, 0);
+  for (size_t i = 0; i < faces.size();) {
+    size_t j = i + 1;
+    while (j < faces.size() && faces[j] == faces[i]) ++j;
+    if (j - i == 1) {
+      const double* a = &X[3 * (size_t)faces[i][0]];
+      const double* b = &X[3 * (size_t)faces[i][1]];
+      const double* c = &X[3 * (size_t)faces[i][2]];
+      const double u[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+      const double v[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+      const double cr[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
+      const double A = 0.5 * std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+      for (int k = 0; k < 3; ++k) {
+        area[faces[i][k]] += A / 3.0;
+        on_boundary[faces[i][k]] = 1;
+      }
+    }
+    i = j;
+  }
+  std::vector<uint64_t> edges;
+  edges.reserve(6 * (size_t)Nt);
+  for (int t = 0; t < Nt; ++t)
+    for (int a = 0; a < 4; ++a)
+      for (int b = a + 1; b < 4; ++b) {
+        uint64_t p = (uint64_t)m->tets_new[4 * (size_t)t + a], q = (uint64_t)m->tets_new[4 * (size_t)t + b];
+        if (p > q) std::swap(p, q);
+        edges.push_back((p << 32) | q);
+      }
+  std::sort(edges.begin(), edges.end());
+  edges.erase(std::unique(edges.begin(), edges.end()), edges.end());
+  double lsum = 0.0;
+  for (uint64_t e : edges) {
+    const double* a = &X[3 * (e >> 32)];
+    const double* b = &X[3 * (e & 0xffffffffu)];
+    lsum += std::sqrt((a[0] - b[0]) * (a[0] - b[0]) + (a[1] - b[1]) * (a[1] - b[1]) + (a[2] - b[2]) * (a[2] - b[2]));
+  }
+  m->h_bar = lsum / (double)edges.size();
+  std::vector<double> Emax(Nn, 0.0);
+  double Eglob = 0.0;
+  for (int t = 0; t < Nt; ++t) {
+    const double E = materials[m->mat[t]].E;
+    Eglob = std::max(Eglob, E);
+    for (int a = 0; a < 4; ++a) Emax[m->tets_new[4 * (size_t)t + a]] = std::max(Emax[m->tets_new[4 * (size_t)t + a]], E);
+  }
+  m->scale_floor = Eglob * m->h_bar * m->h_bar * 1e-3;
+  std::vector<double> kbase(Nn, 0.0);
+  for (int i = 0; i < Nn; ++i)
+    if (on_boundary[i] && m->node_mask[i] != 7) {
+      kbase[i] = Emax[i] * area[i] / m->h_bar;
+      m->n_candidates++;
+    }
+  std::vector<double> lame(2 * (size_t)n_materials);
+  for (int k = 0; k < n_materials; ++k) {
+    const double E = materials[k].E, nu = materials[k].nu;
+    lame[2 * k] = E / (2.0 * (1.0 + nu));
+    lame[2 * k + 1] = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  }
+  // uploads
+  cudaStream_t s = m->stream;
+  double *d_X, *d_kbase, *d_lame;
+  unsigned char* d_mask;
+  {
+    cudaError_t e;
+    if ((e = upload(&d_X, X, s, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "upload X"));
+    if ((e = upload(&d_kbase, kbase, s, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "upload k"));
+    if ((e = upload(&d_lame, lame, s, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "upload lame"));
+    if ((e = upload(&d_mask, m->node_mask, s, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "upload mask"));
+    if ((e = upload(&m->d_perm, m->perm, s, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "upload perm"));
+    WorkDev& W = m->work;
+    if ((e = alloc(&W.u, 3 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
+    if ((e = alloc(&W.vpub, 2 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
+    if ((e = alloc(&W.dpub, (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
+    unsigned long long* d_bar;
+    if ((e = alloc(&d_bar, 2, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
+    W.barrier = d_bar;
+    W.abort_flag = reinterpret_cast<int*>(d_bar + 1);
+    if ((e = alloc(&W.out_R, 3 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
+    W.out_y = W.out_R;
+    if ((e = alloc(&W.out_fc, 3 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
+    double* d_inp;
+    if ((e = alloc(&d_inp, 3 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
+    W.in_p = d_inp;
+    if ((e = alloc(&m->d_stage, 3 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
+    if ((e = alloc(&W.step_force, 3 * (size_t)kMaxSteps, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
+    if ((e = alloc(&W.stats, 1, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
+    if ((e = alloc(&m->d_depths, (size_t)kMaxSteps, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
+    if ((e = alloc(&m->d_presc, 3 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
+    if ((e = cudaMemsetAsync(W.u, 0, 3 * sizeof(double) * Nn, s)) != cudaSuccess) return bail(cuda_fail(e, "memset"));
+    if ((e = cudaMemsetAsync(W.vpub, 0, 2 * sizeof(float4) * Nn, s)) != cudaSuccess) return bail(cuda_fail(e, "memset"));
+    if ((e = cudaMemsetAsync(W.dpub, 0, sizeof(float4) * Nn, s)) != cudaSuccess) return bail(cuda_fail(e, "memset"));
+    W.u_presc = m->d_presc;
+  }
+  MeshDev& D = m->dev;
+  D.n_nodes = Nn;
+  D.n_tets = Nt;
+  D.n_materials = n_materials;
+  D.scale_floor = m->scale_floor;
+  D.X = d_X;
+  D.fixmask = d_mask;
+  D.kbase = d_kbase;
+  D.lame = d_lame;
+  int rc = build_partitions(m, default_parts(m));
+  if (rc != FEM_OK) return bail(rc);
+  *out = m;
+  return FEM_OK;
+}
+
+int fem_repartition(fem_mesh* m, int32_t n_parts) {
+  if (!m) return fail(FEM_ERR_ARG, "mesh is NULL");
+  if (n_parts < 1) return fail(FEM_ERR_ARG, "n_parts=%d", n_parts);
+  return build_partitions(m, n_parts);
+}
+
+int fem_mesh_info_get(const fem_mesh* m, fem_mesh_info* info) {
+  if (!m || !info) return fail(FEM_ERR_ARG, "NULL argument");
+  info->n_nodes = m->n_nodes;
+  info->n_tets = m->n_tets;
+  info->n_parts = m->dev.n_parts;
+  info->part_tets = m->dev.total_pt;
+  info->max_owned_nodes = m->dev.max_own;
+  info->max_local_nodes = m->dev.max_loc;
+  info->max_part_tets = m->dev.max_pt;
+  info->smem_bytes = m->smem_bytes;
+  info->resident = m->dev.resident;
+  info->h_bar = m->h_bar;
+  info->scale_floor = m->scale_floor;
+  info->n_candidates = m->n_candidates;
+  info->device_bytes = (int64_t)m->bytes;
+  return FEM_OK;
+}
+
+int fem_set_indenter(fem_mesh* m, int shape, const double pose[12], const double* params, const double dir[3],
+                     const double* depth_schedule, int32_t n_steps) {
+  if (!m || !pose || !dir || !depth_schedule) return fail(FEM_ERR_ARG, "NULL argument");
+  if (shape < FEM_SPHERE || shape > FEM_PLANE) return fail(FEM_ERR_ARG, "unknown shape %d", shape);
+  if (n_steps < 1 || n_steps > FEM_MAX_STEPS) return fail(FEM_ERR_ARG, "n_steps=%d out of range", n_steps);
+  if (shape != FEM_PLANE && !params) return fail(FEM_ERR_ARG, "params is NULL");
+  for (int k = 0; k < 12; ++k)
+    if (!std::isfinite(pose[k])) return fail(FEM_ERR_NONFINITE, "pose not finite");
+  for (int k = 0; k < 3; ++k)
+    if (!std::isfinite(dir[k]) || (params && shape != FEM_PLANE && !std::isfinite(params[k])))
+      return fail(FEM_ERR_NONFINITE, "dir/params not finite");
+  for (int k = 0; k < n_steps; ++k)
+    if (!std::isfinite(depth_schedule[k])) return fail(FEM_ERR_NONFINITE, "depth_schedule not finite");
+  const double dn = std::sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+  if (std::fabs(dn - 1.0) > 1e-6) return fail(FEM_ERR_ARG, "dir must be a unit vector (|a|=%g)", dn);
+  const double* R = pose + 3;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double d = 0.0;
+      for (int k = 0; k < 3; ++k) d += R[3 * k + i] * R[3 * k + j];
+      if (std::fabs(d - (i == j ? 1.0 : 0.0)) > 1e-6) return fail(FEM_ERR_ARG, "pose rotation is not orthonormal");
+    }
+  if (shape == FEM_SPHERE || shape == FEM_CYLINDER) {
+    if (!(params[0] > 0)) return fail(FEM_ERR_ARG, "radius must be > 0");
+  } else if (shape == FEM_BOX) {
+    if (!(params[0] > 0 && params[1] > 0 && params[2] > 0)) return fail(FEM_ERR_ARG, "box half extents must be > 0");
+  }
+  m->shape = shape;
+  for (int k = 0; k < 3; ++k) {
+    m->origin[k] = pose[k];
+    m->dir[k] = dir[k];
+    m->iparams[k] = (params && shape != FEM_PLANE) ? params[k] : 0.0;
+  }
+  for (int k = 0; k < 9; ++k) m->R[k] = R[k];
+  m->n_steps = n_steps;
+  CUDA_TRY(cudaMemcpyAsync(m->d_depths, depth_schedule, sizeof(double) * n_steps, cudaMemcpyDefault, m->stream),
+           "upload depth schedule");
+  CUDA_TRY(cudaStreamSynchronize(m->stream), "upload depth schedule");
+  m->has_indenter = true;
+  return FEM_OK;
+}
+
+int fem_set_dirichlet_values(fem_mesh* m, const double* values) {
+  if (!m) return fail(FEM_ERR_ARG, "mesh is NULL");
+  if (!values) {
+    m->has_presc = false;
+    return FEM_OK;
+  }
+  const int Nn = (int)m->n_nodes;
+  std::vector<int> iperm(Nn);
+  for (int i = 0; i < Nn; ++i) iperm[m->perm[i]] = i;
+  std::vector<double> pres(3 * (size_t)Nn, 0.0);
+  for (int64_t j = 0; j < m->n_fixed; ++j) {
+    const int g = iperm[m->fixed_nodes[j]];
+    for (int k = 0; k < 3; ++k) {
+      if (!std::isfinite(values[3 * j + k])) return fail(FEM_ERR_NONFINITE, "dirichlet value not finite");
+      if (m->fixed_bits[j] & (1u << k)) pres[3 * (size_t)g + k] = values[3 * j + k];
+    }
+  }
+  CUDA_TRY(cudaMemcpyAsync(m->d_presc, pres.data(), sizeof(double) * pres.size(), cudaMemcpyHostToDevice, m->stream),
+           "upload prescribed values");
+  CUDA_TRY(cudaStreamSynchronize(m->stream), "upload prescribed values");
+  m->has_presc = true;
+  return FEM_OK;
+}
+
+static int fill_params(fem_mesh* m, const fem_options* opt, int mode, int steps, int step, double tol,
+                       SolveParams& P) {
+  fem_options o;
+  fem_default_options(&o);
+  if (opt) o = *opt;
+  if (!(o.c_kappa > 0) || o.max_newton < 0 || o.max_cg < 1 || o.max_backtracks < 0 || !(o.cg_rtol_max > 0) ||
+      !(o.cg_rtol_min > 0) || o.cg_rtol_min > o.cg_rtol_max || (o.tangent < 0 || o.tangent > 3) ||
+      !(o.barrier_timeout_s > 0))
+    return fail(FEM_ERR_ARG, "invalid fem_options");
+  memset(&P, 0, sizeof(P));
+  P.mode = mode;
+  P.n_steps = steps;
+  P.step = step;
+  P.tangent_mode = o.tangent;
+  P.has_presc = m->has_presc ? 1 : 0;
+  P.max_newton = o.max_newton;
+  P.max_cg = o.max_cg;
+  P.max_backtracks = o.max_backtracks;
+  P.tol = tol;
+  P.c_kappa = o.c_kappa;
+  P.cg_rtol_max = o.cg_rtol_max;
+  P.cg_rtol_min = o.cg_rtol_min;
+  P.timeout_ns = (unsigned long long)(o.barrier_timeout_s * 1e9);
+  P.shape = m->shape;
+  for (int k = 0; k < 3; ++k) {
+    P.origin[k] = m->origin[k];
+    P.iparams[k] = m->iparams[k];
+    P.dir[k] = m->dir[k];
+  }
+  for (int k = 0; k < 9; ++k) P.R[k] = m->R[k];
+  P.depths = m->d_depths;
+  return FEM_OK;
+}
+
+static int run_kernel(fem_mesh* m, const SolveParams& P, float* ms, StatsDev* hst) {
+  cudaStream_t s = m->stream;
+  CUDA_TRY(cudaMemsetAsync(m->work.barrier, 0, 2 * sizeof(unsigned long long), s), "reset barrier");
+  CUDA_TRY(cudaMemsetAsync(m->work.stats, 0, sizeof(StatsDev), s), "reset stats");
+  CUDA_TRY(launch_solve(m->dev, m->work, P, s, ms), "solve kernel launch");
+  int abort_flag = 0;
+  CUDA_TRY(cudaMemcpyAsync(hst, m->work.stats, sizeof(StatsDev), cudaMemcpyDeviceToHost, s), "stats copy");
+  CUDA_TRY(cudaMemcpyAsync(&abort_flag, m->work.abort_flag, sizeof(int), cudaMemcpyDeviceToHost, s), "flag copy");
+  CUDA_TRY(cudaStreamSynchronize(s), "solve kernel");
+  if (abort_flag) return fail(FEM_ERR_TIMEOUT, "a grid barrier wait exceeded its bound");
+  return FEM_OK;
+}
+
+static int copy_out_nodes(fem_mesh* m, const double* d_src, double* out) {
+  if (!out) return FEM_OK;
+  CUDA_TRY(launch_permute(d_src, m->d_stage, m->d_perm, (int)m->n_nodes, true, m->stream), "unpermute");
+  CUDA_TRY(cudaMemcpyAsync(out, m->d_stage, 3 * sizeof(double) * m->n_nodes, cudaMemcpyDefault, m->stream),
+           "output copy");
+  return FEM_OK;
+}
+
+static int copy_in_nodes(fem_mesh* m, const double* in, double* d_dst) {
+  CUDA_TRY(cudaMemcpyAsync(m->d_stage, in, 3 * sizeof(double) * m->n_nodes, cudaMemcpyDefault, m->stream),
+           "input copy");
+  CUDA_TRY(launch_permute(m->d_stage, d_dst, m->d_perm, (int)m->n_nodes, false, m->stream), "permute");
+  return FEM_OK;
+}
+
+int fem_solve(fem_mesh* m, int32_t load_steps, double tol, const fem_options* opt, double* out_disp,
+              double* out_contact_force, double* out_nodal_contact, fem_stats* stats) {
+  g_err.clear();
+  if (!m) return fail(FEM_ERR_ARG, "mesh is NULL");
+  if (!m->has_indenter) return fail(FEM_ERR_ARG, "fem_set_indenter was not called");
+  if (load_steps == 0) load_steps = m->n_steps;
+  if (load_steps != m->n_steps) return fail(FEM_ERR_ARG, "load_steps=%d but the schedule has %d", load_steps, m->n_steps);
+  if (!(tol > 0) || !std::isfinite(tol)) return fail(FEM_ERR_ARG, "tol must be > 0");
+  SolveParams P;
+  int rc = fill_params(m, opt, MODE_SOLVE, load_steps, 0, tol, P);
+  if (rc) return rc;
+  CUDA_TRY(cudaMemsetAsync(m->work.u, 0, 3 * sizeof(double) * m->n_nodes, m->stream), "reset u");
+  CUDA_TRY(cudaMemsetAsync(m->work.step_force, 0, 3 * sizeof(double) * kMaxSteps, m->stream), "reset forces");
+  StatsDev hst;
+  float ms = 0.f;
+  rc = run_kernel(m, P, &ms, &hst);
+  if (rc) return rc;
+  if ((rc = copy_out_nodes(m, m->work.u, out_disp))) return rc;
+  if ((rc = copy_out_nodes(m, m->work.out_fc, out_nodal_contact))) return rc;
+  if (out_contact_force)
+    CUDA_TRY(cudaMemcpyAsync(out_contact_force, m->work.step_force, 3 * sizeof(double) * load_steps,
+                             cudaMemcpyDefault, m->stream), "force copy");
+  CUDA_TRY(cudaStreamSynchronize(m->stream), "output copy");
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->steps_done = hst.steps_done;
+    stats->newton_iters = hst.newton_total;
+    stats->cg_iters = hst.cg_total;
+    stats->backtracks = hst.backtracks_total;
+    stats->active_contacts = hst.active;
+    stats->residual = hst.residual;
+    stats->scale = hst.scale;
+    stats->energy = hst.energy;
+    stats->kernel_ms = ms;
+    stats->exact_newton_iters = hst.exact_newton;
+    const double tot = (double)hst.cycles[PH_TOTAL];
+    for (int k = 0; k < PH_N && k < 8; ++k)
+      stats->phase_ms[k] = tot > 0 ? ms * (double)hst.cycles[k] / tot : 0.0;
+    for (int k = 0; k < load_steps; ++k) {
+      stats->newton_per_step[k] = hst.newton_per_step[k];
+      stats->cg_per_step[k] = hst.cg_per_step[k];
+      stats->residual_per_step[k] = hst.residual_per_step[k];
+    }
+  }
+  int code = FEM_OK;
+  switch (hst.status) {
+    case ST_OK: code = FEM_OK; break;
+    case ST_NONFINITE: code = fail(FEM_ERR_NONFINITE, "non-finite residual or inverted tet at step %d", hst.steps_done + 1); break;
+    case ST_LINESEARCH: code = fail(FEM_ERR_NOT_CONVERGED, "line search failed at step %d", hst.steps_done + 1); break;
+    default: code = fail(FEM_ERR_NOT_CONVERGED, "step %d did not converge in max_newton iterations", hst.steps_done + 1);
+  }
+  if (stats) stats->status = code;
+  return code;
+}
+
+int fem_eval_residual(fem_mesh* m, const double* u, int32_t step, const fem_options* opt, double* out_R,
+                      double* out_fc, double* out_energy) {
+  g_err.clear();
+  if (!m || !u || !out_R) return fail(FEM_ERR_ARG, "NULL argument");
+  if (!m->has_indenter) return fail(FEM_ERR_ARG, "fem_set_indenter was not called");
+  if (step < 0 || step > m->n_steps) return fail(FEM_ERR_ARG, "step out of range");
+  SolveParams P;
+  int rc = fill_params(m, opt, MODE_EVAL, m->n_steps, step, 1e-6, P);
+  if (rc) return rc;
+  if ((rc = copy_in_nodes(m, u, m->work.u))) return rc;
+  StatsDev hst;
+  if ((rc = run_kernel(m, P, nullptr, &hst))) return rc;
+  if ((rc = copy_out_nodes(m, m->work.out_R, out_R))) return rc;
+  if ((rc = copy_out_nodes(m, m->work.out_fc, out_fc))) return rc;
+  CUDA_TRY(cudaStreamSynchronize(m->stream), "output copy");
+  if (out_energy) {
+    out_energy[0] = hst.elastic;
+    out_energy[1] = hst.contact_energy;
+  }
+  if (hst.status == ST_NONFINITE) return fail(FEM_ERR_NONFINITE, "inverted tet or non-finite energy");
+  return FEM_OK;
+}
+
+int fem_apply_tangent(fem_mesh* m, const double* u, int32_t step, const fem_options* opt, const double* p,
+                      double* out_y) {
+  g_err.clear();
+  if (!m || !u || !p || !out_y) return fail(FEM_ERR_ARG, "NULL argument");
+  if (!m->has_indenter) return fail(FEM_ERR_ARG, "fem_set_indenter was not called");
+  if (step < 0 || step > m->n_steps) return fail(FEM_ERR_ARG, "step out of range");
+  SolveParams P;
+  int rc = fill_params(m, opt, MODE_APPLY, m->n_steps, step, 1e-6, P);
+  if (rc) return rc;
+  if ((rc = copy_in_nodes(m, u, m->work.u))) return rc;
+  if ((rc = copy_in_nodes(m, p, const_cast<double*>(m->work.in_p)))) return rc;
+  StatsDev hst;
+  if ((rc = run_kernel(m, P, nullptr, &hst))) return rc;
+  if ((rc = copy_out_nodes(m, m->work.out_y, out_y))) return rc;
+  CUDA_TRY(cudaStreamSynchronize(m->stream), "output copy");
+  return FEM_OK;
+}
+
+int fem_debug_barrier_timeout(double timeout_s) {
+  g_err.clear();
+  if (!(timeout_s > 0) || timeout_s > 10) return fail(FEM_ERR_ARG, "timeout_s must be in (0, 10]");
+  unsigned long long* d = nullptr;
+  CUDA_TRY(cudaMalloc(&d, 2 * sizeof(unsigned long long)), "alloc");
+  cudaMemset(d, 0, 2 * sizeof(unsigned long long));
+  MeshDev M{};
+  M.n_parts = 4;
+  WorkDev W{};
+  W.barrier = d;
+  W.abort_flag = reinterpret_cast<int*>(d + 1);
+  SolveParams P{};
+  P.mode = MODE_BARRIER_TEST;
+  P.timeout_ns = (unsigned long long)(timeout_s * 1e9);
+  cudaError_t e = launch_solve(M, W, P, nullptr, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  int flag = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&flag, d + 1, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(e, "barrier test");
+  if (flag) return fail(FEM_ERR_TIMEOUT, "barrier wait expired as intended");
+  return FEM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,937 @@
+// Persistent cooperative solve kernel: the whole quasi-static indentation
+// solve (load steps, Newton, line search, PCG) runs in one launch.
+//
+// Work decomposition. The mesh is cut into P parts, one per CTA. Part c owns a
+// contiguous range of (Morton-ordered) nodes and holds every tet that touches
+// one of them; tets on part boundaries are evaluated by each part that needs
+// them, so a CTA finishes the node sums of its own nodes in shared memory with
+// no atomics and a fixed summation order (deterministic). Vectors of the owned
+// nodes live in shared memory for the whole solve, and so do (when they fit)
+// the part's stored tangent, tet node ids and local node->tet lists. Only the
+// values other parts need (the PCG vector being multiplied, the Newton
+// direction, the displacement) and one reduction slot per CTA go through
+// global memory.
+//
+// Synchronisation. One software grid barrier per PCG iteration (pipelined CG,
+// Ghysels & Vanroose 2014: the dot products of iteration i are reduced while
+// the tangent product of iteration i is formed). Every wait is bounded
+// (globaltimer); on expiry the CTA sets the abort word and returns, and the
+// others leave at their next barrier. The launch is cooperative so that all
+// CTAs are co-resident or the launch fails cleanly.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fem_internal.h"
+#include "fem_math.cuh"
+
+namespace fem {
+
+namespace {
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
+  return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+
+struct Barrier {
+  unsigned long long* counter;
+  int* abort_flag;
+  unsigned long long epoch;
+  unsigned long long timeout_ns;
+  unsigned nblocks;
+};
+
+// Returns false (uniformly in the CTA) when the barrier was abandoned.
+__device__ bool grid_sync(Barrier& b, int* s_flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    b.epoch += 1;
+    const unsigned long long target = b.epoch * (unsigned long long)b.nblocks;
+    __threadfence();
+    atomicAdd(b.counter, 1ull);
+    int failed = 0;
+    const unsigned long long t0 = global_ns();
+    unsigned it = 0;
+    while (ld_volatile_u64(b.counter) < target) {
+      if (*reinterpret_cast<volatile int*>(b.abort_flag)) { failed = 1; break; }
+      if ((++it & 63u) == 0u && global_ns() - t0 > b.timeout_ns) {
+        atomicExch(b.abort_flag, 1);
+        failed = 1;
+        break;
+      }
+    }
+    __threadfence();
+    if (!failed && *reinterpret_cast<volatile int*>(b.abort_flag)) failed = 1;
+    *s_flag = failed;
+  }
+  __syncthreads();
+  return *s_flag == 0;
+}
+
+struct Ctx {
+  int part, n_own, n_loc, node0, halo0, t0, n_pt;
+  double *u, *uprev, *R, *X, *fc, *kp, *ut, *chunkd, *red;
+  float *x, *r, *ucg, *w, *z, *q, *s, *p, *acc, *minv, *hc, *chunkf;
+  float4* lm;
+  float4* tan;            // part tangent, element (g, t) at tan[g * tan_stride + t]
+  int tan_stride;
+  const ushort4* ptn;     // part tet local node ids, index t
+  const int* lptr;        // owned node i: entries lcsr[lptr[i] .. lptr[i+1])
+  const unsigned* lcsr;   // (local tet << 2) | corner, sorted by local tet
+  unsigned char* mask;
+  int* cursor;
+  double* red_out;        // broadcast area for grid reductions (kRed doubles)
+  int* flag;
+  bool timer;             // CTA 0, thread 0 accumulates phase cycles
+  long long cyc[PH_N];
+};
+
+__device__ __forceinline__ long long tick(const Ctx& C) { return C.timer ? clock64() : 0ll; }
+__device__ __forceinline__ void tock(Ctx& C, int ph, long long& t) {
+  if (C.timer) {
+    const long long n = clock64();
+    C.cyc[ph] += n - t;
+    t = n;
+  }
+}
+
+__device__ __forceinline__ int local_to_global(const Ctx& C, const MeshDev& M, int l) {
+  return l < C.n_own ? C.node0 + l : M.halo_nodes[C.halo0 + l - C.n_own];
+}
+
+// Deterministic CTA reduction of nv per-thread doubles into a W.partials slot.
+__device__ void block_reduce_to_slot(Ctx& C, const WorkDev& W, int slot_buf, const double* v, int nv) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = 0; k < nv; ++k) {
+    double a = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) C.red[warp * kRed + k] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    double a = 0.0;
+    for (int w = 0; w < kBlock / 32; ++w) a += C.red[w * kRed + threadIdx.x];
+    W.partials[((size_t)slot_buf * gridDim.x + blockIdx.x) * kRed + threadIdx.x] = a;
+  }
+}
+
+// Every CTA sums all slots in the same order: identical results everywhere.
+__device__ void grid_reduce_from_slot(Ctx& C, const WorkDev& W, int slot_buf, int nv) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp < nv) {
+    double a = 0.0;
+    for (int c = lane; c < (int)gridDim.x; c += 32)
+      a += W.partials[((size_t)slot_buf * gridDim.x + c) * kRed + warp];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) C.red_out[warp] = a;
+  }
+}
+
+struct Bufs {
+  int slot;   // next partial-slot buffer
+  int vec;    // next published-vector buffer
+};
+
+// Local displacements ut = u + alpha * dx for owned (shared) and halo (global).
+__device__ void load_local_positions(Ctx& C, const MeshDev& M, const WorkDev& W, double alpha) {
+  for (int l = threadIdx.x; l < C.n_loc; l += blockDim.x) {
+    double a0, a1, a2;
+    float d0, d1, d2;
+    if (l < C.n_own) {
+      a0 = C.u[3 * l]; a1 = C.u[3 * l + 1]; a2 = C.u[3 * l + 2];
+      d0 = C.x[3 * l]; d1 = C.x[3 * l + 1]; d2 = C.x[3 * l + 2];
+    } else {
+      const int g = M.halo_nodes[C.halo0 + l - C.n_own];
+      a0 = W.u[3 * g]; a1 = W.u[3 * g + 1]; a2 = W.u[3 * g + 2];
+      const float4 d = W.dpub[g];
+      d0 = d.x; d1 = d.y; d2 = d.z;
+    }
+    if (alpha != 0.0) {
+      a0 = fma(alpha, (double)d0, a0);
+      a1 = fma(alpha, (double)d1, a1);
+      a2 = fma(alpha, (double)d2, a2);
+    }
+    C.ut[3 * l] = a0; C.ut[3 * l + 1] = a1; C.ut[3 * l + 2] = a2;
+  }
+}
+
+// Sum the chunk's corner contributions into owned-node accumulators. Entries
+// of each node are sorted by local tet index, so walking them chunk by chunk
+// keeps one fixed summation order.
+template <int NV, typename T>
+__device__ __forceinline__ void gather_chunk(Ctx& C, int chunk, const T* buf, int c0, T* acc) {
+  const int c1 = c0 + chunk;
+  for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
+    int j = C.cursor[i];
+    const int end = C.lptr[i + 1];
+    T s[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) s[k] = acc[NV * i + k];
+    while (j < end) {
+      const unsigned e = C.lcsr[j];
+      const int lt = (int)(e >> 2);
+      if (lt >= c1) break;
+      const T* src = buf + ((lt - c0) * 4 + (int)(e & 3u)) * NV;
+#pragma unroll
+      for (int k = 0; k < NV; ++k) s[k] += src[k];
+      ++j;
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[NV * i + k] = s[k];
+    C.cursor[i] = j;
+  }
+}
+
+__device__ __forceinline__ void reset_cursors(Ctx& C) {
+  for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) C.cursor[i] = C.lptr[i];
+}
+
+// Indices of the reduced values of an evaluation pass.
+enum { EV_ELASTIC = 0, EV_BAD, EV_CONTACT, EV_RR, EV_FCFC, EV_FX, EV_FY, EV_FZ, EV_ACTIVE, EV_SLOPE, EV_N };
+
+// FP64 energy, residual R = dPi/du and contact at ut = u + alpha*dx. Leaves
+// the owned residual in C.R (unmasked), contact forces in C.fc, the contact
+// Gauss-Newton vectors in C.hc, and the grid sums in C.red_out.
+__device__ bool eval_pass(Ctx& C, const MeshDev& M, const WorkDev& W, const SolveParams& P,
+                          Barrier& gb, Bufs& bf, double alpha, const double org[3], bool want_slope) {
+  load_local_positions(C, M, W, alpha);
+  double sl = 0.0;
+  for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
+    if (want_slope)
+      sl += C.R[3 * i] * (double)C.x[3 * i] + C.R[3 * i + 1] * (double)C.x[3 * i + 1] +
+            C.R[3 * i + 2] * (double)C.x[3 * i + 2];
+    C.R[3 * i] = 0.0; C.R[3 * i + 1] = 0.0; C.R[3 * i + 2] = 0.0;
+  }
+  reset_cursors(C);
+  __syncthreads();
+  double e_el = 0.0, bad = 0.0;
+  const int CH = M.chunk;
+  for (int c0 = 0; c0 < C.n_pt; c0 += CH) {
+    const int c1 = min(c0 + CH, C.n_pt);
+    for (int t = c0 + threadIdx.x; t < c1; t += blockDim.x) {
+      const int e = C.t0 + t;
+      const ushort4 ln = C.ptn[t];
+      const int li[4] = {ln.x, ln.y, ln.z, ln.w};
+      double uu[4][3];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) uu[a][k] = C.ut[3 * li[a] + k];
+      double Dm[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Dm[k] = M.pt_dminv[(size_t)k * M.total_pt + e];
+      const int info = M.pt_info[e];
+      const int mat = info & 0xffff;
+      const double mu = M.lame[2 * mat], lam = M.lame[2 * mat + 1];
+      double f[4][3], energy, J;
+      elem_eval_f64(uu, Dm, M.pt_vol[e], mu, lam, f, energy, J);
+      if (!(J > 0.0) || !isfinite(energy)) bad += 1.0;
+      if (info >> 16) e_el += energy;
+      double* dst = C.chunkd + (size_t)(t - c0) * 12;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dst[3 * a + k] = f[a][k];
+    }
+    __syncthreads();
+    gather_chunk<3, double>(C, CH, C.chunkd, c0, C.R);
+    __syncthreads();
+  }
+  double v[EV_N];
+#pragma unroll
+  for (int k = 0; k < EV_N; ++k) v[k] = 0.0;
+  v[EV_ELASTIC] = e_el;
+  v[EV_BAD] = bad;
+  v[EV_SLOPE] = sl;
+  for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
+    const double kp = C.kp[i];
+    double fcv[3] = {0.0, 0.0, 0.0};
+    float h[3] = {0.f, 0.f, 0.f};
+    if (kp > 0.0) {
+      const double xx[3] = {C.X[3 * i] + C.ut[3 * i], C.X[3 * i + 1] + C.ut[3 * i + 1],
+                            C.X[3 * i + 2] + C.ut[3 * i + 2]};
+      double phi, n[3];
+      indenter_sdf(P.shape, org, P.R, P.iparams, xx, phi, n);
+      if (phi < 0.0) {
+        const double g = kp * phi;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          C.R[3 * i + k] += g * n[k];
+          fcv[k] = -g * n[k];
+        }
+        v[EV_CONTACT] += 0.5 * kp * phi * phi;
+        v[EV_ACTIVE] += 1.0;
+        const float sk = (float)sqrt(kp);
+        h[0] = sk * (float)n[0]; h[1] = sk * (float)n[1]; h[2] = sk * (float)n[2];
+      }
+    }
+    const unsigned mk = C.mask[i];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      C.fc[3 * i + k] = fcv[k];
+      C.hc[3 * i + k] = h[k];
+      if (!(mk & (1u << k))) v[EV_RR] += C.R[3 * i + k] * C.R[3 * i + k];
+      v[EV_FCFC] += fcv[k] * fcv[k];
+    }
+    v[EV_FX] += fcv[0]; v[EV_FY] += fcv[1]; v[EV_FZ] += fcv[2];
+  }
+  block_reduce_to_slot(C, W, bf.slot, v, EV_N);
+  if (!grid_sync(gb, C.flag)) return false;
+  grid_reduce_from_slot(C, W, bf.slot, EV_N);
+  bf.slot ^= 1;
+  __syncthreads();
+  return true;
+}
+
+// FP32 tangent at the current ut (the last evaluated state), stored per part
+// tet, and the block-Jacobi preconditioner of the owned nodes.
+__device__ void tangent_pass(Ctx& C, const MeshDev& M, int mode) {
+  for (int i = threadIdx.x; i < C.n_own; i += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) C.acc[6 * i + k] = 0.f;
+  reset_cursors(C);
+  __syncthreads();
+  const int CH = M.chunk;
+  for (int c0 = 0; c0 < C.n_pt; c0 += CH) {
+    const int c1 = min(c0 + CH, C.n_pt);
+    for (int t = c0 + threadIdx.x; t < c1; t += blockDim.x) {
+      const int e = C.t0 + t;
+      const ushort4 ln = C.ptn[t];
+      const int li[4] = {ln.x, ln.y, ln.z, ln.w};
+      float Ds[3][3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) Ds[k][c] = (float)(C.ut[3 * li[c + 1] + k] - C.ut[3 * li[0] + k]);
+      float Dm[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Dm[k] = (float)M.pt_dminv[(size_t)k * M.total_pt + e];
+      float F[9];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+          F[3 * i + j] = (i == j ? 1.f : 0.f) + Ds[i][0] * Dm[j] + Ds[i][1] * Dm[3 + j] + Ds[i][2] * Dm[6 + j];
+      const int mat = M.pt_info[e] & 0xffff;
+      float T[32];
+      float dg[4][6];
+      tangent_build(F, (float)M.lame[2 * mat], (float)M.lame[2 * mat + 1], (float)M.pt_vol[e], Dm,
+                    mode, T, dg);
+      T[30] = 0.f; T[31] = 0.f;
+#pragma unroll
+      for (int g = 0; g < kTanVec; ++g)
+        C.tan[(size_t)g * C.tan_stride + t] = make_float4(T[4 * g], T[4 * g + 1], T[4 * g + 2], T[4 * g + 3]);
+      float* dst = C.chunkf + (size_t)(t - c0) * 24;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) dst[6 * a + k] = dg[a][k];
+    }
+    __syncthreads();
+    gather_chunk<6, float>(C, CH, C.chunkf, c0, C.acc);
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
+    float m[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) m[k] = C.acc[6 * i + k];
+    const float h0 = C.hc[3 * i], h1 = C.hc[3 * i + 1], h2 = C.hc[3 * i + 2];
+    m[0] += h0 * h0; m[1] += h0 * h1; m[2] += h0 * h2;
+    m[3] += h1 * h1; m[4] += h1 * h2; m[5] += h2 * h2;
+    inv_block_masked(m, C.mask[i], C.minv + 6 * i);
+  }
+  __syncthreads();
+}
+
+// acc (3 per owned node) = element tangent applied to the local vector lm.
+__device__ void matvec_pass(Ctx& C, const MeshDev& M) {
+  for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
+    C.acc[3 * i] = 0.f; C.acc[3 * i + 1] = 0.f; C.acc[3 * i + 2] = 0.f;
+  }
+  reset_cursors(C);
+  __syncthreads();
+  const int CH = M.chunk;
+  for (int c0 = 0; c0 < C.n_pt; c0 += CH) {
+    const int c1 = min(c0 + CH, C.n_pt);
+    for (int t = c0 + threadIdx.x; t < c1; t += blockDim.x) {
+      const ushort4 ln = C.ptn[t];
+      float T[32];
+#pragma unroll
+      for (int g = 0; g < kTanVec; ++g) {
+        const float4 v = C.tan[(size_t)g * C.tan_stride + t];
+        T[4 * g] = v.x; T[4 * g + 1] = v.y; T[4 * g + 2] = v.z; T[4 * g + 3] = v.w;
+      }
+      float p[4][3];
+      const int li[4] = {ln.x, ln.y, ln.z, ln.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const float4 q = C.lm[li[a]];
+        p[a][0] = q.x; p[a][1] = q.y; p[a][2] = q.z;
+      }
+      float y[4][3];
+      tangent_apply(T, p, y);
+      float* dst = C.chunkf + (size_t)(t - c0) * 12;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dst[3 * a + k] = y[a][k];
+    }
+    __syncthreads();
+    gather_chunk<3, float>(C, CH, C.chunkf, c0, C.acc);
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ void apply_minv(const float* mi, const float v[3], float out[3]) {
+  out[0] = mi[0] * v[0] + mi[1] * v[1] + mi[2] * v[2];
+  out[1] = mi[1] * v[0] + mi[3] * v[1] + mi[4] * v[2];
+  out[2] = mi[2] * v[0] + mi[4] * v[1] + mi[5] * v[2];
+}
+
+// Contact Gauss-Newton term and Dirichlet mask on the owned product.
+__device__ __forceinline__ void finish_product(const Ctx& C, int i, const float v[3], float out[3]) {
+  const float h0 = C.hc[3 * i], h1 = C.hc[3 * i + 1], h2 = C.hc[3 * i + 2];
+  const float hv = h0 * v[0] + h1 * v[1] + h2 * v[2];
+  const unsigned mk = C.mask[i];
+  out[0] = (mk & 1u) ? 0.f : C.acc[3 * i] + h0 * hv;
+  out[1] = (mk & 2u) ? 0.f : C.acc[3 * i + 1] + h1 * hv;
+  out[2] = (mk & 4u) ? 0.f : C.acc[3 * i + 2] + h2 * hv;
+}
+
+__device__ void load_halo_vector(Ctx& C, const MeshDev& M, const WorkDev& W, int buf) {
+  const float4* src = W.vpub + (size_t)buf * M.n_nodes;
+  for (int l = C.n_own + threadIdx.x; l < C.n_loc; l += blockDim.x)
+    C.lm[l] = src[M.halo_nodes[C.halo0 + l - C.n_own]];
+}
+
+// Preconditioned pipelined CG on K dx = -R_free. Leaves dx in C.x (owned).
+// Returns false if a barrier was abandoned; iters receives the iteration count
+// and neg_curv whether it stopped on a non-positive curvature.
+__device__ bool pcg(Ctx& C, const MeshDev& M, const WorkDev& W, const SolveParams& P, Barrier& gb,
+                    Bufs& bf, double eta, double abs_tol, int& iters, bool& neg_curv) {
+  long long t = tick(C);
+  neg_curv = false;
+  // r0 = -R_free, u0 = M^-1 r0, publish u0
+  float4* pub = W.vpub + (size_t)bf.vec * M.n_nodes;
+  for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
+    const unsigned mk = C.mask[i];
+    float r[3], uu[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      r[k] = (mk & (1u << k)) ? 0.f : (float)(-C.R[3 * i + k]);
+      C.r[3 * i + k] = r[k];
+      C.x[3 * i + k] = 0.f;
+      C.z[3 * i + k] = 0.f; C.q[3 * i + k] = 0.f; C.s[3 * i + k] = 0.f; C.p[3 * i + k] = 0.f;
+    }
+    apply_minv(C.minv + 6 * i, r, uu);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) C.ucg[3 * i + k] = uu[k];
+    const float4 v4 = make_float4(uu[0], uu[1], uu[2], 0.f);
+    C.lm[i] = v4;
+    pub[C.node0 + i] = v4;
+  }
+  if (!grid_sync(gb, C.flag)) return false;
+  load_halo_vector(C, M, W, bf.vec);
+  bf.vec ^= 1;
+  __syncthreads();
+  matvec_pass(C, M);
+  // w0 = A u0, m0 = M^-1 w0, partials (r,u) (w,u) (r,r)
+  pub = W.vpub + (size_t)bf.vec * M.n_nodes;
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
+    const float uu[3] = {C.ucg[3 * i], C.ucg[3 * i + 1], C.ucg[3 * i + 2]};
+    float w[3], m[3];
+    finish_product(C, i, uu, w);
+    apply_minv(C.minv + 6 * i, w, m);
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      C.w[3 * i + k] = w[k];
+      const float rk = C.r[3 * i + k];
+      s0 += rk * uu[k];
+      s1 += w[k] * uu[k];
+      s2 += rk * rk;
+    }
+    v[0] += (double)s0; v[1] += (double)s1; v[2] += (double)s2;
+    const float4 m4 = make_float4(m[0], m[1], m[2], 0.f);
+    C.lm[i] = m4;
+    pub[C.node0 + i] = m4;
+  }
+  block_reduce_to_slot(C, W, bf.slot, v, 3);
+  if (!grid_sync(gb, C.flag)) return false;
+  tock(C, PH_CG_INIT, t);
+  double gamma_prev = 1.0, alpha_prev = 1.0, rr0 = 0.0;
+  int it = 0;
+  for (;; ++it) {
+    grid_reduce_from_slot(C, W, bf.slot, 3);
+    load_halo_vector(C, M, W, bf.vec);
+    bf.slot ^= 1;
+    bf.vec ^= 1;
+    __syncthreads();
+    tock(C, PH_CG_REDUCE, t);
+    const double gamma = C.red_out[0], delta = C.red_out[1], rr = C.red_out[2];
+    if (it == 0) rr0 = rr;
+    double beta = 0.0, alpha;
+    if (it == 0) {
+      alpha = gamma / delta;
+    } else {
+      beta = gamma / gamma_prev;
+      alpha = gamma / (delta - beta * gamma / alpha_prev);
+    }
+    const double denom = it == 0 ? delta : (delta - beta * gamma / alpha_prev);
+    const bool converged = rr <= eta * eta * rr0 || rr <= abs_tol * abs_tol;
+    const bool breakdown = !(denom > 0.0) || !isfinite(alpha) || !isfinite(rr);
+    if (converged || breakdown || it >= P.max_cg) {
+      neg_curv = breakdown && !converged;
+      if (breakdown && it == 0 && !(rr <= abs_tol * abs_tol)) {
+        // non-positive curvature on the first direction: take the
+        // preconditioned steepest-descent direction u0 (== C.ucg at it 0)
+        for (int i = threadIdx.x; i < C.n_own; i += blockDim.x)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) C.x[3 * i + k] = C.ucg[3 * i + k];
+        __syncthreads();
+      }
+      break;
+    }
+    gamma_prev = gamma;
+    alpha_prev = alpha;
+    matvec_pass(C, M);   // n = A m (m in C.lm)
+    tock(C, PH_CG_MATVEC, t);
+    pub = W.vpub + (size_t)bf.vec * M.n_nodes;
+    const float a = (float)alpha, b = (float)beta;
+    double pv[3] = {0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
+      const float4 m4 = C.lm[i];
+      const float m[3] = {m4.x, m4.y, m4.z};
+      float n[3];
+      finish_product(C, i, m, n);
+      float mn[3], wn[3];
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int j = 3 * i + k;
+        const float z = n[k] + b * C.z[j];
+        const float q = m[k] + b * C.q[j];
+        const float s = C.w[j] + b * C.s[j];
+        const float p = C.ucg[j] + b * C.p[j];
+        C.z[j] = z; C.q[j] = q; C.s[j] = s; C.p[j] = p;
+        C.x[j] += a * p;
+        const float r = C.r[j] - a * s;
+        const float uu = C.ucg[j] - a * q;
+        const float w = C.w[j] - a * z;
+        C.r[j] = r; C.ucg[j] = uu; C.w[j] = w;
+        wn[k] = w;
+        s0 += r * uu;
+        s1 += w * uu;
+        s2 += r * r;
+      }
+      apply_minv(C.minv + 6 * i, wn, mn);
+      pv[0] += (double)s0; pv[1] += (double)s1; pv[2] += (double)s2;
+      const float4 o = make_float4(mn[0], mn[1], mn[2], 0.f);
+      C.lm[i] = o;
+      pub[C.node0 + i] = o;
+    }
+    block_reduce_to_slot(C, W, bf.slot, pv, 3);
+    tock(C, PH_CG_UPDATE, t);
+    if (!grid_sync(gb, C.flag)) return false;
+    tock(C, PH_CG_BARRIER, t);
+  }
+  iters = it;
+  return true;
+}
+
+__device__ void publish_u(Ctx& C, const WorkDev& W) {
+  for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
+    const int g = C.node0 + i;
+    W.u[3 * g] = C.u[3 * i]; W.u[3 * g + 1] = C.u[3 * i + 1]; W.u[3 * g + 2] = C.u[3 * i + 2];
+  }
+}
+
+__device__ void publish_dx(Ctx& C, const WorkDev& W) {
+  for (int i = threadIdx.x; i < C.n_own; i += blockDim.x)
+    W.dpub[C.node0 + i] = make_float4(C.x[3 * i], C.x[3 * i + 1], C.x[3 * i + 2], 0.f);
+}
+
+// u <- ut for the owned nodes (the evaluated, accepted state) and publish it.
+__device__ void accept_state(Ctx& C, const WorkDev& W) {
+  for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) C.u[3 * i + k] = C.ut[3 * i + k];
+  }
+  __syncthreads();
+  publish_u(C, W);
+}
+
+__global__ void __launch_bounds__(kBlock, 1) solve_kernel(MeshDev M, WorkDev W, SolveParams P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double s_red_out[kRed];
+  __shared__ int s_flag;
+  if (P.mode == MODE_BARRIER_TEST) {
+    Barrier tb{W.barrier, W.abort_flag, 0ull, P.timeout_ns, gridDim.x};
+    if (blockIdx.x == 0) return;   // never arrives: the others must time out
+    grid_sync(tb, &s_flag);
+    return;
+  }
+  const SmemLayout L = smem_layout(M);
+  Ctx C;
+  C.part = blockIdx.x;
+  C.node0 = M.part_node_begin[C.part];
+  C.n_own = M.part_node_begin[C.part + 1] - C.node0;
+  C.halo0 = M.part_halo_begin[C.part];
+  C.n_loc = C.n_own + (M.part_halo_begin[C.part + 1] - C.halo0);
+  C.t0 = M.part_tet_begin[C.part];
+  C.n_pt = M.part_tet_begin[C.part + 1] - C.t0;
+  C.u = reinterpret_cast<double*>(smem + L.u);
+  C.uprev = reinterpret_cast<double*>(smem + L.uprev);
+  C.R = reinterpret_cast<double*>(smem + L.R);
+  C.X = reinterpret_cast<double*>(smem + L.X);
+  C.fc = reinterpret_cast<double*>(smem + L.fc);
+  C.kp = reinterpret_cast<double*>(smem + L.kp);
+  C.ut = reinterpret_cast<double*>(smem + L.ut);
+  C.chunkd = reinterpret_cast<double*>(smem + L.chunk);
+  C.chunkf = reinterpret_cast<float*>(smem + L.chunk);
+  C.red = reinterpret_cast<double*>(smem + L.red);
+  C.x = reinterpret_cast<float*>(smem + L.x);
+  C.r = reinterpret_cast<float*>(smem + L.r);
+  C.ucg = reinterpret_cast<float*>(smem + L.ucg);
+  C.w = reinterpret_cast<float*>(smem + L.w);
+  C.z = reinterpret_cast<float*>(smem + L.z);
+  C.q = reinterpret_cast<float*>(smem + L.q);
+  C.s = reinterpret_cast<float*>(smem + L.s);
+  C.p = reinterpret_cast<float*>(smem + L.p);
+  C.acc = reinterpret_cast<float*>(smem + L.acc);
+  C.minv = reinterpret_cast<float*>(smem + L.minv);
+  C.hc = reinterpret_cast<float*>(smem + L.hc);
+  C.lm = reinterpret_cast<float4*>(smem + L.lm);
+  C.mask = reinterpret_cast<unsigned char*>(smem + L.mask);
+  C.cursor = reinterpret_cast<int*>(smem + L.cursor);
+  C.red_out = s_red_out;
+  C.flag = &s_flag;
+  C.timer = blockIdx.x == 0 && threadIdx.x == 0;
+#pragma unroll
+  for (int k = 0; k < PH_N; ++k) C.cyc[k] = 0;
+  const long long t_start = tick(C);
+  if (M.resident) {
+    // part tet ids and local CSR copied into shared memory once
+    ushort4* ptn = reinterpret_cast<ushort4*>(smem + L.ptn);
+    int* lptr = reinterpret_cast<int*>(smem + L.lptr);
+    unsigned* lcsr = reinterpret_cast<unsigned*>(smem + L.lcsr);
+    const int base = M.lcsr_ptr[C.node0];
+    const int n_ent = M.lcsr_ptr[C.node0 + C.n_own] - base;
+    for (int t = threadIdx.x; t < C.n_pt; t += blockDim.x) ptn[t] = M.pt_nodes[C.t0 + t];
+    for (int i = threadIdx.x; i <= C.n_own; i += blockDim.x) lptr[i] = M.lcsr_ptr[C.node0 + i] - base;
+    for (int j = threadIdx.x; j < n_ent; j += blockDim.x) lcsr[j] = M.lcsr[base + j];
+    C.ptn = ptn;
+    C.lptr = lptr;
+    C.lcsr = lcsr;
+    C.tan = reinterpret_cast<float4*>(smem + L.tan);
+    C.tan_stride = M.max_pt;
+  } else {
+    C.ptn = M.pt_nodes + C.t0;
+    C.lptr = M.lcsr_ptr + C.node0;
+    C.lcsr = M.lcsr;
+    C.tan = W.tangent + C.t0;
+    C.tan_stride = M.total_pt;
+  }
+
+  Barrier gb{W.barrier, W.abort_flag, 0ull, P.timeout_ns, gridDim.x};
+
+  for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
+    const int g = C.node0 + i;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      C.X[3 * i + k] = M.X[3 * g + k];
+      C.u[3 * i + k] = W.u[3 * g + k];
+      C.uprev[3 * i + k] = C.u[3 * i + k];
+      C.x[3 * i + k] = 0.f;
+      C.R[3 * i + k] = 0.0;
+    }
+    C.mask[i] = M.fixmask[g];
+    C.kp[i] = M.kbase[g] * P.c_kappa;
+  }
+  __syncthreads();
+  Bufs bf{0, 0};
+  StatsDev* st = W.stats;
+  const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+
+  if (P.mode == MODE_EVAL || P.mode == MODE_APPLY) {
+    double org[3];
+    const double d = P.step > 0 ? P.depths[P.step - 1] : 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) org[k] = P.origin[k] + d * P.dir[k];
+    if (!eval_pass(C, M, W, P, gb, bf, 0.0, org, false)) return;
+    if (P.mode == MODE_EVAL) {
+      for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
+        const int g = C.node0 + i;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          W.out_R[3 * g + k] = C.R[3 * i + k];
+          W.out_fc[3 * g + k] = C.fc[3 * i + k];
+        }
+      }
+      if (leader) {
+        st->elastic = C.red_out[EV_ELASTIC];
+        st->contact_energy = C.red_out[EV_CONTACT];
+        st->residual = sqrt(C.red_out[EV_RR]);
+        st->active = (int)C.red_out[EV_ACTIVE];
+        st->status = C.red_out[EV_BAD] > 0.0 ? ST_NONFINITE : ST_OK;
+      }
+      return;
+    }
+    tangent_pass(C, M, P.tangent_mode == 2 ? 0 : P.tangent_mode);
+    for (int l = threadIdx.x; l < C.n_loc; l += blockDim.x) {
+      const int g = local_to_global(C, M, l);
+      const unsigned mk = M.fixmask[g];
+      C.lm[l] = make_float4((mk & 1u) ? 0.f : (float)W.in_p[3 * g], (mk & 2u) ? 0.f : (float)W.in_p[3 * g + 1],
+                            (mk & 4u) ? 0.f : (float)W.in_p[3 * g + 2], 0.f);
+    }
+    __syncthreads();
+    matvec_pass(C, M);
+    for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
+      const float4 q = C.lm[i];
+      const float v[3] = {q.x, q.y, q.z};
+      float y[3];
+      finish_product(C, i, v, y);
+      const int g = C.node0 + i;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) W.out_y[3 * g + k] = y[k];
+    }
+    if (leader) st->status = ST_OK;
+    return;
+  }
+
+  // ---------------------------------------------------------------- solve
+  int status = ST_OK;
+  int newton_total = 0, cg_total = 0, bt_total = 0, exact_total = 0;
+  double rn = 0.0, scale = 1.0, energy = 0.0;
+  int steps_done = 0;
+  for (int step = 1; step <= P.n_steps; ++step) {
+    double org[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) org[k] = P.origin[k] + P.depths[step - 1] * P.dir[k];
+    if (P.has_presc) {
+      const double ramp = (double)step / (double)P.n_steps;
+      for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
+        const unsigned mk = C.mask[i];
+        const int g = C.node0 + i;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+          if (mk & (1u << k)) C.u[3 * i + k] = W.u_presc[3 * g + k] * ramp;
+      }
+    }
+    // secant predictor: start from u_{k-1} + r (u_{k-1} - u_{k-2}), r the ratio
+    // of depth increments; kept only if every tet stays valid
+    double ratio = 0.0;
+    if (step >= 2) {
+      const double d2 = P.depths[step - 1] - P.depths[step - 2];
+      const double d1 = P.depths[step - 2] - (step >= 3 ? P.depths[step - 3] : 0.0);
+      ratio = d1 != 0.0 ? d2 / d1 : 0.0;
+    }
+    for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
+      const unsigned mk = C.mask[i];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        C.x[3 * i + k] = (mk & (1u << k)) ? 0.f : (float)(C.u[3 * i + k] - C.uprev[3 * i + k]);
+        C.uprev[3 * i + k] = C.u[3 * i + k];
+      }
+    }
+    __syncthreads();
+    publish_u(C, W);
+    publish_dx(C, W);
+    if (!grid_sync(gb, C.flag)) return;
+    long long t0 = tick(C);
+    bool have_state = false;
+    if (ratio > 0.0) {
+      if (!eval_pass(C, M, W, P, gb, bf, ratio, org, false)) return;
+      if (C.red_out[EV_BAD] == 0.0 && isfinite(C.red_out[EV_ELASTIC] + C.red_out[EV_CONTACT]) &&
+          isfinite(C.red_out[EV_RR])) {
+        accept_state(C, W);
+        have_state = true;
+        if (!grid_sync(gb, C.flag)) return;
+      }
+    }
+    if (!have_state) {
+      if (!eval_pass(C, M, W, P, gb, bf, 0.0, org, false)) return;
+      if (C.red_out[EV_BAD] > 0.0) { status = ST_NONFINITE; break; }
+    }
+    tock(C, PH_EVAL, t0);
+    energy = C.red_out[EV_ELASTIC] + C.red_out[EV_CONTACT];
+    rn = sqrt(C.red_out[EV_RR]);
+    scale = fmax(sqrt(C.red_out[EV_FCFC]), M.scale_floor);
+    double fs[3] = {C.red_out[EV_FX], C.red_out[EV_FY], C.red_out[EV_FZ]};
+    int active = (int)C.red_out[EV_ACTIVE];
+    double rn_prev = rn;
+    const double rn_step0 = rn;
+    int it = 0, cg_step = 0;
+    bool ok = false;
+    bool use_exact = P.tangent_mode == 1;
+    bool exact_banned = false;
+    for (;;) {
+      if (!isfinite(rn)) { status = ST_NONFINITE; break; }
+      if (rn <= P.tol * scale) { ok = true; break; }
+      if (it >= P.max_newton) { status = ST_NOT_CONVERGED; break; }
+      const int mode = P.tangent_mode == 3 ? 3 : (use_exact ? 1 : 0);
+      long long t = tick(C);
+      tangent_pass(C, M, mode);
+      tock(C, PH_TANGENT, t);
+      double eta = P.cg_rtol_max;
+      if (it > 0) {
+        const double q = rn / rn_prev;
+        eta = fmin(P.cg_rtol_max, fmax(P.cg_rtol_min, 0.9 * q * q));
+      }
+      int cg_it = 0;
+      bool neg_curv = false;
+      if (!pcg(C, M, W, P, gb, bf, eta, 0.1 * P.tol * scale, cg_it, neg_curv)) return;
+      cg_step += cg_it;
+      ++it;
+      if (mode == 1) ++exact_total;
+      publish_dx(C, W);
+      if (!grid_sync(gb, C.flag)) return;
+      t = tick(C);
+      double alpha = 1.0, slope = 0.0;
+      bool accepted = false;
+      for (int bt = 0; bt <= P.max_backtracks; ++bt) {
+        if (!eval_pass(C, M, W, P, gb, bf, alpha, org, bt == 0)) return;
+        if (bt == 0) {
+          slope = C.red_out[EV_SLOPE];
+          if (!(slope < 0.0) && mode == 1) break;   // exact direction is not a descent direction
+        }
+        const double et = C.red_out[EV_ELASTIC] + C.red_out[EV_CONTACT];
+        const bool valid = C.red_out[EV_BAD] == 0.0 && isfinite(et) && isfinite(C.red_out[EV_RR]);
+        if (valid && (rn <= 1e-3 * scale || et <= energy + 1e-4 * alpha * slope)) {
+          accepted = true;
+          energy = et;
+          break;
+        }
+        alpha *= 0.5;
+        ++bt_total;
+      }
+      tock(C, PH_EVAL, t);
+      if (!accepted) {
+        if (mode != 1) { status = ST_LINESEARCH; break; }
+        // exact tangent failed: restore the state at u and continue projected
+        use_exact = false;
+        exact_banned = true;
+        if (!eval_pass(C, M, W, P, gb, bf, 0.0, org, false)) return;
+        continue;
+      }
+      accept_state(C, W);
+      rn_prev = rn;
+      rn = sqrt(C.red_out[EV_RR]);
+      scale = fmax(sqrt(C.red_out[EV_FCFC]), M.scale_floor);
+      fs[0] = C.red_out[EV_FX]; fs[1] = C.red_out[EV_FY]; fs[2] = C.red_out[EV_FZ];
+      active = (int)C.red_out[EV_ACTIVE];
+      if (P.tangent_mode == 2) {
+        // exact tangent once the step is in its asymptotic regime; back to the
+        // projected one for the rest of the step if it misbehaves
+        if (use_exact && (neg_curv || alpha < 1.0)) {
+          use_exact = false;
+          exact_banned = true;
+        } else if (!use_exact && !exact_banned && rn <= 1e-2 * rn_step0) {
+          use_exact = true;
+        }
+      }
+    }
+    newton_total += it;
+    cg_total += cg_step;
+    if (leader) {
+      st->newton_per_step[step - 1] = it;
+      st->cg_per_step[step - 1] = cg_step;
+      st->residual_per_step[step - 1] = rn;
+      W.step_force[3 * (step - 1)] = fs[0];
+      W.step_force[3 * (step - 1) + 1] = fs[1];
+      W.step_force[3 * (step - 1) + 2] = fs[2];
+      st->active = active;
+    }
+    if (!ok) break;
+    steps_done = step;
+  }
+  // outputs: owned displacement and contact forces of the last evaluated state
+  publish_u(C, W);
+  for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
+    const int g = C.node0 + i;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) W.out_fc[3 * g + k] = C.fc[3 * i + k];
+  }
+  if (leader) {
+    st->status = status;
+    st->steps_done = steps_done;
+    st->newton_total = newton_total;
+    st->cg_total = cg_total;
+    st->backtracks_total = bt_total;
+    st->residual = rn;
+    st->scale = scale;
+    st->energy = energy;
+    st->exact_newton = exact_total;
+    C.cyc[PH_TOTAL] = clock64() - t_start;
+#pragma unroll
+    for (int k = 0; k < PH_N; ++k) st->cycles[k] = C.cyc[k];
+  }
+}
+
+__global__ void permute_kernel(const double* __restrict__ src, double* __restrict__ dst,
+                               const int* __restrict__ perm, int n, int to_caller) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int c = perm[i];
+  if (to_caller) {
+    dst[3 * c] = src[3 * i]; dst[3 * c + 1] = src[3 * i + 1]; dst[3 * c + 2] = src[3 * i + 2];
+  } else {
+    dst[3 * i] = src[3 * c]; dst[3 * i + 1] = src[3 * c + 1]; dst[3 * i + 2] = src[3 * c + 2];
+  }
+}
+
+}  // namespace
+
+// Reorder a node vector (3 doubles per node) between the library's Morton
+// numbering and the caller's numbering; perm maps library -> caller index.
+cudaError_t launch_permute(const double* src, double* dst, const int* perm, int n, bool to_caller,
+                           cudaStream_t s) {
+  permute_kernel<<<(n + 255) / 256, 256, 0, s>>>(src, dst, perm, n, to_caller ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t solve_kernel_occupancy(int smem_bytes, int* blocks_per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, solve_kernel, kBlock, smem_bytes);
+}
+
+cudaError_t launch_solve(const MeshDev& mesh, const WorkDev& work, const SolveParams& prm,
+                         cudaStream_t stream, float* kernel_ms) {
+  const SmemLayout L = smem_layout(mesh);
+  cudaError_t e = cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
+  if (e != cudaSuccess) return e;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (kernel_ms) {
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    cudaEventRecord(ev0, stream);
+  }
+  MeshDev m = mesh;
+  WorkDev w = work;
+  SolveParams p = prm;
+  void* args[] = {&m, &w, &p};
+  e = cudaLaunchCooperativeKernel((const void*)solve_kernel, dim3(mesh.n_parts), dim3(kBlock), args,
+                                  (size_t)L.total, stream);
+  if (kernel_ms) {
+    cudaEventRecord(ev1, stream);
+    if (e == cudaSuccess) {
+      cudaError_t s = cudaEventSynchronize(ev1);
+      if (s == cudaSuccess) cudaEventElapsedTime(kernel_ms, ev0, ev1);
+      else e = s;
+    }
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+  }
+  return e;
+}
+
+}  // namespace fem

@@ -1,0 +1,75 @@
+"""CPU-only checks of the C-ABI library: it builds, loads, exports every symbol
+include/fem.h declares, and rejects malformed inputs on the host before any
+CUDA call."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2103_16747_b300 import _lib
+    hdr = open(os.path.join(ROOT, "include", "fem.h")).read()
+    declared = set(re.findall(r"^\s*(?:int|void|const char\*)\s+(fem_\w+)\s*\(", hdr, re.M))
+    assert declared == set(_lib.EXPORTS)
+    raw = ctypes.CDLL(_lib.LIB_PATH)
+    for name in declared:
+        assert hasattr(raw, name), name
+
+
+def test_default_options():
+    from paper_2103_16747_b300 import _lib as L
+    o = L.fem_default_options()
+    assert o.c_kappa == 100.0 and o.max_cg == 2000 and o.tangent == L.FEM_TANGENT_PROJECTED
+
+
+@pytest.mark.parametrize("case", ["index", "repeat", "inverted", "flat", "nan", "material", "mask", "sizes"])
+def test_host_validation(case):
+    from paper_2103_16747_b300 import _lib as L
+    m = W.cube_mesh(2)
+    nodes, tets, mats = m.nodes.copy(), m.tets.copy(), m.materials.copy()
+    fixed, mask = m.fixed_nodes, None
+    want = L.FEM_ERR_ARG
+    if case == "index":
+        tets[3, 1] = len(nodes)
+    elif case == "repeat":
+        tets[0, 1] = tets[0, 0]
+        want = L.FEM_ERR_DEGENERATE_TET
+    elif case == "inverted":
+        tets[0, [2, 3]] = tets[0, [3, 2]]
+        want = L.FEM_ERR_DEGENERATE_TET
+    elif case == "flat":
+        nodes[tets[0, 3]] = nodes[tets[0, 0]] + 0.5 * (nodes[tets[0, 1]] - nodes[tets[0, 0]]) \
+            + 0.5 * (nodes[tets[0, 2]] - nodes[tets[0, 0]])
+        want = L.FEM_ERR_DEGENERATE_TET
+    elif case == "nan":
+        nodes[4, 2] = np.inf
+        want = L.FEM_ERR_NONFINITE
+    elif case == "material":
+        mats[0, 1] = 0.5
+    elif case == "mask":
+        mask = np.full(len(fixed), 9, dtype=np.uint8)
+    elif case == "sizes":
+        tets = tets[:0]
+    with pytest.raises(L.FemError) as ei:
+        L.fem_create_mesh(nodes, tets, m.tet_material[: len(tets)], mats, fixed, mask)
+    assert ei.value.code == want, str(ei.value)
+    assert L.fem_last_error()
+
+
+def test_no_device_is_an_error_not_a_fallback():
+    """Without a GPU the valid call fails loudly with FEM_ERR_CUDA."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2103_16747_b300 import _lib as L
+    m = W.cube_mesh(2)
+    with pytest.raises(L.FemError) as ei:
+        L.fem_create_mesh(m.nodes, m.tets, m.tet_material, m.materials, m.fixed_nodes)
+    assert ei.value.code == L.FEM_ERR_CUDA
