@@ -26,7 +26,7 @@ def test_library_exports_every_declared_symbol():
 def test_default_options():
     from paper_2103_16747_b300 import _lib as L
     o = L.fem_default_options()
-    assert o.c_kappa == 100.0 and o.max_cg == 2000 and o.tangent == L.FEM_TANGENT_PROJECTED
+    assert o.c_kappa == 100.0 and o.max_cg == 2000 and o.tangent == L.FEM_TANGENT_ADAPTIVE
 
 
 @pytest.mark.parametrize("case", ["index", "repeat", "inverted", "flat", "nan", "material", "mask", "sizes"])
