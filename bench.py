@@ -129,7 +129,11 @@ def cpu_oracle_rate(mesh, ind, n_load_steps):
     """Time the oracle (as it stands) on the first n_load_steps of the same
     solve and extrapolate to a full solve by Newton iterations, using the
     oracle's Newton count for the full solve stored in tests/golden."""
-    from threadpoolctl import threadpool_info
+    try:
+        from threadpoolctl import threadpool_info
+    except ImportError:                     # not installed on every host
+        def threadpool_info():
+            return [{"num_threads": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))}]
     from oracle import Problem
     p = Problem(mesh, ind)
     t0 = time.perf_counter()

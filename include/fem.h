@@ -97,10 +97,13 @@ typedef struct {
     double  energy;                         /* final total energy Pi                   */
     double  kernel_ms;                      /* device time of the solve kernel          */
     int32_t exact_newton_iters;             /* Newton iterations on the exact tangent   */
-    double  phase_ms[8];                    /* kernel time split (CTA 0 clock shares):
+    double  phase_ms[10];                   /* kernel time split (CTA 0 clock shares):
                                                eval, tangent, pcg init, pcg reduce+halo,
                                                pcg tangent product, pcg vector update,
-                                               pcg grid barrier, total                 */
+                                               pcg grid barrier, total, pcg scalars,
+                                               pcg gather                              */
+    double  phase_max_ms[10];               /* the same phases, largest over CTAs       */
+    double  phase_min_ms[10];               /* the same phases, smallest over CTAs      */
     int32_t newton_per_step[FEM_MAX_STEPS];
     int32_t cg_per_step[FEM_MAX_STEPS];
     double  residual_per_step[FEM_MAX_STEPS];

@@ -32,7 +32,8 @@ ERR_NAMES = {0: "FEM_OK", -1: "FEM_ERR_ARG", -2: "FEM_ERR_DEGENERATE_TET", -3: "
 FEM_SPHERE, FEM_CYLINDER, FEM_BOX, FEM_PLANE = 0, 1, 2, 3
 FEM_MAX_STEPS = 256
 FEM_TANGENT_PROJECTED, FEM_TANGENT_EXACT, FEM_TANGENT_ADAPTIVE, FEM_TANGENT_ABS = 0, 1, 2, 3
-PHASES = ("eval", "tangent", "pcg_init", "pcg_reduce", "pcg_matvec", "pcg_update", "pcg_barrier", "total")
+PHASES = ("eval", "tangent", "pcg_init", "pcg_reduce", "pcg_matvec", "pcg_update", "pcg_barrier", "total",
+          "pcg_scalar", "pcg_gather")
 
 # Every symbol include/fem.h declares.
 EXPORTS = ("fem_default_options", "fem_create_mesh", "fem_set_indenter", "fem_set_dirichlet_values",
@@ -56,7 +57,8 @@ class fem_stats(C.Structure):
                 ("cg_iters", C.c_int32), ("backtracks", C.c_int32), ("active_contacts", C.c_int32),
                 ("residual", C.c_double), ("scale", C.c_double), ("energy", C.c_double),
                 ("kernel_ms", C.c_double), ("exact_newton_iters", C.c_int32),
-                ("phase_ms", C.c_double * 8),
+                ("phase_ms", C.c_double * 10), ("phase_max_ms", C.c_double * 10),
+                ("phase_min_ms", C.c_double * 10),
                 ("newton_per_step", C.c_int32 * FEM_MAX_STEPS),
                 ("cg_per_step", C.c_int32 * FEM_MAX_STEPS),
                 ("residual_per_step", C.c_double * FEM_MAX_STEPS)]

@@ -126,14 +126,45 @@ namespace {
 
 int build_partitions(fem_mesh* m, int n_parts) {
   const int Nn = (int)m->n_nodes, Nt = (int)m->n_tets;
-  // contiguous node ranges balanced by incident-tet count
+  if (n_parts > 256) return fail(FEM_ERR_TOO_LARGE, "at most 256 parts (asked %d)", n_parts);
+  // contiguous node ranges; a part's cost is its unique tets (halo tets
+  // included, each computed once per part) plus its owned nodes. The cut
+  // target is found by bisection so that exactly n_parts ranges result.
   std::vector<int> nb(n_parts + 1, 0);
-  const double total = (double)m->csr_ptr[Nn];
-  int c = 1;
-  for (int i = 0; i < Nn && c < n_parts; ++i) {
-    if ((double)m->csr_ptr[i + 1] >= total * c / n_parts) nb[c++] = i + 1;
+  std::vector<int> stamp(Nt, -1);
+  auto sweep = [&](double target, std::vector<int>* cuts) {
+    int parts = 1, id = 0;
+    double cost = 0.0;
+    if (cuts) (*cuts)[0] = 0;
+    for (int i = 0; i < Nn; ++i) {
+      double add = 0.25;
+      for (int j = m->csr_ptr[i]; j < m->csr_ptr[i + 1]; ++j) {
+        const int t = m->csr_ent[j] >> 2;
+        if (stamp[t] != id) add += 1.0;
+      }
+      if (cost > 0.0 && cost + add > target) {
+        if (cuts && parts < n_parts) (*cuts)[parts] = i;
+        ++parts;
+        ++id;
+        cost = 0.0;
+        add = 0.25;
+        for (int j = m->csr_ptr[i]; j < m->csr_ptr[i + 1]; ++j) add += (stamp[m->csr_ent[j] >> 2] != id) ? 1.0 : 0.0;
+      }
+      for (int j = m->csr_ptr[i]; j < m->csr_ptr[i + 1]; ++j) stamp[m->csr_ent[j] >> 2] = id;
+      cost += add;
+    }
+    std::fill(stamp.begin(), stamp.end(), -1);
+    return parts;
+  };
+  {
+    double lo = 1.0, hi = 8.0 * (double)Nt + Nn;
+    for (int iter = 0; iter < 60; ++iter) {
+      const double mid = 0.5 * (lo + hi);
+      if (sweep(mid, nullptr) > n_parts) lo = mid; else hi = mid;
+    }
+    const int got = sweep(hi, &nb);
+    for (int c = std::min(got, n_parts); c < n_parts; ++c) nb[c] = std::min(Nn, nb[c - 1] + 1);
   }
-  for (; c < n_parts; ++c) nb[c] = std::min(Nn, nb[c - 1] + 1);
   nb[n_parts] = Nn;
   for (int p = 1; p <= n_parts; ++p)
     if (nb[p] <= nb[p - 1]) return fail(FEM_ERR_TOO_LARGE, "cannot cut %d nodes into %d parts", Nn, n_parts);
@@ -142,6 +173,7 @@ int build_partitions(fem_mesh* m, int n_parts) {
     for (int i = nb[p]; i < nb[p + 1]; ++i) part_of[i] = p;
 
   std::vector<int> tb(n_parts + 1, 0), hb(n_parts + 1, 0), halo;
+
   std::vector<ushort4> pt_nodes;
   std::vector<double> pt_dminv_aos, pt_vol;
   std::vector<int> pt_info, pt_tet;
@@ -258,6 +290,8 @@ int build_partitions(fem_mesh* m, int n_parts) {
   double* d_part;
   CUDA_TRY(alloc(&d_tan, (size_t)kTanVec * total_pt, o, by), "alloc tangent");
   CUDA_TRY(alloc(&d_part, (size_t)2 * n_parts * kRed, o, by), "alloc partials");
+  unsigned long long* d_slot;
+  CUDA_TRY(alloc(&d_slot, (size_t)12 * n_parts + 2, o, by), "alloc slots");
   m->bytes += by;
   MeshDev& D = m->dev;
   D.n_parts = n_parts;
@@ -280,6 +314,7 @@ int build_partitions(fem_mesh* m, int n_parts) {
   D.lcsr = d_lcsr;
   m->work.tangent = d_tan;
   m->work.partials = d_part;
+  m->work.cgslot = d_slot;
   m->smem_bytes = L.total;
   CUDA_TRY(cudaStreamSynchronize(s), "partition upload");
   return FEM_OK;
@@ -555,7 +590,7 @@ int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, i
     if ((e = upload(&m->d_perm, m->perm, s, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "upload perm"));
     WorkDev& W = m->work;
     if ((e = alloc(&W.u, 3 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
-    if ((e = alloc(&W.vpub, 2 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
+    if ((e = alloc(&W.vpub, 6 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
     if ((e = alloc(&W.dpub, (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
     unsigned long long* d_bar;
     if ((e = alloc(&d_bar, 2, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
@@ -573,7 +608,7 @@ int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, i
     if ((e = alloc(&m->d_depths, (size_t)kMaxSteps, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
     if ((e = alloc(&m->d_presc, 3 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
     if ((e = cudaMemsetAsync(W.u, 0, 3 * sizeof(double) * Nn, s)) != cudaSuccess) return bail(cuda_fail(e, "memset"));
-    if ((e = cudaMemsetAsync(W.vpub, 0, 2 * sizeof(float4) * Nn, s)) != cudaSuccess) return bail(cuda_fail(e, "memset"));
+    if ((e = cudaMemsetAsync(W.vpub, 0, 6 * sizeof(unsigned long long) * Nn, s)) != cudaSuccess) return bail(cuda_fail(e, "memset"));
     if ((e = cudaMemsetAsync(W.dpub, 0, sizeof(float4) * Nn, s)) != cudaSuccess) return bail(cuda_fail(e, "memset"));
     W.u_presc = m->d_presc;
   }
@@ -719,7 +754,12 @@ static int fill_params(fem_mesh* m, const fem_options* opt, int mode, int steps,
 static int run_kernel(fem_mesh* m, const SolveParams& P, float* ms, StatsDev* hst) {
   cudaStream_t s = m->stream;
   CUDA_TRY(cudaMemsetAsync(m->work.barrier, 0, 2 * sizeof(unsigned long long), s), "reset barrier");
+  CUDA_TRY(cudaMemsetAsync(m->work.cgslot, 0, sizeof(unsigned long long) * (12 * (size_t)m->dev.n_parts + 2), s),
+           "reset slots");
+  CUDA_TRY(cudaMemsetAsync(m->work.vpub, 0, sizeof(unsigned long long) * 6 * (size_t)m->n_nodes, s),
+           "reset published vectors");
   CUDA_TRY(cudaMemsetAsync(m->work.stats, 0, sizeof(StatsDev), s), "reset stats");
+  CUDA_TRY(cudaMemsetAsync(m->work.stats->cycles_min, 0x7f, sizeof(long long) * PH_N, s), "reset stats");
   CUDA_TRY(launch_solve(m->dev, m->work, P, s, ms), "solve kernel launch");
   int abort_flag = 0;
   CUDA_TRY(cudaMemcpyAsync(hst, m->work.stats, sizeof(StatsDev), cudaMemcpyDeviceToHost, s), "stats copy");
@@ -780,8 +820,12 @@ int fem_solve(fem_mesh* m, int32_t load_steps, double tol, const fem_options* op
     stats->kernel_ms = ms;
     stats->exact_newton_iters = hst.exact_newton;
     const double tot = (double)hst.cycles[PH_TOTAL];
-    for (int k = 0; k < PH_N && k < 8; ++k)
+    for (int k = 0; k < PH_N && k < 10; ++k)
       stats->phase_ms[k] = tot > 0 ? ms * (double)hst.cycles[k] / tot : 0.0;
+    for (int k = 0; k < PH_N && k < 10; ++k) {
+      stats->phase_max_ms[k] = tot > 0 ? ms * (double)hst.cycles_max[k] / tot : 0.0;
+      stats->phase_min_ms[k] = tot > 0 ? ms * (double)hst.cycles_min[k] / tot : 0.0;
+    }
     for (int k = 0; k < load_steps; ++k) {
       stats->newton_per_step[k] = hst.newton_per_step[k];
       stats->cg_per_step[k] = hst.cg_per_step[k];

@@ -47,12 +47,14 @@ struct MeshDev {
 
 // Phases timed with clock64 by CTA 0 (shares of the kernel's SM cycles).
 enum Phase : int { PH_EVAL = 0, PH_TANGENT, PH_CG_INIT, PH_CG_REDUCE, PH_CG_MATVEC, PH_CG_UPDATE,
-                   PH_CG_BARRIER, PH_TOTAL, PH_N };
+                   PH_CG_BARRIER, PH_TOTAL, PH_CG_SCALAR, PH_CG_GATHER, PH_N };
 
 struct StatsDev {
   int status, steps_done, newton_total, cg_total, backtracks_total, active, exact_newton;
   double residual, scale, energy, elastic, contact_energy;
   long long cycles[PH_N];
+  long long cycles_max[PH_N];       // largest per-CTA value of each phase
+  long long cycles_min[PH_N];       // smallest per-CTA value of each phase
   int newton_per_step[kMaxSteps];
   int cg_per_step[kMaxSteps];
   double residual_per_step[kMaxSteps];
@@ -61,12 +63,14 @@ struct StatsDev {
 struct WorkDev {
   double* u;                        // [3*n_nodes] displacement (published copy)
   const double* u_presc;            // [3*n_nodes] prescribed values (or null)
-  float4* vpub;                     // [2][n_nodes] published PCG vector (double buffered)
+  unsigned long long* vpub;         // [2][n_nodes][3] published PCG vector, (epoch, FP32) words
   float4* dpub;                     // [n_nodes] published Newton direction
   float4* tangent;                  // [kTanVec][total_pt]
   double* partials;                 // [2][P][kRed]
   unsigned long long* barrier;      // grid barrier arrival counter
   int* abort_flag;                  // set when any CTA gives up waiting
+  unsigned long long* cgslot;       // [2][P][6 words] PCG dot-product partials (FP32 pairs), then
+                                    // the arrival counter (1 word)
   double* out_R;                    // [3*n_nodes] (MODE_EVAL)
   double* out_fc;                   // [3*n_nodes] nodal contact force at the end
   double* out_y;                    // [3*n_nodes] (MODE_APPLY)
@@ -130,7 +134,7 @@ __host__ __device__ inline SmemLayout smem_layout(int max_own, int max_loc, int 
   L.lptr = take(res_pt ? 4 * (max_own + 1) : 0);
   L.lcsr = take(4 * res_lcsr);
   L.mask = take(max_own);
-  L.cursor = take(4 * max_own);
+  L.cursor = take(4 * 6 * max_own);               // one cursor per (node, component)
   L.total = o;
   return L;
 }

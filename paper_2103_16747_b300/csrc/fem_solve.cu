@@ -38,6 +38,10 @@ __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned lon
   return *reinterpret_cast<const volatile unsigned long long*>(p);
 }
 
+__device__ __forceinline__ int ld_volatile_i32(const int* p) {
+  return *reinterpret_cast<const volatile int*>(p);
+}
+
 struct Barrier {
   unsigned long long* counter;
   int* abort_flag;
@@ -86,6 +90,9 @@ struct Ctx {
   unsigned char* mask;
   int* cursor;
   double* red_out;        // broadcast area for grid reductions (kRed doubles)
+  float2* red_df;         // FP32-pair grid sums of the PCG (kRed)
+  float* coef;            // PCG alpha, beta broadcast by thread 0
+  int* decision;          // per-warp wait results of the slot reduction
   int* flag;
   bool timer;             // CTA 0, thread 0 accumulates phase cycles
   long long cyc[PH_N];
@@ -104,13 +111,86 @@ __device__ __forceinline__ int local_to_global(const Ctx& C, const MeshDev& M, i
   return l < C.n_own ? C.node0 + l : M.halo_nodes[C.halo0 + l - C.n_own];
 }
 
-// Deterministic CTA reduction of nv per-thread doubles into a W.partials slot.
+// Compensated FP32 pair ("double-float", two-sum): about 44 significant bits
+// from FP32 adds only. Used inside a CTA, where FP64 instructions would run on
+// B300's narrow FP64 pipe.
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float err = (a.hi - (s - bb)) + (b.hi - bb);
+  const float lo = err + a.lo + b.lo;
+  const float hi = s + lo;
+  return DF{hi, lo - (hi - s)};
+}
+
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e += a.hi * b.lo + a.lo * b.hi;
+  const float hi = p + e;
+  return DF{hi, e - (hi - p)};
+}
+
+__device__ __forceinline__ DF df_div(DF a, DF b) {
+  const float q1 = a.hi / b.hi;
+  const DF r = df_add(a, df_neg(df_mul(DF{q1, 0.f}, b)));
+  const float q2 = r.hi / b.hi;
+  const float hi = q1 + q2;
+  return DF{hi, q2 - (hi - q1)};
+}
+
+// Deterministic CTA reduction of nv per-thread FP32 values (each thread's
+// share) into a W.partials slot: two-sum tree in a fixed order, one FP64
+// conversion per value at the end.
+template <int NV>
+__device__ void block_reduce_df(Ctx& C, const float* v, int active_warps) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float2* red = reinterpret_cast<float2*>(C.red);
+  if (warp < active_warps) {
+    DF a[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) a[k] = DF{v[k], 0.f};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        const DF b{__shfl_xor_sync(0xffffffffu, a[k].hi, o), __shfl_xor_sync(0xffffffffu, a[k].lo, o)};
+        a[k] = (lane & o) ? df_add(b, a[k]) : df_add(a[k], b);
+      }
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) red[warp * kRed + k] = make_float2(a[k].hi, a[k].lo);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    DF a{0.f, 0.f};
+    for (int w = 0; w < active_warps; ++w) {
+      const float2 b = red[w * kRed + threadIdx.x];
+      a = df_add(a, DF{b.x, b.y});
+    }
+    C.red_df[threadIdx.x] = make_float2(a.hi, a.lo);
+  }
+  __syncthreads();
+}
+
+// Deterministic CTA reduction of nv per-thread doubles into a W.partials slot
+// (warps whose values are all zero skip the FP64 shuffles).
 __device__ void block_reduce_to_slot(Ctx& C, const WorkDev& W, int slot_buf, const double* v, int nv) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int k = 0; k < nv; ++k) {
     double a = v[k];
+    if (__any_sync(0xffffffffu, a != 0.0)) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    }
     if (lane == 0) C.red[warp * kRed + k] = a;
   }
   __syncthreads();
@@ -162,35 +242,48 @@ __device__ void load_local_positions(Ctx& C, const MeshDev& M, const WorkDev& W,
   }
 }
 
-// Sum the chunk's corner contributions into owned-node accumulators. Entries
-// of each node are sorted by local tet index, so walking them chunk by chunk
-// keeps one fixed summation order.
+// Sum the chunk's corner contributions into owned-node accumulators, one
+// thread per (node, component). Chunk layout: value k of corner a of chunk tet
+// tl at buf[(a * NV + k) * CH + tl]. Entries of each node are sorted by local
+// tet index, so walking them chunk by chunk keeps one fixed summation order.
 template <int NV, typename T>
-__device__ __forceinline__ void gather_chunk(Ctx& C, int chunk, const T* buf, int c0, T* acc) {
-  const int c1 = c0 + chunk;
-  for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
-    int j = C.cursor[i];
+__device__ __forceinline__ void gather_chunk(Ctx& C, int CH, const T* buf, int c0, T* acc, bool single) {
+  if (single) {
+    // whole part in one chunk: every entry belongs to it, no cursor needed
+    for (int idx = threadIdx.x; idx < C.n_own * NV; idx += blockDim.x) {
+      const int i = idx / NV, k = idx - i * NV;
+      const int j0 = C.lptr[i], j1 = C.lptr[i + 1];
+      const T* col = buf + k * CH;
+      T s = acc[idx];
+#pragma unroll 4
+      for (int j = j0; j < j1; ++j) {
+        const unsigned e = C.lcsr[j];
+        s += col[(int)(e & 3u) * NV * CH + (int)(e >> 2)];
+      }
+      acc[idx] = s;
+    }
+    return;
+  }
+  const int c1 = c0 + CH;
+  for (int idx = threadIdx.x; idx < C.n_own * NV; idx += blockDim.x) {
+    const int i = idx / NV, k = idx - i * NV;
+    int j = C.cursor[idx];
     const int end = C.lptr[i + 1];
-    T s[NV];
-#pragma unroll
-    for (int k = 0; k < NV; ++k) s[k] = acc[NV * i + k];
+    T s = acc[idx];
     while (j < end) {
       const unsigned e = C.lcsr[j];
       const int lt = (int)(e >> 2);
       if (lt >= c1) break;
-      const T* src = buf + ((lt - c0) * 4 + (int)(e & 3u)) * NV;
-#pragma unroll
-      for (int k = 0; k < NV; ++k) s[k] += src[k];
+      s += buf[((int)(e & 3u) * NV + k) * CH + (lt - c0)];
       ++j;
     }
-#pragma unroll
-    for (int k = 0; k < NV; ++k) acc[NV * i + k] = s[k];
-    C.cursor[i] = j;
+    acc[idx] = s;
+    C.cursor[idx] = j;
   }
 }
 
-__device__ __forceinline__ void reset_cursors(Ctx& C) {
-  for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) C.cursor[i] = C.lptr[i];
+__device__ __forceinline__ void reset_cursors(Ctx& C, int nv) {
+  for (int idx = threadIdx.x; idx < C.n_own * nv; idx += blockDim.x) C.cursor[idx] = C.lptr[idx / nv];
 }
 
 // Indices of the reduced values of an evaluation pass.
@@ -209,10 +302,11 @@ __device__ bool eval_pass(Ctx& C, const MeshDev& M, const WorkDev& W, const Solv
             C.R[3 * i + 2] * (double)C.x[3 * i + 2];
     C.R[3 * i] = 0.0; C.R[3 * i + 1] = 0.0; C.R[3 * i + 2] = 0.0;
   }
-  reset_cursors(C);
+  const int CH = M.chunk;
+  const bool single = CH >= C.n_pt;
+  if (!single) reset_cursors(C, 3);
   __syncthreads();
   double e_el = 0.0, bad = 0.0;
-  const int CH = M.chunk;
   for (int c0 = 0; c0 < C.n_pt; c0 += CH) {
     const int c1 = min(c0 + CH, C.n_pt);
     for (int t = c0 + threadIdx.x; t < c1; t += blockDim.x) {
@@ -234,14 +328,13 @@ __device__ bool eval_pass(Ctx& C, const MeshDev& M, const WorkDev& W, const Solv
       elem_eval_f64(uu, Dm, M.pt_vol[e], mu, lam, f, energy, J);
       if (!(J > 0.0) || !isfinite(energy)) bad += 1.0;
       if (info >> 16) e_el += energy;
-      double* dst = C.chunkd + (size_t)(t - c0) * 12;
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) dst[3 * a + k] = f[a][k];
+        for (int k = 0; k < 3; ++k) C.chunkd[(3 * a + k) * CH + (t - c0)] = f[a][k];
     }
     __syncthreads();
-    gather_chunk<3, double>(C, CH, C.chunkd, c0, C.R);
+    gather_chunk<3, double>(C, CH, C.chunkd, c0, C.R, single);
     __syncthreads();
   }
   double v[EV_N];
@@ -296,9 +389,10 @@ __device__ void tangent_pass(Ctx& C, const MeshDev& M, int mode) {
   for (int i = threadIdx.x; i < C.n_own; i += blockDim.x)
 #pragma unroll
     for (int k = 0; k < 6; ++k) C.acc[6 * i + k] = 0.f;
-  reset_cursors(C);
-  __syncthreads();
   const int CH = M.chunk;
+  const bool single = CH >= C.n_pt;
+  if (!single) reset_cursors(C, 6);
+  __syncthreads();
   for (int c0 = 0; c0 < C.n_pt; c0 += CH) {
     const int c1 = min(c0 + CH, C.n_pt);
     for (int t = c0 + threadIdx.x; t < c1; t += blockDim.x) {
@@ -328,14 +422,13 @@ __device__ void tangent_pass(Ctx& C, const MeshDev& M, int mode) {
 #pragma unroll
       for (int g = 0; g < kTanVec; ++g)
         C.tan[(size_t)g * C.tan_stride + t] = make_float4(T[4 * g], T[4 * g + 1], T[4 * g + 2], T[4 * g + 3]);
-      float* dst = C.chunkf + (size_t)(t - c0) * 24;
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int k = 0; k < 6; ++k) dst[6 * a + k] = dg[a][k];
+        for (int k = 0; k < 6; ++k) C.chunkf[(6 * a + k) * CH + (t - c0)] = dg[a][k];
     }
     __syncthreads();
-    gather_chunk<6, float>(C, CH, C.chunkf, c0, C.acc);
+    gather_chunk<6, float>(C, CH, C.chunkf, c0, C.acc, single);
     __syncthreads();
   }
   for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
@@ -351,13 +444,14 @@ __device__ void tangent_pass(Ctx& C, const MeshDev& M, int mode) {
 }
 
 // acc (3 per owned node) = element tangent applied to the local vector lm.
-__device__ void matvec_pass(Ctx& C, const MeshDev& M) {
+__device__ void matvec_pass(Ctx& C, const MeshDev& M, long long* tp = nullptr) {
   for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
     C.acc[3 * i] = 0.f; C.acc[3 * i + 1] = 0.f; C.acc[3 * i + 2] = 0.f;
   }
-  reset_cursors(C);
-  __syncthreads();
   const int CH = M.chunk;
+  const bool single = CH >= C.n_pt;
+  if (!single) reset_cursors(C, 3);
+  __syncthreads();
   for (int c0 = 0; c0 < C.n_pt; c0 += CH) {
     const int c1 = min(c0 + CH, C.n_pt);
     for (int t = c0 + threadIdx.x; t < c1; t += blockDim.x) {
@@ -377,15 +471,16 @@ __device__ void matvec_pass(Ctx& C, const MeshDev& M) {
       }
       float y[4][3];
       tangent_apply(T, p, y);
-      float* dst = C.chunkf + (size_t)(t - c0) * 12;
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) dst[3 * a + k] = y[a][k];
+        for (int k = 0; k < 3; ++k) C.chunkf[(3 * a + k) * CH + (t - c0)] = y[a][k];
     }
     __syncthreads();
-    gather_chunk<3, float>(C, CH, C.chunkf, c0, C.acc);
+    if (tp) tock(C, PH_CG_MATVEC, *tp);
+    gather_chunk<3, float>(C, CH, C.chunkf, c0, C.acc, single);
     __syncthreads();
+    if (tp) tock(C, PH_CG_GATHER, *tp);
   }
 }
 
@@ -405,21 +500,155 @@ __device__ __forceinline__ void finish_product(const Ctx& C, int i, const float 
   out[2] = (mk & 4u) ? 0.f : C.acc[3 * i + 2] + h2 * hv;
 }
 
-__device__ void load_halo_vector(Ctx& C, const MeshDev& M, const WorkDev& W, int buf) {
-  const float4* src = W.vpub + (size_t)buf * M.n_nodes;
-  for (int l = C.n_own + threadIdx.x; l < C.n_loc; l += blockDim.x)
-    C.lm[l] = src[M.halo_nodes[C.halo0 + l - C.n_own]];
+// ------------------------------------------------------------- PCG sync
+// The PCG needs no grid barrier and no fence. Every value another part reads
+// (the halo entries of the vector being multiplied, the per-part dot-product
+// partials) is published as a 64-bit word holding the FP32 value and the
+// publication epoch, written and read with relaxed GPU-scope 64-bit accesses
+// (single-copy atomic). A reader spins until the epoch of each word it needs
+// matches. Double buffering is safe because no part can publish epoch e+2
+// before every part has consumed epoch e: it first needs every part's e+1
+// partials, which a part writes only after reading all of epoch e.
+
+__device__ __forceinline__ void st_tagged(unsigned long long* p, float v, int ep) {
+  const unsigned long long w = ((unsigned long long)(unsigned)ep << 32) | (unsigned long long)__float_as_uint(v);
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_tagged(const unsigned long long* p) {
+  unsigned long long w;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(p) : "memory");
+  return w;
+}
+
+__device__ __forceinline__ bool tag_is(unsigned long long w, int ep) { return (int)(w >> 32) == ep; }
+__device__ __forceinline__ float tag_val(unsigned long long w) { return __uint_as_float((unsigned)w); }
+
+__device__ bool spin_timeout(const WorkDev& W, unsigned long long& t0, unsigned& it, unsigned long long limit) {
+  if ((++it & 63u) != 0u) return false;
+  if (ld_volatile_i32(W.abort_flag)) return true;
+  const unsigned long long now = global_ns();
+  if (t0 == 0) t0 = now;
+  if (now - t0 > limit) {
+    atomicExch(W.abort_flag, 1);
+    return true;
+  }
+  return false;
+}
+
+// Owned node i of the vector being multiplied, epoch ep.
+__device__ __forceinline__ void publish_node(Ctx& C, const MeshDev& M, const WorkDev& W, int i, const float v[3],
+                                             int ep) {
+  unsigned long long* dst = W.vpub + ((size_t)(ep & 1) * M.n_nodes + C.node0 + i) * 3;
+  st_tagged(dst, v[0], ep);
+  st_tagged(dst + 1, v[1], ep);
+  st_tagged(dst + 2, v[2], ep);
+}
+
+// Halo part of the local vector, waiting (bounded) for epoch ep of each word.
+__device__ bool load_halo_tagged(Ctx& C, const MeshDev& M, const WorkDev& W, int ep, unsigned long long limit) {
+  const unsigned long long* src = W.vpub + (size_t)(ep & 1) * M.n_nodes * 3;
+  int failed = 0;
+  for (int l = C.n_own + threadIdx.x; l < C.n_loc && !failed; l += blockDim.x) {
+    const unsigned long long* q = src + (size_t)M.halo_nodes[C.halo0 + l - C.n_own] * 3;
+    unsigned long long a, b, c, t0 = 0;
+    unsigned it = 0;
+    for (;;) {
+      a = ld_tagged(q);
+      b = ld_tagged(q + 1);
+      c = ld_tagged(q + 2);
+      if (tag_is(a, ep) && tag_is(b, ep) && tag_is(c, ep)) break;
+      if (spin_timeout(W, t0, it, limit)) { failed = 1; break; }
+      __nanosleep(32);
+    }
+    C.lm[l] = make_float4(tag_val(a), tag_val(b), tag_val(c), 0.f);
+  }
+  return __syncthreads_or(failed) == 0;
+}
+
+// Thread 0 stores the CTA's FP32-pair dot products (C.red_df[0..2]) and
+// arrives on the PCG counter with release semantics (the stores are visible
+// to whoever observes the arrival).
+__device__ void write_cg_slot(Ctx& C, const WorkDev& W, int ep) {
+  if (threadIdx.x == 0) {
+    float4* dst = reinterpret_cast<float4*>(W.cgslot + ((size_t)(ep & 1) * gridDim.x + blockIdx.x) * 6);
+    dst[0] = make_float4(C.red_df[0].x, C.red_df[0].y, C.red_df[1].x, C.red_df[1].y);
+    dst[1] = make_float4(C.red_df[2].x, C.red_df[2].y, 0.f, 0.f);
+    unsigned long long* cnt = W.cgslot + (size_t)2 * gridDim.x * 6;
+    asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(cnt) : "memory");
+  }
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Thread 0 waits (bounded, acquire) until all parts arrived n_pub times; then
+// warp 0 sums the three values over the parts in a fixed order (identical in
+// every CTA) into C.red_df.
+__device__ bool reduce_cg_slots(Ctx& C, const WorkDev& W, int ep, unsigned long long n_pub,
+                                unsigned long long limit) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int P = gridDim.x;
+  if (threadIdx.x == 0) {
+    const unsigned long long* cnt = W.cgslot + (size_t)2 * P * 6;
+    const unsigned long long target = n_pub * (unsigned long long)P;
+    unsigned long long t0 = 0;
+    unsigned it = 0;
+    int failed = 0;
+    while (ld_acquire_u64(cnt) < target) {
+      if (spin_timeout(W, t0, it, limit)) { failed = 1; break; }
+    }
+    *C.flag = failed;
+  }
+  __syncthreads();
+  if (*C.flag) return false;
+  if (warp == 0) {
+    const float4* base = reinterpret_cast<const float4*>(W.cgslot + (size_t)(ep & 1) * P * 6);
+    constexpr int kMaxPer = 8;   // up to 256 CTAs, all loads in flight together
+    float4 a4[kMaxPer], b4[kMaxPer];
+#pragma unroll
+    for (int q = 0; q < kMaxPer; ++q) {
+      const int c = lane + 32 * q;
+      a4[q] = c < P ? __ldcg(base + (size_t)c * 3) : make_float4(0.f, 0.f, 0.f, 0.f);
+      b4[q] = c < P ? __ldcg(base + (size_t)c * 3 + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    DF a[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+    for (int q = 0; q < kMaxPer; ++q) {
+      a[0] = df_add(a[0], DF{a4[q].x, a4[q].y});
+      a[1] = df_add(a[1], DF{a4[q].z, a4[q].w});
+      a[2] = df_add(a[2], DF{b4[q].x, b4[q].y});
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const DF b{__shfl_xor_sync(0xffffffffu, a[k].hi, o), __shfl_xor_sync(0xffffffffu, a[k].lo, o)};
+        a[k] = (lane & o) ? df_add(b, a[k]) : df_add(a[k], b);
+      }
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) C.red_df[k] = make_float2(a[k].hi, a[k].lo);
+    }
+  }
+  __syncthreads();
+  return true;
 }
 
 // Preconditioned pipelined CG on K dx = -R_free. Leaves dx in C.x (owned).
-// Returns false if a barrier was abandoned; iters receives the iteration count
+// Returns false if a wait was abandoned; iters receives the iteration count
 // and neg_curv whether it stopped on a non-positive curvature.
-__device__ bool pcg(Ctx& C, const MeshDev& M, const WorkDev& W, const SolveParams& P, Barrier& gb,
-                    Bufs& bf, double eta, double abs_tol, int& iters, bool& neg_curv) {
+__device__ bool pcg(Ctx& C, const MeshDev& M, const WorkDev& W, const SolveParams& P, int& ep,
+                    unsigned long long& n_pub, double eta, double abs_tol, int& iters, bool& neg_curv) {
   long long t = tick(C);
   neg_curv = false;
+  const int active_warps = min((C.n_own + 31) / 32, kBlock / 32);
   // r0 = -R_free, u0 = M^-1 r0, publish u0
-  float4* pub = W.vpub + (size_t)bf.vec * M.n_nodes;
+  ++ep;
   for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
     const unsigned mk = C.mask[i];
     float r[3], uu[3];
@@ -433,18 +662,14 @@ __device__ bool pcg(Ctx& C, const MeshDev& M, const WorkDev& W, const SolveParam
     apply_minv(C.minv + 6 * i, r, uu);
 #pragma unroll
     for (int k = 0; k < 3; ++k) C.ucg[3 * i + k] = uu[k];
-    const float4 v4 = make_float4(uu[0], uu[1], uu[2], 0.f);
-    C.lm[i] = v4;
-    pub[C.node0 + i] = v4;
+    C.lm[i] = make_float4(uu[0], uu[1], uu[2], 0.f);
+    publish_node(C, M, W, i, uu, ep);
   }
-  if (!grid_sync(gb, C.flag)) return false;
-  load_halo_vector(C, M, W, bf.vec);
-  bf.vec ^= 1;
-  __syncthreads();
+  if (!load_halo_tagged(C, M, W, ep, P.timeout_ns)) return false;
   matvec_pass(C, M);
-  // w0 = A u0, m0 = M^-1 w0, partials (r,u) (w,u) (r,r)
-  pub = W.vpub + (size_t)bf.vec * M.n_nodes;
-  double v[3] = {0.0, 0.0, 0.0};
+  // w0 = A u0, m0 = M^-1 w0, partials (r,u) (w,u) (r,r); publish m0
+  ++ep;
+  float v[3] = {0.f, 0.f, 0.f};
   for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
     const float uu[3] = {C.ucg[3 * i], C.ucg[3 * i + 1], C.ucg[3 * i + 2]};
     float w[3], m[3];
@@ -459,54 +684,63 @@ __device__ bool pcg(Ctx& C, const MeshDev& M, const WorkDev& W, const SolveParam
       s1 += w[k] * uu[k];
       s2 += rk * rk;
     }
-    v[0] += (double)s0; v[1] += (double)s1; v[2] += (double)s2;
-    const float4 m4 = make_float4(m[0], m[1], m[2], 0.f);
-    C.lm[i] = m4;
-    pub[C.node0 + i] = m4;
+    v[0] += s0; v[1] += s1; v[2] += s2;
+    C.lm[i] = make_float4(m[0], m[1], m[2], 0.f);
+    publish_node(C, M, W, i, m, ep);
   }
-  block_reduce_to_slot(C, W, bf.slot, v, 3);
-  if (!grid_sync(gb, C.flag)) return false;
+  block_reduce_df<3>(C, v, active_warps);
+  write_cg_slot(C, W, ep);
+  ++n_pub;
   tock(C, PH_CG_INIT, t);
-  double gamma_prev = 1.0, alpha_prev = 1.0, rr0 = 0.0;
+  // PCG scalars: every thread evaluates the same FP32 recurrences from the
+  // same FP32-pair grid sums (identical in every CTA), no broadcast needed;
+  // delta - beta*gamma/alpha_prev, the one cancelling difference, keeps the
+  // pair's low word.
+  float gamma_prev = 1.f, alpha_prev = 1.f, rr0 = 0.f;
+  const float eta2 = (float)(eta * eta), abs2 = (float)(abs_tol * abs_tol);
   int it = 0;
   for (;; ++it) {
-    grid_reduce_from_slot(C, W, bf.slot, 3);
-    load_halo_vector(C, M, W, bf.vec);
-    bf.slot ^= 1;
-    bf.vec ^= 1;
-    __syncthreads();
+    if (!load_halo_tagged(C, M, W, ep, P.timeout_ns)) return false;
+    tock(C, PH_CG_BARRIER, t);
+    matvec_pass(C, M, &t);   // n = A m (m in C.lm)
+    if (!reduce_cg_slots(C, W, ep, n_pub, P.timeout_ns)) return false;
     tock(C, PH_CG_REDUCE, t);
-    const double gamma = C.red_out[0], delta = C.red_out[1], rr = C.red_out[2];
+    const float gamma = C.red_df[0].x, rr = C.red_df[2].x;
     if (it == 0) rr0 = rr;
-    double beta = 0.0, alpha;
-    if (it == 0) {
-      alpha = gamma / delta;
+    float beta = 0.f, denom;
+    if (it > 0) {
+      beta = __fdividef(gamma, gamma_prev);
+      const DF d = df_add(DF{C.red_df[1].x, C.red_df[1].y}, DF{-__fdividef(beta * gamma, alpha_prev), 0.f});
+      denom = d.hi;
     } else {
-      beta = gamma / gamma_prev;
-      alpha = gamma / (delta - beta * gamma / alpha_prev);
+      denom = C.red_df[1].x;
     }
-    const double denom = it == 0 ? delta : (delta - beta * gamma / alpha_prev);
-    const bool converged = rr <= eta * eta * rr0 || rr <= abs_tol * abs_tol;
-    const bool breakdown = !(denom > 0.0) || !isfinite(alpha) || !isfinite(rr);
+    const float alpha = __fdividef(gamma, denom);
+    const bool converged = rr <= eta2 * rr0 || rr <= abs2;
+    const bool breakdown = !(denom > 0.f) || !isfinite(alpha) || !isfinite(rr);
+    int dec = 0;
     if (converged || breakdown || it >= P.max_cg) {
-      neg_curv = breakdown && !converged;
-      if (breakdown && it == 0 && !(rr <= abs_tol * abs_tol)) {
+      dec = 1;
+      if (breakdown && !converged) dec = (it == 0) ? 3 : 2;
+    }
+    gamma_prev = gamma;
+    alpha_prev = alpha;
+    tock(C, PH_CG_SCALAR, t);
+    if (dec) {
+      neg_curv = dec >= 2;
+      if (dec == 3) {
         // non-positive curvature on the first direction: take the
         // preconditioned steepest-descent direction u0 (== C.ucg at it 0)
         for (int i = threadIdx.x; i < C.n_own; i += blockDim.x)
 #pragma unroll
           for (int k = 0; k < 3; ++k) C.x[3 * i + k] = C.ucg[3 * i + k];
-        __syncthreads();
       }
+      __syncthreads();
       break;
     }
-    gamma_prev = gamma;
-    alpha_prev = alpha;
-    matvec_pass(C, M);   // n = A m (m in C.lm)
-    tock(C, PH_CG_MATVEC, t);
-    pub = W.vpub + (size_t)bf.vec * M.n_nodes;
-    const float a = (float)alpha, b = (float)beta;
-    double pv[3] = {0.0, 0.0, 0.0};
+    ++ep;
+    const float a = alpha, b = beta;
+    float pv[3] = {0.f, 0.f, 0.f};
     for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
       const float4 m4 = C.lm[i];
       const float m[3] = {m4.x, m4.y, m4.z};
@@ -533,15 +767,14 @@ __device__ bool pcg(Ctx& C, const MeshDev& M, const WorkDev& W, const SolveParam
         s2 += r * r;
       }
       apply_minv(C.minv + 6 * i, wn, mn);
-      pv[0] += (double)s0; pv[1] += (double)s1; pv[2] += (double)s2;
-      const float4 o = make_float4(mn[0], mn[1], mn[2], 0.f);
-      C.lm[i] = o;
-      pub[C.node0 + i] = o;
+      pv[0] += s0; pv[1] += s1; pv[2] += s2;
+      C.lm[i] = make_float4(mn[0], mn[1], mn[2], 0.f);
+      publish_node(C, M, W, i, mn, ep);
     }
-    block_reduce_to_slot(C, W, bf.slot, pv, 3);
+    block_reduce_df<3>(C, pv, active_warps);
+    write_cg_slot(C, W, ep);
+    ++n_pub;
     tock(C, PH_CG_UPDATE, t);
-    if (!grid_sync(gb, C.flag)) return false;
-    tock(C, PH_CG_BARRIER, t);
   }
   iters = it;
   return true;
@@ -572,6 +805,9 @@ __device__ void accept_state(Ctx& C, const WorkDev& W) {
 __global__ void __launch_bounds__(kBlock, 1) solve_kernel(MeshDev M, WorkDev W, SolveParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double s_red_out[kRed];
+  __shared__ float s_coef[2];
+  __shared__ float2 s_red_df[kRed];
+  __shared__ int s_decision[4];
   __shared__ int s_flag;
   if (P.mode == MODE_BARRIER_TEST) {
     Barrier tb{W.barrier, W.abort_flag, 0ull, P.timeout_ns, gridDim.x};
@@ -613,8 +849,11 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(MeshDev M, WorkDev W, 
   C.mask = reinterpret_cast<unsigned char*>(smem + L.mask);
   C.cursor = reinterpret_cast<int*>(smem + L.cursor);
   C.red_out = s_red_out;
+  C.coef = s_coef;
+  C.red_df = s_red_df;
+  C.decision = s_decision;
   C.flag = &s_flag;
-  C.timer = blockIdx.x == 0 && threadIdx.x == 0;
+  C.timer = threadIdx.x == 0;
 #pragma unroll
   for (int k = 0; k < PH_N; ++k) C.cyc[k] = 0;
   const long long t_start = tick(C);
@@ -658,6 +897,8 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(MeshDev M, WorkDev W, 
   }
   __syncthreads();
   Bufs bf{0, 0};
+  int ep = 0;                      // PCG publication epoch (same sequence in every CTA)
+  unsigned long long n_pub = 0;    // PCG dot-product publications so far
   StatsDev* st = W.stats;
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
 
@@ -788,7 +1029,7 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(MeshDev M, WorkDev W, 
       }
       int cg_it = 0;
       bool neg_curv = false;
-      if (!pcg(C, M, W, P, gb, bf, eta, 0.1 * P.tol * scale, cg_it, neg_curv)) return;
+      if (!pcg(C, M, W, P, ep, n_pub, eta, 0.1 * P.tol * scale, cg_it, neg_curv)) return;
       cg_step += cg_it;
       ++it;
       if (mode == 1) ++exact_total;
@@ -873,6 +1114,14 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(MeshDev M, WorkDev W, 
     C.cyc[PH_TOTAL] = clock64() - t_start;
 #pragma unroll
     for (int k = 0; k < PH_N; ++k) st->cycles[k] = C.cyc[k];
+  }
+  if (threadIdx.x == 0) {
+    if (!leader) C.cyc[PH_TOTAL] = clock64() - t_start;
+#pragma unroll
+    for (int k = 0; k < PH_N; ++k) {
+      atomicMax(&st->cycles_max[k], C.cyc[k]);
+      atomicMin(&st->cycles_min[k], C.cyc[k]);
+    }
   }
 }
 
