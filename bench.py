@@ -38,6 +38,23 @@ WORKLOAD = ("fingertip_sphere: two-layer half-capsule fingertip R=7 mm L=40 mm (
             "8740 nodes; sphere r=4 mm pressed 2 mm normal to a seeded skin point in 20 load steps")
 
 
+def replica_seed(rank: int) -> int:
+    """Skin-point seed of the indentation a replica solves (1001 = the
+    single-fingertip workload; rank r solves its own seeded draw)."""
+    return 1001 + rank
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """MAX of a host scalar over all ranks (timing only, not on the data path)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -125,6 +142,36 @@ def compact_bytes(n_tets, n_nodes, cg_iters, newton_iters, evals):
             + evals * 92 * n_tets)
 
 
+def source_digest():
+    """SHA-256 over the CUDA library sources (the kernel as built)."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2103_16747_b300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the solve kernel from the committed ncu summary,
+    or None if the kernel sources changed since that capture."""
+    path = os.path.join(ROOT, "profiles", "solve_kernel_fingertip_sphere.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.strip().startswith(("- source_digest", "- traffic_bytes_per_launch")):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_digest") != source_digest():
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def cpu_oracle_rate(mesh, ind, n_load_steps):
     """Time the oracle (as it stands) on the first n_load_steps of the same
     solve and extrapolate to a full solve by Newton iterations, using the
@@ -192,8 +239,7 @@ def run_cuda(args, rank, world, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    seed = 1001 + rank                       # each replica: its own seeded skin point
-    mesh, ind = W.fingertip_sphere(seed=seed)
+    mesh, ind = W.fingertip_sphere(seed=replica_seed(rank))
     stream = torch.cuda.Stream(device=dev)
     solver = F.IndentationSolver(mesh, cuda_stream=stream)
     solver.set_indenter(ind)
@@ -228,12 +274,7 @@ def run_cuda(args, rank, world, local):
             stats.append(st)
         torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    local_total = sum(step_ms) / 1000.0
-    total = local_total
-    if world > 1:
-        t = torch.tensor([local_total], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total = float(t.item())
+    total = max_over_ranks(sum(step_ms) / 1000.0, world, dev)
     value = world * args.steps / total
 
     # end to end through the public API from host arrays, every step
@@ -257,12 +298,7 @@ def run_cuda(args, rank, world, local):
         t1 = time.perf_counter()
         if k >= args.warmup:
             e2e_times.append(t1 - t0)
-    e2e_local = sum(e2e_times)
-    e2e_total = e2e_local
-    if world > 1:
-        t = torch.tensor([e2e_local], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = max_over_ranks(sum(e2e_times), world, dev)
 
     # roofline of the dominant kernel (the persistent solve kernel)
     s0 = stats[-1]
@@ -272,13 +308,7 @@ def run_cuda(args, rank, world, local):
     cmp_b = compact_bytes(mesh.n_tets, n, s0.cg_iters, s0.newton_iters, evals)
     peak, peak_kind = peaks()
     achieved = alg / (kms / 1000.0) / 1e9
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        try:
-            traffic = json.load(open(tpath)).get("solve_kernel_fingertip_sphere_bytes")
-        except Exception:
-            traffic = None
+    traffic = profiled_traffic()
     lat = sorted(step_ms)
     p = lambda q: lat[min(len(lat) - 1, int(math.ceil(q * len(lat))) - 1)]   # noqa: E731
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
