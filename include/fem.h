@@ -226,6 +226,30 @@ int fem_eval_residual(fem_mesh* mesh, const double* u, int32_t step, const fem_o
                       double* out_R, double* out_fc, double* out_energy);
 
 /*
+ * Allocation-free variant of fem_eval_residual (the paper has no counterpart:
+ * this is a service of the library). Same arguments, outputs and errors; the
+ * evaluation runs the same kernel, but every device buffer it needs apart from
+ * the mesh itself comes from a fixed 8 MiB block of device memory that the
+ * library keeps in its own module (present on each GPU that loads the library,
+ * until the process exits), so the call itself never calls cudaMalloc,
+ * cudaFree or any allocating routine. It is meant for callers that may not
+ * allocate device memory once they are running: a real-time control loop with
+ * a no-allocation rule after start-up, a host application that hands out all
+ * device memory from its own pool, or a process already at its memory budget.
+ *   - Limit: the block must hold 4 x 3 doubles per node plus per-part
+ *     reduction slots, i.e. up to about 87,000 nodes; larger meshes return
+ *     FEM_ERR_TOO_LARGE with the sizes in the message.
+ *   - The first call on each device looks up the block's device address (with
+ *     that device current) and caches it; make that first call before any
+ *     stream capture.
+ *   - All calls share the one block and each call overwrites it (the words that
+ *     must start at zero are cleared at the start of every call). Calls that can
+ *     overlap on the GPU (other streams, other host threads) race: serialise them.
+ */
+int fem_eval_residual_noalloc(fem_mesh* mesh, const double* u, int32_t step, const fem_options* opt,
+                              double* out_R, double* out_fc, double* out_energy);
+
+/*
  * FP32 tangent product y = K(u) p at displacement u and step `step`: element
  * part from the stored per-tet tangent (projected or exact per opt->tangent)
  * plus the Gauss-Newton contact term, rows and columns of fixed DOFs zeroed.

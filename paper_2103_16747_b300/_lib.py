@@ -38,7 +38,8 @@ PHASES = ("eval", "tangent", "pcg_init", "pcg_reduce", "pcg_matvec", "pcg_update
 # Every symbol include/fem.h declares.
 EXPORTS = ("fem_default_options", "fem_create_mesh", "fem_set_indenter", "fem_set_dirichlet_values",
            "fem_solve", "fem_destroy_mesh", "fem_last_error", "fem_mesh_info_get", "fem_repartition",
-           "fem_eval_residual", "fem_apply_tangent", "fem_debug_barrier_timeout")
+           "fem_eval_residual", "fem_eval_residual_noalloc", "fem_apply_tangent",
+           "fem_debug_barrier_timeout")
 
 
 class fem_material(C.Structure):
@@ -96,6 +97,7 @@ def _load():
         "fem_mesh_info_get": (C.c_int, [P, C.POINTER(fem_mesh_info)]),
         "fem_repartition": (C.c_int, [P, C.c_int32]),
         "fem_eval_residual": (C.c_int, [P, P, C.c_int32, C.POINTER(fem_options), P, P, P]),
+        "fem_eval_residual_noalloc": (C.c_int, [P, P, C.c_int32, C.POINTER(fem_options), P, P, P]),
         "fem_apply_tangent": (C.c_int, [P, P, C.c_int32, C.POINTER(fem_options), P, P]),
         "fem_debug_barrier_timeout": (C.c_int, [C.c_double]),
     }
@@ -221,6 +223,18 @@ def fem_eval_residual(mesh, u, step, opt=None, out_R=None, out_fc=None):
     rc = lib.fem_eval_residual(mesh, _ptr(u, np.float64, keep), int(step),
                                C.byref(opt) if opt is not None else None,
                                _out_ptr(out_R, np.float64, keep), _out_ptr(out_fc, np.float64, keep), e)
+    _check(rc)
+    return float(e[0]), float(e[1])
+
+
+def fem_eval_residual_noalloc(mesh, u, step, opt=None, out_R=None, out_fc=None):
+    """As fem_eval_residual, for callers that may not allocate device memory:
+    the library's fixed scratch block replaces every per-call buffer."""
+    keep = []
+    e = (C.c_double * 2)()
+    rc = lib.fem_eval_residual_noalloc(mesh, _ptr(u, np.float64, keep), int(step),
+                                       C.byref(opt) if opt is not None else None,
+                                       _out_ptr(out_R, np.float64, keep), _out_ptr(out_fc, np.float64, keep), e)
     _check(rc)
     return float(e[0]), float(e[1])
 

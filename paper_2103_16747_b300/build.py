@@ -1,6 +1,8 @@
 """Build the CUDA library libfem_b300.so in-tree (nvcc, sm_103a).
 
-    python -m paper_2103_16747_b300.build        (or build() from Python)
+    python paper_2103_16747_b300/build.py [-v]    (or build() from Python)
+
+Run it by path: importing the package loads the library this script builds.
 """
 import os
 import subprocess

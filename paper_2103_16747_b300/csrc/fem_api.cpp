@@ -866,6 +866,73 @@ int fem_eval_residual(fem_mesh* m, const double* u, int32_t step, const fem_opti
   return FEM_OK;
 }
 
+// Same evaluation as fem_eval_residual, with every buffer the call needs
+// besides the mesh taken from the library's fixed device scratch block
+// (noalloc_scratch): no cudaMalloc, cudaFree or allocating call. The block is
+// shared by all calls in the process, so calls that overlap on the GPU race.
+int fem_eval_residual_noalloc(fem_mesh* m, const double* u, int32_t step, const fem_options* opt,
+                              double* out_R, double* out_fc, double* out_energy) {
+  g_err.clear();
+  if (!m || !u || !out_R) return fail(FEM_ERR_ARG, "NULL argument");
+  if (!m->has_indenter) return fail(FEM_ERR_ARG, "fem_set_indenter was not called");
+  if (step < 0 || step > m->n_steps) return fail(FEM_ERR_ARG, "step out of range");
+  SolveParams P;
+  int rc = fill_params(m, opt, MODE_EVAL, m->n_steps, step, 1e-6, P);
+  if (rc) return rc;
+  const size_t node_bytes = 3 * sizeof(double) * (size_t)m->n_nodes;
+  auto a256 = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t off_stats = 256;
+  const size_t off_part = off_stats + a256(sizeof(StatsDev));
+  const size_t off_u = off_part + a256(sizeof(double) * 2 * (size_t)m->dev.n_parts * kRed);
+  const size_t off_R = off_u + a256(node_bytes);
+  const size_t off_fc = off_R + a256(node_bytes);
+  const size_t off_stage = off_fc + a256(node_bytes);
+  const size_t need = off_stage + a256(node_bytes);
+  if (need > kNoAllocScratchBytes)
+    return fail(FEM_ERR_TOO_LARGE,
+                "fem_eval_residual_noalloc: mesh needs %zu B of scratch, the fixed block holds %zu B "
+                "(about %zu nodes at most)",
+                need, (size_t)kNoAllocScratchBytes, (size_t)(kNoAllocScratchBytes - off_u) / (4 * 3 * sizeof(double)));
+  void* base = nullptr;
+  CUDA_TRY(noalloc_scratch(&base), "scratch address lookup");
+  unsigned char* b = static_cast<unsigned char*>(base);
+  WorkDev W{};
+  W.barrier = reinterpret_cast<unsigned long long*>(b);
+  W.abort_flag = reinterpret_cast<int*>(b + sizeof(unsigned long long));
+  W.stats = reinterpret_cast<StatsDev*>(b + off_stats);
+  W.partials = reinterpret_cast<double*>(b + off_part);
+  W.u = reinterpret_cast<double*>(b + off_u);
+  W.out_R = reinterpret_cast<double*>(b + off_R);
+  W.out_fc = reinterpret_cast<double*>(b + off_fc);
+  W.tangent = m->work.tangent;   // not read by the evaluation
+  double* stage = reinterpret_cast<double*>(b + off_stage);
+  cudaStream_t s = m->stream;
+  // the barrier word, the abort word and the statistics must start at zero
+  CUDA_TRY(cudaMemsetAsync(b, 0, off_part, s), "clear scratch");
+  CUDA_TRY(cudaMemsetAsync(W.stats->cycles_min, 0x7f, sizeof(long long) * PH_N, s), "clear scratch");
+  CUDA_TRY(cudaMemcpyAsync(stage, u, node_bytes, cudaMemcpyDefault, s), "input copy");
+  CUDA_TRY(launch_permute(stage, W.u, m->d_perm, (int)m->n_nodes, false, s), "permute");
+  CUDA_TRY(launch_solve(m->dev, W, P, s, nullptr), "evaluation kernel");
+  StatsDev hst;
+  int abort_flag = 0;
+  CUDA_TRY(cudaMemcpyAsync(&hst, W.stats, sizeof(StatsDev), cudaMemcpyDeviceToHost, s), "stats copy");
+  CUDA_TRY(cudaMemcpyAsync(&abort_flag, W.abort_flag, sizeof(int), cudaMemcpyDeviceToHost, s), "flag copy");
+  CUDA_TRY(launch_permute(W.out_R, stage, m->d_perm, (int)m->n_nodes, true, s), "unpermute");
+  CUDA_TRY(cudaMemcpyAsync(out_R, stage, node_bytes, cudaMemcpyDefault, s), "output copy");
+  if (out_fc) {
+    CUDA_TRY(launch_permute(W.out_fc, stage, m->d_perm, (int)m->n_nodes, true, s), "unpermute");
+    CUDA_TRY(cudaMemcpyAsync(out_fc, stage, node_bytes, cudaMemcpyDefault, s), "output copy");
+  }
+  CUDA_TRY(cudaStreamSynchronize(s), "evaluation");
+  if (abort_flag) return fail(FEM_ERR_TIMEOUT, "a grid barrier wait exceeded its bound");
+  if (out_energy) {
+    out_energy[0] = hst.elastic;
+    out_energy[1] = hst.contact_energy;
+  }
+  if (hst.status == ST_NONFINITE) return fail(FEM_ERR_NONFINITE, "inverted tet or non-finite energy");
+  return FEM_OK;
+}
+
 int fem_apply_tangent(fem_mesh* m, const double* u, int32_t step, const fem_options* opt, const double* p,
                       double* out_y) {
   g_err.clear();

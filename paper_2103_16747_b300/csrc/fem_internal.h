@@ -148,4 +148,9 @@ cudaError_t launch_solve(const MeshDev& mesh, const WorkDev& work, const SolvePa
                          cudaStream_t stream, float* kernel_ms);
 cudaError_t solve_kernel_occupancy(int smem_bytes, int* blocks_per_sm);
 
+// Fixed scratch block for fem_eval_residual_noalloc (fem_solve.cu).
+constexpr size_t kNoAllocScratchBytes = 8u << 20;
+constexpr int kMaxDevices = 64;
+cudaError_t noalloc_scratch(void** ptr);
+
 }  // namespace fem

@@ -21,6 +21,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "fem_internal.h"
 #include "fem_math.cuh"
 
@@ -1181,6 +1183,32 @@ cudaError_t launch_solve(const MeshDev& mesh, const WorkDev& work, const SolvePa
     cudaEventDestroy(ev1);
   }
   return e;
+}
+
+// ------------------------------------------------------------------------
+// Scratch for callers that cannot allocate device memory: a fixed block in the
+// module's own device memory, present on every GPU that loads this library
+// until the process exits. Host code must not use the symbol itself as a
+// device address; noalloc_scratch() looks the real address up once per
+// device (with that device current) and caches it.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+cudaError_t noalloc_scratch(void** ptr) {
+  static std::mutex mu;
+  static void* cache[kMaxDevices] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!cache[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    cache[dev] = p;
+  }
+  *ptr = cache[dev];
+  return cudaSuccess;
 }
 
 }  // namespace fem
