@@ -193,6 +193,40 @@ int fem_solve(fem_mesh* mesh, int32_t load_steps, double tol, const fem_options*
               double* out_disp, double* out_contact_force, double* out_nodal_contact,
               fem_stats* stats);
 
+/* One indenter of a batched solve (same meaning as fem_set_indenter's arguments). */
+typedef struct {
+    int32_t       shape;            /* FEM_SPHERE / FEM_CYLINDER / FEM_BOX / FEM_PLANE      */
+    double        pose[12];         /* origin(3) + rotation (row-major, columns = axes)     */
+    double        params[3];        /* radius | radius | half extents | unused              */
+    double        dir[3];           /* unit approach direction                              */
+    const double* depth_schedule;   /* [n_steps] host or device, depths from the pose       */
+    int32_t       n_steps;          /* 1..FEM_MAX_STEPS                                     */
+} fem_indenter;
+
+/*
+ * Solve n independent indentations in one launch (batched form of fem_solve;
+ * Sec. III-A's indentations of one sensor, or of several meshes). Solve i uses
+ * meshes[i] (the same handle may appear any number of times; all meshes must be
+ * on the current device) and indenters[i]; prescribed values set with
+ * fem_set_dirichlet_values are not used here (fixed DOFs are held at 0).
+ * One CTA runs one solve with only CTA-local synchronisation and takes the next
+ * job from a queue, so uneven meshes share the launch; a solve's result does
+ * not depend on the other jobs. The launch goes to meshes[0]'s stream; the
+ * call synchronises it. The per-solve workspace (~200 B per node + 128 B per
+ * part tet) is allocated stream-ordered for the call and released before it
+ * returns.
+ *   out_disp[i]           [n_nodes(i)*3] displacement after the last step.
+ *   out_contact_force[i]  [n_steps(i)*3] resultant contact force per step (or
+ *                         out_contact_force == NULL).
+ *   stats[i]              per-solve statistics (or stats == NULL); kernel_ms is
+ *                         the whole launch.
+ * Returns FEM_OK if every solve converged, else the first solve's error code
+ * (each stats[i].status holds its own).
+ */
+int fem_solve_batch(fem_mesh* const* meshes, const fem_indenter* indenters, int32_t n, double tol,
+                    const fem_options* opt, double* const* out_disp, double* const* out_contact_force,
+                    fem_stats* stats);
+
 /* Release the mesh and its device memory (NULL is ignored). */
 void fem_destroy_mesh(fem_mesh* mesh);
 

@@ -37,7 +37,7 @@ PHASES = ("eval", "tangent", "pcg_init", "pcg_reduce", "pcg_matvec", "pcg_update
 
 # Every symbol include/fem.h declares.
 EXPORTS = ("fem_default_options", "fem_create_mesh", "fem_set_indenter", "fem_set_dirichlet_values",
-           "fem_solve", "fem_destroy_mesh", "fem_last_error", "fem_mesh_info_get", "fem_repartition",
+           "fem_solve", "fem_solve_batch", "fem_destroy_mesh", "fem_last_error", "fem_mesh_info_get", "fem_repartition",
            "fem_eval_residual", "fem_eval_residual_noalloc", "fem_apply_tangent",
            "fem_debug_barrier_timeout")
 
@@ -63,6 +63,11 @@ class fem_stats(C.Structure):
                 ("newton_per_step", C.c_int32 * FEM_MAX_STEPS),
                 ("cg_per_step", C.c_int32 * FEM_MAX_STEPS),
                 ("residual_per_step", C.c_double * FEM_MAX_STEPS)]
+
+
+class fem_indenter(C.Structure):
+    _fields_ = [("shape", C.c_int32), ("pose", C.c_double * 12), ("params", C.c_double * 3),
+                ("dir", C.c_double * 3), ("depth_schedule", C.c_void_p), ("n_steps", C.c_int32)]
 
 
 class fem_mesh_info(C.Structure):
@@ -92,6 +97,7 @@ def _load():
         "fem_set_dirichlet_values": (C.c_int, [P, P]),
         "fem_solve": (C.c_int, [P, C.c_int32, C.c_double, C.POINTER(fem_options), P, P, P,
                                 C.POINTER(fem_stats)]),
+        "fem_solve_batch": (C.c_int, [P, P, C.c_int32, C.c_double, C.POINTER(fem_options), P, P, P]),
         "fem_destroy_mesh": (None, [P]),
         "fem_last_error": (C.c_char_p, []),
         "fem_mesh_info_get": (C.c_int, [P, C.POINTER(fem_mesh_info)]),
@@ -201,6 +207,39 @@ def fem_solve(mesh, load_steps, tol, opt=None, out_disp=None, out_contact_force=
     if check:
         _check(rc)
     return rc, st
+
+
+def fem_solve_batch(meshes, indenters, tol, opt=None, out_disp=None, out_contact_force=None, check=True):
+    """Batched solves. ``meshes``: list of handles (repeats allowed);
+    ``indenters``: objects with shape/pose/params/direction/depth_schedule;
+    ``out_disp`` / ``out_contact_force``: lists of arrays (numpy or torch, host
+    or device). Returns (rc, list of fem_stats)."""
+    n = len(meshes)
+    keep = []
+    mesh_arr = (C.c_void_p * n)(*[m.value if isinstance(m, C.c_void_p) else m for m in meshes])
+    ind_arr = (fem_indenter * n)()
+    for i, d in enumerate(indenters):
+        sched = np.ascontiguousarray(d.depth_schedule, dtype=np.float64)
+        keep.append(sched)
+        ind_arr[i].shape = int(d.shape)
+        ind_arr[i].pose[:] = [float(v) for v in np.asarray(d.pose, dtype=np.float64)]
+        prm = np.zeros(3) if d.params is None else np.asarray(d.params, dtype=np.float64)
+        ind_arr[i].params[:] = [float(v) for v in prm]
+        ind_arr[i].dir[:] = [float(v) for v in np.asarray(d.direction, dtype=np.float64)]
+        ind_arr[i].depth_schedule = sched.ctypes.data
+        ind_arr[i].n_steps = len(sched)
+    disp = (C.c_void_p * n)(*[_out_ptr(a, np.float64, keep).value for a in out_disp])
+    forces = None
+    if out_contact_force is not None:
+        forces = (C.c_void_p * n)(*[_out_ptr(a, np.float64, keep).value for a in out_contact_force])
+    stats = (fem_stats * n)()
+    rc = lib.fem_solve_batch(C.cast(mesh_arr, C.c_void_p), C.cast(ind_arr, C.c_void_p), n, float(tol),
+                             C.byref(opt) if opt is not None else None, C.cast(disp, C.c_void_p),
+                             C.cast(forces, C.c_void_p) if forces is not None else None,
+                             C.cast(stats, C.c_void_p))
+    if check:
+        _check(rc)
+    return rc, list(stats)
 
 
 def fem_destroy_mesh(mesh):

@@ -103,8 +103,12 @@ struct fem_mesh {
   WorkDev work{};
   int smem_bytes = 0;
   std::vector<void*> owned;     // every device allocation of the mesh
-  std::vector<void*> part_owned;
-  size_t bytes = 0, part_bytes = 0;
+  std::vector<void*> part_owned, bpart_owned;
+  size_t bytes = 0, part_bytes = 0, bpart_bytes = 0;
+  MeshDev bdev{};                // batch partition (built on first batched use)
+  bool has_batch_partition = false;
+  int bsmem_bytes = 0;
+  MeshDev* d_bdev = nullptr;     // device copy of bdev
   // indenter
   bool has_indenter = false;
   int shape = 0;
@@ -124,9 +128,11 @@ cudaError_t launch_permute(const double* src, double* dst, const int* perm, int 
 
 namespace {
 
-int build_partitions(fem_mesh* m, int n_parts) {
+// batch: the partition of the batched kernel (no part limit, whole part in one
+// shared-memory chunk, tangents live in the per-solve workspaces).
+int build_partitions(fem_mesh* m, int n_parts, bool batch = false) {
   const int Nn = (int)m->n_nodes, Nt = (int)m->n_tets;
-  if (n_parts > 256) return fail(FEM_ERR_TOO_LARGE, "at most 256 parts (asked %d)", n_parts);
+  if (!batch && n_parts > 256) return fail(FEM_ERR_TOO_LARGE, "at most 256 parts (asked %d)", n_parts);
   // contiguous node ranges; a part's cost is its unique tets (halo tets
   // included, each computed once per part) plus its owned nodes. The cut
   // target is found by bisection so that exactly n_parts ranges result.
@@ -247,30 +253,37 @@ int build_partitions(fem_mesh* m, int n_parts) {
   int dev_smem = 0;
   CUDA_TRY(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device), "smem attr");
   const int static_smem = 8 * kRed + 64;
-  // resident: the whole part in one chunk with its tangent and local CSR in
-  // shared memory; otherwise stream them from global memory in chunks
-  int resident = 1, chunk = max_pt;
-  SmemLayout L = smem_layout(max_own, max_loc, chunk, max_pt, max_lcsr);
-  if (L.total + static_smem > dev_smem) {
-    resident = 0;
-    chunk = std::min(kChunk, max_pt);
-    L = smem_layout(max_own, max_loc, chunk, 0, 0);
+  int resident = 0, chunk = max_pt, smem_total = 0;
+  if (batch) {
+    smem_total = batch_smem_layout(max_own, max_loc, max_pt).total;
+    if (smem_total + static_smem > dev_smem) return FEM_ERR_TOO_LARGE;   // caller retries with more parts
+  } else {
+    // resident: the whole part in one chunk with its tangent and local CSR in
+    // shared memory; otherwise stream them from global memory in chunks
+    resident = 1;
+    SmemLayout L = smem_layout(max_own, max_loc, chunk, max_pt, max_lcsr);
+    if (L.total + static_smem > dev_smem) {
+      resident = 0;
+      chunk = std::min(kChunk, max_pt);
+      L = smem_layout(max_own, max_loc, chunk, 0, 0);
+    }
+    if (L.total + static_smem > dev_smem)
+      return fail(FEM_ERR_TOO_LARGE, "part needs %d B shared memory, device allows %d", L.total + static_smem,
+                  dev_smem);
+    int per_sm = 0, n_sm = 0;
+    CUDA_TRY(solve_kernel_occupancy(L.total, &per_sm), "occupancy");
+    CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, m->device), "sm count");
+    if (per_sm * n_sm < n_parts)
+      return fail(FEM_ERR_TOO_LARGE, "%d parts exceed the %d co-resident CTAs", n_parts, per_sm * n_sm);
+    smem_total = L.total;
   }
-  if (L.total + static_smem > dev_smem)
-    return fail(FEM_ERR_TOO_LARGE, "part needs %d B shared memory, device allows %d", L.total + static_smem,
-                dev_smem);
-  int per_sm = 0, n_sm = 0;
-  CUDA_TRY(solve_kernel_occupancy(L.total, &per_sm), "occupancy");
-  CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, m->device), "sm count");
-  if (per_sm * n_sm < n_parts)
-    return fail(FEM_ERR_TOO_LARGE, "%d parts exceed the %d co-resident CTAs", n_parts, per_sm * n_sm);
 
-  for (void* q : m->part_owned) cudaFree(q);
-  m->part_owned.clear();
-  m->bytes -= m->part_bytes;
-  m->part_bytes = 0;
-  auto& o = m->part_owned;
-  size_t& by = m->part_bytes;
+  std::vector<void*>& o = batch ? m->bpart_owned : m->part_owned;
+  size_t& by = batch ? m->bpart_bytes : m->part_bytes;
+  for (void* q : o) cudaFree(q);
+  o.clear();
+  m->bytes -= by;
+  by = 0;
   cudaStream_t s = m->stream;
   int *d_nb, *d_tb, *d_hb, *d_halo, *d_info, *d_lcsr_ptr;
   ushort4* d_ptn;
@@ -286,14 +299,17 @@ int build_partitions(fem_mesh* m, int n_parts) {
   CUDA_TRY(upload(&d_info, pt_info, s, o, by), "upload");
   CUDA_TRY(upload(&d_lcsr_ptr, lcsr_ptr, s, o, by), "upload");
   CUDA_TRY(upload(&d_lcsr, lcsr, s, o, by), "upload");
-  float4* d_tan;
-  double* d_part;
-  CUDA_TRY(alloc(&d_tan, (size_t)kTanVec * total_pt, o, by), "alloc tangent");
-  CUDA_TRY(alloc(&d_part, (size_t)2 * n_parts * kRed, o, by), "alloc partials");
-  unsigned long long* d_slot;
-  CUDA_TRY(alloc(&d_slot, (size_t)12 * n_parts + 2, o, by), "alloc slots");
+  float4* d_tan = nullptr;
+  double* d_part = nullptr;
+  unsigned long long* d_slot = nullptr;
+  if (!batch) {
+    CUDA_TRY(alloc(&d_tan, (size_t)kTanVec * total_pt, o, by), "alloc tangent");
+    CUDA_TRY(alloc(&d_part, (size_t)2 * n_parts * kRed, o, by), "alloc partials");
+    CUDA_TRY(alloc(&d_slot, (size_t)12 * n_parts + 2, o, by), "alloc slots");
+  }
   m->bytes += by;
-  MeshDev& D = m->dev;
+  MeshDev& D = batch ? m->bdev : m->dev;
+  if (batch) D = m->dev;   // shared fields (sizes, X, masks, penalty, materials)
   D.n_parts = n_parts;
   D.total_pt = total_pt;
   D.max_own = max_own;
@@ -312,12 +328,32 @@ int build_partitions(fem_mesh* m, int n_parts) {
   D.pt_info = d_info;
   D.lcsr_ptr = d_lcsr_ptr;
   D.lcsr = d_lcsr;
-  m->work.tangent = d_tan;
-  m->work.partials = d_part;
-  m->work.cgslot = d_slot;
-  m->smem_bytes = L.total;
+  if (batch) {
+    m->bsmem_bytes = smem_total;
+    m->has_batch_partition = true;
+  } else {
+    m->work.tangent = d_tan;
+    m->work.partials = d_part;
+    m->work.cgslot = d_slot;
+    m->smem_bytes = smem_total;
+  }
   CUDA_TRY(cudaStreamSynchronize(s), "partition upload");
   return FEM_OK;
+}
+
+// Batch partition: parts of about 1000 part tets, refined until one part fits
+// the batched kernel's shared memory.
+int ensure_batch_partition(fem_mesh* m) {
+  if (m->has_batch_partition) return FEM_OK;
+  int n = (int)std::max<int64_t>(1, (m->n_tets + 699) / 700);
+  n = (int)std::min<int64_t>(n, std::max<int64_t>(1, m->n_nodes / 8));
+  for (int attempt = 0; attempt < 8; ++attempt) {
+    const int rc = build_partitions(m, n, true);
+    if (rc == FEM_OK) return FEM_OK;
+    if (rc != FEM_ERR_TOO_LARGE) return rc;
+    n = n * 3 / 2 + 1;
+  }
+  return fail(FEM_ERR_TOO_LARGE, "no batch partition fits in shared memory");
 }
 
 int default_parts(const fem_mesh* m) {
@@ -348,6 +384,7 @@ const char* fem_last_error(void) { return g_err.c_str(); }
 void fem_destroy_mesh(fem_mesh* m) {
   if (!m) return;
   for (void* q : m->part_owned) cudaFree(q);
+  for (void* q : m->bpart_owned) cudaFree(q);
   for (void* q : m->owned) cudaFree(q);
   delete m;
 }
@@ -651,9 +688,9 @@ int fem_mesh_info_get(const fem_mesh* m, fem_mesh_info* info) {
   return FEM_OK;
 }
 
-int fem_set_indenter(fem_mesh* m, int shape, const double pose[12], const double* params, const double dir[3],
-                     const double* depth_schedule, int32_t n_steps) {
-  if (!m || !pose || !dir || !depth_schedule) return fail(FEM_ERR_ARG, "NULL argument");
+static int validate_indenter(int shape, const double pose[12], const double* params, const double dir[3],
+                             const double* depth_schedule, int32_t n_steps) {
+  if (!pose || !dir || !depth_schedule) return fail(FEM_ERR_ARG, "NULL argument");
   if (shape < FEM_SPHERE || shape > FEM_PLANE) return fail(FEM_ERR_ARG, "unknown shape %d", shape);
   if (n_steps < 1 || n_steps > FEM_MAX_STEPS) return fail(FEM_ERR_ARG, "n_steps=%d out of range", n_steps);
   if (shape != FEM_PLANE && !params) return fail(FEM_ERR_ARG, "params is NULL");
@@ -662,8 +699,6 @@ int fem_set_indenter(fem_mesh* m, int shape, const double pose[12], const double
   for (int k = 0; k < 3; ++k)
     if (!std::isfinite(dir[k]) || (params && shape != FEM_PLANE && !std::isfinite(params[k])))
       return fail(FEM_ERR_NONFINITE, "dir/params not finite");
-  for (int k = 0; k < n_steps; ++k)
-    if (!std::isfinite(depth_schedule[k])) return fail(FEM_ERR_NONFINITE, "depth_schedule not finite");
   const double dn = std::sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
   if (std::fabs(dn - 1.0) > 1e-6) return fail(FEM_ERR_ARG, "dir must be a unit vector (|a|=%g)", dn);
   const double* R = pose + 3;
@@ -678,6 +713,20 @@ int fem_set_indenter(fem_mesh* m, int shape, const double pose[12], const double
   } else if (shape == FEM_BOX) {
     if (!(params[0] > 0 && params[1] > 0 && params[2] > 0)) return fail(FEM_ERR_ARG, "box half extents must be > 0");
   }
+  return FEM_OK;
+}
+
+int fem_set_indenter(fem_mesh* m, int shape, const double pose[12], const double* params, const double dir[3],
+                     const double* depth_schedule, int32_t n_steps) {
+  if (!m) return fail(FEM_ERR_ARG, "NULL argument");
+  if (!pose || !depth_schedule) return fail(FEM_ERR_ARG, "NULL argument");
+  {
+    const int rc = validate_indenter(shape, pose, params, dir, depth_schedule, n_steps);
+    if (rc) return rc;
+  }
+  for (int k = 0; k < n_steps; ++k)
+    if (!std::isfinite(depth_schedule[k])) return fail(FEM_ERR_NONFINITE, "depth_schedule not finite");
+  const double* R = pose + 3;
   m->shape = shape;
   for (int k = 0; k < 3; ++k) {
     m->origin[k] = pose[k];
@@ -840,6 +889,162 @@ int fem_solve(fem_mesh* m, int32_t load_steps, double tol, const fem_options* op
     default: code = fail(FEM_ERR_NOT_CONVERGED, "step %d did not converge in max_newton iterations", hst.steps_done + 1);
   }
   if (stats) stats->status = code;
+  return code;
+}
+
+int fem_solve_batch(fem_mesh* const* meshes, const fem_indenter* ind, int32_t n, double tol,
+                    const fem_options* opt, double* const* out_disp, double* const* out_contact_force,
+                    fem_stats* stats) {
+  g_err.clear();
+  if (!meshes || !ind || !out_disp || n < 1) return fail(FEM_ERR_ARG, "meshes, indenters, out_disp and n >= 1 required");
+  if (!(tol > 0) || !std::isfinite(tol)) return fail(FEM_ERR_ARG, "tol must be > 0");
+  fem_options o;
+  fem_default_options(&o);
+  if (opt) o = *opt;
+  if (!(o.c_kappa > 0) || o.max_newton < 0 || o.max_cg < 1 || o.max_backtracks < 0 || !(o.cg_rtol_max > 0) ||
+      !(o.cg_rtol_min > 0) || o.cg_rtol_min > o.cg_rtol_max || o.tangent < 0 || o.tangent > 3)
+    return fail(FEM_ERR_ARG, "invalid fem_options");
+  for (int i = 0; i < n; ++i) {
+    if (!meshes[i] || !out_disp[i]) return fail(FEM_ERR_ARG, "solve %d: NULL mesh or output", i);
+    const fem_indenter& d = ind[i];
+    int rc = validate_indenter(d.shape, d.pose, d.params, d.dir, d.depth_schedule, d.n_steps);
+    if (rc) return fail(rc, "solve %d: %s", i, g_err.c_str());
+  }
+  const cudaStream_t s = meshes[0]->stream;
+  // batch partitions (built once per mesh) and their device copies
+  int smem = 0;
+  std::vector<fem_mesh*> uniq;
+  for (int i = 0; i < n; ++i)
+    if (std::find(uniq.begin(), uniq.end(), meshes[i]) == uniq.end()) uniq.push_back(meshes[i]);
+  for (fem_mesh* m : uniq) {
+    if (m->device != meshes[0]->device) return fail(FEM_ERR_ARG, "all meshes must be on one device");
+    int rc = ensure_batch_partition(m);
+    if (rc) return rc;
+    if (!m->d_bdev) {
+      CUDA_TRY(alloc(&m->d_bdev, 1, m->bpart_owned, m->bpart_bytes), "alloc batch mesh");
+      CUDA_TRY(cudaMemcpy(m->d_bdev, &m->bdev, sizeof(MeshDev), cudaMemcpyHostToDevice), "upload batch mesh");
+    }
+    smem = std::max(smem, m->bsmem_bytes);
+  }
+  int per_sm = 0, n_sm = 0;
+  CUDA_TRY(batch_kernel_occupancy(smem, &per_sm), "batch occupancy");
+  CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, meshes[0]->device), "sm count");
+  if (per_sm < 1) return fail(FEM_ERR_TOO_LARGE, "batched kernel does not fit on an SM (%d B shared memory)", smem);
+  // workspace layout
+  auto a256 = [](size_t b) { return (b + 255) / 256 * 256; };
+  std::vector<size_t> off(n + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    const size_t Nn = (size_t)meshes[i]->n_nodes, T = (size_t)meshes[i]->bdev.total_pt;
+    const size_t K = (size_t)ind[i].n_steps;
+    off[i + 1] = off[i] + 4 * a256(24 * Nn) + 6 * a256(12 * Nn) + a256(24 * Nn) + a256(16 * kTanVec * T) +
+                 a256(24 * K) + a256(sizeof(StatsDev)) + a256(8 * K);
+  }
+  const size_t jobs_off = off[n], queue_off = jobs_off + a256(sizeof(BatchJob) * n);
+  const size_t total = queue_off + 256;
+  unsigned char* ws = nullptr;
+  {
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), total, s);
+    if (e != cudaSuccess) return cuda_fail(e, "batch workspace");
+  }
+  auto release = [&]() { cudaFreeAsync(ws, s); cudaStreamSynchronize(s); };
+  std::vector<BatchJob> jobs(n);
+  {
+    cudaError_t e = cudaMemsetAsync(ws, 0, jobs_off, s);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+      const size_t Nn = (size_t)meshes[i]->n_nodes, T = (size_t)meshes[i]->bdev.total_pt;
+      const size_t K = (size_t)ind[i].n_steps;
+      unsigned char* b = ws + off[i];
+      auto take = [&](size_t bytes) { unsigned char* at = b; b += a256(bytes); return at; };
+      BatchJob& J = jobs[i];
+      J.mesh = meshes[i]->d_bdev;
+      J.u = reinterpret_cast<double*>(take(24 * Nn));
+      J.uprev = reinterpret_cast<double*>(take(24 * Nn));
+      J.R = reinterpret_cast<double*>(take(24 * Nn));
+      J.fc = reinterpret_cast<double*>(take(24 * Nn));
+      J.x = reinterpret_cast<float*>(take(12 * Nn));
+      J.r = reinterpret_cast<float*>(take(12 * Nn));
+      J.z = reinterpret_cast<float*>(take(12 * Nn));
+      J.p = reinterpret_cast<float*>(take(12 * Nn));
+      J.q = reinterpret_cast<float*>(take(12 * Nn));
+      J.hc = reinterpret_cast<float*>(take(12 * Nn));
+      J.minv = reinterpret_cast<float*>(take(24 * Nn));
+      J.tangent = reinterpret_cast<float4*>(take(16 * kTanVec * T));
+      J.step_force = reinterpret_cast<double*>(take(24 * K));
+      J.stats = reinterpret_cast<StatsDev*>(take(sizeof(StatsDev)));
+      double* depths = reinterpret_cast<double*>(take(8 * K));
+      J.depths = depths;
+      J.shape = ind[i].shape;
+      J.n_steps = ind[i].n_steps;
+      for (int k = 0; k < 3; ++k) {
+        J.origin[k] = ind[i].pose[k];
+        J.dir[k] = ind[i].dir[k];
+        J.iparams[k] = ind[i].shape == FEM_PLANE ? 0.0 : ind[i].params[k];
+      }
+      for (int k = 0; k < 9; ++k) J.rot[k] = ind[i].pose[3 + k];
+      e = cudaMemcpyAsync(depths, ind[i].depth_schedule, 8 * K, cudaMemcpyDefault, s);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ws + jobs_off, jobs.data(), sizeof(BatchJob) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws + queue_off, 0, 256, s);
+    if (e != cudaSuccess) { release(); return cuda_fail(e, "batch set-up"); }
+  }
+  BatchParams P{};
+  P.n_jobs = n;
+  P.tangent_mode = o.tangent;
+  P.max_newton = o.max_newton;
+  P.max_cg = o.max_cg;
+  P.max_backtracks = o.max_backtracks;
+  P.tol = tol;
+  P.c_kappa = o.c_kappa;
+  P.cg_rtol_max = o.cg_rtol_max;
+  P.cg_rtol_min = o.cg_rtol_min;
+  float ms = 0.f;
+  const int n_ctas = std::min(n, n_sm * per_sm);
+  cudaError_t e = launch_batch(reinterpret_cast<const BatchJob*>(ws + jobs_off), reinterpret_cast<int*>(ws + queue_off),
+                               P, smem, n_ctas, s, &ms);
+  if (e != cudaSuccess) { release(); return cuda_fail(e, "batch kernel"); }
+  std::vector<StatsDev> hst(n);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    fem_mesh* m = meshes[i];
+    const BatchJob& J = jobs[i];
+    e = launch_permute(J.u, J.R, m->d_perm, (int)m->n_nodes, true, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out_disp[i], J.R, 24 * (size_t)m->n_nodes, cudaMemcpyDefault, s);
+    if (e == cudaSuccess && out_contact_force && out_contact_force[i])
+      e = cudaMemcpyAsync(out_contact_force[i], J.step_force, 24 * (size_t)J.n_steps, cudaMemcpyDefault, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hst[i], J.stats, sizeof(StatsDev), cudaMemcpyDeviceToHost, s);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  release();
+  if (e != cudaSuccess) return cuda_fail(e, "batch outputs");
+  int code = FEM_OK;
+  for (int i = 0; i < n; ++i) {
+    int c = FEM_OK;
+    if (hst[i].status == ST_NONFINITE) c = FEM_ERR_NONFINITE;
+    else if (hst[i].status != ST_OK) c = FEM_ERR_NOT_CONVERGED;
+    if (c != FEM_OK && code == FEM_OK) {
+      code = c;
+      fail(c, "solve %d stopped at step %d (status %d)", i, hst[i].steps_done + 1, hst[i].status);
+    }
+    if (stats) {
+      fem_stats& st = stats[i];
+      memset(&st, 0, sizeof(st));
+      st.status = c;
+      st.steps_done = hst[i].steps_done;
+      st.newton_iters = hst[i].newton_total;
+      st.cg_iters = hst[i].cg_total;
+      st.backtracks = hst[i].backtracks_total;
+      st.active_contacts = hst[i].active;
+      st.residual = hst[i].residual;
+      st.scale = hst[i].scale;
+      st.energy = hst[i].energy;
+      st.kernel_ms = ms;
+      st.exact_newton_iters = hst[i].exact_newton;
+      for (int k = 0; k < ind[i].n_steps; ++k) {
+        st.newton_per_step[k] = hst[i].newton_per_step[k];
+        st.cg_per_step[k] = hst[i].cg_per_step[k];
+        st.residual_per_step[k] = hst[i].residual_per_step[k];
+      }
+    }
+  }
   return code;
 }
 

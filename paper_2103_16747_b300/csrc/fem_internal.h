@@ -143,6 +143,49 @@ __host__ __device__ inline SmemLayout smem_layout(const MeshDev& M) {
   return smem_layout(M.max_own, M.max_loc, M.chunk, M.resident ? M.max_pt : 0, M.resident ? M.max_lcsr : 0);
 }
 
+// ---------------------------------------------------------------- batched solves
+// One CTA runs one whole solve; CTAs take jobs from a queue. The mesh uses its
+// batch partition (parts of ~1000 tets, processed one after another), every
+// per-solve array lives in global memory.
+struct BatchJob {
+  const MeshDev* mesh;              // device copy of the mesh's batch partition
+  double *u, *uprev, *R, *fc;       // [3 Nn] FP64
+  float *x, *r, *z, *p, *q, *hc;    // [3 Nn] FP32
+  float* minv;                      // [6 Nn]
+  float4* tangent;                  // [kTanVec][total_pt]
+  double* step_force;               // [3 K]
+  StatsDev* stats;
+  int shape, n_steps;
+  double origin[3], rot[9], iparams[3], dir[3];
+  const double* depths;             // [K] device
+};
+
+struct BatchParams {
+  int n_jobs, tangent_mode, max_newton, max_cg, max_backtracks;
+  double tol, c_kappa, cg_rtol_max, cg_rtol_min;
+};
+
+struct BatchSmem {
+  int ut, lm, chunk, acc, red, total;
+};
+
+__host__ __device__ inline BatchSmem batch_smem_layout(int max_own, int max_loc, int max_pt) {
+  BatchSmem L;
+  int o = 0;
+  auto take = [&](int bytes) { int at = o; o = align_up(o + bytes, 16); return at; };
+  L.ut = take(24 * max_loc);
+  L.lm = take(16 * max_loc);
+  L.chunk = take(96 * max_pt);
+  L.acc = take(24 * max_own);
+  L.red = take(8 * kRed * (kBlock / 32 + 1));
+  L.total = o;
+  return L;
+}
+
+cudaError_t launch_batch(const BatchJob* d_jobs, int* d_queue, const BatchParams& prm, int smem_bytes,
+                         int n_ctas, cudaStream_t stream, float* kernel_ms);
+cudaError_t batch_kernel_occupancy(int smem_bytes, int* blocks_per_sm);
+
 // Host-side launcher (fem_solve.cu).
 cudaError_t launch_solve(const MeshDev& mesh, const WorkDev& work, const SolveParams& prm,
                          cudaStream_t stream, float* kernel_ms);

@@ -448,6 +448,41 @@ __device__ __forceinline__ void indenter_sdf(int shape, const double o[3], const
   for (int i = 0; i < 3; ++i) n[i] = R[3 * i] * nl[0] + R[3 * i + 1] * nl[1] + R[3 * i + 2] * nl[2];
 }
 
+// ------------------------------------------------------------------ FP32 pairs
+// Compensated FP32 pair ("double-float", two-sum): about 44 significant bits
+// from FP32 adds only. Used inside a CTA, where FP64 instructions would run on
+// B300's narrow FP64 pipe.
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float err = (a.hi - (s - bb)) + (b.hi - bb);
+  const float lo = err + a.lo + b.lo;
+  const float hi = s + lo;
+  return DF{hi, lo - (hi - s)};
+}
+
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e += a.hi * b.lo + a.lo * b.hi;
+  const float hi = p + e;
+  return DF{hi, e - (hi - p)};
+}
+
+__device__ __forceinline__ DF df_div(DF a, DF b) {
+  const float q1 = a.hi / b.hi;
+  const DF r = df_add(a, df_neg(df_mul(DF{q1, 0.f}, b)));
+  const float q2 = r.hi / b.hi;
+  const float hi = q1 + q2;
+  return DF{hi, q2 - (hi - q1)};
+}
+
 // ------------------------------------------------------------------ preconditioner
 // Inverse of a symmetric 3x3 block (m00 m01 m02 m11 m12 m22) restricted to the
 // free DOFs (mask bits set = fixed); rows/columns of fixed DOFs are zero.

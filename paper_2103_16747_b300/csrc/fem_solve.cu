@@ -12,9 +12,9 @@
 // direction, the displacement) and one reduction slot per CTA go through
 // global memory.
 //
-// Synchronisation. One software grid barrier per PCG iteration (pipelined CG,
-// Ghysels & Vanroose 2014: the dot products of iteration i are reduced while
-// the tangent product of iteration i is formed). Every wait is bounded
+// Synchronisation. The PCG (Chronopoulos-Gear form) needs per iteration one
+// halo exchange of fenceless (epoch, value) words and one grid reduction
+// announced on a release-ordered counter. Every wait is bounded
 // (globaltimer); on expiry the CTA sets the abort word and returns, and the
 // others leave at their next barrier. The launch is cooperative so that all
 // CTAs are co-resident or the launch fails cleanly.
@@ -111,40 +111,6 @@ __device__ __forceinline__ void tock(Ctx& C, int ph, long long& t) {
 
 __device__ __forceinline__ int local_to_global(const Ctx& C, const MeshDev& M, int l) {
   return l < C.n_own ? C.node0 + l : M.halo_nodes[C.halo0 + l - C.n_own];
-}
-
-// Compensated FP32 pair ("double-float", two-sum): about 44 significant bits
-// from FP32 adds only. Used inside a CTA, where FP64 instructions would run on
-// B300's narrow FP64 pipe.
-struct DF {
-  float hi, lo;
-};
-
-__device__ __forceinline__ DF df_add(DF a, DF b) {
-  const float s = a.hi + b.hi;
-  const float bb = s - a.hi;
-  const float err = (a.hi - (s - bb)) + (b.hi - bb);
-  const float lo = err + a.lo + b.lo;
-  const float hi = s + lo;
-  return DF{hi, lo - (hi - s)};
-}
-
-__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
-
-__device__ __forceinline__ DF df_mul(DF a, DF b) {
-  const float p = a.hi * b.hi;
-  float e = fmaf(a.hi, b.hi, -p);
-  e += a.hi * b.lo + a.lo * b.hi;
-  const float hi = p + e;
-  return DF{hi, e - (hi - p)};
-}
-
-__device__ __forceinline__ DF df_div(DF a, DF b) {
-  const float q1 = a.hi / b.hi;
-  const DF r = df_add(a, df_neg(df_mul(DF{q1, 0.f}, b)));
-  const float q2 = r.hi / b.hi;
-  const float hi = q1 + q2;
-  return DF{hi, q2 - (hi - q1)};
 }
 
 // Deterministic CTA reduction of nv per-thread FP32 values (each thread's
@@ -641,15 +607,18 @@ __device__ bool reduce_cg_slots(Ctx& C, const WorkDev& W, int ep, unsigned long 
   return true;
 }
 
-// Preconditioned pipelined CG on K dx = -R_free. Leaves dx in C.x (owned).
-// Returns false if a wait was abandoned; iters receives the iteration count
-// and neg_curv whether it stopped on a non-positive curvature.
+// Preconditioned CG on K dx = -R_free in the Chronopoulos-Gear form: one
+// halo exchange, one tangent product and one grid reduction (of (r,u), (w,u)
+// and (r,r) together) per iteration; s = A p is carried by recurrence.
+// Leaves dx in C.x (owned). Returns false if a wait was abandoned; iters
+// receives the iteration count, neg_curv whether it stopped on a
+// non-positive curvature.
 __device__ bool pcg(Ctx& C, const MeshDev& M, const WorkDev& W, const SolveParams& P, int& ep,
                     unsigned long long& n_pub, double eta, double abs_tol, int& iters, bool& neg_curv) {
   long long t = tick(C);
   neg_curv = false;
   const int active_warps = min((C.n_own + 31) / 32, kBlock / 32);
-  // r0 = -R_free, u0 = M^-1 r0, publish u0
+  // x = 0, r = -R_free, u = M^-1 r, p = s = 0; publish u
   ++ep;
   for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
     const unsigned mk = C.mask[i];
@@ -659,7 +628,8 @@ __device__ bool pcg(Ctx& C, const MeshDev& M, const WorkDev& W, const SolveParam
       r[k] = (mk & (1u << k)) ? 0.f : (float)(-C.R[3 * i + k]);
       C.r[3 * i + k] = r[k];
       C.x[3 * i + k] = 0.f;
-      C.z[3 * i + k] = 0.f; C.q[3 * i + k] = 0.f; C.s[3 * i + k] = 0.f; C.p[3 * i + k] = 0.f;
+      C.p[3 * i + k] = 0.f;
+      C.s[3 * i + k] = 0.f;
     }
     apply_minv(C.minv + 6 * i, r, uu);
 #pragma unroll
@@ -667,46 +637,37 @@ __device__ bool pcg(Ctx& C, const MeshDev& M, const WorkDev& W, const SolveParam
     C.lm[i] = make_float4(uu[0], uu[1], uu[2], 0.f);
     publish_node(C, M, W, i, uu, ep);
   }
-  if (!load_halo_tagged(C, M, W, ep, P.timeout_ns)) return false;
-  matvec_pass(C, M);
-  // w0 = A u0, m0 = M^-1 w0, partials (r,u) (w,u) (r,r); publish m0
-  ++ep;
-  float v[3] = {0.f, 0.f, 0.f};
-  for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
-    const float uu[3] = {C.ucg[3 * i], C.ucg[3 * i + 1], C.ucg[3 * i + 2]};
-    float w[3], m[3];
-    finish_product(C, i, uu, w);
-    apply_minv(C.minv + 6 * i, w, m);
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      C.w[3 * i + k] = w[k];
-      const float rk = C.r[3 * i + k];
-      s0 += rk * uu[k];
-      s1 += w[k] * uu[k];
-      s2 += rk * rk;
-    }
-    v[0] += s0; v[1] += s1; v[2] += s2;
-    C.lm[i] = make_float4(m[0], m[1], m[2], 0.f);
-    publish_node(C, M, W, i, m, ep);
-  }
-  block_reduce_df<3>(C, v, active_warps);
-  write_cg_slot(C, W, ep);
-  ++n_pub;
   tock(C, PH_CG_INIT, t);
-  // PCG scalars: every thread evaluates the same FP32 recurrences from the
-  // same FP32-pair grid sums (identical in every CTA), no broadcast needed;
-  // delta - beta*gamma/alpha_prev, the one cancelling difference, keeps the
-  // pair's low word.
   float gamma_prev = 1.f, alpha_prev = 1.f, rr0 = 0.f;
   const float eta2 = (float)(eta * eta), abs2 = (float)(abs_tol * abs_tol);
   int it = 0;
   for (;; ++it) {
     if (!load_halo_tagged(C, M, W, ep, P.timeout_ns)) return false;
     tock(C, PH_CG_BARRIER, t);
-    matvec_pass(C, M, &t);   // n = A m (m in C.lm)
+    matvec_pass(C, M, &t);   // w = A u (u in C.lm)
+    float v[3] = {0.f, 0.f, 0.f};
+    for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
+      const float4 u4 = C.lm[i];
+      const float uu[3] = {u4.x, u4.y, u4.z};
+      float w[3];
+      finish_product(C, i, uu, w);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        C.w[3 * i + k] = w[k];
+        const float rk = C.r[3 * i + k];
+        v[0] += rk * uu[k];
+        v[1] += w[k] * uu[k];
+        v[2] += rk * rk;
+      }
+    }
+    block_reduce_df<3>(C, v, active_warps);
+    write_cg_slot(C, W, ep);
+    ++n_pub;
     if (!reduce_cg_slots(C, W, ep, n_pub, P.timeout_ns)) return false;
     tock(C, PH_CG_REDUCE, t);
+    // scalars: every thread evaluates the same FP32 recurrences from the same
+    // FP32-pair grid sums (identical in every CTA); delta - beta*gamma/alpha_prev,
+    // the one cancelling difference, keeps the pair's low word.
     const float gamma = C.red_df[0].x, rr = C.red_df[2].x;
     if (it == 0) rr0 = rr;
     float beta = 0.f, denom;
@@ -732,7 +693,7 @@ __device__ bool pcg(Ctx& C, const MeshDev& M, const WorkDev& W, const SolveParam
       neg_curv = dec >= 2;
       if (dec == 3) {
         // non-positive curvature on the first direction: take the
-        // preconditioned steepest-descent direction u0 (== C.ucg at it 0)
+        // preconditioned steepest-descent direction u0
         for (int i = threadIdx.x; i < C.n_own; i += blockDim.x)
 #pragma unroll
           for (int k = 0; k < 3; ++k) C.x[3 * i + k] = C.ucg[3 * i + k];
@@ -740,42 +701,27 @@ __device__ bool pcg(Ctx& C, const MeshDev& M, const WorkDev& W, const SolveParam
       __syncthreads();
       break;
     }
+    // p = u + beta p; s = w + beta s; x += alpha p; r -= alpha s; u = M^-1 r
     ++ep;
-    const float a = alpha, b = beta;
-    float pv[3] = {0.f, 0.f, 0.f};
     for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
-      const float4 m4 = C.lm[i];
-      const float m[3] = {m4.x, m4.y, m4.z};
-      float n[3];
-      finish_product(C, i, m, n);
-      float mn[3], wn[3];
-      float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+      float rn[3], un[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         const int j = 3 * i + k;
-        const float z = n[k] + b * C.z[j];
-        const float q = m[k] + b * C.q[j];
-        const float s = C.w[j] + b * C.s[j];
-        const float p = C.ucg[j] + b * C.p[j];
-        C.z[j] = z; C.q[j] = q; C.s[j] = s; C.p[j] = p;
-        C.x[j] += a * p;
-        const float r = C.r[j] - a * s;
-        const float uu = C.ucg[j] - a * q;
-        const float w = C.w[j] - a * z;
-        C.r[j] = r; C.ucg[j] = uu; C.w[j] = w;
-        wn[k] = w;
-        s0 += r * uu;
-        s1 += w * uu;
-        s2 += r * r;
+        const float pk = C.ucg[j] + beta * C.p[j];
+        const float sk = C.w[j] + beta * C.s[j];
+        C.p[j] = pk;
+        C.s[j] = sk;
+        C.x[j] += alpha * pk;
+        rn[k] = C.r[j] - alpha * sk;
+        C.r[j] = rn[k];
       }
-      apply_minv(C.minv + 6 * i, wn, mn);
-      pv[0] += s0; pv[1] += s1; pv[2] += s2;
-      C.lm[i] = make_float4(mn[0], mn[1], mn[2], 0.f);
-      publish_node(C, M, W, i, mn, ep);
+      apply_minv(C.minv + 6 * i, rn, un);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) C.ucg[3 * i + k] = un[k];
+      C.lm[i] = make_float4(un[0], un[1], un[2], 0.f);
+      publish_node(C, M, W, i, un, ep);
     }
-    block_reduce_df<3>(C, pv, active_warps);
-    write_cg_slot(C, W, ep);
-    ++n_pub;
     tock(C, PH_CG_UPDATE, t);
   }
   iters = it;

@@ -1,0 +1,91 @@
+"""Batched solves (one CTA per solve, jobs from a queue) on the GPU: parity
+with the FP64 oracle and with the single-solve kernel, independence of a
+job's result from the rest of the batch, uneven meshes in one launch."""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import Problem
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def F():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2103_16747_b300 as F
+    return F
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+def _batch(F, meshes, handles, inds, tol=1e-6, max_newton=None):
+    out = [np.zeros((m.n_nodes, 3)) for m in meshes]
+    frc = [np.zeros((d.n_steps, 3)) for d in inds]
+    opt = None
+    if max_newton is not None:
+        opt = F.fem_default_options()
+        opt.max_newton = max_newton
+    rc, st = F.fem_solve_batch(handles, inds, tol, opt, out, frc)
+    return rc, out, frc, st
+
+
+def test_batch_cube_matches_oracle(F):
+    m, ind = W.cube_sphere()
+    h = F.fem_create_mesh(m.nodes, m.tets, m.tet_material, m.materials, m.fixed_nodes)
+    ref = Problem(m, ind).solve(tol=1e-10)
+    rc, out, frc, st = _batch(F, [m] * 3, [h] * 3, [ind] * 3)
+    assert rc == 0
+    for k in range(3):
+        assert st[k].steps_done == 10 and st[k].residual <= 1e-6 * st[k].scale
+        assert rel(out[k], ref.u) <= 1e-4
+        assert max(rel(frc[k][s], ref.step_force[s]) for s in range(10)) <= 1e-3
+    # identical jobs give bitwise identical results whichever CTA ran them
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
+    F.fem_destroy_mesh(h)
+
+
+def test_batch_fingertip_matches_golden_and_is_mix_independent(F):
+    g = np.load(os.path.join(HERE, "golden", "fingertip_sphere_oracle.npz"))
+    m, ind = W.fingertip_sphere()
+    draws = W.draw_indentations(m, 5, seed=77)
+    h = F.fem_create_mesh(m.nodes, m.tets, m.tet_material, m.materials, m.fixed_nodes)
+    # deep random draws need more Newton iterations in their last load steps
+    # than the default cap allows
+    rc, out, frc, st = _batch(F, [m] * 6, [h] * 6, [ind] + draws, max_newton=200)
+    assert rc == 0, [s.status for s in st]
+    e_u = rel(out[0], g["u"])
+    e_f = max(rel(frc[0][s], g["step_force"][s]) for s in range(20))
+    print(f"batch fingertip: rel-L2(u)={e_u:.2e} max rel F={e_f:.2e} newton={st[0].newton_iters} "
+          f"cg={st[0].cg_iters} kernel={st[0].kernel_ms:.1f} ms")
+    assert e_u <= 1e-4 and e_f <= 1e-3
+    # the same job alone: bitwise identical to its result inside the mix
+    rc1, out1, frc1, _ = _batch(F, [m], [h], [draws[2]], max_newton=200)
+    assert rc1 == 0
+    assert np.array_equal(out1[0], out[3]) and np.array_equal(frc1[0], frc[3])
+    # every draw certified by the oracle's own FP64 residual
+    for k, d in enumerate(draws):
+        rn, scale, _ = Problem(m, d).residual_norm(out[k + 1], d.n_steps)
+        assert rn <= 1e-6 * scale, (k, rn, scale)
+    F.fem_destroy_mesh(h)
+
+
+def test_batch_uneven_meshes(F):
+    jobs = W.uneven_fingertips(3, seed=5, tet_min=4e3, tet_max=2e4)
+    meshes = [m for m, _ in jobs]
+    inds = [d for _, d in jobs]
+    handles = [F.fem_create_mesh(m.nodes, m.tets, m.tet_material, m.materials, m.fixed_nodes) for m in meshes]
+    rc, out, frc, st = _batch(F, meshes, handles, inds, max_newton=200)
+    assert rc == 0, [s.status for s in st]
+    for k, (m, d) in enumerate(jobs):
+        rn, scale, _ = Problem(m, d).residual_norm(out[k], d.n_steps)
+        assert rn <= 1e-6 * scale
+    for h in handles:
+        F.fem_destroy_mesh(h)
