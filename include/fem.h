@@ -83,7 +83,18 @@ typedef struct {
     int32_t max_backtracks;   /* Armijo halvings per Newton iteration (default 30)    */
     int32_t tangent;          /* FEM_TANGENT_* (default ADAPTIVE)                     */
     double  barrier_timeout_s;/* bound on every device-side wait (default 5 s)        */
+    int32_t batch_engine;     /* fem_solve_batch: FEM_BATCH_AUTO (default),           */
+                              /* FEM_BATCH_GROUPS or FEM_BATCH_CLUSTERS                */
+    int32_t batch_parts;      /* CTAs per solve in fem_solve_batch (clusters: 1, 2,   */
+                              /* 4, 8 or 16); 0 = chosen from the largest mesh        */
 } fem_options;
+
+/* engines of fem_solve_batch */
+#define FEM_BATCH_AUTO     0
+#define FEM_BATCH_GROUPS   1  /* cooperative launch of CTA groups, one solve per group;  */
+                              /* parts sync through global memory (bounded waits)       */
+#define FEM_BATCH_CLUSTERS 2  /* one thread-block cluster per solve; parts sync through */
+                              /* distributed shared memory and cluster barriers         */
 
 typedef struct {
     int32_t status;                         /* FEM_OK or the FEM_ERR_* of fem_solve    */
@@ -101,9 +112,11 @@ typedef struct {
                                                eval, tangent, pcg init, pcg reduce+halo,
                                                pcg tangent product, pcg vector update,
                                                pcg grid barrier, total, pcg scalars,
-                                               pcg gather                              */
+                                               pcg gather. fem_solve_batch: fractions
+                                               of that solve's own time instead        */
     double  phase_max_ms[10];               /* the same phases, largest over CTAs       */
     double  phase_min_ms[10];               /* the same phases, smallest over CTAs      */
+                                            /* (both 0 in fem_solve_batch)              */
     int32_t newton_per_step[FEM_MAX_STEPS];
     int32_t cg_per_step[FEM_MAX_STEPS];
     double  residual_per_step[FEM_MAX_STEPS];
@@ -209,19 +222,25 @@ typedef struct {
  * meshes[i] (the same handle may appear any number of times; all meshes must be
  * on the current device) and indenters[i]; prescribed values set with
  * fem_set_dirichlet_values are not used here (fixed DOFs are held at 0).
- * One CTA runs one solve with only CTA-local synchronisation and takes the next
- * job from a queue, so uneven meshes share the launch; a solve's result does
- * not depend on the other jobs. The launch goes to meshes[0]'s stream; the
- * call synchronises it. The per-solve workspace (~200 B per node + 128 B per
- * part tet) is allocated stream-ordered for the call and released before it
- * returns.
+ * A slot of opt->batch_parts CTAs runs one solve (each mesh is cut into that
+ * many parts, once per part count) and takes the next job from a queue when
+ * done, so uneven meshes share the launch; the slots are CTA groups of one
+ * cooperative launch (FEM_BATCH_GROUPS, the default) or thread-block clusters
+ * (FEM_BATCH_CLUSTERS). A solve's result is bitwise independent of the other
+ * jobs and of which slot ran it. The launch goes to meshes[0]'s stream; the
+ * call synchronises it. The workspace (per solve ~56 B per node; per slot
+ * ~110 B per node and 128 B per part tet of the largest mesh) is allocated
+ * stream-ordered for the call and released before it returns.
  *   out_disp[i]           [n_nodes(i)*3] displacement after the last step.
  *   out_contact_force[i]  [n_steps(i)*3] resultant contact force per step (or
  *                         out_contact_force == NULL).
  *   stats[i]              per-solve statistics (or stats == NULL); kernel_ms is
  *                         the whole launch.
  * Returns FEM_OK if every solve converged, else the first solve's error code
- * (each stats[i].status holds its own).
+ * (each stats[i].status holds its own; FEM_ERR_TIMEOUT for a solve whose
+ * group abandoned a bounded wait, or that never started because of it).
+ * FEM_ERR_TOO_LARGE if a part of the largest mesh does not fit one CTA or no
+ * slot of that size fits the GPU.
  */
 int fem_solve_batch(fem_mesh* const* meshes, const fem_indenter* indenters, int32_t n, double tol,
                     const fem_options* opt, double* const* out_disp, double* const* out_contact_force,

@@ -32,6 +32,7 @@ ERR_NAMES = {0: "FEM_OK", -1: "FEM_ERR_ARG", -2: "FEM_ERR_DEGENERATE_TET", -3: "
 FEM_SPHERE, FEM_CYLINDER, FEM_BOX, FEM_PLANE = 0, 1, 2, 3
 FEM_MAX_STEPS = 256
 FEM_TANGENT_PROJECTED, FEM_TANGENT_EXACT, FEM_TANGENT_ADAPTIVE, FEM_TANGENT_ABS = 0, 1, 2, 3
+FEM_BATCH_AUTO, FEM_BATCH_GROUPS, FEM_BATCH_CLUSTERS = 0, 1, 2
 PHASES = ("eval", "tangent", "pcg_init", "pcg_reduce", "pcg_matvec", "pcg_update", "pcg_barrier", "total",
           "pcg_scalar", "pcg_gather")
 
@@ -50,7 +51,7 @@ class fem_options(C.Structure):
     _fields_ = [("c_kappa", C.c_double), ("max_newton", C.c_int32), ("max_cg", C.c_int32),
                 ("cg_rtol_max", C.c_double), ("cg_rtol_min", C.c_double),
                 ("max_backtracks", C.c_int32), ("tangent", C.c_int32),
-                ("barrier_timeout_s", C.c_double)]
+                ("barrier_timeout_s", C.c_double), ("batch_engine", C.c_int32), ("batch_parts", C.c_int32)]
 
 
 class fem_stats(C.Structure):

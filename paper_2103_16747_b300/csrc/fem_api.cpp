@@ -9,10 +9,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <string>
@@ -99,16 +101,16 @@ struct fem_mesh {
   std::vector<int> csr_ptr, csr_ent;   // node -> (tet << 2 | corner), new numbering
   double h_bar = 0, scale_floor = 0;
   int64_t n_candidates = 0;
-  MeshDev dev{};
+  MeshDev dev{};                 // partition of the single-solve kernel (one part per CTA)
   WorkDev work{};
-  int smem_bytes = 0;
+  SmemLayout layout{};
+  PartDims dims{};
   std::vector<void*> owned;     // every device allocation of the mesh
-  std::vector<void*> part_owned, bpart_owned;
-  size_t bytes = 0, part_bytes = 0, bpart_bytes = 0;
-  MeshDev bdev{};                // batch partition (built on first batched use)
-  bool has_batch_partition = false;
-  int bsmem_bytes = 0;
-  MeshDev* d_bdev = nullptr;     // device copy of bdev
+  std::vector<void*> part_owned, cpart_owned;
+  size_t bytes = 0, part_bytes = 0, cpart_bytes = 0;
+  MeshDev cdev{};                // partition for clustered solves (built on first batched use)
+  PartDims cdims{};
+  int c_parts = 0;               // parts of cdev (0: not built)
   // indenter
   bool has_indenter = false;
   int shape = 0;
@@ -128,11 +130,13 @@ cudaError_t launch_permute(const double* src, double* dst, const int* perm, int 
 
 namespace {
 
-// batch: the partition of the batched kernel (no part limit, whole part in one
-// shared-memory chunk, tangents live in the per-solve workspaces).
-int build_partitions(fem_mesh* m, int n_parts, bool batch = false) {
+// Cut the (Morton-ordered) node range into n_parts contiguous parts and build
+// the per-part arrays: part tets (every tet touching an owned node), local
+// node ids, local node->tet lists, and the halo tables. Fills the partition
+// fields of D (the mesh-wide fields are copied from m->dev) and dims; device
+// arrays go to o (freed first) and their bytes to by.
+int build_partition(fem_mesh* m, int n_parts, MeshDev& D, PartDims& dims, std::vector<void*>& o, size_t& by) {
   const int Nn = (int)m->n_nodes, Nt = (int)m->n_tets;
-  if (!batch && n_parts > 256) return fail(FEM_ERR_TOO_LARGE, "at most 256 parts (asked %d)", n_parts);
   // contiguous node ranges; a part's cost is its unique tets (halo tets
   // included, each computed once per part) plus its owned nodes. The cut
   // target is found by bisection so that exactly n_parts ranges result.
@@ -179,10 +183,10 @@ int build_partitions(fem_mesh* m, int n_parts, bool batch = false) {
     for (int i = nb[p]; i < nb[p + 1]; ++i) part_of[i] = p;
 
   std::vector<int> tb(n_parts + 1, 0), hb(n_parts + 1, 0), halo;
-
+  std::vector<unsigned> halo_src;
   std::vector<ushort4> pt_nodes;
   std::vector<double> pt_dminv_aos, pt_vol;
-  std::vector<int> pt_info, pt_tet;
+  std::vector<int> pt_info;
   std::vector<int> lcsr_ptr(Nn + 1, 0);
   std::vector<unsigned> lcsr;
   std::vector<int> local_of_tet(Nt, -1);
@@ -223,7 +227,6 @@ int build_partitions(fem_mesh* m, int n_parts, bool batch = false) {
       pt_vol.push_back(m->vol[t]);
       const int owner = part_of[mn] == p ? 1 : 0;
       pt_info.push_back(m->mat[t] | (owner << 16));
-      pt_tet.push_back(t);
     }
     for (int i = nb[p]; i < nb[p + 1]; ++i) {
       lcsr_ptr[i] = (int)lcsr.size();
@@ -235,6 +238,10 @@ int build_partitions(fem_mesh* m, int n_parts, bool batch = false) {
     for (int t : tl) local_of_tet[t] = -1;
     for (int g : hl) local_of_node[g] = -1;
     for (int i = nb[p]; i < nb[p + 1]; ++i) local_of_node[i] = -1;
+    for (int g : hl) {
+      const int q = part_of[g];
+      halo_src.push_back(((unsigned)q << 16) | (unsigned)(g - nb[q]));
+    }
     halo.insert(halo.end(), hl.begin(), hl.end());
     tb[p + 1] = (int)pt_nodes.size();
     hb[p + 1] = (int)halo.size();
@@ -247,45 +254,16 @@ int build_partitions(fem_mesh* m, int n_parts, bool batch = false) {
   std::vector<double> pt_dminv((size_t)9 * total_pt);
   for (int e = 0; e < total_pt; ++e)
     for (int k = 0; k < 9; ++k) pt_dminv[(size_t)k * total_pt + e] = pt_dminv_aos[(size_t)9 * e + k];
-
   int max_lcsr = 0;
   for (int p = 0; p < n_parts; ++p) max_lcsr = std::max(max_lcsr, lcsr_ptr[nb[p + 1]] - lcsr_ptr[nb[p]]);
-  int dev_smem = 0;
-  CUDA_TRY(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device), "smem attr");
-  const int static_smem = 8 * kRed + 64;
-  int resident = 0, chunk = max_pt, smem_total = 0;
-  if (batch) {
-    smem_total = batch_smem_layout(max_own, max_loc, max_pt).total;
-    if (smem_total + static_smem > dev_smem) return FEM_ERR_TOO_LARGE;   // caller retries with more parts
-  } else {
-    // resident: the whole part in one chunk with its tangent and local CSR in
-    // shared memory; otherwise stream them from global memory in chunks
-    resident = 1;
-    SmemLayout L = smem_layout(max_own, max_loc, chunk, max_pt, max_lcsr);
-    if (L.total + static_smem > dev_smem) {
-      resident = 0;
-      chunk = std::min(kChunk, max_pt);
-      L = smem_layout(max_own, max_loc, chunk, 0, 0);
-    }
-    if (L.total + static_smem > dev_smem)
-      return fail(FEM_ERR_TOO_LARGE, "part needs %d B shared memory, device allows %d", L.total + static_smem,
-                  dev_smem);
-    int per_sm = 0, n_sm = 0;
-    CUDA_TRY(solve_kernel_occupancy(L.total, &per_sm), "occupancy");
-    CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, m->device), "sm count");
-    if (per_sm * n_sm < n_parts)
-      return fail(FEM_ERR_TOO_LARGE, "%d parts exceed the %d co-resident CTAs", n_parts, per_sm * n_sm);
-    smem_total = L.total;
-  }
 
-  std::vector<void*>& o = batch ? m->bpart_owned : m->part_owned;
-  size_t& by = batch ? m->bpart_bytes : m->part_bytes;
   for (void* q : o) cudaFree(q);
   o.clear();
   m->bytes -= by;
   by = 0;
   cudaStream_t s = m->stream;
   int *d_nb, *d_tb, *d_hb, *d_halo, *d_info, *d_lcsr_ptr;
+  unsigned* d_hsrc;
   ushort4* d_ptn;
   double *d_dminv, *d_vol;
   unsigned* d_lcsr;
@@ -293,67 +271,186 @@ int build_partitions(fem_mesh* m, int n_parts, bool batch = false) {
   CUDA_TRY(upload(&d_tb, tb, s, o, by), "upload");
   CUDA_TRY(upload(&d_hb, hb, s, o, by), "upload");
   CUDA_TRY(upload(&d_halo, halo, s, o, by), "upload");
+  CUDA_TRY(upload(&d_hsrc, halo_src, s, o, by), "upload");
   CUDA_TRY(upload(&d_ptn, pt_nodes, s, o, by), "upload");
   CUDA_TRY(upload(&d_dminv, pt_dminv, s, o, by), "upload");
   CUDA_TRY(upload(&d_vol, pt_vol, s, o, by), "upload");
   CUDA_TRY(upload(&d_info, pt_info, s, o, by), "upload");
   CUDA_TRY(upload(&d_lcsr_ptr, lcsr_ptr, s, o, by), "upload");
   CUDA_TRY(upload(&d_lcsr, lcsr, s, o, by), "upload");
-  float4* d_tan = nullptr;
-  double* d_part = nullptr;
-  unsigned long long* d_slot = nullptr;
-  if (!batch) {
-    CUDA_TRY(alloc(&d_tan, (size_t)kTanVec * total_pt, o, by), "alloc tangent");
-    CUDA_TRY(alloc(&d_part, (size_t)2 * n_parts * kRed, o, by), "alloc partials");
-    CUDA_TRY(alloc(&d_slot, (size_t)12 * n_parts + 2, o, by), "alloc slots");
-  }
   m->bytes += by;
-  MeshDev& D = batch ? m->bdev : m->dev;
-  if (batch) D = m->dev;   // shared fields (sizes, X, masks, penalty, materials)
+  D = m->dev;   // mesh-wide fields (sizes, X, masks, penalty, materials)
   D.n_parts = n_parts;
   D.total_pt = total_pt;
   D.max_own = max_own;
   D.max_loc = max_loc;
   D.max_pt = max_pt;
   D.max_lcsr = max_lcsr;
-  D.chunk = chunk;
-  D.resident = resident;
+  D.resident = 0;
   D.part_node_begin = d_nb;
   D.part_tet_begin = d_tb;
   D.part_halo_begin = d_hb;
   D.halo_nodes = d_halo;
+  D.halo_src = d_hsrc;
   D.pt_nodes = d_ptn;
   D.pt_dminv = d_dminv;
   D.pt_vol = d_vol;
   D.pt_info = d_info;
   D.lcsr_ptr = d_lcsr_ptr;
   D.lcsr = d_lcsr;
-  if (batch) {
-    m->bsmem_bytes = smem_total;
-    m->has_batch_partition = true;
-  } else {
-    m->work.tangent = d_tan;
-    m->work.partials = d_part;
-    m->work.cgslot = d_slot;
-    m->smem_bytes = smem_total;
-  }
+  dims = PartDims{max_own, max_loc, max_pt, max_lcsr};
   CUDA_TRY(cudaStreamSynchronize(s), "partition upload");
   return FEM_OK;
 }
 
-// Batch partition: parts of about 1000 part tets, refined until one part fits
-// the batched kernel's shared memory.
-int ensure_batch_partition(fem_mesh* m) {
-  if (m->has_batch_partition) return FEM_OK;
-  int n = (int)std::max<int64_t>(1, (m->n_tets + 699) / 700);
-  n = (int)std::min<int64_t>(n, std::max<int64_t>(1, m->n_nodes / 8));
-  for (int attempt = 0; attempt < 8; ++attempt) {
-    const int rc = build_partitions(m, n, true);
-    if (rc == FEM_OK) return FEM_OK;
-    if (rc != FEM_ERR_TOO_LARGE) return rc;
-    n = n * 3 / 2 + 1;
+// Placement of one CTA's working arrays for parts up to the sizes in d, with
+// `budget` bytes of dynamic shared memory. First choice: everything in shared
+// memory with the whole part in one chunk. Otherwise chunks of kChunk tets,
+// and the arrays in order of how often the PCG touches them go to shared
+// memory while they fit; the rest go to the CTA's global scratch region (the
+// tangent, tet ids and node->tet lists are then read from their global
+// arrays). Returns total = -1 if even the fixed part does not fit.
+SmemLayout plan_layout(const PartDims& d, int budget) {
+  SmemLayout L{};
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    const bool resident = attempt == 0;
+    const int CH = resident ? std::max(d.max_pt, 1) : std::max(1, std::min(kChunk, d.max_pt));
+    const bool multi = CH < d.max_pt;
+    int o = 0, g = 0;
+    bool all_shared = true;
+    auto fits = [&](int bytes) { return align_up(o + bytes, 16) <= budget; };
+    auto take = [&](int bytes) { const int at = o; o = align_up(o + bytes, 16); return at; };
+    auto place = [&](int bytes) {
+      if (fits(bytes)) return take(bytes);
+      all_shared = false;
+      const int at = g;
+      g = align_up(g + bytes, 16);
+      return at | kInGlobal;
+    };
+    auto place_opt = [&](int bytes) {
+      if (fits(bytes)) return take(bytes);
+      all_shared = false;
+      return -1;
+    };
+    L.lm = take(16 * d.max_loc);
+    L.red = take(8 * kRed * (kBlock / 32 + 1));
+    L.chunk = take(96 * CH);
+    if (o > budget) {
+      if (resident) continue;
+      L.total = -1;
+      return L;
+    }
+    L.acc = place(24 * d.max_own);
+    L.r = place(12 * d.max_own);
+    L.ucg = place(12 * d.max_own);
+    L.w = place(12 * d.max_own);
+    L.p = place(12 * d.max_own);
+    L.s = place(12 * d.max_own);
+    L.x = place(12 * d.max_own);
+    L.minv = place(24 * d.max_own);
+    L.hc = place(12 * d.max_own);
+    L.mask = place(d.max_own);
+    L.cursor = place(multi ? 24 * d.max_own : 16);
+    L.ptn = place_opt(8 * d.max_pt);
+    const int lptr_bytes = align_up(4 * (d.max_own + 1), 16);
+    if (fits(lptr_bytes + 4 * d.max_lcsr)) {
+      L.lptr = take(4 * (d.max_own + 1));
+      L.lcsr = take(4 * d.max_lcsr);
+    } else {
+      L.lptr = L.lcsr = -1;
+      all_shared = false;
+    }
+    L.ut = place(24 * d.max_loc);
+    L.tan = place_opt(16 * kTanVec * d.max_pt);
+    if (resident && !all_shared) continue;
+    L.chunk_tets = CH;
+    L.total = o;
+    L.gbytes = align_up(g, 256);
+    return L;
   }
-  return fail(FEM_ERR_TOO_LARGE, "no batch partition fits in shared memory");
+  L.total = -1;
+  return L;
+}
+
+int smem_budget(const fem_mesh* m, int static_smem) {
+  int dev_smem = 0;
+  cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device);
+  return dev_smem - static_smem;
+}
+
+// Partition of the single-solve kernel: n_parts CTAs, all co-resident.
+int build_partitions(fem_mesh* m, int n_parts) {
+  if (n_parts > 256) return fail(FEM_ERR_TOO_LARGE, "at most 256 parts (asked %d)", n_parts);
+  MeshDev D{};
+  PartDims dims{};
+  std::vector<void*> o;
+  size_t by = 0;
+  int rc = build_partition(m, n_parts, D, dims, o, by);
+  if (rc) {
+    for (void* q : o) cudaFree(q);
+    m->bytes -= by;
+    return rc;
+  }
+  size_t added = by;   // build_partition counted these bytes in m->bytes
+  auto drop = [&](int code) {
+    for (void* q : o) cudaFree(q);
+    m->bytes -= added;
+    return code;
+  };
+  int static_smem = 0, per_sm = 0, n_sm = 0;
+  {
+    cudaError_t e = solve_kernel_attrs(0, &static_smem, nullptr);
+    if (e != cudaSuccess) return drop(cuda_fail(e, "kernel attributes"));
+  }
+  const SmemLayout L = plan_layout(dims, smem_budget(m, static_smem));
+  if (L.total < 0)
+    return drop(fail(FEM_ERR_TOO_LARGE, "a part of %d owned / %d local nodes does not fit one CTA", dims.max_own,
+                     dims.max_loc));
+  {
+    cudaError_t e = solve_kernel_attrs(L.total, nullptr, &per_sm);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, m->device);
+    if (e != cudaSuccess) return drop(cuda_fail(e, "occupancy"));
+  }
+  if (per_sm * n_sm < n_parts)
+    return drop(fail(FEM_ERR_TOO_LARGE, "%d parts exceed the %d co-resident CTAs", n_parts, per_sm * n_sm));
+  float4* d_tan = nullptr;
+  double* d_part = nullptr;
+  unsigned long long* d_slot = nullptr;
+  unsigned char* d_scr = nullptr;
+  {
+    cudaError_t e = alloc(&d_tan, (size_t)kTanVec * D.total_pt, o, by);
+    if (e == cudaSuccess) e = alloc(&d_part, (size_t)2 * n_parts * kRed, o, by);
+    if (e == cudaSuccess) e = alloc(&d_slot, (size_t)12 * n_parts + 2, o, by);
+    if (e == cudaSuccess && L.gbytes > 0) e = alloc(&d_scr, (size_t)L.gbytes * n_parts, o, by);
+    m->bytes += by - added;
+    added = by;
+    if (e != cudaSuccess) return drop(cuda_fail(e, "alloc partition workspace"));
+  }
+  for (void* q : m->part_owned) cudaFree(q);
+  m->bytes -= m->part_bytes;
+  m->part_owned = o;
+  m->part_bytes = by;
+  D.resident = L.tan >= 0 ? 1 : 0;
+  m->dev = D;
+  m->dims = dims;
+  m->layout = L;
+  m->work.tangent = d_tan;
+  m->work.partials = d_part;
+  m->work.cgslot = d_slot;
+  m->work.cta_scratch = d_scr;
+  m->work.cta_stride = L.gbytes;
+  return FEM_OK;
+}
+
+// Partition for batched solves with `parts` CTAs per solve (rebuilt when the
+// part count changes).
+int ensure_batch_partition(fem_mesh* m, int parts) {
+  if (m->c_parts == parts) return FEM_OK;
+  m->c_parts = 0;
+  const int rc = build_partition(m, parts, m->cdev, m->cdims, m->cpart_owned, m->cpart_bytes);
+  if (rc) return rc;
+  m->c_parts = parts;
+  return FEM_OK;
 }
 
 int default_parts(const fem_mesh* m) {
@@ -377,6 +474,8 @@ void fem_default_options(fem_options* opt) {
   opt->max_backtracks = 30;
   opt->tangent = FEM_TANGENT_ADAPTIVE;
   opt->barrier_timeout_s = 5.0;
+  opt->batch_engine = FEM_BATCH_AUTO;
+  opt->batch_parts = 0;
 }
 
 const char* fem_last_error(void) { return g_err.c_str(); }
@@ -384,7 +483,7 @@ const char* fem_last_error(void) { return g_err.c_str(); }
 void fem_destroy_mesh(fem_mesh* m) {
   if (!m) return;
   for (void* q : m->part_owned) cudaFree(q);
-  for (void* q : m->bpart_owned) cudaFree(q);
+  for (void* q : m->cpart_owned) cudaFree(q);
   for (void* q : m->owned) cudaFree(q);
   delete m;
 }
@@ -627,6 +726,8 @@ int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, i
     if ((e = upload(&m->d_perm, m->perm, s, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "upload perm"));
     WorkDev& W = m->work;
     if ((e = alloc(&W.u, 3 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
+    if ((e = alloc(&W.R, 3 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
+    if ((e = alloc(&W.uprev, 3 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
     if ((e = alloc(&W.vpub, 6 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
     if ((e = alloc(&W.dpub, (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
     unsigned long long* d_bar;
@@ -679,7 +780,7 @@ int fem_mesh_info_get(const fem_mesh* m, fem_mesh_info* info) {
   info->max_owned_nodes = m->dev.max_own;
   info->max_local_nodes = m->dev.max_loc;
   info->max_part_tets = m->dev.max_pt;
-  info->smem_bytes = m->smem_bytes;
+  info->smem_bytes = m->layout.total;
   info->resident = m->dev.resident;
   info->h_bar = m->h_bar;
   info->scale_floor = m->scale_floor;
@@ -800,7 +901,7 @@ static int fill_params(fem_mesh* m, const fem_options* opt, int mode, int steps,
   return FEM_OK;
 }
 
-static int run_kernel(fem_mesh* m, const SolveParams& P, float* ms, StatsDev* hst) {
+static int run_kernel(fem_mesh* m, const WorkDev& W, const SolveParams& P, float* ms, StatsDev* hst) {
   cudaStream_t s = m->stream;
   CUDA_TRY(cudaMemsetAsync(m->work.barrier, 0, 2 * sizeof(unsigned long long), s), "reset barrier");
   CUDA_TRY(cudaMemsetAsync(m->work.cgslot, 0, sizeof(unsigned long long) * (12 * (size_t)m->dev.n_parts + 2), s),
@@ -809,7 +910,7 @@ static int run_kernel(fem_mesh* m, const SolveParams& P, float* ms, StatsDev* hs
            "reset published vectors");
   CUDA_TRY(cudaMemsetAsync(m->work.stats, 0, sizeof(StatsDev), s), "reset stats");
   CUDA_TRY(cudaMemsetAsync(m->work.stats->cycles_min, 0x7f, sizeof(long long) * PH_N, s), "reset stats");
-  CUDA_TRY(launch_solve(m->dev, m->work, P, s, ms), "solve kernel launch");
+  CUDA_TRY(launch_solve(m->dev, W, P, m->layout, s, ms), "solve kernel launch");
   int abort_flag = 0;
   CUDA_TRY(cudaMemcpyAsync(hst, m->work.stats, sizeof(StatsDev), cudaMemcpyDeviceToHost, s), "stats copy");
   CUDA_TRY(cudaMemcpyAsync(&abort_flag, m->work.abort_flag, sizeof(int), cudaMemcpyDeviceToHost, s), "flag copy");
@@ -848,7 +949,7 @@ int fem_solve(fem_mesh* m, int32_t load_steps, double tol, const fem_options* op
   CUDA_TRY(cudaMemsetAsync(m->work.step_force, 0, 3 * sizeof(double) * kMaxSteps, m->stream), "reset forces");
   StatsDev hst;
   float ms = 0.f;
-  rc = run_kernel(m, P, &ms, &hst);
+  rc = run_kernel(m, m->work, P, &ms, &hst);
   if (rc) return rc;
   if ((rc = copy_out_nodes(m, m->work.u, out_disp))) return rc;
   if ((rc = copy_out_nodes(m, m->work.out_fc, out_nodal_contact))) return rc;
@@ -901,115 +1002,190 @@ int fem_solve_batch(fem_mesh* const* meshes, const fem_indenter* ind, int32_t n,
   fem_options o;
   fem_default_options(&o);
   if (opt) o = *opt;
+  const bool clusters = o.batch_engine == FEM_BATCH_CLUSTERS;
   if (!(o.c_kappa > 0) || o.max_newton < 0 || o.max_cg < 1 || o.max_backtracks < 0 || !(o.cg_rtol_max > 0) ||
-      !(o.cg_rtol_min > 0) || o.cg_rtol_min > o.cg_rtol_max || o.tangent < 0 || o.tangent > 3)
+      !(o.cg_rtol_min > 0) || o.cg_rtol_min > o.cg_rtol_max || o.tangent < 0 || o.tangent > 3 ||
+      !(o.barrier_timeout_s > 0) || o.batch_engine < FEM_BATCH_AUTO || o.batch_engine > FEM_BATCH_CLUSTERS ||
+      o.batch_parts < 0 || o.batch_parts > 256 ||
+      (clusters && !(o.batch_parts == 0 || o.batch_parts == 1 || o.batch_parts == 2 || o.batch_parts == 4 ||
+                     o.batch_parts == 8 || o.batch_parts == 16)))
     return fail(FEM_ERR_ARG, "invalid fem_options");
+  int64_t max_tets = 0;
   for (int i = 0; i < n; ++i) {
     if (!meshes[i] || !out_disp[i]) return fail(FEM_ERR_ARG, "solve %d: NULL mesh or output", i);
     const fem_indenter& d = ind[i];
     int rc = validate_indenter(d.shape, d.pose, d.params, d.dir, d.depth_schedule, d.n_steps);
     if (rc) return fail(rc, "solve %d: %s", i, g_err.c_str());
+    max_tets = std::max(max_tets, meshes[i]->n_tets);
+  }
+  int n_sm = 1;
+  CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, meshes[0]->device), "sm count");
+  // CTAs per solve, from the largest mesh only (not from the number of jobs,
+  // so that a job gets the same partition alone and in any batch of meshes no
+  // larger than its own). Groups: about 1,000 tets per CTA with the SMs shared
+  // evenly between the groups. Clusters: about 2,500 tets per CTA, a power of
+  // two up to 16.
+  int parts = o.batch_parts;
+  if (parts == 0) {
+    if (clusters) {
+      parts = 1;
+      while (parts < 16 && max_tets > (int64_t)2500 * parts) parts *= 2;
+    } else {
+      int64_t g = (int64_t)std::llround((double)n_sm * 1000.0 / (double)std::max<int64_t>(max_tets, 1));
+      g = std::max<int64_t>(1, std::min<int64_t>(g, n_sm));
+      parts = (int)(n_sm / g);
+    }
   }
   const cudaStream_t s = meshes[0]->stream;
-  // batch partitions (built once per mesh) and their device copies
-  int smem = 0;
   std::vector<fem_mesh*> uniq;
   for (int i = 0; i < n; ++i)
     if (std::find(uniq.begin(), uniq.end(), meshes[i]) == uniq.end()) uniq.push_back(meshes[i]);
+  PartDims dims{0, 0, 0, 0};
+  size_t max_nodes = 0, max_pt = 0;
   for (fem_mesh* m : uniq) {
     if (m->device != meshes[0]->device) return fail(FEM_ERR_ARG, "all meshes must be on one device");
-    int rc = ensure_batch_partition(m);
+    if (m->n_nodes < parts) return fail(FEM_ERR_ARG, "a mesh of %lld nodes cannot be cut into %d parts",
+                                        (long long)m->n_nodes, parts);
+    int rc = ensure_batch_partition(m, parts);
     if (rc) return rc;
-    if (!m->d_bdev) {
-      CUDA_TRY(alloc(&m->d_bdev, 1, m->bpart_owned, m->bpart_bytes), "alloc batch mesh");
-      CUDA_TRY(cudaMemcpy(m->d_bdev, &m->bdev, sizeof(MeshDev), cudaMemcpyHostToDevice), "upload batch mesh");
-    }
-    smem = std::max(smem, m->bsmem_bytes);
+    dims.max_own = std::max(dims.max_own, m->cdims.max_own);
+    dims.max_loc = std::max(dims.max_loc, m->cdims.max_loc);
+    dims.max_pt = std::max(dims.max_pt, m->cdims.max_pt);
+    dims.max_lcsr = std::max(dims.max_lcsr, m->cdims.max_lcsr);
+    max_nodes = std::max(max_nodes, (size_t)m->n_nodes);
+    max_pt = std::max(max_pt, (size_t)m->cdev.total_pt);
   }
-  int per_sm = 0, n_sm = 0;
-  CUDA_TRY(batch_kernel_occupancy(smem, &per_sm), "batch occupancy");
-  CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, meshes[0]->device), "sm count");
-  if (per_sm < 1) return fail(FEM_ERR_TOO_LARGE, "batched kernel does not fit on an SM (%d B shared memory)", smem);
-  // workspace layout
+  int static_smem = 0;
+  if (clusters) CUDA_TRY(cluster_kernel_attrs(parts, 0, &static_smem, nullptr), "cluster kernel attributes");
+  else CUDA_TRY(group_kernel_attrs(0, &static_smem, nullptr), "group kernel attributes");
+  const SmemLayout L = plan_layout(dims, smem_budget(meshes[0], static_smem));
+  if (L.total < 0)
+    return fail(FEM_ERR_TOO_LARGE, "a part of %d owned / %d local nodes does not fit one CTA (%d parts)",
+                dims.max_own, dims.max_loc, parts);
+  int max_slots = 0;
+  if (clusters) {
+    CUDA_TRY(cluster_kernel_attrs(parts, L.total, nullptr, &max_slots), "cluster occupancy");
+  } else {
+    int per_sm = 0;
+    CUDA_TRY(group_kernel_attrs(L.total, nullptr, &per_sm), "group occupancy");
+    max_slots = per_sm * n_sm / parts;
+  }
+  if (max_slots < 1) return fail(FEM_ERR_TOO_LARGE, "no slot of %d CTAs fits the device", parts);
+  const int n_slots = std::min(n, max_slots);
+  if (getenv("FEM_VERBOSE"))
+    fprintf(stderr,
+            "fem_solve_batch: %s of %d CTAs, %d slots (max %d); part dims own %d loc %d pt %d lcsr %d; shared %d B, "
+            "global %d B per CTA; chunk %d; resident tan %d ids %d lists %d; ut %s\n",
+            clusters ? "clusters" : "groups", parts, n_slots, max_slots, dims.max_own, dims.max_loc, dims.max_pt,
+            dims.max_lcsr, L.total, L.gbytes, L.chunk_tets, L.tan >= 0, L.ptn >= 0, L.lcsr >= 0,
+            (L.ut & kInGlobal) ? "global" : "shared");
+  // workspace: per job outputs and schedule, the job table, the queue, then
+  // one scratch block per slot
   auto a256 = [](size_t b) { return (b + 255) / 256 * 256; };
   std::vector<size_t> off(n + 1, 0);
   for (int i = 0; i < n; ++i) {
-    const size_t Nn = (size_t)meshes[i]->n_nodes, T = (size_t)meshes[i]->bdev.total_pt;
-    const size_t K = (size_t)ind[i].n_steps;
-    off[i + 1] = off[i] + 4 * a256(24 * Nn) + 6 * a256(12 * Nn) + a256(24 * Nn) + a256(16 * kTanVec * T) +
-                 a256(24 * K) + a256(sizeof(StatsDev)) + a256(8 * K);
+    const size_t Nn = (size_t)meshes[i]->n_nodes, K = (size_t)ind[i].n_steps;
+    off[i + 1] = off[i] + 2 * a256(24 * Nn) + a256(24 * K) + a256(sizeof(StatsDev)) + a256(8 * K);
   }
   const size_t jobs_off = off[n], queue_off = jobs_off + a256(sizeof(BatchJob) * n);
-  const size_t total = queue_off + 256;
+  SlotScratch S{};
+  {
+    long long o2 = 0;
+    auto take = [&](size_t bytes) { const long long at = o2; o2 += (long long)a256(bytes); return at; };
+    S.ctrl = take(3 * sizeof(unsigned long long));
+    S.cgslot = take(sizeof(unsigned long long) * (12 * (size_t)parts + 2));
+    S.vpub = clusters ? 0 : take(48 * max_nodes);
+    const long long zero_end = o2;   // ctrl, counters and published words start at zero
+    S.partials = clusters ? 0 : take(16 * (size_t)parts * kRed);
+    S.dpub = take(16 * max_nodes);
+    S.R = take(24 * max_nodes);
+    S.uprev = take(24 * max_nodes);
+    S.tangent = take(L.tan >= 0 ? 16 : 16 * (size_t)kTanVec * max_pt);
+    S.cta = take((size_t)L.gbytes * parts);
+    S.cta_stride = L.gbytes;
+    S.stride = o2;
+    S.base = nullptr;
+    (void)zero_end;
+  }
+  const size_t slots_off = queue_off + 256;
+  const size_t total = slots_off + (size_t)S.stride * n_slots;
   unsigned char* ws = nullptr;
   {
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), total, s);
     if (e != cudaSuccess) return cuda_fail(e, "batch workspace");
   }
+  S.base = ws + slots_off;
   auto release = [&]() { cudaFreeAsync(ws, s); cudaStreamSynchronize(s); };
   std::vector<BatchJob> jobs(n);
+  std::vector<double*> stage(n);
   {
-    cudaError_t e = cudaMemsetAsync(ws, 0, jobs_off, s);
+    StatsDev st0;
+    memset(&st0, 0, sizeof(st0));
+    st0.status = ST_TIMEOUT;   // overwritten by the solve when it ends
+    for (int k = 0; k < PH_N; ++k) st0.cycles_min[k] = LLONG_MAX;
+    cudaError_t e = cudaMemsetAsync(ws, 0, total, s);
     for (int i = 0; i < n && e == cudaSuccess; ++i) {
-      const size_t Nn = (size_t)meshes[i]->n_nodes, T = (size_t)meshes[i]->bdev.total_pt;
-      const size_t K = (size_t)ind[i].n_steps;
+      fem_mesh* m = meshes[i];
+      const size_t Nn = (size_t)m->n_nodes, K = (size_t)ind[i].n_steps;
       unsigned char* b = ws + off[i];
       auto take = [&](size_t bytes) { unsigned char* at = b; b += a256(bytes); return at; };
       BatchJob& J = jobs[i];
-      J.mesh = meshes[i]->d_bdev;
+      J.mesh = m->cdev;
       J.u = reinterpret_cast<double*>(take(24 * Nn));
-      J.uprev = reinterpret_cast<double*>(take(24 * Nn));
-      J.R = reinterpret_cast<double*>(take(24 * Nn));
-      J.fc = reinterpret_cast<double*>(take(24 * Nn));
-      J.x = reinterpret_cast<float*>(take(12 * Nn));
-      J.r = reinterpret_cast<float*>(take(12 * Nn));
-      J.z = reinterpret_cast<float*>(take(12 * Nn));
-      J.p = reinterpret_cast<float*>(take(12 * Nn));
-      J.q = reinterpret_cast<float*>(take(12 * Nn));
-      J.hc = reinterpret_cast<float*>(take(12 * Nn));
-      J.minv = reinterpret_cast<float*>(take(24 * Nn));
-      J.tangent = reinterpret_cast<float4*>(take(16 * kTanVec * T));
+      J.out_fc = reinterpret_cast<double*>(take(24 * Nn));
       J.step_force = reinterpret_cast<double*>(take(24 * K));
       J.stats = reinterpret_cast<StatsDev*>(take(sizeof(StatsDev)));
       double* depths = reinterpret_cast<double*>(take(8 * K));
-      J.depths = depths;
-      J.shape = ind[i].shape;
-      J.n_steps = ind[i].n_steps;
+      stage[i] = J.out_fc;   // the displacement is unpermuted through this array after the solve
+      SolveParams& P = J.prm;
+      memset(&P, 0, sizeof(P));
+      P.mode = MODE_SOLVE;
+      P.n_steps = ind[i].n_steps;
+      P.tangent_mode = o.tangent;
+      P.max_newton = o.max_newton;
+      P.max_cg = o.max_cg;
+      P.max_backtracks = o.max_backtracks;
+      P.tol = tol;
+      P.c_kappa = o.c_kappa;
+      P.cg_rtol_max = o.cg_rtol_max;
+      P.cg_rtol_min = o.cg_rtol_min;
+      P.timeout_ns = (unsigned long long)(o.barrier_timeout_s * 1e9);
+      P.shape = ind[i].shape;
       for (int k = 0; k < 3; ++k) {
-        J.origin[k] = ind[i].pose[k];
-        J.dir[k] = ind[i].dir[k];
-        J.iparams[k] = ind[i].shape == FEM_PLANE ? 0.0 : ind[i].params[k];
+        P.origin[k] = ind[i].pose[k];
+        P.dir[k] = ind[i].dir[k];
+        P.iparams[k] = ind[i].shape == FEM_PLANE ? 0.0 : ind[i].params[k];
       }
-      for (int k = 0; k < 9; ++k) J.rot[k] = ind[i].pose[3 + k];
+      for (int k = 0; k < 9; ++k) P.R[k] = ind[i].pose[3 + k];
+      P.depths = depths;
       e = cudaMemcpyAsync(depths, ind[i].depth_schedule, 8 * K, cudaMemcpyDefault, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(J.stats, &st0, sizeof(StatsDev), cudaMemcpyHostToDevice, s);
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(ws + jobs_off, jobs.data(), sizeof(BatchJob) * n, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ws + queue_off, 0, 256, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ws + jobs_off, jobs.data(), sizeof(BatchJob) * n, cudaMemcpyHostToDevice, s);
+    // the host copies above are staged from pageable memory that lives until
+    // this function returns; wait before the launch so the launch's own
+    // timing covers the kernel alone
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { release(); return cuda_fail(e, "batch set-up"); }
   }
-  BatchParams P{};
-  P.n_jobs = n;
-  P.tangent_mode = o.tangent;
-  P.max_newton = o.max_newton;
-  P.max_cg = o.max_cg;
-  P.max_backtracks = o.max_backtracks;
-  P.tol = tol;
-  P.c_kappa = o.c_kappa;
-  P.cg_rtol_max = o.cg_rtol_max;
-  P.cg_rtol_min = o.cg_rtol_min;
   float ms = 0.f;
-  const int n_ctas = std::min(n, n_sm * per_sm);
-  cudaError_t e = launch_batch(reinterpret_cast<const BatchJob*>(ws + jobs_off), reinterpret_cast<int*>(ws + queue_off),
-                               P, smem, n_ctas, s, &ms);
+  cudaError_t e;
+  if (clusters)
+    e = launch_cluster(reinterpret_cast<const BatchJob*>(ws + jobs_off), n, reinterpret_cast<int*>(ws + queue_off), S,
+                       L, parts, n_slots, s, &ms);
+  else
+    e = launch_groups(reinterpret_cast<const BatchJob*>(ws + jobs_off), n, reinterpret_cast<int*>(ws + queue_off), S,
+                      L, parts, n_slots, (unsigned long long)(o.barrier_timeout_s * 1e9), s, &ms);
   if (e != cudaSuccess) { release(); return cuda_fail(e, "batch kernel"); }
   std::vector<StatsDev> hst(n);
   for (int i = 0; i < n && e == cudaSuccess; ++i) {
     fem_mesh* m = meshes[i];
     const BatchJob& J = jobs[i];
-    e = launch_permute(J.u, J.R, m->d_perm, (int)m->n_nodes, true, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(out_disp[i], J.R, 24 * (size_t)m->n_nodes, cudaMemcpyDefault, s);
+    e = launch_permute(J.u, stage[i], m->d_perm, (int)m->n_nodes, true, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out_disp[i], stage[i], 24 * (size_t)m->n_nodes, cudaMemcpyDefault, s);
     if (e == cudaSuccess && out_contact_force && out_contact_force[i])
-      e = cudaMemcpyAsync(out_contact_force[i], J.step_force, 24 * (size_t)J.n_steps, cudaMemcpyDefault, s);
+      e = cudaMemcpyAsync(out_contact_force[i], J.step_force, 24 * (size_t)J.prm.n_steps, cudaMemcpyDefault, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hst[i], J.stats, sizeof(StatsDev), cudaMemcpyDeviceToHost, s);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1019,6 +1195,7 @@ int fem_solve_batch(fem_mesh* const* meshes, const fem_indenter* ind, int32_t n,
   for (int i = 0; i < n; ++i) {
     int c = FEM_OK;
     if (hst[i].status == ST_NONFINITE) c = FEM_ERR_NONFINITE;
+    else if (hst[i].status == ST_TIMEOUT) c = FEM_ERR_TIMEOUT;
     else if (hst[i].status != ST_OK) c = FEM_ERR_NOT_CONVERGED;
     if (c != FEM_OK && code == FEM_OK) {
       code = c;
@@ -1038,6 +1215,9 @@ int fem_solve_batch(fem_mesh* const* meshes, const fem_indenter* ind, int32_t n,
       st.energy = hst[i].energy;
       st.kernel_ms = ms;
       st.exact_newton_iters = hst[i].exact_newton;
+      // per-solve phase split: shares of this solve's own clock (part 0)
+      const double tot = (double)hst[i].cycles[PH_TOTAL];
+      for (int k = 0; k < PH_N && k < 10; ++k) st.phase_ms[k] = tot > 0 ? (double)hst[i].cycles[k] / tot : 0.0;
       for (int k = 0; k < ind[i].n_steps; ++k) {
         st.newton_per_step[k] = hst[i].newton_per_step[k];
         st.cg_per_step[k] = hst[i].cg_per_step[k];
@@ -1058,8 +1238,10 @@ int fem_eval_residual(fem_mesh* m, const double* u, int32_t step, const fem_opti
   int rc = fill_params(m, opt, MODE_EVAL, m->n_steps, step, 1e-6, P);
   if (rc) return rc;
   if ((rc = copy_in_nodes(m, u, m->work.u))) return rc;
+  WorkDev W = m->work;
+  W.R = W.out_R;   // the evaluation's residual is the output
   StatsDev hst;
-  if ((rc = run_kernel(m, P, nullptr, &hst))) return rc;
+  if ((rc = run_kernel(m, W, P, nullptr, &hst))) return rc;
   if ((rc = copy_out_nodes(m, m->work.out_R, out_R))) return rc;
   if ((rc = copy_out_nodes(m, m->work.out_fc, out_fc))) return rc;
   CUDA_TRY(cudaStreamSynchronize(m->stream), "output copy");
@@ -1092,7 +1274,8 @@ int fem_eval_residual_noalloc(fem_mesh* m, const double* u, int32_t step, const 
   const size_t off_R = off_u + a256(node_bytes);
   const size_t off_fc = off_R + a256(node_bytes);
   const size_t off_stage = off_fc + a256(node_bytes);
-  const size_t need = off_stage + a256(node_bytes);
+  const size_t off_cta = off_stage + a256(node_bytes);
+  const size_t need = off_cta + (size_t)m->layout.gbytes * m->dev.n_parts;
   if (need > kNoAllocScratchBytes)
     return fail(FEM_ERR_TOO_LARGE,
                 "fem_eval_residual_noalloc: mesh needs %zu B of scratch, the fixed block holds %zu B "
@@ -1109,7 +1292,12 @@ int fem_eval_residual_noalloc(fem_mesh* m, const double* u, int32_t step, const 
   W.u = reinterpret_cast<double*>(b + off_u);
   W.out_R = reinterpret_cast<double*>(b + off_R);
   W.out_fc = reinterpret_cast<double*>(b + off_fc);
+  W.R = W.out_R;
   W.tangent = m->work.tangent;   // not read by the evaluation
+  if (m->layout.gbytes > 0) {
+    W.cta_scratch = b + off_cta;
+    W.cta_stride = m->layout.gbytes;
+  }
   double* stage = reinterpret_cast<double*>(b + off_stage);
   cudaStream_t s = m->stream;
   // the barrier word, the abort word and the statistics must start at zero
@@ -1117,7 +1305,7 @@ int fem_eval_residual_noalloc(fem_mesh* m, const double* u, int32_t step, const 
   CUDA_TRY(cudaMemsetAsync(W.stats->cycles_min, 0x7f, sizeof(long long) * PH_N, s), "clear scratch");
   CUDA_TRY(cudaMemcpyAsync(stage, u, node_bytes, cudaMemcpyDefault, s), "input copy");
   CUDA_TRY(launch_permute(stage, W.u, m->d_perm, (int)m->n_nodes, false, s), "permute");
-  CUDA_TRY(launch_solve(m->dev, W, P, s, nullptr), "evaluation kernel");
+  CUDA_TRY(launch_solve(m->dev, W, P, m->layout, s, nullptr), "evaluation kernel");
   StatsDev hst;
   int abort_flag = 0;
   CUDA_TRY(cudaMemcpyAsync(&hst, W.stats, sizeof(StatsDev), cudaMemcpyDeviceToHost, s), "stats copy");
@@ -1150,7 +1338,7 @@ int fem_apply_tangent(fem_mesh* m, const double* u, int32_t step, const fem_opti
   if ((rc = copy_in_nodes(m, u, m->work.u))) return rc;
   if ((rc = copy_in_nodes(m, p, const_cast<double*>(m->work.in_p)))) return rc;
   StatsDev hst;
-  if ((rc = run_kernel(m, P, nullptr, &hst))) return rc;
+  if ((rc = run_kernel(m, m->work, P, nullptr, &hst))) return rc;
   if ((rc = copy_out_nodes(m, m->work.out_y, out_y))) return rc;
   CUDA_TRY(cudaStreamSynchronize(m->stream), "output copy");
   return FEM_OK;
@@ -1170,7 +1358,8 @@ int fem_debug_barrier_timeout(double timeout_s) {
   SolveParams P{};
   P.mode = MODE_BARRIER_TEST;
   P.timeout_ns = (unsigned long long)(timeout_s * 1e9);
-  cudaError_t e = launch_solve(M, W, P, nullptr, nullptr);
+  const SmemLayout L{};
+  cudaError_t e = launch_solve(M, W, P, L, nullptr, nullptr);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   int flag = 0;
   if (e == cudaSuccess) e = cudaMemcpy(&flag, d + 1, sizeof(int), cudaMemcpyDeviceToHost);

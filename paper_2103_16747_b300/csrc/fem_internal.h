@@ -7,7 +7,8 @@
 namespace fem {
 
 constexpr int kBlock = 512;       // threads per CTA of the solve kernel
-constexpr int kChunk = 512;       // part tets staged per shared-memory chunk (1 per thread)
+constexpr int kChunk = 256;       // part tets per chunk of the evaluation passes (the tangent
+                                  // product stages half the bytes per tet: chunks of 2*kChunk)
 constexpr int kRed = 12;          // doubles per CTA reduction slot
 constexpr int kMaxSteps = 256;
 constexpr int kTanVec = 8;        // float4 groups of the stored per-tet tangent
@@ -24,8 +25,7 @@ enum Status : int {
 struct MeshDev {
   int n_nodes, n_tets, n_parts, total_pt;
   int max_own, max_loc, max_pt;
-  int chunk;                        // part tets per shared-memory chunk
-  int resident;                     // 1: tangent, tet ids and local CSR live in shared memory
+  int resident;                     // 1: the part's stored tangent lives in shared memory
   int max_lcsr;                     // most local-CSR entries of one part
   int n_materials;
   double scale_floor;               // E_max * h_bar^2 * 1e-3
@@ -33,6 +33,7 @@ struct MeshDev {
   const int* part_tet_begin;        // [P+1]  range into the part-tet arrays
   const int* part_halo_begin;       // [P+1]  range into halo_nodes
   const int* halo_nodes;            // global ids of non-owned local nodes (local id n_own + j)
+  const unsigned* halo_src;         // same order: (owner part << 16) | index among the owner's nodes
   const ushort4* pt_nodes;          // [total_pt] local node ids of each part tet
   const double* pt_dminv;           // [9][total_pt] Dm^-1, row-major entries, SoA
   const double* pt_vol;             // [total_pt]
@@ -61,11 +62,15 @@ struct StatsDev {
 };
 
 struct WorkDev {
-  double* u;                        // [3*n_nodes] displacement (published copy)
+  double* u;                        // [3*n_nodes] displacement (owned entries written by their part)
+  double* R;                        // [3*n_nodes] residual of the last evaluation
+  double* uprev;                    // [3*n_nodes] converged displacement of the previous load step
   const double* u_presc;            // [3*n_nodes] prescribed values (or null)
   unsigned long long* vpub;         // [2][n_nodes][3] published PCG vector, (epoch, FP32) words
   float4* dpub;                     // [n_nodes] published Newton direction
-  float4* tangent;                  // [kTanVec][total_pt]
+  float4* tangent;                  // [kTanVec][total_pt] (parts whose tangent is not resident)
+  unsigned char* cta_scratch;       // per-CTA arrays that did not fit in shared memory
+  long long cta_stride;             // bytes per CTA in cta_scratch
   double* partials;                 // [2][P][kRed]
   unsigned long long* barrier;      // grid barrier arrival counter
   int* abort_flag;                  // set when any CTA gives up waiting
@@ -89,107 +94,68 @@ struct SolveParams {
   const double* depths;             // [n_steps] device
 };
 
-// Shared-memory layout of one CTA (bytes), identical on host and device.
-// With resident != 0 the part's stored tangent, tet node ids and local CSR are
-// kept in shared memory for the whole solve.
-struct SmemLayout {
-  int u, uprev, R, X, fc, kp, ut, chunk, red;     // double arrays
-  int x, r, ucg, w, z, q, s, p, acc, minv, hc;    // float arrays (3 or 6 per node)
-  int lm;                                         // float4 per local node
-  int tan, ptn, lptr, lcsr;                       // resident part data
-  int mask, cursor;
-  int total;
-};
+// Per-CTA working arrays and where they live. An offset with kInGlobal set is
+// a byte offset into the CTA's region of WorkDev::cta_scratch instead of
+// dynamic shared memory; the kernels use generic pointers, so placement does
+// not change the code that reads them. The host plans the layout (fem_api.cpp)
+// and passes it to the kernel.
+constexpr int kInGlobal = 1 << 30;
 
 __host__ __device__ inline int align_up(int v, int a) { return (v + a - 1) / a * a; }
 
-__host__ __device__ inline SmemLayout smem_layout(int max_own, int max_loc, int chunk, int res_pt,
-                                                  int res_lcsr) {
-  SmemLayout L;
-  int o = 0;
-  auto take = [&](int bytes) { int at = o; o = align_up(o + bytes, 16); return at; };
-  L.u = take(24 * max_own);
-  L.uprev = take(24 * max_own);
-  L.R = take(24 * max_own);
-  L.X = take(24 * max_own);
-  L.fc = take(24 * max_own);
-  L.kp = take(8 * max_own);
-  L.ut = take(24 * max_loc);
-  L.chunk = take(96 * chunk);                     // 4 corners x 3 doubles, or 4 x 6 floats
-  L.red = take(8 * kRed * (kBlock / 32 + 1));
-  L.tan = take(16 * kTanVec * res_pt);
-  L.x = take(12 * max_own);
-  L.r = take(12 * max_own);
-  L.ucg = take(12 * max_own);
-  L.w = take(12 * max_own);
-  L.z = take(12 * max_own);
-  L.q = take(12 * max_own);
-  L.s = take(12 * max_own);
-  L.p = take(12 * max_own);
-  L.acc = take(24 * max_own);                     // 6 floats (diagonal block) or 3
-  L.minv = take(24 * max_own);
-  L.hc = take(12 * max_own);
-  L.lm = take(16 * max_loc);
-  L.ptn = take(8 * res_pt);
-  L.lptr = take(res_pt ? 4 * (max_own + 1) : 0);
-  L.lcsr = take(4 * res_lcsr);
-  L.mask = take(max_own);
-  L.cursor = take(4 * 6 * max_own);               // one cursor per (node, component)
-  L.total = o;
-  return L;
-}
+struct SmemLayout {
+  int lm, red, chunk;                             // always shared
+  int acc, x, r, ucg, w, s, p, minv, hc, mask, cursor, ut;
+  int tan, ptn, lptr, lcsr;                       // resident part data, or -1: read from global memory
+  int chunk_tets;                                 // part tets per chunk of the evaluation passes
+  int total;                                      // dynamic shared bytes
+  int gbytes;                                     // global scratch bytes per CTA
+};
 
-__host__ __device__ inline SmemLayout smem_layout(const MeshDev& M) {
-  return smem_layout(M.max_own, M.max_loc, M.chunk, M.resident ? M.max_pt : 0, M.resident ? M.max_lcsr : 0);
-}
+// Part sizes a layout must hold (maxima over the parts, and over the meshes of
+// a batched launch).
+struct PartDims {
+  int max_own, max_loc, max_pt, max_lcsr;
+};
 
 // ---------------------------------------------------------------- batched solves
-// One CTA runs one whole solve; CTAs take jobs from a queue. The mesh uses its
-// batch partition (parts of ~1000 tets, processed one after another), every
-// per-solve array lives in global memory.
+// Two engines run many independent solves in one launch; each takes jobs from
+// a queue until it is empty. Mesh data and outputs are per job; the per-solve
+// scratch belongs to the CTA group ("slot") that runs the job.
+//  * group engine: a cooperative launch of G groups of P CTAs; a group runs
+//    one solve with the single-solve kernel's global-memory synchronisation.
+//  * cluster engine: one thread-block cluster per solve; halo values and
+//    partial sums through distributed shared memory, hardware barriers.
 struct BatchJob {
-  const MeshDev* mesh;              // device copy of the mesh's batch partition
-  double *u, *uprev, *R, *fc;       // [3 Nn] FP64
-  float *x, *r, *z, *p, *q, *hc;    // [3 Nn] FP32
-  float* minv;                      // [6 Nn]
-  float4* tangent;                  // [kTanVec][total_pt]
+  MeshDev mesh;                     // partition into exactly as many parts as a slot has CTAs
+  SolveParams prm;
+  double* u;                        // [3 Nn] zero on entry; displacement on exit
+  double* out_fc;                   // [3 Nn] nodal contact force on exit
   double* step_force;               // [3 K]
-  StatsDev* stats;
-  int shape, n_steps;
-  double origin[3], rot[9], iparams[3], dir[3];
-  const double* depths;             // [K] device
+  StatsDev* stats;                  // status ST_TIMEOUT on entry: overwritten when the solve ends
 };
 
-struct BatchParams {
-  int n_jobs, tangent_mode, max_newton, max_cg, max_backtracks;
-  double tol, c_kappa, cg_rtol_max, cg_rtol_min;
+struct SlotScratch {
+  unsigned char* base;              // slot s at base + s * stride
+  long long stride;
+  long long ctrl;                   // group engine: barrier counter, abort word, job word (u64 each)
+  long long vpub, cgslot, partials; // group engine: as in WorkDev
+  long long dpub, tangent, R, uprev, cta;   // offsets inside a slot
+  long long cta_stride;             // per-CTA bytes of the cta region
 };
 
-struct BatchSmem {
-  int ut, lm, chunk, acc, red, total;
-};
-
-__host__ __device__ inline BatchSmem batch_smem_layout(int max_own, int max_loc, int max_pt) {
-  BatchSmem L;
-  int o = 0;
-  auto take = [&](int bytes) { int at = o; o = align_up(o + bytes, 16); return at; };
-  L.ut = take(24 * max_loc);
-  L.lm = take(16 * max_loc);
-  L.chunk = take(96 * max_pt);
-  L.acc = take(24 * max_own);
-  L.red = take(8 * kRed * (kBlock / 32 + 1));
-  L.total = o;
-  return L;
-}
-
-cudaError_t launch_batch(const BatchJob* d_jobs, int* d_queue, const BatchParams& prm, int smem_bytes,
-                         int n_ctas, cudaStream_t stream, float* kernel_ms);
-cudaError_t batch_kernel_occupancy(int smem_bytes, int* blocks_per_sm);
+cudaError_t cluster_kernel_attrs(int cluster, int smem_bytes, int* static_smem, int* max_clusters);
+cudaError_t launch_cluster(const BatchJob* d_jobs, int n_jobs, int* d_queue, const SlotScratch& S,
+                           const SmemLayout& L, int cluster, int n_slots, cudaStream_t stream, float* kernel_ms);
+cudaError_t group_kernel_attrs(int smem_bytes, int* static_smem, int* blocks_per_sm);
+cudaError_t launch_groups(const BatchJob* d_jobs, int n_jobs, int* d_queue, const SlotScratch& S,
+                          const SmemLayout& L, int parts, int n_groups, unsigned long long timeout_ns,
+                          cudaStream_t stream, float* kernel_ms);
 
 // Host-side launcher (fem_solve.cu).
-cudaError_t launch_solve(const MeshDev& mesh, const WorkDev& work, const SolveParams& prm,
+cudaError_t launch_solve(const MeshDev& mesh, const WorkDev& work, const SolveParams& prm, const SmemLayout& L,
                          cudaStream_t stream, float* kernel_ms);
-cudaError_t solve_kernel_occupancy(int smem_bytes, int* blocks_per_sm);
+cudaError_t solve_kernel_attrs(int smem_bytes, int* static_smem, int* blocks_per_sm);
 
 // Fixed scratch block for fem_eval_residual_noalloc (fem_solve.cu).
 constexpr size_t kNoAllocScratchBytes = 8u << 20;

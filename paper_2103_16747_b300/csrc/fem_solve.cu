@@ -1,23 +1,37 @@
-// Persistent cooperative solve kernel: the whole quasi-static indentation
-// solve (load steps, Newton, line search, PCG) runs in one launch.
+// Persistent solve kernels: the whole quasi-static indentation solve (load
+// steps, Newton, line search, PCG) runs inside one launch.
 //
-// Work decomposition. The mesh is cut into P parts, one per CTA. Part c owns a
-// contiguous range of (Morton-ordered) nodes and holds every tet that touches
-// one of them; tets on part boundaries are evaluated by each part that needs
-// them, so a CTA finishes the node sums of its own nodes in shared memory with
-// no atomics and a fixed summation order (deterministic). Vectors of the owned
-// nodes live in shared memory for the whole solve, and so do (when they fit)
-// the part's stored tangent, tet node ids and local node->tet lists. Only the
-// values other parts need (the PCG vector being multiplied, the Newton
-// direction, the displacement) and one reduction slot per CTA go through
-// global memory.
+// Work decomposition. The mesh is cut into P parts. Part c owns a contiguous
+// range of (Morton-ordered) nodes and holds every tet that touches one of
+// them; tets on part boundaries are evaluated by each part that needs them,
+// so a CTA finishes the node sums of its own nodes on chip with no atomics and
+// a fixed summation order (deterministic). The PCG vectors of the owned nodes
+// live in shared memory when they fit (the host plans the placement, see
+// SmemLayout), and so do, when there is room, the part's stored tangent, tet
+// node ids and local node->tet lists. Newton-level state (u, R, contact
+// forces) lives in global memory, each entry written by its owning part.
 //
-// Synchronisation. The PCG (Chronopoulos-Gear form) needs per iteration one
-// halo exchange of fenceless (epoch, value) words and one grid reduction
-// announced on a release-ordered counter. Every wait is bounded
-// (globaltimer); on expiry the CTA sets the abort word and returns, and the
-// others leave at their next barrier. The launch is cooperative so that all
-// CTAs are co-resident or the launch fails cleanly.
+// Three launch forms share one solve body (template flag CL):
+//  * solve_kernel: one solve over the whole GPU, one part per CTA of a
+//    cooperative launch. PCG halo values and dot-product partials travel as
+//    fenceless (epoch, value) 64-bit words in global memory; Newton-level
+//    syncs are a software grid barrier. Every wait is bounded (globaltimer);
+//    on expiry the CTA raises the abort word and returns, and the others
+//    leave at their next wait.
+//  * group_kernel: G groups of P CTAs in one cooperative launch, each group
+//    running one solve at a time with the same synchronisation as
+//    solve_kernel on its own counters; groups take jobs from a queue
+//    (batched and uneven solves).
+//  * cluster_kernel: one solve per thread-block cluster, one part per CTA of
+//    the cluster; clusters take jobs from a queue. Halo values are read straight from the owner CTA's shared
+//    memory and dot-product partials from each CTA's shared slot
+//    (distributed shared memory), between hardware cluster barriers. Every CTA
+//    of a cluster takes the same branches (all decisions come from
+//    cluster-wide sums that each CTA forms in the same order), so every CTA
+//    reaches every barrier.
+//
+// The PCG is the Chronopoulos-Gear form: per iteration one halo exchange, one
+// tangent product and one reduction of (r,u), (w,u), (r,r) together.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -44,6 +58,33 @@ __device__ __forceinline__ int ld_volatile_i32(const int* p) {
   return *reinterpret_cast<const volatile int*>(p);
 }
 
+// ------------------------------------------------------------ cluster helpers
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ unsigned cluster_ncta() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+
+// All threads of all CTAs of the cluster; release/acquire at cluster scope.
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive;\n\tbarrier.cluster.wait;" ::: "memory");
+}
+
+// Generic address of the same shared-memory object in CTA `rank` of the cluster.
+template <typename T>
+__device__ __forceinline__ T* peer(T* p, unsigned rank) {
+  unsigned long long a = reinterpret_cast<unsigned long long>(p), out;
+  asm volatile("mapa.u64 %0, %1, %2;" : "=l"(out) : "l"(a), "r"(rank));
+  return reinterpret_cast<T*>(out);
+}
+
+// --------------------------------------------------------------- grid barrier
 struct Barrier {
   unsigned long long* counter;
   int* abort_flag;
@@ -79,24 +120,33 @@ __device__ bool grid_sync(Barrier& b, int* s_flag) {
   return *s_flag == 0;
 }
 
+// Static shared state of one CTA.
+struct Statics {
+  double red_out[kRed];   // broadcast area of the Newton-level reductions
+  double eslot[2 * kRed]; // cluster form: this CTA's Newton-level partials (double-buffered)
+  float2 red_df[kRed];    // FP32-pair sums of the PCG
+  float2 cgs[8];          // cluster form: this CTA's PCG partials (double-buffered, 3 used of 4)
+  int flag;
+};
+
 struct Ctx {
-  int part, n_own, n_loc, node0, halo0, t0, n_pt;
-  double *u, *uprev, *R, *X, *fc, *kp, *ut, *chunkd, *red;
-  float *x, *r, *ucg, *w, *z, *q, *s, *p, *acc, *minv, *hc, *chunkf;
+  int part, nparts, n_own, n_loc, node0, halo0, t0, n_pt;
+  int CH;                 // part tets per chunk of the evaluation passes
+  double *u, *uprev, *R, *fc;   // owned entries of global node arrays (index 3*i+k)
+  const double *X, *kb;
+  double *ut, *chunkd, *red;
+  float *x, *r, *ucg, *w, *s, *p, *acc, *minv, *hc, *chunkf;
   float4* lm;
   float4* tan;            // part tangent, element (g, t) at tan[g * tan_stride + t]
   int tan_stride;
   const ushort4* ptn;     // part tet local node ids, index t
   const int* lptr;        // owned node i: entries lcsr[lptr[i] .. lptr[i+1])
   const unsigned* lcsr;   // (local tet << 2) | corner, sorted by local tet
+  const unsigned* hsrc;   // halo entry j: (owner part << 16) | owner-local index
   unsigned char* mask;
   int* cursor;
-  double* red_out;        // broadcast area for grid reductions (kRed doubles)
-  float2* red_df;         // FP32-pair grid sums of the PCG (kRed)
-  float* coef;            // PCG alpha, beta broadcast by thread 0
-  int* decision;          // per-warp wait results of the slot reduction
-  int* flag;
-  bool timer;             // CTA 0, thread 0 accumulates phase cycles
+  Statics* st;
+  bool timer;             // thread 0 of each CTA accumulates phase cycles
   long long cyc[PH_N];
 };
 
@@ -113,9 +163,21 @@ __device__ __forceinline__ int local_to_global(const Ctx& C, const MeshDev& M, i
   return l < C.n_own ? C.node0 + l : M.halo_nodes[C.halo0 + l - C.n_own];
 }
 
-// Deterministic CTA reduction of nv per-thread FP32 values (each thread's
-// share) into a W.partials slot: two-sum tree in a fixed order, one FP64
-// conversion per value at the end.
+// Newton-level synchronisation of all parts; global-memory writes before it
+// are visible to every part after it.
+template <bool CL>
+__device__ __forceinline__ bool sync_parts(Ctx& C, Barrier& gb) {
+  if constexpr (CL) {
+    __threadfence();
+    cluster_sync();
+    return true;
+  } else {
+    return grid_sync(gb, &C.st->flag);
+  }
+}
+
+// Deterministic CTA reduction of NV per-thread FP32 values into C.st->red_df:
+// two-sum tree in a fixed order.
 template <int NV>
 __device__ void block_reduce_df(Ctx& C, const float* v, int active_warps) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -144,13 +206,14 @@ __device__ void block_reduce_df(Ctx& C, const float* v, int active_warps) {
       const float2 b = red[w * kRed + threadIdx.x];
       a = df_add(a, DF{b.x, b.y});
     }
-    C.red_df[threadIdx.x] = make_float2(a.hi, a.lo);
+    C.st->red_df[threadIdx.x] = make_float2(a.hi, a.lo);
   }
   __syncthreads();
 }
 
-// Deterministic CTA reduction of nv per-thread doubles into a W.partials slot
+// Deterministic CTA reduction of nv per-thread doubles into this part's slot
 // (warps whose values are all zero skip the FP64 shuffles).
+template <bool CL>
 __device__ void block_reduce_to_slot(Ctx& C, const WorkDev& W, int slot_buf, const double* v, int nv) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int k = 0; k < nv; ++k) {
@@ -165,41 +228,43 @@ __device__ void block_reduce_to_slot(Ctx& C, const WorkDev& W, int slot_buf, con
   if (threadIdx.x < nv) {
     double a = 0.0;
     for (int w = 0; w < kBlock / 32; ++w) a += C.red[w * kRed + threadIdx.x];
-    W.partials[((size_t)slot_buf * gridDim.x + blockIdx.x) * kRed + threadIdx.x] = a;
+    if constexpr (CL) C.st->eslot[slot_buf * kRed + threadIdx.x] = a;
+    else W.partials[((size_t)slot_buf * C.nparts + C.part) * kRed + threadIdx.x] = a;
   }
 }
 
-// Every CTA sums all slots in the same order: identical results everywhere.
-__device__ void grid_reduce_from_slot(Ctx& C, const WorkDev& W, int slot_buf, int nv) {
+// Every part sums all slots in the same order: identical results everywhere.
+template <bool CL>
+__device__ void reduce_from_slots(Ctx& C, const WorkDev& W, int slot_buf, int nv) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (warp < nv) {
     double a = 0.0;
-    for (int c = lane; c < (int)gridDim.x; c += 32)
-      a += W.partials[((size_t)slot_buf * gridDim.x + c) * kRed + warp];
+    for (int c = lane; c < C.nparts; c += 32) {
+      if constexpr (CL) a += peer(C.st->eslot, (unsigned)c)[slot_buf * kRed + warp];
+      else a += __ldcg(W.partials + ((size_t)slot_buf * C.nparts + c) * kRed + warp);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    if (lane == 0) C.red_out[warp] = a;
+    if (lane == 0) C.st->red_out[warp] = a;
   }
 }
 
-struct Bufs {
-  int slot;   // next partial-slot buffer
-  int vec;    // next published-vector buffer
-};
-
-// Local displacements ut = u + alpha * dx for owned (shared) and halo (global).
+// Local displacements ut = u + alpha * dx: owned entries from this part,
+// halo entries from the global copies their owners wrote before the last sync.
 __device__ void load_local_positions(Ctx& C, const MeshDev& M, const WorkDev& W, double alpha) {
   for (int l = threadIdx.x; l < C.n_loc; l += blockDim.x) {
     double a0, a1, a2;
-    float d0, d1, d2;
+    float d0 = 0.f, d1 = 0.f, d2 = 0.f;
     if (l < C.n_own) {
       a0 = C.u[3 * l]; a1 = C.u[3 * l + 1]; a2 = C.u[3 * l + 2];
       d0 = C.x[3 * l]; d1 = C.x[3 * l + 1]; d2 = C.x[3 * l + 2];
     } else {
       const int g = M.halo_nodes[C.halo0 + l - C.n_own];
-      a0 = W.u[3 * g]; a1 = W.u[3 * g + 1]; a2 = W.u[3 * g + 2];
-      const float4 d = W.dpub[g];
-      d0 = d.x; d1 = d.y; d2 = d.z;
+      a0 = __ldcg(W.u + 3 * g); a1 = __ldcg(W.u + 3 * g + 1); a2 = __ldcg(W.u + 3 * g + 2);
+      if (alpha != 0.0) {   // the direction array exists only where a step is taken
+        const float4 d = __ldcg(W.dpub + g);
+        d0 = d.x; d1 = d.y; d2 = d.z;
+      }
     }
     if (alpha != 0.0) {
       a0 = fma(alpha, (double)d0, a0);
@@ -257,9 +322,14 @@ __device__ __forceinline__ void reset_cursors(Ctx& C, int nv) {
 // Indices of the reduced values of an evaluation pass.
 enum { EV_ELASTIC = 0, EV_BAD, EV_CONTACT, EV_RR, EV_FCFC, EV_FX, EV_FY, EV_FZ, EV_ACTIVE, EV_SLOPE, EV_N };
 
+struct Bufs {
+  int slot;   // next partial-slot buffer
+};
+
 // FP64 energy, residual R = dPi/du and contact at ut = u + alpha*dx. Leaves
 // the owned residual in C.R (unmasked), contact forces in C.fc, the contact
-// Gauss-Newton vectors in C.hc, and the grid sums in C.red_out.
+// Gauss-Newton vectors in C.hc, and the sums over all parts in red_out.
+template <bool CL>
 __device__ bool eval_pass(Ctx& C, const MeshDev& M, const WorkDev& W, const SolveParams& P,
                           Barrier& gb, Bufs& bf, double alpha, const double org[3], bool want_slope) {
   load_local_positions(C, M, W, alpha);
@@ -270,7 +340,7 @@ __device__ bool eval_pass(Ctx& C, const MeshDev& M, const WorkDev& W, const Solv
             C.R[3 * i + 2] * (double)C.x[3 * i + 2];
     C.R[3 * i] = 0.0; C.R[3 * i + 1] = 0.0; C.R[3 * i + 2] = 0.0;
   }
-  const int CH = M.chunk;
+  const int CH = C.CH;
   const bool single = CH >= C.n_pt;
   if (!single) reset_cursors(C, 3);
   __syncthreads();
@@ -312,7 +382,7 @@ __device__ bool eval_pass(Ctx& C, const MeshDev& M, const WorkDev& W, const Solv
   v[EV_BAD] = bad;
   v[EV_SLOPE] = sl;
   for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
-    const double kp = C.kp[i];
+    const double kp = C.kb[i] * P.c_kappa;
     double fcv[3] = {0.0, 0.0, 0.0};
     float h[3] = {0.f, 0.f, 0.f};
     if (kp > 0.0) {
@@ -343,9 +413,9 @@ __device__ bool eval_pass(Ctx& C, const MeshDev& M, const WorkDev& W, const Solv
     }
     v[EV_FX] += fcv[0]; v[EV_FY] += fcv[1]; v[EV_FZ] += fcv[2];
   }
-  block_reduce_to_slot(C, W, bf.slot, v, EV_N);
-  if (!grid_sync(gb, C.flag)) return false;
-  grid_reduce_from_slot(C, W, bf.slot, EV_N);
+  block_reduce_to_slot<CL>(C, W, bf.slot, v, EV_N);
+  if (!sync_parts<CL>(C, gb)) return false;
+  reduce_from_slots<CL>(C, W, bf.slot, EV_N);
   bf.slot ^= 1;
   __syncthreads();
   return true;
@@ -357,7 +427,7 @@ __device__ void tangent_pass(Ctx& C, const MeshDev& M, int mode) {
   for (int i = threadIdx.x; i < C.n_own; i += blockDim.x)
 #pragma unroll
     for (int k = 0; k < 6; ++k) C.acc[6 * i + k] = 0.f;
-  const int CH = M.chunk;
+  const int CH = C.CH;
   const bool single = CH >= C.n_pt;
   if (!single) reset_cursors(C, 6);
   __syncthreads();
@@ -412,11 +482,13 @@ __device__ void tangent_pass(Ctx& C, const MeshDev& M, int mode) {
 }
 
 // acc (3 per owned node) = element tangent applied to the local vector lm.
+// The product stores 12 floats per tet, half the evaluation passes' 96 bytes,
+// so its chunks hold twice as many tets.
 __device__ void matvec_pass(Ctx& C, const MeshDev& M, long long* tp = nullptr) {
   for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
     C.acc[3 * i] = 0.f; C.acc[3 * i + 1] = 0.f; C.acc[3 * i + 2] = 0.f;
   }
-  const int CH = M.chunk;
+  const int CH = C.CH >= C.n_pt ? C.CH : 2 * C.CH;
   const bool single = CH >= C.n_pt;
   if (!single) reset_cursors(C, 3);
   __syncthreads();
@@ -468,15 +540,15 @@ __device__ __forceinline__ void finish_product(const Ctx& C, int i, const float 
   out[2] = (mk & 4u) ? 0.f : C.acc[3 * i + 2] + h2 * hv;
 }
 
-// ------------------------------------------------------------- PCG sync
-// The PCG needs no grid barrier and no fence. Every value another part reads
-// (the halo entries of the vector being multiplied, the per-part dot-product
-// partials) is published as a 64-bit word holding the FP32 value and the
-// publication epoch, written and read with relaxed GPU-scope 64-bit accesses
-// (single-copy atomic). A reader spins until the epoch of each word it needs
-// matches. Double buffering is safe because no part can publish epoch e+2
-// before every part has consumed epoch e: it first needs every part's e+1
-// partials, which a part writes only after reading all of epoch e.
+// ------------------------------------------------- PCG sync, cooperative form
+// Every value another part reads (the halo entries of the vector being
+// multiplied, the per-part dot-product partials) is published as a 64-bit
+// word holding the FP32 value and the publication epoch, written and read with
+// relaxed GPU-scope 64-bit accesses (single-copy atomic). A reader spins until
+// the epoch of each word it needs matches. Double buffering is safe because no
+// part can publish epoch e+2 before every part has consumed epoch e: it first
+// needs every part's e+1 partials, which a part writes only after reading all
+// of epoch e.
 
 __device__ __forceinline__ void st_tagged(unsigned long long* p, float v, int ep) {
   const unsigned long long w = ((unsigned long long)(unsigned)ep << 32) | (unsigned long long)__float_as_uint(v);
@@ -534,15 +606,16 @@ __device__ bool load_halo_tagged(Ctx& C, const MeshDev& M, const WorkDev& W, int
   return __syncthreads_or(failed) == 0;
 }
 
-// Thread 0 stores the CTA's FP32-pair dot products (C.red_df[0..2]) and
+// Thread 0 stores the CTA's FP32-pair dot products (red_df[0..2]) and
 // arrives on the PCG counter with release semantics (the stores are visible
 // to whoever observes the arrival).
 __device__ void write_cg_slot(Ctx& C, const WorkDev& W, int ep) {
   if (threadIdx.x == 0) {
-    float4* dst = reinterpret_cast<float4*>(W.cgslot + ((size_t)(ep & 1) * gridDim.x + blockIdx.x) * 6);
-    dst[0] = make_float4(C.red_df[0].x, C.red_df[0].y, C.red_df[1].x, C.red_df[1].y);
-    dst[1] = make_float4(C.red_df[2].x, C.red_df[2].y, 0.f, 0.f);
-    unsigned long long* cnt = W.cgslot + (size_t)2 * gridDim.x * 6;
+    const float2* rd = C.st->red_df;
+    float4* dst = reinterpret_cast<float4*>(W.cgslot + ((size_t)(ep & 1) * C.nparts + C.part) * 6);
+    dst[0] = make_float4(rd[0].x, rd[0].y, rd[1].x, rd[1].y);
+    dst[1] = make_float4(rd[2].x, rd[2].y, 0.f, 0.f);
+    unsigned long long* cnt = W.cgslot + (size_t)2 * C.nparts * 6;
     asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(cnt) : "memory");
   }
 }
@@ -555,11 +628,11 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
 
 // Thread 0 waits (bounded, acquire) until all parts arrived n_pub times; then
 // warp 0 sums the three values over the parts in a fixed order (identical in
-// every CTA) into C.red_df.
+// every CTA) into red_df.
 __device__ bool reduce_cg_slots(Ctx& C, const WorkDev& W, int ep, unsigned long long n_pub,
                                 unsigned long long limit) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int P = gridDim.x;
+  const int P = C.nparts;
   if (threadIdx.x == 0) {
     const unsigned long long* cnt = W.cgslot + (size_t)2 * P * 6;
     const unsigned long long target = n_pub * (unsigned long long)P;
@@ -569,10 +642,10 @@ __device__ bool reduce_cg_slots(Ctx& C, const WorkDev& W, int ep, unsigned long 
     while (ld_acquire_u64(cnt) < target) {
       if (spin_timeout(W, t0, it, limit)) { failed = 1; break; }
     }
-    *C.flag = failed;
+    C.st->flag = failed;
   }
   __syncthreads();
-  if (*C.flag) return false;
+  if (C.st->flag) return false;
   if (warp == 0) {
     const float4* base = reinterpret_cast<const float4*>(W.cgslot + (size_t)(ep & 1) * P * 6);
     constexpr int kMaxPer = 8;   // up to 256 CTAs, all loads in flight together
@@ -600,19 +673,68 @@ __device__ bool reduce_cg_slots(Ctx& C, const WorkDev& W, int ep, unsigned long 
     }
     if (lane == 0) {
 #pragma unroll
-      for (int k = 0; k < 3; ++k) C.red_df[k] = make_float2(a[k].hi, a[k].lo);
+      for (int k = 0; k < 3; ++k) C.st->red_df[k] = make_float2(a[k].hi, a[k].lo);
     }
   }
   __syncthreads();
   return true;
 }
 
+// ------------------------------------------------------ PCG sync, cluster form
+// Halo entries of the vector being multiplied, read from the owners' shared
+// memory after the barrier that follows every part's update. An owner writes
+// its entries again only after the next reduction barrier, which every reader
+// reaches after its reads.
+__device__ void load_halo_cluster(Ctx& C) {
+  cluster_sync();
+  for (int l = C.n_own + threadIdx.x; l < C.n_loc; l += blockDim.x) {
+    const unsigned src = C.hsrc[l - C.n_own];
+    C.lm[l] = peer(C.lm, src >> 16)[src & 0xffffu];
+  }
+  __syncthreads();
+}
+
+// Cluster sums of the three FP32-pair dot products: each CTA leaves its sums
+// in its own slot (buffer ep & 1) and, after the barrier, warp 0 of every CTA
+// sums all slots in rank order with the same shuffle tree (identical results).
+__device__ void reduce_cluster(Ctx& C, int ep) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int b = (ep & 1) * 4;
+  if (threadIdx.x < 3) C.st->cgs[b + threadIdx.x] = C.st->red_df[threadIdx.x];
+  cluster_sync();
+  if (warp == 0) {
+    DF a[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    if (lane < C.nparts) {
+      const float2* src = peer(C.st->cgs, (unsigned)lane);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float2 v = src[b + k];
+        a[k] = DF{v.x, v.y};
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const DF q{__shfl_xor_sync(0xffffffffu, a[k].hi, o), __shfl_xor_sync(0xffffffffu, a[k].lo, o)};
+        a[k] = (lane & o) ? df_add(q, a[k]) : df_add(a[k], q);
+      }
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) C.st->red_df[k] = make_float2(a[k].hi, a[k].lo);
+    }
+  }
+  __syncthreads();
+}
+
 // Preconditioned CG on K dx = -R_free in the Chronopoulos-Gear form: one
-// halo exchange, one tangent product and one grid reduction (of (r,u), (w,u)
+// halo exchange, one tangent product and one reduction (of (r,u), (w,u)
 // and (r,r) together) per iteration; s = A p is carried by recurrence.
 // Leaves dx in C.x (owned). Returns false if a wait was abandoned; iters
 // receives the iteration count, neg_curv whether it stopped on a
 // non-positive curvature.
+template <bool CL>
 __device__ bool pcg(Ctx& C, const MeshDev& M, const WorkDev& W, const SolveParams& P, int& ep,
                     unsigned long long& n_pub, double eta, double abs_tol, int& iters, bool& neg_curv) {
   long long t = tick(C);
@@ -635,14 +757,18 @@ __device__ bool pcg(Ctx& C, const MeshDev& M, const WorkDev& W, const SolveParam
 #pragma unroll
     for (int k = 0; k < 3; ++k) C.ucg[3 * i + k] = uu[k];
     C.lm[i] = make_float4(uu[0], uu[1], uu[2], 0.f);
-    publish_node(C, M, W, i, uu, ep);
+    if constexpr (!CL) publish_node(C, M, W, i, uu, ep);
   }
   tock(C, PH_CG_INIT, t);
   float gamma_prev = 1.f, alpha_prev = 1.f, rr0 = 0.f;
   const float eta2 = (float)(eta * eta), abs2 = (float)(abs_tol * abs_tol);
   int it = 0;
   for (;; ++it) {
-    if (!load_halo_tagged(C, M, W, ep, P.timeout_ns)) return false;
+    if constexpr (CL) {
+      load_halo_cluster(C);
+    } else {
+      if (!load_halo_tagged(C, M, W, ep, P.timeout_ns)) return false;
+    }
     tock(C, PH_CG_BARRIER, t);
     matvec_pass(C, M, &t);   // w = A u (u in C.lm)
     float v[3] = {0.f, 0.f, 0.f};
@@ -661,22 +787,27 @@ __device__ bool pcg(Ctx& C, const MeshDev& M, const WorkDev& W, const SolveParam
       }
     }
     block_reduce_df<3>(C, v, active_warps);
-    write_cg_slot(C, W, ep);
-    ++n_pub;
-    if (!reduce_cg_slots(C, W, ep, n_pub, P.timeout_ns)) return false;
+    if constexpr (CL) {
+      reduce_cluster(C, ep);
+    } else {
+      write_cg_slot(C, W, ep);
+      ++n_pub;
+      if (!reduce_cg_slots(C, W, ep, n_pub, P.timeout_ns)) return false;
+    }
     tock(C, PH_CG_REDUCE, t);
     // scalars: every thread evaluates the same FP32 recurrences from the same
-    // FP32-pair grid sums (identical in every CTA); delta - beta*gamma/alpha_prev,
+    // FP32-pair sums (identical in every CTA); delta - beta*gamma/alpha_prev,
     // the one cancelling difference, keeps the pair's low word.
-    const float gamma = C.red_df[0].x, rr = C.red_df[2].x;
+    const float2* rd = C.st->red_df;
+    const float gamma = rd[0].x, rr = rd[2].x;
     if (it == 0) rr0 = rr;
     float beta = 0.f, denom;
     if (it > 0) {
       beta = __fdividef(gamma, gamma_prev);
-      const DF d = df_add(DF{C.red_df[1].x, C.red_df[1].y}, DF{-__fdividef(beta * gamma, alpha_prev), 0.f});
+      const DF d = df_add(DF{rd[1].x, rd[1].y}, DF{-__fdividef(beta * gamma, alpha_prev), 0.f});
       denom = d.hi;
     } else {
-      denom = C.red_df[1].x;
+      denom = rd[1].x;
     }
     const float alpha = __fdividef(gamma, denom);
     const bool converged = rr <= eta2 * rr0 || rr <= abs2;
@@ -720,7 +851,7 @@ __device__ bool pcg(Ctx& C, const MeshDev& M, const WorkDev& W, const SolveParam
 #pragma unroll
       for (int k = 0; k < 3; ++k) C.ucg[3 * i + k] = un[k];
       C.lm[i] = make_float4(un[0], un[1], un[2], 0.f);
-      publish_node(C, M, W, i, un, ep);
+      if constexpr (!CL) publish_node(C, M, W, i, un, ep);
     }
     tock(C, PH_CG_UPDATE, t);
   }
@@ -728,175 +859,115 @@ __device__ bool pcg(Ctx& C, const MeshDev& M, const WorkDev& W, const SolveParam
   return true;
 }
 
-__device__ void publish_u(Ctx& C, const WorkDev& W) {
-  for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
-    const int g = C.node0 + i;
-    W.u[3 * g] = C.u[3 * i]; W.u[3 * g + 1] = C.u[3 * i + 1]; W.u[3 * g + 2] = C.u[3 * i + 2];
-  }
-}
-
 __device__ void publish_dx(Ctx& C, const WorkDev& W) {
   for (int i = threadIdx.x; i < C.n_own; i += blockDim.x)
     W.dpub[C.node0 + i] = make_float4(C.x[3 * i], C.x[3 * i + 1], C.x[3 * i + 2], 0.f);
 }
 
-// u <- ut for the owned nodes (the evaluated, accepted state) and publish it.
-__device__ void accept_state(Ctx& C, const WorkDev& W) {
+// u <- ut for the owned nodes (the evaluated, accepted state). Other parts
+// read these entries only after the next sync of all parts.
+__device__ void accept_state(Ctx& C) {
   for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) C.u[3 * i + k] = C.ut[3 * i + k];
   }
   __syncthreads();
-  publish_u(C, W);
 }
 
-__global__ void __launch_bounds__(kBlock, 1) solve_kernel(MeshDev M, WorkDev W, SolveParams P) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double s_red_out[kRed];
-  __shared__ float s_coef[2];
-  __shared__ float2 s_red_df[kRed];
-  __shared__ int s_decision[4];
-  __shared__ int s_flag;
-  if (P.mode == MODE_BARRIER_TEST) {
-    Barrier tb{W.barrier, W.abort_flag, 0ull, P.timeout_ns, gridDim.x};
-    if (blockIdx.x == 0) return;   // never arrives: the others must time out
-    grid_sync(tb, &s_flag);
-    return;
-  }
-  const SmemLayout L = smem_layout(M);
-  Ctx C;
-  C.part = blockIdx.x;
-  C.node0 = M.part_node_begin[C.part];
-  C.n_own = M.part_node_begin[C.part + 1] - C.node0;
-  C.halo0 = M.part_halo_begin[C.part];
-  C.n_loc = C.n_own + (M.part_halo_begin[C.part + 1] - C.halo0);
-  C.t0 = M.part_tet_begin[C.part];
-  C.n_pt = M.part_tet_begin[C.part + 1] - C.t0;
-  C.u = reinterpret_cast<double*>(smem + L.u);
-  C.uprev = reinterpret_cast<double*>(smem + L.uprev);
-  C.R = reinterpret_cast<double*>(smem + L.R);
-  C.X = reinterpret_cast<double*>(smem + L.X);
-  C.fc = reinterpret_cast<double*>(smem + L.fc);
-  C.kp = reinterpret_cast<double*>(smem + L.kp);
-  C.ut = reinterpret_cast<double*>(smem + L.ut);
+// Points the context at this part's data. smem: dynamic shared memory;
+// gscr: this CTA's region of the global scratch (arrays placed there by L).
+__device__ void setup_ctx(Ctx& C, const MeshDev& M, const WorkDev& W, const SmemLayout& L, unsigned char* smem,
+                          unsigned char* gscr, Statics* st, int part, int nparts) {
+  auto at = [&](int off) -> unsigned char* { return (off & kInGlobal) ? gscr + (off & ~kInGlobal) : smem + off; };
+  C.part = part;
+  C.nparts = nparts;
+  C.node0 = M.part_node_begin[part];
+  C.n_own = M.part_node_begin[part + 1] - C.node0;
+  C.halo0 = M.part_halo_begin[part];
+  C.n_loc = C.n_own + (M.part_halo_begin[part + 1] - C.halo0);
+  C.t0 = M.part_tet_begin[part];
+  C.n_pt = M.part_tet_begin[part + 1] - C.t0;
+  C.CH = L.chunk_tets;
+  C.u = W.u + 3 * (size_t)C.node0;
+  C.uprev = W.uprev ? W.uprev + 3 * (size_t)C.node0 : nullptr;
+  C.R = W.R + 3 * (size_t)C.node0;
+  C.fc = W.out_fc + 3 * (size_t)C.node0;
+  C.X = M.X + 3 * (size_t)C.node0;
+  C.kb = M.kbase + C.node0;
+  C.ut = reinterpret_cast<double*>(at(L.ut));
   C.chunkd = reinterpret_cast<double*>(smem + L.chunk);
   C.chunkf = reinterpret_cast<float*>(smem + L.chunk);
   C.red = reinterpret_cast<double*>(smem + L.red);
-  C.x = reinterpret_cast<float*>(smem + L.x);
-  C.r = reinterpret_cast<float*>(smem + L.r);
-  C.ucg = reinterpret_cast<float*>(smem + L.ucg);
-  C.w = reinterpret_cast<float*>(smem + L.w);
-  C.z = reinterpret_cast<float*>(smem + L.z);
-  C.q = reinterpret_cast<float*>(smem + L.q);
-  C.s = reinterpret_cast<float*>(smem + L.s);
-  C.p = reinterpret_cast<float*>(smem + L.p);
-  C.acc = reinterpret_cast<float*>(smem + L.acc);
-  C.minv = reinterpret_cast<float*>(smem + L.minv);
-  C.hc = reinterpret_cast<float*>(smem + L.hc);
   C.lm = reinterpret_cast<float4*>(smem + L.lm);
-  C.mask = reinterpret_cast<unsigned char*>(smem + L.mask);
-  C.cursor = reinterpret_cast<int*>(smem + L.cursor);
-  C.red_out = s_red_out;
-  C.coef = s_coef;
-  C.red_df = s_red_df;
-  C.decision = s_decision;
-  C.flag = &s_flag;
+  C.x = reinterpret_cast<float*>(at(L.x));
+  C.r = reinterpret_cast<float*>(at(L.r));
+  C.ucg = reinterpret_cast<float*>(at(L.ucg));
+  C.w = reinterpret_cast<float*>(at(L.w));
+  C.s = reinterpret_cast<float*>(at(L.s));
+  C.p = reinterpret_cast<float*>(at(L.p));
+  C.acc = reinterpret_cast<float*>(at(L.acc));
+  C.minv = reinterpret_cast<float*>(at(L.minv));
+  C.hc = reinterpret_cast<float*>(at(L.hc));
+  C.mask = at(L.mask);
+  C.cursor = reinterpret_cast<int*>(at(L.cursor));
+  C.hsrc = M.halo_src + C.halo0;
+  C.st = st;
   C.timer = threadIdx.x == 0;
 #pragma unroll
   for (int k = 0; k < PH_N; ++k) C.cyc[k] = 0;
-  const long long t_start = tick(C);
-  if (M.resident) {
-    // part tet ids and local CSR copied into shared memory once
+  // resident part data: copied into shared memory once per solve
+  if (L.ptn >= 0) {
     ushort4* ptn = reinterpret_cast<ushort4*>(smem + L.ptn);
+    for (int t = threadIdx.x; t < C.n_pt; t += blockDim.x) ptn[t] = M.pt_nodes[C.t0 + t];
+    C.ptn = ptn;
+  } else {
+    C.ptn = M.pt_nodes + C.t0;
+  }
+  if (L.lcsr >= 0) {
     int* lptr = reinterpret_cast<int*>(smem + L.lptr);
     unsigned* lcsr = reinterpret_cast<unsigned*>(smem + L.lcsr);
     const int base = M.lcsr_ptr[C.node0];
     const int n_ent = M.lcsr_ptr[C.node0 + C.n_own] - base;
-    for (int t = threadIdx.x; t < C.n_pt; t += blockDim.x) ptn[t] = M.pt_nodes[C.t0 + t];
     for (int i = threadIdx.x; i <= C.n_own; i += blockDim.x) lptr[i] = M.lcsr_ptr[C.node0 + i] - base;
     for (int j = threadIdx.x; j < n_ent; j += blockDim.x) lcsr[j] = M.lcsr[base + j];
-    C.ptn = ptn;
     C.lptr = lptr;
     C.lcsr = lcsr;
-    C.tan = reinterpret_cast<float4*>(smem + L.tan);
-    C.tan_stride = M.max_pt;
   } else {
-    C.ptn = M.pt_nodes + C.t0;
     C.lptr = M.lcsr_ptr + C.node0;
     C.lcsr = M.lcsr;
+  }
+  if (L.tan >= 0) {
+    C.tan = reinterpret_cast<float4*>(smem + L.tan);
+    C.tan_stride = C.n_pt;
+  } else {
     C.tan = W.tangent + C.t0;
     C.tan_stride = M.total_pt;
   }
-
-  Barrier gb{W.barrier, W.abort_flag, 0ull, P.timeout_ns, gridDim.x};
-
   for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
-    const int g = C.node0 + i;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      C.X[3 * i + k] = M.X[3 * g + k];
-      C.u[3 * i + k] = W.u[3 * g + k];
-      C.uprev[3 * i + k] = C.u[3 * i + k];
       C.x[3 * i + k] = 0.f;
-      C.R[3 * i + k] = 0.0;
+      if (C.uprev) C.uprev[3 * i + k] = C.u[3 * i + k];
     }
-    C.mask[i] = M.fixmask[g];
-    C.kp[i] = M.kbase[g] * P.c_kappa;
+    C.mask[i] = M.fixmask[C.node0 + i];
   }
   __syncthreads();
-  Bufs bf{0, 0};
-  int ep = 0;                      // PCG publication epoch (same sequence in every CTA)
-  unsigned long long n_pub = 0;    // PCG dot-product publications so far
+}
+
+// The quasi-static solve over all load steps (MODE_SOLVE). Each part runs it
+// on its own nodes; every decision comes from sums over all parts.
+// ep (PCG publication epoch) and n_pub (PCG dot-product publications) run on
+// across the solves a group of CTAs performs one after another, so published
+// words and counters of an earlier solve never match a later one. Returns
+// false when a bounded wait was abandoned.
+template <bool CL>
+__device__ bool solve_body(Ctx& C, const MeshDev& M, const WorkDev& W, const SolveParams& P, Barrier& gb, int& ep,
+                           unsigned long long& n_pub) {
+  const long long t_start = tick(C);
+  Bufs bf{0};
   StatsDev* st = W.stats;
-  const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
-
-  if (P.mode == MODE_EVAL || P.mode == MODE_APPLY) {
-    double org[3];
-    const double d = P.step > 0 ? P.depths[P.step - 1] : 0.0;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) org[k] = P.origin[k] + d * P.dir[k];
-    if (!eval_pass(C, M, W, P, gb, bf, 0.0, org, false)) return;
-    if (P.mode == MODE_EVAL) {
-      for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
-        const int g = C.node0 + i;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          W.out_R[3 * g + k] = C.R[3 * i + k];
-          W.out_fc[3 * g + k] = C.fc[3 * i + k];
-        }
-      }
-      if (leader) {
-        st->elastic = C.red_out[EV_ELASTIC];
-        st->contact_energy = C.red_out[EV_CONTACT];
-        st->residual = sqrt(C.red_out[EV_RR]);
-        st->active = (int)C.red_out[EV_ACTIVE];
-        st->status = C.red_out[EV_BAD] > 0.0 ? ST_NONFINITE : ST_OK;
-      }
-      return;
-    }
-    tangent_pass(C, M, P.tangent_mode == 2 ? 0 : P.tangent_mode);
-    for (int l = threadIdx.x; l < C.n_loc; l += blockDim.x) {
-      const int g = local_to_global(C, M, l);
-      const unsigned mk = M.fixmask[g];
-      C.lm[l] = make_float4((mk & 1u) ? 0.f : (float)W.in_p[3 * g], (mk & 2u) ? 0.f : (float)W.in_p[3 * g + 1],
-                            (mk & 4u) ? 0.f : (float)W.in_p[3 * g + 2], 0.f);
-    }
-    __syncthreads();
-    matvec_pass(C, M);
-    for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
-      const float4 q = C.lm[i];
-      const float v[3] = {q.x, q.y, q.z};
-      float y[3];
-      finish_product(C, i, v, y);
-      const int g = C.node0 + i;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) W.out_y[3 * g + k] = y[k];
-    }
-    if (leader) st->status = ST_OK;
-    return;
-  }
-
-  // ---------------------------------------------------------------- solve
+  const bool leader = C.part == 0 && threadIdx.x == 0;
+  const double* red_out = C.st->red_out;
   int status = ST_OK;
   int newton_total = 0, cg_total = 0, bt_total = 0, exact_total = 0;
   double rn = 0.0, scale = 1.0, energy = 0.0;
@@ -932,30 +1003,29 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(MeshDev M, WorkDev W, 
       }
     }
     __syncthreads();
-    publish_u(C, W);
     publish_dx(C, W);
-    if (!grid_sync(gb, C.flag)) return;
+    if (!sync_parts<CL>(C, gb)) return false;
     long long t0 = tick(C);
     bool have_state = false;
     if (ratio > 0.0) {
-      if (!eval_pass(C, M, W, P, gb, bf, ratio, org, false)) return;
-      if (C.red_out[EV_BAD] == 0.0 && isfinite(C.red_out[EV_ELASTIC] + C.red_out[EV_CONTACT]) &&
-          isfinite(C.red_out[EV_RR])) {
-        accept_state(C, W);
+      if (!eval_pass<CL>(C, M, W, P, gb, bf, ratio, org, false)) return false;
+      if (red_out[EV_BAD] == 0.0 && isfinite(red_out[EV_ELASTIC] + red_out[EV_CONTACT]) &&
+          isfinite(red_out[EV_RR])) {
+        accept_state(C);
         have_state = true;
-        if (!grid_sync(gb, C.flag)) return;
+        if (!sync_parts<CL>(C, gb)) return false;
       }
     }
     if (!have_state) {
-      if (!eval_pass(C, M, W, P, gb, bf, 0.0, org, false)) return;
-      if (C.red_out[EV_BAD] > 0.0) { status = ST_NONFINITE; break; }
+      if (!eval_pass<CL>(C, M, W, P, gb, bf, 0.0, org, false)) return false;
+      if (red_out[EV_BAD] > 0.0) { status = ST_NONFINITE; break; }
     }
     tock(C, PH_EVAL, t0);
-    energy = C.red_out[EV_ELASTIC] + C.red_out[EV_CONTACT];
-    rn = sqrt(C.red_out[EV_RR]);
-    scale = fmax(sqrt(C.red_out[EV_FCFC]), M.scale_floor);
-    double fs[3] = {C.red_out[EV_FX], C.red_out[EV_FY], C.red_out[EV_FZ]};
-    int active = (int)C.red_out[EV_ACTIVE];
+    energy = red_out[EV_ELASTIC] + red_out[EV_CONTACT];
+    rn = sqrt(red_out[EV_RR]);
+    scale = fmax(sqrt(red_out[EV_FCFC]), M.scale_floor);
+    double fs[3] = {red_out[EV_FX], red_out[EV_FY], red_out[EV_FZ]};
+    int active = (int)red_out[EV_ACTIVE];
     double rn_prev = rn;
     const double rn_step0 = rn;
     int it = 0, cg_step = 0;
@@ -977,23 +1047,23 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(MeshDev M, WorkDev W, 
       }
       int cg_it = 0;
       bool neg_curv = false;
-      if (!pcg(C, M, W, P, ep, n_pub, eta, 0.1 * P.tol * scale, cg_it, neg_curv)) return;
+      if (!pcg<CL>(C, M, W, P, ep, n_pub, eta, 0.1 * P.tol * scale, cg_it, neg_curv)) return false;
       cg_step += cg_it;
       ++it;
       if (mode == 1) ++exact_total;
       publish_dx(C, W);
-      if (!grid_sync(gb, C.flag)) return;
+      if (!sync_parts<CL>(C, gb)) return false;
       t = tick(C);
       double alpha = 1.0, slope = 0.0;
       bool accepted = false;
       for (int bt = 0; bt <= P.max_backtracks; ++bt) {
-        if (!eval_pass(C, M, W, P, gb, bf, alpha, org, bt == 0)) return;
+        if (!eval_pass<CL>(C, M, W, P, gb, bf, alpha, org, bt == 0)) return false;
         if (bt == 0) {
-          slope = C.red_out[EV_SLOPE];
+          slope = red_out[EV_SLOPE];
           if (!(slope < 0.0) && mode == 1) break;   // exact direction is not a descent direction
         }
-        const double et = C.red_out[EV_ELASTIC] + C.red_out[EV_CONTACT];
-        const bool valid = C.red_out[EV_BAD] == 0.0 && isfinite(et) && isfinite(C.red_out[EV_RR]);
+        const double et = red_out[EV_ELASTIC] + red_out[EV_CONTACT];
+        const bool valid = red_out[EV_BAD] == 0.0 && isfinite(et) && isfinite(red_out[EV_RR]);
         if (valid && (rn <= 1e-3 * scale || et <= energy + 1e-4 * alpha * slope)) {
           accepted = true;
           energy = et;
@@ -1008,15 +1078,15 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(MeshDev M, WorkDev W, 
         // exact tangent failed: restore the state at u and continue projected
         use_exact = false;
         exact_banned = true;
-        if (!eval_pass(C, M, W, P, gb, bf, 0.0, org, false)) return;
+        if (!eval_pass<CL>(C, M, W, P, gb, bf, 0.0, org, false)) return false;
         continue;
       }
-      accept_state(C, W);
+      accept_state(C);
       rn_prev = rn;
-      rn = sqrt(C.red_out[EV_RR]);
-      scale = fmax(sqrt(C.red_out[EV_FCFC]), M.scale_floor);
-      fs[0] = C.red_out[EV_FX]; fs[1] = C.red_out[EV_FY]; fs[2] = C.red_out[EV_FZ];
-      active = (int)C.red_out[EV_ACTIVE];
+      rn = sqrt(red_out[EV_RR]);
+      scale = fmax(sqrt(red_out[EV_FCFC]), M.scale_floor);
+      fs[0] = red_out[EV_FX]; fs[1] = red_out[EV_FY]; fs[2] = red_out[EV_FZ];
+      active = (int)red_out[EV_ACTIVE];
       if (P.tangent_mode == 2) {
         // exact tangent once the step is in its asymptotic regime; back to the
         // projected one for the rest of the step if it misbehaves
@@ -1042,13 +1112,8 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(MeshDev M, WorkDev W, 
     if (!ok) break;
     steps_done = step;
   }
-  // outputs: owned displacement and contact forces of the last evaluated state
-  publish_u(C, W);
-  for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
-    const int g = C.node0 + i;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) W.out_fc[3 * g + k] = C.fc[3 * i + k];
-  }
+  // outputs: u and the contact forces of the last evaluated state are already
+  // in W.u and W.out_fc
   if (leader) {
     st->status = status;
     st->steps_done = steps_done;
@@ -1059,16 +1124,194 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(MeshDev M, WorkDev W, 
     st->scale = scale;
     st->energy = energy;
     st->exact_newton = exact_total;
-    C.cyc[PH_TOTAL] = clock64() - t_start;
-#pragma unroll
-    for (int k = 0; k < PH_N; ++k) st->cycles[k] = C.cyc[k];
   }
   if (threadIdx.x == 0) {
-    if (!leader) C.cyc[PH_TOTAL] = clock64() - t_start;
+    C.cyc[PH_TOTAL] = clock64() - t_start;
+    if (leader) {
+#pragma unroll
+      for (int k = 0; k < PH_N; ++k) st->cycles[k] = C.cyc[k];
+    }
 #pragma unroll
     for (int k = 0; k < PH_N; ++k) {
       atomicMax(&st->cycles_max[k], C.cyc[k]);
       atomicMin(&st->cycles_min[k], C.cyc[k]);
+    }
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(kBlock, 1) solve_kernel(MeshDev M, WorkDev W, SolveParams P, SmemLayout L) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ Statics S;
+  if (P.mode == MODE_BARRIER_TEST) {
+    Barrier tb{W.barrier, W.abort_flag, 0ull, P.timeout_ns, gridDim.x};
+    if (blockIdx.x == 0) return;   // never arrives: the others must time out
+    grid_sync(tb, &S.flag);
+    return;
+  }
+  Ctx C;
+  unsigned char* gscr = W.cta_scratch ? W.cta_scratch + (size_t)blockIdx.x * W.cta_stride : nullptr;
+  setup_ctx(C, M, W, L, smem, gscr, &S, blockIdx.x, gridDim.x);
+  Barrier gb{W.barrier, W.abort_flag, 0ull, P.timeout_ns, gridDim.x};
+  const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+  StatsDev* st = W.stats;
+
+  if (P.mode == MODE_EVAL || P.mode == MODE_APPLY) {
+    double org[3];
+    const double d = P.step > 0 ? P.depths[P.step - 1] : 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) org[k] = P.origin[k] + d * P.dir[k];
+    Bufs bf{0};
+    if (!eval_pass<false>(C, M, W, P, gb, bf, 0.0, org, false)) return;
+    if (P.mode == MODE_EVAL) {
+      // the residual went to W.R (the host points it at the output array)
+      if (leader) {
+        st->elastic = S.red_out[EV_ELASTIC];
+        st->contact_energy = S.red_out[EV_CONTACT];
+        st->residual = sqrt(S.red_out[EV_RR]);
+        st->active = (int)S.red_out[EV_ACTIVE];
+        st->status = S.red_out[EV_BAD] > 0.0 ? ST_NONFINITE : ST_OK;
+      }
+      return;
+    }
+    tangent_pass(C, M, P.tangent_mode == 2 ? 0 : P.tangent_mode);
+    for (int l = threadIdx.x; l < C.n_loc; l += blockDim.x) {
+      const int g = local_to_global(C, M, l);
+      const unsigned mk = M.fixmask[g];
+      C.lm[l] = make_float4((mk & 1u) ? 0.f : (float)W.in_p[3 * g], (mk & 2u) ? 0.f : (float)W.in_p[3 * g + 1],
+                            (mk & 4u) ? 0.f : (float)W.in_p[3 * g + 2], 0.f);
+    }
+    __syncthreads();
+    matvec_pass(C, M);
+    for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
+      const float4 q = C.lm[i];
+      const float v[3] = {q.x, q.y, q.z};
+      float y[3];
+      finish_product(C, i, v, y);
+      const int g = C.node0 + i;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) W.out_y[3 * g + k] = y[k];
+    }
+    if (leader) st->status = ST_OK;
+    return;
+  }
+  int ep = 0;
+  unsigned long long n_pub = 0;
+  solve_body<false>(C, M, W, P, gb, ep, n_pub);
+}
+
+// One solve per cluster; the cluster's rank-0 CTA takes the next job from the
+// queue and every CTA of the cluster reads it from there. All CTAs leave the
+// loop together.
+__global__ void __launch_bounds__(kBlock, 1) cluster_kernel(const BatchJob* __restrict__ jobs, int n_jobs,
+                                                            int* queue, SlotScratch S, SmemLayout L) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ Statics ST;
+  __shared__ MeshDev sM;
+  __shared__ SolveParams sP;
+  __shared__ WorkDev sW;
+  __shared__ int s_job;
+  const unsigned rank = cluster_rank(), ncta = cluster_ncta();
+  const size_t slot = blockIdx.x / ncta;
+  unsigned char* sb = S.base + slot * (size_t)S.stride;
+  unsigned char* gscr = S.cta_stride > 0 ? sb + S.cta + (size_t)rank * (size_t)S.cta_stride : nullptr;
+  for (;;) {
+    if (rank == 0 && threadIdx.x == 0) s_job = atomicAdd(queue, 1);
+    cluster_sync();
+    const int j = *peer(&s_job, 0u);
+    cluster_sync();   // rank 0 leaves or rewrites s_job only after every CTA read it
+    if (j >= n_jobs) return;
+    const BatchJob* J = jobs + j;
+    {
+      const int* src = reinterpret_cast<const int*>(&J->mesh);
+      int* dst = reinterpret_cast<int*>(&sM);
+      for (int i = threadIdx.x; i < (int)(sizeof(MeshDev) / 4); i += blockDim.x) dst[i] = src[i];
+      src = reinterpret_cast<const int*>(&J->prm);
+      dst = reinterpret_cast<int*>(&sP);
+      for (int i = threadIdx.x; i < (int)(sizeof(SolveParams) / 4); i += blockDim.x) dst[i] = src[i];
+    }
+    if (threadIdx.x == 0) {
+      WorkDev w{};
+      w.u = J->u;
+      w.R = reinterpret_cast<double*>(sb + S.R);
+      w.uprev = reinterpret_cast<double*>(sb + S.uprev);
+      w.dpub = reinterpret_cast<float4*>(sb + S.dpub);
+      w.tangent = reinterpret_cast<float4*>(sb + S.tangent);
+      w.out_fc = J->out_fc;
+      w.step_force = J->step_force;
+      w.stats = J->stats;
+      sW = w;
+    }
+    __syncthreads();
+    Ctx C;
+    setup_ctx(C, sM, sW, L, smem, gscr, &ST, (int)rank, (int)ncta);
+    Barrier unused{nullptr, nullptr, 0ull, 0ull, 0u};
+    int ep = 0;
+    unsigned long long n_pub = 0;
+    solve_body<true>(C, sM, sW, sP, unused, ep, n_pub);
+    cluster_sync();   // no CTA starts the next job while a peer still reads its shared memory
+  }
+}
+
+// Group engine: CTAs [g*P, (g+1)*P) form group g and run one solve at a time
+// with the single-solve kernel's synchronisation on the group's own counters;
+// part 0 takes the next job from the queue. The launch is cooperative, so all
+// groups are co-resident; a group whose wait expires marks its job and leaves.
+__global__ void __launch_bounds__(kBlock, 1) group_kernel(const BatchJob* __restrict__ jobs, int n_jobs,
+                                                          int* queue, SlotScratch S, SmemLayout L, int parts,
+                                                          unsigned long long timeout_ns) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ Statics ST;
+  __shared__ MeshDev sM;
+  __shared__ SolveParams sP;
+  __shared__ WorkDev sW;
+  const int group = blockIdx.x / parts, part = blockIdx.x - group * parts;
+  unsigned char* sb = S.base + (size_t)group * (size_t)S.stride;
+  unsigned long long* ctrl = reinterpret_cast<unsigned long long*>(sb + S.ctrl);
+  unsigned char* gscr = S.cta_stride > 0 ? sb + S.cta + (size_t)part * (size_t)S.cta_stride : nullptr;
+  Barrier gb{ctrl, reinterpret_cast<int*>(ctrl + 1), 0ull, timeout_ns, (unsigned)parts};
+  int ep = 0;
+  unsigned long long n_pub = 0;
+  for (;;) {
+    if (part == 0 && threadIdx.x == 0)
+      *reinterpret_cast<volatile unsigned long long*>(ctrl + 2) = (unsigned long long)atomicAdd(queue, 1);
+    if (!grid_sync(gb, &ST.flag)) return;
+    // part 0 rewrites the job word only after the next solve's first barrier,
+    // which every part reaches after this read
+    const int j = (int)ld_volatile_u64(ctrl + 2);
+    if (j >= n_jobs) return;
+    const BatchJob* J = jobs + j;
+    {
+      const int* src = reinterpret_cast<const int*>(&J->mesh);
+      int* dst = reinterpret_cast<int*>(&sM);
+      for (int i = threadIdx.x; i < (int)(sizeof(MeshDev) / 4); i += blockDim.x) dst[i] = src[i];
+      src = reinterpret_cast<const int*>(&J->prm);
+      dst = reinterpret_cast<int*>(&sP);
+      for (int i = threadIdx.x; i < (int)(sizeof(SolveParams) / 4); i += blockDim.x) dst[i] = src[i];
+    }
+    if (threadIdx.x == 0) {
+      WorkDev w{};
+      w.u = J->u;
+      w.R = reinterpret_cast<double*>(sb + S.R);
+      w.uprev = reinterpret_cast<double*>(sb + S.uprev);
+      w.vpub = reinterpret_cast<unsigned long long*>(sb + S.vpub);
+      w.dpub = reinterpret_cast<float4*>(sb + S.dpub);
+      w.tangent = reinterpret_cast<float4*>(sb + S.tangent);
+      w.partials = reinterpret_cast<double*>(sb + S.partials);
+      w.cgslot = reinterpret_cast<unsigned long long*>(sb + S.cgslot);
+      w.barrier = ctrl;
+      w.abort_flag = reinterpret_cast<int*>(ctrl + 1);
+      w.out_fc = J->out_fc;
+      w.step_force = J->step_force;
+      w.stats = J->stats;
+      sW = w;
+    }
+    __syncthreads();
+    Ctx C;
+    setup_ctx(C, sM, sW, L, smem, gscr, &ST, part, parts);
+    if (!solve_body<false>(C, sM, sW, sP, gb, ep, n_pub)) {
+      if (part == 0 && threadIdx.x == 0) sW.stats->status = ST_TIMEOUT;
+      return;
     }
   }
 }
@@ -1095,15 +1338,19 @@ cudaError_t launch_permute(const double* src, double* dst, const int* perm, int 
   return cudaGetLastError();
 }
 
-cudaError_t solve_kernel_occupancy(int smem_bytes, int* blocks_per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+cudaError_t solve_kernel_attrs(int smem_bytes, int* static_smem, int* blocks_per_sm) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, solve_kernel);
+  if (e != cudaSuccess) return e;
+  if (static_smem) *static_smem = (int)fa.sharedSizeBytes;
+  if (!blocks_per_sm) return cudaSuccess;
+  e = cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, solve_kernel, kBlock, smem_bytes);
 }
 
-cudaError_t launch_solve(const MeshDev& mesh, const WorkDev& work, const SolveParams& prm,
+cudaError_t launch_solve(const MeshDev& mesh, const WorkDev& work, const SolveParams& prm, const SmemLayout& L,
                          cudaStream_t stream, float* kernel_ms) {
-  const SmemLayout L = smem_layout(mesh);
   cudaError_t e = cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
   if (e != cudaSuccess) return e;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -1115,7 +1362,8 @@ cudaError_t launch_solve(const MeshDev& mesh, const WorkDev& work, const SolvePa
   MeshDev m = mesh;
   WorkDev w = work;
   SolveParams p = prm;
-  void* args[] = {&m, &w, &p};
+  SmemLayout l = L;
+  void* args[] = {&m, &w, &p, &l};
   e = cudaLaunchCooperativeKernel((const void*)solve_kernel, dim3(mesh.n_parts), dim3(kBlock), args,
                                   (size_t)L.total, stream);
   if (kernel_ms) {
@@ -1124,6 +1372,117 @@ cudaError_t launch_solve(const MeshDev& mesh, const WorkDev& work, const SolvePa
       cudaError_t s = cudaEventSynchronize(ev1);
       if (s == cudaSuccess) cudaEventElapsedTime(kernel_ms, ev0, ev1);
       else e = s;
+    }
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+  }
+  return e;
+}
+
+static cudaLaunchConfig_t cluster_config(int cluster, int n_slots, int smem_bytes, cudaStream_t stream,
+                                         cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)(cluster * n_slots));
+  cfg.blockDim = dim3(kBlock);
+  cfg.dynamicSmemBytes = (size_t)smem_bytes;
+  cfg.stream = stream;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+static cudaError_t cluster_func_setup(int cluster, int smem_bytes) {
+  cudaError_t e = cudaFuncSetAttribute(cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+  if (e != cudaSuccess) return e;
+  if (cluster > 8) e = cudaFuncSetAttribute(cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return e;
+}
+
+// Static shared bytes of the cluster kernel and, for a cluster size and
+// dynamic shared size, how many clusters can be resident at once.
+cudaError_t cluster_kernel_attrs(int cluster, int smem_bytes, int* static_smem, int* max_clusters) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, cluster_kernel);
+  if (e != cudaSuccess) return e;
+  if (static_smem) *static_smem = (int)fa.sharedSizeBytes;
+  if (!max_clusters) return cudaSuccess;
+  e = cluster_func_setup(cluster, smem_bytes);
+  if (e != cudaSuccess) return e;
+  cudaLaunchAttribute attr[1];
+  int n_sm = 1, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  cudaLaunchConfig_t cfg = cluster_config(cluster, (n_sm + cluster - 1) / cluster, smem_bytes, 0, attr);
+  return cudaOccupancyMaxActiveClusters(max_clusters, (const void*)cluster_kernel, &cfg);
+}
+
+cudaError_t launch_cluster(const BatchJob* d_jobs, int n_jobs, int* d_queue, const SlotScratch& S,
+                           const SmemLayout& L, int cluster, int n_slots, cudaStream_t stream, float* kernel_ms) {
+  cudaError_t e = cluster_func_setup(cluster, L.total);
+  if (e != cudaSuccess) return e;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (kernel_ms) {
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    cudaEventRecord(ev0, stream);
+  }
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = cluster_config(cluster, n_slots, L.total, stream, attr);
+  e = cudaLaunchKernelEx(&cfg, cluster_kernel, d_jobs, n_jobs, d_queue, S, L);
+  if (kernel_ms) {
+    cudaEventRecord(ev1, stream);
+    if (e == cudaSuccess) {
+      cudaError_t s = cudaEventSynchronize(ev1);
+      if (s == cudaSuccess) cudaEventElapsedTime(kernel_ms, ev0, ev1);
+      else e = s;
+    }
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+  }
+  return e;
+}
+
+cudaError_t group_kernel_attrs(int smem_bytes, int* static_smem, int* blocks_per_sm) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, group_kernel);
+  if (e != cudaSuccess) return e;
+  if (static_smem) *static_smem = (int)fa.sharedSizeBytes;
+  if (!blocks_per_sm) return cudaSuccess;
+  e = cudaFuncSetAttribute(group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, group_kernel, kBlock, smem_bytes);
+}
+
+cudaError_t launch_groups(const BatchJob* d_jobs, int n_jobs, int* d_queue, const SlotScratch& S,
+                          const SmemLayout& L, int parts, int n_groups, unsigned long long timeout_ns,
+                          cudaStream_t stream, float* kernel_ms) {
+  cudaError_t e = cudaFuncSetAttribute(group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
+  if (e != cudaSuccess) return e;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (kernel_ms) {
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    cudaEventRecord(ev0, stream);
+  }
+  const BatchJob* j = d_jobs;
+  int n = n_jobs, p = parts;
+  int* q = d_queue;
+  SlotScratch s = S;
+  SmemLayout l = L;
+  unsigned long long t = timeout_ns;
+  void* args[] = {&j, &n, &q, &s, &l, &p, &t};
+  e = cudaLaunchCooperativeKernel((const void*)group_kernel, dim3((unsigned)(parts * n_groups)), dim3(kBlock), args,
+                                  (size_t)L.total, stream);
+  if (kernel_ms) {
+    cudaEventRecord(ev1, stream);
+    if (e == cudaSuccess) {
+      cudaError_t s2 = cudaEventSynchronize(ev1);
+      if (s2 == cudaSuccess) cudaEventElapsedTime(kernel_ms, ev0, ev1);
+      else e = s2;
     }
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);

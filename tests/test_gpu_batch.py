@@ -1,6 +1,7 @@
-"""Batched solves (one CTA per solve, jobs from a queue) on the GPU: parity
-with the FP64 oracle and with the single-solve kernel, independence of a
-job's result from the rest of the batch, uneven meshes in one launch."""
+"""Batched solves on the GPU, both engines (CTA groups of one cooperative
+launch; thread-block clusters), jobs taken from a queue: parity with the FP64
+oracle, a job's result bitwise independent of the rest of the batch and of the
+slot that ran it, uneven meshes in one launch."""
 import os
 
 import numpy as np
@@ -26,22 +27,26 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
 
 
-def _batch(F, meshes, handles, inds, tol=1e-6, max_newton=None):
+ENGINES = [(1, 0), (2, 0)]        # (FEM_BATCH_GROUPS, automatic parts), (FEM_BATCH_CLUSTERS, automatic)
+
+
+def _batch(F, meshes, handles, inds, tol=1e-6, max_newton=None, engine=(1, 0)):
     out = [np.zeros((m.n_nodes, 3)) for m in meshes]
     frc = [np.zeros((d.n_steps, 3)) for d in inds]
-    opt = None
+    opt = F.fem_default_options()
     if max_newton is not None:
-        opt = F.fem_default_options()
         opt.max_newton = max_newton
+    opt.batch_engine, opt.batch_parts = engine
     rc, st = F.fem_solve_batch(handles, inds, tol, opt, out, frc)
     return rc, out, frc, st
 
 
-def test_batch_cube_matches_oracle(F):
+@pytest.mark.parametrize("engine", ENGINES + [(1, 3), (2, 4)])
+def test_batch_cube_matches_oracle(F, engine):
     m, ind = W.cube_sphere()
     h = F.fem_create_mesh(m.nodes, m.tets, m.tet_material, m.materials, m.fixed_nodes)
     ref = Problem(m, ind).solve(tol=1e-10)
-    rc, out, frc, st = _batch(F, [m] * 3, [h] * 3, [ind] * 3)
+    rc, out, frc, st = _batch(F, [m] * 3, [h] * 3, [ind] * 3, engine=engine)
     assert rc == 0
     for k in range(3):
         assert st[k].steps_done == 10 and st[k].residual <= 1e-6 * st[k].scale
@@ -52,22 +57,23 @@ def test_batch_cube_matches_oracle(F):
     F.fem_destroy_mesh(h)
 
 
-def test_batch_fingertip_matches_golden_and_is_mix_independent(F):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_batch_fingertip_matches_golden_and_is_mix_independent(F, engine):
     g = np.load(os.path.join(HERE, "golden", "fingertip_sphere_oracle.npz"))
     m, ind = W.fingertip_sphere()
     draws = W.draw_indentations(m, 5, seed=77)
     h = F.fem_create_mesh(m.nodes, m.tets, m.tet_material, m.materials, m.fixed_nodes)
     # deep random draws need more Newton iterations in their last load steps
     # than the default cap allows
-    rc, out, frc, st = _batch(F, [m] * 6, [h] * 6, [ind] + draws, max_newton=200)
+    rc, out, frc, st = _batch(F, [m] * 6, [h] * 6, [ind] + draws, max_newton=200, engine=engine)
     assert rc == 0, [s.status for s in st]
     e_u = rel(out[0], g["u"])
     e_f = max(rel(frc[0][s], g["step_force"][s]) for s in range(20))
-    print(f"batch fingertip: rel-L2(u)={e_u:.2e} max rel F={e_f:.2e} newton={st[0].newton_iters} "
+    print(f"batch fingertip {engine}: rel-L2(u)={e_u:.2e} max rel F={e_f:.2e} newton={st[0].newton_iters} "
           f"cg={st[0].cg_iters} kernel={st[0].kernel_ms:.1f} ms")
     assert e_u <= 1e-4 and e_f <= 1e-3
     # the same job alone: bitwise identical to its result inside the mix
-    rc1, out1, frc1, _ = _batch(F, [m], [h], [draws[2]], max_newton=200)
+    rc1, out1, frc1, _ = _batch(F, [m], [h], [draws[2]], max_newton=200, engine=engine)
     assert rc1 == 0
     assert np.array_equal(out1[0], out[3]) and np.array_equal(frc1[0], frc[3])
     # every draw certified by the oracle's own FP64 residual
@@ -77,12 +83,13 @@ def test_batch_fingertip_matches_golden_and_is_mix_independent(F):
     F.fem_destroy_mesh(h)
 
 
-def test_batch_uneven_meshes(F):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_batch_uneven_meshes(F, engine):
     jobs = W.uneven_fingertips(3, seed=5, tet_min=4e3, tet_max=2e4)
     meshes = [m for m, _ in jobs]
     inds = [d for _, d in jobs]
     handles = [F.fem_create_mesh(m.nodes, m.tets, m.tet_material, m.materials, m.fixed_nodes) for m in meshes]
-    rc, out, frc, st = _batch(F, meshes, handles, inds, max_newton=200)
+    rc, out, frc, st = _batch(F, meshes, handles, inds, max_newton=200, engine=engine)
     assert rc == 0, [s.status for s in st]
     for k, (m, d) in enumerate(jobs):
         rn, scale, _ = Problem(m, d).residual_norm(out[k], d.n_steps)

@@ -27,6 +27,27 @@ def test_default_options():
     from paper_2103_16747_b300 import _lib as L
     o = L.fem_default_options()
     assert o.c_kappa == 100.0 and o.max_cg == 2000 and o.tangent == L.FEM_TANGENT_ADAPTIVE
+    assert o.batch_engine == L.FEM_BATCH_AUTO and o.batch_parts == 0
+
+
+@pytest.mark.parametrize("field,value", [("batch_engine", 3), ("batch_parts", -1), ("batch_parts", 300),
+                                         ("tangent", 7), ("max_cg", 0)])
+def test_batch_options_are_checked_before_any_device_call(field, value):
+    """Invalid options are rejected on the host (no mesh is touched)."""
+    from paper_2103_16747_b300 import _lib as L
+    o = L.fem_default_options()
+    setattr(o, field, value)
+    ind = W.cube_sphere_indenter()
+    rc, _ = L.fem_solve_batch([None], [ind], 1e-6, o, [np.zeros((8, 3))], check=False)
+    assert rc == L.FEM_ERR_ARG and "fem_options" in L.fem_last_error()
+
+
+def test_cluster_engine_takes_powers_of_two_up_to_16():
+    from paper_2103_16747_b300 import _lib as L
+    o = L.fem_default_options()
+    o.batch_engine, o.batch_parts = L.FEM_BATCH_CLUSTERS, 3
+    rc, _ = L.fem_solve_batch([None], [W.cube_sphere_indenter()], 1e-6, o, [np.zeros((8, 3))], check=False)
+    assert rc == L.FEM_ERR_ARG and "fem_options" in L.fem_last_error()
 
 
 @pytest.mark.parametrize("case", ["index", "repeat", "inverted", "flat", "nan", "material", "mask", "sizes"])
