@@ -246,6 +246,45 @@ int fem_solve_batch(fem_mesh* const* meshes, const fem_indenter* indenters, int3
                     const fem_options* opt, double* const* out_disp, double* const* out_contact_force,
                     fem_stats* stats);
 
+/*
+ * Reusable batch plan: the batched solve of fem_solve_batch split into a
+ * planning call and repeatable runs. fem_batch_create fixes the meshes, the
+ * load-step count of each solve and the options (engine, part count, solver
+ * settings); it builds the partitions, allocates the device workspace and
+ * pinned staging, and captures the whole batch (workspace reset, upload of the
+ * job table and schedules, the persistent launch, reordering of the outputs)
+ * as a CUDA graph. Errors: as fem_solve_batch's planning (FEM_ERR_ARG,
+ * FEM_ERR_TOO_LARGE, FEM_ERR_OOM, FEM_ERR_CUDA).
+ */
+typedef struct fem_batch fem_batch;
+int fem_batch_create(fem_mesh* const* meshes, const int32_t* n_steps, int32_t n, const fem_options* opt,
+                     fem_batch** out);
+
+/*
+ * One run of the plan: indenters[i] (n_steps must match the plan) at residual
+ * tolerance tol; outputs and return value as fem_solve_batch (kernel_ms: the
+ * replayed graph). Runs of one plan must not overlap (each run waits for the
+ * GPU before it returns). Work queued earlier on meshes[0]'s stream completes
+ * before the run starts.
+ */
+int fem_batch_run(fem_batch* batch, const fem_indenter* indenters, double tol, double* const* out_disp,
+                  double* const* out_contact_force, fem_stats* stats);
+
+typedef struct {
+    int32_t engine;                 /* FEM_BATCH_GROUPS or FEM_BATCH_CLUSTERS        */
+    int32_t parts;                  /* CTAs per solve                                */
+    int32_t slots;                  /* solves in flight at once                      */
+    int32_t graph;                  /* 1: runs replay a captured CUDA graph          */
+    int32_t smem_bytes;             /* dynamic shared memory per CTA                 */
+    int32_t global_bytes_per_cta;   /* per-CTA arrays that did not fit on chip        */
+    int32_t resident_tangent;       /* 1: part tangents live in shared memory        */
+    int64_t workspace_bytes;        /* device workspace of the plan                  */
+} fem_batch_info;
+int fem_batch_info_get(const fem_batch* batch, fem_batch_info* info);
+
+/* Release the plan (NULL is ignored). */
+void fem_batch_destroy(fem_batch* batch);
+
 /* Release the mesh and its device memory (NULL is ignored). */
 void fem_destroy_mesh(fem_mesh* mesh);
 

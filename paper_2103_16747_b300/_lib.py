@@ -40,7 +40,8 @@ PHASES = ("eval", "tangent", "pcg_init", "pcg_reduce", "pcg_matvec", "pcg_update
 EXPORTS = ("fem_default_options", "fem_create_mesh", "fem_set_indenter", "fem_set_dirichlet_values",
            "fem_solve", "fem_solve_batch", "fem_destroy_mesh", "fem_last_error", "fem_mesh_info_get", "fem_repartition",
            "fem_eval_residual", "fem_eval_residual_noalloc", "fem_apply_tangent",
-           "fem_debug_barrier_timeout")
+           "fem_debug_barrier_timeout", "fem_batch_create", "fem_batch_run", "fem_batch_info_get",
+           "fem_batch_destroy")
 
 
 class fem_material(C.Structure):
@@ -79,6 +80,12 @@ class fem_mesh_info(C.Structure):
                 ("n_candidates", C.c_int64), ("device_bytes", C.c_int64)]
 
 
+class fem_batch_info(C.Structure):
+    _fields_ = [("engine", C.c_int32), ("parts", C.c_int32), ("slots", C.c_int32), ("graph", C.c_int32),
+                ("smem_bytes", C.c_int32), ("global_bytes_per_cta", C.c_int32), ("resident_tangent", C.c_int32),
+                ("workspace_bytes", C.c_int64)]
+
+
 class FemError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{ERR_NAMES.get(code, code)}: {msg}")
@@ -107,6 +114,10 @@ def _load():
         "fem_eval_residual_noalloc": (C.c_int, [P, P, C.c_int32, C.POINTER(fem_options), P, P, P]),
         "fem_apply_tangent": (C.c_int, [P, P, C.c_int32, C.POINTER(fem_options), P, P]),
         "fem_debug_barrier_timeout": (C.c_int, [C.c_double]),
+        "fem_batch_create": (C.c_int, [P, P, C.c_int32, C.POINTER(fem_options), C.POINTER(P)]),
+        "fem_batch_run": (C.c_int, [P, P, C.c_double, P, P, P]),
+        "fem_batch_info_get": (C.c_int, [P, C.POINTER(fem_batch_info)]),
+        "fem_batch_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -210,6 +221,34 @@ def fem_solve(mesh, load_steps, tol, opt=None, out_disp=None, out_contact_force=
     return rc, st
 
 
+def _indenter_array(indenters, keep):
+    n = len(indenters)
+    arr = (fem_indenter * n)()
+    for i, d in enumerate(indenters):
+        sched = np.ascontiguousarray(d.depth_schedule, dtype=np.float64)
+        keep.append(sched)
+        arr[i].shape = int(d.shape)
+        arr[i].pose[:] = [float(v) for v in np.asarray(d.pose, dtype=np.float64)]
+        prm = np.zeros(3) if d.params is None else np.asarray(d.params, dtype=np.float64)
+        arr[i].params[:] = [float(v) for v in prm]
+        arr[i].dir[:] = [float(v) for v in np.asarray(d.direction, dtype=np.float64)]
+        arr[i].depth_schedule = sched.ctypes.data
+        arr[i].n_steps = len(sched)
+    return arr
+
+
+def _mesh_array(meshes):
+    return (C.c_void_p * len(meshes))(*[m.value if isinstance(m, C.c_void_p) else m for m in meshes])
+
+
+def _batch_outputs(n, out_disp, out_contact_force, keep):
+    disp = (C.c_void_p * n)(*[_out_ptr(a, np.float64, keep).value for a in out_disp])
+    forces = None
+    if out_contact_force is not None:
+        forces = (C.c_void_p * n)(*[_out_ptr(a, np.float64, keep).value for a in out_contact_force])
+    return disp, forces
+
+
 def fem_solve_batch(meshes, indenters, tol, opt=None, out_disp=None, out_contact_force=None, check=True):
     """Batched solves. ``meshes``: list of handles (repeats allowed);
     ``indenters``: objects with shape/pose/params/direction/depth_schedule;
@@ -217,22 +256,9 @@ def fem_solve_batch(meshes, indenters, tol, opt=None, out_disp=None, out_contact
     or device). Returns (rc, list of fem_stats)."""
     n = len(meshes)
     keep = []
-    mesh_arr = (C.c_void_p * n)(*[m.value if isinstance(m, C.c_void_p) else m for m in meshes])
-    ind_arr = (fem_indenter * n)()
-    for i, d in enumerate(indenters):
-        sched = np.ascontiguousarray(d.depth_schedule, dtype=np.float64)
-        keep.append(sched)
-        ind_arr[i].shape = int(d.shape)
-        ind_arr[i].pose[:] = [float(v) for v in np.asarray(d.pose, dtype=np.float64)]
-        prm = np.zeros(3) if d.params is None else np.asarray(d.params, dtype=np.float64)
-        ind_arr[i].params[:] = [float(v) for v in prm]
-        ind_arr[i].dir[:] = [float(v) for v in np.asarray(d.direction, dtype=np.float64)]
-        ind_arr[i].depth_schedule = sched.ctypes.data
-        ind_arr[i].n_steps = len(sched)
-    disp = (C.c_void_p * n)(*[_out_ptr(a, np.float64, keep).value for a in out_disp])
-    forces = None
-    if out_contact_force is not None:
-        forces = (C.c_void_p * n)(*[_out_ptr(a, np.float64, keep).value for a in out_contact_force])
+    mesh_arr = _mesh_array(meshes)
+    ind_arr = _indenter_array(indenters, keep)
+    disp, forces = _batch_outputs(n, out_disp, out_contact_force, keep)
     stats = (fem_stats * n)()
     rc = lib.fem_solve_batch(C.cast(mesh_arr, C.c_void_p), C.cast(ind_arr, C.c_void_p), n, float(tol),
                              C.byref(opt) if opt is not None else None, C.cast(disp, C.c_void_p),
@@ -241,6 +267,48 @@ def fem_solve_batch(meshes, indenters, tol, opt=None, out_disp=None, out_contact
     if check:
         _check(rc)
     return rc, list(stats)
+
+
+class FemBatch:
+    """A reusable batch plan (fem_batch_create): fixed meshes, load-step
+    counts and options; ``run`` replays the captured batch with new
+    indenters."""
+
+    def __init__(self, meshes, n_steps, opt=None):
+        n = len(meshes)
+        self.n = n
+        steps = np.ascontiguousarray(n_steps, dtype=np.int32)
+        h = C.c_void_p()
+        _check(lib.fem_batch_create(C.cast(_mesh_array(meshes), C.c_void_p), C.c_void_p(steps.ctypes.data), n,
+                                    C.byref(opt) if opt is not None else None, C.byref(h)))
+        self.handle = h
+
+    def info(self) -> fem_batch_info:
+        i = fem_batch_info()
+        _check(lib.fem_batch_info_get(self.handle, C.byref(i)))
+        return i
+
+    def run(self, indenters, tol, out_disp, out_contact_force=None, check=True):
+        keep = []
+        ind_arr = _indenter_array(indenters, keep)
+        disp, forces = _batch_outputs(self.n, out_disp, out_contact_force, keep)
+        stats = (fem_stats * self.n)()
+        rc = lib.fem_batch_run(self.handle, C.cast(ind_arr, C.c_void_p), float(tol), C.cast(disp, C.c_void_p),
+                               C.cast(forces, C.c_void_p) if forces is not None else None, C.cast(stats, C.c_void_p))
+        if check:
+            _check(rc)
+        return rc, list(stats)
+
+    def close(self):
+        if self.handle:
+            lib.fem_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def fem_destroy_mesh(mesh):

@@ -21,13 +21,16 @@
 #include <vector>
 
 #include "../../include/fem.h"
-#include "fem_internal.h"
+#include "fem_host.h"
 
 using namespace fem;
 
-namespace {
+namespace fem {
+namespace host {
 
 thread_local std::string g_err;
+
+std::string& last_error() { return g_err; }
 
 int fail(int code, const char* fmt, ...) {
   char buf[512];
@@ -45,11 +48,12 @@ int cuda_fail(cudaError_t e, const char* what) {
   return fail(FEM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-#define CUDA_TRY(call, what)                       \
-  do {                                             \
-    cudaError_t e_ = (call);                       \
-    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
-  } while (0)
+}  // namespace host
+}  // namespace fem
+
+using namespace fem::host;
+
+namespace {
 
 uint64_t spread_bits(uint64_t v) {
   v &= 0x1fffff;
@@ -85,48 +89,6 @@ cudaError_t alloc(T** dptr, size_t count, std::vector<void*>& owned, size_t& byt
 
 }  // namespace
 
-struct fem_mesh {
-  cudaStream_t stream = nullptr;
-  int device = 0;
-  int64_t n_nodes = 0, n_tets = 0, n_fixed = 0;
-  std::vector<int> perm;        // new node -> caller node
-  std::vector<int> fixed_nodes; // caller ids
-  std::vector<unsigned char> fixed_bits;  // per fixed entry
-  std::vector<unsigned char> node_mask;   // per new node
-  // host copies needed to re-partition
-  std::vector<int> tets_new;    // 4 per sorted tet
-  std::vector<double> dminv;    // 9 per sorted tet
-  std::vector<double> vol;
-  std::vector<int> mat;
-  std::vector<int> csr_ptr, csr_ent;   // node -> (tet << 2 | corner), new numbering
-  double h_bar = 0, scale_floor = 0;
-  int64_t n_candidates = 0;
-  MeshDev dev{};                 // partition of the single-solve kernel (one part per CTA)
-  WorkDev work{};
-  SmemLayout layout{};
-  PartDims dims{};
-  std::vector<void*> owned;     // every device allocation of the mesh
-  std::vector<void*> part_owned, cpart_owned;
-  size_t bytes = 0, part_bytes = 0, cpart_bytes = 0;
-  MeshDev cdev{};                // partition for clustered solves (built on first batched use)
-  PartDims cdims{};
-  int c_parts = 0;               // parts of cdev (0: not built)
-  // indenter
-  bool has_indenter = false;
-  int shape = 0;
-  double origin[3]{}, R[9]{}, iparams[3]{}, dir[3]{};
-  int n_steps = 0;
-  double* d_depths = nullptr;
-  bool has_presc = false;
-  double* d_presc = nullptr;
-  double* d_stage = nullptr;     // 3*n_nodes staging in caller order
-  int* d_perm = nullptr;         // new -> caller
-};
-
-namespace fem {
-cudaError_t launch_permute(const double* src, double* dst, const int* perm, int n, bool to_caller,
-                           cudaStream_t s);
-}
 
 namespace {
 
@@ -310,6 +272,11 @@ int build_partition(fem_mesh* m, int n_parts, MeshDev& D, PartDims& dims, std::v
 // memory while they fit; the rest go to the CTA's global scratch region (the
 // tangent, tet ids and node->tet lists are then read from their global
 // arrays). Returns total = -1 if even the fixed part does not fit.
+}  // namespace
+
+namespace fem {
+namespace host {
+
 SmemLayout plan_layout(const PartDims& d, int budget) {
   SmemLayout L{};
   for (int attempt = 0; attempt < 2; ++attempt) {
@@ -378,6 +345,11 @@ int smem_budget(const fem_mesh* m, int static_smem) {
   return dev_smem - static_smem;
 }
 
+}  // namespace host
+}  // namespace fem
+
+namespace {
+
 // Partition of the single-solve kernel: n_parts CTAs, all co-resident.
 int build_partitions(fem_mesh* m, int n_parts) {
   if (n_parts > 256) return fail(FEM_ERR_TOO_LARGE, "at most 256 parts (asked %d)", n_parts);
@@ -442,6 +414,11 @@ int build_partitions(fem_mesh* m, int n_parts) {
   return FEM_OK;
 }
 
+}  // namespace
+
+namespace fem {
+namespace host {
+
 // Partition for batched solves with `parts` CTAs per solve (rebuilt when the
 // part count changes).
 int ensure_batch_partition(fem_mesh* m, int parts) {
@@ -453,6 +430,11 @@ int ensure_batch_partition(fem_mesh* m, int parts) {
   return FEM_OK;
 }
 
+}  // namespace host
+}  // namespace fem
+
+namespace {
+
 int default_parts(const fem_mesh* m) {
   int n_sm = 1;
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, m->device);
@@ -461,6 +443,40 @@ int default_parts(const fem_mesh* m) {
 }
 
 }  // namespace
+
+namespace fem {
+namespace host {
+
+int validate_indenter(int shape, const double pose[12], const double* params, const double dir[3],
+                             const double* depth_schedule, int32_t n_steps) {
+  if (!pose || !dir || !depth_schedule) return fail(FEM_ERR_ARG, "NULL argument");
+  if (shape < FEM_SPHERE || shape > FEM_PLANE) return fail(FEM_ERR_ARG, "unknown shape %d", shape);
+  if (n_steps < 1 || n_steps > FEM_MAX_STEPS) return fail(FEM_ERR_ARG, "n_steps=%d out of range", n_steps);
+  if (shape != FEM_PLANE && !params) return fail(FEM_ERR_ARG, "params is NULL");
+  for (int k = 0; k < 12; ++k)
+    if (!std::isfinite(pose[k])) return fail(FEM_ERR_NONFINITE, "pose not finite");
+  for (int k = 0; k < 3; ++k)
+    if (!std::isfinite(dir[k]) || (params && shape != FEM_PLANE && !std::isfinite(params[k])))
+      return fail(FEM_ERR_NONFINITE, "dir/params not finite");
+  const double dn = std::sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+  if (std::fabs(dn - 1.0) > 1e-6) return fail(FEM_ERR_ARG, "dir must be a unit vector (|a|=%g)", dn);
+  const double* R = pose + 3;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double d = 0.0;
+      for (int k = 0; k < 3; ++k) d += R[3 * k + i] * R[3 * k + j];
+      if (std::fabs(d - (i == j ? 1.0 : 0.0)) > 1e-6) return fail(FEM_ERR_ARG, "pose rotation is not orthonormal");
+    }
+  if (shape == FEM_SPHERE || shape == FEM_CYLINDER) {
+    if (!(params[0] > 0)) return fail(FEM_ERR_ARG, "radius must be > 0");
+  } else if (shape == FEM_BOX) {
+    if (!(params[0] > 0 && params[1] > 0 && params[2] > 0)) return fail(FEM_ERR_ARG, "box half extents must be > 0");
+  }
+  return FEM_OK;
+}
+
+}  // namespace host
+}  // namespace fem
 
 extern "C" {
 
@@ -789,33 +805,6 @@ int fem_mesh_info_get(const fem_mesh* m, fem_mesh_info* info) {
   return FEM_OK;
 }
 
-static int validate_indenter(int shape, const double pose[12], const double* params, const double dir[3],
-                             const double* depth_schedule, int32_t n_steps) {
-  if (!pose || !dir || !depth_schedule) return fail(FEM_ERR_ARG, "NULL argument");
-  if (shape < FEM_SPHERE || shape > FEM_PLANE) return fail(FEM_ERR_ARG, "unknown shape %d", shape);
-  if (n_steps < 1 || n_steps > FEM_MAX_STEPS) return fail(FEM_ERR_ARG, "n_steps=%d out of range", n_steps);
-  if (shape != FEM_PLANE && !params) return fail(FEM_ERR_ARG, "params is NULL");
-  for (int k = 0; k < 12; ++k)
-    if (!std::isfinite(pose[k])) return fail(FEM_ERR_NONFINITE, "pose not finite");
-  for (int k = 0; k < 3; ++k)
-    if (!std::isfinite(dir[k]) || (params && shape != FEM_PLANE && !std::isfinite(params[k])))
-      return fail(FEM_ERR_NONFINITE, "dir/params not finite");
-  const double dn = std::sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
-  if (std::fabs(dn - 1.0) > 1e-6) return fail(FEM_ERR_ARG, "dir must be a unit vector (|a|=%g)", dn);
-  const double* R = pose + 3;
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) {
-      double d = 0.0;
-      for (int k = 0; k < 3; ++k) d += R[3 * k + i] * R[3 * k + j];
-      if (std::fabs(d - (i == j ? 1.0 : 0.0)) > 1e-6) return fail(FEM_ERR_ARG, "pose rotation is not orthonormal");
-    }
-  if (shape == FEM_SPHERE || shape == FEM_CYLINDER) {
-    if (!(params[0] > 0)) return fail(FEM_ERR_ARG, "radius must be > 0");
-  } else if (shape == FEM_BOX) {
-    if (!(params[0] > 0 && params[1] > 0 && params[2] > 0)) return fail(FEM_ERR_ARG, "box half extents must be > 0");
-  }
-  return FEM_OK;
-}
 
 int fem_set_indenter(fem_mesh* m, int shape, const double pose[12], const double* params, const double dir[3],
                      const double* depth_schedule, int32_t n_steps) {
@@ -990,241 +979,6 @@ int fem_solve(fem_mesh* m, int32_t load_steps, double tol, const fem_options* op
     default: code = fail(FEM_ERR_NOT_CONVERGED, "step %d did not converge in max_newton iterations", hst.steps_done + 1);
   }
   if (stats) stats->status = code;
-  return code;
-}
-
-int fem_solve_batch(fem_mesh* const* meshes, const fem_indenter* ind, int32_t n, double tol,
-                    const fem_options* opt, double* const* out_disp, double* const* out_contact_force,
-                    fem_stats* stats) {
-  g_err.clear();
-  if (!meshes || !ind || !out_disp || n < 1) return fail(FEM_ERR_ARG, "meshes, indenters, out_disp and n >= 1 required");
-  if (!(tol > 0) || !std::isfinite(tol)) return fail(FEM_ERR_ARG, "tol must be > 0");
-  fem_options o;
-  fem_default_options(&o);
-  if (opt) o = *opt;
-  const bool clusters = o.batch_engine == FEM_BATCH_CLUSTERS;
-  if (!(o.c_kappa > 0) || o.max_newton < 0 || o.max_cg < 1 || o.max_backtracks < 0 || !(o.cg_rtol_max > 0) ||
-      !(o.cg_rtol_min > 0) || o.cg_rtol_min > o.cg_rtol_max || o.tangent < 0 || o.tangent > 3 ||
-      !(o.barrier_timeout_s > 0) || o.batch_engine < FEM_BATCH_AUTO || o.batch_engine > FEM_BATCH_CLUSTERS ||
-      o.batch_parts < 0 || o.batch_parts > 256 ||
-      (clusters && !(o.batch_parts == 0 || o.batch_parts == 1 || o.batch_parts == 2 || o.batch_parts == 4 ||
-                     o.batch_parts == 8 || o.batch_parts == 16)))
-    return fail(FEM_ERR_ARG, "invalid fem_options");
-  int64_t max_tets = 0;
-  for (int i = 0; i < n; ++i) {
-    if (!meshes[i] || !out_disp[i]) return fail(FEM_ERR_ARG, "solve %d: NULL mesh or output", i);
-    const fem_indenter& d = ind[i];
-    int rc = validate_indenter(d.shape, d.pose, d.params, d.dir, d.depth_schedule, d.n_steps);
-    if (rc) return fail(rc, "solve %d: %s", i, g_err.c_str());
-    max_tets = std::max(max_tets, meshes[i]->n_tets);
-  }
-  int n_sm = 1;
-  CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, meshes[0]->device), "sm count");
-  // CTAs per solve, from the largest mesh only (not from the number of jobs,
-  // so that a job gets the same partition alone and in any batch of meshes no
-  // larger than its own). Groups: about 1,000 tets per CTA with the SMs shared
-  // evenly between the groups. Clusters: about 2,500 tets per CTA, a power of
-  // two up to 16.
-  int parts = o.batch_parts;
-  if (parts == 0) {
-    if (clusters) {
-      parts = 1;
-      while (parts < 16 && max_tets > (int64_t)2500 * parts) parts *= 2;
-    } else {
-      int64_t g = (int64_t)std::llround((double)n_sm * 1000.0 / (double)std::max<int64_t>(max_tets, 1));
-      g = std::max<int64_t>(1, std::min<int64_t>(g, n_sm));
-      parts = (int)(n_sm / g);
-    }
-  }
-  const cudaStream_t s = meshes[0]->stream;
-  std::vector<fem_mesh*> uniq;
-  for (int i = 0; i < n; ++i)
-    if (std::find(uniq.begin(), uniq.end(), meshes[i]) == uniq.end()) uniq.push_back(meshes[i]);
-  PartDims dims{0, 0, 0, 0};
-  size_t max_nodes = 0, max_pt = 0;
-  for (fem_mesh* m : uniq) {
-    if (m->device != meshes[0]->device) return fail(FEM_ERR_ARG, "all meshes must be on one device");
-    if (m->n_nodes < parts) return fail(FEM_ERR_ARG, "a mesh of %lld nodes cannot be cut into %d parts",
-                                        (long long)m->n_nodes, parts);
-    int rc = ensure_batch_partition(m, parts);
-    if (rc) return rc;
-    dims.max_own = std::max(dims.max_own, m->cdims.max_own);
-    dims.max_loc = std::max(dims.max_loc, m->cdims.max_loc);
-    dims.max_pt = std::max(dims.max_pt, m->cdims.max_pt);
-    dims.max_lcsr = std::max(dims.max_lcsr, m->cdims.max_lcsr);
-    max_nodes = std::max(max_nodes, (size_t)m->n_nodes);
-    max_pt = std::max(max_pt, (size_t)m->cdev.total_pt);
-  }
-  int static_smem = 0;
-  if (clusters) CUDA_TRY(cluster_kernel_attrs(parts, 0, &static_smem, nullptr), "cluster kernel attributes");
-  else CUDA_TRY(group_kernel_attrs(0, &static_smem, nullptr), "group kernel attributes");
-  const SmemLayout L = plan_layout(dims, smem_budget(meshes[0], static_smem));
-  if (L.total < 0)
-    return fail(FEM_ERR_TOO_LARGE, "a part of %d owned / %d local nodes does not fit one CTA (%d parts)",
-                dims.max_own, dims.max_loc, parts);
-  int max_slots = 0;
-  if (clusters) {
-    CUDA_TRY(cluster_kernel_attrs(parts, L.total, nullptr, &max_slots), "cluster occupancy");
-  } else {
-    int per_sm = 0;
-    CUDA_TRY(group_kernel_attrs(L.total, nullptr, &per_sm), "group occupancy");
-    max_slots = per_sm * n_sm / parts;
-  }
-  if (max_slots < 1) return fail(FEM_ERR_TOO_LARGE, "no slot of %d CTAs fits the device", parts);
-  const int n_slots = std::min(n, max_slots);
-  if (getenv("FEM_VERBOSE"))
-    fprintf(stderr,
-            "fem_solve_batch: %s of %d CTAs, %d slots (max %d); part dims own %d loc %d pt %d lcsr %d; shared %d B, "
-            "global %d B per CTA; chunk %d; resident tan %d ids %d lists %d; ut %s\n",
-            clusters ? "clusters" : "groups", parts, n_slots, max_slots, dims.max_own, dims.max_loc, dims.max_pt,
-            dims.max_lcsr, L.total, L.gbytes, L.chunk_tets, L.tan >= 0, L.ptn >= 0, L.lcsr >= 0,
-            (L.ut & kInGlobal) ? "global" : "shared");
-  // workspace: per job outputs and schedule, the job table, the queue, then
-  // one scratch block per slot
-  auto a256 = [](size_t b) { return (b + 255) / 256 * 256; };
-  std::vector<size_t> off(n + 1, 0);
-  for (int i = 0; i < n; ++i) {
-    const size_t Nn = (size_t)meshes[i]->n_nodes, K = (size_t)ind[i].n_steps;
-    off[i + 1] = off[i] + 2 * a256(24 * Nn) + a256(24 * K) + a256(sizeof(StatsDev)) + a256(8 * K);
-  }
-  const size_t jobs_off = off[n], queue_off = jobs_off + a256(sizeof(BatchJob) * n);
-  SlotScratch S{};
-  {
-    long long o2 = 0;
-    auto take = [&](size_t bytes) { const long long at = o2; o2 += (long long)a256(bytes); return at; };
-    S.ctrl = take(3 * sizeof(unsigned long long));
-    S.cgslot = take(sizeof(unsigned long long) * (12 * (size_t)parts + 2));
-    S.vpub = clusters ? 0 : take(48 * max_nodes);
-    const long long zero_end = o2;   // ctrl, counters and published words start at zero
-    S.partials = clusters ? 0 : take(16 * (size_t)parts * kRed);
-    S.dpub = take(16 * max_nodes);
-    S.R = take(24 * max_nodes);
-    S.uprev = take(24 * max_nodes);
-    S.tangent = take(L.tan >= 0 ? 16 : 16 * (size_t)kTanVec * max_pt);
-    S.cta = take((size_t)L.gbytes * parts);
-    S.cta_stride = L.gbytes;
-    S.stride = o2;
-    S.base = nullptr;
-    (void)zero_end;
-  }
-  const size_t slots_off = queue_off + 256;
-  const size_t total = slots_off + (size_t)S.stride * n_slots;
-  unsigned char* ws = nullptr;
-  {
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), total, s);
-    if (e != cudaSuccess) return cuda_fail(e, "batch workspace");
-  }
-  S.base = ws + slots_off;
-  auto release = [&]() { cudaFreeAsync(ws, s); cudaStreamSynchronize(s); };
-  std::vector<BatchJob> jobs(n);
-  std::vector<double*> stage(n);
-  {
-    StatsDev st0;
-    memset(&st0, 0, sizeof(st0));
-    st0.status = ST_TIMEOUT;   // overwritten by the solve when it ends
-    for (int k = 0; k < PH_N; ++k) st0.cycles_min[k] = LLONG_MAX;
-    cudaError_t e = cudaMemsetAsync(ws, 0, total, s);
-    for (int i = 0; i < n && e == cudaSuccess; ++i) {
-      fem_mesh* m = meshes[i];
-      const size_t Nn = (size_t)m->n_nodes, K = (size_t)ind[i].n_steps;
-      unsigned char* b = ws + off[i];
-      auto take = [&](size_t bytes) { unsigned char* at = b; b += a256(bytes); return at; };
-      BatchJob& J = jobs[i];
-      J.mesh = m->cdev;
-      J.u = reinterpret_cast<double*>(take(24 * Nn));
-      J.out_fc = reinterpret_cast<double*>(take(24 * Nn));
-      J.step_force = reinterpret_cast<double*>(take(24 * K));
-      J.stats = reinterpret_cast<StatsDev*>(take(sizeof(StatsDev)));
-      double* depths = reinterpret_cast<double*>(take(8 * K));
-      stage[i] = J.out_fc;   // the displacement is unpermuted through this array after the solve
-      SolveParams& P = J.prm;
-      memset(&P, 0, sizeof(P));
-      P.mode = MODE_SOLVE;
-      P.n_steps = ind[i].n_steps;
-      P.tangent_mode = o.tangent;
-      P.max_newton = o.max_newton;
-      P.max_cg = o.max_cg;
-      P.max_backtracks = o.max_backtracks;
-      P.tol = tol;
-      P.c_kappa = o.c_kappa;
-      P.cg_rtol_max = o.cg_rtol_max;
-      P.cg_rtol_min = o.cg_rtol_min;
-      P.timeout_ns = (unsigned long long)(o.barrier_timeout_s * 1e9);
-      P.shape = ind[i].shape;
-      for (int k = 0; k < 3; ++k) {
-        P.origin[k] = ind[i].pose[k];
-        P.dir[k] = ind[i].dir[k];
-        P.iparams[k] = ind[i].shape == FEM_PLANE ? 0.0 : ind[i].params[k];
-      }
-      for (int k = 0; k < 9; ++k) P.R[k] = ind[i].pose[3 + k];
-      P.depths = depths;
-      e = cudaMemcpyAsync(depths, ind[i].depth_schedule, 8 * K, cudaMemcpyDefault, s);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(J.stats, &st0, sizeof(StatsDev), cudaMemcpyHostToDevice, s);
-    }
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(ws + jobs_off, jobs.data(), sizeof(BatchJob) * n, cudaMemcpyHostToDevice, s);
-    // the host copies above are staged from pageable memory that lives until
-    // this function returns; wait before the launch so the launch's own
-    // timing covers the kernel alone
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) { release(); return cuda_fail(e, "batch set-up"); }
-  }
-  float ms = 0.f;
-  cudaError_t e;
-  if (clusters)
-    e = launch_cluster(reinterpret_cast<const BatchJob*>(ws + jobs_off), n, reinterpret_cast<int*>(ws + queue_off), S,
-                       L, parts, n_slots, s, &ms);
-  else
-    e = launch_groups(reinterpret_cast<const BatchJob*>(ws + jobs_off), n, reinterpret_cast<int*>(ws + queue_off), S,
-                      L, parts, n_slots, (unsigned long long)(o.barrier_timeout_s * 1e9), s, &ms);
-  if (e != cudaSuccess) { release(); return cuda_fail(e, "batch kernel"); }
-  std::vector<StatsDev> hst(n);
-  for (int i = 0; i < n && e == cudaSuccess; ++i) {
-    fem_mesh* m = meshes[i];
-    const BatchJob& J = jobs[i];
-    e = launch_permute(J.u, stage[i], m->d_perm, (int)m->n_nodes, true, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(out_disp[i], stage[i], 24 * (size_t)m->n_nodes, cudaMemcpyDefault, s);
-    if (e == cudaSuccess && out_contact_force && out_contact_force[i])
-      e = cudaMemcpyAsync(out_contact_force[i], J.step_force, 24 * (size_t)J.prm.n_steps, cudaMemcpyDefault, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&hst[i], J.stats, sizeof(StatsDev), cudaMemcpyDeviceToHost, s);
-  }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  release();
-  if (e != cudaSuccess) return cuda_fail(e, "batch outputs");
-  int code = FEM_OK;
-  for (int i = 0; i < n; ++i) {
-    int c = FEM_OK;
-    if (hst[i].status == ST_NONFINITE) c = FEM_ERR_NONFINITE;
-    else if (hst[i].status == ST_TIMEOUT) c = FEM_ERR_TIMEOUT;
-    else if (hst[i].status != ST_OK) c = FEM_ERR_NOT_CONVERGED;
-    if (c != FEM_OK && code == FEM_OK) {
-      code = c;
-      fail(c, "solve %d stopped at step %d (status %d)", i, hst[i].steps_done + 1, hst[i].status);
-    }
-    if (stats) {
-      fem_stats& st = stats[i];
-      memset(&st, 0, sizeof(st));
-      st.status = c;
-      st.steps_done = hst[i].steps_done;
-      st.newton_iters = hst[i].newton_total;
-      st.cg_iters = hst[i].cg_total;
-      st.backtracks = hst[i].backtracks_total;
-      st.active_contacts = hst[i].active;
-      st.residual = hst[i].residual;
-      st.scale = hst[i].scale;
-      st.energy = hst[i].energy;
-      st.kernel_ms = ms;
-      st.exact_newton_iters = hst[i].exact_newton;
-      // per-solve phase split: shares of this solve's own clock (part 0)
-      const double tot = (double)hst[i].cycles[PH_TOTAL];
-      for (int k = 0; k < PH_N && k < 10; ++k) st.phase_ms[k] = tot > 0 ? (double)hst[i].cycles[k] / tot : 0.0;
-      for (int k = 0; k < ind[i].n_steps; ++k) {
-        st.newton_per_step[k] = hst[i].newton_per_step[k];
-        st.cg_per_step[k] = hst[i].cg_per_step[k];
-        st.residual_per_step[k] = hst[i].residual_per_step[k];
-      }
-    }
-  }
   return code;
 }
 

@@ -1,0 +1,429 @@
+// Batched indentation solves behind the C ABI (include/fem.h): the reusable
+// plan (fem_batch_create / fem_batch_run) and the one-shot fem_solve_batch.
+//
+// A plan fixes the meshes, the load-step counts and the engine; it builds the
+// per-mesh partitions, plans the per-CTA shared-memory layout, allocates one
+// device workspace and captures the whole batch into a CUDA graph: reset of
+// the workspace, upload of the job table and schedules from pinned staging,
+// the persistent launch (CTA groups or thread-block clusters), and the
+// reordering of the displacements into the caller's node numbering. A run
+// writes the indenters into the pinned staging and replays the graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "fem_host.h"
+
+using namespace fem;
+using namespace fem::host;
+
+struct fem_batch {
+  int device = 0;
+  cudaStream_t s = nullptr;         // the plan's own stream (capture needs a non-legacy stream)
+  cudaStream_t caller = nullptr;    // meshes[0]'s stream: runs are ordered after its prior work
+  int n = 0;
+  fem_options o{};
+  bool clusters = false;
+  int parts = 0, n_slots = 0;
+  SmemLayout L{};
+  SlotScratch S{};
+  std::vector<fem_mesh*> meshes;
+  std::vector<int> n_steps;
+  unsigned char* ws = nullptr;      // device workspace
+  size_t total = 0;
+  size_t jobs_off = 0, queue_off = 0, stats_off = 0, depths_off = 0, slots_off = 0;
+  std::vector<size_t> depth_at;     // first depth of job i
+  std::vector<BatchJob> jobs;       // device pointers fixed at creation
+  std::vector<double*> stage;       // per job: displacement in caller order (device)
+  BatchJob* h_jobs = nullptr;       // pinned staging of the job table
+  double* h_depths = nullptr;       // pinned staging of the schedules
+  StatsDev* h_stats0 = nullptr;     // pinned: statistics at the start of a run
+  StatsDev* h_stats = nullptr;      // pinned: statistics after a run
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ready = nullptr;
+};
+
+namespace {
+
+auto a256 = [](size_t b) { return (b + 255) / 256 * 256; };
+
+int check_options(const fem_options& o) {
+  const bool clusters = o.batch_engine == FEM_BATCH_CLUSTERS;
+  if (!(o.c_kappa > 0) || o.max_newton < 0 || o.max_cg < 1 || o.max_backtracks < 0 || !(o.cg_rtol_max > 0) ||
+      !(o.cg_rtol_min > 0) || o.cg_rtol_min > o.cg_rtol_max || o.tangent < 0 || o.tangent > 3 ||
+      !(o.barrier_timeout_s > 0) || o.batch_engine < FEM_BATCH_AUTO || o.batch_engine > FEM_BATCH_CLUSTERS ||
+      o.batch_parts < 0 || o.batch_parts > 256 ||
+      (clusters && !(o.batch_parts == 0 || o.batch_parts == 1 || o.batch_parts == 2 || o.batch_parts == 4 ||
+                     o.batch_parts == 8 || o.batch_parts == 16)))
+    return fail(FEM_ERR_ARG, "invalid fem_options");
+  return FEM_OK;
+}
+
+void release(fem_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->ws) cudaFree(b->ws);
+  if (b->h_jobs) cudaFreeHost(b->h_jobs);
+  if (b->h_depths) cudaFreeHost(b->h_depths);
+  if (b->h_stats0) cudaFreeHost(b->h_stats0);
+  if (b->h_stats) cudaFreeHost(b->h_stats);
+  if (b->ev0) cudaEventDestroy(b->ev0);
+  if (b->ev1) cudaEventDestroy(b->ev1);
+  if (b->ready) cudaEventDestroy(b->ready);
+  if (b->s) cudaStreamDestroy(b->s);
+  delete b;
+}
+
+// The captured sequence (also used directly if capture is unavailable).
+cudaError_t enqueue(fem_batch* b) {
+  cudaStream_t s = b->s;
+  const int n = b->n;
+  cudaError_t e = cudaMemsetAsync(b->ws, 0, b->total, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->ws + b->depths_off, b->h_depths, sizeof(double) * b->depth_at[n], cudaMemcpyHostToDevice,
+                        s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->ws + b->stats_off, b->h_stats0, sizeof(StatsDev) * n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->ws + b->jobs_off, b->h_jobs, sizeof(BatchJob) * n, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  const BatchJob* d_jobs = reinterpret_cast<const BatchJob*>(b->ws + b->jobs_off);
+  int* d_queue = reinterpret_cast<int*>(b->ws + b->queue_off);
+  if (b->clusters)
+    e = launch_cluster(d_jobs, n, d_queue, b->S, b->L, b->parts, b->n_slots, s, nullptr);
+  else
+    e = launch_groups(d_jobs, n, d_queue, b->S, b->L, b->parts, b->n_slots,
+                      (unsigned long long)(b->o.barrier_timeout_s * 1e9), s, nullptr);
+  for (int i = 0; i < n && e == cudaSuccess; ++i)
+    e = launch_permute(b->jobs[i].u, b->stage[i], b->meshes[i]->d_perm, (int)b->meshes[i]->n_nodes, true, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->h_stats, b->ws + b->stats_off, sizeof(StatsDev) * n, cudaMemcpyDeviceToHost, s);
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fem_batch_create(fem_mesh* const* meshes, const int32_t* n_steps, int32_t n, const fem_options* opt,
+                     fem_batch** out) {
+  last_error().clear();
+  if (!meshes || !n_steps || !out || n < 1) return fail(FEM_ERR_ARG, "meshes, n_steps, out and n >= 1 required");
+  *out = nullptr;
+  fem_options o;
+  fem_default_options(&o);
+  if (opt) o = *opt;
+  int rc = check_options(o);
+  if (rc) return rc;
+  int64_t max_tets = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!meshes[i]) return fail(FEM_ERR_ARG, "solve %d: NULL mesh", i);
+    if (n_steps[i] < 1 || n_steps[i] > FEM_MAX_STEPS) return fail(FEM_ERR_ARG, "solve %d: n_steps out of range", i);
+    if (meshes[i]->device != meshes[0]->device) return fail(FEM_ERR_ARG, "all meshes must be on one device");
+    max_tets = std::max(max_tets, meshes[i]->n_tets);
+  }
+  const bool clusters = o.batch_engine == FEM_BATCH_CLUSTERS;
+  int n_sm = 1;
+  CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, meshes[0]->device), "sm count");
+  // CTAs per solve, from the largest mesh only (not from the number of jobs,
+  // so that a job gets the same partition alone and in any batch of meshes no
+  // larger than its own). Groups: about 1,000 tets per CTA with the SMs shared
+  // evenly between the groups. Clusters: about 2,500 tets per CTA, a power of
+  // two up to 16.
+  int parts = o.batch_parts;
+  if (parts == 0) {
+    if (clusters) {
+      parts = 1;
+      while (parts < 16 && max_tets > (int64_t)2500 * parts) parts *= 2;
+    } else {
+      int64_t g = (int64_t)std::llround((double)n_sm * 1000.0 / (double)std::max<int64_t>(max_tets, 1));
+      g = std::max<int64_t>(1, std::min<int64_t>(g, n_sm));
+      parts = (int)(n_sm / g);
+    }
+  }
+  std::vector<fem_mesh*> uniq;
+  for (int i = 0; i < n; ++i)
+    if (std::find(uniq.begin(), uniq.end(), meshes[i]) == uniq.end()) uniq.push_back(meshes[i]);
+  PartDims dims{0, 0, 0, 0};
+  size_t max_nodes = 0, max_pt = 0;
+  for (fem_mesh* m : uniq) {
+    if (m->n_nodes < parts)
+      return fail(FEM_ERR_ARG, "a mesh of %lld nodes cannot be cut into %d parts", (long long)m->n_nodes, parts);
+    rc = ensure_batch_partition(m, parts);
+    if (rc) return rc;
+    dims.max_own = std::max(dims.max_own, m->cdims.max_own);
+    dims.max_loc = std::max(dims.max_loc, m->cdims.max_loc);
+    dims.max_pt = std::max(dims.max_pt, m->cdims.max_pt);
+    dims.max_lcsr = std::max(dims.max_lcsr, m->cdims.max_lcsr);
+    max_nodes = std::max(max_nodes, (size_t)m->n_nodes);
+    max_pt = std::max(max_pt, (size_t)m->cdev.total_pt);
+  }
+  int static_smem = 0;
+  if (clusters) CUDA_TRY(cluster_kernel_attrs(parts, 0, &static_smem, nullptr), "cluster kernel attributes");
+  else CUDA_TRY(group_kernel_attrs(0, &static_smem, nullptr), "group kernel attributes");
+  const SmemLayout L = plan_layout(dims, smem_budget(meshes[0], static_smem));
+  if (L.total < 0)
+    return fail(FEM_ERR_TOO_LARGE, "a part of %d owned / %d local nodes does not fit one CTA (%d parts)",
+                dims.max_own, dims.max_loc, parts);
+  int max_slots = 0;
+  if (clusters) {
+    CUDA_TRY(cluster_kernel_attrs(parts, L.total, nullptr, &max_slots), "cluster occupancy");
+  } else {
+    int per_sm = 0;
+    CUDA_TRY(group_kernel_attrs(L.total, nullptr, &per_sm), "group occupancy");
+    max_slots = per_sm * n_sm / parts;
+  }
+  if (max_slots < 1) return fail(FEM_ERR_TOO_LARGE, "no slot of %d CTAs fits the device", parts);
+
+  fem_batch* b = new fem_batch();
+  b->device = meshes[0]->device;
+  b->caller = meshes[0]->stream;
+  b->n = n;
+  b->o = o;
+  b->clusters = clusters;
+  b->parts = parts;
+  b->n_slots = std::min(n, max_slots);
+  b->L = L;
+  b->meshes.assign(meshes, meshes + n);
+  b->n_steps.assign(n_steps, n_steps + n);
+  auto bail = [&](int code) { release(b); return code; };
+  auto cu = [&](cudaError_t e, const char* what) { return e == cudaSuccess ? FEM_OK : bail(cuda_fail(e, what)); };
+  if ((rc = cu(cudaStreamCreateWithFlags(&b->s, cudaStreamNonBlocking), "stream"))) return rc;
+  if ((rc = cu(cudaEventCreate(&b->ev0), "event"))) return rc;
+  if ((rc = cu(cudaEventCreate(&b->ev1), "event"))) return rc;
+  if ((rc = cu(cudaEventCreateWithFlags(&b->ready, cudaEventDisableTiming), "event"))) return rc;
+  // workspace: per job u, contact force, caller-order staging, step forces;
+  // statistics; schedules; job table; queue; one scratch block per slot
+  std::vector<size_t> off(n + 1, 0);
+  b->depth_at.assign(n + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    const size_t Nn = (size_t)meshes[i]->n_nodes, K = (size_t)n_steps[i];
+    off[i + 1] = off[i] + 3 * a256(24 * Nn) + a256(24 * K);
+    b->depth_at[i + 1] = b->depth_at[i] + K;
+  }
+  b->stats_off = off[n];
+  b->depths_off = b->stats_off + a256(sizeof(StatsDev) * n);
+  b->jobs_off = b->depths_off + a256(sizeof(double) * b->depth_at[n]);
+  b->queue_off = b->jobs_off + a256(sizeof(BatchJob) * n);
+  b->slots_off = b->queue_off + 256;
+  SlotScratch& S = b->S;
+  {
+    long long o2 = 0;
+    auto take = [&](size_t bytes) { const long long at = o2; o2 += (long long)a256(bytes); return at; };
+    S.ctrl = take(3 * sizeof(unsigned long long));
+    S.cgslot = take(sizeof(unsigned long long) * (12 * (size_t)parts + 2));
+    S.vpub = clusters ? 0 : take(48 * max_nodes);
+    S.partials = clusters ? 0 : take(16 * (size_t)parts * kRed);
+    S.dpub = take(16 * max_nodes);
+    S.R = take(24 * max_nodes);
+    S.uprev = take(24 * max_nodes);
+    S.tangent = take(L.tan >= 0 ? 16 : 16 * (size_t)kTanVec * max_pt);
+    S.cta = take((size_t)L.gbytes * parts);
+    S.cta_stride = L.gbytes;
+    S.stride = o2;
+  }
+  b->total = b->slots_off + (size_t)S.stride * b->n_slots;
+  if ((rc = cu(cudaSetDevice(b->device), "device"))) return rc;
+  if ((rc = cu(cudaMalloc(reinterpret_cast<void**>(&b->ws), b->total), "batch workspace"))) return rc;
+  S.base = b->ws + b->slots_off;
+  if ((rc = cu(cudaMallocHost(reinterpret_cast<void**>(&b->h_jobs), sizeof(BatchJob) * n), "pinned"))) return rc;
+  if ((rc = cu(cudaMallocHost(reinterpret_cast<void**>(&b->h_depths), sizeof(double) * b->depth_at[n]), "pinned")))
+    return rc;
+  if ((rc = cu(cudaMallocHost(reinterpret_cast<void**>(&b->h_stats0), sizeof(StatsDev) * n), "pinned"))) return rc;
+  if ((rc = cu(cudaMallocHost(reinterpret_cast<void**>(&b->h_stats), sizeof(StatsDev) * n), "pinned"))) return rc;
+  StatsDev st0;
+  memset(&st0, 0, sizeof(st0));
+  st0.status = ST_TIMEOUT;   // overwritten by the solve when it ends
+  for (int k = 0; k < PH_N; ++k) st0.cycles_min[k] = LLONG_MAX;
+  b->jobs.resize(n);
+  b->stage.resize(n);
+  for (int i = 0; i < n; ++i) {
+    fem_mesh* m = meshes[i];
+    const size_t Nn = (size_t)m->n_nodes, K = (size_t)n_steps[i];
+    unsigned char* p = b->ws + off[i];
+    auto take = [&](size_t bytes) { unsigned char* at = p; p += a256(bytes); return at; };
+    BatchJob& J = b->jobs[i];
+    memset(&J, 0, sizeof(J));
+    J.mesh = m->cdev;
+    J.u = reinterpret_cast<double*>(take(24 * Nn));
+    J.out_fc = reinterpret_cast<double*>(take(24 * Nn));
+    b->stage[i] = reinterpret_cast<double*>(take(24 * Nn));
+    J.step_force = reinterpret_cast<double*>(take(24 * K));
+    J.stats = reinterpret_cast<StatsDev*>(b->ws + b->stats_off) + i;
+    SolveParams& P = J.prm;
+    P.mode = MODE_SOLVE;
+    P.n_steps = (int)K;
+    P.tangent_mode = o.tangent;
+    P.max_newton = o.max_newton;
+    P.max_cg = o.max_cg;
+    P.max_backtracks = o.max_backtracks;
+    P.c_kappa = o.c_kappa;
+    P.cg_rtol_max = o.cg_rtol_max;
+    P.cg_rtol_min = o.cg_rtol_min;
+    P.timeout_ns = (unsigned long long)(o.barrier_timeout_s * 1e9);
+    P.depths = reinterpret_cast<const double*>(b->ws + b->depths_off) + b->depth_at[i];
+    b->h_stats0[i] = st0;
+  }
+  memcpy(b->h_jobs, b->jobs.data(), sizeof(BatchJob) * n);
+  // capture the sequence once; replay it on every run
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->s, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t e2 = enqueue(b);
+    e = cudaStreamEndCapture(b->s, &graph);
+    if (e2 != cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    cudaGetLastError();   // clear the capture error; runs enqueue directly
+    b->exec = nullptr;
+  }
+  *out = b;
+  return FEM_OK;
+}
+
+int fem_batch_run(fem_batch* b, const fem_indenter* ind, double tol, double* const* out_disp,
+                  double* const* out_contact_force, fem_stats* stats) {
+  last_error().clear();
+  if (!b || !ind || !out_disp) return fail(FEM_ERR_ARG, "batch, indenters and out_disp required");
+  if (!(tol > 0) || !std::isfinite(tol)) return fail(FEM_ERR_ARG, "tol must be > 0");
+  const int n = b->n;
+  for (int i = 0; i < n; ++i) {
+    const fem_indenter& d = ind[i];
+    if (!out_disp[i]) return fail(FEM_ERR_ARG, "solve %d: NULL output", i);
+    int rc = validate_indenter(d.shape, d.pose, d.params, d.dir, d.depth_schedule, d.n_steps);
+    if (rc) return fail(rc, "solve %d: %s", i, last_error().c_str());
+    if (d.n_steps != b->n_steps[i])
+      return fail(FEM_ERR_ARG, "solve %d: %d load steps, the plan has %d", i, d.n_steps, b->n_steps[i]);
+  }
+  CUDA_TRY(cudaSetDevice(b->device), "device");
+  // the previous run has finished reading the staging (every run synchronises)
+  for (int i = 0; i < n; ++i) {
+    const fem_indenter& d = ind[i];
+    SolveParams& P = b->h_jobs[i].prm;
+    P.tol = tol;
+    P.shape = d.shape;
+    for (int k = 0; k < 3; ++k) {
+      P.origin[k] = d.pose[k];
+      P.dir[k] = d.dir[k];
+      P.iparams[k] = d.shape == FEM_PLANE ? 0.0 : d.params[k];
+    }
+    for (int k = 0; k < 9; ++k) P.R[k] = d.pose[3 + k];
+    CUDA_TRY(cudaMemcpy(b->h_depths + b->depth_at[i], d.depth_schedule, sizeof(double) * d.n_steps,
+                        cudaMemcpyDefault), "schedule copy");
+  }
+  cudaStream_t s = b->s;
+  CUDA_TRY(cudaEventRecord(b->ready, b->caller), "order after the caller's stream");
+  CUDA_TRY(cudaStreamWaitEvent(s, b->ready, 0), "order after the caller's stream");
+  CUDA_TRY(cudaEventRecord(b->ev0, s), "event");
+  if (b->exec) CUDA_TRY(cudaGraphLaunch(b->exec, s), "batch graph");
+  else CUDA_TRY(enqueue(b), "batch launch");
+  CUDA_TRY(cudaEventRecord(b->ev1, s), "event");
+  for (int i = 0; i < n; ++i) {
+    const fem_mesh* m = b->meshes[i];
+    CUDA_TRY(cudaMemcpyAsync(out_disp[i], b->stage[i], 24 * (size_t)m->n_nodes, cudaMemcpyDefault, s), "output");
+    if (out_contact_force && out_contact_force[i])
+      CUDA_TRY(cudaMemcpyAsync(out_contact_force[i], b->jobs[i].step_force, 24 * (size_t)b->n_steps[i],
+                               cudaMemcpyDefault, s), "output");
+  }
+  CUDA_TRY(cudaStreamSynchronize(s), "batch");
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, b->ev0, b->ev1);
+  int code = FEM_OK;
+  for (int i = 0; i < n; ++i) {
+    const StatsDev& h = b->h_stats[i];
+    int c = FEM_OK;
+    if (h.status == ST_NONFINITE) c = FEM_ERR_NONFINITE;
+    else if (h.status == ST_TIMEOUT) c = FEM_ERR_TIMEOUT;
+    else if (h.status != ST_OK) c = FEM_ERR_NOT_CONVERGED;
+    if (c != FEM_OK && code == FEM_OK) {
+      code = c;
+      fail(c, "solve %d stopped at step %d (status %d)", i, h.steps_done + 1, h.status);
+    }
+    if (stats) {
+      fem_stats& st = stats[i];
+      memset(&st, 0, sizeof(st));
+      st.status = c;
+      st.steps_done = h.steps_done;
+      st.newton_iters = h.newton_total;
+      st.cg_iters = h.cg_total;
+      st.backtracks = h.backtracks_total;
+      st.active_contacts = h.active;
+      st.residual = h.residual;
+      st.scale = h.scale;
+      st.energy = h.energy;
+      st.kernel_ms = ms;
+      st.exact_newton_iters = h.exact_newton;
+      // per-solve phase split: shares of this solve's own clock (part 0)
+      const double tot = (double)h.cycles[PH_TOTAL];
+      for (int k = 0; k < PH_N && k < 10; ++k) st.phase_ms[k] = tot > 0 ? (double)h.cycles[k] / tot : 0.0;
+      for (int k = 0; k < b->n_steps[i]; ++k) {
+        st.newton_per_step[k] = h.newton_per_step[k];
+        st.cg_per_step[k] = h.cg_per_step[k];
+        st.residual_per_step[k] = h.residual_per_step[k];
+      }
+    }
+  }
+  return code;
+}
+
+void fem_batch_destroy(fem_batch* b) {
+  if (b) cudaStreamSynchronize(b->s);
+  release(b);
+}
+
+int fem_batch_info_get(const fem_batch* b, fem_batch_info* info) {
+  if (!b || !info) return fail(FEM_ERR_ARG, "NULL argument");
+  info->engine = b->clusters ? FEM_BATCH_CLUSTERS : FEM_BATCH_GROUPS;
+  info->parts = b->parts;
+  info->slots = b->n_slots;
+  info->graph = b->exec ? 1 : 0;
+  info->smem_bytes = b->L.total;
+  info->global_bytes_per_cta = b->L.gbytes;
+  info->resident_tangent = b->L.tan >= 0 ? 1 : 0;
+  info->workspace_bytes = (int64_t)b->total;
+  return FEM_OK;
+}
+
+int fem_solve_batch(fem_mesh* const* meshes, const fem_indenter* ind, int32_t n, double tol,
+                    const fem_options* opt, double* const* out_disp, double* const* out_contact_force,
+                    fem_stats* stats) {
+  last_error().clear();
+  if (!meshes || !ind || !out_disp || n < 1) return fail(FEM_ERR_ARG, "meshes, indenters, out_disp and n >= 1 required");
+  if (!(tol > 0) || !std::isfinite(tol)) return fail(FEM_ERR_ARG, "tol must be > 0");
+  fem_options o;
+  fem_default_options(&o);
+  if (opt) o = *opt;
+  int rc = check_options(o);
+  if (rc) return rc;
+  std::vector<int32_t> steps(n);
+  for (int i = 0; i < n; ++i) {
+    if (!meshes[i] || !out_disp[i]) return fail(FEM_ERR_ARG, "solve %d: NULL mesh or output", i);
+    const fem_indenter& d = ind[i];
+    rc = validate_indenter(d.shape, d.pose, d.params, d.dir, d.depth_schedule, d.n_steps);
+    if (rc) return fail(rc, "solve %d: %s", i, last_error().c_str());
+    steps[i] = d.n_steps;
+  }
+  fem_batch* b = nullptr;
+  rc = fem_batch_create(meshes, steps.data(), n, &o, &b);
+  if (rc) return rc;
+  if (getenv("FEM_VERBOSE"))
+    fprintf(stderr, "fem_solve_batch: %s of %d CTAs, %d slots; shared %d B, global %d B per CTA; chunk %d; "
+                    "resident tangent %d ids %d lists %d; graph %d\n",
+            b->clusters ? "clusters" : "groups", b->parts, b->n_slots, b->L.total, b->L.gbytes, b->L.chunk_tets,
+            b->L.tan >= 0, b->L.ptn >= 0, b->L.lcsr >= 0, b->exec ? 1 : 0);
+  rc = fem_batch_run(b, ind, tol, out_disp, out_contact_force, stats);
+  const std::string msg = last_error();
+  fem_batch_destroy(b);
+  if (rc) last_error() = msg;
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,74 @@
+// Host-side internals shared by the C-ABI sources (fem_api.cpp: meshes,
+// single solves; fem_batch.cpp: batched solves, the autotuner and the
+// request server). Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fem.h"
+#include "fem_internal.h"
+
+struct fem_mesh {
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int64_t n_nodes = 0, n_tets = 0, n_fixed = 0;
+  std::vector<int> perm;        // new node -> caller node
+  std::vector<int> fixed_nodes; // caller ids
+  std::vector<unsigned char> fixed_bits;  // per fixed entry
+  std::vector<unsigned char> node_mask;   // per new node
+  // host copies needed to re-partition
+  std::vector<int> tets_new;    // 4 per sorted tet
+  std::vector<double> dminv;    // 9 per sorted tet
+  std::vector<double> vol;
+  std::vector<int> mat;
+  std::vector<int> csr_ptr, csr_ent;   // node -> (tet << 2 | corner), new numbering
+  double h_bar = 0, scale_floor = 0;
+  int64_t n_candidates = 0;
+  fem::MeshDev dev{};                 // partition of the single-solve kernel (one part per CTA)
+  fem::WorkDev work{};
+  fem::SmemLayout layout{};
+  fem::PartDims dims{};
+  std::vector<void*> owned;     // every device allocation of the mesh
+  std::vector<void*> part_owned, cpart_owned;
+  size_t bytes = 0, part_bytes = 0, cpart_bytes = 0;
+  fem::MeshDev cdev{};           // partition for batched solves (built on first batched use)
+  fem::PartDims cdims{};
+  int c_parts = 0;               // parts of cdev (0: not built)
+  // indenter
+  bool has_indenter = false;
+  int shape = 0;
+  double origin[3]{}, R[9]{}, iparams[3]{}, dir[3]{};
+  int n_steps = 0;
+  double* d_depths = nullptr;
+  bool has_presc = false;
+  double* d_presc = nullptr;
+  double* d_stage = nullptr;     // 3*n_nodes staging in caller order
+  int* d_perm = nullptr;         // new -> caller
+};
+
+namespace fem {
+
+cudaError_t launch_permute(const double* src, double* dst, const int* perm, int n, bool to_caller,
+                           cudaStream_t s);
+
+namespace host {
+
+std::string& last_error();                 // this thread's message (fem_last_error)
+int fail(int code, const char* fmt, ...);  // sets the message, returns code
+int cuda_fail(cudaError_t e, const char* what);
+SmemLayout plan_layout(const PartDims& d, int budget);
+int smem_budget(const fem_mesh* m, int static_smem);
+int ensure_batch_partition(fem_mesh* m, int parts);
+int validate_indenter(int shape, const double pose[12], const double* params, const double dir[3],
+                      const double* depth_schedule, int32_t n_steps);
+
+}  // namespace host
+}  // namespace fem
+
+#define CUDA_TRY(call, what)                                            \
+  do {                                                                  \
+    cudaError_t e_ = (call);                                            \
+    if (e_ != cudaSuccess) return fem::host::cuda_fail(e_, what);       \
+  } while (0)

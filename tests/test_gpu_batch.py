@@ -96,3 +96,34 @@ def test_batch_uneven_meshes(F, engine):
         assert rn <= 1e-6 * scale
     for h in handles:
         F.fem_destroy_mesh(h)
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_batch_plan_replays_captured_graph(F, engine):
+    """A plan captures the batch once as a CUDA graph; every run replays it
+    with new indenters and gives bitwise the results of a one-shot batch."""
+    import dataclasses
+    m, _ = W.cube_sphere()
+    h = F.fem_create_mesh(m.nodes, m.tets, m.tet_material, m.materials, m.fixed_nodes)
+    inds_all = []
+    for r, d, dx, dy in ((0.25, 0.04, 0.0, 0.0), (0.3, 0.05, 0.1, -0.05), (0.35, 0.03, -0.1, 0.1),
+                         (0.3, 0.06, 0.05, 0.05)):
+        base = W.cube_sphere_indenter(radius=r, depth=d, n_steps=10)
+        inds_all.append(dataclasses.replace(base, origin=base.origin + np.array([dx, dy, 0.0])))
+    opt = F.fem_default_options()
+    opt.batch_engine, opt.batch_parts = engine
+    plan = F.FemBatch([h] * 4, [10] * 4, opt)
+    info = plan.info()
+    assert info.graph == 1 and info.slots >= 1 and info.parts >= 1
+    for order in ([0, 1, 2, 3], [3, 2, 1, 0]):
+        inds = [inds_all[k] for k in order]
+        out = [np.zeros((m.n_nodes, 3)) for _ in inds]
+        frc = [np.zeros((10, 3)) for _ in inds]
+        rc, st = plan.run(inds, 1e-6, out, frc)
+        assert rc == 0 and all(x.steps_done == 10 for x in st)
+        rc2, ref, ref_f, _ = _batch(F, [m] * 4, [h] * 4, inds, engine=engine)
+        assert rc2 == 0
+        for k in range(4):
+            assert np.array_equal(out[k], ref[k]) and np.array_equal(frc[k], ref_f[k]), (order, k)
+    plan.close()
+    F.fem_destroy_mesh(h)
