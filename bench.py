@@ -1,15 +1,26 @@
 """Benchmark of the quasi-static tet-FEM indentation solve on B300.
 
-One step = one complete indentation solve (all 20 load steps: FP64 residual,
-FP32 projected tangent, pipelined PCG, line search) of the single-fingertip
-sphere workload: a two-layer half-capsule fingertip (R = 7 mm, L = 40 mm,
-38,880 tets / 8,740 nodes) pressed 2 mm by a sphere of radius 4 mm in 20 load
-steps, to a relative residual of 1e-6. The mesh is resident on the device when
-the timed region starts; outputs go to device buffers. The end-to-end figure
-goes through the same public C ABI from host arrays (mesh upload, indenter,
-solve, host outputs, release) every step.
+Default workload (--workload fingertip): one step = one complete indentation
+solve (all 20 load steps: FP64 residual, FP32 tangent, block-Jacobi PCG in
+Chronopoulos-Gear form, line search) of the single-fingertip sphere workload:
+a two-layer half-capsule fingertip (R = 7 mm, L = 40 mm, 38,880 tets / 8,740
+nodes) pressed 2 mm by a sphere of radius 4 mm in 20 load steps, to a
+relative residual of 1e-6. The mesh is resident on the device when the timed
+region starts; outputs go to device buffers. The end-to-end figure goes
+through the same public C ABI from host arrays (mesh upload, indenter, solve,
+host outputs, release) every step.
+
+Batched workloads print their own line:
+  --workload batch   one step = 256 random indentations of that fingertip
+                     (sphere / cylinder / box edge, tilt <= 30 deg, depth
+                     0.5-3 mm) in one replayed CUDA graph of the persistent
+                     batched kernel (fem_batch_run).
+  --workload uneven  one step = 64 fingertips of uneven size (R 5-10 mm,
+                     5k-200k tets log-uniform), one random indentation each,
+                     in one launch; the slot shape comes from fem_batch_tune.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference]
+                    [--workload fingertip|batch|uneven]
 
 Multi-GPU runs (torchrun) are independent replicas: every rank solves its own
 indentation, no collectives on the data path (weak scaling).
@@ -337,6 +348,140 @@ def run_cuda(args, rank, world, local):
         torch.distributed.destroy_process_group()
 
 
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+
+
+def flops_per_solve(n_tets, n_nodes, cg_iters, newton_iters):
+    """FP32 work of the hot path: ~300 flop/tet + ~40 flop/node per PCG
+    iteration, ~600 flop/tet per Newton iteration (tangent build)."""
+    return cg_iters * (300 * n_tets + 40 * n_nodes) + newton_iters * 600 * n_tets
+
+
+def run_batch(args, rank, world, local):
+    """Batched workloads: many independent solves per step in one launch."""
+    import torch
+    import workloads as W
+    import paper_2103_16747_b300 as F
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    opt = F.fem_default_options()
+    opt.max_newton = 200            # deep random draws need more Newton steps in their last load steps
+    if args.workload == "batch":
+        mesh, _ = W.fingertip_sphere()
+        draws = W.draw_indentations(mesh, args.n_solves, seed=1002 + 1000 * rank)
+        meshes = [mesh] * len(draws)
+        workload = (f"batch: {len(draws)} random indentations (sphere r 2-6 / cylinder r 1-4 / 20 mm box edge, "
+                    f"tilt <= 30 deg, depth 0.5-3 mm, 20 load steps) of the fingertip of the single-solve "
+                    f"workload ({mesh.n_tets} tets / {mesh.n_nodes} nodes), one replayed CUDA graph per step")
+    else:
+        jobs = W.uneven_fingertips(args.n_solves, seed=1003 + 1000 * rank)
+        meshes = [m for m, _ in jobs]
+        draws = [d for _, d in jobs]
+        workload = (f"uneven: {len(draws)} fingertips R 5-10 mm, {min(m.n_tets for m in meshes)}-"
+                    f"{max(m.n_tets for m in meshes)} tets (log-uniform 5k-200k, {sum(m.n_tets for m in meshes)} "
+                    f"total), one random indentation each, one launch per step")
+    uniq = {id(m): m for m in meshes}
+    handles = {k: F.fem_create_mesh(m.nodes, m.tets, m.tet_material, m.materials, m.fixed_nodes)
+               for k, m in uniq.items()}
+    hs = [handles[id(m)] for m in meshes]
+    tune = None
+    if args.workload == "uneven":
+        t0 = time.perf_counter()
+        opt, rep = F.fem_batch_tune(hs, draws, TOL, opt, proxy_steps=4)
+        tune = {"seconds": time.perf_counter() - t0,
+                "chosen": {"engine": opt.batch_engine, "parts": opt.batch_parts,
+                           "tets_per_cta": opt.batch_tets_per_cta},
+                "candidates": [{"engine": rep.engine[k], "parts": rep.parts[k], "tets_per_cta": rep.tets_per_cta[k],
+                                "proxy_solves_per_s": rep.rate[k]} for k in range(rep.n_candidates)]}
+    plan = F.FemBatch(hs, [d.n_steps for d in draws], opt)
+    info = plan.info()
+    outs = [torch.zeros((m.n_nodes, 3), dtype=torch.float64, device=dev) for m in meshes]
+    frcs = [torch.zeros((d.n_steps, 3), dtype=torch.float64, device=dev) for d in draws]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(max(args.warmup, 0)):
+        plan.run(draws, TOL, outs, frcs, check=False)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    step_s, stats = [], None
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, stats = plan.run(draws, TOL, outs, frcs, check=False)
+            torch.cuda.synchronize()
+            step_s.append(time.perf_counter() - t0)
+    kernel_ms = stats[0].kernel_ms
+    total = max_over_ranks(sum(step_s), world, dev)
+    n = len(draws)
+    value = world * n * args.steps / total
+    ok = sum(1 for s_ in stats if s_.status == 0)
+    alg = sum(algorithmic_bytes(m.n_tets, m.n_nodes, s_.cg_iters, s_.newton_iters,
+                                s_.newton_iters + s_.backtracks + d.n_steps)
+              for m, s_, d in zip(meshes, stats, draws))
+    flops = sum(flops_per_solve(m.n_tets, m.n_nodes, s_.cg_iters, s_.newton_iters) for m, s_ in zip(meshes, stats))
+    peak, peak_kind = peaks()
+    achieved = alg / (kernel_ms / 1000.0) / 1e9
+    # the plain one-solve-per-launch path (fem_solve, one cooperative launch
+    # per solve) on every draw of the step, kernel time
+    single_s = 0.0
+    for i in range(n):
+        s1 = F.IndentationSolver(meshes[i])
+        s1.set_indenter(draws[i])
+        r = s1.solve(TOL, opt, check=False)
+        single_s += r["stats"].kernel_ms / 1000.0
+        s1.close()
+    # end to end: public one-shot call from host arrays (meshes uploaded every step)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()   # noqa: E731
+    h_out = [torch.zeros((m.n_nodes, 3), dtype=torch.float64).pin_memory() for m in meshes]
+    h_frc = [torch.zeros((d.n_steps, 3), dtype=torch.float64).pin_memory() for d in draws]
+    h2d = sum(m.nodes.size * 8 + m.tets.size * 4 + m.tet_material.size * 4 + m.fixed_nodes.size * 4
+              for m in uniq.values()) + sum((12 + 3 + 3 + d.n_steps) * 8 for d in draws)
+    d2h = sum(o.numel() * 8 for o in h_out) + sum(f.numel() * 8 for f in h_frc)
+    t0 = time.perf_counter()
+    eh = {k: F.fem_create_mesh(pin(m.nodes), pin(m.tets.astype(np.int32)), pin(m.tet_material.astype(np.int32)),
+                               m.materials, pin(m.fixed_nodes.astype(np.int32))) for k, m in uniq.items()}
+    F.fem_solve_batch([eh[id(m)] for m in meshes], draws, TOL, opt, h_out, h_frc, check=False)
+    for h_ in eh.values():
+        F.fem_destroy_mesh(h_)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total * 1000.0 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (tangent, PCG vectors) + f64 (residual, energy, reductions, displacement)",
+            "data": "synthetic",
+            "config": {"workload": workload, "tol": TOL, "solves_per_step": n, "converged": ok,
+                       "engine": {1: "cta_groups", 2: "clusters"}[info.engine], "ctas_per_solve": info.parts,
+                       "slots": info.slots, "graph": bool(info.graph), "resident_tangent": bool(info.resident_tangent),
+                       "cg_iters_total": sum(s_.cg_iters for s_ in stats),
+                       "newton_iters_total": sum(s_.newton_iters for s_ in stats),
+                       "l2": "flushed between timed steps (256 MiB write, L2 is 126 MB)", "autotune": tune},
+            "single_path_same_draws": {"value": n / single_s, "unit": UNIT, "solves": n,
+                                       "note": "fem_solve (one cooperative launch per solve) on every draw "
+                                               "of the step, sum of kernel times"},
+            "e2e": {"value": world * n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": (1 + n) * args.steps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "group_kernel" if info.engine == 1 else "cluster_kernel",
+                         "kernel_ms": kernel_ms, "algorithmic_bytes": alg, "peak_kind": peak_kind,
+                         "fp32_tflops": flops / (kernel_ms / 1000.0) / 1e12, "fp32_peak_tflops": FP32_PEAK_TFLOPS},
+            "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    for h_ in handles.values():
+        F.fem_destroy_mesh(h_)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -344,12 +489,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["fingertip", "batch", "uneven"], default="fingertip")
+    ap.add_argument("--n-solves", type=int, default=None,
+                    help="solves per step of the batched workloads (default 256 / 64)")
     args = ap.parse_args()
+    if args.n_solves is None:
+        args.n_solves = 256 if args.workload == "batch" else 64
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
-    else:
+    elif args.workload == "fingertip":
         run_cuda(args, rank, world, local)
+    else:
+        run_batch(args, rank, world, local)
 
 
 if __name__ == "__main__":

@@ -85,8 +85,11 @@ typedef struct {
     double  barrier_timeout_s;/* bound on every device-side wait (default 5 s)        */
     int32_t batch_engine;     /* fem_solve_batch: FEM_BATCH_AUTO (default),           */
                               /* FEM_BATCH_GROUPS or FEM_BATCH_CLUSTERS                */
-    int32_t batch_parts;      /* CTAs per solve in fem_solve_batch (clusters: 1, 2,   */
-                              /* 4, 8 or 16); 0 = chosen from the largest mesh        */
+    int32_t batch_parts;      /* CTAs per solve in fem_solve_batch, the same for all  */
+                              /* solves (clusters: 1, 2, 4, 8 or 16); 0 = automatic:  */
+                              /* groups get CTAs per solve from each mesh's size       */
+                              /* (size classes), clusters from the largest mesh        */
+    int32_t batch_tets_per_cta;/* automatic groups: target tets per CTA (default 1300) */
 } fem_options;
 
 /* engines of fem_solve_batch */
@@ -281,6 +284,28 @@ typedef struct {
     int64_t workspace_bytes;        /* device workspace of the plan                  */
 } fem_batch_info;
 int fem_batch_info_get(const fem_batch* batch, fem_batch_info* info);
+
+/*
+ * Autotuner of fem_solve_batch's slot shape: times candidate (engine, CTAs per
+ * solve) pairs on the given jobs truncated to their first proxy_steps load
+ * steps (one planned run each) and writes opt (NULL = defaults) with the
+ * fastest batch_engine / batch_parts / batch_tets_per_cta to out_opt.
+ * Candidates: CTA groups in size classes of 700, 1000, 1300, 1800, 2600 or
+ * 3600 tets per CTA; uniform CTA groups with 1, 2, 4 or 8 groups sharing the SMs;
+ * clusters of 8 or 16 CTAs. report (may be NULL) lists every candidate's proxy
+ * rate (solves/s; 0 = did not fit or did not run) and the index of the best. Errors:
+ * FEM_ERR_ARG, FEM_ERR_TOO_LARGE (no candidate runs), FEM_ERR_CUDA.
+ */
+typedef struct {
+    int32_t n_candidates;
+    int32_t engine[16];
+    int32_t parts[16];              /* 0: size classes                               */
+    int32_t tets_per_cta[16];       /* size classes: target tets per CTA             */
+    double  rate[16];
+    int32_t best;
+} fem_tune_report;
+int fem_batch_tune(fem_mesh* const* meshes, const fem_indenter* indenters, int32_t n, double tol,
+                   const fem_options* opt, int32_t proxy_steps, fem_options* out_opt, fem_tune_report* report);
 
 /* Release the plan (NULL is ignored). */
 void fem_batch_destroy(fem_batch* batch);

@@ -41,7 +41,7 @@ EXPORTS = ("fem_default_options", "fem_create_mesh", "fem_set_indenter", "fem_se
            "fem_solve", "fem_solve_batch", "fem_destroy_mesh", "fem_last_error", "fem_mesh_info_get", "fem_repartition",
            "fem_eval_residual", "fem_eval_residual_noalloc", "fem_apply_tangent",
            "fem_debug_barrier_timeout", "fem_batch_create", "fem_batch_run", "fem_batch_info_get",
-           "fem_batch_destroy")
+           "fem_batch_destroy", "fem_batch_tune")
 
 
 class fem_material(C.Structure):
@@ -52,7 +52,8 @@ class fem_options(C.Structure):
     _fields_ = [("c_kappa", C.c_double), ("max_newton", C.c_int32), ("max_cg", C.c_int32),
                 ("cg_rtol_max", C.c_double), ("cg_rtol_min", C.c_double),
                 ("max_backtracks", C.c_int32), ("tangent", C.c_int32),
-                ("barrier_timeout_s", C.c_double), ("batch_engine", C.c_int32), ("batch_parts", C.c_int32)]
+                ("barrier_timeout_s", C.c_double), ("batch_engine", C.c_int32), ("batch_parts", C.c_int32),
+                ("batch_tets_per_cta", C.c_int32)]
 
 
 class fem_stats(C.Structure):
@@ -84,6 +85,11 @@ class fem_batch_info(C.Structure):
     _fields_ = [("engine", C.c_int32), ("parts", C.c_int32), ("slots", C.c_int32), ("graph", C.c_int32),
                 ("smem_bytes", C.c_int32), ("global_bytes_per_cta", C.c_int32), ("resident_tangent", C.c_int32),
                 ("workspace_bytes", C.c_int64)]
+
+
+class fem_tune_report(C.Structure):
+    _fields_ = [("n_candidates", C.c_int32), ("engine", C.c_int32 * 16), ("parts", C.c_int32 * 16),
+                ("tets_per_cta", C.c_int32 * 16), ("rate", C.c_double * 16), ("best", C.c_int32)]
 
 
 class FemError(RuntimeError):
@@ -118,6 +124,8 @@ def _load():
         "fem_batch_run": (C.c_int, [P, P, C.c_double, P, P, P]),
         "fem_batch_info_get": (C.c_int, [P, C.POINTER(fem_batch_info)]),
         "fem_batch_destroy": (None, [P]),
+        "fem_batch_tune": (C.c_int, [P, P, C.c_int32, C.c_double, C.POINTER(fem_options), C.c_int32,
+                                     C.POINTER(fem_options), C.POINTER(fem_tune_report)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -267,6 +275,19 @@ def fem_solve_batch(meshes, indenters, tol, opt=None, out_disp=None, out_contact
     if check:
         _check(rc)
     return rc, list(stats)
+
+
+def fem_batch_tune(meshes, indenters, tol, opt=None, proxy_steps=2):
+    """Autotune the batch slot shape; returns (options, report)."""
+    keep = []
+    n = len(meshes)
+    ind_arr = _indenter_array(indenters, keep)
+    out = fem_options()
+    rep = fem_tune_report()
+    _check(lib.fem_batch_tune(C.cast(_mesh_array(meshes), C.c_void_p), C.cast(ind_arr, C.c_void_p), n, float(tol),
+                              C.byref(opt) if opt is not None else None, int(proxy_steps), C.byref(out),
+                              C.byref(rep)))
+    return out, rep
 
 
 class FemBatch:

@@ -419,14 +419,20 @@ int build_partitions(fem_mesh* m, int n_parts) {
 namespace fem {
 namespace host {
 
-// Partition for batched solves with `parts` CTAs per solve (rebuilt when the
-// part count changes).
-int ensure_batch_partition(fem_mesh* m, int parts) {
-  if (m->c_parts == parts) return FEM_OK;
-  m->c_parts = 0;
-  const int rc = build_partition(m, parts, m->cdev, m->cdims, m->cpart_owned, m->cpart_bytes);
-  if (rc) return rc;
-  m->c_parts = parts;
+int batch_partition(fem_mesh* m, int parts, const MeshDev** dev, const PartDims** dims) {
+  auto it = m->batch_parts.find(parts);
+  if (it == m->batch_parts.end()) {
+    fem_mesh::BatchPart bp;
+    const int rc = build_partition(m, parts, bp.dev, bp.dims, bp.owned, bp.bytes);
+    if (rc) {
+      for (void* q : bp.owned) cudaFree(q);
+      m->bytes -= bp.bytes;
+      return rc;
+    }
+    it = m->batch_parts.emplace(parts, std::move(bp)).first;
+  }
+  *dev = &it->second.dev;
+  *dims = &it->second.dims;
   return FEM_OK;
 }
 
@@ -492,6 +498,7 @@ void fem_default_options(fem_options* opt) {
   opt->barrier_timeout_s = 5.0;
   opt->batch_engine = FEM_BATCH_AUTO;
   opt->batch_parts = 0;
+  opt->batch_tets_per_cta = 1300;
 }
 
 const char* fem_last_error(void) { return g_err.c_str(); }
@@ -499,7 +506,8 @@ const char* fem_last_error(void) { return g_err.c_str(); }
 void fem_destroy_mesh(fem_mesh* m) {
   if (!m) return;
   for (void* q : m->part_owned) cudaFree(q);
-  for (void* q : m->cpart_owned) cudaFree(q);
+  for (auto& kv : m->batch_parts)
+    for (void* q : kv.second.owned) cudaFree(q);
   for (void* q : m->owned) cudaFree(q);
   delete m;
 }

@@ -4,6 +4,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -31,11 +32,17 @@ struct fem_mesh {
   fem::SmemLayout layout{};
   fem::PartDims dims{};
   std::vector<void*> owned;     // every device allocation of the mesh
-  std::vector<void*> part_owned, cpart_owned;
-  size_t bytes = 0, part_bytes = 0, cpart_bytes = 0;
-  fem::MeshDev cdev{};           // partition for batched solves (built on first batched use)
-  fem::PartDims cdims{};
-  int c_parts = 0;               // parts of cdev (0: not built)
+  std::vector<void*> part_owned;
+  size_t bytes = 0, part_bytes = 0;
+  // partitions for batched solves, one per part count used so far (kept
+  // until the mesh is destroyed, so every plan's device pointers stay valid)
+  struct BatchPart {
+    fem::MeshDev dev{};
+    fem::PartDims dims{};
+    std::vector<void*> owned;
+    size_t bytes = 0;
+  };
+  std::map<int, BatchPart> batch_parts;
   // indenter
   bool has_indenter = false;
   int shape = 0;
@@ -60,7 +67,8 @@ int fail(int code, const char* fmt, ...);  // sets the message, returns code
 int cuda_fail(cudaError_t e, const char* what);
 SmemLayout plan_layout(const PartDims& d, int budget);
 int smem_budget(const fem_mesh* m, int static_smem);
-int ensure_batch_partition(fem_mesh* m, int parts);
+// The mesh's partition into `parts` parts for batched solves (built on first use).
+int batch_partition(fem_mesh* m, int parts, const fem::MeshDev** dev, const fem::PartDims** dims);
 int validate_indenter(int shape, const double pose[12], const double* params, const double dir[3],
                       const double* depth_schedule, int32_t n_steps);
 

@@ -147,10 +147,41 @@ struct SlotScratch {
 cudaError_t cluster_kernel_attrs(int cluster, int smem_bytes, int* static_smem, int* max_clusters);
 cudaError_t launch_cluster(const BatchJob* d_jobs, int n_jobs, int* d_queue, const SlotScratch& S,
                            const SmemLayout& L, int cluster, int n_slots, cudaStream_t stream, float* kernel_ms);
+// Group engine layout: group g owns CTAs [first, first + parts) and takes its
+// jobs from queue `queue`. Groups may differ in size (one size class per
+// queue); every job of a queue is partitioned into that queue's part count.
+struct GroupDesc {
+  int first, parts, queue;
+};
+
+// A job queue. Batch form: ids[0..n) taken in order through the head counter.
+// Served form (tail != null): the host publishes ids into the ring ids[0..cap)
+// and raises *tail (pinned host memory); a group that takes position h waits
+// until *tail > h, the stop word is set, or the deadline passes.
+struct JobQueue {
+  int* head;                        // device counter of positions taken
+  const int* ids;
+  int n;                            // batch: number of jobs
+  int cap;                          // served: ring capacity
+  const volatile int* tail;         // served: positions published so far (host memory)
+};
+
+struct GroupRun {
+  const BatchJob* jobs;
+  const GroupDesc* groups;
+  const int* group_of_cta;          // [grid] group of each CTA
+  const JobQueue* queues;
+  unsigned long long timeout_ns;    // bound of the waits inside a solve
+  // served form
+  const volatile int* stop;         // host sets it to end the session (or null)
+  unsigned long long deadline_ns;   // globaltimer value after which idle groups leave (0: none)
+  volatile int* done;               // [jobs] host memory: 1 once job j's outputs are written (or null)
+};
+
 cudaError_t group_kernel_attrs(int smem_bytes, int* static_smem, int* blocks_per_sm);
-cudaError_t launch_groups(const BatchJob* d_jobs, int n_jobs, int* d_queue, const SlotScratch& S,
-                          const SmemLayout& L, int parts, int n_groups, unsigned long long timeout_ns,
+cudaError_t launch_groups(const GroupRun& R, const SlotScratch& S, const SmemLayout& L, int n_ctas,
                           cudaStream_t stream, float* kernel_ms);
+unsigned long long device_clock_ns();   // %globaltimer now (one tiny launch; for served deadlines)
 
 // Host-side launcher (fem_solve.cu).
 cudaError_t launch_solve(const MeshDev& mesh, const WorkDev& work, const SolveParams& prm, const SmemLayout& L,

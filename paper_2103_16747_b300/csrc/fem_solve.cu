@@ -1253,34 +1253,62 @@ __global__ void __launch_bounds__(kBlock, 1) cluster_kernel(const BatchJob* __re
   }
 }
 
-// Group engine: CTAs [g*P, (g+1)*P) form group g and run one solve at a time
-// with the single-solve kernel's synchronisation on the group's own counters;
-// part 0 takes the next job from the queue. The launch is cooperative, so all
-// groups are co-resident; a group whose wait expires marks its job and leaves.
-__global__ void __launch_bounds__(kBlock, 1) group_kernel(const BatchJob* __restrict__ jobs, int n_jobs,
-                                                          int* queue, SlotScratch S, SmemLayout L, int parts,
-                                                          unsigned long long timeout_ns) {
+// Group engine: group g (CTAs [first, first + parts) of its GroupDesc) runs one
+// solve at a time with the single-solve kernel's synchronisation on the
+// group's own counters; part 0 takes the next job from the group's queue. The
+// launch is cooperative, so all groups are co-resident. A group whose wait
+// expires marks its job and leaves; in the served form a group also leaves
+// when the host sets the stop word or the deadline passes while it waits for
+// work.
+__device__ __forceinline__ int ld_acquire_sys_i32(const volatile int* p) {
+  int v;
+  asm volatile("ld.acquire.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ int next_job(const GroupRun& R, const JobQueue& q) {
+  const int h = atomicAdd(q.head, 1);
+  if (!q.tail) return h < q.n ? q.ids[h] : -1;
+  for (unsigned it = 0;; ++it) {
+    if (ld_acquire_sys_i32(q.tail) > h) return q.ids[h % q.cap];
+    // no deadline: never wait (a served queue always comes with one)
+    if ((R.stop && *R.stop) || R.deadline_ns == 0 || global_ns() > R.deadline_ns) return -1;
+    __nanosleep(2000);
+  }
+}
+
+__global__ void __launch_bounds__(kBlock, 1) group_kernel(GroupRun R, SlotScratch S, SmemLayout L) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Statics ST;
   __shared__ MeshDev sM;
   __shared__ SolveParams sP;
   __shared__ WorkDev sW;
-  const int group = blockIdx.x / parts, part = blockIdx.x - group * parts;
+  const int group = R.group_of_cta[blockIdx.x];
+  const GroupDesc G = R.groups[group];
+  const int part = blockIdx.x - G.first;
   unsigned char* sb = S.base + (size_t)group * (size_t)S.stride;
   unsigned long long* ctrl = reinterpret_cast<unsigned long long*>(sb + S.ctrl);
   unsigned char* gscr = S.cta_stride > 0 ? sb + S.cta + (size_t)part * (size_t)S.cta_stride : nullptr;
-  Barrier gb{ctrl, reinterpret_cast<int*>(ctrl + 1), 0ull, timeout_ns, (unsigned)parts};
+  // waits between solves can last as long as the host takes to send work
+  const unsigned long long idle_ns =
+      R.deadline_ns ? (R.deadline_ns > global_ns() ? R.deadline_ns - global_ns() : 0ull) + R.timeout_ns
+                    : R.timeout_ns;
+  Barrier gb{ctrl, reinterpret_cast<int*>(ctrl + 1), 0ull, R.timeout_ns, (unsigned)G.parts};
   int ep = 0;
   unsigned long long n_pub = 0;
   for (;;) {
     if (part == 0 && threadIdx.x == 0)
-      *reinterpret_cast<volatile unsigned long long*>(ctrl + 2) = (unsigned long long)atomicAdd(queue, 1);
-    if (!grid_sync(gb, &ST.flag)) return;
+      *reinterpret_cast<volatile unsigned long long*>(ctrl + 2) =
+          (unsigned long long)(long long)next_job(R, R.queues[G.queue]);
+    gb.timeout_ns = idle_ns;
+    const bool ok = grid_sync(gb, &ST.flag);
+    gb.timeout_ns = R.timeout_ns;
+    if (!ok) return;
     // part 0 rewrites the job word only after the next solve's first barrier,
     // which every part reaches after this read
-    const int j = (int)ld_volatile_u64(ctrl + 2);
-    if (j >= n_jobs) return;
-    const BatchJob* J = jobs + j;
+    const int j = (int)(long long)ld_volatile_u64(ctrl + 2);
+    if (j < 0) return;
+    const BatchJob* J = R.jobs + j;
     {
       const int* src = reinterpret_cast<const int*>(&J->mesh);
       int* dst = reinterpret_cast<int*>(&sM);
@@ -1308,13 +1336,22 @@ __global__ void __launch_bounds__(kBlock, 1) group_kernel(const BatchJob* __rest
     }
     __syncthreads();
     Ctx C;
-    setup_ctx(C, sM, sW, L, smem, gscr, &ST, part, parts);
-    if (!solve_body<false>(C, sM, sW, sP, gb, ep, n_pub)) {
-      if (part == 0 && threadIdx.x == 0) sW.stats->status = ST_TIMEOUT;
-      return;
+    setup_ctx(C, sM, sW, L, smem, gscr, &ST, part, G.parts);
+    const bool solved = solve_body<false>(C, sM, sW, sP, gb, ep, n_pub);
+    if (!solved && part == 0 && threadIdx.x == 0) sW.stats->status = ST_TIMEOUT;
+    if (R.done) {
+      // every part's outputs are written before part 0 reports the job done
+      if (solved && !grid_sync(gb, &ST.flag)) return;
+      if (part == 0 && threadIdx.x == 0) {
+        __threadfence_system();
+        R.done[j] = 1;
+      }
     }
+    if (!solved) return;
   }
 }
+
+__global__ void clock_kernel(unsigned long long* out) { *out = global_ns(); }
 
 __global__ void permute_kernel(const double* __restrict__ src, double* __restrict__ dst,
                                const int* __restrict__ perm, int n, int to_caller) {
@@ -1457,8 +1494,7 @@ cudaError_t group_kernel_attrs(int smem_bytes, int* static_smem, int* blocks_per
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, group_kernel, kBlock, smem_bytes);
 }
 
-cudaError_t launch_groups(const BatchJob* d_jobs, int n_jobs, int* d_queue, const SlotScratch& S,
-                          const SmemLayout& L, int parts, int n_groups, unsigned long long timeout_ns,
+cudaError_t launch_groups(const GroupRun& R, const SlotScratch& S, const SmemLayout& L, int n_ctas,
                           cudaStream_t stream, float* kernel_ms) {
   cudaError_t e = cudaFuncSetAttribute(group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
   if (e != cudaSuccess) return e;
@@ -1468,14 +1504,11 @@ cudaError_t launch_groups(const BatchJob* d_jobs, int n_jobs, int* d_queue, cons
     cudaEventCreate(&ev1);
     cudaEventRecord(ev0, stream);
   }
-  const BatchJob* j = d_jobs;
-  int n = n_jobs, p = parts;
-  int* q = d_queue;
+  GroupRun r = R;
   SlotScratch s = S;
   SmemLayout l = L;
-  unsigned long long t = timeout_ns;
-  void* args[] = {&j, &n, &q, &s, &l, &p, &t};
-  e = cudaLaunchCooperativeKernel((const void*)group_kernel, dim3((unsigned)(parts * n_groups)), dim3(kBlock), args,
+  void* args[] = {&r, &s, &l};
+  e = cudaLaunchCooperativeKernel((const void*)group_kernel, dim3((unsigned)n_ctas), dim3(kBlock), args,
                                   (size_t)L.total, stream);
   if (kernel_ms) {
     cudaEventRecord(ev1, stream);
@@ -1488,6 +1521,16 @@ cudaError_t launch_groups(const BatchJob* d_jobs, int n_jobs, int* d_queue, cons
     cudaEventDestroy(ev1);
   }
   return e;
+}
+
+unsigned long long device_clock_ns() {
+  unsigned long long* d = nullptr;
+  unsigned long long h = 0;
+  if (cudaMalloc(&d, sizeof(h)) != cudaSuccess) return 0;
+  clock_kernel<<<1, 1>>>(d);
+  cudaMemcpy(&h, d, sizeof(h), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  return h;
 }
 
 // ------------------------------------------------------------------------
