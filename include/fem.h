@@ -50,6 +50,8 @@ extern "C" {
                                        outputs hold the last iterate, stats are filled */
 #define FEM_ERR_TIMEOUT        -6   /* a bounded device wait (grid barrier) expired */
 #define FEM_ERR_CUDA           -7   /* a CUDA runtime call failed / no device */
+#define FEM_ERR_BUSY           -9   /* request server: not running, or its admission queue is full */
+#define FEM_PENDING             1   /* request server: the request has not finished yet */
 #define FEM_ERR_TOO_LARGE      -8   /* mesh does not fit the single-solve kernel */
 
 /* ---------------------------------------------------------------- shapes */
@@ -306,6 +308,65 @@ typedef struct {
 } fem_tune_report;
 int fem_batch_tune(fem_mesh* const* meshes, const fem_indenter* indenters, int32_t n, double tol,
                    const fem_options* opt, int32_t proxy_steps, fem_options* out_opt, fem_tune_report* report);
+
+/* ------------------------------------------------------- request server
+ * Continuous batching of indentation solves on a resident pool of meshes.
+ * One persistent launch holds CTA groups in size classes (a mesh's class is
+ * the smallest power of two up to 64 CTAs that keeps its parts near
+ * opt->batch_tets_per_cta tets; groups per class in proportion to the class's
+ * share of the work when requests are spread evenly over the pool). A host
+ * thread admits submitted requests while result memory is free, publishes
+ * them to the GPU through pinned host memory and collects the results; a
+ * request that arrives while others run starts as soon as a group of its
+ * class is idle. A request's result is bitwise independent of the others
+ * (its partition depends only on its mesh).
+ */
+typedef struct fem_server fem_server;
+
+/* meshes: the resident pool (handles stay owned by the caller and must outlive
+ * the server); max_steps: most load steps of any request; result_bytes: device
+ * memory for results in flight (one result slot ~ 48 B per node of the largest
+ * mesh + 32 B per step; at least one slot per group). Errors: FEM_ERR_ARG,
+ * FEM_ERR_TOO_LARGE, FEM_ERR_OOM, FEM_ERR_CUDA. */
+int fem_server_create(fem_mesh* const* meshes, int32_t n_meshes, int32_t max_steps, const fem_options* opt,
+                      int64_t result_bytes, fem_server** out);
+
+/* Launch the persistent kernel; it serves until fem_server_stop or for at most
+ * max_seconds (groups leave once idle after that). */
+int fem_server_start(fem_server* server, double max_seconds);
+
+/* Queue one request (mesh = index into the pool); never blocks. *request_id
+ * identifies it. FEM_ERR_BUSY if the server is not running or 4 x result-slot
+ * requests already wait for admission (the request is rejected). */
+int fem_server_submit(fem_server* server, int32_t mesh, const fem_indenter* indenter, double tol,
+                      int64_t* request_id);
+
+/* Wait up to wait_ms for a request. FEM_PENDING if it has not finished yet;
+ * otherwise the request's status (as fem_solve) with out_disp [n_nodes*3]
+ * (caller order), out_contact_force [n_steps*3], stats (kernel_ms: time from
+ * admission to completion) and times [3] = (submitted, admitted, done) in
+ * seconds of a monotonic host clock filled (each may be NULL); the request is
+ * then forgotten. */
+int fem_server_result(fem_server* server, int64_t request_id, int32_t wait_ms, double* out_disp,
+                      double* out_contact_force, fem_stats* stats, double* times);
+
+/* Stop serving: idle groups leave at once, busy ones after their solve;
+ * requests not run finish with FEM_ERR_TIMEOUT. */
+int fem_server_stop(fem_server* server);
+
+typedef struct {
+    int32_t n_classes;
+    int32_t class_parts[8];         /* CTAs per solve of each size class */
+    int32_t class_groups[8];        /* groups serving each class         */
+    int32_t n_ctas;                 /* CTAs of the persistent launch      */
+    int32_t result_slots;           /* requests in flight at most         */
+    int64_t admitted, completed, rejected;
+    int64_t workspace_bytes;
+} fem_server_info;
+int fem_server_info_get(const fem_server* server, fem_server_info* info);
+
+/* Stop (if running) and release the server (NULL is ignored). */
+void fem_server_destroy(fem_server* server);
 
 /* Release the plan (NULL is ignored). */
 void fem_batch_destroy(fem_batch* batch);

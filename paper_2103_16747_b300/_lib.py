@@ -25,9 +25,11 @@ FEM_ERR_NOT_CONVERGED = -5
 FEM_ERR_TIMEOUT = -6
 FEM_ERR_CUDA = -7
 FEM_ERR_TOO_LARGE = -8
+FEM_ERR_BUSY = -9
+FEM_PENDING = 1
 ERR_NAMES = {0: "FEM_OK", -1: "FEM_ERR_ARG", -2: "FEM_ERR_DEGENERATE_TET", -3: "FEM_ERR_NONFINITE",
              -4: "FEM_ERR_OOM", -5: "FEM_ERR_NOT_CONVERGED", -6: "FEM_ERR_TIMEOUT", -7: "FEM_ERR_CUDA",
-             -8: "FEM_ERR_TOO_LARGE"}
+             -8: "FEM_ERR_TOO_LARGE", -9: "FEM_ERR_BUSY", 1: "FEM_PENDING"}
 
 FEM_SPHERE, FEM_CYLINDER, FEM_BOX, FEM_PLANE = 0, 1, 2, 3
 FEM_MAX_STEPS = 256
@@ -41,7 +43,8 @@ EXPORTS = ("fem_default_options", "fem_create_mesh", "fem_set_indenter", "fem_se
            "fem_solve", "fem_solve_batch", "fem_destroy_mesh", "fem_last_error", "fem_mesh_info_get", "fem_repartition",
            "fem_eval_residual", "fem_eval_residual_noalloc", "fem_apply_tangent",
            "fem_debug_barrier_timeout", "fem_batch_create", "fem_batch_run", "fem_batch_info_get",
-           "fem_batch_destroy", "fem_batch_tune")
+           "fem_batch_destroy", "fem_batch_tune", "fem_server_create", "fem_server_start", "fem_server_submit",
+           "fem_server_result", "fem_server_stop", "fem_server_info_get", "fem_server_destroy")
 
 
 class fem_material(C.Structure):
@@ -92,6 +95,12 @@ class fem_tune_report(C.Structure):
                 ("tets_per_cta", C.c_int32 * 16), ("rate", C.c_double * 16), ("best", C.c_int32)]
 
 
+class fem_server_info(C.Structure):
+    _fields_ = [("n_classes", C.c_int32), ("class_parts", C.c_int32 * 8), ("class_groups", C.c_int32 * 8),
+                ("n_ctas", C.c_int32), ("result_slots", C.c_int32), ("admitted", C.c_int64),
+                ("completed", C.c_int64), ("rejected", C.c_int64), ("workspace_bytes", C.c_int64)]
+
+
 class FemError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{ERR_NAMES.get(code, code)}: {msg}")
@@ -126,6 +135,13 @@ def _load():
         "fem_batch_destroy": (None, [P]),
         "fem_batch_tune": (C.c_int, [P, P, C.c_int32, C.c_double, C.POINTER(fem_options), C.c_int32,
                                      C.POINTER(fem_options), C.POINTER(fem_tune_report)]),
+        "fem_server_create": (C.c_int, [P, C.c_int32, C.c_int32, C.POINTER(fem_options), C.c_int64, C.POINTER(P)]),
+        "fem_server_start": (C.c_int, [P, C.c_double]),
+        "fem_server_submit": (C.c_int, [P, C.c_int32, P, C.c_double, C.POINTER(C.c_int64)]),
+        "fem_server_result": (C.c_int, [P, C.c_int64, C.c_int32, P, P, C.POINTER(fem_stats), P]),
+        "fem_server_stop": (C.c_int, [P]),
+        "fem_server_info_get": (C.c_int, [P, C.POINTER(fem_server_info)]),
+        "fem_server_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -288,6 +304,60 @@ def fem_batch_tune(meshes, indenters, tol, opt=None, proxy_steps=2):
                               C.byref(opt) if opt is not None else None, int(proxy_steps), C.byref(out),
                               C.byref(rep)))
     return out, rep
+
+
+class FemServer:
+    """Request server (fem_server_*): continuous batching on a resident mesh
+    pool. ``submit`` returns a request id; ``result`` waits for it."""
+
+    def __init__(self, meshes, max_steps, opt=None, result_bytes=256 << 20):
+        self.n_nodes = None
+        h = C.c_void_p()
+        _check(lib.fem_server_create(C.cast(_mesh_array(meshes), C.c_void_p), len(meshes), int(max_steps),
+                                     C.byref(opt) if opt is not None else None, int(result_bytes), C.byref(h)))
+        self.handle = h
+
+    def start(self, max_seconds):
+        _check(lib.fem_server_start(self.handle, float(max_seconds)))
+
+    def submit(self, mesh_index, indenter, tol):
+        keep = []
+        arr = _indenter_array([indenter], keep)
+        rid = C.c_int64()
+        rc = lib.fem_server_submit(self.handle, int(mesh_index), C.cast(arr, C.c_void_p), float(tol), C.byref(rid))
+        return rc, rid.value
+
+    def result(self, request_id, n_nodes, n_steps, wait_ms=0):
+        """(rc, u (n_nodes, 3), forces (n_steps, 3), fem_stats, times) or
+        (FEM_PENDING, None, ...) while it runs."""
+        u = np.zeros((n_nodes, 3))
+        f = np.zeros((n_steps, 3))
+        st = fem_stats()
+        t = np.zeros(3)
+        rc = lib.fem_server_result(self.handle, int(request_id), int(wait_ms), C.c_void_p(u.ctypes.data),
+                                   C.c_void_p(f.ctypes.data), C.byref(st), C.c_void_p(t.ctypes.data))
+        if rc == FEM_PENDING:
+            return rc, None, None, None, None
+        return rc, u, f, st, t
+
+    def info(self) -> fem_server_info:
+        i = fem_server_info()
+        _check(lib.fem_server_info_get(self.handle, C.byref(i)))
+        return i
+
+    def stop(self):
+        return lib.fem_server_stop(self.handle)
+
+    def close(self):
+        if self.handle:
+            lib.fem_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class FemBatch:

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libfem_b300.so")
-SOURCES = ["fem_solve.cu", "fem_api.cpp", "fem_batch.cpp"]
+SOURCES = ["fem_solve.cu", "fem_api.cpp", "fem_batch.cpp", "fem_server.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -32,7 +32,8 @@ def build(verbose: bool = False, force: bool = False, extra=()) -> str:
         if all(os.path.getmtime(d) <= t for d in deps):
             return LIB
     cmd = [nvcc(), "-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC", "-shared",
-           "-I", os.path.join(ROOT, "include"), "-o", LIB + ".tmp", *srcs, "-cudart=static", *extra]
+           "-I", os.path.join(ROOT, "include"), "-o", LIB + ".tmp", *srcs, "-cudart=static", "-Xcompiler", "-pthread",
+           *extra]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
         print(" ".join(cmd))

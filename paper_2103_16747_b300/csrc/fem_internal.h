@@ -86,6 +86,7 @@ struct WorkDev {
 
 struct SolveParams {
   int mode, n_steps, step, tangent_mode, has_presc;
+  int init_zero;                    // 1: the solve starts from u = 0 it writes itself (served jobs)
   int max_newton, max_cg, max_backtracks;
   double tol, c_kappa, cg_rtol_max, cg_rtol_min;
   unsigned long long timeout_ns;

@@ -111,6 +111,7 @@ __device__ bool grid_sync(Barrier& b, int* s_flag) {
         failed = 1;
         break;
       }
+      if (it > 256u) __nanosleep(128);   // long waits (idle server groups) poll gently
     }
     __threadfence();
     if (!failed && *reinterpret_cast<volatile int*>(b.abort_flag)) failed = 1;
@@ -877,7 +878,7 @@ __device__ void accept_state(Ctx& C) {
 // Points the context at this part's data. smem: dynamic shared memory;
 // gscr: this CTA's region of the global scratch (arrays placed there by L).
 __device__ void setup_ctx(Ctx& C, const MeshDev& M, const WorkDev& W, const SmemLayout& L, unsigned char* smem,
-                          unsigned char* gscr, Statics* st, int part, int nparts) {
+                          unsigned char* gscr, Statics* st, int part, int nparts, bool zero_u = false) {
   auto at = [&](int off) -> unsigned char* { return (off & kInGlobal) ? gscr + (off & ~kInGlobal) : smem + off; };
   C.part = part;
   C.nparts = nparts;
@@ -947,6 +948,7 @@ __device__ void setup_ctx(Ctx& C, const MeshDev& M, const WorkDev& W, const Smem
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       C.x[3 * i + k] = 0.f;
+      if (zero_u) C.u[3 * i + k] = 0.0;
       if (C.uprev) C.uprev[3 * i + k] = C.u[3 * i + k];
     }
     C.mask[i] = M.fixmask[C.node0 + i];
@@ -975,7 +977,9 @@ __device__ bool solve_body(Ctx& C, const MeshDev& M, const WorkDev& W, const Sol
   for (int step = 1; step <= P.n_steps; ++step) {
     double org[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) org[k] = P.origin[k] + P.depths[step - 1] * P.dir[k];
+    // schedules of served jobs are rewritten between jobs: read past L1
+    const double dk = __ldcg(P.depths + step - 1);
+    for (int k = 0; k < 3; ++k) org[k] = P.origin[k] + dk * P.dir[k];
     if (P.has_presc) {
       const double ramp = (double)step / (double)P.n_steps;
       for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
@@ -990,8 +994,8 @@ __device__ bool solve_body(Ctx& C, const MeshDev& M, const WorkDev& W, const Sol
     // of depth increments; kept only if every tet stays valid
     double ratio = 0.0;
     if (step >= 2) {
-      const double d2 = P.depths[step - 1] - P.depths[step - 2];
-      const double d1 = P.depths[step - 2] - (step >= 3 ? P.depths[step - 3] : 0.0);
+      const double d2 = dk - __ldcg(P.depths + step - 2);
+      const double d1 = __ldcg(P.depths + step - 2) - (step >= 3 ? __ldcg(P.depths + step - 3) : 0.0);
       ratio = d1 != 0.0 ? d2 / d1 : 0.0;
     }
     for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
@@ -1267,12 +1271,17 @@ __device__ __forceinline__ int ld_acquire_sys_i32(const volatile int* p) {
 }
 
 __device__ int next_job(const GroupRun& R, const JobQueue& q) {
+  if (!q.tail) {
+    const int h = atomicAdd(q.head, 1);
+    return h < q.n ? q.ids[h] : -1;
+  }
+  // served: no new position once the session is over (no deadline: over)
+  auto over = [&]() { return (R.stop && *R.stop) || R.deadline_ns == 0 || global_ns() > R.deadline_ns; };
+  if (over()) return -1;
   const int h = atomicAdd(q.head, 1);
-  if (!q.tail) return h < q.n ? q.ids[h] : -1;
-  for (unsigned it = 0;; ++it) {
-    if (ld_acquire_sys_i32(q.tail) > h) return q.ids[h % q.cap];
-    // no deadline: never wait (a served queue always comes with one)
-    if ((R.stop && *R.stop) || R.deadline_ns == 0 || global_ns() > R.deadline_ns) return -1;
+  for (;;) {
+    if (ld_acquire_sys_i32(q.tail) > h) return __ldcg(q.ids + h % q.cap);
+    if (over()) return -1;
     __nanosleep(2000);
   }
 }
@@ -1308,18 +1317,19 @@ __global__ void __launch_bounds__(kBlock, 1) group_kernel(GroupRun R, SlotScratc
     // which every part reaches after this read
     const int j = (int)(long long)ld_volatile_u64(ctrl + 2);
     if (j < 0) return;
+    // job entries of served queues are rewritten between jobs: read past L1
     const BatchJob* J = R.jobs + j;
     {
       const int* src = reinterpret_cast<const int*>(&J->mesh);
       int* dst = reinterpret_cast<int*>(&sM);
-      for (int i = threadIdx.x; i < (int)(sizeof(MeshDev) / 4); i += blockDim.x) dst[i] = src[i];
+      for (int i = threadIdx.x; i < (int)(sizeof(MeshDev) / 4); i += blockDim.x) dst[i] = __ldcg(src + i);
       src = reinterpret_cast<const int*>(&J->prm);
       dst = reinterpret_cast<int*>(&sP);
-      for (int i = threadIdx.x; i < (int)(sizeof(SolveParams) / 4); i += blockDim.x) dst[i] = src[i];
+      for (int i = threadIdx.x; i < (int)(sizeof(SolveParams) / 4); i += blockDim.x) dst[i] = __ldcg(src + i);
     }
     if (threadIdx.x == 0) {
       WorkDev w{};
-      w.u = J->u;
+      w.u = reinterpret_cast<double*>(__ldcg(reinterpret_cast<const unsigned long long*>(&J->u)));
       w.R = reinterpret_cast<double*>(sb + S.R);
       w.uprev = reinterpret_cast<double*>(sb + S.uprev);
       w.vpub = reinterpret_cast<unsigned long long*>(sb + S.vpub);
@@ -1329,14 +1339,14 @@ __global__ void __launch_bounds__(kBlock, 1) group_kernel(GroupRun R, SlotScratc
       w.cgslot = reinterpret_cast<unsigned long long*>(sb + S.cgslot);
       w.barrier = ctrl;
       w.abort_flag = reinterpret_cast<int*>(ctrl + 1);
-      w.out_fc = J->out_fc;
-      w.step_force = J->step_force;
-      w.stats = J->stats;
+      w.out_fc = reinterpret_cast<double*>(__ldcg(reinterpret_cast<const unsigned long long*>(&J->out_fc)));
+      w.step_force = reinterpret_cast<double*>(__ldcg(reinterpret_cast<const unsigned long long*>(&J->step_force)));
+      w.stats = reinterpret_cast<StatsDev*>(__ldcg(reinterpret_cast<const unsigned long long*>(&J->stats)));
       sW = w;
     }
     __syncthreads();
     Ctx C;
-    setup_ctx(C, sM, sW, L, smem, gscr, &ST, part, G.parts);
+    setup_ctx(C, sM, sW, L, smem, gscr, &ST, part, G.parts, sP.init_zero != 0);
     const bool solved = solve_body<false>(C, sM, sW, sP, gb, ep, n_pub);
     if (!solved && part == 0 && threadIdx.x == 0) sW.stats->status = ST_TIMEOUT;
     if (R.done) {

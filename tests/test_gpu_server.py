@@ -1,0 +1,76 @@
+"""Request server (continuous batching) on the GPU: a request's result is
+bitwise the same alone and inside a burst of mixed requests, matches the FP64
+oracle, and requests submitted after stop are rejected."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import Problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2103_16747_b300 as F
+    return F
+
+
+def test_server_alone_equals_mix_and_matches_oracle(F):
+    cube, cube_ind = W.cube_sphere()
+    pool = [cube] + [m for m, _ in W.uneven_fingertips(3, seed=21, tet_min=4e3, tet_max=2e4)]
+    handles = [F.fem_create_mesh(m.nodes, m.tets, m.tet_material, m.materials, m.fixed_nodes) for m in pool]
+    draws = {k: W.draw_indentations(pool[k], 3, seed=100 + k) for k in range(1, len(pool))}
+    opt = F.fem_default_options()
+    opt.max_newton = 200
+    srv = F.FemServer(handles, 20, opt, result_bytes=64 << 20)
+    info = srv.info()
+    assert info.n_ctas >= 1 and info.result_slots >= 1
+    srv.start(120.0)
+
+    def wait(rid, k, n_steps):
+        rc, u, f, st, t = srv.result(rid, pool[k].n_nodes, n_steps, wait_ms=100000)
+        assert rc != F.FEM_PENDING
+        return rc, u, f, st, t
+
+    # alone
+    rc, rid = srv.submit(2, draws[2][0], 1e-6)
+    assert rc == 0
+    rc_a, u_a, f_a, st_a, _ = wait(rid, 2, 20)
+    # a deep random draw may exhaust max_newton: the comparison below holds
+    # for whatever the solver reached
+    assert rc_a in (F.FEM_OK, F.FEM_ERR_NOT_CONVERGED)
+    # a burst over the whole pool, the same request among them
+    burst = [(0, cube_ind)] + [(k, d) for k in range(1, len(pool)) for d in draws[k]]
+    ids = []
+    for k, d in burst:
+        rc, rid = srv.submit(k, d, 1e-6)
+        assert rc == 0
+        ids.append((rid, k, d))
+    res = [wait(rid, k, d.n_steps) for rid, k, d in ids]
+    for (rid, k, d), r in zip(ids, res):
+        assert r[0] in (F.FEM_OK, F.FEM_ERR_NOT_CONVERGED), (k, r[0])
+    assert res[0][0] == F.FEM_OK and sum(r[0] == F.FEM_OK for r in res) >= len(res) - 2
+    j = [i for i, (_, k, d) in enumerate(ids) if k == 2 and d is draws[2][0]][0]
+    assert res[j][0] == rc_a and np.array_equal(res[j][1], u_a) and np.array_equal(res[j][2], f_a)
+    # the cube request against the oracle
+    ref = Problem(cube, cube_ind).solve(tol=1e-10)
+    u0, f0 = res[0][1], res[0][2]
+    assert np.linalg.norm(u0 - ref.u) / np.linalg.norm(ref.u) <= 1e-4
+    assert np.linalg.norm(f0[-1] - ref.step_force[-1]) / np.linalg.norm(ref.step_force[-1]) <= 1e-3
+    # every converged fingertip request certified by the oracle's FP64 residual
+    for (rid, k, d), r in zip(ids[1:], res[1:]):
+        if r[0] == F.FEM_OK:
+            rn, scale, _ = Problem(pool[k], d).residual_norm(r[1], d.n_steps)
+            assert rn <= 1e-6 * scale
+    assert srv.stop() == 0
+    rc, _ = srv.submit(0, cube_ind, 1e-6)
+    assert rc == F.FEM_ERR_BUSY
+    info = srv.info()
+    assert info.completed == 1 + len(burst) and info.admitted == info.completed
+    srv.close()
+    for h in handles:
+        F.fem_destroy_mesh(h)
