@@ -18,9 +18,14 @@ Batched workloads print their own line:
   --workload uneven  one step = 64 fingertips of uneven size (R 5-10 mm,
                      5k-200k tets log-uniform), one random indentation each,
                      in one launch; the slot shape comes from fem_batch_tune.
+  --workload serve   Poisson streams of requests over a resident pool of 16
+                     fingertip meshes (5k-200k tets) through the request
+                     server (continuous batching), one session per offered
+                     rate; latency p50/p99 and throughput beside the plain
+                     one-solve-per-launch path on the same arrival trace.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference]
-                    [--workload fingertip|batch|uneven]
+                    [--workload fingertip|batch|uneven|serve]
 
 Multi-GPU runs (torchrun) are independent replicas: every rank solves its own
 indentation, no collectives on the data path (weak scaling).
@@ -482,6 +487,110 @@ def run_batch(args, rank, world, local):
         torch.distributed.destroy_process_group()
 
 
+def percentile(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    return xs[min(len(xs) - 1, max(0, int(math.ceil(q * len(xs))) - 1))]
+
+
+def run_serve(args, rank, world, local):
+    """Request server under Poisson arrivals (one session per offered rate)."""
+    import torch
+    import workloads as W
+    import paper_2103_16747_b300 as F
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    jobs = W.uneven_fingertips(16, seed=1004 + 1000 * rank)
+    pool = [m for m, _ in jobs]
+    kinds = [(k, d) for k, m in enumerate(pool) for d in W.draw_indentations(m, 4, seed=2000 + k)]
+    handles = [F.fem_create_mesh(m.nodes, m.tets, m.tet_material, m.materials, m.fixed_nodes) for m in pool]
+    opt = F.fem_default_options()
+    opt.max_newton = 200
+    sopt = F.fem_default_options()
+    sopt.max_newton = 200
+    sopt.batch_parts = args.serve_class_cap
+    # the plain path: one fem_solve (cooperative launch) per request kind, kernel time
+    t_plain = []
+    for k, d in kinds:
+        s1 = F.IndentationSolver(pool[k])
+        s1.set_indenter(d)
+        t_plain.append(s1.solve(TOL, opt, check=False)["stats"].kernel_ms / 1000.0)
+        s1.close()
+    srv = F.FemServer(handles, 20, sopt, result_bytes=1 << 30)
+    info = srv.info()
+    rng = np.random.Generator(np.random.PCG64(1004 + 1000 * rank))
+    sessions = []
+    with ClockSampler(local) as clk:
+        for rate in args.rates:
+            n_req = int(rng.poisson(rate * args.serve_seconds))
+            arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
+            arrivals = arrivals[arrivals < args.serve_seconds]
+            picks = rng.integers(0, len(kinds), size=len(arrivals))
+            srv.start(args.serve_seconds + args.drain_seconds)
+            t0 = time.perf_counter()
+            ids, rejected = [], 0
+            for a, p_ in zip(arrivals, picks):
+                dt = t0 + a - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                k, d = kinds[p_]
+                rc, rid = srv.submit(k, d, TOL)
+                if rc == 0:
+                    ids.append((rid, p_))
+                else:
+                    rejected += 1
+            lat, ok, t_first, t_last = [], 0, None, None
+            for rid, p_ in ids:
+                k, d = kinds[p_]
+                left = max(1, int(1000 * (t0 + args.serve_seconds + args.drain_seconds - time.perf_counter())))
+                rc, _, _, st, tm = srv.result(rid, pool[k].n_nodes, d.n_steps, wait_ms=left)
+                if rc == F.FEM_PENDING:
+                    continue
+                lat.append(1000.0 * (tm[2] - tm[0]))
+                ok += rc == 0
+                t_first = tm[0] if t_first is None else min(t_first, tm[0])
+                t_last = tm[2] if t_last is None else max(t_last, tm[2])
+            srv.stop()
+            done = len(lat)
+            # the plain path on the same trace: one GPU worker, FIFO, each
+            # request taking its kind's measured fem_solve time
+            fin, plain_lat = 0.0, []
+            for a, p_ in zip(arrivals, picks):
+                fin = max(fin, a) + t_plain[p_]
+                plain_lat.append(1000.0 * (fin - a))
+            sessions.append({
+                "offered_per_s": rate, "requests": int(len(arrivals)), "rejected": rejected, "completed": done,
+                "converged": int(ok), "throughput": done / (t_last - t_first) if done > 1 else None,
+                "p50_ms": percentile(lat, 0.5), "p99_ms": percentile(lat, 0.99),
+                "plain_path": {"throughput": len(arrivals) / fin if fin > 0 else None,
+                               "p50_ms": percentile(plain_lat, 0.5), "p99_ms": percentile(plain_lat, 0.99)}})
+            print(json.dumps({"session": sessions[-1]}), file=sys.stderr, flush=True)
+    best = max((x["throughput"] or 0.0) for x in sessions)
+    line = {"metric": METRIC, "value": best, "unit": UNIT, "n_gpus": world, "steps": len(sessions), "warmup": 0,
+            "ms_per_step": 1000.0 * args.serve_seconds, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32 (tangent, PCG vectors) + f64 (residual, energy, reductions, displacement)",
+            "data": "synthetic",
+            "config": {"workload": (f"serve: Poisson requests over a resident pool of 16 fingertips "
+                                    f"({min(m.n_tets for m in pool)}-{max(m.n_tets for m in pool)} tets), "
+                                    f"4 random indentations per mesh, {args.serve_seconds:.0f} s per offered rate"),
+                       "tol": TOL, "size_classes": list(info.class_parts[:info.n_classes]),
+                       "groups": list(info.class_groups[:info.n_classes]), "result_slots": info.result_slots,
+                       "plain_path": "fem_solve per request in arrival order, measured kernel time per request kind "
+                                     "(queueing simulated on the same trace)"},
+            "sessions": sessions,
+            "latency_ms": {"p50": sessions[0]["p50_ms"], "p99": sessions[0]["p99_ms"],
+                           "at_offered_per_s": sessions[0]["offered_per_s"]},
+            "gpu_launches": len(sessions), "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    srv.close()
+    for h_ in handles:
+        F.fem_destroy_mesh(h_)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -489,7 +598,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["fingertip", "batch", "uneven"], default="fingertip")
+    ap.add_argument("--workload", choices=["fingertip", "batch", "uneven", "serve"], default="fingertip")
+    ap.add_argument("--rates", type=float, nargs="+", default=[1.0, 2.0, 4.0, 8.0, 16.0],
+                    help="offered request rates (req/s) of the serve workload")
+    ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--drain-seconds", type=float, default=90.0)
+    ap.add_argument("--serve-class-cap", type=int, default=32,
+                    help="largest CTA group of the request server (power of two)")
     ap.add_argument("--n-solves", type=int, default=None,
                     help="solves per step of the batched workloads (default 256 / 64)")
     args = ap.parse_args()
@@ -500,6 +615,8 @@ def main():
         run_reference(args, rank, world)
     elif args.workload == "fingertip":
         run_cuda(args, rank, world, local)
+    elif args.workload == "serve":
+        run_serve(args, rank, world, local)
     else:
         run_batch(args, rank, world, local)
 

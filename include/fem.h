@@ -312,9 +312,10 @@ int fem_batch_tune(fem_mesh* const* meshes, const fem_indenter* indenters, int32
 /* ------------------------------------------------------- request server
  * Continuous batching of indentation solves on a resident pool of meshes.
  * One persistent launch holds CTA groups in size classes (a mesh's class is
- * the smallest power of two up to 64 CTAs that keeps its parts near
- * opt->batch_tets_per_cta tets; groups per class in proportion to the class's
- * share of the work when requests are spread evenly over the pool). A host
+ * the smallest power of two up to opt->batch_parts, or 64, CTAs that keeps its
+ * parts near opt->batch_tets_per_cta tets; one group per class, the remaining
+ * SMs going one group at a time to the class with the most work per CTA when
+ * requests are spread evenly over the pool). A host
  * thread admits submitted requests while result memory is free, publishes
  * them to the GPU through pinned host memory and collects the results; a
  * request that arrives while others run starts as soon as a group of its

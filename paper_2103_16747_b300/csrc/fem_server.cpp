@@ -315,13 +315,20 @@ int fem_server_create(fem_mesh* const* meshes, int32_t n_meshes, int32_t max_ste
   int n_sm = 1;
   CUDA_TRY(cudaSetDevice(meshes[0]->device), "device");
   CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, meshes[0]->device), "sm count");
-  // size classes: the smallest power of two up to 64 CTAs that keeps a
-  // mesh's parts at batch_tets_per_cta tets (all classes run at once)
+  // size classes: the smallest power of two up to the cap (batch_parts, or
+  // 64 CTAs) that keeps a mesh's parts at batch_tets_per_cta tets; all
+  // classes run at once, so a lower cap leaves room for more groups of the
+  // largest meshes
   const int64_t T = o.batch_tets_per_cta > 0 ? o.batch_tets_per_cta : 1300;
+  int pcap = 64;
+  if (o.batch_parts > 0) {
+    pcap = 1;
+    while (pcap * 2 <= std::min(o.batch_parts, 64)) pcap *= 2;
+  }
   std::vector<int> parts(n_meshes);
   for (int i = 0; i < n_meshes; ++i) {
     int p = 1;
-    while (p < 64 && (int64_t)p * T < meshes[i]->n_tets && 2 * p <= meshes[i]->n_nodes) p *= 2;
+    while (p < pcap && (int64_t)p * T < meshes[i]->n_tets && 2 * p <= meshes[i]->n_nodes) p *= 2;
     parts[i] = std::min(p, n_sm);
   }
   std::vector<const MeshDev*> part(n_meshes);
@@ -364,13 +371,9 @@ int fem_server_create(fem_mesh* const* meshes, int32_t n_meshes, int32_t max_ste
     W += class_work[c];
   }
   if (used > cap) return fail(FEM_ERR_TOO_LARGE, "the size classes need %d co-resident CTAs of %d", used, cap);
+  // one group per class, then one more group at a time to the class with the
+  // most work per CTA that still fits
   std::vector<int> class_groups(C, 1);
-  for (int c = 0; c < C; ++c) {
-    const int want = (int)std::floor((double)cap * class_work[c] / W / class_parts[c]);
-    const int fit = std::max(0, std::min(want - 1, (cap - used) / class_parts[c]));
-    class_groups[c] += fit;
-    used += fit * class_parts[c];
-  }
   for (;;) {
     int best = -1;
     double best_w = 0.0;
