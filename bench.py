@@ -394,7 +394,7 @@ def run_batch(args, rank, world, local):
                for k, m in uniq.items()}
     hs = [handles[id(m)] for m in meshes]
     tune = None
-    if args.workload == "uneven":
+    if True:   # both batched workloads: slot shape from the autotuner
         t0 = time.perf_counter()
         opt, rep = F.fem_batch_tune(hs, draws, TOL, opt, proxy_steps=4)
         tune = {"seconds": time.perf_counter() - t0,

@@ -265,26 +265,34 @@ int build_partition(fem_mesh* m, int n_parts, MeshDev& D, PartDims& dims, std::v
   return FEM_OK;
 }
 
-// Placement of one CTA's working arrays for parts up to the sizes in d, with
-// `budget` bytes of dynamic shared memory. First choice: everything in shared
-// memory with the whole part in one chunk. Otherwise chunks of kChunk tets,
-// and the arrays in order of how often the PCG touches them go to shared
-// memory while they fit; the rest go to the CTA's global scratch region (the
-// tangent, tet ids and node->tet lists are then read from their global
-// arrays). Returns total = -1 if even the fixed part does not fit.
 }  // namespace
 
 namespace fem {
 namespace host {
 
+// Placement of one CTA's working arrays for parts up to the sizes in d, with
+// `budget` bytes of dynamic shared memory, in order of preference:
+//  1. everything in shared memory, the whole part in one chunk;
+//  2. the whole part in one chunk of the tangent product (which stages 48 B
+//     per tet, the evaluation passes 96 B: they take it in two chunks), with
+//     every node array in shared memory;
+//  3. chunks of kChunk tets (2 * kChunk for the product).
+// In 2 and 3 the arrays go to shared memory in order of how often the PCG
+// touches them while they fit; the rest go to the CTA's global scratch region
+// (the tangent, tet ids and node->tet lists are then read from their global
+// arrays). Returns total = -1 if even the fixed part does not fit.
 SmemLayout plan_layout(const PartDims& d, int budget) {
   SmemLayout L{};
-  for (int attempt = 0; attempt < 2; ++attempt) {
-    const bool resident = attempt == 0;
-    const int CH = resident ? std::max(d.max_pt, 1) : std::max(1, std::min(kChunk, d.max_pt));
-    const bool multi = CH < d.max_pt;
+  const int max_pt = std::max(d.max_pt, 1);
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    int CH;
+    if (attempt == 0) CH = max_pt;
+    else if (attempt == 1) CH = (max_pt + 1) / 2;
+    else CH = std::min(kChunk, max_pt);
+    if (attempt == 1 && CH <= kChunk) continue;   // the same as attempt 3
+    const bool multi = CH < max_pt;
     int o = 0, g = 0;
-    bool all_shared = true;
+    bool all_shared = true, nodes_shared = true;
     auto fits = [&](int bytes) { return align_up(o + bytes, 16) <= budget; };
     auto take = [&](int bytes) { const int at = o; o = align_up(o + bytes, 16); return at; };
     auto place = [&](int bytes) {
@@ -293,6 +301,11 @@ SmemLayout plan_layout(const PartDims& d, int budget) {
       const int at = g;
       g = align_up(g + bytes, 16);
       return at | kInGlobal;
+    };
+    auto place_node = [&](int bytes) {
+      const int at = place(bytes);
+      if (at & kInGlobal) nodes_shared = false;
+      return at;
     };
     auto place_opt = [&](int bytes) {
       if (fits(bytes)) return take(bytes);
@@ -303,21 +316,22 @@ SmemLayout plan_layout(const PartDims& d, int budget) {
     L.red = take(8 * kRed * (kBlock / 32 + 1));
     L.chunk = take(96 * CH);
     if (o > budget) {
-      if (resident) continue;
+      if (attempt < 2) continue;
       L.total = -1;
       return L;
     }
-    L.acc = place(24 * d.max_own);
-    L.r = place(12 * d.max_own);
-    L.ucg = place(12 * d.max_own);
-    L.w = place(12 * d.max_own);
-    L.p = place(12 * d.max_own);
-    L.s = place(12 * d.max_own);
-    L.x = place(12 * d.max_own);
-    L.minv = place(24 * d.max_own);
-    L.hc = place(12 * d.max_own);
-    L.mask = place(d.max_own);
-    L.cursor = place(multi ? 24 * d.max_own : 16);
+    L.acc = place_node(24 * d.max_own);
+    L.r = place_node(12 * d.max_own);
+    L.ucg = place_node(12 * d.max_own);
+    L.w = place_node(12 * d.max_own);
+    L.p = place_node(12 * d.max_own);
+    L.s = place_node(12 * d.max_own);
+    L.x = place_node(12 * d.max_own);
+    L.minv = place_node(24 * d.max_own);
+    L.hc = place_node(12 * d.max_own);
+    L.mask = place_node(d.max_own);
+    L.cursor = place_node(multi ? 24 * d.max_own : 16);
+    if (attempt == 1 && !nodes_shared) continue;
     L.ptn = place_opt(8 * d.max_pt);
     const int lptr_bytes = align_up(4 * (d.max_own + 1), 16);
     if (fits(lptr_bytes + 4 * d.max_lcsr)) {
@@ -329,7 +343,7 @@ SmemLayout plan_layout(const PartDims& d, int budget) {
     }
     L.ut = place(24 * d.max_loc);
     L.tan = place_opt(16 * kTanVec * d.max_pt);
-    if (resident && !all_shared) continue;
+    if (attempt == 0 && !all_shared) continue;
     L.chunk_tets = CH;
     L.total = o;
     L.gbytes = align_up(g, 256);

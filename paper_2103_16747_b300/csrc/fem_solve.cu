@@ -976,9 +976,9 @@ __device__ bool solve_body(Ctx& C, const MeshDev& M, const WorkDev& W, const Sol
   int steps_done = 0;
   for (int step = 1; step <= P.n_steps; ++step) {
     double org[3];
-#pragma unroll
     // schedules of served jobs are rewritten between jobs: read past L1
     const double dk = __ldcg(P.depths + step - 1);
+#pragma unroll
     for (int k = 0; k < 3; ++k) org[k] = P.origin[k] + dk * P.dir[k];
     if (P.has_presc) {
       const double ramp = (double)step / (double)P.n_steps;
