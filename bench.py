@@ -137,24 +137,26 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def algorithmic_bytes(n_tets, n_nodes, cg_iters, newton_iters, evals):
+def algorithmic_bytes(n_tets, n_nodes, products, newton_iters, evals):
     """Per-launch algorithmic bytes of the solve kernel.
 
-    Stored-tangent accounting of the indentation problem (FP32 = 4 B):
-    per PCG iteration 264 B/tet + 160 B/node (tangent 45 floats + Dm^-1 9 floats,
-    tet ids, CSR, p read / y write, fused PCG vectors); per Newton iteration
+    Stored-tangent accounting of the indentation problem (FP32 = 4 B): per
+    element-tangent product (each PCG iteration and each Chebyshev step of the
+    preconditioner) 264 B/tet + 160 B/node (tangent 45 floats + Dm^-1 9 floats,
+    tet ids, CSR, p read / y write, fused vector updates); per Newton iteration
     464 B/tet + 48 B/node extra (u read, tangent write, FP64 forces, CSR); per
     line-search energy pass 60 B/tet."""
-    return (cg_iters * (264 * n_tets + 160 * n_nodes) + newton_iters * (464 * n_tets + 48 * n_nodes)
+    return (products * (264 * n_tets + 160 * n_nodes) + newton_iters * (464 * n_tets + 48 * n_nodes)
             + evals * 60 * n_tets)
 
 
-def compact_bytes(n_tets, n_nodes, cg_iters, newton_iters, evals):
+def compact_bytes(n_tets, n_nodes, products, newton_iters, evals):
     """The same, for this library's compressed tangent (30 floats + ushort4 local
-    ids per tet, node vectors in shared memory): per PCG iteration 128 B/tet read
-    + 32 B/node published/loaded; per Newton iteration the FP64 pass (Dm^-1 72 B,
-    V 8 B, ids 8 B, info 4 B) + tangent write 128 B; per energy pass 92 B/tet."""
-    return (cg_iters * (128 * n_tets + 32 * n_nodes) + newton_iters * (220 * n_tets + 48 * n_nodes)
+    ids per tet, node vectors in shared memory): per tangent product 128 B/tet
+    read + 32 B/node published/loaded; per Newton iteration the FP64 pass (Dm^-1
+    72 B, V 8 B, ids 8 B, info 4 B) + tangent write 128 B; per energy pass
+    92 B/tet."""
+    return (products * (128 * n_tets + 32 * n_nodes) + newton_iters * (220 * n_tets + 48 * n_nodes)
             + evals * 92 * n_tets)
 
 
@@ -320,8 +322,8 @@ def run_cuda(args, rank, world, local):
     s0 = stats[-1]
     evals = s0.newton_iters + s0.backtracks + ind.n_steps
     kms = statistics.mean(kernel_ms)
-    alg = algorithmic_bytes(mesh.n_tets, n, s0.cg_iters, s0.newton_iters, evals)
-    cmp_b = compact_bytes(mesh.n_tets, n, s0.cg_iters, s0.newton_iters, evals)
+    alg = algorithmic_bytes(mesh.n_tets, n, s0.tangent_products, s0.newton_iters, evals)
+    cmp_b = compact_bytes(mesh.n_tets, n, s0.tangent_products, s0.newton_iters, evals)
     peak, peak_kind = peaks()
     achieved = alg / (kms / 1000.0) / 1e9
     traffic = profiled_traffic()
@@ -334,7 +336,9 @@ def run_cuda(args, rank, world, local):
             "config": {"workload": WORKLOAD, "tol": TOL, "n_parts": info.n_parts,
                        "l2": "flushed between timed steps (256 MiB write, L2 is 126 MB)",
                        "replicas": world, "newton_iters": s0.newton_iters, "cg_iters": s0.cg_iters,
-                       "backtracks": s0.backtracks},
+                       "tangent_products": s0.tangent_products, "backtracks": s0.backtracks,
+                       "preconditioner": f"Chebyshev degree {opt.precond_degree} on block-Jacobi, "
+                                         f"interval [4/{opt.precond_ratio:g}, 4]"},
             "latency_ms": {"p50": p(0.5), "p99": p(0.99)},
             "e2e": {"value": world * args.steps / e2e_total, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
@@ -356,10 +360,10 @@ def run_cuda(args, rank, world, local):
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 
 
-def flops_per_solve(n_tets, n_nodes, cg_iters, newton_iters):
-    """FP32 work of the hot path: ~300 flop/tet + ~40 flop/node per PCG
-    iteration, ~600 flop/tet per Newton iteration (tangent build)."""
-    return cg_iters * (300 * n_tets + 40 * n_nodes) + newton_iters * 600 * n_tets
+def flops_per_solve(n_tets, n_nodes, products, newton_iters):
+    """FP32 work of the hot path: ~300 flop/tet + ~40 flop/node per tangent
+    product, ~600 flop/tet per Newton iteration (tangent build)."""
+    return products * (300 * n_tets + 40 * n_nodes) + newton_iters * 600 * n_tets
 
 
 def run_batch(args, rank, world, local):
@@ -393,15 +397,14 @@ def run_batch(args, rank, world, local):
     handles = {k: F.fem_create_mesh(m.nodes, m.tets, m.tet_material, m.materials, m.fixed_nodes)
                for k, m in uniq.items()}
     hs = [handles[id(m)] for m in meshes]
-    tune = None
-    if True:   # both batched workloads: slot shape from the autotuner
-        t0 = time.perf_counter()
-        opt, rep = F.fem_batch_tune(hs, draws, TOL, opt, proxy_steps=4)
-        tune = {"seconds": time.perf_counter() - t0,
-                "chosen": {"engine": opt.batch_engine, "parts": opt.batch_parts,
-                           "tets_per_cta": opt.batch_tets_per_cta},
-                "candidates": [{"engine": rep.engine[k], "parts": rep.parts[k], "tets_per_cta": rep.tets_per_cta[k],
-                                "proxy_solves_per_s": rep.rate[k]} for k in range(rep.n_candidates)]}
+    # both batched workloads take their slot shape from the autotuner
+    t0 = time.perf_counter()
+    opt, rep = F.fem_batch_tune(hs, draws, TOL, opt, proxy_steps=4)
+    tune = {"seconds": time.perf_counter() - t0,
+            "chosen": {"engine": opt.batch_engine, "parts": opt.batch_parts,
+                       "tets_per_cta": opt.batch_tets_per_cta},
+            "candidates": [{"engine": rep.engine[k], "parts": rep.parts[k], "tets_per_cta": rep.tets_per_cta[k],
+                            "proxy_solves_per_s": rep.rate[k]} for k in range(rep.n_candidates)]}
     plan = F.FemBatch(hs, [d.n_steps for d in draws], opt)
     info = plan.info()
     outs = [torch.zeros((m.n_nodes, 3), dtype=torch.float64, device=dev) for m in meshes]
@@ -426,10 +429,11 @@ def run_batch(args, rank, world, local):
     n = len(draws)
     value = world * n * args.steps / total
     ok = sum(1 for s_ in stats if s_.status == 0)
-    alg = sum(algorithmic_bytes(m.n_tets, m.n_nodes, s_.cg_iters, s_.newton_iters,
+    alg = sum(algorithmic_bytes(m.n_tets, m.n_nodes, s_.tangent_products, s_.newton_iters,
                                 s_.newton_iters + s_.backtracks + d.n_steps)
               for m, s_, d in zip(meshes, stats, draws))
-    flops = sum(flops_per_solve(m.n_tets, m.n_nodes, s_.cg_iters, s_.newton_iters) for m, s_ in zip(meshes, stats))
+    flops = sum(flops_per_solve(m.n_tets, m.n_nodes, s_.tangent_products, s_.newton_iters)
+                for m, s_ in zip(meshes, stats))
     peak, peak_kind = peaks()
     achieved = alg / (kernel_ms / 1000.0) / 1e9
     # the plain one-solve-per-launch path (fem_solve, one cooperative launch

@@ -92,6 +92,11 @@ typedef struct {
                               /* groups get CTAs per solve from each mesh's size       */
                               /* (size classes), clusters from the largest mesh        */
     int32_t batch_tets_per_cta;/* automatic groups: target tets per CTA (default 1300) */
+    int32_t precond_degree;   /* PCG preconditioner: 1 = block-Jacobi; d = 2..8:      */
+                              /* Chebyshev polynomial of degree d in the block-Jacobi */
+                              /* preconditioned tangent (d tangent products and one  */
+                              /* reduction per PCG iteration; default 5)              */
+    double  precond_ratio;    /* Chebyshev interval [4/ratio, 4] (default 60)          */
 } fem_options;
 
 /* engines of fem_solve_batch */
@@ -125,6 +130,8 @@ typedef struct {
     int32_t newton_per_step[FEM_MAX_STEPS];
     int32_t cg_per_step[FEM_MAX_STEPS];
     double  residual_per_step[FEM_MAX_STEPS];
+    int64_t tangent_products;               /* element-tangent products (PCG and     */
+                                            /* preconditioner) of the whole solve    */
 } fem_stats;
 
 typedef struct {

@@ -56,7 +56,8 @@ class fem_options(C.Structure):
                 ("cg_rtol_max", C.c_double), ("cg_rtol_min", C.c_double),
                 ("max_backtracks", C.c_int32), ("tangent", C.c_int32),
                 ("barrier_timeout_s", C.c_double), ("batch_engine", C.c_int32), ("batch_parts", C.c_int32),
-                ("batch_tets_per_cta", C.c_int32)]
+                ("batch_tets_per_cta", C.c_int32), ("precond_degree", C.c_int32),
+                ("precond_ratio", C.c_double)]
 
 
 class fem_stats(C.Structure):
@@ -68,7 +69,7 @@ class fem_stats(C.Structure):
                 ("phase_min_ms", C.c_double * 10),
                 ("newton_per_step", C.c_int32 * FEM_MAX_STEPS),
                 ("cg_per_step", C.c_int32 * FEM_MAX_STEPS),
-                ("residual_per_step", C.c_double * FEM_MAX_STEPS)]
+                ("residual_per_step", C.c_double * FEM_MAX_STEPS), ("tangent_products", C.c_int64)]
 
 
 class fem_indenter(C.Structure):

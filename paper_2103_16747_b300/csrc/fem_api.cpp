@@ -281,6 +281,16 @@ namespace host {
 // touches them while they fit; the rest go to the CTA's global scratch region
 // (the tangent, tet ids and node->tet lists are then read from their global
 // arrays). Returns total = -1 if even the fixed part does not fit.
+// Chebyshev interval of the preconditioner: the top is the bound 4 on the
+// spectrum of the block-Jacobi-preconditioned tangent (every clamped element
+// tangent is at most 4 times its own block diagonal).
+void set_precond(const fem_options& o, SolveParams& P) {
+  const double b = 4.0, a = b / o.precond_ratio;
+  P.cheb_deg = o.precond_degree;
+  P.cheb_theta = (float)(0.5 * (b + a));
+  P.cheb_delta = (float)(0.5 * (b - a));
+}
+
 SmemLayout plan_layout(const PartDims& d, int budget) {
   SmemLayout L{};
   const int max_pt = std::max(d.max_pt, 1);
@@ -331,6 +341,7 @@ SmemLayout plan_layout(const PartDims& d, int budget) {
     L.hc = place_node(12 * d.max_own);
     L.mask = place_node(d.max_own);
     L.cursor = place_node(multi ? 24 * d.max_own : 16);
+    L.cd = place_node(12 * d.max_own);
     if (attempt == 1 && !nodes_shared) continue;
     L.ptn = place_opt(8 * d.max_pt);
     const int lptr_bytes = align_up(4 * (d.max_own + 1), 16);
@@ -513,6 +524,8 @@ void fem_default_options(fem_options* opt) {
   opt->batch_engine = FEM_BATCH_AUTO;
   opt->batch_parts = 0;
   opt->batch_tets_per_cta = 1300;
+  opt->precond_degree = 5;
+  opt->precond_ratio = 60.0;
 }
 
 const char* fem_last_error(void) { return g_err.c_str(); }
@@ -885,9 +898,10 @@ static int fill_params(fem_mesh* m, const fem_options* opt, int mode, int steps,
   if (opt) o = *opt;
   if (!(o.c_kappa > 0) || o.max_newton < 0 || o.max_cg < 1 || o.max_backtracks < 0 || !(o.cg_rtol_max > 0) ||
       !(o.cg_rtol_min > 0) || o.cg_rtol_min > o.cg_rtol_max || (o.tangent < 0 || o.tangent > 3) ||
-      !(o.barrier_timeout_s > 0))
+      !(o.barrier_timeout_s > 0) || o.precond_degree < 1 || o.precond_degree > 8 || !(o.precond_ratio > 1.0))
     return fail(FEM_ERR_ARG, "invalid fem_options");
   memset(&P, 0, sizeof(P));
+  set_precond(o, P);
   P.mode = mode;
   P.n_steps = steps;
   P.step = step;
@@ -973,6 +987,7 @@ int fem_solve(fem_mesh* m, int32_t load_steps, double tol, const fem_options* op
     stats->steps_done = hst.steps_done;
     stats->newton_iters = hst.newton_total;
     stats->cg_iters = hst.cg_total;
+    stats->tangent_products = hst.products;
     stats->backtracks = hst.backtracks_total;
     stats->active_contacts = hst.active;
     stats->residual = hst.residual;

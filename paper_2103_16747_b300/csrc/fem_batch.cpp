@@ -69,6 +69,7 @@ int check_options(const fem_options& o) {
   if (!(o.c_kappa > 0) || o.max_newton < 0 || o.max_cg < 1 || o.max_backtracks < 0 || !(o.cg_rtol_max > 0) ||
       !(o.cg_rtol_min > 0) || o.cg_rtol_min > o.cg_rtol_max || o.tangent < 0 || o.tangent > 3 ||
       !(o.barrier_timeout_s > 0) || o.batch_engine < FEM_BATCH_AUTO || o.batch_engine > FEM_BATCH_CLUSTERS ||
+      o.precond_degree < 1 || o.precond_degree > 8 || !(o.precond_ratio > 1.0) ||
       o.batch_parts < 0 || o.batch_parts > 256 ||
       (clusters && !(o.batch_parts == 0 || o.batch_parts == 1 || o.batch_parts == 2 || o.batch_parts == 4 ||
                      o.batch_parts == 8 || o.batch_parts == 16)))
@@ -369,6 +370,7 @@ int fem_batch_create(fem_mesh* const* meshes, const int32_t* n_steps, int32_t n,
     P.cg_rtol_max = o.cg_rtol_max;
     P.cg_rtol_min = o.cg_rtol_min;
     P.timeout_ns = (unsigned long long)(o.barrier_timeout_s * 1e9);
+    set_precond(o, P);
     P.depths = reinterpret_cast<const double*>(b->ws + b->depths_off) + b->depth_at[i];
     b->h_stats0[i] = st0;
   }
@@ -513,6 +515,7 @@ int fem_batch_run(fem_batch* b, const fem_indenter* ind, double tol, double* con
       st.steps_done = h.steps_done;
       st.newton_iters = h.newton_total;
       st.cg_iters = h.cg_total;
+      st.tangent_products = h.products;
       st.backtracks = h.backtracks_total;
       st.active_contacts = h.active;
       st.residual = h.residual;

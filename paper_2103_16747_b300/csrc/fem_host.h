@@ -66,6 +66,7 @@ std::string& last_error();                 // this thread's message (fem_last_er
 int fail(int code, const char* fmt, ...);  // sets the message, returns code
 int cuda_fail(cudaError_t e, const char* what);
 SmemLayout plan_layout(const PartDims& d, int budget);
+void set_precond(const fem_options& o, SolveParams& P);
 int smem_budget(const fem_mesh* m, int static_smem);
 // The mesh's partition into `parts` parts for batched solves (built on first use).
 int batch_partition(fem_mesh* m, int parts, const fem::MeshDev** dev, const fem::PartDims** dims);

@@ -52,6 +52,7 @@ enum Phase : int { PH_EVAL = 0, PH_TANGENT, PH_CG_INIT, PH_CG_REDUCE, PH_CG_MATV
 
 struct StatsDev {
   int status, steps_done, newton_total, cg_total, backtracks_total, active, exact_newton;
+  long long products;               // tangent products (PCG products + preconditioner products)
   double residual, scale, energy, elastic, contact_energy;
   long long cycles[PH_N];
   long long cycles_max[PH_N];       // largest per-CTA value of each phase
@@ -87,6 +88,8 @@ struct WorkDev {
 struct SolveParams {
   int mode, n_steps, step, tangent_mode, has_presc;
   int init_zero;                    // 1: the solve starts from u = 0 it writes itself (served jobs)
+  int cheb_deg;                     // preconditioner: 1 = block-Jacobi, d > 1 = Chebyshev of degree d on it
+  float cheb_theta, cheb_delta;     // centre and half-width of the Chebyshev interval
   int max_newton, max_cg, max_backtracks;
   double tol, c_kappa, cg_rtol_max, cg_rtol_min;
   unsigned long long timeout_ns;
@@ -106,7 +109,7 @@ __host__ __device__ inline int align_up(int v, int a) { return (v + a - 1) / a *
 
 struct SmemLayout {
   int lm, red, chunk;                             // always shared
-  int acc, x, r, ucg, w, s, p, minv, hc, mask, cursor, ut;
+  int acc, x, r, ucg, w, s, p, minv, hc, mask, cursor, ut, cd;
   int tan, ptn, lptr, lcsr;                       // resident part data, or -1: read from global memory
   int chunk_tets;                                 // part tets per chunk of the evaluation passes
   int total;                                      // dynamic shared bytes

@@ -172,6 +172,7 @@ bool admit(fem_server* v, int slot, Request& q) {
   P.cg_rtol_min = v->o.cg_rtol_min;
   P.timeout_ns = (unsigned long long)(v->o.barrier_timeout_s * 1e9);
   P.init_zero = 1;
+  set_precond(v->o, P);
   P.shape = q.ind.shape;
   for (int k = 0; k < 3; ++k) {
     P.origin[k] = q.ind.pose[k];
@@ -227,6 +228,7 @@ void finish(fem_server* v, int slot) {
   st.steps_done = h.steps_done;
   st.newton_iters = h.newton_total;
   st.cg_iters = h.cg_total;
+  st.tangent_products = h.products;
   st.backtracks = h.backtracks_total;
   st.active_contacts = h.active;
   st.residual = h.residual;
@@ -306,7 +308,8 @@ int fem_server_create(fem_mesh* const* meshes, int32_t n_meshes, int32_t max_ste
   if (opt) o = *opt;
   if (!(o.c_kappa > 0) || o.max_newton < 0 || o.max_cg < 1 || o.max_backtracks < 0 || !(o.cg_rtol_max > 0) ||
       !(o.cg_rtol_min > 0) || o.cg_rtol_min > o.cg_rtol_max || o.tangent < 0 || o.tangent > 3 ||
-      !(o.barrier_timeout_s > 0) || o.batch_tets_per_cta < 0)
+      !(o.barrier_timeout_s > 0) || o.batch_tets_per_cta < 0 || o.precond_degree < 1 || o.precond_degree > 8 ||
+      !(o.precond_ratio > 1.0))
     return fail(FEM_ERR_ARG, "invalid fem_options");
   for (int i = 0; i < n_meshes; ++i) {
     if (!meshes[i]) return fail(FEM_ERR_ARG, "mesh %d is NULL", i);

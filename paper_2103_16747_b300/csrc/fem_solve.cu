@@ -136,7 +136,7 @@ struct Ctx {
   double *u, *uprev, *R, *fc;   // owned entries of global node arrays (index 3*i+k)
   const double *X, *kb;
   double *ut, *chunkd, *red;
-  float *x, *r, *ucg, *w, *s, *p, *acc, *minv, *hc, *chunkf;
+  float *x, *r, *ucg, *w, *s, *p, *acc, *minv, *hc, *chunkf, *cd;
   float4* lm;
   float4* tan;            // part tangent, element (g, t) at tan[g * tan_stride + t]
   int tan_stride;
@@ -729,6 +729,85 @@ __device__ void reduce_cluster(Ctx& C, int ep) {
   __syncthreads();
 }
 
+// Halo exchange of the vector being multiplied (its owned values are in C.lm
+// and, in the cooperative form, published at epoch ep).
+template <bool CL>
+__device__ __forceinline__ bool exchange_halo(Ctx& C, const MeshDev& M, const WorkDev& W, int ep,
+                                              unsigned long long limit) {
+  if constexpr (CL) {
+    load_halo_cluster(C);
+    return true;
+  } else {
+    return load_halo_tagged(C, M, W, ep, limit);
+  }
+}
+
+// u = M^-1 r for the owned nodes (r in C.r): block-Jacobi B^-1 r, or with
+// cheb_deg = d > 1 the Chebyshev polynomial of degree d in B^-1 K applied to
+// B^-1 r (d - 1 tangent products): Chebyshev iteration for K z = r from z = 0
+// on the interval [theta - delta, theta + delta] that holds the spectrum of
+// B^-1 K, a fixed polynomial p with p(lambda) > 0 for every lambda below the
+// interval's top, so M^-1 = p(B^-1 K) B^-1 is symmetric positive definite
+// whenever the top bounds the spectrum (the clamped element tangents satisfy
+// K_e <= 4 blockdiag(K_e), and the exact tangent lies below the clamped one).
+// Leaves u in C.ucg and C.lm (owned) and publishes it at a new epoch.
+template <bool CL>
+__device__ bool apply_precond(Ctx& C, const MeshDev& M, const WorkDev& W, const SolveParams& P, int& ep,
+                              long long& products) {
+  const int deg = P.cheb_deg > 1 ? P.cheb_deg : 1;
+  const float theta = P.cheb_theta, delta = P.cheb_delta;
+  const float sigma = deg > 1 ? theta / delta : 1.f;
+  float rho = deg > 1 ? delta / theta : 0.f;
+  ++ep;
+  for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
+    const float r3[3] = {C.r[3 * i], C.r[3 * i + 1], C.r[3 * i + 2]};
+    float z[3];
+    apply_minv(C.minv + 6 * i, r3, z);
+    if (deg > 1) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        z[k] *= 1.f / theta;
+        C.cd[3 * i + k] = z[k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) C.ucg[3 * i + k] = z[k];
+    C.lm[i] = make_float4(z[0], z[1], z[2], 0.f);
+    if constexpr (!CL) publish_node(C, M, W, i, z, ep);
+  }
+  for (int j = 1; j < deg; ++j) {
+    if (!exchange_halo<CL>(C, M, W, ep, P.timeout_ns)) return false;
+    matvec_pass(C, M);   // acc = element tangent applied to z
+    ++products;
+    // the owners overwrite their shared z below: every peer has read it
+    if constexpr (CL) cluster_sync();
+    const float rho_new = 1.f / (2.f * sigma - rho);
+    const float c_old = rho_new * rho, c_res = 2.f * rho_new / delta;
+    ++ep;
+    for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
+      const float4 z4 = C.lm[i];
+      const float zo[3] = {z4.x, z4.y, z4.z};
+      float kz[3], res[3], br[3], z[3];
+      finish_product(C, i, zo, kz);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) res[k] = C.r[3 * i + k] - kz[k];
+      apply_minv(C.minv + 6 * i, res, br);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float d = c_old * C.cd[3 * i + k] + c_res * br[k];
+        C.cd[3 * i + k] = d;
+        z[k] = zo[k] + d;
+        C.ucg[3 * i + k] = z[k];
+      }
+      C.lm[i] = make_float4(z[0], z[1], z[2], 0.f);
+      if constexpr (!CL) publish_node(C, M, W, i, z, ep);
+    }
+    rho = rho_new;
+  }
+  __syncthreads();
+  return true;
+}
+
 // Preconditioned CG on K dx = -R_free in the Chronopoulos-Gear form: one
 // halo exchange, one tangent product and one reduction (of (r,u), (w,u)
 // and (r,r) together) per iteration; s = A p is carried by recurrence.
@@ -737,41 +816,33 @@ __device__ void reduce_cluster(Ctx& C, int ep) {
 // non-positive curvature.
 template <bool CL>
 __device__ bool pcg(Ctx& C, const MeshDev& M, const WorkDev& W, const SolveParams& P, int& ep,
-                    unsigned long long& n_pub, double eta, double abs_tol, int& iters, bool& neg_curv) {
+                    unsigned long long& n_pub, double eta, double abs_tol, int& iters, bool& neg_curv,
+                    long long& products) {
   long long t = tick(C);
   neg_curv = false;
   const int active_warps = min((C.n_own + 31) / 32, kBlock / 32);
-  // x = 0, r = -R_free, u = M^-1 r, p = s = 0; publish u
-  ++ep;
+  // x = 0, r = -R_free, p = s = 0, u = M^-1 r (published)
   for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
     const unsigned mk = C.mask[i];
-    float r[3], uu[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      r[k] = (mk & (1u << k)) ? 0.f : (float)(-C.R[3 * i + k]);
-      C.r[3 * i + k] = r[k];
+      C.r[3 * i + k] = (mk & (1u << k)) ? 0.f : (float)(-C.R[3 * i + k]);
       C.x[3 * i + k] = 0.f;
       C.p[3 * i + k] = 0.f;
       C.s[3 * i + k] = 0.f;
     }
-    apply_minv(C.minv + 6 * i, r, uu);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) C.ucg[3 * i + k] = uu[k];
-    C.lm[i] = make_float4(uu[0], uu[1], uu[2], 0.f);
-    if constexpr (!CL) publish_node(C, M, W, i, uu, ep);
   }
+  __syncthreads();
+  if (!apply_precond<CL>(C, M, W, P, ep, products)) return false;
   tock(C, PH_CG_INIT, t);
   float gamma_prev = 1.f, alpha_prev = 1.f, rr0 = 0.f;
   const float eta2 = (float)(eta * eta), abs2 = (float)(abs_tol * abs_tol);
   int it = 0;
   for (;; ++it) {
-    if constexpr (CL) {
-      load_halo_cluster(C);
-    } else {
-      if (!load_halo_tagged(C, M, W, ep, P.timeout_ns)) return false;
-    }
+    if (!exchange_halo<CL>(C, M, W, ep, P.timeout_ns)) return false;
     tock(C, PH_CG_BARRIER, t);
     matvec_pass(C, M, &t);   // w = A u (u in C.lm)
+    ++products;
     float v[3] = {0.f, 0.f, 0.f};
     for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
       const float4 u4 = C.lm[i];
@@ -833,10 +904,8 @@ __device__ bool pcg(Ctx& C, const MeshDev& M, const WorkDev& W, const SolveParam
       __syncthreads();
       break;
     }
-    // p = u + beta p; s = w + beta s; x += alpha p; r -= alpha s; u = M^-1 r
-    ++ep;
+    // p = u + beta p; s = w + beta s; x += alpha p; r -= alpha s; then u = M^-1 r
     for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
-      float rn[3], un[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         const int j = 3 * i + k;
@@ -845,15 +914,13 @@ __device__ bool pcg(Ctx& C, const MeshDev& M, const WorkDev& W, const SolveParam
         C.p[j] = pk;
         C.s[j] = sk;
         C.x[j] += alpha * pk;
-        rn[k] = C.r[j] - alpha * sk;
-        C.r[j] = rn[k];
+        C.r[j] -= alpha * sk;
       }
-      apply_minv(C.minv + 6 * i, rn, un);
-#pragma unroll
-      for (int k = 0; k < 3; ++k) C.ucg[3 * i + k] = un[k];
-      C.lm[i] = make_float4(un[0], un[1], un[2], 0.f);
-      if constexpr (!CL) publish_node(C, M, W, i, un, ep);
     }
+    // the peers read the shared u of this iteration before the reduction
+    // barrier above, so the preconditioner may overwrite it now
+    __syncthreads();
+    if (!apply_precond<CL>(C, M, W, P, ep, products)) return false;
     tock(C, PH_CG_UPDATE, t);
   }
   iters = it;
@@ -909,6 +976,7 @@ __device__ void setup_ctx(Ctx& C, const MeshDev& M, const WorkDev& W, const Smem
   C.acc = reinterpret_cast<float*>(at(L.acc));
   C.minv = reinterpret_cast<float*>(at(L.minv));
   C.hc = reinterpret_cast<float*>(at(L.hc));
+  C.cd = reinterpret_cast<float*>(at(L.cd));
   C.mask = at(L.mask);
   C.cursor = reinterpret_cast<int*>(at(L.cursor));
   C.hsrc = M.halo_src + C.halo0;
@@ -972,6 +1040,7 @@ __device__ bool solve_body(Ctx& C, const MeshDev& M, const WorkDev& W, const Sol
   const double* red_out = C.st->red_out;
   int status = ST_OK;
   int newton_total = 0, cg_total = 0, bt_total = 0, exact_total = 0;
+  long long products = 0;
   double rn = 0.0, scale = 1.0, energy = 0.0;
   int steps_done = 0;
   for (int step = 1; step <= P.n_steps; ++step) {
@@ -1051,7 +1120,7 @@ __device__ bool solve_body(Ctx& C, const MeshDev& M, const WorkDev& W, const Sol
       }
       int cg_it = 0;
       bool neg_curv = false;
-      if (!pcg<CL>(C, M, W, P, ep, n_pub, eta, 0.1 * P.tol * scale, cg_it, neg_curv)) return false;
+      if (!pcg<CL>(C, M, W, P, ep, n_pub, eta, 0.1 * P.tol * scale, cg_it, neg_curv, products)) return false;
       cg_step += cg_it;
       ++it;
       if (mode == 1) ++exact_total;
@@ -1123,6 +1192,7 @@ __device__ bool solve_body(Ctx& C, const MeshDev& M, const WorkDev& W, const Sol
     st->steps_done = steps_done;
     st->newton_total = newton_total;
     st->cg_total = cg_total;
+    st->products = products;
     st->backtracks_total = bt_total;
     st->residual = rn;
     st->scale = scale;
