@@ -607,7 +607,7 @@ def main():
                     help="offered request rates (req/s) of the serve workload")
     ap.add_argument("--serve-seconds", type=float, default=20.0)
     ap.add_argument("--drain-seconds", type=float, default=90.0)
-    ap.add_argument("--serve-class-cap", type=int, default=32,
+    ap.add_argument("--serve-class-cap", type=int, default=64,
                     help="largest CTA group of the request server (power of two)")
     ap.add_argument("--n-solves", type=int, default=None,
                     help="solves per step of the batched workloads (default 256 / 64)")

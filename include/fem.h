@@ -322,12 +322,17 @@ int fem_batch_tune(fem_mesh* const* meshes, const fem_indenter* indenters, int32
  * the smallest power of two up to opt->batch_parts, or 64, CTAs that keeps its
  * parts near opt->batch_tets_per_cta tets; one group per class, the remaining
  * SMs going one group at a time to the class with the most work per CTA when
- * requests are spread evenly over the pool). A host
- * thread admits submitted requests while result memory is free, publishes
- * them to the GPU through pinned host memory and collects the results; a
- * request that arrives while others run starts as soon as a group of its
- * class is idle. A request's result is bitwise independent of the others
- * (its partition depends only on its mesh).
+ * requests are spread evenly over the pool). A host thread admits submitted
+ * requests while result memory is free, publishes them to the GPU through
+ * pinned host memory and collects the results; a request that arrives while
+ * others run starts as soon as a group of its class is idle. Meshes with more
+ * than 64 x batch_tets_per_cta tets are served in whole-GPU passes: when one of
+ * their requests waits, the persistent launch finishes the solves it holds and
+ * leaves, the waiting large requests run one after another with the
+ * single-solve kernel on all SMs (fem_solve on the pool's handle, which the
+ * caller must not use meanwhile), and the persistent launch resumes. A
+ * request's result is bitwise independent of the others (its partition
+ * depends only on its mesh).
  */
 typedef struct fem_server fem_server;
 

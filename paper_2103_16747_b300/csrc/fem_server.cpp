@@ -13,6 +13,13 @@
 // engine and are put into the caller's node order on the host, so the only
 // kernel on the device is the persistent one. A request that arrives while
 // others run is picked up by the first idle group of its class.
+//
+// Meshes too large for a class of at most 64 CTAs (more than 64 x
+// batch_tets_per_cta tets) are served in whole-GPU passes: when one of their
+// requests waits, the dispatcher stops admitting, lets the persistent launch
+// finish the solves it holds and leave, runs the waiting large requests one
+// after another with the single-solve kernel on all SMs, and launches the
+// persistent kernel again (republishing the queued small requests).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -102,7 +109,13 @@ struct fem_server {
   std::condition_variable cv;
   std::thread th;
   std::atomic<bool> quit{false};
-  bool running = false;
+  bool running = false;             // a session is open (start .. stop)
+  bool kernel_live = false;         // the persistent launch is on the device
+  bool draining = false;            // stop word set for a whole-GPU pass
+  bool stopping = false;
+  bool big_busy = false;            // the dispatcher is running a whole-GPU solve
+  double session_end = 0.0;         // host clock at which the session ends
+  std::vector<char> big;            // per mesh: served in whole-GPU passes
   int64_t admitted = 0, completed = 0, rejected = 0;
 };
 
@@ -248,44 +261,144 @@ void finish(fem_server* v, int slot) {
   s.req = -1;
 }
 
+// Launch (or relaunch) the persistent kernel for the rest of the session;
+// requests already in result slots but not run are published again from the
+// start of their rings. Caller holds the lock.
+int launch_persistent(fem_server* v) {
+  const double left = v->session_end - now_s();
+  if (left <= 0.0) return FEM_OK;
+  CUDA_TRY(cudaMemsetAsync(v->ws, 0, v->jobs_off, v->ks), "reset");   // group counters, queue heads
+  for (size_t c = 0; c < v->class_parts.size(); ++c) v->h_tail[c] = 0;
+  const int n_slots = (int)v->slots.size();
+  for (int k = 0; k < n_slots; ++k) {
+    if (v->slots[k].state != SLOT_RUNNING) continue;
+    const int c = v->mesh_class[v->reqs[v->slots[k].req].mesh];
+    const int pos = v->h_tail[c];
+    v->h_ids[(size_t)c * n_slots + pos % n_slots] = k;
+    v->h_tail[c] = pos + 1;
+  }
+  __atomic_store_n(v->h_stop, 0, __ATOMIC_RELEASE);
+  const unsigned long long t0 = device_clock_ns();
+  if (!t0) return fail(FEM_ERR_CUDA, "could not read the device clock");
+  v->run.deadline_ns = t0 + (unsigned long long)(left * 1e9);
+  CUDA_TRY(launch_groups(v->run, v->S, v->L, v->n_ctas, v->ks, nullptr), "server kernel");
+  v->kernel_live = true;
+  v->draining = false;
+  return FEM_OK;
+}
+
+// One large request on all SMs (the single-solve kernel); the lock is
+// released while it runs.
+void run_big(fem_server* v, std::unique_lock<std::mutex>& lk, int64_t id) {
+  Request& q0 = v->reqs[id];
+  fem_mesh* m = v->meshes[q0.mesh];
+  const fem_indenter ind = q0.ind;
+  const std::vector<double> depths = q0.depths;
+  const double tol = q0.tol;
+  std::vector<double> u(3 * (size_t)m->n_nodes), force(3 * (size_t)ind.n_steps);
+  q0.state = 1;
+  q0.t_admit = now_s();
+  v->big_busy = true;
+  lk.unlock();
+  fem_stats st;
+  memset(&st, 0, sizeof(st));
+  int rc = fem_set_indenter(m, ind.shape, ind.pose, ind.params, ind.dir, depths.data(), ind.n_steps);
+  if (rc == FEM_OK) rc = fem_solve(m, ind.n_steps, tol, &v->o, u.data(), force.data(), nullptr, &st);
+  lk.lock();
+  v->big_busy = false;
+  Request& q = v->reqs[id];
+  q.u = std::move(u);
+  q.force = std::move(force);
+  q.stats = st;
+  q.rc = rc;
+  q.t_done = now_s();
+  q.state = 2;
+  ++v->admitted;
+  ++v->completed;
+}
+
+// Start the copy-out of every solve the kernel reported done and finish the
+// requests whose copies arrived (with wait, block until they have). Caller
+// holds the lock. Returns whether anything happened.
+bool retire(fem_server* v, bool wait) {
+  const ResLayout R = res_layout(v->max_nodes, v->max_steps);
+  const int n_slots = (int)v->slots.size();
+  bool worked = false;
+  for (int k = 0; k < n_slots; ++k) {
+    Slot& s = v->slots[k];
+    if (s.state == SLOT_RUNNING && __atomic_load_n(&v->h_done[k], __ATOMIC_ACQUIRE)) {
+      __atomic_store_n(&v->h_done[k], 0, __ATOMIC_RELAXED);
+      const fem_mesh* m = v->meshes[v->reqs[s.req].mesh];
+      cudaMemcpyAsync(s.h_u, slot_ptr(v, k, R.u), 24 * (size_t)m->n_nodes, cudaMemcpyDeviceToHost, v->cs);
+      cudaMemcpyAsync(s.h_force, slot_ptr(v, k, R.force), 24 * (size_t)v->max_steps, cudaMemcpyDeviceToHost, v->cs);
+      cudaMemcpyAsync(s.h_stats, slot_ptr(v, k, R.stats), sizeof(StatsDev), cudaMemcpyDeviceToHost, v->cs);
+      cudaEventRecord(s.ev, v->cs);
+      s.state = SLOT_COPYING;
+      worked = true;
+    }
+  }
+  if (wait) cudaStreamSynchronize(v->cs);
+  for (int k = 0; k < n_slots; ++k) {
+    Slot& s = v->slots[k];
+    if (s.state == SLOT_COPYING && cudaEventQuery(s.ev) == cudaSuccess) {
+      finish(v, k);
+      worked = true;
+    }
+  }
+  return worked;
+}
+
 void dispatcher(fem_server* v) {
   cudaSetDevice(v->device);
-  const ResLayout R = res_layout(v->max_nodes, v->max_steps);
   const int n_slots = (int)v->slots.size();
   while (!v->quit.load()) {
     bool worked = false;
     {
       std::unique_lock<std::mutex> lk(v->mu);
-      for (int k = 0; k < n_slots; ++k) {
-        Slot& s = v->slots[k];
-        if (s.state == SLOT_RUNNING && __atomic_load_n(&v->h_done[k], __ATOMIC_ACQUIRE)) {
-          __atomic_store_n(&v->h_done[k], 0, __ATOMIC_RELAXED);
-          const fem_mesh* m = v->meshes[v->reqs[s.req].mesh];
-          cudaMemcpyAsync(s.h_u, slot_ptr(v, k, R.u), 24 * (size_t)m->n_nodes, cudaMemcpyDeviceToHost, v->cs);
-          cudaMemcpyAsync(s.h_force, slot_ptr(v, k, R.force), 24 * (size_t)v->max_steps, cudaMemcpyDeviceToHost,
-                          v->cs);
-          cudaMemcpyAsync(s.h_stats, slot_ptr(v, k, R.stats), sizeof(StatsDev), cudaMemcpyDeviceToHost, v->cs);
-          cudaEventRecord(s.ev, v->cs);
-          s.state = SLOT_COPYING;
+      worked |= retire(v, false);
+      if (v->running && !v->stopping) {
+        const bool big_waiting = std::any_of(v->pending.begin(), v->pending.end(),
+                                             [&](int64_t id) { return v->big[v->reqs[id].mesh] != 0; });
+        if (v->kernel_live && big_waiting && !v->draining) {
+          __atomic_store_n(v->h_stop, 1, __ATOMIC_RELEASE);   // idle groups leave, busy ones finish first
+          v->draining = true;
           worked = true;
         }
-      }
-      for (int k = 0; k < n_slots; ++k) {
-        Slot& s = v->slots[k];
-        if (s.state == SLOT_COPYING && cudaEventQuery(s.ev) == cudaSuccess) {
-          finish(v, k);
+        if (v->kernel_live && cudaStreamQuery(v->ks) != cudaErrorNotReady) {
+          v->kernel_live = false;   // drained (or the session deadline passed)
+          // done words set after this iteration's first pass: retire them now,
+          // before any relaunch republishes the solves that were not run
+          retire(v, true);
           worked = true;
         }
-      }
-      for (int k = 0; k < n_slots && !v->pending.empty(); ++k) {
-        if (v->slots[k].state != SLOT_FREE || !v->running) continue;
-        const int64_t id = v->pending.front();
-        v->pending.pop_front();
-        if (!admit(v, k, v->reqs[id])) {
-          v->reqs[id].rc = FEM_ERR_CUDA;
-          v->reqs[id].state = 2;
+        if (!v->kernel_live && v->draining) {
+          // whole-GPU pass: every waiting large request, in arrival order
+          for (;;) {
+            auto it = std::find_if(v->pending.begin(), v->pending.end(),
+                                   [&](int64_t id) { return v->big[v->reqs[id].mesh] != 0; });
+            if (it == v->pending.end() || v->stopping) break;
+            const int64_t id = *it;
+            v->pending.erase(it);
+            run_big(v, lk, id);
+          }
+          v->draining = false;
+          if (!v->stopping && launch_persistent(v) != FEM_OK) v->stopping = true;
+          worked = true;
         }
-        worked = true;
+        // small requests into free result slots while the persistent launch serves
+        for (auto it = v->pending.begin(); it != v->pending.end() && v->kernel_live && !v->draining;) {
+          if (v->big[v->reqs[*it].mesh]) { ++it; continue; }
+          int k = 0;
+          while (k < n_slots && v->slots[k].state != SLOT_FREE) ++k;
+          if (k == n_slots) break;
+          const int64_t id = *it;
+          it = v->pending.erase(it);
+          if (!admit(v, k, v->reqs[id])) {
+            v->reqs[id].rc = FEM_ERR_CUDA;
+            v->reqs[id].state = 2;
+          }
+          worked = true;
+        }
       }
       if (worked) v->cv.notify_all();
     }
@@ -329,15 +442,20 @@ int fem_server_create(fem_mesh* const* meshes, int32_t n_meshes, int32_t max_ste
     while (pcap * 2 <= std::min(o.batch_parts, 64)) pcap *= 2;
   }
   std::vector<int> parts(n_meshes);
+  std::vector<char> big(n_meshes, 0);
   for (int i = 0; i < n_meshes; ++i) {
     int p = 1;
     while (p < pcap && (int64_t)p * T < meshes[i]->n_tets && 2 * p <= meshes[i]->n_nodes) p *= 2;
     parts[i] = std::min(p, n_sm);
+    // too large for the largest class: whole-GPU passes
+    big[i] = (int64_t)64 * T < meshes[i]->n_tets ? 1 : 0;
   }
+  if (std::all_of(big.begin(), big.end(), [](char b) { return b != 0; })) big.assign(n_meshes, 0);
   std::vector<const MeshDev*> part(n_meshes);
   PartDims dims{0, 0, 0, 0};
   size_t max_nodes = 0, max_pt = 0;
   for (int i = 0; i < n_meshes; ++i) {
+    if (big[i]) continue;
     const PartDims* pd = nullptr;
     int rc = batch_partition(meshes[i], parts[i], &part[i], &pd);
     if (rc) return rc;
@@ -357,6 +475,10 @@ int fem_server_create(fem_mesh* const* meshes, int32_t n_meshes, int32_t max_ste
   std::vector<int> class_parts, mesh_class(n_meshes);
   std::vector<double> class_work;
   for (int i = 0; i < n_meshes; ++i) {
+    if (big[i]) {
+      mesh_class[i] = -1;
+      continue;
+    }
     int c = (int)(std::find(class_parts.begin(), class_parts.end(), parts[i]) - class_parts.begin());
     if (c == (int)class_parts.size()) {
       class_parts.push_back(parts[i]);
@@ -406,6 +528,7 @@ int fem_server_create(fem_mesh* const* meshes, int32_t n_meshes, int32_t max_ste
   v->max_steps = max_steps;
   v->meshes.assign(meshes, meshes + n_meshes);
   v->mesh_class = mesh_class;
+  v->big = big;
   v->mesh_part = part;
   v->class_parts = class_parts;
   v->class_groups = class_groups;
@@ -519,15 +642,12 @@ int fem_server_start(fem_server* v, double max_seconds) {
   std::unique_lock<std::mutex> lk(v->mu);
   if (v->running) return fail(FEM_ERR_ARG, "the server is already running");
   CUDA_TRY(cudaSetDevice(v->device), "device");
-  // fresh group counters and queue positions for this session
-  CUDA_TRY(cudaMemsetAsync(v->ws, 0, v->jobs_off, v->ks), "reset");
-  for (size_t c = 0; c < v->class_parts.size(); ++c) v->h_tail[c] = 0;
   for (size_t k = 0; k < v->slots.size(); ++k) v->h_done[k] = 0;
-  *v->h_stop = 0;
-  const unsigned long long t0 = device_clock_ns();
-  if (!t0) return fail(FEM_ERR_CUDA, "could not read the device clock");
-  v->run.deadline_ns = t0 + (unsigned long long)(max_seconds * 1e9);
-  CUDA_TRY(launch_groups(v->run, v->S, v->L, v->n_ctas, v->ks, nullptr), "server kernel");
+  v->session_end = now_s() + max_seconds;
+  v->stopping = false;
+  v->draining = false;
+  const int rc = launch_persistent(v);
+  if (rc) return rc;
   v->running = true;
   return FEM_OK;
 }
@@ -597,15 +717,17 @@ int fem_server_stop(fem_server* v) {
   {
     std::unique_lock<std::mutex> lk(v->mu);
     if (!v->running) return FEM_OK;
+    v->stopping = true;   // no further whole-GPU pass or relaunch
     __atomic_store_n(v->h_stop, 1, __ATOMIC_RELEASE);
   }
-  // groups finish the solve they hold, then leave
+  // groups finish the solve they hold, then leave; a whole-GPU solve in
+  // progress finishes too
   const cudaError_t e = cudaStreamSynchronize(v->ks);
-  // let the dispatcher retire the solves that finished (bounded: 1 s)
-  for (int k = 0; k < 1000; ++k) {
+  for (int k = 0; k < 600000; ++k) {   // bounded: 10 min for a running whole-GPU solve
     bool busy = false;
     {
       std::unique_lock<std::mutex> lk(v->mu);
+      busy = v->big_busy;
       for (size_t j = 0; j < v->slots.size(); ++j)
         busy |= v->slots[j].state == SLOT_COPYING ||
                 (v->slots[j].state == SLOT_RUNNING && __atomic_load_n(&v->h_done[j], __ATOMIC_ACQUIRE));
@@ -615,6 +737,7 @@ int fem_server_stop(fem_server* v) {
   }
   std::unique_lock<std::mutex> lk(v->mu);
   v->running = false;
+  v->kernel_live = false;
   // whatever was not run is reported as not run
   for (Slot& s : v->slots)
     if (s.state == SLOT_RUNNING) {

@@ -74,3 +74,54 @@ def test_server_alone_equals_mix_and_matches_oracle(F):
     srv.close()
     for h in handles:
         F.fem_destroy_mesh(h)
+
+
+def test_server_whole_gpu_passes_for_large_meshes(F):
+    """Meshes too large for a 64-CTA class (here: more than 64 x 100 tets)
+    are served in whole-GPU passes between runs of the persistent launch: a
+    large request's result equals a direct fem_solve, a small one's result
+    equals the same request served alone."""
+    cube, cube_ind = W.cube_sphere()
+    pool = [cube] + [m for m, _ in W.uneven_fingertips(2, seed=21, tet_min=8e3, tet_max=1.2e4)]
+    assert all(m.n_tets > 6400 for m in pool[1:])
+    handles = [F.fem_create_mesh(m.nodes, m.tets, m.tet_material, m.materials, m.fixed_nodes) for m in pool]
+    draws = {k: W.draw_indentations(pool[k], 2, seed=300 + k) for k in range(1, len(pool))}
+    opt = F.fem_default_options()
+    opt.max_newton = 200
+    opt.batch_tets_per_cta = 100
+    # direct single solves of the large requests (reference)
+    ref = {}
+    for k in range(1, len(pool)):
+        for j, d in enumerate(draws[k]):
+            s = F.IndentationSolver(pool[k])
+            s.set_indenter(d)
+            r = s.solve(1e-6, opt, check=False)
+            ref[(k, j)] = (r["rc"], r["u"], r["step_force"])
+            s.close()
+    srv = F.FemServer(handles, 20, opt, result_bytes=32 << 20)
+    srv.start(120.0)
+    rc, rid = srv.submit(0, cube_ind, 1e-6)
+    alone = srv.result(rid, cube.n_nodes, 10, wait_ms=100000)
+    assert alone[0] == 0
+    ids = []
+    for rep in range(2):
+        rc, rid = srv.submit(0, cube_ind, 1e-6)
+        ids.append((rid, 0, None))
+        for k in range(1, len(pool)):
+            for j, d in enumerate(draws[k]):
+                rc, rid = srv.submit(k, d, 1e-6)
+                assert rc == 0
+                ids.append((rid, k, j))
+    for rid, k, j in ids:
+        n_steps = 10 if k == 0 else 20
+        r = srv.result(rid, pool[k].n_nodes, n_steps, wait_ms=100000)
+        assert r[0] != F.FEM_PENDING
+        if k == 0:
+            assert r[0] == 0 and np.array_equal(r[1], alone[1]) and np.array_equal(r[2], alone[2])
+        else:
+            rc_ref, u_ref, f_ref = ref[(k, j)]
+            assert r[0] == rc_ref and np.array_equal(r[1], u_ref) and np.array_equal(r[2], f_ref), (k, j)
+    assert srv.stop() == 0
+    srv.close()
+    for h in handles:
+        F.fem_destroy_mesh(h)
