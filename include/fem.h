@@ -401,6 +401,16 @@ int fem_mesh_info_get(const fem_mesh* mesh, fem_mesh_info* info);
  */
 int fem_repartition(fem_mesh* mesh, int32_t n_parts);
 
+/*
+ * Element stress output (the paper's simulator reports element stress
+ * tensors, Sec. III-A): Cauchy stress and von Mises equivalent stress of every
+ * tet at displacement u [n_nodes*3] (caller node order, host or device), FP64.
+ *   out_cauchy     [n_tets*6] per tet (xx, yy, zz, yz, xz, xy), caller tet order.
+ *   out_von_mises  [n_tets] sqrt(3/2 s:s) of the deviator, or NULL.
+ * Errors: FEM_ERR_ARG, FEM_ERR_OOM, FEM_ERR_CUDA.
+ */
+int fem_element_stress(fem_mesh* mesh, const double* u, double* out_cauchy, double* out_von_mises);
+
 /* ------------------------------------------------------- diagnostics
  * Single passes of the hot-path kernels, for parity tests. They run the same
  * device code as fem_solve (same kernel, one phase) on a caller-supplied

@@ -74,3 +74,18 @@ def project_psd(C):
     w, Q = np.linalg.eigh(Cs)
     w = np.maximum(w, 0.0)
     return np.einsum("...ik,...k,...jk->...ij", Q, w, Q)
+
+
+def cauchy(F, mu, lam):
+    """Cauchy stress sigma = P F^T / J (Sec. III-A of the paper reports element
+    stress tensors; this is their true-stress form). Computed from pk1, the
+    definition, so that a mistake in either shows in the pins below."""
+    J = np.linalg.det(F)
+    return pk1(F, mu, lam) @ np.swapaxes(F, -1, -2) / J[..., None, None]
+
+
+def von_mises(sigma):
+    """Equivalent stress sqrt(3/2 s:s) of the deviator s = sigma - tr(sigma)/3 I."""
+    tr = np.trace(sigma, axis1=-2, axis2=-1)
+    s = sigma - tr[..., None, None] / 3.0 * np.eye(3)
+    return np.sqrt(1.5 * np.einsum("...ij,...ij->...", s, s))

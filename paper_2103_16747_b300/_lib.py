@@ -44,7 +44,8 @@ EXPORTS = ("fem_default_options", "fem_create_mesh", "fem_set_indenter", "fem_se
            "fem_eval_residual", "fem_eval_residual_noalloc", "fem_apply_tangent",
            "fem_debug_barrier_timeout", "fem_batch_create", "fem_batch_run", "fem_batch_info_get",
            "fem_batch_destroy", "fem_batch_tune", "fem_server_create", "fem_server_start", "fem_server_submit",
-           "fem_server_result", "fem_server_stop", "fem_server_info_get", "fem_server_destroy")
+           "fem_server_result", "fem_server_stop", "fem_server_info_get", "fem_server_destroy",
+           "fem_element_stress")
 
 
 class fem_material(C.Structure):
@@ -143,6 +144,7 @@ def _load():
         "fem_server_stop": (C.c_int, [P]),
         "fem_server_info_get": (C.c_int, [P, C.POINTER(fem_server_info)]),
         "fem_server_destroy": (None, [P]),
+        "fem_element_stress": (C.c_int, [P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -401,6 +403,17 @@ class FemBatch:
             self.close()
         except Exception:
             pass
+
+
+def fem_element_stress(mesh, u, n_tets, out_cauchy=None, out_von_mises=None):
+    """Cauchy stress (n_tets, 6: xx yy zz yz xz xy) and von Mises stress
+    (n_tets,) at displacement u (caller orders). Returns (sigma, von_mises)."""
+    keep = []
+    sig = np.zeros((n_tets, 6)) if out_cauchy is None else out_cauchy
+    vm = np.zeros(n_tets) if out_von_mises is None else out_von_mises
+    _check(lib.fem_element_stress(mesh, _ptr(u, np.float64, keep), _out_ptr(sig, np.float64, keep),
+                                  _out_ptr(vm, np.float64, keep)))
+    return sig, vm
 
 
 def fem_destroy_mesh(mesh):

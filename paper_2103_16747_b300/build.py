@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libfem_b300.so")
-SOURCES = ["fem_solve.cu", "fem_api.cpp", "fem_batch.cpp", "fem_server.cpp"]
+SOURCES = ["fem_solve.cu", "fem_stress.cu", "fem_api.cpp", "fem_batch.cpp", "fem_server.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

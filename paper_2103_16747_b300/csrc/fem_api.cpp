@@ -669,8 +669,10 @@ int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, i
   m->dminv.resize(9 * (size_t)Nt);
   m->vol.resize(Nt);
   m->mat.resize(Nt);
+  m->tet_perm.resize(Nt);
   for (int t = 0; t < Nt; ++t) {
     const int to = tkey[t].second;
+    m->tet_perm[t] = to;
     for (int a = 0; a < 4; ++a) m->tets_new[4 * (size_t)t + a] = iperm[tets[4 * to + a]];
     for (int k = 0; k < 9; ++k) m->dminv[9 * (size_t)t + k] = dminv_old[9 * (size_t)to + k];
     m->vol[t] = vol_old[to];
@@ -1132,6 +1134,38 @@ int fem_apply_tangent(fem_mesh* m, const double* u, int32_t step, const fem_opti
   if ((rc = run_kernel(m, m->work, P, nullptr, &hst))) return rc;
   if ((rc = copy_out_nodes(m, m->work.out_y, out_y))) return rc;
   CUDA_TRY(cudaStreamSynchronize(m->stream), "output copy");
+  return FEM_OK;
+}
+
+int fem_element_stress(fem_mesh* m, const double* u, double* out_cauchy, double* out_von_mises) {
+  g_err.clear();
+  if (!m || !u || !out_cauchy) return fail(FEM_ERR_ARG, "NULL argument");
+  const size_t Nt = (size_t)m->n_tets;
+  cudaStream_t s = m->stream;
+  if (!m->d_stress_tets) {
+    std::vector<int4> t4(Nt);
+    std::vector<double> dm((size_t)9 * Nt);
+    for (size_t t = 0; t < Nt; ++t) {
+      t4[t] = make_int4(m->tets_new[4 * t], m->tets_new[4 * t + 1], m->tets_new[4 * t + 2], m->tets_new[4 * t + 3]);
+      for (int k = 0; k < 9; ++k) dm[(size_t)k * Nt + t] = m->dminv[9 * t + k];
+    }
+    CUDA_TRY(upload(&m->d_stress_tets, t4, s, m->owned, m->bytes), "upload");
+    CUDA_TRY(upload(&m->d_stress_dminv, dm, s, m->owned, m->bytes), "upload");
+    CUDA_TRY(upload(&m->d_stress_mat, m->mat, s, m->owned, m->bytes), "upload");
+    CUDA_TRY(upload(&m->d_tet_perm, m->tet_perm, s, m->owned, m->bytes), "upload");
+    CUDA_TRY(alloc(&m->d_stress_u, 3 * (size_t)m->n_nodes, m->owned, m->bytes), "alloc");
+    CUDA_TRY(alloc(&m->d_stress_out, 7 * Nt, m->owned, m->bytes), "alloc");
+  }
+  int rc = copy_in_nodes(m, u, m->d_stress_u);
+  if (rc) return rc;
+  double* sig = m->d_stress_out;
+  double* vm = m->d_stress_out + 6 * Nt;
+  CUDA_TRY(launch_stress(m->d_stress_tets, m->d_stress_dminv, m->d_stress_mat, m->dev.lame, m->d_stress_u,
+                         m->d_tet_perm, (int)Nt, sig, vm, s), "stress kernel");
+  CUDA_TRY(cudaMemcpyAsync(out_cauchy, sig, sizeof(double) * 6 * Nt, cudaMemcpyDefault, s), "output copy");
+  if (out_von_mises)
+    CUDA_TRY(cudaMemcpyAsync(out_von_mises, vm, sizeof(double) * Nt, cudaMemcpyDefault, s), "output copy");
+  CUDA_TRY(cudaStreamSynchronize(s), "stress");
   return FEM_OK;
 }
 

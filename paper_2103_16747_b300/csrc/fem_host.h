@@ -53,6 +53,14 @@ struct fem_mesh {
   double* d_presc = nullptr;
   double* d_stage = nullptr;     // 3*n_nodes staging in caller order
   int* d_perm = nullptr;         // new -> caller
+  std::vector<int> tet_perm;     // sorted tet -> caller tet
+  // element stress output (uploaded on first use)
+  int4* d_stress_tets = nullptr;
+  double* d_stress_dminv = nullptr;
+  int* d_stress_mat = nullptr;
+  int* d_tet_perm = nullptr;
+  double* d_stress_u = nullptr;
+  double* d_stress_out = nullptr;   // [7 Nt]: sigma (6 per tet), von Mises
 };
 
 namespace fem {

@@ -192,6 +192,11 @@ cudaError_t launch_solve(const MeshDev& mesh, const WorkDev& work, const SolvePa
                          cudaStream_t stream, float* kernel_ms);
 cudaError_t solve_kernel_attrs(int smem_bytes, int* static_smem, int* blocks_per_sm);
 
+// Element stress of every tet at u (fem_stress.cu); sig and vm in caller tet order.
+cudaError_t launch_stress(const int4* tets, const double* dminv, const int* mat, const double* lame,
+                          const double* u, const int* tet_perm, int n_tets, double* sig, double* vm,
+                          cudaStream_t s);
+
 // Fixed scratch block for fem_eval_residual_noalloc (fem_solve.cu).
 constexpr size_t kNoAllocScratchBytes = 8u << 20;
 constexpr int kMaxDevices = 64;
