@@ -18,6 +18,9 @@ Batched workloads print their own line:
   --workload uneven  one step = 64 fingertips of uneven size (R 5-10 mm,
                      5k-200k tets log-uniform), one random indentation each,
                      in one launch; the slot shape comes from fem_batch_tune.
+  --workload dynamic the fingertip solve as 20 backward-Euler time steps of
+                     1e-4 s (the paper's implicit time step) from rest, with
+                     the lumped mass of a 1100 kg/m^3 body; same line format.
   --workload serve   Poisson streams of requests over a resident pool of 16
                      fingertip meshes (5k-200k tets) through the request
                      server (continuous batching), one session per offered
@@ -25,7 +28,7 @@ Batched workloads print their own line:
                      one-solve-per-launch path on the same arrival trace.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference]
-                    [--workload fingertip|batch|uneven|serve]
+                    [--workload fingertip|dynamic|batch|uneven|serve]
 
 Multi-GPU runs (torchrun) are independent replicas: every rank solves its own
 indentation, no collectives on the data path (weak scaling).
@@ -52,6 +55,9 @@ TOL = 1e-6
 WORKLOAD = ("fingertip_sphere: two-layer half-capsule fingertip R=7 mm L=40 mm (1 mm skin "
             "E=1.5 MPa nu=0.45 over 2 mm inner E=0.2 MPa nu=0.48, core fixed), 38880 tets / "
             "8740 nodes; sphere r=4 mm pressed 2 mm normal to a seeded skin point in 20 load steps")
+DYN_DT, DYN_DENSITY = 1e-4, 1.1e-9     # s; t/mm^3 (1100 kg/m^3)
+DYN_WORKLOAD = (WORKLOAD + f"; dynamic: each load step one backward-Euler time step of {DYN_DT:g} s from rest, "
+                f"lumped mass of density {DYN_DENSITY:g} t/mm^3")
 
 
 def replica_seed(rank: int) -> int:
@@ -190,7 +196,7 @@ def profiled_traffic():
         return None
 
 
-def cpu_oracle_rate(mesh, ind, n_load_steps):
+def cpu_oracle_rate(mesh, ind, n_load_steps, dynamic=False):
     """Time the oracle (as it stands) on the first n_load_steps of the same
     solve and extrapolate to a full solve by Newton iterations, using the
     oracle's Newton count for the full solve stored in tests/golden."""
@@ -200,13 +206,14 @@ def cpu_oracle_rate(mesh, ind, n_load_steps):
         def threadpool_info():
             return [{"num_threads": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))}]
     from oracle import Problem
-    p = Problem(mesh, ind)
+    p = Problem(mesh, ind, dt=DYN_DT, density=DYN_DENSITY) if dynamic else Problem(mesh, ind)
     t0 = time.perf_counter()
     r = p.solve(tol=1e-10, load_steps=n_load_steps)
     dt = time.perf_counter() - t0
     its = int(np.sum(r.newton_iters[:n_load_steps]))
     full_its = None
-    g = os.path.join(ROOT, "tests", "golden", "fingertip_sphere_oracle.npz")
+    g = os.path.join(ROOT, "tests", "golden",
+                     "fingertip_sphere_dynamic_oracle.npz" if dynamic else "fingertip_sphere_oracle.npz")
     if os.path.exists(g):
         full_its = int(np.sum(np.load(g)["newton_iters"]))
     per_it = dt / max(its, 1)
@@ -226,12 +233,13 @@ def run_reference(args, rank, world):
         return
     import workloads as W
     mesh, ind = W.fingertip_sphere()
+    dyn = args.workload == "dynamic"
     for _ in range(args.warmup):
-        cpu_oracle_rate(mesh, ind, 1)
+        cpu_oracle_rate(mesh, ind, 1, dyn)
     times, rates = [], []
     cores = 1
     for _ in range(args.steps):
-        r = cpu_oracle_rate(mesh, ind, 1)
+        r = cpu_oracle_rate(mesh, ind, 1, dyn)
         times.append(r["seconds"])
         rates.append(r["value"])
         cores = r["cores"]
@@ -239,7 +247,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "tol": TOL},
+            "data": "synthetic", "config": {"workload": DYN_WORKLOAD if dyn else WORKLOAD, "tol": TOL},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "each step: load step 1 of 20 of the solve, extrapolated by "
                                        "Newton iterations to a full solve"},
@@ -263,6 +271,9 @@ def run_cuda(args, rank, world, local):
     solver.set_indenter(ind)
     info = solver.info()
     opt = F.fem_default_options()
+    dyn = args.workload == "dynamic"
+    if dyn:
+        opt.dt, opt.density = DYN_DT, DYN_DENSITY
     n = mesh.n_nodes
     d_u = torch.zeros((n, 3), dtype=torch.float64, device=dev)
     d_f = torch.zeros((ind.n_steps, 3), dtype=torch.float64, device=dev)
@@ -333,7 +344,7 @@ def run_cuda(args, rank, world, local):
             "warmup": args.warmup, "ms_per_step": total * 1000.0 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 (tangent, PCG vectors) + f64 (residual, "
             "energy, reductions, displacement)", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "tol": TOL, "n_parts": info.n_parts,
+            "config": {"workload": DYN_WORKLOAD if dyn else WORKLOAD, "tol": TOL, "n_parts": info.n_parts,
                        "l2": "flushed between timed steps (256 MiB write, L2 is 126 MB)",
                        "replicas": world, "newton_iters": s0.newton_iters, "cg_iters": s0.cg_iters,
                        "tangent_products": s0.tangent_products, "backtracks": s0.backtracks,
@@ -349,7 +360,7 @@ def run_cuda(args, rank, world, local):
                          "compact_accounting_GBs": cmp_b / (kms / 1000.0) / 1e9},
             "clocks": clk.summary()}
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = {k: v for k, v in cpu_oracle_rate(mesh, ind, 2).items() if k != "seconds"}
+        line["cpu_baseline"] = {k: v for k, v in cpu_oracle_rate(mesh, ind, 2, dyn).items() if k != "seconds"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     solver.close()
@@ -602,7 +613,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["fingertip", "batch", "uneven", "serve"], default="fingertip")
+    ap.add_argument("--workload", choices=["fingertip", "dynamic", "batch", "uneven", "serve"],
+                    default="fingertip")
     ap.add_argument("--rates", type=float, nargs="+", default=[1.0, 2.0, 4.0, 8.0, 16.0],
                     help="offered request rates (req/s) of the serve workload")
     ap.add_argument("--serve-seconds", type=float, default=20.0)
@@ -617,7 +629,7 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
-    elif args.workload == "fingertip":
+    elif args.workload in ("fingertip", "dynamic"):
         run_cuda(args, rank, world, local)
     elif args.workload == "serve":
         run_serve(args, rank, world, local)

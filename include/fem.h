@@ -97,6 +97,14 @@ typedef struct {
                               /* preconditioned tangent (d tangent products and one  */
                               /* reduction per PCG iteration; default 5)              */
     double  precond_ratio;    /* Chebyshev interval [4/ratio, 4] (default 60)          */
+    double  dt;               /* load-step time step: 0 = quasi-static (default); > 0 */
+                              /* = dynamic implicit stepping (backward Euler, lumped  */
+                              /* mass): each load step of fem_solve, fem_solve_batch, */
+                              /* fem_batch_run and the server is one time step of     */
+                              /* length dt, starting from rest                         */
+    double  density;          /* mass density for dt > 0, in the mesh's mass unit per */
+                              /* unit volume (default 1.1e-9: 1100 kg/m^3 in t/mm^3   */
+                              /* for coordinates in mm and moduli in MPa)             */
 } fem_options;
 
 /* engines of fem_solve_batch */

@@ -28,6 +28,21 @@ this oracle solves the quasi-static problem plainly:
 
 Prescribed (Dirichlet) values, when given, are ramped linearly over the load
 steps: at step k the fixed DOFs hold values * k / K.
+
+Dynamic stepping (dt > 0). The paper integrates the deformable body's dynamics
+implicitly in time, with a time step of 1e-4 s (Sec. III-A). Reading: backward
+(implicit) Euler with a lumped mass matrix, m_i = rho * sum over the tets at
+node i of V_e / 4. Every load step is then one time step. Its solution is the
+minimiser of the incremental potential
+
+    Phi_k(u) = Pi_k(u) + sum_{i, free DOFs} m_i / (2 dt^2) (u_i - u~_i)^2,
+    u~ = u_{k-1} + dt v_{k-1},
+
+and the velocity is updated afterwards as v_k = (u_k - u_{k-1}) / dt. Setting
+the gradient to zero gives m (v_k - v_{k-1}) / dt = -grad Pi_k(u_k), which is
+backward Euler. Prescribed components carry no inertia term, because on them
+the term would only be a constant. The body starts at rest unless a v0 is
+given (only the oracle takes v0; the pins use it).
 """
 from __future__ import annotations
 
@@ -57,7 +72,8 @@ class SolveResult:
 class Problem:
     """One mesh + one indenter (+ optional prescribed values on fixed DOFs)."""
 
-    def __init__(self, mesh, indenter, c_kappa: float = 100.0, dirichlet_values=None):
+    def __init__(self, mesh, indenter, c_kappa: float = 100.0, dirichlet_values=None,
+                 dt: float = 0.0, density: float = 1.1e-9):
         self.X = np.asarray(mesh.nodes, dtype=np.float64)
         self.tets = np.asarray(mesh.tets, dtype=np.int64)
         self.n = len(self.X)
@@ -65,6 +81,9 @@ class Problem:
         tm = np.asarray(mesh.tet_material, dtype=np.int64)
         self.E = mats[tm, 0]
         self.mu, self.lam = material.lame(mats[tm, 0], mats[tm, 1])
+        # element law per material: column 2 (if present) 0 neo-Hookean, 1 co-rotational
+        self.model = (mats[tm, 2].astype(np.int64) if mats.shape[1] > 2
+                      else np.zeros(len(tm), dtype=np.int64))
         _, self.Dminv, self.V = geometry.shape_matrices(self.X, self.tets)
         if np.any(self.V <= 0):
             raise ValueError("non-positive tet volume")
@@ -73,6 +92,12 @@ class Problem:
         self.free = ~self.fixed.ravel()
         self.k, self.h_bar, _ = geometry.penalty_stiffness(
             self.X, self.tets, self.E, self.fixed, c_kappa)
+        # lumped mass: a quarter of each tet's mass to each of its nodes
+        self.dt = float(dt)
+        self.mass = np.zeros(self.n)
+        for a in range(4):
+            np.add.at(self.mass, self.tets[:, a], 0.25 * float(density) * self.V)
+        self.u_tilde = None      # inertial prediction u~ of the current time step (dt > 0)
         self.E_max = float(self.E.max())
         self.scale_floor = self.E_max * self.h_bar ** 2 * 1e-3
         self.u_presc = np.zeros((self.n, 3))
@@ -107,11 +132,12 @@ class Problem:
         J = np.linalg.det(F)
         if np.any(J <= 0):
             return np.inf, float(J.min())
-        return float(np.sum(self.V * material.energy_density(F, self.mu, self.lam))), float(J.min())
+        psi = material.law_energy_density(F, self.mu, self.lam, self.model)
+        return float(np.sum(self.V * psi)), float(J.min())
 
     def elastic_gradient(self, u):
         """Nodal gradient of the elastic energy (Nn, 3): sum_e V_e P_e grad N_a."""
-        P = material.pk1(self.F(u), self.mu, self.lam)
+        P = material.law_pk1(self.F(u), self.mu, self.lam, self.model)
         fe = np.einsum("e,eij,eaj->eai", self.V, P, self.grads)
         g = np.zeros((self.n, 3))
         for a in range(4):
@@ -120,7 +146,7 @@ class Problem:
 
     def element_tangents(self, u, projected=False):
         """Element stiffness (Nt, 12, 12) = V B^T C B."""
-        C = material.dpdf(self.F(u), self.mu, self.lam)
+        C = material.law_dpdf(self.F(u), self.mu, self.lam, self.model)
         if projected:
             C = material.project_psd(C)
         C4 = C.reshape(-1, 3, 3, 3, 3)
@@ -132,15 +158,27 @@ class Problem:
         x = self.X + u
         return contact.penalty(self.shape, self.origin_at(step), self.R, self.params, x, self.k)
 
+    def inertia_terms(self, u):
+        """(energy, gradient (Nn,3), diagonal (Nn,3)) of the backward-Euler
+        inertia term sum_free m_i/(2 dt^2) |u_i - u~_i|^2; zeros when
+        quasi-static."""
+        if self.dt <= 0.0 or self.u_tilde is None:
+            z = np.zeros((self.n, 3))
+            return 0.0, z, z
+        w = np.where(self.fixed, 0.0, (self.mass / self.dt ** 2)[:, None])
+        d = u - self.u_tilde
+        return float(0.5 * np.sum(w * d * d)), w * d, w
+
     def energy(self, u, step):
         Ee, minJ = self.elastic_energy(u)
         ec = self.contact_terms(u, step)[0]
-        return Ee + float(ec.sum()), minJ
+        return Ee + float(ec.sum()) + self.inertia_terms(u)[0], minJ
 
     def gradient(self, u, step):
-        """(R, f_c): full gradient of Pi (Nn,3) and nodal contact forces on the body."""
+        """(R, f_c): full gradient of Pi (plus the inertia term when dynamic)
+        (Nn,3) and nodal contact forces on the body."""
         _, gc, _, _, _ = self.contact_terms(u, step)
-        return self.elastic_gradient(u) + gc, -gc
+        return self.elastic_gradient(u) + gc + self.inertia_terms(u)[1], -gc
 
     def hessian(self, u, step, projected=False):
         """Global tangent (3Nn x 3Nn CSR). Exact: exact element tangent + exact
@@ -155,6 +193,9 @@ class Problem:
         c = (3 * idx[:, None, None] + np.arange(3)[None, None, :]).repeat(3, axis=1)
         K = K + sp.coo_matrix((blocks.ravel(), (r.ravel(), c.ravel())),
                               shape=K.shape).tocsr()
+        w = self.inertia_terms(u)[2]
+        if np.any(w):
+            K = K + sp.diags(w.ravel())
         return K
 
     def residual_norm(self, u, step):
@@ -181,9 +222,12 @@ class Problem:
 
     def solve(self, tol: float = 1e-10, load_steps: int | None = None,
               max_newton: int = 100, max_backtracks: int = 60, u0=None,
-              verbose: bool = False) -> SolveResult:
+              verbose: bool = False, v0=None) -> SolveResult:
         K = self.K if not load_steps else int(load_steps)
         u = np.zeros((self.n, 3)) if u0 is None else np.array(u0, dtype=np.float64)
+        vel = np.zeros((self.n, 3)) if v0 is None else np.array(v0, dtype=np.float64)
+        vel[self.fixed] = 0.0
+        self.step_v = []
         step_force = np.zeros((K, 3))
         iters = np.zeros(K, dtype=np.int64)
         resid = np.zeros(K)
@@ -194,6 +238,9 @@ class Problem:
         fc = np.zeros((self.n, 3))
         g = np.zeros((self.n, 3))
         for step in range(1, K + 1):
+            u_prev = u.copy()
+            if self.dt > 0.0:
+                self.u_tilde = u_prev + self.dt * vel
             u[self.fixed] = (self.u_presc * (step / K))[self.fixed]
             ok = False
             for it in range(max_newton + 1):
@@ -233,9 +280,13 @@ class Problem:
             scales[step - 1] = scale
             step_force[step - 1] = fc.sum(axis=0)
             step_u.append(u.copy())
+            if self.dt > 0.0:
+                vel = np.where(self.fixed, 0.0, (u - u_prev) / self.dt)
+                self.step_v.append(vel.copy())
             if not ok:
                 converged = False
                 break
         reactions = np.where(self.fixed, g, 0.0)
+        self.u_tilde = None
         return SolveResult(u, step_force, fc, reactions, iters, resid, scales,
                            converged, n_proj, step_u)

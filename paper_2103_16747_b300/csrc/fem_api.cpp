@@ -291,6 +291,18 @@ void set_precond(const fem_options& o, SolveParams& P) {
   P.cheb_delta = (float)(0.5 * (b - a));
 }
 
+void set_dynamics(const fem_options& o, SolveParams& P) {
+  P.inv_dt = o.dt > 0.0 ? 1.0 / o.dt : 0.0;
+  P.density = o.dt > 0.0 ? o.density : 0.0;
+}
+
+bool common_options_valid(const fem_options& o) {
+  return o.c_kappa > 0 && o.max_newton >= 0 && o.max_cg >= 1 && o.max_backtracks >= 0 && o.cg_rtol_max > 0 &&
+         o.cg_rtol_min > 0 && o.cg_rtol_min <= o.cg_rtol_max && o.tangent >= 0 && o.tangent <= 3 &&
+         o.barrier_timeout_s > 0 && o.precond_degree >= 1 && o.precond_degree <= 8 && o.precond_ratio > 1.0 &&
+         o.dt >= 0.0 && std::isfinite(o.dt) && (o.dt == 0.0 || (o.density > 0.0 && std::isfinite(o.density)));
+}
+
 SmemLayout plan_layout(const PartDims& d, int budget) {
   SmemLayout L{};
   const int max_pt = std::max(d.max_pt, 1);
@@ -342,6 +354,7 @@ SmemLayout plan_layout(const PartDims& d, int budget) {
     L.mask = place_node(d.max_own);
     L.cursor = place_node(multi ? 24 * d.max_own : 16);
     L.cd = place_node(12 * d.max_own);
+    L.mh2 = place_node(4 * d.max_own);
     if (attempt == 1 && !nodes_shared) continue;
     L.ptn = place_opt(8 * d.max_pt);
     const int lptr_bytes = align_up(4 * (d.max_own + 1), 16);
@@ -526,6 +539,8 @@ void fem_default_options(fem_options* opt) {
   opt->batch_tets_per_cta = 1300;
   opt->precond_degree = 5;
   opt->precond_ratio = 60.0;
+  opt->dt = 0.0;
+  opt->density = 1.1e-9;
 }
 
 const char* fem_last_error(void) { return g_err.c_str(); }
@@ -760,6 +775,10 @@ int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, i
       kbase[i] = Emax[i] * area[i] / m->h_bar;
       m->n_candidates++;
     }
+  // lumped mass per unit density: a quarter of each tet's volume to each of its nodes
+  std::vector<double> vol_lumped(Nn, 0.0);
+  for (int t = 0; t < Nt; ++t)
+    for (int a = 0; a < 4; ++a) vol_lumped[m->tets_new[4 * (size_t)t + a]] += 0.25 * m->vol[t];
   std::vector<double> lame(2 * (size_t)n_materials);
   for (int k = 0; k < n_materials; ++k) {
     const double E = materials[k].E, nu = materials[k].nu;
@@ -768,19 +787,21 @@ int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, i
   }
   // uploads
   cudaStream_t s = m->stream;
-  double *d_X, *d_kbase, *d_lame;
+  double *d_X, *d_kbase, *d_lame, *d_vl;
   unsigned char* d_mask;
   {
     cudaError_t e;
     if ((e = upload(&d_X, X, s, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "upload X"));
     if ((e = upload(&d_kbase, kbase, s, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "upload k"));
     if ((e = upload(&d_lame, lame, s, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "upload lame"));
+    if ((e = upload(&d_vl, vol_lumped, s, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "upload mass"));
     if ((e = upload(&d_mask, m->node_mask, s, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "upload mask"));
     if ((e = upload(&m->d_perm, m->perm, s, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "upload perm"));
     WorkDev& W = m->work;
     if ((e = alloc(&W.u, 3 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
     if ((e = alloc(&W.R, 3 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
     if ((e = alloc(&W.uprev, 3 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
+    if ((e = alloc(&W.vel, 3 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
     if ((e = alloc(&W.vpub, 6 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
     if ((e = alloc(&W.dpub, (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
     unsigned long long* d_bar;
@@ -812,6 +833,7 @@ int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, i
   D.fixmask = d_mask;
   D.kbase = d_kbase;
   D.lame = d_lame;
+  D.vol_lumped = d_vl;
   int rc = build_partitions(m, default_parts(m));
   if (rc != FEM_OK) return bail(rc);
   *out = m;
@@ -898,12 +920,11 @@ static int fill_params(fem_mesh* m, const fem_options* opt, int mode, int steps,
   fem_options o;
   fem_default_options(&o);
   if (opt) o = *opt;
-  if (!(o.c_kappa > 0) || o.max_newton < 0 || o.max_cg < 1 || o.max_backtracks < 0 || !(o.cg_rtol_max > 0) ||
-      !(o.cg_rtol_min > 0) || o.cg_rtol_min > o.cg_rtol_max || (o.tangent < 0 || o.tangent > 3) ||
-      !(o.barrier_timeout_s > 0) || o.precond_degree < 1 || o.precond_degree > 8 || !(o.precond_ratio > 1.0))
-    return fail(FEM_ERR_ARG, "invalid fem_options");
+  if (!common_options_valid(o)) return fail(FEM_ERR_ARG, "invalid fem_options");
   memset(&P, 0, sizeof(P));
   set_precond(o, P);
+  // the evaluation and product entry points are those of the quasi-static step
+  if (mode == MODE_SOLVE) set_dynamics(o, P);
   P.mode = mode;
   P.n_steps = steps;
   P.step = step;

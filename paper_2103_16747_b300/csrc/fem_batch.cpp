@@ -66,10 +66,7 @@ auto a256 = [](size_t b) { return (b + 255) / 256 * 256; };
 
 int check_options(const fem_options& o) {
   const bool clusters = o.batch_engine == FEM_BATCH_CLUSTERS;
-  if (!(o.c_kappa > 0) || o.max_newton < 0 || o.max_cg < 1 || o.max_backtracks < 0 || !(o.cg_rtol_max > 0) ||
-      !(o.cg_rtol_min > 0) || o.cg_rtol_min > o.cg_rtol_max || o.tangent < 0 || o.tangent > 3 ||
-      !(o.barrier_timeout_s > 0) || o.batch_engine < FEM_BATCH_AUTO || o.batch_engine > FEM_BATCH_CLUSTERS ||
-      o.precond_degree < 1 || o.precond_degree > 8 || !(o.precond_ratio > 1.0) ||
+  if (!common_options_valid(o) || o.batch_engine < FEM_BATCH_AUTO || o.batch_engine > FEM_BATCH_CLUSTERS ||
       o.batch_parts < 0 || o.batch_parts > 256 ||
       (clusters && !(o.batch_parts == 0 || o.batch_parts == 1 || o.batch_parts == 2 || o.batch_parts == 4 ||
                      o.batch_parts == 8 || o.batch_parts == 16)))
@@ -326,6 +323,7 @@ int fem_batch_create(fem_mesh* const* meshes, const int32_t* n_steps, int32_t n,
     S.dpub = take(16 * max_nodes);
     S.R = take(24 * max_nodes);
     S.uprev = take(24 * max_nodes);
+    S.vel = take(24 * max_nodes);
     S.tangent = take(L.tan >= 0 ? 16 : 16 * (size_t)kTanVec * max_pt);
     S.cta = take((size_t)L.gbytes * max_parts);
     S.cta_stride = L.gbytes;
@@ -371,6 +369,7 @@ int fem_batch_create(fem_mesh* const* meshes, const int32_t* n_steps, int32_t n,
     P.cg_rtol_min = o.cg_rtol_min;
     P.timeout_ns = (unsigned long long)(o.barrier_timeout_s * 1e9);
     set_precond(o, P);
+    set_dynamics(o, P);
     P.depths = reinterpret_cast<const double*>(b->ws + b->depths_off) + b->depth_at[i];
     b->h_stats0[i] = st0;
   }

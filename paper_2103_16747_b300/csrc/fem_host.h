@@ -75,6 +75,10 @@ int fail(int code, const char* fmt, ...);  // sets the message, returns code
 int cuda_fail(cudaError_t e, const char* what);
 SmemLayout plan_layout(const PartDims& d, int budget);
 void set_precond(const fem_options& o, SolveParams& P);
+// Time stepping of the solve: inv_dt = 1/dt and the density (dt = 0: quasi-static).
+void set_dynamics(const fem_options& o, SolveParams& P);
+// Checks the option fields every solve entry point shares.
+bool common_options_valid(const fem_options& o);
 int smem_budget(const fem_mesh* m, int static_smem);
 // The mesh's partition into `parts` parts for batched solves (built on first use).
 int batch_partition(fem_mesh* m, int parts, const fem::MeshDev** dev, const fem::PartDims** dims);

@@ -43,6 +43,7 @@ struct MeshDev {
   const double* X;                  // [3*n_nodes]
   const unsigned char* fixmask;     // [n_nodes] bit0=x bit1=y bit2=z
   const double* kbase;              // [n_nodes] E_max A / h_bar (0 = not a candidate)
+  const double* vol_lumped;         // [n_nodes] one quarter of the volume of the tets at each node
   const double* lame;               // [2*n_materials] (mu, lam)
 };
 
@@ -66,6 +67,7 @@ struct WorkDev {
   double* u;                        // [3*n_nodes] displacement (owned entries written by their part)
   double* R;                        // [3*n_nodes] residual of the last evaluation
   double* uprev;                    // [3*n_nodes] converged displacement of the previous load step
+  double* vel;                      // [3*n_nodes] velocity (dynamic stepping; null when quasi-static)
   const double* u_presc;            // [3*n_nodes] prescribed values (or null)
   unsigned long long* vpub;         // [2][n_nodes][3] published PCG vector, (epoch, FP32) words
   float4* dpub;                     // [n_nodes] published Newton direction
@@ -90,6 +92,7 @@ struct SolveParams {
   int init_zero;                    // 1: the solve starts from u = 0 it writes itself (served jobs)
   int cheb_deg;                     // preconditioner: 1 = block-Jacobi, d > 1 = Chebyshev of degree d on it
   float cheb_theta, cheb_delta;     // centre and half-width of the Chebyshev interval
+  double inv_dt, density;           // dynamic stepping: 1 / time step (0: quasi-static), mass density
   int max_newton, max_cg, max_backtracks;
   double tol, c_kappa, cg_rtol_max, cg_rtol_min;
   unsigned long long timeout_ns;
@@ -109,7 +112,7 @@ __host__ __device__ inline int align_up(int v, int a) { return (v + a - 1) / a *
 
 struct SmemLayout {
   int lm, red, chunk;                             // always shared
-  int acc, x, r, ucg, w, s, p, minv, hc, mask, cursor, ut, cd;
+  int acc, x, r, ucg, w, s, p, minv, hc, mask, cursor, ut, cd, mh2;
   int tan, ptn, lptr, lcsr;                       // resident part data, or -1: read from global memory
   int chunk_tets;                                 // part tets per chunk of the evaluation passes
   int total;                                      // dynamic shared bytes
@@ -145,6 +148,7 @@ struct SlotScratch {
   long long ctrl;                   // group engine: barrier counter, abort word, job word (u64 each)
   long long vpub, cgslot, partials; // group engine: as in WorkDev
   long long dpub, tangent, R, uprev, cta;   // offsets inside a slot
+  long long vel;
   long long cta_stride;             // per-CTA bytes of the cta region
 };
 

@@ -186,6 +186,7 @@ bool admit(fem_server* v, int slot, Request& q) {
   P.timeout_ns = (unsigned long long)(v->o.barrier_timeout_s * 1e9);
   P.init_zero = 1;
   set_precond(v->o, P);
+  set_dynamics(v->o, P);
   P.shape = q.ind.shape;
   for (int k = 0; k < 3; ++k) {
     P.origin[k] = q.ind.pose[k];
@@ -419,10 +420,7 @@ int fem_server_create(fem_mesh* const* meshes, int32_t n_meshes, int32_t max_ste
   fem_options o;
   fem_default_options(&o);
   if (opt) o = *opt;
-  if (!(o.c_kappa > 0) || o.max_newton < 0 || o.max_cg < 1 || o.max_backtracks < 0 || !(o.cg_rtol_max > 0) ||
-      !(o.cg_rtol_min > 0) || o.cg_rtol_min > o.cg_rtol_max || o.tangent < 0 || o.tangent > 3 ||
-      !(o.barrier_timeout_s > 0) || o.batch_tets_per_cta < 0 || o.precond_degree < 1 || o.precond_degree > 8 ||
-      !(o.precond_ratio > 1.0))
+  if (!common_options_valid(o) || o.batch_tets_per_cta < 0)
     return fail(FEM_ERR_ARG, "invalid fem_options");
   for (int i = 0; i < n_meshes; ++i) {
     if (!meshes[i]) return fail(FEM_ERR_ARG, "mesh %d is NULL", i);
@@ -553,6 +551,7 @@ int fem_server_create(fem_mesh* const* meshes, int32_t n_meshes, int32_t max_ste
     S.dpub = take(16 * max_nodes);
     S.R = take(24 * max_nodes);
     S.uprev = take(24 * max_nodes);
+    S.vel = take(24 * max_nodes);
     S.tangent = take(L.tan >= 0 ? 16 : 16 * (size_t)kTanVec * max_pt);
     S.cta = take((size_t)L.gbytes * max_parts);
     S.cta_stride = L.gbytes;

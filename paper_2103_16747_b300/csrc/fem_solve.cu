@@ -134,7 +134,9 @@ struct Ctx {
   int part, nparts, n_own, n_loc, node0, halo0, t0, n_pt;
   int CH;                 // part tets per chunk of the evaluation passes
   double *u, *uprev, *R, *fc;   // owned entries of global node arrays (index 3*i+k)
-  const double *X, *kb;
+  double* vel;                  // owned velocities (dynamic stepping) or null
+  const double *X, *kb, *vl;
+  float* mh2;                   // owned nodes: lumped mass / dt^2 (0 when quasi-static)
   double *ut, *chunkd, *red;
   float *x, *r, *ucg, *w, *s, *p, *acc, *minv, *hc, *chunkf, *cd;
   float4* lm;
@@ -379,10 +381,20 @@ __device__ bool eval_pass(Ctx& C, const MeshDev& M, const WorkDev& W, const Solv
   double v[EV_N];
 #pragma unroll
   for (int k = 0; k < EV_N; ++k) v[k] = 0.0;
-  v[EV_ELASTIC] = e_el;
   v[EV_BAD] = bad;
   v[EV_SLOPE] = sl;
+  const double dt = P.inv_dt > 0.0 ? 1.0 / P.inv_dt : 0.0;
   for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
+    if (P.inv_dt > 0.0) {
+      // backward Euler: inertia m / (2 dt^2) |u - (u_n + dt v_n)|^2 (u_n = uprev)
+      const double mh = P.density * C.vl[i] * P.inv_dt * P.inv_dt;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const double d = C.ut[3 * i + k] - (C.uprev[3 * i + k] + dt * C.vel[3 * i + k]);
+        C.R[3 * i + k] += mh * d;
+        e_el += 0.5 * mh * d * d;
+      }
+    }
     const double kp = C.kb[i] * P.c_kappa;
     double fcv[3] = {0.0, 0.0, 0.0};
     float h[3] = {0.f, 0.f, 0.f};
@@ -414,6 +426,7 @@ __device__ bool eval_pass(Ctx& C, const MeshDev& M, const WorkDev& W, const Solv
     }
     v[EV_FX] += fcv[0]; v[EV_FY] += fcv[1]; v[EV_FZ] += fcv[2];
   }
+  v[EV_ELASTIC] = e_el;
   block_reduce_to_slot<CL>(C, W, bf.slot, v, EV_N);
   if (!sync_parts<CL>(C, gb)) return false;
   reduce_from_slots<CL>(C, W, bf.slot, EV_N);
@@ -477,6 +490,8 @@ __device__ void tangent_pass(Ctx& C, const MeshDev& M, int mode) {
     const float h0 = C.hc[3 * i], h1 = C.hc[3 * i + 1], h2 = C.hc[3 * i + 2];
     m[0] += h0 * h0; m[1] += h0 * h1; m[2] += h0 * h2;
     m[3] += h1 * h1; m[4] += h1 * h2; m[5] += h2 * h2;
+    const float mh = C.mh2[i];
+    m[0] += mh; m[3] += mh; m[5] += mh;
     inv_block_masked(m, C.mask[i], C.minv + 6 * i);
   }
   __syncthreads();
@@ -531,14 +546,16 @@ __device__ __forceinline__ void apply_minv(const float* mi, const float v[3], fl
   out[2] = mi[2] * v[0] + mi[4] * v[1] + mi[5] * v[2];
 }
 
-// Contact Gauss-Newton term and Dirichlet mask on the owned product.
+// Contact Gauss-Newton term, lumped mass / dt^2 (dynamic stepping) and
+// Dirichlet mask on the owned product.
 __device__ __forceinline__ void finish_product(const Ctx& C, int i, const float v[3], float out[3]) {
   const float h0 = C.hc[3 * i], h1 = C.hc[3 * i + 1], h2 = C.hc[3 * i + 2];
   const float hv = h0 * v[0] + h1 * v[1] + h2 * v[2];
+  const float mh = C.mh2[i];
   const unsigned mk = C.mask[i];
-  out[0] = (mk & 1u) ? 0.f : C.acc[3 * i] + h0 * hv;
-  out[1] = (mk & 2u) ? 0.f : C.acc[3 * i + 1] + h1 * hv;
-  out[2] = (mk & 4u) ? 0.f : C.acc[3 * i + 2] + h2 * hv;
+  out[0] = (mk & 1u) ? 0.f : C.acc[3 * i] + h0 * hv + mh * v[0];
+  out[1] = (mk & 2u) ? 0.f : C.acc[3 * i + 1] + h1 * hv + mh * v[1];
+  out[2] = (mk & 4u) ? 0.f : C.acc[3 * i + 2] + h2 * hv + mh * v[2];
 }
 
 // ------------------------------------------------- PCG sync, cooperative form
@@ -945,7 +962,8 @@ __device__ void accept_state(Ctx& C) {
 // Points the context at this part's data. smem: dynamic shared memory;
 // gscr: this CTA's region of the global scratch (arrays placed there by L).
 __device__ void setup_ctx(Ctx& C, const MeshDev& M, const WorkDev& W, const SmemLayout& L, unsigned char* smem,
-                          unsigned char* gscr, Statics* st, int part, int nparts, bool zero_u = false) {
+                          unsigned char* gscr, Statics* st, int part, int nparts, bool zero_u = false,
+                          double mass_scale = 0.0) {
   auto at = [&](int off) -> unsigned char* { return (off & kInGlobal) ? gscr + (off & ~kInGlobal) : smem + off; };
   C.part = part;
   C.nparts = nparts;
@@ -962,6 +980,8 @@ __device__ void setup_ctx(Ctx& C, const MeshDev& M, const WorkDev& W, const Smem
   C.fc = W.out_fc + 3 * (size_t)C.node0;
   C.X = M.X + 3 * (size_t)C.node0;
   C.kb = M.kbase + C.node0;
+  C.vl = M.vol_lumped + C.node0;
+  C.vel = W.vel ? W.vel + 3 * (size_t)C.node0 : nullptr;
   C.ut = reinterpret_cast<double*>(at(L.ut));
   C.chunkd = reinterpret_cast<double*>(smem + L.chunk);
   C.chunkf = reinterpret_cast<float*>(smem + L.chunk);
@@ -977,6 +997,7 @@ __device__ void setup_ctx(Ctx& C, const MeshDev& M, const WorkDev& W, const Smem
   C.minv = reinterpret_cast<float*>(at(L.minv));
   C.hc = reinterpret_cast<float*>(at(L.hc));
   C.cd = reinterpret_cast<float*>(at(L.cd));
+  C.mh2 = reinterpret_cast<float*>(at(L.mh2));
   C.mask = at(L.mask);
   C.cursor = reinterpret_cast<int*>(at(L.cursor));
   C.hsrc = M.halo_src + C.halo0;
@@ -1020,6 +1041,11 @@ __device__ void setup_ctx(Ctx& C, const MeshDev& M, const WorkDev& W, const Smem
       if (C.uprev) C.uprev[3 * i + k] = C.u[3 * i + k];
     }
     C.mask[i] = M.fixmask[C.node0 + i];
+    C.mh2[i] = (float)(mass_scale * C.vl[i]);
+    if (C.vel) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) C.vel[3 * i + k] = 0.0;
+    }
   }
   __syncthreads();
 }
@@ -1066,12 +1092,17 @@ __device__ bool solve_body(Ctx& C, const MeshDev& M, const WorkDev& W, const Sol
       const double d2 = dk - __ldcg(P.depths + step - 2);
       const double d1 = __ldcg(P.depths + step - 2) - (step >= 3 ? __ldcg(P.depths + step - 3) : 0.0);
       ratio = d1 != 0.0 ? d2 / d1 : 0.0;
+      if (P.inv_dt > 0.0) ratio = 1.0;   // dynamic stepping: start from u_n + dt v_n
     }
     for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
       const unsigned mk = C.mask[i];
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         C.x[3 * i + k] = (mk & (1u << k)) ? 0.f : (float)(C.u[3 * i + k] - C.uprev[3 * i + k]);
+        // backward Euler: v_n = (u_n - u_{n-1}) / dt, from the step just finished;
+        // prescribed components carry no inertia (their term would be a constant)
+        if (P.inv_dt > 0.0)
+          C.vel[3 * i + k] = (mk & (1u << k)) ? 0.0 : (C.u[3 * i + k] - C.uprev[3 * i + k]) * P.inv_dt;
         C.uprev[3 * i + k] = C.u[3 * i + k];
       }
     }
@@ -1225,7 +1256,7 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(MeshDev M, WorkDev W, 
   }
   Ctx C;
   unsigned char* gscr = W.cta_scratch ? W.cta_scratch + (size_t)blockIdx.x * W.cta_stride : nullptr;
-  setup_ctx(C, M, W, L, smem, gscr, &S, blockIdx.x, gridDim.x);
+  setup_ctx(C, M, W, L, smem, gscr, &S, blockIdx.x, gridDim.x, false, P.density * P.inv_dt * P.inv_dt);
   Barrier gb{W.barrier, W.abort_flag, 0ull, P.timeout_ns, gridDim.x};
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
   StatsDev* st = W.stats;
@@ -1309,6 +1340,7 @@ __global__ void __launch_bounds__(kBlock, 1) cluster_kernel(const BatchJob* __re
       w.u = J->u;
       w.R = reinterpret_cast<double*>(sb + S.R);
       w.uprev = reinterpret_cast<double*>(sb + S.uprev);
+      w.vel = reinterpret_cast<double*>(sb + S.vel);
       w.dpub = reinterpret_cast<float4*>(sb + S.dpub);
       w.tangent = reinterpret_cast<float4*>(sb + S.tangent);
       w.out_fc = J->out_fc;
@@ -1318,7 +1350,7 @@ __global__ void __launch_bounds__(kBlock, 1) cluster_kernel(const BatchJob* __re
     }
     __syncthreads();
     Ctx C;
-    setup_ctx(C, sM, sW, L, smem, gscr, &ST, (int)rank, (int)ncta);
+    setup_ctx(C, sM, sW, L, smem, gscr, &ST, (int)rank, (int)ncta, false, sP.density * sP.inv_dt * sP.inv_dt);
     Barrier unused{nullptr, nullptr, 0ull, 0ull, 0u};
     int ep = 0;
     unsigned long long n_pub = 0;
@@ -1402,6 +1434,7 @@ __global__ void __launch_bounds__(kBlock, 1) group_kernel(GroupRun R, SlotScratc
       w.u = reinterpret_cast<double*>(__ldcg(reinterpret_cast<const unsigned long long*>(&J->u)));
       w.R = reinterpret_cast<double*>(sb + S.R);
       w.uprev = reinterpret_cast<double*>(sb + S.uprev);
+      w.vel = reinterpret_cast<double*>(sb + S.vel);
       w.vpub = reinterpret_cast<unsigned long long*>(sb + S.vpub);
       w.dpub = reinterpret_cast<float4*>(sb + S.dpub);
       w.tangent = reinterpret_cast<float4*>(sb + S.tangent);
@@ -1416,7 +1449,8 @@ __global__ void __launch_bounds__(kBlock, 1) group_kernel(GroupRun R, SlotScratc
     }
     __syncthreads();
     Ctx C;
-    setup_ctx(C, sM, sW, L, smem, gscr, &ST, part, G.parts, sP.init_zero != 0);
+    setup_ctx(C, sM, sW, L, smem, gscr, &ST, part, G.parts, sP.init_zero != 0,
+              sP.density * sP.inv_dt * sP.inv_dt);
     const bool solved = solve_body<false>(C, sM, sW, sP, gb, ep, n_pub);
     if (!solved && part == 0 && threadIdx.x == 0) sW.stats->status = ST_TIMEOUT;
     if (R.done) {

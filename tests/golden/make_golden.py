@@ -1,10 +1,16 @@
-"""Write the oracle's reference solution of the single-fingertip sphere
+"""Write the oracle's reference solutions of the single-fingertip sphere
 indentation (R=7 mm, L=40 mm two-layer fingertip, sphere r=4 mm, 2 mm in 20
-load steps) to ``fingertip_sphere_oracle.npz``.
+load steps):
+
+  fingertip_sphere_oracle.npz          quasi-static load steps
+  fingertip_sphere_dynamic_oracle.npz  the same schedule as 20 backward-Euler
+                                       time steps of DYN_DT s, from rest, with
+                                       the lumped mass of density DYN_DENSITY
+                                       (mm, N, s units: t/mm^3)
 
 Calls only ``oracle/`` and the seeded input generators; the GPU parity tests
 compare against the stored arrays because the full oracle solve takes minutes.
-Run from the repository root:  python tests/golden/make_golden.py
+Run from the repository root:  python tests/golden/make_golden.py [static|dynamic]
 """
 import hashlib
 import os
@@ -28,12 +34,22 @@ def mesh_digest(mesh, ind):
     return h.hexdigest()
 
 
-def main():
+# time step of the paper's implicit integration (Sec. III-A) and a skin-like density
+DYN_DT = 1e-4
+DYN_DENSITY = 1.1e-9
+
+
+def main(kind="static"):
     mesh, ind = W.fingertip_sphere()
     t = time.time()
-    r = Problem(mesh, ind).solve(tol=1e-10)
+    if kind == "dynamic":
+        r = Problem(mesh, ind, dt=DYN_DT, density=DYN_DENSITY).solve(tol=1e-10)
+        name = "fingertip_sphere_dynamic_oracle.npz"
+    else:
+        r = Problem(mesh, ind).solve(tol=1e-10)
+        name = "fingertip_sphere_oracle.npz"
     assert r.converged
-    out = os.path.join(HERE, "fingertip_sphere_oracle.npz")
+    out = os.path.join(HERE, name)
     np.savez_compressed(out, u=r.u, step_force=r.step_force, nodal_contact=r.nodal_contact,
                         reactions=r.reactions, residual=r.residual, scale=r.scale,
                         newton_iters=r.newton_iters, digest=np.array(mesh_digest(mesh, ind)))
@@ -41,4 +57,5 @@ def main():
 
 
 if __name__ == "__main__":
-    main()
+    for k in (sys.argv[1:] or ["static", "dynamic"]):
+        main(k)
