@@ -74,7 +74,16 @@ extern "C" {
 
 typedef struct fem_mesh fem_mesh;           /* opaque; owns its device memory */
 
-typedef struct { double E, nu; } fem_material;   /* Young's modulus, Poisson's ratio */
+/* element laws (Sec. III-A: the paper's skin model is co-rotational linear elastic;
+   its target data come from a Neo-Hookean model) */
+#define FEM_MODEL_NEO_HOOKEAN 0  /* Psi = mu/2 (I1 - 3) - mu ln J + lam/2 (ln J)^2            */
+#define FEM_MODEL_COROTATED   1  /* Psi = mu |F - R|^2 + lam/2 (tr(R^T F) - 3)^2, F = R S     */
+
+typedef struct {
+    double  E, nu;       /* Young's modulus, Poisson's ratio (Lame parameters mu, lam) */
+    int32_t model;       /* FEM_MODEL_*                                               */
+    int32_t reserved;    /* set to 0                                                  */
+} fem_material;
 
 typedef struct {
     double  c_kappa;          /* penalty factor (default 100)                         */

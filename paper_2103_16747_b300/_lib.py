@@ -17,6 +17,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libfem_b300.so")
 
 FEM_OK = 0
+FEM_MODEL_NEO_HOOKEAN = 0
+FEM_MODEL_COROTATED = 1
 FEM_ERR_ARG = -1
 FEM_ERR_DEGENERATE_TET = -2
 FEM_ERR_NONFINITE = -3
@@ -49,7 +51,7 @@ EXPORTS = ("fem_default_options", "fem_create_mesh", "fem_set_indenter", "fem_se
 
 
 class fem_material(C.Structure):
-    _fields_ = [("E", C.c_double), ("nu", C.c_double)]
+    _fields_ = [("E", C.c_double), ("nu", C.c_double), ("model", C.c_int32), ("reserved", C.c_int32)]
 
 
 class fem_options(C.Structure):
@@ -201,13 +203,17 @@ def fem_default_options() -> fem_options:
 
 def fem_create_mesh(nodes, tets, tet_material, materials, fixed_nodes, fixed_mask=None,
                     cuda_stream=None):
-    """Returns an opaque handle (c_void_p). ``materials``: (M, 2) array of (E, nu).
+    """Returns an opaque handle (c_void_p). ``materials``: (M, 2) array of (E, nu),
+    or (M, 3) with a third column FEM_MODEL_* (0 neo-Hookean, 1 co-rotational).
     ``cuda_stream``: a torch.cuda.Stream, a raw cudaStream_t int, or None."""
     keep = []
     nodes = np.ascontiguousarray(nodes, dtype=np.float64)
     tets = np.ascontiguousarray(tets, dtype=np.int32)
-    mats = np.ascontiguousarray(materials, dtype=np.float64).reshape(-1, 2)
-    mat_arr = (fem_material * len(mats))(*[fem_material(float(e), float(n)) for e, n in mats])
+    mats = np.asarray(materials, dtype=np.float64)
+    mats = mats.reshape(-1, mats.shape[-1] if mats.ndim == 2 else 2)
+    model = mats[:, 2].astype(np.int32) if mats.shape[1] > 2 else np.zeros(len(mats), dtype=np.int32)
+    mat_arr = (fem_material * len(mats))(*[fem_material(float(e), float(n), int(md), 0)
+                                            for (e, n), md in zip(mats[:, :2], model)])
     fixed = np.ascontiguousarray(fixed_nodes if fixed_nodes is not None else [], dtype=np.int32)
     stream = getattr(cuda_stream, "cuda_stream", cuda_stream)
     out = C.c_void_p()

@@ -573,6 +573,8 @@ int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, i
     const double E = materials[k].E, nu = materials[k].nu;
     if (!std::isfinite(E) || !std::isfinite(nu)) return fail(FEM_ERR_NONFINITE, "material %d not finite", k);
     if (!(E > 0) || !(nu > -1.0 && nu < 0.5)) return fail(FEM_ERR_ARG, "material %d: need E>0, -1<nu<0.5", k);
+    if (materials[k].model != FEM_MODEL_NEO_HOOKEAN && materials[k].model != FEM_MODEL_COROTATED)
+      return fail(FEM_ERR_ARG, "material %d: model %d is not a FEM_MODEL_*", k, materials[k].model);
   }
   for (int t = 0; t < Nt; ++t) {
     for (int a = 0; a < 4; ++a) {
@@ -780,6 +782,8 @@ int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, i
   for (int t = 0; t < Nt; ++t)
     for (int a = 0; a < 4; ++a) vol_lumped[m->tets_new[4 * (size_t)t + a]] += 0.25 * m->vol[t];
   std::vector<double> lame(2 * (size_t)n_materials);
+  std::vector<int> mat_model(n_materials);
+  for (int k = 0; k < n_materials; ++k) mat_model[k] = materials[k].model;
   for (int k = 0; k < n_materials; ++k) {
     const double E = materials[k].E, nu = materials[k].nu;
     lame[2 * k] = E / (2.0 * (1.0 + nu));
@@ -788,6 +792,7 @@ int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, i
   // uploads
   cudaStream_t s = m->stream;
   double *d_X, *d_kbase, *d_lame, *d_vl;
+  int* d_model;
   unsigned char* d_mask;
   {
     cudaError_t e;
@@ -795,6 +800,7 @@ int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, i
     if ((e = upload(&d_kbase, kbase, s, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "upload k"));
     if ((e = upload(&d_lame, lame, s, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "upload lame"));
     if ((e = upload(&d_vl, vol_lumped, s, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "upload mass"));
+    if ((e = upload(&d_model, mat_model, s, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "upload model"));
     if ((e = upload(&d_mask, m->node_mask, s, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "upload mask"));
     if ((e = upload(&m->d_perm, m->perm, s, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "upload perm"));
     WorkDev& W = m->work;
@@ -834,6 +840,7 @@ int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, i
   D.kbase = d_kbase;
   D.lame = d_lame;
   D.vol_lumped = d_vl;
+  D.mat_model = d_model;
   int rc = build_partitions(m, default_parts(m));
   if (rc != FEM_OK) return bail(rc);
   *out = m;
@@ -1181,7 +1188,8 @@ int fem_element_stress(fem_mesh* m, const double* u, double* out_cauchy, double*
   if (rc) return rc;
   double* sig = m->d_stress_out;
   double* vm = m->d_stress_out + 6 * Nt;
-  CUDA_TRY(launch_stress(m->d_stress_tets, m->d_stress_dminv, m->d_stress_mat, m->dev.lame, m->d_stress_u,
+  CUDA_TRY(launch_stress(m->d_stress_tets, m->d_stress_dminv, m->d_stress_mat, m->dev.lame, m->dev.mat_model,
+                         m->d_stress_u,
                          m->d_tet_perm, (int)Nt, sig, vm, s), "stress kernel");
   CUDA_TRY(cudaMemcpyAsync(out_cauchy, sig, sizeof(double) * 6 * Nt, cudaMemcpyDefault, s), "output copy");
   if (out_von_mises)

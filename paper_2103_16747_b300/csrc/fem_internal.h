@@ -45,6 +45,7 @@ struct MeshDev {
   const double* kbase;              // [n_nodes] E_max A / h_bar (0 = not a candidate)
   const double* vol_lumped;         // [n_nodes] one quarter of the volume of the tets at each node
   const double* lame;               // [2*n_materials] (mu, lam)
+  const int* mat_model;             // [n_materials] FEM_MODEL_* element law
 };
 
 // Phases timed with clock64 by CTA 0 (shares of the kernel's SM cycles).
@@ -198,8 +199,8 @@ cudaError_t solve_kernel_attrs(int smem_bytes, int* static_smem, int* blocks_per
 
 // Element stress of every tet at u (fem_stress.cu); sig and vm in caller tet order.
 cudaError_t launch_stress(const int4* tets, const double* dminv, const int* mat, const double* lame,
-                          const double* u, const int* tet_perm, int n_tets, double* sig, double* vm,
-                          cudaStream_t s);
+                          const int* mat_model, const double* u, const int* tet_perm, int n_tets, double* sig,
+                          double* vm, cudaStream_t s);
 
 // Fixed scratch block for fem_eval_residual_noalloc (fem_solve.cu).
 constexpr size_t kNoAllocScratchBytes = 8u << 20;

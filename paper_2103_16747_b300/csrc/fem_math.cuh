@@ -8,6 +8,13 @@
 // gradient of V Psi is V P grad N_a with grad N_a = Dm^-T e_a (a=1..3),
 // grad N_0 = -sum.
 //
+// Co-rotational linear elasticity (model 1; the paper's simulator uses a
+// co-rotational linear-elastic skin, Sec. III-A), F = R S polar:
+//   Psi(F) = mu |S - I|^2 + lam/2 (tr S - 3)^2
+//   P(F)   = R (2 mu (S - I) + lam tr(S - I) I)
+// In principal stretches psi_i = 2 mu (s_i - 1) + lam (sum s - 3): A_ij =
+// 2 mu d_ij + lam, pair eigenvalues 2 mu and (psi_i + psi_j)/(s_i + s_j).
+//
 // Tangent (FP32) in the principal-stretch frame F = U diag(s) V^T
 // (Teran, Sifakis, Irving, Fedkiw 2005, "Robust quasistatic finite elements and
 // flesh simulation"): with c = mu - lam ln J,
@@ -24,11 +31,138 @@
 
 namespace fem {
 
+// ------------------------------------------------------------------ FP32 3x3 eigen
+// Cyclic Jacobi on a symmetric 3x3 matrix (a00 a01 a02 a11 a12 a22), fixed
+// number of sweeps (Golub & Van Loan, Matrix Computations, Alg. 8.5.2). On
+// return a holds the (unsorted) eigenvalues on its diagonal slots 0, 3, 5 and
+// V (row-major) holds the eigenvectors as columns.
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
+
+// One Jacobi rotation zeroing A[p][q]; V accumulates the rotations.
+template <typename T>
+__device__ __forceinline__ void jacobi_rotate(T A[3][3], T V[3][3], int p, int q, T rel_skip) {
+  const int r = 3 - p - q;
+  const T apq = A[p][q];
+  const T scale = fabs(A[p][p]) + fabs(A[q][q]);
+  if (fabs(apq) <= T(1e-30) + rel_skip * scale) return;
+  const T tau = (A[q][q] - A[p][p]) / (T(2) * apq);
+  const T t = copysign(T(1), tau) / (fabs(tau) + sqrt(T(1) + tau * tau));
+  const T c = rsqrt_t(T(1) + t * t);
+  const T s = t * c;
+  const T arp = A[r][p], arq = A[r][q];
+  A[p][p] -= t * apq;
+  A[q][q] += t * apq;
+  A[p][q] = A[q][p] = T(0);
+  A[r][p] = A[p][r] = c * arp - s * arq;
+  A[r][q] = A[q][r] = s * arp + c * arq;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const T vp = V[k][p], vq = V[k][q];
+    V[k][p] = c * vp - s * vq;
+    V[k][q] = s * vp + c * vq;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void jacobi_sweep(T A[3][3], T V[3][3], T rel_skip) {
+  jacobi_rotate(A, V, 0, 1, rel_skip);
+  jacobi_rotate(A, V, 0, 2, rel_skip);
+  jacobi_rotate(A, V, 1, 2, rel_skip);
+}
+
+__device__ __forceinline__ void jacobi_eig3(float A[3][3], float V[3][3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? 1.f : 0.f;
+#pragma unroll 1
+  for (int sweep = 0; sweep < 5; ++sweep) jacobi_sweep(A, V, 1e-9f);
+}
+
 // ------------------------------------------------------------------ FP64 element
-// u[a][i]: displacement of corner a; Dm: Dm^-1 row-major. Writes the nodal
-// gradient of V*Psi into f, returns V*Psi in energy and J.
+// Co-rotational stress from H = F - I (det F > 0). The stretch S comes from the
+// eigen-decomposition of F^T F - I = H + H^T + H^T H = V diag(delta) V^T: an
+// FP32 Jacobi pass gives V, which is re-orthonormalised and refined by two FP64
+// sweeps. With s_i - 1 = delta_i / (1 + sqrt(1 + delta_i)) nothing cancels at
+// small strain. P = F V diag(psi_i / s_i) V^T (= R V diag(psi_i) V^T).
+__device__ __noinline__ void corot_stress_f64(const double H[9], double mu, double lam, double P[9],
+                                                 double& psi) {
+  double Cm[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      Cm[i][j] = H[3 * i + j] + H[3 * j + i] + (H[i] * H[j] + H[3 + i] * H[3 + j] + H[6 + i] * H[6 + j]);
+  float A32[3][3], V32[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) A32[i][j] = (float)Cm[i][j];
+  jacobi_eig3(A32, V32);
+  double V[3][3];
+  {
+    double a[3] = {V32[0][0], V32[1][0], V32[2][0]}, b[3] = {V32[0][1], V32[1][1], V32[2][1]};
+    const double na = rsqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) a[k] *= na;
+    const double ab = a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) b[k] -= ab * a[k];
+    const double nb = rsqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) b[k] *= nb;
+    const double c[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { V[k][0] = a[k]; V[k][1] = b[k]; V[k][2] = c[k]; }
+  }
+  double B[3][3];
+  {
+    double CV[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) CV[i][j] = Cm[i][0] * V[0][j] + Cm[i][1] * V[1][j] + Cm[i][2] * V[2][j];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) B[i][j] = V[0][i] * CV[0][j] + V[1][i] * CV[1][j] + V[2][i] * CV[2][j];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < i; ++j) B[i][j] = B[j][i] = 0.5 * (B[i][j] + B[j][i]);
+  }
+  jacobi_sweep(B, V, 1e-18);
+  jacobi_sweep(B, V, 1e-18);
+  double sm1[3], s[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double d = B[k][k];
+    sm1[k] = d / (1.0 + sqrt(1.0 + d));
+    s[k] = 1.0 + sm1[k];
+  }
+  const double trE = sm1[0] + sm1[1] + sm1[2];
+  psi = mu * (sm1[0] * sm1[0] + sm1[1] * sm1[1] + sm1[2] * sm1[2]) + 0.5 * lam * trE * trE;
+  double w[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) w[k] = (2.0 * mu * sm1[k] + lam * trE) / s[k];
+  double Mt[3][3];  // V diag(w) V^T
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Mt[i][j] = V[i][0] * w[0] * V[j][0] + V[i][1] * w[1] * V[j][1] + V[i][2] * w[2] * V[j][2];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      P[3 * i + j] = Mt[i][j] + (H[3 * i] * Mt[0][j] + H[3 * i + 1] * Mt[1][j] + H[3 * i + 2] * Mt[2][j]);
+}
+
+// u[a][i]: displacement of corner a; Dm: Dm^-1 row-major; model 0 neo-Hookean,
+// 1 co-rotational. Writes the nodal gradient of V*Psi into f, returns V*Psi in
+// energy and J.
 __device__ __forceinline__ void elem_eval_f64(const double u[4][3], const double Dm[9], double vol,
-                                              double mu, double lam, double f[4][3],
+                                              double mu, double lam, int model, double f[4][3],
                                               double& energy, double& J) {
   double Ds[9];
 #pragma unroll
@@ -48,30 +182,40 @@ __device__ __forceinline__ void elem_eval_f64(const double u[4][3], const double
                       H[2] * (H[3] * H[7] - H[4] * H[6]);
   const double Jm1 = trH + m2 + detH;
   J = 1.0 + Jm1;
-  double F[9];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) F[k] = H[k];
-  F[0] += 1.0; F[4] += 1.0; F[8] += 1.0;
-  double cof[9];
-  cof[0] = F[4] * F[8] - F[5] * F[7];
-  cof[1] = F[5] * F[6] - F[3] * F[8];
-  cof[2] = F[3] * F[7] - F[4] * F[6];
-  cof[3] = F[2] * F[7] - F[1] * F[8];
-  cof[4] = F[0] * F[8] - F[2] * F[6];
-  cof[5] = F[1] * F[6] - F[0] * F[7];
-  cof[6] = F[1] * F[5] - F[2] * F[4];
-  cof[7] = F[2] * F[3] - F[0] * F[5];
-  cof[8] = F[0] * F[4] - F[1] * F[3];
-  const double lnJ = log1p(Jm1);
-  double hh = 0.0;
-#pragma unroll
-  for (int k = 0; k < 9; ++k) hh += H[k] * H[k];
-  const double I1m3 = 2.0 * trH + hh;
-  energy = vol * (0.5 * mu * I1m3 - mu * lnJ + 0.5 * lam * lnJ * lnJ);
-  const double cf = (lam * lnJ - mu) / J;
   double P[9];
+  if (model == 1) {
+    double psi = 0.0;
+    if (J > 0.0) corot_stress_f64(H, mu, lam, P, psi);
+    else {
 #pragma unroll
-  for (int k = 0; k < 9; ++k) P[k] = mu * F[k] + cf * cof[k];
+      for (int k = 0; k < 9; ++k) P[k] = 0.0;
+    }
+    energy = vol * psi;
+  } else {
+    double F[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) F[k] = H[k];
+    F[0] += 1.0; F[4] += 1.0; F[8] += 1.0;
+    double cof[9];
+    cof[0] = F[4] * F[8] - F[5] * F[7];
+    cof[1] = F[5] * F[6] - F[3] * F[8];
+    cof[2] = F[3] * F[7] - F[4] * F[6];
+    cof[3] = F[2] * F[7] - F[1] * F[8];
+    cof[4] = F[0] * F[8] - F[2] * F[6];
+    cof[5] = F[1] * F[6] - F[0] * F[7];
+    cof[6] = F[1] * F[5] - F[2] * F[4];
+    cof[7] = F[2] * F[3] - F[0] * F[5];
+    cof[8] = F[0] * F[4] - F[1] * F[3];
+    const double lnJ = log1p(Jm1);
+    double hh = 0.0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) hh += H[k] * H[k];
+    const double I1m3 = 2.0 * trH + hh;
+    energy = vol * (0.5 * mu * I1m3 - mu * lnJ + 0.5 * lam * lnJ * lnJ);
+    const double cf = (lam * lnJ - mu) / J;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) P[k] = mu * F[k] + cf * cof[k];
+  }
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     double s = 0.0;
@@ -83,46 +227,6 @@ __device__ __forceinline__ void elem_eval_f64(const double u[4][3], const double
       s += v;
     }
     f[0][i] = -s;
-  }
-}
-
-// ------------------------------------------------------------------ FP32 3x3 eigen
-// Cyclic Jacobi on a symmetric 3x3 matrix (a00 a01 a02 a11 a12 a22), fixed
-// number of sweeps (Golub & Van Loan, Matrix Computations, Alg. 8.5.2). On
-// return a holds the (unsorted) eigenvalues on its diagonal slots 0, 3, 5 and
-// V (row-major) holds the eigenvectors as columns.
-__device__ __forceinline__ void jacobi_eig3(float A[3][3], float V[3][3]) {
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? 1.f : 0.f;
-#pragma unroll 1
-  for (int sweep = 0; sweep < 5; ++sweep) {
-#pragma unroll
-    for (int pair = 0; pair < 3; ++pair) {
-      const int p = pair == 2 ? 1 : 0;
-      const int q = pair == 0 ? 1 : 2;
-      const int r = 3 - p - q;
-      const float apq = A[p][q];
-      const float scale = fabsf(A[p][p]) + fabsf(A[q][q]);
-      if (fabsf(apq) <= 1e-30f + 1e-9f * scale) continue;
-      const float tau = (A[q][q] - A[p][p]) / (2.f * apq);
-      const float t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-      const float c = rsqrtf(1.f + t * t);
-      const float s = t * c;
-      const float arp = A[r][p], arq = A[r][q];
-      A[p][p] -= t * apq;
-      A[q][q] += t * apq;
-      A[p][q] = A[q][p] = 0.f;
-      A[r][p] = A[p][r] = c * arp - s * arq;
-      A[r][q] = A[q][r] = s * arp + c * arq;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const float vp = V[k][p], vq = V[k][q];
-        V[k][p] = c * vp - s * vq;
-        V[k][q] = s * vp + c * vq;
-      }
-    }
   }
 }
 
@@ -255,31 +359,49 @@ __device__ __forceinline__ void corner_blocks(const float U[3][3], const float G
 }
 
 __device__ __forceinline__ void tangent_build(const float F[9], float mu, float lam, float vol,
-                                              const float Dm[9], int mode, float T[30],
+                                              const float Dm[9], int mode, int model, float T[30],
                                               float diag[4][6]) {
   float U[3][3], V[3][3], s[3];
   svd3(F, U, s, V);
-  const float detF = F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
-                     F[2] * (F[3] * F[7] - F[4] * F[6]);
-  const float J = fmaxf(detF, 1e-20f);
-  const float c = mu - lam * logf(J);
   // keep the stretches away from zero (J > 0 is guaranteed by the line search)
 #pragma unroll
   for (int i = 0; i < 3; ++i) s[i] = fmaxf(s[i], 1e-6f);
-  const float is[3] = {1.f / s[0], 1.f / s[1], 1.f / s[2]};
-  float A[3][3];
+  float A[3][3], es[3], ea[3];   // pairs in the order (0,1) (0,2) (1,2)
+  bool a_psd;
+  if (model == 1) {
+    // co-rotational: A = 2 mu I + lam 1 1^T (PSD); pair eigenvalues 2 mu
+    // (symmetric mode) and (psi_i + psi_j)/(s_i + s_j) (rotation mode)
+    const float trE = (s[0] - 1.f) + (s[1] - 1.f) + (s[2] - 1.f);
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int j = 0; j < 3; ++j) A[i][j] = lam * is[i] * is[j] + (i == j ? mu + c * is[i] * is[i] : 0.f);
-  // pair (i,j) eigenvalues: symmetric mode mu + c/(s_i s_j), rotation mode mu - c/(s_i s_j)
-  float es[3], ea[3];
-  const float kk[3] = {c * is[0] * is[1], c * is[0] * is[2], c * is[1] * is[2]};
+      for (int j = 0; j < 3; ++j) A[i][j] = lam + (i == j ? 2.f * mu : 0.f);
+    const float ps[3] = {2.f * mu * (s[0] - 1.f) + lam * trE, 2.f * mu * (s[1] - 1.f) + lam * trE,
+                         2.f * mu * (s[2] - 1.f) + lam * trE};
+    const int pi[3] = {0, 0, 1}, pj[3] = {1, 2, 2};
 #pragma unroll
-  for (int k = 0; k < 3; ++k) { es[k] = mu + kk[k]; ea[k] = mu - kk[k]; }
-  // diagonal block: PSD whenever its diagonal part diag(mu + c/s_i^2) is
-  const bool a_psd = mu + c * is[0] * is[0] >= 0.f && mu + c * is[1] * is[1] >= 0.f &&
-                     mu + c * is[2] * is[2] >= 0.f;
+    for (int k = 0; k < 3; ++k) {
+      es[k] = 2.f * mu;
+      ea[k] = (ps[pi[k]] + ps[pj[k]]) / (s[pi[k]] + s[pj[k]]);
+    }
+    a_psd = true;
+  } else {
+    const float detF = F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
+                       F[2] * (F[3] * F[7] - F[4] * F[6]);
+    const float J = fmaxf(detF, 1e-20f);
+    const float c = mu - lam * logf(J);
+    const float is[3] = {1.f / s[0], 1.f / s[1], 1.f / s[2]};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) A[i][j] = lam * is[i] * is[j] + (i == j ? mu + c * is[i] * is[i] : 0.f);
+    // pair (i,j) eigenvalues: symmetric mode mu + c/(s_i s_j), rotation mode mu - c/(s_i s_j)
+    const float kk[3] = {c * is[0] * is[1], c * is[0] * is[2], c * is[1] * is[2]};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { es[k] = mu + kk[k]; ea[k] = mu - kk[k]; }
+    // diagonal block: PSD whenever its diagonal part diag(mu + c/s_i^2) is
+    a_psd = mu + c * is[0] * is[0] >= 0.f && mu + c * is[1] * is[1] >= 0.f && mu + c * is[2] * is[2] >= 0.f;
+  }
   float Ap[3][3];
   if (a_psd) {
 #pragma unroll

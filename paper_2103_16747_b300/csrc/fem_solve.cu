@@ -366,7 +366,7 @@ __device__ bool eval_pass(Ctx& C, const MeshDev& M, const WorkDev& W, const Solv
       const int mat = info & 0xffff;
       const double mu = M.lame[2 * mat], lam = M.lame[2 * mat + 1];
       double f[4][3], energy, J;
-      elem_eval_f64(uu, Dm, M.pt_vol[e], mu, lam, f, energy, J);
+      elem_eval_f64(uu, Dm, M.pt_vol[e], mu, lam, M.mat_model[mat], f, energy, J);
       if (!(J > 0.0) || !isfinite(energy)) bad += 1.0;
       if (info >> 16) e_el += energy;
 #pragma unroll
@@ -469,7 +469,7 @@ __device__ void tangent_pass(Ctx& C, const MeshDev& M, int mode) {
       float T[32];
       float dg[4][6];
       tangent_build(F, (float)M.lame[2 * mat], (float)M.lame[2 * mat + 1], (float)M.pt_vol[e], Dm,
-                    mode, T, dg);
+                    mode, M.mat_model[mat], T, dg);
       T[30] = 0.f; T[31] = 0.f;
 #pragma unroll
       for (int g = 0; g < kTanVec; ++g)

@@ -5,10 +5,12 @@
 // For the compressible neo-Hookean law P = mu F + (lam ln J - mu) F^-T, so
 //   sigma = P F^T / J = (mu (F F^T - I) + lam ln J I) / J,
 // with F F^T - I = H + H^T + H H^T for H = grad u (no cancellation at small
-// strain) and J - 1 from the invariants of H.
+// strain) and J - 1 from the invariants of H. For the co-rotational law
+// sigma = P F^T / J with P from the polar decomposition (fem_math.cuh).
 #include <cuda_runtime.h>
 
 #include "fem_internal.h"
+#include "fem_math.cuh"
 
 namespace fem {
 
@@ -16,6 +18,7 @@ namespace {
 
 __global__ void stress_kernel(const int4* __restrict__ tets, const double* __restrict__ dminv,
                               const int* __restrict__ mat, const double* __restrict__ lame,
+                              const int* __restrict__ mat_model,
                               const double* __restrict__ u, const int* __restrict__ tet_perm, int n_tets,
                               double* __restrict__ sig, double* __restrict__ vm) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -47,13 +50,27 @@ __global__ void stress_kernel(const int4* __restrict__ tets, const double* __res
   const double mu = lame[2 * mt], lam = lame[2 * mt + 1];
   const double lnJ = log1p(Jm1);
   double s[3][3];
+  if (mat_model[mt] == 1) {
+    double Hf[9], P[9], psi;
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const double b = H[i][j] + H[j][i] + H[i][0] * H[j][0] + H[i][1] * H[j][1] + H[i][2] * H[j][2];
-      s[i][j] = (mu * b + (i == j ? lam * lnJ : 0.0)) / J;
-    }
+      for (int j = 0; j < 3; ++j) Hf[3 * i + j] = H[i][j];
+    corot_stress_f64(Hf, mu, lam, P, psi);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)   // (P F^T)_ij = P_ij + sum_k P_ik H_jk
+        s[i][j] = (P[3 * i + j] + P[3 * i] * H[j][0] + P[3 * i + 1] * H[j][1] + P[3 * i + 2] * H[j][2]) / J;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const double b = H[i][j] + H[j][i] + H[i][0] * H[j][0] + H[i][1] * H[j][1] + H[i][2] * H[j][2];
+        s[i][j] = (mu * b + (i == j ? lam * lnJ : 0.0)) / J;
+      }
+  }
   const int o = tet_perm[t];
   double* out = sig + 6 * (size_t)o;
   out[0] = s[0][0]; out[1] = s[1][1]; out[2] = s[2][2];
@@ -69,10 +86,11 @@ __global__ void stress_kernel(const int4* __restrict__ tets, const double* __res
 }  // namespace
 
 cudaError_t launch_stress(const int4* tets, const double* dminv, const int* mat, const double* lame,
-                          const double* u, const int* tet_perm, int n_tets, double* sig, double* vm,
-                          cudaStream_t s) {
+                          const int* mat_model, const double* u, const int* tet_perm, int n_tets, double* sig,
+                          double* vm, cudaStream_t s) {
   if (n_tets <= 0) return cudaSuccess;
-  stress_kernel<<<(n_tets + 255) / 256, 256, 0, s>>>(tets, dminv, mat, lame, u, tet_perm, n_tets, sig, vm);
+  stress_kernel<<<(n_tets + 255) / 256, 256, 0, s>>>(tets, dminv, mat, lame, mat_model, u, tet_perm, n_tets, sig,
+                                                     vm);
   return cudaGetLastError();
 }
 

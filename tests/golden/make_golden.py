@@ -7,10 +7,12 @@ load steps):
                                        time steps of DYN_DT s, from rest, with
                                        the lumped mass of density DYN_DENSITY
                                        (mm, N, s units: t/mm^3)
+  fingertip_sphere_corot_oracle.npz    quasi-static, both layers co-rotational
+                                       linear elastic
 
 Calls only ``oracle/`` and the seeded input generators; the GPU parity tests
 compare against the stored arrays because the full oracle solve takes minutes.
-Run from the repository root:  python tests/golden/make_golden.py [static|dynamic]
+Run from the repository root:  python tests/golden/make_golden.py [static|dynamic|corot]
 """
 import hashlib
 import os
@@ -45,6 +47,9 @@ def main(kind="static"):
     if kind == "dynamic":
         r = Problem(mesh, ind, dt=DYN_DT, density=DYN_DENSITY).solve(tol=1e-10)
         name = "fingertip_sphere_dynamic_oracle.npz"
+    elif kind == "corot":
+        r = Problem(W.with_model(mesh, 1), ind).solve(tol=1e-10)
+        name = "fingertip_sphere_corot_oracle.npz"
     else:
         r = Problem(mesh, ind).solve(tol=1e-10)
         name = "fingertip_sphere_oracle.npz"
@@ -57,5 +62,5 @@ def main(kind="static"):
 
 
 if __name__ == "__main__":
-    for k in (sys.argv[1:] or ["static", "dynamic"]):
+    for k in (sys.argv[1:] or ["static", "dynamic", "corot"]):
         main(k)

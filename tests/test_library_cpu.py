@@ -54,7 +54,8 @@ def test_cluster_engine_takes_powers_of_two_up_to_16():
     assert rc == L.FEM_ERR_ARG and "fem_options" in L.fem_last_error()
 
 
-@pytest.mark.parametrize("case", ["index", "repeat", "inverted", "flat", "nan", "material", "mask", "sizes"])
+@pytest.mark.parametrize("case", ["index", "repeat", "inverted", "flat", "nan", "material", "model", "mask",
+                                  "sizes"])
 def test_host_validation(case):
     from paper_2103_16747_b300 import _lib as L
     m = W.cube_mesh(2)
@@ -78,6 +79,8 @@ def test_host_validation(case):
         want = L.FEM_ERR_NONFINITE
     elif case == "material":
         mats[0, 1] = 0.5
+    elif case == "model":
+        mats = np.column_stack([mats, [2.0]])
     elif case == "mask":
         mask = np.full(len(fixed), 9, dtype=np.uint8)
     elif case == "sizes":

@@ -17,6 +17,8 @@ synthetic geometry):
   * ``fingertip_draws``    random sphere / cylinder / box-edge indentations of the
                            same fingertip.
   * ``uneven_fingertips``  fingertips with R~U[5,10] and a log-uniform tet count.
+  * ``with_model``         a copy of a mesh whose materials carry an element-law
+                           id (third column: 0 neo-Hookean, 1 co-rotational).
 """
 from __future__ import annotations
 
@@ -37,6 +39,17 @@ SEED_BASE = 1000
 def cube_sphere():
     """Unit cube with a sphere pressed into the top face."""
     return cube_mesh(8), cube_sphere_indenter()
+
+
+def with_model(mesh, model):
+    """Copy of ``mesh`` with an element-law id per material (an int, or one per
+    material) in a third materials column."""
+    import copy
+    m = copy.copy(mesh)
+    mats = np.asarray(mesh.materials, dtype=np.float64)[:, :2]
+    ids = np.broadcast_to(np.asarray(model, dtype=np.float64), (len(mats),))
+    m.materials = np.column_stack([mats, ids])
+    return m
 
 
 def fingertip_sphere(seed: int = SEED_BASE + 1):
