@@ -3,8 +3,9 @@
 The paper drives rigid indenters (spheres, cylinders, objects with edges) into
 the fingertip (Sec. III-A, Sec. III-C). Contact here is node-versus-analytic
 surface with a penalty: a candidate node at x with phi(x) < 0 (inside the
-indenter) stores energy k/2 phi^2 (frictionless; the paper's Coulomb friction is
-not part of this path).
+indenter) stores energy k/2 phi^2. Coulomb friction (the paper's contact model is
+isotropic Coulomb, Sec. III-A) is optional, as a lagged and smoothed dissipation
+potential (``friction`` below).
 
 Indenter description (identical to the library's): origin c, rotation R whose
 columns are the local axes, shape parameters, all translated by d_k a at load
@@ -95,3 +96,46 @@ def penalty(shape, origin, R, params, x, k):
     gn = (k * act)[:, None, None] * _outer(g, g)
     hess = gn + (k * pm)[:, None, None] * H
     return energy, grad, hess, gn, act
+
+
+def friction_f0(y, eps):
+    """Smoothed Coulomb magnitude: f0(y) = y^2/eps - y^3/(3 eps^2) + eps/3 below
+    the slip eps, y above; C1 at eps, f0' rises from 0 to 1 over [0, eps]."""
+    y = np.asarray(y, dtype=np.float64)
+    return np.where(y < eps, y * y / eps - y ** 3 / (3 * eps * eps) + eps / 3, y)
+
+
+def friction(x, x_start, dc, normal, fn, mu_f, eps):
+    """Lagged, smoothed Coulomb friction of the nodes against a translating
+    rigid indenter. Reading of the paper's Coulomb contact (Sec. III-A) for
+    load steps solved by energy minimisation: per node the dissipation
+    potential
+
+        D_i(x) = mu_f fn_i f0(|s_i|),  s_i = (I - n_i n_i^T)(x_i - x_start_i - dc),
+
+    with the normal n_i and the normal force magnitude fn_i frozen at the start
+    of the load step (x_start, indenter at its previous pose), and dc the
+    indenter's translation over the step. A node sliding by more than eps
+    carries a friction force of magnitude mu_f fn_i against its slip relative
+    to the indenter; below eps it sticks elastically with stiffness 2 mu_f
+    fn_i / eps.
+
+    Returns energy per node (N,), gradient (N,3) and the Hessian (N,3,3)
+      mu_f fn [ (f1/y) P - q s s^T ],  P = I - n n^T, f1 = f0',
+      q = 1/(eps^2 y) below eps, 1/y^3 above (PSD: eigenvalues 2/eps - 2y/eps^2
+      or 0 along s, f1/y across it, 0 along n)."""
+    r = np.asarray(x, dtype=np.float64) - x_start - np.asarray(dc, dtype=np.float64)
+    n = np.asarray(normal, dtype=np.float64)
+    s = r - np.einsum("ni,ni->n", n, r)[:, None] * n
+    y = np.linalg.norm(s, axis=1)
+    w = mu_f * np.asarray(fn, dtype=np.float64)
+    energy = w * friction_f0(y, eps)
+    below = y < eps
+    ysafe = np.where(y > 0, y, 1.0)
+    f1_over_y = np.where(below, 2.0 / eps - y / (eps * eps), 1.0 / ysafe)
+    grad = (w * f1_over_y)[:, None] * s
+    shat = s / ysafe[:, None]
+    q_y2 = np.where(below, y / (eps * eps), 1.0 / ysafe)     # q * y^2
+    P = np.eye(3)[None] - _outer(n, n)
+    hess = w[:, None, None] * (f1_over_y[:, None, None] * P - q_y2[:, None, None] * _outer(shat, shat))
+    return energy, grad, hess

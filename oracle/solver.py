@@ -29,6 +29,16 @@ this oracle solves the quasi-static problem plainly:
 Prescribed (Dirichlet) values, when given, are ramped linearly over the load
 steps: at step k the fixed DOFs hold values * k / K.
 
+Friction (mu_f > 0). The paper's contact is isotropic Coulomb (Sec. III-A).
+Reading: at each load step the nodes' normal force magnitudes fn_i = k_i
+max(0, -phi_i) and SDF normals n_i are taken at the start of the step (the
+previous converged state, indenter at its previous pose) and frozen, and
+Pi_k gains the smoothed dissipation potential sum_i mu_f fn_i f0(|s_i|) of
+contact.friction, with s_i the tangential slip of node i relative to the
+indenter's translation over the step and the smoothing slip
+eps = fric_eps_rel * h_bar. The reported contact forces include the
+friction forces.
+
 Dynamic stepping (dt > 0). The paper integrates the deformable body's dynamics
 implicitly in time, with a time step of 1e-4 s (Sec. III-A). Reading: backward
 (implicit) Euler with a lumped mass matrix, m_i = rho * sum over the tets at
@@ -73,7 +83,8 @@ class Problem:
     """One mesh + one indenter (+ optional prescribed values on fixed DOFs)."""
 
     def __init__(self, mesh, indenter, c_kappa: float = 100.0, dirichlet_values=None,
-                 dt: float = 0.0, density: float = 1.1e-9):
+                 dt: float = 0.0, density: float = 1.1e-9, mu_f: float = 0.0,
+                 fric_eps_rel: float = 0.01):
         self.X = np.asarray(mesh.nodes, dtype=np.float64)
         self.tets = np.asarray(mesh.tets, dtype=np.int64)
         self.n = len(self.X)
@@ -99,6 +110,8 @@ class Problem:
             np.add.at(self.mass, self.tets[:, a], 0.25 * float(density) * self.V)
         self.u_tilde = None      # inertial prediction u~ of the current time step (dt > 0)
         self.E_max = float(self.E.max())
+        self.mu_f = float(mu_f)
+        self.fric = None         # lagged friction state of the current load step
         self.scale_floor = self.E_max * self.h_bar ** 2 * 1e-3
         self.u_presc = np.zeros((self.n, 3))
         if dirichlet_values is not None:
@@ -113,6 +126,7 @@ class Problem:
         self.a = np.asarray(indenter.direction, dtype=np.float64)
         self.depths = np.asarray(indenter.depth_schedule, dtype=np.float64)
         self.K = len(self.depths)
+        self.fric_eps = float(fric_eps_rel) * self.h_bar
         # element -> global DOF map for assembly
         dof = (3 * self.tets[:, :, None] + np.arange(3)[None, None, :]).reshape(-1, 12)
         self._rows = np.repeat(dof, 12, axis=1).ravel()
@@ -169,16 +183,37 @@ class Problem:
         d = u - self.u_tilde
         return float(0.5 * np.sum(w * d * d)), w * d, w
 
+    def set_friction_lag(self, u_start, step):
+        """Freeze the friction state of load step ``step`` at the converged
+        displacement u_start of the previous step (indenter at its previous pose)."""
+        x0 = self.X + u_start
+        phi, n, _ = contact.sdf(self.shape, self.origin_at(step - 1), self.R, self.params, x0)
+        fn = np.where((phi < 0) & (self.k > 0), -self.k * phi, 0.0)
+        self.fric = dict(x_start=x0, dc=self.origin_at(step) - self.origin_at(step - 1),
+                         normal=n, fn=fn)
+
+    def friction_terms(self, u):
+        """(energy, gradient (Nn,3), Hessian blocks (Nn,3,3)) of the lagged
+        friction potential; zeros when frictionless."""
+        if self.mu_f <= 0.0 or self.fric is None:
+            return 0.0, np.zeros((self.n, 3)), np.zeros((self.n, 3, 3))
+        f = self.fric
+        e, g, H = contact.friction(self.X + u, f["x_start"], f["dc"], f["normal"], f["fn"],
+                                   self.mu_f, self.fric_eps)
+        return float(e.sum()), g, H
+
     def energy(self, u, step):
         Ee, minJ = self.elastic_energy(u)
         ec = self.contact_terms(u, step)[0]
-        return Ee + float(ec.sum()) + self.inertia_terms(u)[0], minJ
+        return Ee + float(ec.sum()) + self.inertia_terms(u)[0] + self.friction_terms(u)[0], minJ
 
     def gradient(self, u, step):
-        """(R, f_c): full gradient of Pi (plus the inertia term when dynamic)
-        (Nn,3) and nodal contact forces on the body."""
+        """(R, f_c): full gradient of Pi (plus the inertia and friction terms
+        when present) (Nn,3) and nodal contact forces on the body (normal
+        penalty plus friction)."""
         _, gc, _, _, _ = self.contact_terms(u, step)
-        return self.elastic_gradient(u) + gc + self.inertia_terms(u)[1], -gc
+        gf = self.friction_terms(u)[1]
+        return self.elastic_gradient(u) + gc + gf + self.inertia_terms(u)[1], -(gc + gf)
 
     def hessian(self, u, step, projected=False):
         """Global tangent (3Nn x 3Nn CSR). Exact: exact element tangent + exact
@@ -196,6 +231,9 @@ class Problem:
         w = self.inertia_terms(u)[2]
         if np.any(w):
             K = K + sp.diags(w.ravel())
+        if self.mu_f > 0.0 and self.fric is not None:
+            Hf = self.friction_terms(u)[2]
+            K = K + sp.coo_matrix((Hf.ravel(), (r.ravel(), c.ravel())), shape=K.shape).tocsr()
         return K
 
     def residual_norm(self, u, step):
@@ -241,6 +279,8 @@ class Problem:
             u_prev = u.copy()
             if self.dt > 0.0:
                 self.u_tilde = u_prev + self.dt * vel
+            if self.mu_f > 0.0:
+                self.set_friction_lag(u_prev, step)
             u[self.fixed] = (self.u_presc * (step / K))[self.fixed]
             ok = False
             for it in range(max_newton + 1):
@@ -288,5 +328,6 @@ class Problem:
                 break
         reactions = np.where(self.fixed, g, 0.0)
         self.u_tilde = None
+        self.fric = None
         return SolveResult(u, step_force, fc, reactions, iters, resid, scales,
                            converged, n_proj, step_u)
