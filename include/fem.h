@@ -114,6 +114,14 @@ typedef struct {
     double  density;          /* mass density for dt > 0, in the mesh's mass unit per */
                               /* unit volume (default 1.1e-9: 1100 kg/m^3 in t/mm^3   */
                               /* for coordinates in mm and moduli in MPa)             */
+    double  mu_f;             /* Coulomb friction coefficient (default 0: frictionless)*/
+                              /* Lagged and smoothed: at each load step the nodes'    */
+                              /* normal forces and contact normals are frozen at the  */
+                              /* step's start; the slip relative to the indenter's    */
+                              /* translation carries the dissipation mu_f fn f0(|s|)  */
+    double  friction_eps;     /* smoothing slip of f0, relative to the mesh's mean    */
+                              /* edge length (default 0.01): below it a node sticks   */
+                              /* elastically, above it it slides with force mu_f fn   */
 } fem_options;
 
 /* engines of fem_solve_batch */

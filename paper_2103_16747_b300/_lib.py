@@ -60,7 +60,8 @@ class fem_options(C.Structure):
                 ("max_backtracks", C.c_int32), ("tangent", C.c_int32),
                 ("barrier_timeout_s", C.c_double), ("batch_engine", C.c_int32), ("batch_parts", C.c_int32),
                 ("batch_tets_per_cta", C.c_int32), ("precond_degree", C.c_int32),
-                ("precond_ratio", C.c_double), ("dt", C.c_double), ("density", C.c_double)]
+                ("precond_ratio", C.c_double), ("dt", C.c_double), ("density", C.c_double),
+                ("mu_f", C.c_double), ("friction_eps", C.c_double)]
 
 
 class fem_stats(C.Structure):

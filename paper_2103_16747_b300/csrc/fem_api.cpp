@@ -291,16 +291,19 @@ void set_precond(const fem_options& o, SolveParams& P) {
   P.cheb_delta = (float)(0.5 * (b - a));
 }
 
-void set_dynamics(const fem_options& o, SolveParams& P) {
+void set_physics(const fem_options& o, double h_bar, SolveParams& P) {
   P.inv_dt = o.dt > 0.0 ? 1.0 / o.dt : 0.0;
   P.density = o.dt > 0.0 ? o.density : 0.0;
+  P.mu_f = o.mu_f;
+  P.fric_eps = o.friction_eps * h_bar;
 }
 
 bool common_options_valid(const fem_options& o) {
   return o.c_kappa > 0 && o.max_newton >= 0 && o.max_cg >= 1 && o.max_backtracks >= 0 && o.cg_rtol_max > 0 &&
          o.cg_rtol_min > 0 && o.cg_rtol_min <= o.cg_rtol_max && o.tangent >= 0 && o.tangent <= 3 &&
          o.barrier_timeout_s > 0 && o.precond_degree >= 1 && o.precond_degree <= 8 && o.precond_ratio > 1.0 &&
-         o.dt >= 0.0 && std::isfinite(o.dt) && (o.dt == 0.0 || (o.density > 0.0 && std::isfinite(o.density)));
+         o.dt >= 0.0 && std::isfinite(o.dt) && (o.dt == 0.0 || (o.density > 0.0 && std::isfinite(o.density))) &&
+         o.mu_f >= 0.0 && std::isfinite(o.mu_f) && o.friction_eps > 0.0 && std::isfinite(o.friction_eps);
 }
 
 SmemLayout plan_layout(const PartDims& d, int budget) {
@@ -356,6 +359,15 @@ SmemLayout plan_layout(const PartDims& d, int budget) {
     L.cd = place_node(12 * d.max_own);
     L.mh2 = place_node(4 * d.max_own);
     if (attempt == 1 && !nodes_shared) continue;
+    // friction Hessian blocks: touched only with friction on, so they take
+    // shared memory only where it is left over and never change the placement
+    // of the arrays above
+    if (fits(24 * d.max_own)) {
+      L.hf = take(24 * d.max_own);
+    } else {
+      L.hf = g | kInGlobal;
+      g = align_up(g + 24 * d.max_own, 16);
+    }
     L.ptn = place_opt(8 * d.max_pt);
     const int lptr_bytes = align_up(4 * (d.max_own + 1), 16);
     if (fits(lptr_bytes + 4 * d.max_lcsr)) {
@@ -541,6 +553,8 @@ void fem_default_options(fem_options* opt) {
   opt->precond_ratio = 60.0;
   opt->dt = 0.0;
   opt->density = 1.1e-9;
+  opt->mu_f = 0.0;
+  opt->friction_eps = 0.01;
 }
 
 const char* fem_last_error(void) { return g_err.c_str(); }
@@ -808,6 +822,7 @@ int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, i
     if ((e = alloc(&W.R, 3 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
     if ((e = alloc(&W.uprev, 3 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
     if ((e = alloc(&W.vel, 3 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
+    if ((e = alloc(&W.fric, 4 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
     if ((e = alloc(&W.vpub, 6 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
     if ((e = alloc(&W.dpub, (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
     unsigned long long* d_bar;
@@ -931,7 +946,7 @@ static int fill_params(fem_mesh* m, const fem_options* opt, int mode, int steps,
   memset(&P, 0, sizeof(P));
   set_precond(o, P);
   // the evaluation and product entry points are those of the quasi-static step
-  if (mode == MODE_SOLVE) set_dynamics(o, P);
+  if (mode == MODE_SOLVE) set_physics(o, m->h_bar, P);
   P.mode = mode;
   P.n_steps = steps;
   P.step = step;

@@ -324,6 +324,7 @@ int fem_batch_create(fem_mesh* const* meshes, const int32_t* n_steps, int32_t n,
     S.R = take(24 * max_nodes);
     S.uprev = take(24 * max_nodes);
     S.vel = take(24 * max_nodes);
+    S.fric = take(32 * max_nodes);
     S.tangent = take(L.tan >= 0 ? 16 : 16 * (size_t)kTanVec * max_pt);
     S.cta = take((size_t)L.gbytes * max_parts);
     S.cta_stride = L.gbytes;
@@ -369,7 +370,7 @@ int fem_batch_create(fem_mesh* const* meshes, const int32_t* n_steps, int32_t n,
     P.cg_rtol_min = o.cg_rtol_min;
     P.timeout_ns = (unsigned long long)(o.barrier_timeout_s * 1e9);
     set_precond(o, P);
-    set_dynamics(o, P);
+    set_physics(o, m->h_bar, P);
     P.depths = reinterpret_cast<const double*>(b->ws + b->depths_off) + b->depth_at[i];
     b->h_stats0[i] = st0;
   }

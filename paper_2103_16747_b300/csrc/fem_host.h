@@ -75,8 +75,10 @@ int fail(int code, const char* fmt, ...);  // sets the message, returns code
 int cuda_fail(cudaError_t e, const char* what);
 SmemLayout plan_layout(const PartDims& d, int budget);
 void set_precond(const fem_options& o, SolveParams& P);
-// Time stepping of the solve: inv_dt = 1/dt and the density (dt = 0: quasi-static).
-void set_dynamics(const fem_options& o, SolveParams& P);
+// Time stepping (inv_dt = 1/dt, density; dt = 0: quasi-static) and friction
+// (mu_f, smoothing slip friction_eps * h_bar) of a solve on a mesh of mean
+// edge length h_bar.
+void set_physics(const fem_options& o, double h_bar, SolveParams& P);
 // Checks the option fields every solve entry point shares.
 bool common_options_valid(const fem_options& o);
 int smem_budget(const fem_mesh* m, int static_smem);

@@ -69,6 +69,7 @@ struct WorkDev {
   double* R;                        // [3*n_nodes] residual of the last evaluation
   double* uprev;                    // [3*n_nodes] converged displacement of the previous load step
   double* vel;                      // [3*n_nodes] velocity (dynamic stepping; null when quasi-static)
+  double* fric;                     // [4*n_nodes] friction state of the load step: normal, normal force
   const double* u_presc;            // [3*n_nodes] prescribed values (or null)
   unsigned long long* vpub;         // [2][n_nodes][3] published PCG vector, (epoch, FP32) words
   float4* dpub;                     // [n_nodes] published Newton direction
@@ -94,6 +95,7 @@ struct SolveParams {
   int cheb_deg;                     // preconditioner: 1 = block-Jacobi, d > 1 = Chebyshev of degree d on it
   float cheb_theta, cheb_delta;     // centre and half-width of the Chebyshev interval
   double inv_dt, density;           // dynamic stepping: 1 / time step (0: quasi-static), mass density
+  double mu_f, fric_eps;            // Coulomb coefficient (0: frictionless), smoothing slip
   int max_newton, max_cg, max_backtracks;
   double tol, c_kappa, cg_rtol_max, cg_rtol_min;
   unsigned long long timeout_ns;
@@ -113,7 +115,7 @@ __host__ __device__ inline int align_up(int v, int a) { return (v + a - 1) / a *
 
 struct SmemLayout {
   int lm, red, chunk;                             // always shared
-  int acc, x, r, ucg, w, s, p, minv, hc, mask, cursor, ut, cd, mh2;
+  int acc, x, r, ucg, w, s, p, minv, hc, mask, cursor, ut, cd, mh2, hf;
   int tan, ptn, lptr, lcsr;                       // resident part data, or -1: read from global memory
   int chunk_tets;                                 // part tets per chunk of the evaluation passes
   int total;                                      // dynamic shared bytes
@@ -149,7 +151,7 @@ struct SlotScratch {
   long long ctrl;                   // group engine: barrier counter, abort word, job word (u64 each)
   long long vpub, cgslot, partials; // group engine: as in WorkDev
   long long dpub, tangent, R, uprev, cta;   // offsets inside a slot
-  long long vel;
+  long long vel, fric;
   long long cta_stride;             // per-CTA bytes of the cta region
 };
 

@@ -86,7 +86,7 @@ __device__ __forceinline__ void jacobi_eig3(float A[3][3], float V[3][3]) {
 // FP32 Jacobi pass gives V, which is re-orthonormalised and refined by two FP64
 // sweeps. With s_i - 1 = delta_i / (1 + sqrt(1 + delta_i)) nothing cancels at
 // small strain. P = F V diag(psi_i / s_i) V^T (= R V diag(psi_i) V^T).
-__device__ __noinline__ void corot_stress_f64(const double H[9], double mu, double lam, double P[9],
+static __device__ __noinline__ void corot_stress_f64(const double H[9], double mu, double lam, double P[9],
                                                  double& psi) {
   double Cm[3][3];
 #pragma unroll

@@ -186,7 +186,7 @@ bool admit(fem_server* v, int slot, Request& q) {
   P.timeout_ns = (unsigned long long)(v->o.barrier_timeout_s * 1e9);
   P.init_zero = 1;
   set_precond(v->o, P);
-  set_dynamics(v->o, P);
+  set_physics(v->o, m->h_bar, P);
   P.shape = q.ind.shape;
   for (int k = 0; k < 3; ++k) {
     P.origin[k] = q.ind.pose[k];
@@ -196,7 +196,6 @@ bool admit(fem_server* v, int slot, Request& q) {
   for (int k = 0; k < 9; ++k) P.R[k] = q.ind.pose[3 + k];
   P.depths = slot_ptr(v, slot, R.depths);
   std::copy(q.depths.begin(), q.depths.end(), v->h_dep);
-  (void)m;
   cudaError_t e = cudaMemcpyAsync(slot_ptr(v, slot, R.depths), v->h_dep, 8 * q.depths.size(),
                                   cudaMemcpyHostToDevice, v->cs);
   if (e == cudaSuccess)
@@ -552,6 +551,7 @@ int fem_server_create(fem_mesh* const* meshes, int32_t n_meshes, int32_t max_ste
     S.R = take(24 * max_nodes);
     S.uprev = take(24 * max_nodes);
     S.vel = take(24 * max_nodes);
+    S.fric = take(32 * max_nodes);
     S.tangent = take(L.tan >= 0 ? 16 : 16 * (size_t)kTanVec * max_pt);
     S.cta = take((size_t)L.gbytes * max_parts);
     S.cta_stride = L.gbytes;

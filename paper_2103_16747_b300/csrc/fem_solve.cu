@@ -135,8 +135,12 @@ struct Ctx {
   int CH;                 // part tets per chunk of the evaluation passes
   double *u, *uprev, *R, *fc;   // owned entries of global node arrays (index 3*i+k)
   double* vel;                  // owned velocities (dynamic stepping) or null
+  double* fric;                 // owned friction state of the load step (normal, normal force) or null
   const double *X, *kb, *vl;
   float* mh2;                   // owned nodes: lumped mass / dt^2 (0 when quasi-static)
+  float* hf;                    // owned nodes: friction Hessian block (xx xy xz yy yz zz)
+  bool fric_on;                 // friction in this solve
+  double dc[3];                 // indenter translation over the current load step
   double *ut, *chunkd, *red;
   float *x, *r, *ucg, *w, *s, *p, *acc, *minv, *hc, *chunkf, *cd;
   float4* lm;
@@ -385,11 +389,14 @@ __device__ bool eval_pass(Ctx& C, const MeshDev& M, const WorkDev& W, const Solv
   v[EV_SLOPE] = sl;
   const double dt = P.inv_dt > 0.0 ? 1.0 / P.inv_dt : 0.0;
   for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
+    const unsigned mk = C.mask[i];
     if (P.inv_dt > 0.0) {
       // backward Euler: inertia m / (2 dt^2) |u - (u_n + dt v_n)|^2 (u_n = uprev)
+      // on the free components
       const double mh = P.density * C.vl[i] * P.inv_dt * P.inv_dt;
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
+        if (mk & (1u << k)) continue;
         const double d = C.ut[3 * i + k] - (C.uprev[3 * i + k] + dt * C.vel[3 * i + k]);
         C.R[3 * i + k] += mh * d;
         e_el += 0.5 * mh * d * d;
@@ -416,7 +423,48 @@ __device__ bool eval_pass(Ctx& C, const MeshDev& M, const WorkDev& W, const Solv
         h[0] = sk * (float)n[0]; h[1] = sk * (float)n[1]; h[2] = sk * (float)n[2];
       }
     }
-    const unsigned mk = C.mask[i];
+    if (C.fric_on) {
+      // lagged, smoothed Coulomb friction: mu_f fn f0(|s|), s the slip across
+      // the frozen normal relative to the indenter's translation
+      const double fn = C.fric[4 * i + 3];
+      float hb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (fn > 0.0) {
+        const double nn[3] = {C.fric[4 * i], C.fric[4 * i + 1], C.fric[4 * i + 2]};
+        double r[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) r[k] = C.ut[3 * i + k] - C.uprev[3 * i + k] - C.dc[k];
+        const double rn = nn[0] * r[0] + nn[1] * r[1] + nn[2] * r[2];
+        const double sl[3] = {r[0] - rn * nn[0], r[1] - rn * nn[1], r[2] - rn * nn[2]};
+        const double y = sqrt(sl[0] * sl[0] + sl[1] * sl[1] + sl[2] * sl[2]);
+        const double eps = P.fric_eps, wf = P.mu_f * fn;
+        double f0, f1y, qy2;   // f0(y), f0'(y)/y and q y^2 of the Hessian
+        if (y < eps) {
+          f0 = y * y / eps - y * y * y / (3.0 * eps * eps) + eps / 3.0;
+          f1y = 2.0 / eps - y / (eps * eps);
+          qy2 = y / (eps * eps);
+        } else {
+          f0 = y;
+          f1y = 1.0 / y;
+          qy2 = 1.0 / y;
+        }
+        v[EV_CONTACT] += wf * f0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const double g = wf * f1y * sl[k];
+          C.R[3 * i + k] += g;
+          fcv[k] -= g;
+        }
+        const double iy = y > 0.0 ? 1.0 / y : 0.0;
+        const double sh[3] = {sl[0] * iy, sl[1] * iy, sl[2] * iy};
+        const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+          hb[k] = (float)(wf * (f1y * ((ia[k] == ib[k] ? 1.0 : 0.0) - nn[ia[k]] * nn[ib[k]]) -
+                                qy2 * sh[ia[k]] * sh[ib[k]]));
+      }
+#pragma unroll
+      for (int k = 0; k < 6; ++k) C.hf[6 * i + k] = hb[k];
+    }
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       C.fc[3 * i + k] = fcv[k];
@@ -492,6 +540,10 @@ __device__ void tangent_pass(Ctx& C, const MeshDev& M, int mode) {
     m[3] += h1 * h1; m[4] += h1 * h2; m[5] += h2 * h2;
     const float mh = C.mh2[i];
     m[0] += mh; m[3] += mh; m[5] += mh;
+    if (C.fric_on) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) m[k] += C.hf[6 * i + k];
+    }
     inv_block_masked(m, C.mask[i], C.minv + 6 * i);
   }
   __syncthreads();
@@ -546,16 +598,25 @@ __device__ __forceinline__ void apply_minv(const float* mi, const float v[3], fl
   out[2] = mi[2] * v[0] + mi[4] * v[1] + mi[5] * v[2];
 }
 
-// Contact Gauss-Newton term, lumped mass / dt^2 (dynamic stepping) and
-// Dirichlet mask on the owned product.
+// Contact Gauss-Newton term, lumped mass / dt^2 (dynamic stepping), friction
+// block and Dirichlet mask on the owned product.
 __device__ __forceinline__ void finish_product(const Ctx& C, int i, const float v[3], float out[3]) {
   const float h0 = C.hc[3 * i], h1 = C.hc[3 * i + 1], h2 = C.hc[3 * i + 2];
   const float hv = h0 * v[0] + h1 * v[1] + h2 * v[2];
   const float mh = C.mh2[i];
   const unsigned mk = C.mask[i];
-  out[0] = (mk & 1u) ? 0.f : C.acc[3 * i] + h0 * hv + mh * v[0];
-  out[1] = (mk & 2u) ? 0.f : C.acc[3 * i + 1] + h1 * hv + mh * v[1];
-  out[2] = (mk & 4u) ? 0.f : C.acc[3 * i + 2] + h2 * hv + mh * v[2];
+  float a0 = C.acc[3 * i] + h0 * hv + mh * v[0];
+  float a1 = C.acc[3 * i + 1] + h1 * hv + mh * v[1];
+  float a2 = C.acc[3 * i + 2] + h2 * hv + mh * v[2];
+  if (C.fric_on) {
+    const float* f = C.hf + 6 * i;
+    a0 += f[0] * v[0] + f[1] * v[1] + f[2] * v[2];
+    a1 += f[1] * v[0] + f[3] * v[1] + f[4] * v[2];
+    a2 += f[2] * v[0] + f[4] * v[1] + f[5] * v[2];
+  }
+  out[0] = (mk & 1u) ? 0.f : a0;
+  out[1] = (mk & 2u) ? 0.f : a1;
+  out[2] = (mk & 4u) ? 0.f : a2;
 }
 
 // ------------------------------------------------- PCG sync, cooperative form
@@ -982,6 +1043,9 @@ __device__ void setup_ctx(Ctx& C, const MeshDev& M, const WorkDev& W, const Smem
   C.kb = M.kbase + C.node0;
   C.vl = M.vol_lumped + C.node0;
   C.vel = W.vel ? W.vel + 3 * (size_t)C.node0 : nullptr;
+  C.fric = W.fric ? W.fric + 4 * (size_t)C.node0 : nullptr;
+  C.fric_on = false;
+  C.dc[0] = C.dc[1] = C.dc[2] = 0.0;
   C.ut = reinterpret_cast<double*>(at(L.ut));
   C.chunkd = reinterpret_cast<double*>(smem + L.chunk);
   C.chunkf = reinterpret_cast<float*>(smem + L.chunk);
@@ -998,6 +1062,7 @@ __device__ void setup_ctx(Ctx& C, const MeshDev& M, const WorkDev& W, const Smem
   C.hc = reinterpret_cast<float*>(at(L.hc));
   C.cd = reinterpret_cast<float*>(at(L.cd));
   C.mh2 = reinterpret_cast<float*>(at(L.mh2));
+  C.hf = reinterpret_cast<float*>(at(L.hf));
   C.mask = at(L.mask);
   C.cursor = reinterpret_cast<int*>(at(L.cursor));
   C.hsrc = M.halo_src + C.halo0;
@@ -1068,6 +1133,7 @@ __device__ bool solve_body(Ctx& C, const MeshDev& M, const WorkDev& W, const Sol
   int newton_total = 0, cg_total = 0, bt_total = 0, exact_total = 0;
   long long products = 0;
   double rn = 0.0, scale = 1.0, energy = 0.0;
+  C.fric_on = P.mu_f > 0.0 && C.fric != nullptr;
   int steps_done = 0;
   for (int step = 1; step <= P.n_steps; ++step) {
     double org[3];
@@ -1075,25 +1141,23 @@ __device__ bool solve_body(Ctx& C, const MeshDev& M, const WorkDev& W, const Sol
     const double dk = __ldcg(P.depths + step - 1);
 #pragma unroll
     for (int k = 0; k < 3; ++k) org[k] = P.origin[k] + dk * P.dir[k];
-    if (P.has_presc) {
-      const double ramp = (double)step / (double)P.n_steps;
-      for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
-        const unsigned mk = C.mask[i];
-        const int g = C.node0 + i;
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-          if (mk & (1u << k)) C.u[3 * i + k] = W.u_presc[3 * g + k] * ramp;
-      }
-    }
     // secant predictor: start from u_{k-1} + r (u_{k-1} - u_{k-2}), r the ratio
     // of depth increments; kept only if every tet stays valid
+    const double dkp = step >= 2 ? __ldcg(P.depths + step - 2) : 0.0;   // previous depth
     double ratio = 0.0;
     if (step >= 2) {
-      const double d2 = dk - __ldcg(P.depths + step - 2);
-      const double d1 = __ldcg(P.depths + step - 2) - (step >= 3 ? __ldcg(P.depths + step - 3) : 0.0);
+      const double d2 = dk - dkp;
+      const double d1 = dkp - (step >= 3 ? __ldcg(P.depths + step - 3) : 0.0);
       ratio = d1 != 0.0 ? d2 / d1 : 0.0;
       if (P.inv_dt > 0.0) ratio = 1.0;   // dynamic stepping: start from u_n + dt v_n
     }
+    double orgp[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      orgp[k] = P.origin[k] + dkp * P.dir[k];
+      C.dc[k] = (dk - dkp) * P.dir[k];
+    }
+    // state of the step start, all from u_n (the converged previous step)
     for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
       const unsigned mk = C.mask[i];
 #pragma unroll
@@ -1104,6 +1168,31 @@ __device__ bool solve_body(Ctx& C, const MeshDev& M, const WorkDev& W, const Sol
         if (P.inv_dt > 0.0)
           C.vel[3 * i + k] = (mk & (1u << k)) ? 0.0 : (C.u[3 * i + k] - C.uprev[3 * i + k]) * P.inv_dt;
         C.uprev[3 * i + k] = C.u[3 * i + k];
+      }
+      if (C.fric_on) {
+        // friction state frozen for the step: contact normal and normal force
+        // at u_n with the indenter at its previous pose
+        const double kp = C.kb[i] * P.c_kappa;
+        double fn = 0.0, n[3] = {0.0, 0.0, 0.0};
+        if (kp > 0.0) {
+          const double xx[3] = {C.X[3 * i] + C.u[3 * i], C.X[3 * i + 1] + C.u[3 * i + 1],
+                                C.X[3 * i + 2] + C.u[3 * i + 2]};
+          double phi;
+          indenter_sdf(P.shape, orgp, P.R, P.iparams, xx, phi, n);
+          if (phi < 0.0) fn = -kp * phi;
+        }
+        C.fric[4 * i] = n[0]; C.fric[4 * i + 1] = n[1]; C.fric[4 * i + 2] = n[2];
+        C.fric[4 * i + 3] = fn;
+      }
+    }
+    if (P.has_presc) {
+      const double ramp = (double)step / (double)P.n_steps;
+      for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
+        const unsigned mk = C.mask[i];
+        const int g = C.node0 + i;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+          if (mk & (1u << k)) C.u[3 * i + k] = W.u_presc[3 * g + k] * ramp;
       }
     }
     __syncthreads();
@@ -1341,6 +1430,7 @@ __global__ void __launch_bounds__(kBlock, 1) cluster_kernel(const BatchJob* __re
       w.R = reinterpret_cast<double*>(sb + S.R);
       w.uprev = reinterpret_cast<double*>(sb + S.uprev);
       w.vel = reinterpret_cast<double*>(sb + S.vel);
+      w.fric = reinterpret_cast<double*>(sb + S.fric);
       w.dpub = reinterpret_cast<float4*>(sb + S.dpub);
       w.tangent = reinterpret_cast<float4*>(sb + S.tangent);
       w.out_fc = J->out_fc;
@@ -1435,6 +1525,7 @@ __global__ void __launch_bounds__(kBlock, 1) group_kernel(GroupRun R, SlotScratc
       w.R = reinterpret_cast<double*>(sb + S.R);
       w.uprev = reinterpret_cast<double*>(sb + S.uprev);
       w.vel = reinterpret_cast<double*>(sb + S.vel);
+      w.fric = reinterpret_cast<double*>(sb + S.fric);
       w.vpub = reinterpret_cast<unsigned long long*>(sb + S.vpub);
       w.dpub = reinterpret_cast<float4*>(sb + S.dpub);
       w.tangent = reinterpret_cast<float4*>(sb + S.tangent);
