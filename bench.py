@@ -21,6 +21,9 @@ Batched workloads print their own line:
   --workload dynamic the fingertip solve as 20 backward-Euler time steps of
                      1e-4 s (the paper's implicit time step) from rest, with
                      the lumped mass of a 1100 kg/m^3 body; same line format.
+  --workload calibrated  the same solve on the paper's calibrated model: one
+                     co-rotational shell, E=1.55 MPa, nu=0.316.
+  --workload friction    the fingertip solve with Coulomb friction mu=0.783.
   --workload serve   Poisson streams of requests over a resident pool of 16
                      fingertip meshes (5k-200k tets) through the request
                      server (continuous batching), one session per offered
@@ -28,7 +31,7 @@ Batched workloads print their own line:
                      one-solve-per-launch path on the same arrival trace.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference]
-                    [--workload fingertip|dynamic|batch|uneven|serve]
+                    [--workload fingertip|dynamic|calibrated|friction|batch|uneven|serve]
 
 Multi-GPU runs (torchrun) are independent replicas: every rank solves its own
 indentation, no collectives on the data path (weak scaling).
@@ -56,8 +59,36 @@ WORKLOAD = ("fingertip_sphere: two-layer half-capsule fingertip R=7 mm L=40 mm (
             "E=1.5 MPa nu=0.45 over 2 mm inner E=0.2 MPa nu=0.48, core fixed), 38880 tets / "
             "8740 nodes; sphere r=4 mm pressed 2 mm normal to a seeded skin point in 20 load steps")
 DYN_DT, DYN_DENSITY = 1e-4, 1.1e-9     # s; t/mm^3 (1100 kg/m^3)
-DYN_WORKLOAD = (WORKLOAD + f"; dynamic: each load step one backward-Euler time step of {DYN_DT:g} s from rest, "
-                f"lumped mass of density {DYN_DENSITY:g} t/mm^3")
+FRICTION_MU = 0.783                    # the paper's calibrated Coulomb coefficient
+# single-solve variants of the fingertip workload: description, oracle
+# arguments, stored oracle solution (its Newton count extrapolates the CPU leg)
+VARIANTS = {
+    "fingertip": (WORKLOAD, {}, "fingertip_sphere_oracle.npz"),
+    "dynamic": (WORKLOAD + f"; dynamic: each load step one backward-Euler time step of {DYN_DT:g} s from "
+                f"rest, lumped mass of density {DYN_DENSITY:g} t/mm^3",
+                {"dt": DYN_DT, "density": DYN_DENSITY}, "fingertip_sphere_dynamic_oracle.npz"),
+    "calibrated": ("fingertip_calibrated: the same geometry and load as one co-rotational linear-elastic shell "
+                   "(E=1.55 MPa, nu=0.316, the paper's calibrated parameters) over the fixed core",
+                   {}, "fingertip_calibrated_oracle.npz"),
+    "friction": (WORKLOAD + f"; lagged smoothed Coulomb friction mu={FRICTION_MU} (slip smoothing 0.01 h_bar)",
+                 {"mu_f": FRICTION_MU}, "fingertip_sphere_friction_oracle.npz"),
+}
+
+
+def variant_case(name, seed=None):
+    """(mesh, indenter) of a single-solve variant."""
+    import workloads as W
+    kw = {} if seed is None else {"seed": seed}
+    return W.fingertip_calibrated(**kw) if name == "calibrated" else W.fingertip_sphere(**kw)
+
+
+def variant_options(F, name):
+    opt = F.fem_default_options()
+    if name == "dynamic":
+        opt.dt, opt.density = DYN_DT, DYN_DENSITY
+    elif name == "friction":
+        opt.mu_f = FRICTION_MU
+    return opt
 
 
 def replica_seed(rank: int) -> int:
@@ -196,7 +227,7 @@ def profiled_traffic():
         return None
 
 
-def cpu_oracle_rate(mesh, ind, n_load_steps, dynamic=False):
+def cpu_oracle_rate(mesh, ind, n_load_steps, variant="fingertip"):
     """Time the oracle (as it stands) on the first n_load_steps of the same
     solve and extrapolate to a full solve by Newton iterations, using the
     oracle's Newton count for the full solve stored in tests/golden."""
@@ -206,14 +237,14 @@ def cpu_oracle_rate(mesh, ind, n_load_steps, dynamic=False):
         def threadpool_info():
             return [{"num_threads": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))}]
     from oracle import Problem
-    p = Problem(mesh, ind, dt=DYN_DT, density=DYN_DENSITY) if dynamic else Problem(mesh, ind)
+    _, kwargs, golden = VARIANTS[variant]
+    p = Problem(mesh, ind, **kwargs)
     t0 = time.perf_counter()
     r = p.solve(tol=1e-10, load_steps=n_load_steps)
     dt = time.perf_counter() - t0
     its = int(np.sum(r.newton_iters[:n_load_steps]))
     full_its = None
-    g = os.path.join(ROOT, "tests", "golden",
-                     "fingertip_sphere_dynamic_oracle.npz" if dynamic else "fingertip_sphere_oracle.npz")
+    g = os.path.join(ROOT, "tests", "golden", golden)
     if os.path.exists(g):
         full_its = int(np.sum(np.load(g)["newton_iters"]))
     per_it = dt / max(its, 1)
@@ -231,15 +262,14 @@ def run_reference(args, rank, world):
     """The oracle as it stands on the host cores (rank 0 only)."""
     if rank != 0:
         return
-    import workloads as W
-    mesh, ind = W.fingertip_sphere()
-    dyn = args.workload == "dynamic"
+    variant = args.workload if args.workload in VARIANTS else "fingertip"
+    mesh, ind = variant_case(variant)
     for _ in range(args.warmup):
-        cpu_oracle_rate(mesh, ind, 1, dyn)
+        cpu_oracle_rate(mesh, ind, 1, variant)
     times, rates = [], []
     cores = 1
     for _ in range(args.steps):
-        r = cpu_oracle_rate(mesh, ind, 1, dyn)
+        r = cpu_oracle_rate(mesh, ind, 1, variant)
         times.append(r["seconds"])
         rates.append(r["value"])
         cores = r["cores"]
@@ -247,7 +277,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": DYN_WORKLOAD if dyn else WORKLOAD, "tol": TOL},
+            "data": "synthetic", "config": {"workload": VARIANTS[variant][0], "tol": TOL},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "each step: load step 1 of 20 of the solve, extrapolated by "
                                        "Newton iterations to a full solve"},
@@ -265,15 +295,13 @@ def run_cuda(args, rank, world, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    mesh, ind = W.fingertip_sphere(seed=replica_seed(rank))
+    variant = args.workload
+    mesh, ind = variant_case(variant, seed=replica_seed(rank))
     stream = torch.cuda.Stream(device=dev)
     solver = F.IndentationSolver(mesh, cuda_stream=stream)
     solver.set_indenter(ind)
     info = solver.info()
-    opt = F.fem_default_options()
-    dyn = args.workload == "dynamic"
-    if dyn:
-        opt.dt, opt.density = DYN_DT, DYN_DENSITY
+    opt = variant_options(F, variant)
     n = mesh.n_nodes
     d_u = torch.zeros((n, 3), dtype=torch.float64, device=dev)
     d_f = torch.zeros((ind.n_steps, 3), dtype=torch.float64, device=dev)
@@ -344,7 +372,7 @@ def run_cuda(args, rank, world, local):
             "warmup": args.warmup, "ms_per_step": total * 1000.0 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 (tangent, PCG vectors) + f64 (residual, "
             "energy, reductions, displacement)", "data": "synthetic",
-            "config": {"workload": DYN_WORKLOAD if dyn else WORKLOAD, "tol": TOL, "n_parts": info.n_parts,
+            "config": {"workload": VARIANTS[variant][0], "tol": TOL, "n_parts": info.n_parts,
                        "l2": "flushed between timed steps (256 MiB write, L2 is 126 MB)",
                        "replicas": world, "newton_iters": s0.newton_iters, "cg_iters": s0.cg_iters,
                        "tangent_products": s0.tangent_products, "backtracks": s0.backtracks,
@@ -360,7 +388,7 @@ def run_cuda(args, rank, world, local):
                          "compact_accounting_GBs": cmp_b / (kms / 1000.0) / 1e9},
             "clocks": clk.summary()}
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = {k: v for k, v in cpu_oracle_rate(mesh, ind, 2, dyn).items() if k != "seconds"}
+        line["cpu_baseline"] = {k: v for k, v in cpu_oracle_rate(mesh, ind, 2, variant).items() if k != "seconds"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     solver.close()
@@ -613,8 +641,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["fingertip", "dynamic", "batch", "uneven", "serve"],
-                    default="fingertip")
+    ap.add_argument("--workload", choices=["fingertip", "dynamic", "calibrated", "friction", "batch", "uneven",
+                                           "serve"], default="fingertip")
     ap.add_argument("--rates", type=float, nargs="+", default=[1.0, 2.0, 4.0, 8.0, 16.0],
                     help="offered request rates (req/s) of the serve workload")
     ap.add_argument("--serve-seconds", type=float, default=20.0)
@@ -629,7 +657,7 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
-    elif args.workload in ("fingertip", "dynamic"):
+    elif args.workload in VARIANTS:
         run_cuda(args, rank, world, local)
     elif args.workload == "serve":
         run_serve(args, rank, world, local)

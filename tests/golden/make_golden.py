@@ -7,12 +7,17 @@ load steps):
                                        time steps of DYN_DT s, from rest, with
                                        the lumped mass of density DYN_DENSITY
                                        (mm, N, s units: t/mm^3)
-  fingertip_sphere_corot_oracle.npz    quasi-static, both layers co-rotational
-                                       linear elastic
+  fingertip_calibrated_oracle.npz      quasi-static, the calibrated preset: one
+                                       co-rotational shell (E=1.55 MPa, nu=0.316)
+                                       over the fixed core, same load
+  fingertip_sphere_friction_oracle.npz quasi-static with Coulomb friction
+                                       mu_f = FRICTION_MU (the paper's calibrated
+                                       coefficient)
 
 Calls only ``oracle/`` and the seeded input generators; the GPU parity tests
 compare against the stored arrays because the full oracle solve takes minutes.
-Run from the repository root:  python tests/golden/make_golden.py [static|dynamic|corot]
+Run from the repository root:
+    python tests/golden/make_golden.py [static|dynamic|corot|friction]
 """
 import hashlib
 import os
@@ -39,6 +44,8 @@ def mesh_digest(mesh, ind):
 # time step of the paper's implicit integration (Sec. III-A) and a skin-like density
 DYN_DT = 1e-4
 DYN_DENSITY = 1.1e-9
+# Coulomb coefficient calibrated in the paper (Sec. III-A)
+FRICTION_MU = 0.783
 
 
 def main(kind="static"):
@@ -47,9 +54,13 @@ def main(kind="static"):
     if kind == "dynamic":
         r = Problem(mesh, ind, dt=DYN_DT, density=DYN_DENSITY).solve(tol=1e-10)
         name = "fingertip_sphere_dynamic_oracle.npz"
+    elif kind == "friction":
+        r = Problem(mesh, ind, mu_f=FRICTION_MU).solve(tol=1e-10)
+        name = "fingertip_sphere_friction_oracle.npz"
     elif kind == "corot":
-        r = Problem(W.with_model(mesh, 1), ind).solve(tol=1e-10)
-        name = "fingertip_sphere_corot_oracle.npz"
+        mesh, ind = W.fingertip_calibrated()
+        r = Problem(mesh, ind).solve(tol=1e-10)
+        name = "fingertip_calibrated_oracle.npz"
     else:
         r = Problem(mesh, ind).solve(tol=1e-10)
         name = "fingertip_sphere_oracle.npz"
@@ -62,5 +73,5 @@ def main(kind="static"):
 
 
 if __name__ == "__main__":
-    for k in (sys.argv[1:] or ["static", "dynamic", "corot"]):
+    for k in (sys.argv[1:] or ["static", "dynamic", "corot", "friction"]):
         main(k)

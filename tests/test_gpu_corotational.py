@@ -3,7 +3,8 @@ paper's simulator uses for the skin, Sec. III-A) against the FP64 oracle,
 through the C ABI: the FP64 residual and energy, the FP32 tangent product,
 full solves (all co-rotational, and both laws mixed in one mesh), the
 homogeneous uniaxial closed form under prescribed displacements, element
-stress and the fingertip against its stored oracle solution.
+stress and the calibrated co-rotational fingertip against its stored oracle
+solution.
 
 Tolerances as for the neo-Hookean law: residual 1e-10 relative, tangent
 product 2e-5, solves rel-L2(u) <= 1e-4 and step forces <= 1e-3."""
@@ -154,19 +155,20 @@ def test_element_stress_matches_oracle(F):
 
 
 @pytest.fixture(scope="module")
-def fingertip_corot_golden():
-    path = os.path.join(HERE, "golden", "fingertip_sphere_corot_oracle.npz")
+def fingertip_calibrated_golden():
+    path = os.path.join(HERE, "golden", "fingertip_calibrated_oracle.npz")
     if not os.path.exists(path):
         pytest.skip("golden file missing: run tests/golden/make_golden.py corot")
     g = np.load(path)
-    m, ind = W.fingertip_sphere()
+    m, ind = W.fingertip_calibrated()
     from tests.golden.make_golden import mesh_digest
     assert str(g["digest"]) == mesh_digest(m, ind), "workload generator changed: regenerate golden"
-    return W.with_model(m, 1), ind, g
+    return m, ind, g
 
 
-def test_fingertip_corot_matches_oracle(F, fingertip_corot_golden):
-    m, ind, g = fingertip_corot_golden
+def test_fingertip_calibrated_matches_oracle(F, fingertip_calibrated_golden):
+    """The paper's calibrated co-rotational shell (E=1.55 MPa, nu=0.316)."""
+    m, ind, g = fingertip_calibrated_golden
     out = _solver(F, m, ind).solve(1e-6)
     st = out["stats"]
     assert out["rc"] == 0 and st.steps_done == 20

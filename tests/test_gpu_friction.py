@@ -122,3 +122,24 @@ def test_friction_options_are_validated(F):
         opt = F.fem_default_options()
         setattr(opt, field, value)
         assert s.solve(1e-6, opt, check=False)["rc"] == F.FEM_ERR_ARG
+
+
+def test_fingertip_with_friction_matches_oracle(F):
+    import os
+    here = os.path.dirname(os.path.abspath(__file__))
+    path = os.path.join(here, "golden", "fingertip_sphere_friction_oracle.npz")
+    if not os.path.exists(path):
+        pytest.skip("golden file missing: run tests/golden/make_golden.py friction")
+    from tests.golden.make_golden import FRICTION_MU, mesh_digest
+    g = np.load(path)
+    m, ind = W.fingertip_sphere()
+    assert str(g["digest"]) == mesh_digest(m, ind), "workload generator changed: regenerate golden"
+    out = _solve(F, m, ind, FRICTION_MU)
+    st = out["stats"]
+    assert out["rc"] == 0 and st.steps_done == 20
+    e_u = rel(out["u"], g["u"])
+    e_f = [rel(out["step_force"][k], g["step_force"][k]) for k in range(1, 20)]
+    print(f"fingertip with friction: rel-L2(u)={e_u:.2e} max rel F={max(e_f):.2e} newton={st.newton_iters} "
+          f"cg={st.cg_iters} kernel={st.kernel_ms:.1f} ms")
+    assert e_u <= 1e-4
+    assert max(e_f) <= 1e-3

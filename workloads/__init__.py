@@ -19,6 +19,10 @@ synthetic geometry):
   * ``uneven_fingertips``  fingertips with R~U[5,10] and a log-uniform tet count.
   * ``with_model``         a copy of a mesh whose materials carry an element-law
                            id (third column: 0 neo-Hookean, 1 co-rotational).
+  * ``fingertip_calibrated`` the fingertip geometry as one co-rotational shell
+                           (skin and inner layer alike: E=1.55 MPa, nu=0.316, the
+                           paper's calibrated simulator parameters, Sec. III-A) over
+                           the fixed core, with the single-fingertip sphere load.
 """
 from __future__ import annotations
 
@@ -50,6 +54,12 @@ def with_model(mesh, model):
     ids = np.broadcast_to(np.asarray(model, dtype=np.float64), (len(mats),))
     m.materials = np.column_stack([mats, ids])
     return m
+
+
+def fingertip_calibrated(seed: int = SEED_BASE + 1):
+    """Calibrated co-rotational shell over the rigid core, sphere indentation."""
+    mesh = with_model(fingertip_mesh(E_skin=1.55, nu_skin=0.316, E_inner=1.55, nu_inner=0.316), 1)
+    return mesh, fingertip_sphere_indentation(mesh, seed=seed)
 
 
 def fingertip_sphere(seed: int = SEED_BASE + 1):
