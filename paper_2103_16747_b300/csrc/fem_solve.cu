@@ -288,7 +288,8 @@ __device__ void load_local_positions(Ctx& C, const MeshDev& M, const WorkDev& W,
 // tl at buf[(a * NV + k) * CH + tl]. Entries of each node are sorted by local
 // tet index, so walking them chunk by chunk keeps one fixed summation order.
 template <int NV, typename T>
-__device__ __forceinline__ void gather_chunk(Ctx& C, int CH, const T* buf, int c0, T* acc, bool single) {
+__device__ __forceinline__ void gather_chunk(Ctx& C, int CH, const T* buf, int c0, T* acc, bool single,
+                                             bool assign = false) {
   if (single) {
     // whole part in one chunk: every entry belongs to it, no cursor needed.
     // 2^gseg consecutive lanes share a node: lane g of the group sums entries
@@ -316,7 +317,7 @@ __device__ __forceinline__ void gather_chunk(Ctx& C, int CH, const T* buf, int c
         for (int k = 0; k < NV; ++k) sum[k] += __shfl_xor_sync(0xffffffffu, sum[k], o);
       if (i < C.n_own && g == 0)
 #pragma unroll
-        for (int k = 0; k < NV; ++k) acc[NV * i + k] += sum[k];
+        for (int k = 0; k < NV; ++k) acc[NV * i + k] = assign ? sum[k] : acc[NV * i + k] + sum[k];
     }
     return;
   }
@@ -348,6 +349,69 @@ enum { EV_ELASTIC = 0, EV_BAD, EV_CONTACT, EV_RR, EV_FCFC, EV_FX, EV_FY, EV_FZ, 
 struct Bufs {
   int slot;   // next partial-slot buffer
 };
+
+// Lagged, smoothed Coulomb friction at owned node i (friction on): mu_f fn
+// f0(|s|), s the slip across the frozen normal relative to the indenter's
+// translation. Adds the force to R and fcv, stores the node's FP32 Hessian
+// block in hf and returns the energy. Kept out of line: it runs per owned
+// node, and inlined it would raise the register pressure of the whole kernel.
+__device__ __noinline__ double friction_node(Ctx& C, const SolveParams& P, int i, double fcv[3]) {
+  const double fn = C.fric[4 * i + 3];
+  float hb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  double energy = 0.0;
+  if (fn > 0.0) {
+    const double nn[3] = {C.fric[4 * i], C.fric[4 * i + 1], C.fric[4 * i + 2]};
+    double r[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r[k] = C.ut[3 * i + k] - C.uprev[3 * i + k] - C.dc[k];
+    const double rn = nn[0] * r[0] + nn[1] * r[1] + nn[2] * r[2];
+    const double sl[3] = {r[0] - rn * nn[0], r[1] - rn * nn[1], r[2] - rn * nn[2]};
+    const double y = sqrt(sl[0] * sl[0] + sl[1] * sl[1] + sl[2] * sl[2]);
+    const double eps = P.fric_eps, wf = P.mu_f * fn;
+    double f0, f1y, qy2;   // f0(y), f0'(y)/y and q y^2 of the Hessian
+    if (y < eps) {
+      f0 = y * y / eps - y * y * y / (3.0 * eps * eps) + eps / 3.0;
+      f1y = 2.0 / eps - y / (eps * eps);
+      qy2 = y / (eps * eps);
+    } else {
+      f0 = y;
+      f1y = 1.0 / y;
+      qy2 = 1.0 / y;
+    }
+    energy = wf * f0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double g = wf * f1y * sl[k];
+      C.R[3 * i + k] += g;
+      fcv[k] -= g;
+    }
+    const double iy = y > 0.0 ? 1.0 / y : 0.0;
+    const double sh[3] = {sl[0] * iy, sl[1] * iy, sl[2] * iy};
+    const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      hb[k] = (float)(wf * (f1y * ((ia[k] == ib[k] ? 1.0 : 0.0) - nn[ia[k]] * nn[ib[k]]) -
+                            qy2 * sh[ia[k]] * sh[ib[k]]));
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) C.hf[6 * i + k] = hb[k];
+  return energy;
+}
+
+// Friction state of owned node i for the load step: contact normal and
+// normal force at u_n with the indenter at its previous pose orgp.
+__device__ __noinline__ void friction_lag_node(Ctx& C, const SolveParams& P, int i, const double orgp[3]) {
+  const double kp = C.kb[i] * P.c_kappa;
+  double fn = 0.0, n[3] = {0.0, 0.0, 0.0};
+  if (kp > 0.0) {
+    const double xx[3] = {C.X[3 * i] + C.u[3 * i], C.X[3 * i + 1] + C.u[3 * i + 1], C.X[3 * i + 2] + C.u[3 * i + 2]};
+    double phi;
+    indenter_sdf(P.shape, orgp, P.R, P.iparams, xx, phi, n);
+    if (phi < 0.0) fn = -kp * phi;
+  }
+  C.fric[4 * i] = n[0]; C.fric[4 * i + 1] = n[1]; C.fric[4 * i + 2] = n[2];
+  C.fric[4 * i + 3] = fn;
+}
 
 // FP64 energy, residual R = dPi/du and contact at ut = u + alpha*dx. Leaves
 // the owned residual in C.R (unmasked), contact forces in C.fc, the contact
@@ -439,48 +503,7 @@ __device__ bool eval_pass(Ctx& C, const MeshDev& M, const WorkDev& W, const Solv
         h[0] = sk * (float)n[0]; h[1] = sk * (float)n[1]; h[2] = sk * (float)n[2];
       }
     }
-    if (C.fric_on) {
-      // lagged, smoothed Coulomb friction: mu_f fn f0(|s|), s the slip across
-      // the frozen normal relative to the indenter's translation
-      const double fn = C.fric[4 * i + 3];
-      float hb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      if (fn > 0.0) {
-        const double nn[3] = {C.fric[4 * i], C.fric[4 * i + 1], C.fric[4 * i + 2]};
-        double r[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) r[k] = C.ut[3 * i + k] - C.uprev[3 * i + k] - C.dc[k];
-        const double rn = nn[0] * r[0] + nn[1] * r[1] + nn[2] * r[2];
-        const double sl[3] = {r[0] - rn * nn[0], r[1] - rn * nn[1], r[2] - rn * nn[2]};
-        const double y = sqrt(sl[0] * sl[0] + sl[1] * sl[1] + sl[2] * sl[2]);
-        const double eps = P.fric_eps, wf = P.mu_f * fn;
-        double f0, f1y, qy2;   // f0(y), f0'(y)/y and q y^2 of the Hessian
-        if (y < eps) {
-          f0 = y * y / eps - y * y * y / (3.0 * eps * eps) + eps / 3.0;
-          f1y = 2.0 / eps - y / (eps * eps);
-          qy2 = y / (eps * eps);
-        } else {
-          f0 = y;
-          f1y = 1.0 / y;
-          qy2 = 1.0 / y;
-        }
-        v[EV_CONTACT] += wf * f0;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const double g = wf * f1y * sl[k];
-          C.R[3 * i + k] += g;
-          fcv[k] -= g;
-        }
-        const double iy = y > 0.0 ? 1.0 / y : 0.0;
-        const double sh[3] = {sl[0] * iy, sl[1] * iy, sl[2] * iy};
-        const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
-#pragma unroll
-        for (int k = 0; k < 6; ++k)
-          hb[k] = (float)(wf * (f1y * ((ia[k] == ib[k] ? 1.0 : 0.0) - nn[ia[k]] * nn[ib[k]]) -
-                                qy2 * sh[ia[k]] * sh[ib[k]]));
-      }
-#pragma unroll
-      for (int k = 0; k < 6; ++k) C.hf[6 * i + k] = hb[k];
-    }
+    if (C.fric_on) v[EV_CONTACT] += friction_node(C, P, i, fcv);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       C.fc[3 * i + k] = fcv[k];
@@ -569,13 +592,16 @@ __device__ void tangent_pass(Ctx& C, const MeshDev& M, int mode) {
 // The product stores 12 floats per tet, half the evaluation passes' 96 bytes,
 // so its chunks hold twice as many tets.
 __device__ void matvec_pass(Ctx& C, const MeshDev& M, long long* tp = nullptr) {
-  for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
-    C.acc[3 * i] = 0.f; C.acc[3 * i + 1] = 0.f; C.acc[3 * i + 2] = 0.f;
-  }
   const int CH = C.CH >= C.n_pt ? C.CH : 2 * C.CH;
   const bool single = CH >= C.n_pt;
-  if (!single) reset_cursors(C, 3);
-  __syncthreads();
+  if (!single) {
+    // several chunks accumulate into acc; one chunk assigns it in its gather
+    for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
+      C.acc[3 * i] = 0.f; C.acc[3 * i + 1] = 0.f; C.acc[3 * i + 2] = 0.f;
+    }
+    reset_cursors(C, 3);
+    __syncthreads();
+  }
   for (int c0 = 0; c0 < C.n_pt; c0 += CH) {
     const int c1 = min(c0 + CH, C.n_pt);
     for (int t = c0 + threadIdx.x; t < c1; t += blockDim.x) {
@@ -602,7 +628,7 @@ __device__ void matvec_pass(Ctx& C, const MeshDev& M, long long* tp = nullptr) {
     }
     __syncthreads();
     if (tp) tock(C, PH_CG_MATVEC, *tp);
-    gather_chunk<3, float>(C, CH, C.chunkf, c0, C.acc, single);
+    gather_chunk<3, float>(C, CH, C.chunkf, c0, C.acc, single, single);
     __syncthreads();
     if (tp) tock(C, PH_CG_GATHER, *tp);
   }
@@ -1187,21 +1213,8 @@ __device__ bool solve_body(Ctx& C, const MeshDev& M, const WorkDev& W, const Sol
           C.vel[3 * i + k] = (mk & (1u << k)) ? 0.0 : (C.u[3 * i + k] - C.uprev[3 * i + k]) * P.inv_dt;
         C.uprev[3 * i + k] = C.u[3 * i + k];
       }
-      if (C.fric_on) {
-        // friction state frozen for the step: contact normal and normal force
-        // at u_n with the indenter at its previous pose
-        const double kp = C.kb[i] * P.c_kappa;
-        double fn = 0.0, n[3] = {0.0, 0.0, 0.0};
-        if (kp > 0.0) {
-          const double xx[3] = {C.X[3 * i] + C.u[3 * i], C.X[3 * i + 1] + C.u[3 * i + 1],
-                                C.X[3 * i + 2] + C.u[3 * i + 2]};
-          double phi;
-          indenter_sdf(P.shape, orgp, P.R, P.iparams, xx, phi, n);
-          if (phi < 0.0) fn = -kp * phi;
-        }
-        C.fric[4 * i] = n[0]; C.fric[4 * i + 1] = n[1]; C.fric[4 * i + 2] = n[2];
-        C.fric[4 * i + 3] = fn;
-      }
+      // friction state frozen for the step
+      if (C.fric_on) friction_lag_node(C, P, i, orgp);
     }
     if (P.has_presc) {
       const double ramp = (double)step / (double)P.n_steps;
