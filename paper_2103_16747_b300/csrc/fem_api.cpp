@@ -338,7 +338,7 @@ SmemLayout plan_layout(const PartDims& d, int budget) {
       return -1;
     };
     L.lm = take(16 * d.max_loc);
-    L.red = take(8 * kRed * (kBlock / 32 + 1));
+    L.red = take(8 * kRed * (kMaxBlock / 32 + 1));
     L.chunk = take(96 * CH);
     if (o > budget) {
       if (attempt < 2) continue;

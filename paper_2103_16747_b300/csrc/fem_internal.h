@@ -6,7 +6,10 @@
 
 namespace fem {
 
-constexpr int kBlock = 512;       // threads per CTA of the solve kernel
+constexpr int kSolveBlock = 256;  // threads per CTA of the single-solve kernel (up to 255 registers
+                                  // each: the whole solve runs in one kernel)
+constexpr int kGroupBlock = 384;  // threads per CTA of the batched kernels (larger parts per CTA)
+constexpr int kMaxBlock = 512;    // bound on the CTA size, for shared-memory sizing
 constexpr int kChunk = 256;       // part tets per chunk of the evaluation passes (the tangent
                                   // product stages half the bytes per tet: chunks of 2*kChunk)
 constexpr int kRed = 12;          // doubles per CTA reduction slot

@@ -235,25 +235,28 @@ __device__ void block_reduce_to_slot(Ctx& C, const WorkDev& W, int slot_buf, con
   __syncthreads();
   if (threadIdx.x < nv) {
     double a = 0.0;
-    for (int w = 0; w < kBlock / 32; ++w) a += C.red[w * kRed + threadIdx.x];
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += C.red[w * kRed + threadIdx.x];
     if constexpr (CL) C.st->eslot[slot_buf * kRed + threadIdx.x] = a;
     else W.partials[((size_t)slot_buf * C.nparts + C.part) * kRed + threadIdx.x] = a;
   }
 }
 
 // Every part sums all slots in the same order: identical results everywhere.
+// Value k is summed by warp k mod (warps of the CTA), so every value is
+// reduced whatever the CTA size.
 template <bool CL>
 __device__ void reduce_from_slots(Ctx& C, const WorkDev& W, int slot_buf, int nv) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (warp < nv) {
+  const int n_warps = (int)(blockDim.x >> 5);
+  for (int k = warp; k < nv; k += n_warps) {
     double a = 0.0;
     for (int c = lane; c < C.nparts; c += 32) {
-      if constexpr (CL) a += peer(C.st->eslot, (unsigned)c)[slot_buf * kRed + warp];
-      else a += __ldcg(W.partials + ((size_t)slot_buf * C.nparts + c) * kRed + warp);
+      if constexpr (CL) a += peer(C.st->eslot, (unsigned)c)[slot_buf * kRed + k];
+      else a += __ldcg(W.partials + ((size_t)slot_buf * C.nparts + c) * kRed + k);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    if (lane == 0) C.st->red_out[warp] = a;
+    if (lane == 0) C.st->red_out[k] = a;
   }
 }
 
@@ -353,9 +356,8 @@ struct Bufs {
 // Lagged, smoothed Coulomb friction at owned node i (friction on): mu_f fn
 // f0(|s|), s the slip across the frozen normal relative to the indenter's
 // translation. Adds the force to R and fcv, stores the node's FP32 Hessian
-// block in hf and returns the energy. Kept out of line: it runs per owned
-// node, and inlined it would raise the register pressure of the whole kernel.
-__device__ __noinline__ double friction_node(Ctx& C, const SolveParams& P, int i, double fcv[3]) {
+// block in hf and returns the energy.
+__device__ __forceinline__ double friction_node(Ctx& C, const SolveParams& P, int i, double fcv[3]) {
   const double fn = C.fric[4 * i + 3];
   float hb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   double energy = 0.0;
@@ -400,7 +402,7 @@ __device__ __noinline__ double friction_node(Ctx& C, const SolveParams& P, int i
 
 // Friction state of owned node i for the load step: contact normal and
 // normal force at u_n with the indenter at its previous pose orgp.
-__device__ __noinline__ void friction_lag_node(Ctx& C, const SolveParams& P, int i, const double orgp[3]) {
+__device__ __forceinline__ void friction_lag_node(Ctx& C, const SolveParams& P, int i, const double orgp[3]) {
   const double kp = C.kb[i] * P.c_kappa;
   double fn = 0.0, n[3] = {0.0, 0.0, 0.0};
   if (kp > 0.0) {
@@ -940,7 +942,7 @@ __device__ bool pcg(Ctx& C, const MeshDev& M, const WorkDev& W, const SolveParam
                     long long& products) {
   long long t = tick(C);
   neg_curv = false;
-  const int active_warps = min((C.n_own + 31) / 32, kBlock / 32);
+  const int active_warps = min((C.n_own + 31) / 32, (int)(blockDim.x >> 5));
   // x = 0, r = -R_free, p = s = 0, u = M^-1 r (published)
   for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
     const unsigned mk = C.mask[i];
@@ -1365,7 +1367,7 @@ __device__ bool solve_body(Ctx& C, const MeshDev& M, const WorkDev& W, const Sol
   return true;
 }
 
-__global__ void __launch_bounds__(kBlock, 1) solve_kernel(MeshDev M, WorkDev W, SolveParams P, SmemLayout L) {
+__global__ void __launch_bounds__(kSolveBlock, 1) solve_kernel(MeshDev M, WorkDev W, SolveParams P, SmemLayout L) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Statics S;
   if (P.mode == MODE_BARRIER_TEST) {
@@ -1428,7 +1430,7 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(MeshDev M, WorkDev W, 
 // One solve per cluster; the cluster's rank-0 CTA takes the next job from the
 // queue and every CTA of the cluster reads it from there. All CTAs leave the
 // loop together.
-__global__ void __launch_bounds__(kBlock, 1) cluster_kernel(const BatchJob* __restrict__ jobs, int n_jobs,
+__global__ void __launch_bounds__(kGroupBlock, 1) cluster_kernel(const BatchJob* __restrict__ jobs, int n_jobs,
                                                             int* queue, SlotScratch S, SmemLayout L) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Statics ST;
@@ -1509,7 +1511,7 @@ __device__ int next_job(const GroupRun& R, const JobQueue& q) {
   }
 }
 
-__global__ void __launch_bounds__(kBlock, 1) group_kernel(GroupRun R, SlotScratch S, SmemLayout L) {
+__global__ void __launch_bounds__(kGroupBlock, 1) group_kernel(GroupRun R, SlotScratch S, SmemLayout L) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Statics ST;
   __shared__ MeshDev sM;
@@ -1619,7 +1621,7 @@ cudaError_t solve_kernel_attrs(int smem_bytes, int* static_smem, int* blocks_per
   if (!blocks_per_sm) return cudaSuccess;
   e = cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, solve_kernel, kBlock, smem_bytes);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, solve_kernel, kSolveBlock, smem_bytes);
 }
 
 cudaError_t launch_solve(const MeshDev& mesh, const WorkDev& work, const SolveParams& prm, const SmemLayout& L,
@@ -1637,7 +1639,7 @@ cudaError_t launch_solve(const MeshDev& mesh, const WorkDev& work, const SolvePa
   SolveParams p = prm;
   SmemLayout l = L;
   void* args[] = {&m, &w, &p, &l};
-  e = cudaLaunchCooperativeKernel((const void*)solve_kernel, dim3(mesh.n_parts), dim3(kBlock), args,
+  e = cudaLaunchCooperativeKernel((const void*)solve_kernel, dim3(mesh.n_parts), dim3(kSolveBlock), args,
                                   (size_t)L.total, stream);
   if (kernel_ms) {
     cudaEventRecord(ev1, stream);
@@ -1656,7 +1658,7 @@ static cudaLaunchConfig_t cluster_config(int cluster, int n_slots, int smem_byte
                                          cudaLaunchAttribute* attr) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)(cluster * n_slots));
-  cfg.blockDim = dim3(kBlock);
+  cfg.blockDim = dim3(kGroupBlock);
   cfg.dynamicSmemBytes = (size_t)smem_bytes;
   cfg.stream = stream;
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1727,7 +1729,7 @@ cudaError_t group_kernel_attrs(int smem_bytes, int* static_smem, int* blocks_per
   if (!blocks_per_sm) return cudaSuccess;
   e = cudaFuncSetAttribute(group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, group_kernel, kBlock, smem_bytes);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, group_kernel, kGroupBlock, smem_bytes);
 }
 
 cudaError_t launch_groups(const GroupRun& R, const SlotScratch& S, const SmemLayout& L, int n_ctas,
@@ -1744,7 +1746,7 @@ cudaError_t launch_groups(const GroupRun& R, const SlotScratch& S, const SmemLay
   SlotScratch s = S;
   SmemLayout l = L;
   void* args[] = {&r, &s, &l};
-  e = cudaLaunchCooperativeKernel((const void*)group_kernel, dim3((unsigned)n_ctas), dim3(kBlock), args,
+  e = cudaLaunchCooperativeKernel((const void*)group_kernel, dim3((unsigned)n_ctas), dim3(kGroupBlock), args,
                                   (size_t)L.total, stream);
   if (kernel_ms) {
     cudaEventRecord(ev1, stream);
