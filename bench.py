@@ -208,21 +208,21 @@ def source_digest():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the solve kernel from the committed ncu summary,
-    or None if the kernel sources changed since that capture."""
-    path = os.path.join(ROOT, "profiles", "solve_kernel_fingertip_sphere.md")
+def profiled_traffic(summary="solve_kernel_fingertip_sphere.md", key="traffic_bytes_per_launch"):
+    """DRAM bytes (per launch, or per solve) from a committed ncu summary, or
+    None if the kernel sources changed since that capture."""
+    path = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(path):
         return None
     vals = {}
     for line in open(path):
-        if ":" in line and line.strip().startswith(("- source_digest", "- traffic_bytes_per_launch")):
+        if ":" in line and line.strip().startswith(("- source_digest", "- " + key)):
             k, v = line.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
     if vals.get("source_digest") != source_digest():
         return None
     try:
-        return float(vals["traffic_bytes_per_launch"])
+        return float(vals[key])
     except (KeyError, ValueError):
         return None
 
@@ -436,14 +436,21 @@ def run_batch(args, rank, world, local):
     handles = {k: F.fem_create_mesh(m.nodes, m.tets, m.tet_material, m.materials, m.fixed_nodes)
                for k, m in uniq.items()}
     hs = [handles[id(m)] for m in meshes]
-    # both batched workloads take their slot shape from the autotuner
+    # both batched workloads take their slot shape from the autotuner, unless
+    # a fixed group size is asked for (profiling: then the plan's launches are
+    # the only ones)
     t0 = time.perf_counter()
-    opt, rep = F.fem_batch_tune(hs, draws, TOL, opt, proxy_steps=4)
-    tune = {"seconds": time.perf_counter() - t0,
-            "chosen": {"engine": opt.batch_engine, "parts": opt.batch_parts,
-                       "tets_per_cta": opt.batch_tets_per_cta},
-            "candidates": [{"engine": rep.engine[k], "parts": rep.parts[k], "tets_per_cta": rep.tets_per_cta[k],
-                            "proxy_solves_per_s": rep.rate[k]} for k in range(rep.n_candidates)]}
+    if args.batch_parts:
+        opt.batch_engine, opt.batch_parts = F.FEM_BATCH_GROUPS, args.batch_parts
+        tune = {"skipped": f"uniform groups of {args.batch_parts} CTAs (--batch-parts)"}
+    else:
+        opt, rep = F.fem_batch_tune(hs, draws, TOL, opt, proxy_steps=4)
+        tune = {"seconds": time.perf_counter() - t0,
+                "chosen": {"engine": opt.batch_engine, "parts": opt.batch_parts,
+                           "tets_per_cta": opt.batch_tets_per_cta},
+                "candidates": [{"engine": rep.engine[k], "parts": rep.parts[k],
+                                "tets_per_cta": rep.tets_per_cta[k], "proxy_solves_per_s": rep.rate[k]}
+                               for k in range(rep.n_candidates)]}
     plan = F.FemBatch(hs, [d.n_steps for d in draws], opt)
     info = plan.info()
     outs = [torch.zeros((m.n_nodes, 3), dtype=torch.float64, device=dev) for m in meshes]
@@ -498,6 +505,13 @@ def run_batch(args, rank, world, local):
     for h_ in eh.values():
         F.fem_destroy_mesh(h_)
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    # DRAM traffic from the committed capture of the same slot shape (uniform
+    # 37-CTA groups on this fingertip, 8 solves), scaled by the solves of the
+    # launch; None for other shapes or changed sources
+    traffic = None
+    if args.workload == "batch" and info.engine == 1 and info.parts == 37:
+        per_solve = profiled_traffic("group_kernel_fingertip_batch.md", "traffic_bytes_per_solve")
+        traffic = per_solve * n if per_solve is not None else None
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total * 1000.0 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
@@ -516,7 +530,7 @@ def run_batch(args, rank, world, local):
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": (1 + n) * args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": traffic,
                          "kernel": "group_kernel" if info.engine == 1 else "cluster_kernel",
                          "kernel_ms": kernel_ms, "algorithmic_bytes": alg, "peak_kind": peak_kind,
                          "fp32_tflops": flops / (kernel_ms / 1000.0) / 1e12, "fp32_peak_tflops": FP32_PEAK_TFLOPS},
@@ -649,6 +663,8 @@ def main():
     ap.add_argument("--drain-seconds", type=float, default=90.0)
     ap.add_argument("--serve-class-cap", type=int, default=64,
                     help="largest CTA group of the request server (power of two)")
+    ap.add_argument("--batch-parts", type=int, default=0,
+                    help="batched workloads: uniform CTA groups of this size instead of the autotuner")
     ap.add_argument("--n-solves", type=int, default=None,
                     help="solves per step of the batched workloads (default 256 / 64)")
     args = ap.parse_args()
