@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <climits>
 #include <array>
 #include <cmath>
@@ -55,6 +56,25 @@ using namespace fem::host;
 
 namespace {
 
+// Host phase times of mesh creation, printed to stderr when FEM_VERBOSE is set.
+struct HostPhases {
+  bool on = getenv("FEM_VERBOSE") != nullptr;
+  std::chrono::steady_clock::time_point t = std::chrono::steady_clock::now();
+  std::string out;
+  void mark(const char* name) {
+    if (!on) return;
+    const auto n = std::chrono::steady_clock::now();
+    char buf[96];
+    snprintf(buf, sizeof(buf), " %s %.2f ms", name, std::chrono::duration<double, std::milli>(n - t).count());
+    out += buf;
+    t = n;
+  }
+  void print(const char* what) {
+    if (on) fprintf(stderr, "[fem] %s:%s\n", what, out.c_str());
+  }
+};
+
+
 uint64_t spread_bits(uint64_t v) {
   v &= 0x1fffff;
   v = (v | v << 32) & 0x1f00000000ffffull;
@@ -98,6 +118,7 @@ namespace {
 // fields of D (the mesh-wide fields are copied from m->dev) and dims; device
 // arrays go to o (freed first) and their bytes to by.
 int build_partition(fem_mesh* m, int n_parts, MeshDev& D, PartDims& dims, std::vector<void*>& o, size_t& by) {
+  HostPhases hp;
   const int Nn = (int)m->n_nodes, Nt = (int)m->n_tets;
   // contiguous node ranges; a part's cost is its unique tets (halo tets
   // included, each computed once per part) plus its owned nodes. The cut
@@ -129,8 +150,9 @@ int build_partition(fem_mesh* m, int n_parts, MeshDev& D, PartDims& dims, std::v
     return parts;
   };
   {
+    // part costs are multiples of 0.25: a bracket narrower than that fixes the cuts
     double lo = 1.0, hi = 8.0 * (double)Nt + Nn;
-    for (int iter = 0; iter < 60; ++iter) {
+    for (int iter = 0; iter < 60 && hi - lo > 0.125; ++iter) {
       const double mid = 0.5 * (lo + hi);
       if (sweep(mid, nullptr) > n_parts) lo = mid; else hi = mid;
     }
@@ -138,6 +160,7 @@ int build_partition(fem_mesh* m, int n_parts, MeshDev& D, PartDims& dims, std::v
     for (int c = std::min(got, n_parts); c < n_parts; ++c) nb[c] = std::min(Nn, nb[c - 1] + 1);
   }
   nb[n_parts] = Nn;
+  hp.mark("cut");
   for (int p = 1; p <= n_parts; ++p)
     if (nb[p] <= nb[p - 1]) return fail(FEM_ERR_TOO_LARGE, "cannot cut %d nodes into %d parts", Nn, n_parts);
   std::vector<int> part_of(Nn);
@@ -153,24 +176,38 @@ int build_partition(fem_mesh* m, int n_parts, MeshDev& D, PartDims& dims, std::v
   std::vector<unsigned> lcsr;
   std::vector<int> local_of_tet(Nt, -1);
   std::vector<int> local_of_node(Nn, -1);
+  {
+    // part tets are about twice the mesh's at the usual part sizes
+    const size_t guess = 2 * (size_t)Nt + 1024;
+    pt_nodes.reserve(guess);
+    pt_dminv_aos.reserve(9 * guess);
+    pt_vol.reserve(guess);
+    pt_info.reserve(guess);
+    lcsr.reserve(4 * (size_t)Nt);
+  }
   int max_own = 0, max_loc = 0, max_pt = 0;
   std::vector<int> tl;
   for (int p = 0; p < n_parts; ++p) {
     tl.clear();
     for (int i = nb[p]; i < nb[p + 1]; ++i)
-      for (int j = m->csr_ptr[i]; j < m->csr_ptr[i + 1]; ++j) tl.push_back(m->csr_ent[j] >> 2);
+      for (int j = m->csr_ptr[i]; j < m->csr_ptr[i + 1]; ++j) {
+        const int t = m->csr_ent[j] >> 2;
+        if (local_of_tet[t] == -2) continue;   // seen (reset with the other stamps below)
+        local_of_tet[t] = -2;
+        tl.push_back(t);
+      }
     std::sort(tl.begin(), tl.end());
-    tl.erase(std::unique(tl.begin(), tl.end()), tl.end());
     const int n_own = nb[p + 1] - nb[p];
     for (int i = nb[p]; i < nb[p + 1]; ++i) local_of_node[i] = i - nb[p];
     std::vector<int> hl;
     for (int t : tl)
       for (int a = 0; a < 4; ++a) {
         const int g = m->tets_new[4 * t + a];
-        if (g < nb[p] || g >= nb[p + 1]) hl.push_back(g);
+        if (local_of_node[g] != -1) continue;   // owned, or a halo node already listed
+        local_of_node[g] = -2;
+        hl.push_back(g);
       }
     std::sort(hl.begin(), hl.end());
-    hl.erase(std::unique(hl.begin(), hl.end()), hl.end());
     for (size_t j = 0; j < hl.size(); ++j) local_of_node[hl[j]] = n_own + (int)j;
     const int n_loc = n_own + (int)hl.size();
     if (n_loc >= 65535) return fail(FEM_ERR_TOO_LARGE, "part %d has %d local nodes (max 65534)", p, n_loc);
@@ -212,6 +249,7 @@ int build_partition(fem_mesh* m, int n_parts, MeshDev& D, PartDims& dims, std::v
     max_pt = std::max(max_pt, (int)tl.size());
   }
   lcsr_ptr[Nn] = (int)lcsr.size();
+  hp.mark("parts");
   const int total_pt = (int)pt_nodes.size();
   std::vector<double> pt_dminv((size_t)9 * total_pt);
   for (int e = 0; e < total_pt; ++e)
@@ -262,6 +300,8 @@ int build_partition(fem_mesh* m, int n_parts, MeshDev& D, PartDims& dims, std::v
   D.lcsr = d_lcsr;
   dims = PartDims{max_own, max_loc, max_pt, max_lcsr};
   CUDA_TRY(cudaStreamSynchronize(s), "partition upload");
+  hp.mark("upload");
+  hp.print("partition");
   return FEM_OK;
 }
 
@@ -573,6 +613,7 @@ int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, i
                     const int32_t* fixed_nodes, int64_t n_fixed, const uint8_t* fixed_mask,
                     void* cuda_stream, fem_mesh** out) {
   g_err.clear();
+  HostPhases hp;
   if (!out) return fail(FEM_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (!nodes || !tets || !materials) return fail(FEM_ERR_ARG, "nodes, tets and materials must be non-NULL");
@@ -645,6 +686,7 @@ int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, i
     o[8] = (Dm[0] * Dm[4] - Dm[1] * Dm[3]) * id;
     vol_old[t] = V;
   }
+  hp.mark("validate+Dm");
   // ---------------------------------------------------------------- device
   int device = 0;
   {
@@ -696,6 +738,7 @@ int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, i
     tkey[t] = {mn, t};
   }
   std::sort(tkey.begin(), tkey.end());
+  hp.mark("order");
   m->tets_new.resize(4 * (size_t)Nt);
   m->dminv.resize(9 * (size_t)Nt);
   m->vol.resize(Nt);
@@ -727,56 +770,88 @@ int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, i
     for (int k = 0; k < 3; ++k) X[3 * (size_t)i + k] = nodes[3 * (size_t)m->perm[i] + k];
     m->node_mask[i] = mask_old[m->perm[i]];
   }
-  // boundary faces (seen once) -> lumped areas; unique edges -> h_bar
-  std::vector<std::array<int, 3>> faces;
-  faces.reserve(4 * (size_t)Nt);
-  static const int fidx[4][3] = {{0, 1, 2}, {0, 1, 3}, {0, 2, 3}, {1, 2, 3}};
-  for (int t = 0; t < Nt; ++t)
-    for (int f = 0; f < 4; ++f) {
-      std::array<int, 3> v = {m->tets_new[4 * (size_t)t + fidx[f][0]], m->tets_new[4 * (size_t)t + fidx[f][1]],
-                              m->tets_new[4 * (size_t)t + fidx[f][2]]};
-      std::sort(v.begin(), v.end());
-      faces.push_back(v);
-    }
-  std::sort(faces.begin(), faces.end());
+  // boundary faces (faces of exactly one tet) -> lumped areas; unique edges
+  // -> h_bar, both in linear time. Faces are bucketed by their smallest vertex
+  // and each small bucket is sorted by the other two; a key seen once is a
+  // boundary face. An edge (p, q), p < q, is counted once at p with a per-node
+  // stamp.
   std::vector<double> area(Nn, 0.0);
   std::vector<char> on_boundary(Nn, 0);
-  for (size_t i = 0; i < faces.size();) {
-    size_t j = i + 1;
-    while (j < faces.size() && faces[j] == faces[i]) ++j;
-    if (j - i == 1) {
-      const double* a = &X[3 * (size_t)faces[i][0]];
-      const double* b = &X[3 * (size_t)faces[i][1]];
-      const double* c = &X[3 * (size_t)faces[i][2]];
-      const double u[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
-      const double v[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
-      const double cr[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
-      const double A = 0.5 * std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
-      for (int k = 0; k < 3; ++k) {
-        area[faces[i][k]] += A / 3.0;
-        on_boundary[faces[i][k]] = 1;
+  {
+    static const int fidx[4][3] = {{0, 1, 2}, {0, 1, 3}, {0, 2, 3}, {1, 2, 3}};
+    const int* tn = m->tets_new.data();
+    std::vector<int> fptr(Nn + 1, 0);
+    auto sorted3 = [&](int t, int f, int& a, int& b, int& c) {
+      a = tn[4 * (size_t)t + fidx[f][0]];
+      b = tn[4 * (size_t)t + fidx[f][1]];
+      c = tn[4 * (size_t)t + fidx[f][2]];
+      if (a > b) std::swap(a, b);
+      if (b > c) std::swap(b, c);
+      if (a > b) std::swap(a, b);
+    };
+    for (int t = 0; t < Nt; ++t)
+      for (int f = 0; f < 4; ++f) {
+        int a, b, c;
+        sorted3(t, f, a, b, c);
+        fptr[a + 1]++;
+      }
+    for (int i = 0; i < Nn; ++i) fptr[i + 1] += fptr[i];
+    std::vector<uint64_t> fkey(4 * (size_t)Nt);
+    {
+      std::vector<int> fill(fptr.begin(), fptr.end() - 1);
+      for (int t = 0; t < Nt; ++t)
+        for (int f = 0; f < 4; ++f) {
+          int a, b, c;
+          sorted3(t, f, a, b, c);
+          fkey[fill[a]++] = ((uint64_t)(unsigned)b << 32) | (uint64_t)(unsigned)c;
+        }
+    }
+    for (int a = 0; a < Nn; ++a) {
+      uint64_t* lo = fkey.data() + fptr[a];
+      uint64_t* hi = fkey.data() + fptr[a + 1];
+      std::sort(lo, hi);
+      for (uint64_t* q = lo; q < hi;) {
+        uint64_t* r = q + 1;
+        while (r < hi && *r == *q) ++r;
+        if (r - q == 1) {
+          const int b = (int)(*q >> 32), c = (int)(*q & 0xffffffffu);
+          const double* pa = &X[3 * (size_t)a];
+          const double* pb = &X[3 * (size_t)b];
+          const double* pc = &X[3 * (size_t)c];
+          const double e1[3] = {pb[0] - pa[0], pb[1] - pa[1], pb[2] - pa[2]};
+          const double e2[3] = {pc[0] - pa[0], pc[1] - pa[1], pc[2] - pa[2]};
+          const double cr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                                e1[0] * e2[1] - e1[1] * e2[0]};
+          const double A = 0.5 * std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+          for (const int w : {a, b, c}) {
+            area[w] += A / 3.0;
+            on_boundary[w] = 1;
+          }
+        }
+        q = r;
       }
     }
-    i = j;
   }
-  std::vector<uint64_t> edges;
-  edges.reserve(6 * (size_t)Nt);
-  for (int t = 0; t < Nt; ++t)
-    for (int a = 0; a < 4; ++a)
-      for (int b = a + 1; b < 4; ++b) {
-        uint64_t p = (uint64_t)m->tets_new[4 * (size_t)t + a], q = (uint64_t)m->tets_new[4 * (size_t)t + b];
-        if (p > q) std::swap(p, q);
-        edges.push_back((p << 32) | q);
-      }
-  std::sort(edges.begin(), edges.end());
-  edges.erase(std::unique(edges.begin(), edges.end()), edges.end());
   double lsum = 0.0;
-  for (uint64_t e : edges) {
-    const double* a = &X[3 * (e >> 32)];
-    const double* b = &X[3 * (e & 0xffffffffu)];
-    lsum += std::sqrt((a[0] - b[0]) * (a[0] - b[0]) + (a[1] - b[1]) * (a[1] - b[1]) + (a[2] - b[2]) * (a[2] - b[2]));
+  size_t n_edges = 0;
+  {
+    std::vector<int> stamp(Nn, -1);
+    for (int p = 0; p < Nn; ++p)
+      for (int j = m->csr_ptr[p]; j < m->csr_ptr[p + 1]; ++j) {
+        const int t = m->csr_ent[j] >> 2;
+        for (int k = 0; k < 4; ++k) {
+          const int q = m->tets_new[4 * (size_t)t + k];
+          if (q <= p || stamp[q] == p) continue;
+          stamp[q] = p;
+          const double* a = &X[3 * (size_t)p];
+          const double* b = &X[3 * (size_t)q];
+          lsum += std::sqrt((a[0] - b[0]) * (a[0] - b[0]) + (a[1] - b[1]) * (a[1] - b[1]) +
+                            (a[2] - b[2]) * (a[2] - b[2]));
+          ++n_edges;
+        }
+      }
   }
-  m->h_bar = lsum / (double)edges.size();
+  m->h_bar = lsum / (double)n_edges;
   std::vector<double> Emax(Nn, 0.0);
   double Eglob = 0.0;
   for (int t = 0; t < Nt; ++t) {
@@ -803,6 +878,7 @@ int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, i
     lame[2 * k] = E / (2.0 * (1.0 + nu));
     lame[2 * k + 1] = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
   }
+  hp.mark("topology");
   // uploads
   cudaStream_t s = m->stream;
   double *d_X, *d_kbase, *d_lame, *d_vl;
@@ -856,8 +932,11 @@ int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, i
   D.lame = d_lame;
   D.vol_lumped = d_vl;
   D.mat_model = d_model;
+  hp.mark("upload");
   int rc = build_partitions(m, default_parts(m));
   if (rc != FEM_OK) return bail(rc);
+  hp.mark("partition");
+  hp.print("create");
   *out = m;
   return FEM_OK;
 }
