@@ -197,12 +197,17 @@ def compact_bytes(n_tets, n_nodes, products, newton_iters, evals):
             + evals * 92 * n_tets)
 
 
+# device-side sources of the profiled kernels and of the shared-memory layout
+# they run with (host code that only prepares the same inputs is left out)
+KERNEL_SOURCES = ("fem_internal.h", "fem_math.cuh", "fem_solve.cu")
+
+
 def source_digest():
-    """SHA-256 over the CUDA library sources (the kernel as built)."""
+    """SHA-256 over the kernel sources (the kernels as built)."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2103_16747_b300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
