@@ -105,7 +105,7 @@ typedef struct {
                               /* Chebyshev polynomial of degree d in the block-Jacobi */
                               /* preconditioned tangent (d tangent products and one  */
                               /* reduction per PCG iteration; default 5)              */
-    double  precond_ratio;    /* Chebyshev interval [4/ratio, 4] (default 60)          */
+    double  precond_ratio;    /* Chebyshev interval [4/ratio, 4] (default 120)         */
     double  dt;               /* load-step time step: 0 = quasi-static (default); > 0 */
                               /* = dynamic implicit stepping (backward Euler, lumped  */
                               /* mass): each load step of fem_solve, fem_solve_batch, */

@@ -590,7 +590,7 @@ void fem_default_options(fem_options* opt) {
   opt->batch_parts = 0;
   opt->batch_tets_per_cta = 1300;
   opt->precond_degree = 5;
-  opt->precond_ratio = 60.0;
+  opt->precond_ratio = 120.0;
   opt->dt = 0.0;
   opt->density = 1.1e-9;
   opt->mu_f = 0.0;

@@ -28,7 +28,7 @@ def test_default_options():
     o = L.fem_default_options()
     assert o.c_kappa == 100.0 and o.max_cg == 2000 and o.tangent == L.FEM_TANGENT_ADAPTIVE
     assert o.batch_engine == L.FEM_BATCH_AUTO and o.batch_parts == 0
-    assert o.precond_degree == 5 and o.precond_ratio == 60.0
+    assert o.precond_degree == 5 and o.precond_ratio == 120.0
     assert o.dt == 0.0 and o.density == 1.1e-9
 
 
