@@ -125,3 +125,36 @@ def test_server_whole_gpu_passes_for_large_meshes(F):
     srv.close()
     for h in handles:
         F.fem_destroy_mesh(h)
+
+
+@pytest.mark.parametrize("physics", ["dynamic", "friction", "corotational"])
+def test_server_physics_options_match_oracle(F, physics):
+    """The served path runs every physics option: dynamic stepping, Coulomb
+    friction and the co-rotational law, each against the FP64 oracle."""
+    m, ind = W.cube_sphere()
+    opt = F.fem_default_options()
+    kw = {}
+    if physics == "dynamic":
+        opt.dt, opt.density = 1e-3, 1.0
+        kw = {"dt": 1e-3, "density": 1.0}
+    elif physics == "friction":
+        opt.mu_f = 0.783
+        kw = {"mu_f": 0.783}
+    else:
+        m = W.with_model(m, 1)
+    ref = Problem(m, ind, **kw).solve(tol=1e-10)
+    assert ref.converged
+    h = F.fem_create_mesh(m.nodes, m.tets, m.tet_material, m.materials, m.fixed_nodes)
+    srv = F.FemServer([h], ind.n_steps, opt, result_bytes=16 << 20)
+    srv.start(60.0)
+    rc, rid = srv.submit(0, ind, 1e-6)
+    assert rc == 0
+    rc, u, f, st, _ = srv.result(rid, m.n_nodes, ind.n_steps, wait_ms=60000)
+    assert rc == F.FEM_OK
+    assert np.linalg.norm(u - ref.u) / np.linalg.norm(ref.u) <= 1e-4
+    k0 = 1 if physics == "friction" else 0
+    for k in range(k0, ind.n_steps):
+        assert np.linalg.norm(f[k] - ref.step_force[k]) / np.linalg.norm(ref.step_force[k]) <= 1e-3
+    assert srv.stop() == 0
+    srv.close()
+    F.fem_destroy_mesh(h)
