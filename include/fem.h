@@ -89,8 +89,9 @@ typedef struct {
     double  c_kappa;          /* penalty factor (default 100)                         */
     int32_t max_newton;       /* Newton iterations per load step (default 60)         */
     int32_t max_cg;           /* PCG iterations per Newton iteration (default 2000)   */
-    double  cg_rtol_max;      /* forcing term eta upper bound (default 0.1)           */
-    double  cg_rtol_min;      /* forcing term eta lower bound (default 1e-4)          */
+    double  cg_rtol_max;      /* forcing term eta upper bound (default 0.2)           */
+    double  cg_rtol_min;      /* forcing term eta lower bound (default 1e-2); Newton  */
+                              /* stops on the FP64 residual whatever eta is            */
     int32_t max_backtracks;   /* Armijo halvings per Newton iteration (default 30)    */
     int32_t tangent;          /* FEM_TANGENT_* (default ADAPTIVE)                     */
     double  barrier_timeout_s;/* bound on every device-side wait (default 5 s)        */

@@ -581,8 +581,8 @@ void fem_default_options(fem_options* opt) {
   opt->c_kappa = 100.0;
   opt->max_newton = 60;
   opt->max_cg = 2000;
-  opt->cg_rtol_max = 0.1;
-  opt->cg_rtol_min = 1e-4;
+  opt->cg_rtol_max = 0.2;
+  opt->cg_rtol_min = 1e-2;
   opt->max_backtracks = 30;
   opt->tangent = FEM_TANGENT_ADAPTIVE;
   opt->barrier_timeout_s = 5.0;

@@ -27,6 +27,7 @@ def test_default_options():
     from paper_2103_16747_b300 import _lib as L
     o = L.fem_default_options()
     assert o.c_kappa == 100.0 and o.max_cg == 2000 and o.tangent == L.FEM_TANGENT_ADAPTIVE
+    assert o.cg_rtol_max == 0.2 and o.cg_rtol_min == 1e-2
     assert o.batch_engine == L.FEM_BATCH_AUTO and o.batch_parts == 0
     assert o.precond_degree == 5 and o.precond_ratio == 120.0
     assert o.dt == 0.0 and o.density == 1.1e-9
