@@ -370,7 +370,8 @@ def run_cuda(args, rank, world, local):
     cmp_b = compact_bytes(mesh.n_tets, n, s0.tangent_products, s0.newton_iters, evals)
     peak, peak_kind = peaks()
     achieved = alg / (kms / 1000.0) / 1e9
-    traffic = profiled_traffic()
+    # the committed capture is of the default variant
+    traffic = profiled_traffic() if variant == "fingertip" else None
     lat = sorted(step_ms)
     p = lambda q: lat[min(len(lat) - 1, int(math.ceil(q * len(lat))) - 1)]   # noqa: E731
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
