@@ -144,7 +144,6 @@ struct Ctx {
   double *ut, *chunkd, *red;
   float *x, *r, *ucg, *w, *s, *p, *acc, *minv, *hc, *chunkf, *cd;
   float4* lm;
-  int gseg;               // log2 of the lanes per owned node in single-chunk gathers
   float4* tan;            // part tangent, element (g, t) at tan[g * tan_stride + t]
   int tan_stride;
   const ushort4* ptn;     // part tet local node ids, index t
@@ -295,32 +294,21 @@ __device__ __forceinline__ void gather_chunk(Ctx& C, int CH, const T* buf, int c
                                              bool assign = false) {
   if (single) {
     // whole part in one chunk: every entry belongs to it, no cursor needed.
-    // 2^gseg consecutive lanes share a node: lane g of the group sums entries
-    // g, g + 2^gseg, ... of the node's list (all NV components), then a fixed
-    // xor-shuffle tree over the group adds the lanes' sums.
-    const int lg = C.gseg, S = 1 << lg;
-    const int n_idx = C.n_own << lg;
-    for (int base = 0; base < n_idx; base += blockDim.x) {   // trip count uniform over the CTA
-      const int idx = base + threadIdx.x;
-      const int i = idx >> lg, g = idx & (S - 1);
-      T sum[NV];
-#pragma unroll
-      for (int k = 0; k < NV; ++k) sum[k] = T(0);
-      if (i < C.n_own) {
-        const int j1 = C.lptr[i + 1];
-        for (int j = C.lptr[i] + g; j < j1; j += S) {
-          const unsigned e = C.lcsr[j];
-          const T* src = buf + (int)(e & 3u) * NV * CH + (int)(e >> 2);
-#pragma unroll
-          for (int k = 0; k < NV; ++k) sum[k] += src[k * CH];
-        }
+    // One thread per (node, component) walks the node's list in order: the
+    // same additions in the same order as the chunked walk below, so a part's
+    // sums do not depend on how its tets were chunked (a solve gives the same
+    // bits alone and in any batch, whatever layout the batch needs).
+    for (int idx = threadIdx.x; idx < C.n_own * NV; idx += blockDim.x) {
+      const int i = idx / NV, k = idx - i * NV;
+      const int j0 = C.lptr[i], j1 = C.lptr[i + 1];
+      const T* col = buf + k * CH;
+      T s = assign ? T(0) : acc[idx];
+#pragma unroll 4
+      for (int j = j0; j < j1; ++j) {
+        const unsigned e = C.lcsr[j];
+        s += col[(int)(e & 3u) * NV * CH + (int)(e >> 2)];
       }
-      for (int o = 1; o < S; o <<= 1)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) sum[k] += __shfl_xor_sync(0xffffffffu, sum[k], o);
-      if (i < C.n_own && g == 0)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) acc[NV * i + k] = assign ? sum[k] : acc[NV * i + k] + sum[k];
+      acc[idx] = s;
     }
     return;
   }
@@ -1088,8 +1076,6 @@ __device__ void setup_ctx(Ctx& C, const MeshDev& M, const WorkDev& W, const Smem
   C.vl = M.vol_lumped + C.node0;
   C.vel = W.vel ? W.vel + 3 * (size_t)C.node0 : nullptr;
   C.fric = W.fric ? W.fric + 4 * (size_t)C.node0 : nullptr;
-  C.gseg = 0;
-  while (C.gseg < 5 && (C.n_own << (C.gseg + 1)) <= (int)blockDim.x) ++C.gseg;
   C.fric_on = false;
   C.dc[0] = C.dc[1] = C.dc[2] = 0.0;
   C.ut = reinterpret_cast<double*>(at(L.ut));

@@ -133,3 +133,33 @@ def test_batch_plan_replays_captured_graph(F, engine):
             assert np.array_equal(out[k], ref[k]) and np.array_equal(frc[k], ref_f[k]), (order, k)
     plan.close()
     F.fem_destroy_mesh(h)
+
+
+def test_result_independent_of_the_launch_layout(F):
+    """A job's shared-memory layout is planned for the whole launch: alone, the
+    cube's parts fit one chunk; next to a fingertip the launch is chunked. The
+    node sums walk each node's list in the same order either way, so the cube
+    gives the same bits in both launches."""
+    cube, cind = W.cube_sphere()
+    tip, tind = W.fingertip_sphere()
+    hc = F.fem_create_mesh(cube.nodes, cube.tets, cube.tet_material, cube.materials, cube.fixed_nodes)
+    ht = F.fem_create_mesh(tip.nodes, tip.tets, tip.tet_material, tip.materials, tip.fixed_nodes)
+    opt = F.fem_default_options()
+    opt.batch_engine, opt.batch_parts = F.FEM_BATCH_GROUPS, 0
+    alone = F.FemBatch([hc], [cind.n_steps], opt)
+    mixed = F.FemBatch([hc, ht], [cind.n_steps, tind.n_steps], opt)
+    ia, im = alone.info(), mixed.info()
+    print(f"alone: smem {ia.smem_bytes} B, mixed: smem {im.smem_bytes} B, global/CTA {im.global_bytes_per_cta} B")
+    oa = [np.zeros((cube.n_nodes, 3))]
+    fa = [np.zeros((cind.n_steps, 3))]
+    om = [np.zeros((cube.n_nodes, 3)), np.zeros((tip.n_nodes, 3))]
+    fm = [np.zeros((cind.n_steps, 3)), np.zeros((tind.n_steps, 3))]
+    rc, _ = alone.run([cind], 1e-6, oa, fa)
+    assert rc == 0
+    rc, st = mixed.run([cind, tind], 1e-6, om, fm)
+    assert rc == 0
+    assert np.array_equal(oa[0], om[0]) and np.array_equal(fa[0], fm[0])
+    alone.close()
+    mixed.close()
+    F.fem_destroy_mesh(hc)
+    F.fem_destroy_mesh(ht)
