@@ -136,10 +136,10 @@ def test_batch_plan_replays_captured_graph(F, engine):
 
 
 def test_result_independent_of_the_launch_layout(F):
-    """A job's shared-memory layout is planned for the whole launch: alone, the
-    cube's parts fit one chunk; next to a fingertip the launch is chunked. The
-    node sums walk each node's list in the same order either way, so the cube
-    gives the same bits in both launches."""
+    """A job's shared-memory layout (chunk size, placement) is planned for the
+    whole launch: the cube alone and next to a fingertip runs under different
+    layouts. The node sums walk each node's list in the same order whatever
+    the chunking, so the cube gives the same bits in both launches."""
     cube, cind = W.cube_sphere()
     tip, tind = W.fingertip_sphere()
     hc = F.fem_create_mesh(cube.nodes, cube.tets, cube.tet_material, cube.materials, cube.fixed_nodes)
@@ -150,6 +150,7 @@ def test_result_independent_of_the_launch_layout(F):
     mixed = F.FemBatch([hc, ht], [cind.n_steps, tind.n_steps], opt)
     ia, im = alone.info(), mixed.info()
     print(f"alone: smem {ia.smem_bytes} B, mixed: smem {im.smem_bytes} B, global/CTA {im.global_bytes_per_cta} B")
+    assert ia.smem_bytes != im.smem_bytes
     oa = [np.zeros((cube.n_nodes, 3))]
     fa = [np.zeros((cind.n_steps, 3))]
     om = [np.zeros((cube.n_nodes, 3)), np.zeros((tip.n_nodes, 3))]
