@@ -574,6 +574,8 @@ def run_serve(args, rank, world, local):
     sopt = F.fem_default_options()
     sopt.max_newton = 200
     sopt.batch_parts = args.serve_class_cap
+    if args.serve_tets_per_cta:
+        sopt.batch_tets_per_cta = args.serve_tets_per_cta
     # the plain path: one fem_solve (cooperative launch) per request kind, kernel time
     t_plain = []
     for k, d in kinds:
@@ -639,7 +641,8 @@ def run_serve(args, rank, world, local):
             "config": {"workload": (f"serve: Poisson requests over a resident pool of 16 fingertips "
                                     f"({min(m.n_tets for m in pool)}-{max(m.n_tets for m in pool)} tets), "
                                     f"4 random indentations per mesh, {args.serve_seconds:.0f} s per offered rate"),
-                       "tol": TOL, "size_classes": list(info.class_parts[:info.n_classes]),
+                       "tol": TOL, "tets_per_cta_target": sopt.batch_tets_per_cta,
+                       "size_classes": list(info.class_parts[:info.n_classes]),
                        "groups": list(info.class_groups[:info.n_classes]), "result_slots": info.result_slots,
                        "plain_path": "fem_solve per request in arrival order, measured kernel time per request kind "
                                      "(queueing simulated on the same trace)"},
@@ -669,6 +672,9 @@ def main():
     ap.add_argument("--drain-seconds", type=float, default=90.0)
     ap.add_argument("--serve-class-cap", type=int, default=64,
                     help="largest CTA group of the request server (power of two)")
+    ap.add_argument("--serve-tets-per-cta", type=int, default=650,
+                    help="size-class target of the request server (0: the library default, 1300); "
+                         "650 gives larger groups per request than batches use")
     ap.add_argument("--batch-parts", type=int, default=0,
                     help="batched workloads: uniform CTA groups of this size instead of the autotuner")
     ap.add_argument("--n-solves", type=int, default=None,
