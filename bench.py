@@ -232,6 +232,38 @@ def profiled_traffic(summary="solve_kernel_fingertip_sphere.md", key="traffic_by
         return None
 
 
+def _oracle_steps(job):
+    """One worker of cpu_oracle_batch_rate: the oracle's first load steps of
+    one solve, timed (run in a spawned process)."""
+    mesh, ind, n_load_steps = job
+    from oracle import Problem
+    t0 = time.perf_counter()
+    r = Problem(mesh, ind).solve(tol=1e-10, load_steps=n_load_steps)
+    return time.perf_counter() - t0, int(np.sum(r.newton_iters[:n_load_steps]))
+
+
+def cpu_oracle_batch_rate(meshes, draws, n_jobs=16, n_load_steps=2):
+    """The oracle as it stands on independent solves, one process per solve
+    across the host cores (spawned, so no process inherits a CUDA context):
+    the first n_load_steps of n_jobs seeded solves, extrapolated to the full
+    load schedule by load steps."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    jobs = [(meshes[i], draws[i], n_load_steps) for i in range(min(n_jobs, len(draws)))]
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(processes=min(cores, len(jobs))) as pool:
+        res = pool.map(_oracle_steps, jobs)
+    wall = time.perf_counter() - t0
+    full = [t * d.n_steps / n_load_steps for (t, _), d in zip(res, draws)]
+    # throughput of a pool of min(cores, jobs) workers running such solves back to back
+    workers = min(cores, len(jobs))
+    value = workers / (sum(full) / len(full))
+    return {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
+            "sample": (f"{len(jobs)} of the step's solves, load steps 1-{n_load_steps} each ({sum(n for _, n in res)} "
+                       f"Newton iterations, {wall:.1f} s wall on {workers} processes), extrapolated to their full "
+                       f"schedules by load steps; one spawned process per solve, nproc {cores}")}
+
+
 def cpu_oracle_rate(mesh, ind, n_load_steps, variant="fingertip"):
     """Time the oracle (as it stands) on the first n_load_steps of the same
     solve and extrapolate to a full solve by Newton iterations, using the
@@ -541,6 +573,10 @@ def run_batch(args, rank, world, local):
                          "kernel_ms": kernel_ms, "algorithmic_bytes": alg, "peak_kind": peak_kind,
                          "fp32_tflops": flops / (kernel_ms / 1000.0) / 1e12, "fp32_peak_tflops": FP32_PEAK_TFLOPS},
             "clocks": clk.summary()}
+    if rank == 0 and not args.no_cpu_baseline:
+        # the oracle's direct solve is for meshes up to the fingertip's size
+        small = [k for k, m in enumerate(meshes) if m.n_tets <= 40000]
+        line["cpu_baseline"] = cpu_oracle_batch_rate([meshes[k] for k in small], [draws[k] for k in small])
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()
