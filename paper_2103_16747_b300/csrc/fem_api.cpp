@@ -150,8 +150,18 @@ int build_partition(fem_mesh* m, int n_parts, MeshDev& D, PartDims& dims, std::v
     return parts;
   };
   {
-    // part costs are multiples of 0.25: a bracket narrower than that fixes the cuts
+    // part costs are multiples of 0.25: a bracket narrower than that fixes the
+    // cuts. Every tet is counted in some part, so the largest part costs at
+    // least (Nt + Nn/4) / n_parts; start from a bracket a few times that wide
+    // when its top already gives at most n_parts ranges.
     double lo = 1.0, hi = 8.0 * (double)Nt + Nn;
+    {
+      const double low = ((double)Nt + 0.25 * Nn) / n_parts;
+      if (sweep(8.0 * low, nullptr) <= n_parts) {
+        lo = std::max(1.0, low - 1.0);
+        hi = 8.0 * low;
+      }
+    }
     for (int iter = 0; iter < 60 && hi - lo > 0.125; ++iter) {
       const double mid = 0.5 * (lo + hi);
       if (sweep(mid, nullptr) > n_parts) lo = mid; else hi = mid;
