@@ -494,6 +494,17 @@ int fem_apply_tangent(fem_mesh* mesh, const double* u, int32_t step, const fem_o
  */
 int fem_debug_barrier_timeout(double timeout_s);
 
+/*
+ * Self-check of the FP64 reciprocal and reciprocal square root that the element
+ * kernels use instead of FP64 division and square root (FP32 hardware value
+ * refined by one Newton-Raphson step): out_rcp[i] = 1/x[i], out_rsqrt[i] =
+ * 1/sqrt(x[i]) as the kernels compute them, for n host values x with x and 1/x
+ * in FP32's normal range (positive where out_rsqrt is asked for). out_rsqrt may
+ * be NULL.
+ * FEM_ERR_ARG on NULL x/out_rcp or n < 1; FEM_ERR_CUDA without a device.
+ */
+int fem_debug_reciprocals(const double* x, int64_t n, double* out_rcp, double* out_rsqrt);
+
 #ifdef __cplusplus
 }
 #endif

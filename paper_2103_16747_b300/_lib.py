@@ -44,7 +44,7 @@ PHASES = ("eval", "tangent", "pcg_init", "pcg_reduce", "pcg_matvec", "pcg_update
 EXPORTS = ("fem_default_options", "fem_create_mesh", "fem_set_indenter", "fem_set_dirichlet_values",
            "fem_solve", "fem_solve_batch", "fem_destroy_mesh", "fem_last_error", "fem_mesh_info_get", "fem_repartition",
            "fem_eval_residual", "fem_eval_residual_noalloc", "fem_apply_tangent",
-           "fem_debug_barrier_timeout", "fem_batch_create", "fem_batch_run", "fem_batch_info_get",
+           "fem_debug_barrier_timeout", "fem_debug_reciprocals", "fem_batch_create", "fem_batch_run", "fem_batch_info_get",
            "fem_batch_destroy", "fem_batch_tune", "fem_server_create", "fem_server_start", "fem_server_submit",
            "fem_server_result", "fem_server_stop", "fem_server_info_get", "fem_server_destroy",
            "fem_element_stress")
@@ -134,6 +134,7 @@ def _load():
         "fem_eval_residual_noalloc": (C.c_int, [P, P, C.c_int32, C.POINTER(fem_options), P, P, P]),
         "fem_apply_tangent": (C.c_int, [P, P, C.c_int32, C.POINTER(fem_options), P, P]),
         "fem_debug_barrier_timeout": (C.c_int, [C.c_double]),
+        "fem_debug_reciprocals": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
         "fem_batch_create": (C.c_int, [P, P, C.c_int32, C.POINTER(fem_options), C.POINTER(P)]),
         "fem_batch_run": (C.c_int, [P, P, C.c_double, P, P, P]),
         "fem_batch_info_get": (C.c_int, [P, C.POINTER(fem_batch_info)]),
@@ -468,3 +469,13 @@ def fem_apply_tangent(mesh, u, step, p, out_y, opt=None):
 
 def fem_debug_barrier_timeout(timeout_s):
     return lib.fem_debug_barrier_timeout(float(timeout_s))
+
+
+def fem_debug_reciprocals(x):
+    """(1/x, 1/sqrt(x)) as the element kernels compute them in FP64 (x > 0)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    r = np.zeros_like(x)
+    q = np.zeros_like(x)
+    _check(lib.fem_debug_reciprocals(C.c_void_p(x.ctypes.data), x.size, C.c_void_p(r.ctypes.data),
+                                     C.c_void_p(q.ctypes.data)))
+    return r, q

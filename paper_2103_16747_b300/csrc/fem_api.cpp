@@ -1327,4 +1327,21 @@ int fem_debug_barrier_timeout(double timeout_s) {
   return FEM_OK;
 }
 
+int fem_debug_reciprocals(const double* x, int64_t n, double* out_rcp, double* out_rsqrt) {
+  g_err.clear();
+  if (!x || !out_rcp || n < 1 || n > (1 << 28)) return fail(FEM_ERR_ARG, "x, out_rcp and 1 <= n required");
+  double* d = nullptr;
+  const size_t bytes = sizeof(double) * (size_t)n;
+  CUDA_TRY(cudaMalloc(&d, 3 * bytes), "alloc");
+  double* d_rcp = d + n;
+  double* d_rsq = out_rsqrt ? d + 2 * n : nullptr;
+  cudaError_t e = cudaMemcpy(d, x, bytes, cudaMemcpyDefault);
+  if (e == cudaSuccess) e = launch_reciprocals(d, (int)n, d_rcp, d_rsq, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(out_rcp, d_rcp, bytes, cudaMemcpyDefault);
+  if (e == cudaSuccess && out_rsqrt) e = cudaMemcpy(out_rsqrt, d_rsq, bytes, cudaMemcpyDefault);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(e, "reciprocals");
+  return FEM_OK;
+}
+
 }  // extern "C"

@@ -203,6 +203,8 @@ cudaError_t launch_solve(const MeshDev& mesh, const WorkDev& work, const SolvePa
 cudaError_t solve_kernel_attrs(int smem_bytes, int* static_smem, int* blocks_per_sm);
 
 // Element stress of every tet at u (fem_stress.cu); sig and vm in caller tet order.
+// The element kernels' FP64 reciprocal and reciprocal square root on n values (self-check).
+cudaError_t launch_reciprocals(const double* x, int n, double* rcp, double* rsq, cudaStream_t s);
 cudaError_t launch_stress(const int4* tets, const double* dminv, const int* mat, const double* lame,
                           const int* mat_model, const double* u, const int* tet_perm, int n_tets, double* sig,
                           double* vm, cudaStream_t s);

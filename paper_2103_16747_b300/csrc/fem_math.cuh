@@ -39,6 +39,50 @@ namespace fem {
 __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
 
+// ------------------------------------------------------------------ FP64 reciprocals
+// FP64 reciprocal and reciprocal square root without FP64 divide or square-root
+// sequences, each of which takes many slots of B300's narrow FP64 pipe: the FP32
+// hardware value refined by one Newton-Raphson step, y <- y + y (1 - x y) for
+// 1/x and y <- y + (y/2) (1 - x y^2) for 1/sqrt(x). One step squares the
+// relative error: about 1e-14 from FP32's ~1e-7. x and 1/x must lie in FP32's
+// normal range (x positive for the square root).
+__device__ __forceinline__ double rcp_nr(double x) {
+  const double y = (double)__frcp_rn((float)x);
+  return fma(y, fma(-x, y, 1.0), y);
+}
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  const double y = (double)rsqrtf((float)x);
+  return fma(0.5 * y, fma(-x * y, y, 1.0), y);
+}
+
+// One FP64 Jacobi rotation of the refinement sweep (same rotation as
+// jacobi_rotate) with its divisions and square roots from rcp_nr / rsqrt_nr.
+// A rotation is taken only if |A_pq| > 1e-30 + 1e-18 (|A_pp| + |A_qq|), so
+// |tau| < 5e17 and every argument stays in FP32 range.
+__device__ __forceinline__ void jacobi_rotate_nr(double A[3][3], double V[3][3], int p, int q) {
+  const int r = 3 - p - q;
+  const double apq = A[p][q];
+  const double scale = fabs(A[p][p]) + fabs(A[q][q]);
+  if (fabs(apq) <= 1e-30 + 1e-18 * scale) return;
+  const double tau = (A[q][q] - A[p][p]) * rcp_nr(2.0 * apq);
+  const double q2 = 1.0 + tau * tau;
+  const double t = copysign(1.0, tau) * rcp_nr(fabs(tau) + q2 * rsqrt_nr(q2));
+  const double c = rsqrt_nr(1.0 + t * t);
+  const double s = t * c;
+  const double arp = A[r][p], arq = A[r][q];
+  A[p][p] -= t * apq;
+  A[q][q] += t * apq;
+  A[p][q] = A[q][p] = 0.0;
+  A[r][p] = A[p][r] = c * arp - s * arq;
+  A[r][q] = A[q][r] = s * arp + c * arq;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double vp = V[k][p], vq = V[k][q];
+    V[k][p] = c * vp - s * vq;
+    V[k][q] = s * vp + c * vq;
+  }
+}
+
 // One Jacobi rotation zeroing A[p][q]; V accumulates the rotations.
 template <typename T>
 __device__ __forceinline__ void jacobi_rotate(T A[3][3], T V[3][3], int p, int q, T rel_skip) {
@@ -83,9 +127,11 @@ __device__ __forceinline__ void jacobi_eig3(float A[3][3], float V[3][3]) {
 // ------------------------------------------------------------------ FP64 element
 // Co-rotational stress from H = F - I (det F > 0). The stretch S comes from the
 // eigen-decomposition of F^T F - I = H + H^T + H^T H = V diag(delta) V^T: an
-// FP32 Jacobi pass gives V, which is re-orthonormalised and refined by two FP64
-// sweeps. With s_i - 1 = delta_i / (1 + sqrt(1 + delta_i)) nothing cancels at
-// small strain. P = F V diag(psi_i / s_i) V^T (= R V diag(psi_i) V^T).
+// FP32 Jacobi pass gives V to ~1e-7, which is re-orthonormalised and refined by
+// one FP64 sweep (Jacobi converges quadratically: ~1e-14). With s_i - 1 =
+// delta_i / (1 + sqrt(1 + delta_i)) nothing cancels at small strain.
+// P = F V diag(psi_i / s_i) V^T (= R V diag(psi_i) V^T). Divisions and square
+// roots go through rcp_nr / rsqrt_nr.
 static __device__ __noinline__ void corot_stress_f64(const double H[9], double mu, double lam, double P[9],
                                                  double& psi) {
   double Cm[3][3];
@@ -103,13 +149,13 @@ static __device__ __noinline__ void corot_stress_f64(const double H[9], double m
   double V[3][3];
   {
     double a[3] = {V32[0][0], V32[1][0], V32[2][0]}, b[3] = {V32[0][1], V32[1][1], V32[2][1]};
-    const double na = rsqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    const double na = rsqrt_nr(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
 #pragma unroll
     for (int k = 0; k < 3; ++k) a[k] *= na;
     const double ab = a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
 #pragma unroll
     for (int k = 0; k < 3; ++k) b[k] -= ab * a[k];
-    const double nb = rsqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+    const double nb = rsqrt_nr(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
 #pragma unroll
     for (int k = 0; k < 3; ++k) b[k] *= nb;
     const double c[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
@@ -132,20 +178,22 @@ static __device__ __noinline__ void corot_stress_f64(const double H[9], double m
 #pragma unroll
       for (int j = 0; j < i; ++j) B[i][j] = B[j][i] = 0.5 * (B[i][j] + B[j][i]);
   }
-  jacobi_sweep(B, V, 1e-18);
-  jacobi_sweep(B, V, 1e-18);
+  jacobi_rotate_nr(B, V, 0, 1);
+  jacobi_rotate_nr(B, V, 0, 2);
+  jacobi_rotate_nr(B, V, 1, 2);
   double sm1[3], s[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const double d = B[k][k];
-    sm1[k] = d / (1.0 + sqrt(1.0 + d));
+    const double q = 1.0 + d;   // s_k^2 > 0
+    sm1[k] = d * rcp_nr(1.0 + q * rsqrt_nr(q));
     s[k] = 1.0 + sm1[k];
   }
   const double trE = sm1[0] + sm1[1] + sm1[2];
   psi = mu * (sm1[0] * sm1[0] + sm1[1] * sm1[1] + sm1[2] * sm1[2]) + 0.5 * lam * trE * trE;
   double w[3];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) w[k] = (2.0 * mu * sm1[k] + lam * trE) / s[k];
+  for (int k = 0; k < 3; ++k) w[k] = (2.0 * mu * sm1[k] + lam * trE) * rcp_nr(s[k]);
   double Mt[3][3];  // V diag(w) V^T
 #pragma unroll
   for (int i = 0; i < 3; ++i)
@@ -212,7 +260,7 @@ __device__ __forceinline__ void elem_eval_f64(const double u[4][3], const double
     for (int k = 0; k < 9; ++k) hh += H[k] * H[k];
     const double I1m3 = 2.0 * trH + hh;
     energy = vol * (0.5 * mu * I1m3 - mu * lnJ + 0.5 * lam * lnJ * lnJ);
-    const double cf = (lam * lnJ - mu) / J;
+    const double cf = (lam * lnJ - mu) * rcp_nr(J);
 #pragma unroll
     for (int k = 0; k < 9; ++k) P[k] = mu * F[k] + cf * cof[k];
   }

@@ -83,7 +83,21 @@ __global__ void stress_kernel(const int4* __restrict__ tets, const double* __res
   }
 }
 
+__global__ void reciprocals_kernel(const double* __restrict__ x, int n, double* __restrict__ rcp,
+                                   double* __restrict__ rsq) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  rcp[i] = rcp_nr(x[i]);
+  if (rsq) rsq[i] = rsqrt_nr(x[i]);
+}
+
 }  // namespace
+
+cudaError_t launch_reciprocals(const double* x, int n, double* rcp, double* rsq, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  reciprocals_kernel<<<(n + 255) / 256, 256, 0, s>>>(x, n, rcp, rsq);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_stress(const int4* tets, const double* dminv, const int* mat, const double* lame,
                           const int* mat_model, const double* u, const int* tet_perm, int n_tets, double* sig,

@@ -243,3 +243,16 @@ def test_fingertip_sphere_parity(F, fingertip_golden):
     # certify: the oracle's own FP64 residual of the GPU displacement
     rn, scale, _ = Problem(m, ind).residual_norm(out["u"], 20)
     assert rn <= 1e-6 * scale
+
+
+def test_fp64_reciprocals_meet_their_error_bound(F):
+    """The element kernels take FP64 1/x and 1/sqrt(x) from the FP32 hardware
+    value refined by one Newton-Raphson step; one step squares FP32's relative
+    error (<= ~2e-7), so both stay within 1e-13 of the FP64 values wherever x
+    and 1/x are FP32-normal."""
+    rng = np.random.default_rng(17)
+    x = 10.0 ** rng.uniform(-30, 30, 200000)
+    x = np.concatenate([x, 1.0 + rng.uniform(-1e-3, 1e-3, 1000), [1.0, 2.0, 0.5, 3.0, 1e-37, 1e37]])
+    r, q = F.fem_debug_reciprocals(x)
+    assert np.max(np.abs(r * x - 1.0)) < 1e-13
+    assert np.max(np.abs(q * np.sqrt(x) - 1.0)) < 1e-13
