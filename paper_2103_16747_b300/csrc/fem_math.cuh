@@ -131,7 +131,8 @@ __device__ __forceinline__ void jacobi_eig3(float A[3][3], float V[3][3]) {
 // one FP64 sweep (Jacobi converges quadratically: ~1e-14). With s_i - 1 =
 // delta_i / (1 + sqrt(1 + delta_i)) nothing cancels at small strain.
 // P = F V diag(psi_i / s_i) V^T (= R V diag(psi_i) V^T). Divisions and square
-// roots go through rcp_nr / rsqrt_nr.
+// roots go through rcp_nr / rsqrt_nr. Out of line: only co-rotational elements
+// call it, and inlined it would take registers from the whole solve kernel.
 static __device__ __noinline__ void corot_stress_f64(const double H[9], double mu, double lam, double P[9],
                                                  double& psi) {
   double Cm[3][3];
