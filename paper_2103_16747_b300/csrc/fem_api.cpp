@@ -117,16 +117,22 @@ namespace {
 // node ids, local node->tet lists, and the halo tables. Fills the partition
 // fields of D (the mesh-wide fields are copied from m->dev) and dims; device
 // arrays go to o (freed first) and their bytes to by.
-int build_partition(fem_mesh* m, int n_parts, MeshDev& D, PartDims& dims, std::vector<void*>& o, size_t& by) {
+int build_partition(fem_mesh* m, int n_parts, int node_cap, MeshDev& D, PartDims& dims, std::vector<void*>& o,
+                    size_t& by) {
   HostPhases hp;
   const int Nn = (int)m->n_nodes, Nt = (int)m->n_tets;
   // contiguous node ranges; a part's cost is its unique tets (halo tets
   // included, each computed once per part) plus its owned nodes. The cut
   // target is found by bisection so that exactly n_parts ranges result.
+  // node_cap > 0 also ends a part at that many owned nodes (the kernel's node
+  // gathers take one thread per node component: a part over CTA size / 3
+  // nodes needs a second pass and holds up every CTA at the next sync); it
+  // applies only where the average part stays well below it.
+  if (node_cap > 0 && (double)Nn > 0.8 * (double)node_cap * n_parts) node_cap = 0;
   std::vector<int> nb(n_parts + 1, 0);
   std::vector<int> stamp(Nt, -1);
   auto sweep = [&](double target, std::vector<int>* cuts) {
-    int parts = 1, id = 0;
+    int parts = 1, id = 0, nodes = 0;
     double cost = 0.0;
     if (cuts) (*cuts)[0] = 0;
     for (int i = 0; i < Nn; ++i) {
@@ -135,16 +141,18 @@ int build_partition(fem_mesh* m, int n_parts, MeshDev& D, PartDims& dims, std::v
         const int t = m->csr_ent[j] >> 2;
         if (stamp[t] != id) add += 1.0;
       }
-      if (cost > 0.0 && cost + add > target) {
+      if ((cost > 0.0 && cost + add > target) || (node_cap > 0 && nodes == node_cap)) {
         if (cuts && parts < n_parts) (*cuts)[parts] = i;
         ++parts;
         ++id;
         cost = 0.0;
+        nodes = 0;
         add = 0.25;
         for (int j = m->csr_ptr[i]; j < m->csr_ptr[i + 1]; ++j) add += (stamp[m->csr_ent[j] >> 2] != id) ? 1.0 : 0.0;
       }
       for (int j = m->csr_ptr[i]; j < m->csr_ptr[i + 1]; ++j) stamp[m->csr_ent[j] >> 2] = id;
       cost += add;
+      ++nodes;
     }
     std::fill(stamp.begin(), stamp.end(), -1);
     return parts;
@@ -457,7 +465,7 @@ int build_partitions(fem_mesh* m, int n_parts) {
   PartDims dims{};
   std::vector<void*> o;
   size_t by = 0;
-  int rc = build_partition(m, n_parts, D, dims, o, by);
+  int rc = build_partition(m, n_parts, kSolveBlock / 3, D, dims, o, by);
   if (rc) {
     for (void* q : o) cudaFree(q);
     m->bytes -= by;
@@ -523,7 +531,7 @@ int batch_partition(fem_mesh* m, int parts, const MeshDev** dev, const PartDims*
   auto it = m->batch_parts.find(parts);
   if (it == m->batch_parts.end()) {
     fem_mesh::BatchPart bp;
-    const int rc = build_partition(m, parts, bp.dev, bp.dims, bp.owned, bp.bytes);
+    const int rc = build_partition(m, parts, kGroupBlock / 3, bp.dev, bp.dims, bp.owned, bp.bytes);
     if (rc) {
       for (void* q : bp.owned) cudaFree(q);
       m->bytes -= bp.bytes;
