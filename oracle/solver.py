@@ -37,7 +37,11 @@ Pi_k gains the smoothed dissipation potential sum_i mu_f fn_i f0(|s_i|) of
 contact.friction, with s_i the tangential slip of node i relative to the
 indenter's translation over the step and the smoothing slip
 eps = fric_eps_rel * h_bar. The reported contact forces include the
-friction forces.
+friction forces. With friction_passes = n > 1 each load step is solved n times:
+after each solve the normal forces and normals are frozen again at the
+current state, with the indenter at this step's pose (the slip still counts
+from the step's start); the passes converge to friction that uses the step's
+own normal forces.
 
 Dynamic stepping (dt > 0). The paper integrates the deformable body's dynamics
 implicitly in time, with a time step of 1e-4 s (Sec. III-A). Reading: backward
@@ -84,7 +88,7 @@ class Problem:
 
     def __init__(self, mesh, indenter, c_kappa: float = 100.0, dirichlet_values=None,
                  dt: float = 0.0, density: float = 1.1e-9, mu_f: float = 0.0,
-                 fric_eps_rel: float = 0.01):
+                 fric_eps_rel: float = 0.01, friction_passes: int = 1):
         self.X = np.asarray(mesh.nodes, dtype=np.float64)
         self.tets = np.asarray(mesh.tets, dtype=np.int64)
         self.n = len(self.X)
@@ -111,6 +115,7 @@ class Problem:
         self.u_tilde = None      # inertial prediction u~ of the current time step (dt > 0)
         self.E_max = float(self.E.max())
         self.mu_f = float(mu_f)
+        self.friction_passes = max(1, int(friction_passes))
         self.fric = None         # lagged friction state of the current load step
         self.scale_floor = self.E_max * self.h_bar ** 2 * 1e-3
         self.u_presc = np.zeros((self.n, 3))
@@ -191,6 +196,14 @@ class Problem:
         fn = np.where((phi < 0) & (self.k > 0), -self.k * phi, 0.0)
         self.fric = dict(x_start=x0, dc=self.origin_at(step) - self.origin_at(step - 1),
                          normal=n, fn=fn)
+
+    def refresh_friction(self, u, step):
+        """Freeze the normal forces and normals again at the current state u,
+        indenter at this step's pose; the slip origin and translation stay."""
+        x = self.X + u
+        phi, n, _ = contact.sdf(self.shape, self.origin_at(step), self.R, self.params, x)
+        self.fric["normal"] = n
+        self.fric["fn"] = np.where((phi < 0) & (self.k > 0), -self.k * phi, 0.0)
 
     def friction_terms(self, u):
         """(energy, gradient (Nn,3), Hessian blocks (Nn,3,3)) of the lagged
@@ -282,40 +295,49 @@ class Problem:
             if self.mu_f > 0.0:
                 self.set_friction_lag(u_prev, step)
             u[self.fixed] = (self.u_presc * (step / K))[self.fixed]
+            passes = self.friction_passes if self.mu_f > 0.0 else 1
             ok = False
-            for it in range(max_newton + 1):
-                g, fc = self.gradient(u, step)
-                g_free = g.ravel()[self.free]
-                rn = float(np.linalg.norm(g_free))
-                scale = max(float(np.linalg.norm(fc)), self.scale_floor)
-                if verbose:
-                    print(f"step {step} it {it} |R|={rn:.3e} scale={scale:.3e}")
-                if rn <= tol * scale:
-                    ok = True
-                    break
-                if it == max_newton:
-                    break
-                d_free, proj = self._direction(u, step, g_free)
-                n_proj += int(proj)
-                du = np.zeros(3 * self.n)
-                du[self.free] = d_free
-                du = du.reshape(-1, 3)
-                slope = float(g_free @ d_free)
-                e0, _ = self.energy(u, step)
-                alpha = 1.0
-                accepted = False
-                for _ in range(max_backtracks):
-                    ut = u + alpha * du
-                    et, minJ = self.energy(ut, step)
-                    if minJ > 0 and np.isfinite(et):
-                        if rn <= 1e-3 * scale or et <= e0 + 1e-4 * alpha * slope:
-                            accepted = True
-                            break
-                    alpha *= 0.5
-                if not accepted:
-                    break
-                u = ut
-            iters[step - 1] = it
+            it_total = 0
+            for pss in range(passes):
+              if pss > 0:
+                  if not ok:
+                      break
+                  self.refresh_friction(u, step)
+              ok = False
+              for it in range(max_newton + 1):
+                  g, fc = self.gradient(u, step)
+                  g_free = g.ravel()[self.free]
+                  rn = float(np.linalg.norm(g_free))
+                  scale = max(float(np.linalg.norm(fc)), self.scale_floor)
+                  if verbose:
+                      print(f"step {step} it {it} |R|={rn:.3e} scale={scale:.3e}")
+                  if rn <= tol * scale:
+                      ok = True
+                      break
+                  if it == max_newton:
+                      break
+                  d_free, proj = self._direction(u, step, g_free)
+                  n_proj += int(proj)
+                  du = np.zeros(3 * self.n)
+                  du[self.free] = d_free
+                  du = du.reshape(-1, 3)
+                  slope = float(g_free @ d_free)
+                  e0, _ = self.energy(u, step)
+                  alpha = 1.0
+                  accepted = False
+                  for _ in range(max_backtracks):
+                      ut = u + alpha * du
+                      et, minJ = self.energy(ut, step)
+                      if minJ > 0 and np.isfinite(et):
+                          if rn <= 1e-3 * scale or et <= e0 + 1e-4 * alpha * slope:
+                              accepted = True
+                              break
+                      alpha *= 0.5
+                  if not accepted:
+                      break
+                  u = ut
+              it_total += it
+            iters[step - 1] = it_total
             resid[step - 1] = rn
             scales[step - 1] = scale
             step_force[step - 1] = fc.sum(axis=0)

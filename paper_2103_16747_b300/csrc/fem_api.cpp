@@ -354,6 +354,7 @@ void set_physics(const fem_options& o, double h_bar, SolveParams& P) {
   P.density = o.dt > 0.0 ? o.density : 0.0;
   P.mu_f = o.mu_f;
   P.fric_eps = o.friction_eps * h_bar;
+  P.fric_passes = o.friction_passes;
 }
 
 bool common_options_valid(const fem_options& o) {
@@ -361,7 +362,8 @@ bool common_options_valid(const fem_options& o) {
          o.cg_rtol_min > 0 && o.cg_rtol_min <= o.cg_rtol_max && o.tangent >= 0 && o.tangent <= 3 &&
          o.barrier_timeout_s > 0 && o.precond_degree >= 1 && o.precond_degree <= 8 && o.precond_ratio > 1.0 &&
          o.dt >= 0.0 && std::isfinite(o.dt) && (o.dt == 0.0 || (o.density > 0.0 && std::isfinite(o.density))) &&
-         o.mu_f >= 0.0 && std::isfinite(o.mu_f) && o.friction_eps > 0.0 && std::isfinite(o.friction_eps);
+         o.mu_f >= 0.0 && std::isfinite(o.mu_f) && o.friction_eps > 0.0 && std::isfinite(o.friction_eps) &&
+         o.friction_passes >= 1 && o.friction_passes <= 64;
 }
 
 SmemLayout plan_layout(const PartDims& d, int budget) {
@@ -613,6 +615,7 @@ void fem_default_options(fem_options* opt) {
   opt->density = 1.1e-9;
   opt->mu_f = 0.0;
   opt->friction_eps = 0.01;
+  opt->friction_passes = 1;
 }
 
 const char* fem_last_error(void) { return g_err.c_str(); }

@@ -99,6 +99,7 @@ struct SolveParams {
   float cheb_theta, cheb_delta;     // centre and half-width of the Chebyshev interval
   double inv_dt, density;           // dynamic stepping: 1 / time step (0: quasi-static), mass density
   double mu_f, fric_eps;            // Coulomb coefficient (0: frictionless), smoothing slip
+  int fric_passes;                  // solves per load step, friction state refreshed between them
   int max_newton, max_cg, max_backtracks;
   double tol, c_kappa, cg_rtol_max, cg_rtol_min;
   unsigned long long timeout_ns;

@@ -1239,15 +1239,39 @@ __device__ bool solve_body(Ctx& C, const MeshDev& M, const WorkDev& W, const Sol
     double fs[3] = {red_out[EV_FX], red_out[EV_FY], red_out[EV_FZ]};
     int active = (int)red_out[EV_ACTIVE];
     double rn_prev = rn;
-    const double rn_step0 = rn;
-    int it = 0, cg_step = 0;
+    double rn_step0 = rn;
+    int it = 0, it_pass0 = 0, pass = 1, cg_step = 0;
     bool ok = false;
     bool use_exact = P.tangent_mode == 1;
     bool exact_banned = false;
     for (;;) {
       if (!isfinite(rn)) { status = ST_NONFINITE; break; }
-      if (rn <= P.tol * scale) { ok = true; break; }
-      if (it >= P.max_newton) { status = ST_NOT_CONVERGED; break; }
+      if (rn <= P.tol * scale) {
+        if (!C.fric_on || pass >= P.fric_passes) { ok = true; break; }
+        // friction pass: normal forces and normals again from the converged
+        // state, indenter at this step's pose (slip origin and translation
+        // stay); then Newton again from that state
+        ++pass;
+        it_pass0 = it;
+        if (!sync_parts<CL>(C, gb)) return false;   // other parts' accepted u
+        for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) friction_lag_node(C, P, i, org);
+        __syncthreads();
+        long long t = tick(C);
+        if (!eval_pass<CL>(C, M, W, P, gb, bf, 0.0, org, false)) return false;
+        tock(C, PH_EVAL, t);
+        if (red_out[EV_BAD] > 0.0) { status = ST_NONFINITE; break; }
+        energy = red_out[EV_ELASTIC] + red_out[EV_CONTACT];
+        rn = sqrt(red_out[EV_RR]);
+        scale = fmax(sqrt(red_out[EV_FCFC]), M.scale_floor);
+        fs[0] = red_out[EV_FX]; fs[1] = red_out[EV_FY]; fs[2] = red_out[EV_FZ];
+        active = (int)red_out[EV_ACTIVE];
+        rn_prev = rn;
+        rn_step0 = rn;
+        use_exact = P.tangent_mode == 1;
+        exact_banned = false;
+        continue;
+      }
+      if (it - it_pass0 >= P.max_newton) { status = ST_NOT_CONVERGED; break; }
       const int mode = P.tangent_mode == 3 ? 3 : (use_exact ? 1 : 0);
       long long t = tick(C);
       tangent_pass(C, M, mode);

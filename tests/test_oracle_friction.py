@@ -10,6 +10,9 @@ model is isotropic Coulomb, Sec. III-A; reading in oracle/solver.py).
     tangential resultant equals mu times the normal resultant of the previous
     step (the lagged normal force), exactly;
   - with a large coefficient the contact nodes stick to the moving plane;
+  - re-solving each step with the normal forces refreshed at its own end state
+    (friction passes) converges to Coulomb's law with the step's own normal
+    forces: the per-node mismatch contracts pass by pass;
   - mu_f = 0 is the frictionless solve."""
 import numpy as np
 import pytest
@@ -135,6 +138,37 @@ def test_large_coefficient_sticks_contact_nodes_to_the_plane():
     ux_plane = (ind.depth_schedule[-1] - ind.depth_schedule[0]) * ind.direction[0]
     np.testing.assert_allclose(r.u[inside, 0] - r.step_u[0][inside, 0], ux_plane, atol=2 * p.fric_eps)
     p.fric = None
+
+
+def _current_state_mismatch(p, r, mu):
+    """max_i | |f_t,i| - mu fn_i(u_end) | / max |f_t|: Coulomb's law with the
+    normal forces of the converged end state, indenter at the last pose."""
+    p.set_friction_lag(r.step_u[-2], p.K)
+    p.refresh_friction(r.u, p.K)
+    ft = np.linalg.norm(r.nodal_contact[:, :2], axis=1)
+    out = float(np.abs(ft - mu * p.fric["fn"]).max() / ft.max())
+    p.fric = None
+    return out
+
+
+def test_friction_passes_converge_to_the_current_normal_forces():
+    mu = 0.783
+    m, ind, _ = _dragged_plane(mu)
+    errs, fx = [], []
+    for passes in (1, 3, 8):
+        p = Problem(m, ind, mu_f=mu, friction_passes=passes)
+        r = p.solve(tol=1e-10)
+        assert r.converged
+        errs.append(_current_state_mismatch(p, r, mu))
+        fx.append(r.step_force[-1, 0])
+        if passes == 1:
+            it1 = r.newton_iters.copy()
+        else:
+            # every pass after the first costs at least one Newton iteration
+            assert np.all(r.newton_iters[1:] > it1[1:])
+    assert errs[0] > 0.1 and errs[1] < 0.25 * errs[0] and errs[2] < 1e-3
+    # the lagged normal force trails the load: refreshed, the drag grows
+    assert fx[0] < fx[1] < fx[2]
 
 
 def test_zero_coefficient_is_frictionless():
