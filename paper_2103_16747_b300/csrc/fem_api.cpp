@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <climits>
 #include <array>
@@ -19,6 +20,8 @@
 #include <cstring>
 #include <numeric>
 #include <string>
+#include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/fem.h"
@@ -85,239 +88,358 @@ uint64_t spread_bits(uint64_t v) {
   return v;
 }
 
-template <typename T>
-cudaError_t upload(T** dptr, const std::vector<T>& h, cudaStream_t s, std::vector<void*>& owned,
-                   size_t& bytes) {
-  const size_t n = std::max<size_t>(h.size(), 1) * sizeof(T);
-  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dptr), n);
-  if (e != cudaSuccess) return e;
-  owned.push_back(*dptr);
-  bytes += n;
-  if (!h.empty()) e = cudaMemcpyAsync(*dptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s);
-  return e;
-}
+// One device allocation for a set of arrays. add() records an array's length
+// and, optionally, host contents to upload or a zero fill; commit() allocates
+// the total once (each array 256-byte aligned, uploaded arrays first), points
+// every array into the block, copies all uploaded contents with one
+// host-to-device copy through a pageable staging buffer (the call returns once
+// the buffer is staged) and zero-fills the rest that asked for it. The block's
+// base pointer goes to `owned`, its size to `bytes`.
+class DeviceArena {
+ public:
+  template <typename P>
+  void add(P** dst, size_t count, bool zero = false) {
+    items_.push_back({reinterpret_cast<void**>(const_cast<std::remove_const_t<P>**>(dst)),
+                      std::max<size_t>(count, 1) * sizeof(P), 0, nullptr, zero});
+  }
+  template <typename P, typename T>
+  void upload(P** dst, const std::vector<T>& h) {
+    static_assert(std::is_same<std::remove_const_t<P>, T>::value, "pointer and vector types differ");
+    items_.push_back({reinterpret_cast<void**>(const_cast<T**>(dst)), std::max<size_t>(h.size(), 1) * sizeof(T),
+                      h.size() * sizeof(T), h.data(), false});
+  }
+  cudaError_t commit(cudaStream_t s, std::vector<void*>& owned, size_t& bytes) {
+    size_t off = 0, up_end = 0;
+    for (int pass = 0; pass < 2; ++pass)
+      for (Item& it : items_)
+        if ((it.src != nullptr) == (pass == 0)) {
+          it.off = off;
+          if (it.src) up_end = off + it.copy;
+          off += (it.bytes + 255) & ~(size_t)255;
+        }
+    unsigned char* base = nullptr;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&base), std::max<size_t>(off, 256));
+    if (e != cudaSuccess) return e;
+    owned.push_back(base);
+    bytes += std::max<size_t>(off, 256);
+    for (Item& it : items_) *it.dst = base + it.off;
+    if (up_end > 0) {
+      std::vector<unsigned char> stage(up_end);
+      for (const Item& it : items_)
+        if (it.src && it.copy) std::memcpy(stage.data() + it.off, it.src, it.copy);
+      e = cudaMemcpyAsync(base, stage.data(), up_end, cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) return e;
+    }
+    for (const Item& it : items_)
+      if (it.zero && (e = cudaMemsetAsync(base + it.off, 0, it.bytes, s)) != cudaSuccess) return e;
+    items_.clear();
+    return cudaSuccess;
+  }
 
-template <typename T>
-cudaError_t alloc(T** dptr, size_t count, std::vector<void*>& owned, size_t& bytes) {
-  const size_t n = std::max<size_t>(count, 1) * sizeof(T);
-  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dptr), n);
-  if (e != cudaSuccess) return e;
-  owned.push_back(*dptr);
-  bytes += n;
-  return cudaSuccess;
-}
+ private:
+  struct Item {
+    void** dst;
+    size_t bytes, copy;
+    const void* src;
+    bool zero;
+    size_t off = 0;
+  };
+  std::vector<Item> items_;
+};
+
+// Host half of a partition (plan_partition): the cut and the per-part arrays.
+struct PartPlan {
+  std::vector<int> nb, tb, hb, halo, pt_info, lcsr_ptr;
+  std::vector<unsigned> halo_src, lcsr;
+  std::vector<ushort4> pt_nodes;
+  std::vector<double> pt_dminv, pt_vol;   // pt_dminv: [9][total_pt]
+  int total_pt = 0, max_own = 0, max_loc = 0, max_pt = 0, max_lcsr = 0;
+};
 
 }  // namespace
 
 
 namespace {
 
-// Cut the (Morton-ordered) node range into n_parts contiguous parts and build
-// the per-part arrays: part tets (every tet touching an owned node), local
-// node ids, local node->tet lists, and the halo tables. Fills the partition
-// fields of D (the mesh-wide fields are copied from m->dev) and dims; device
-// arrays go to o (freed first) and their bytes to by.
-int build_partition(fem_mesh* m, int n_parts, int node_cap, MeshDev& D, PartDims& dims, std::vector<void*>& o,
-                    size_t& by) {
-  HostPhases hp;
+// Runs f(p, w) for p in [0, n) on up to `workers` threads (w = the worker's
+// index, for per-worker scratch); the calling thread is worker 0. Items are
+// taken from a shared counter, so the assignment varies but every item runs
+// exactly once; if a thread cannot be started its items run on the others.
+template <typename F>
+void parallel_items(int n, int workers, F&& f) {
+  std::atomic<int> next{0};
+  auto run = [&](int w) {
+    for (int p; (p = next.fetch_add(1, std::memory_order_relaxed)) < n;) f(p, w);
+  };
+  std::vector<std::thread> th;
+  for (int w = 1; w < workers; ++w) {
+    try {
+      th.emplace_back(run, w);
+    } catch (...) {
+      break;
+    }
+  }
+  run(0);
+  for (auto& t : th) t.join();
+}
+
+// Host threads for the per-part work of a mesh: none below ~20k tets (a
+// thread start costs about what a small mesh's whole pass does), at most 16,
+// and per-worker scratch (one int per node and per tet) kept under 256 MB.
+int host_workers(int64_t Nn, int64_t Nt) {
+  if (Nt < 20000) return 1;
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const int64_t by_mem = std::max<int64_t>(1, (int64_t)(256 << 20) / (4 * (Nn + Nt)));
+  return (int)std::min<int64_t>({(int64_t)hw, 16, by_mem});
+}
+
+// Cut the (Morton-ordered) node range into n_parts contiguous ranges nb. A
+// part's cost is its unique tets (halo tets included, each computed once per
+// part) plus a quarter per owned node; the cut target is the smallest at which
+// a greedy sweep makes at most n_parts ranges, found by bisection (the greedy
+// count does not grow with the target). node_cap > 0 also ends a part at that
+// many owned nodes (the kernel's node gathers take one thread per node
+// component: a part over CTA size / 3 nodes needs a second pass and holds up
+// every CTA at the next sync); it applies only where the average part stays
+// well below it.
+int cut_node_range(const fem_mesh* m, int n_parts, int node_cap, std::vector<int>& nb) {
   const int Nn = (int)m->n_nodes, Nt = (int)m->n_tets;
-  // contiguous node ranges; a part's cost is its unique tets (halo tets
-  // included, each computed once per part) plus its owned nodes. The cut
-  // target is found by bisection so that exactly n_parts ranges result.
-  // node_cap > 0 also ends a part at that many owned nodes (the kernel's node
-  // gathers take one thread per node component: a part over CTA size / 3
-  // nodes needs a second pass and holds up every CTA at the next sync); it
-  // applies only where the average part stays well below it.
   if (node_cap > 0 && (double)Nn > 0.8 * (double)node_cap * n_parts) node_cap = 0;
-  std::vector<int> nb(n_parts + 1, 0);
+  nb.assign(n_parts + 1, 0);
+  const int* cp = m->csr_ptr.data();
+  const int* ce = m->csr_ent.data();
+  // stamp[t] = the last part that counted tet t; every part of every sweep
+  // takes a fresh id, so no reset is needed between sweeps
   std::vector<int> stamp(Nt, -1);
+  int epoch = -1;
+  auto fresh_id = [&]() {
+    if (epoch == INT_MAX) {
+      std::fill(stamp.begin(), stamp.end(), -1);
+      epoch = -1;
+    }
+    return ++epoch;
+  };
+  // number of ranges at this target (stops early past n_parts unless the cuts
+  // are wanted)
   auto sweep = [&](double target, std::vector<int>* cuts) {
-    int parts = 1, id = 0, nodes = 0;
+    int parts = 1, nodes = 0, id = fresh_id();
     double cost = 0.0;
     if (cuts) (*cuts)[0] = 0;
     for (int i = 0; i < Nn; ++i) {
-      double add = 0.25;
-      for (int j = m->csr_ptr[i]; j < m->csr_ptr[i + 1]; ++j) {
-        const int t = m->csr_ent[j] >> 2;
-        if (stamp[t] != id) add += 1.0;
+      const int j0 = cp[i], j1 = cp[i + 1];
+      int fresh = 0;
+      for (int j = j0; j < j1; ++j) {   // a tet appears once in a node's list
+        const int t = ce[j] >> 2;
+        fresh += stamp[t] != id;
+        stamp[t] = id;
       }
+      double add = 0.25 + fresh;
       if ((cost > 0.0 && cost + add > target) || (node_cap > 0 && nodes == node_cap)) {
         if (cuts && parts < n_parts) (*cuts)[parts] = i;
         ++parts;
-        ++id;
+        if (!cuts && parts > n_parts) return parts;
+        id = fresh_id();
         cost = 0.0;
         nodes = 0;
-        add = 0.25;
-        for (int j = m->csr_ptr[i]; j < m->csr_ptr[i + 1]; ++j) add += (stamp[m->csr_ent[j] >> 2] != id) ? 1.0 : 0.0;
+        add = 0.25 + (j1 - j0);   // the new part has seen none of these tets
+        for (int j = j0; j < j1; ++j) stamp[ce[j] >> 2] = id;
       }
-      for (int j = m->csr_ptr[i]; j < m->csr_ptr[i + 1]; ++j) stamp[m->csr_ent[j] >> 2] = id;
       cost += add;
       ++nodes;
     }
-    std::fill(stamp.begin(), stamp.end(), -1);
     return parts;
   };
+  // part costs are multiples of 0.25: a bracket narrower than that fixes the
+  // cuts. Every tet is counted in some part, so the largest part costs at
+  // least (Nt + Nn/4) / n_parts; start from a bracket a few times that wide
+  // when its top already gives at most n_parts ranges.
+  double lo = 1.0, hi = 8.0 * (double)Nt + Nn;
   {
-    // part costs are multiples of 0.25: a bracket narrower than that fixes the
-    // cuts. Every tet is counted in some part, so the largest part costs at
-    // least (Nt + Nn/4) / n_parts; start from a bracket a few times that wide
-    // when its top already gives at most n_parts ranges.
-    double lo = 1.0, hi = 8.0 * (double)Nt + Nn;
-    {
-      const double low = ((double)Nt + 0.25 * Nn) / n_parts;
-      if (sweep(8.0 * low, nullptr) <= n_parts) {
-        lo = std::max(1.0, low - 1.0);
-        hi = 8.0 * low;
-      }
+    const double low = ((double)Nt + 0.25 * Nn) / n_parts;
+    if (sweep(8.0 * low, nullptr) <= n_parts) {
+      lo = std::max(1.0, low - 1.0);
+      hi = 8.0 * low;
     }
-    for (int iter = 0; iter < 60 && hi - lo > 0.125; ++iter) {
-      const double mid = 0.5 * (lo + hi);
-      if (sweep(mid, nullptr) > n_parts) lo = mid; else hi = mid;
-    }
-    const int got = sweep(hi, &nb);
-    for (int c = std::min(got, n_parts); c < n_parts; ++c) nb[c] = std::min(Nn, nb[c - 1] + 1);
   }
+  for (int iter = 0; iter < 60 && hi - lo > 0.125; ++iter) {
+    const double mid = 0.5 * (lo + hi);
+    if (sweep(mid, nullptr) > n_parts) lo = mid; else hi = mid;
+  }
+  const int got = sweep(hi, &nb);
+  for (int c = std::min(got, n_parts); c < n_parts; ++c) nb[c] = std::min(Nn, nb[c - 1] + 1);
   nb[n_parts] = Nn;
-  hp.mark("cut");
   for (int p = 1; p <= n_parts; ++p)
     if (nb[p] <= nb[p - 1]) return fail(FEM_ERR_TOO_LARGE, "cannot cut %d nodes into %d parts", Nn, n_parts);
-  std::vector<int> part_of(Nn);
-  for (int p = 0; p < n_parts; ++p)
-    for (int i = nb[p]; i < nb[p + 1]; ++i) part_of[i] = p;
+  return FEM_OK;
+}
 
-  std::vector<int> tb(n_parts + 1, 0), hb(n_parts + 1, 0), halo;
-  std::vector<unsigned> halo_src;
-  std::vector<ushort4> pt_nodes;
-  std::vector<double> pt_dminv_aos, pt_vol;
-  std::vector<int> pt_info;
-  std::vector<int> lcsr_ptr(Nn + 1, 0);
-  std::vector<unsigned> lcsr;
-  std::vector<int> local_of_tet(Nt, -1);
-  std::vector<int> local_of_node(Nn, -1);
-  {
-    // part tets are about twice the mesh's at the usual part sizes
-    const size_t guess = 2 * (size_t)Nt + 1024;
-    pt_nodes.reserve(guess);
-    pt_dminv_aos.reserve(9 * guess);
-    pt_vol.reserve(guess);
-    pt_info.reserve(guess);
-    lcsr.reserve(4 * (size_t)Nt);
-  }
-  int max_own = 0, max_loc = 0, max_pt = 0;
-  std::vector<int> tl;
-  for (int p = 0; p < n_parts; ++p) {
-    tl.clear();
-    for (int i = nb[p]; i < nb[p + 1]; ++i)
-      for (int j = m->csr_ptr[i]; j < m->csr_ptr[i + 1]; ++j) {
-        const int t = m->csr_ent[j] >> 2;
-        if (local_of_tet[t] == -2) continue;   // seen (reset with the other stamps below)
-        local_of_tet[t] = -2;
-        tl.push_back(t);
-      }
-    std::sort(tl.begin(), tl.end());
-    const int n_own = nb[p + 1] - nb[p];
-    for (int i = nb[p]; i < nb[p + 1]; ++i) local_of_node[i] = i - nb[p];
-    std::vector<int> hl;
-    for (int t : tl)
+// Build the per-part arrays of a cut (host only): part tets (every tet
+// touching an owned node, ascending), local node ids (owned nodes first, then
+// the halo ascending), local node->tet lists, and the halo tables. The parts
+// are independent: their lists are found in parallel, then each part fills
+// its own slices at offsets from prefix sums.
+int plan_partition(const fem_mesh* m, int n_parts, int node_cap, PartPlan& H) {
+  HostPhases hp;
+  const int Nn = (int)m->n_nodes, Nt = (int)m->n_tets;
+  int rc = cut_node_range(m, n_parts, node_cap, H.nb);
+  if (rc != FEM_OK) return rc;
+  hp.mark("cut");
+  const std::vector<int>& nb = H.nb;
+  const int* cp = m->csr_ptr.data();
+  const int* ce = m->csr_ent.data();
+  const int* tn = m->tets_new.data();
+  const int workers = host_workers(Nn, Nt);
+  struct Scratch {
+    std::vector<int> tet, node;   // -1 between parts
+  };
+  std::vector<Scratch> scr(workers);
+  auto scratch = [&](int w) -> Scratch& {
+    Scratch& S = scr[w];
+    if (S.tet.empty()) {
+      S.tet.assign(Nt, -1);
+      S.node.assign(Nn, -1);
+    }
+    return S;
+  };
+  std::vector<std::vector<int>> tl(n_parts), hl(n_parts);
+  std::atomic<int> too_many{-1};
+  parallel_items(n_parts, workers, [&](int p, int w) {
+    Scratch& S = scratch(w);
+    std::vector<int>& T = tl[p];
+    std::vector<int>& Hh = hl[p];
+    T.reserve(2 * (size_t)(cp[nb[p + 1]] - cp[nb[p]]) / 4 + 16);
+    for (int j = cp[nb[p]]; j < cp[nb[p + 1]]; ++j) {
+      const int t = ce[j] >> 2;
+      if (S.tet[t] == -2) continue;
+      S.tet[t] = -2;
+      T.push_back(t);
+    }
+    std::sort(T.begin(), T.end());
+    for (int i = nb[p]; i < nb[p + 1]; ++i) S.node[i] = -2;   // owned
+    for (int t : T)
       for (int a = 0; a < 4; ++a) {
-        const int g = m->tets_new[4 * t + a];
-        if (local_of_node[g] != -1) continue;   // owned, or a halo node already listed
-        local_of_node[g] = -2;
-        hl.push_back(g);
+        const int g = tn[4 * (size_t)t + a];
+        if (S.node[g] != -1) continue;   // owned, or a halo node already listed
+        S.node[g] = -2;
+        Hh.push_back(g);
       }
-    std::sort(hl.begin(), hl.end());
-    for (size_t j = 0; j < hl.size(); ++j) local_of_node[hl[j]] = n_own + (int)j;
-    const int n_loc = n_own + (int)hl.size();
-    if (n_loc >= 65535) return fail(FEM_ERR_TOO_LARGE, "part %d has %d local nodes (max 65534)", p, n_loc);
-    for (size_t k = 0; k < tl.size(); ++k) {
-      const int t = tl[k];
-      local_of_tet[t] = (int)k;
+    std::sort(Hh.begin(), Hh.end());
+    for (int t : T) S.tet[t] = -1;
+    for (int g : Hh) S.node[g] = -1;
+    for (int i = nb[p]; i < nb[p + 1]; ++i) S.node[i] = -1;
+    if ((nb[p + 1] - nb[p]) + (int)Hh.size() >= 65535) too_many.store(p);
+  });
+  hp.mark("lists");
+  if (too_many.load() >= 0) {
+    const int p = too_many.load();
+    return fail(FEM_ERR_TOO_LARGE, "part %d has %d local nodes (max 65534)", p,
+                (nb[p + 1] - nb[p]) + (int)hl[p].size());
+  }
+  H.tb.assign(n_parts + 1, 0);
+  H.hb.assign(n_parts + 1, 0);
+  H.max_own = H.max_loc = H.max_pt = H.max_lcsr = 0;
+  for (int p = 0; p < n_parts; ++p) {
+    const int n_own = nb[p + 1] - nb[p];
+    H.tb[p + 1] = H.tb[p] + (int)tl[p].size();
+    H.hb[p + 1] = H.hb[p] + (int)hl[p].size();
+    H.max_own = std::max(H.max_own, n_own);
+    H.max_loc = std::max(H.max_loc, n_own + (int)hl[p].size());
+    H.max_pt = std::max(H.max_pt, (int)tl[p].size());
+    H.max_lcsr = std::max(H.max_lcsr, cp[nb[p + 1]] - cp[nb[p]]);
+  }
+  const int total_pt = H.tb[n_parts];
+  H.total_pt = total_pt;
+  H.pt_nodes.resize(total_pt);
+  H.pt_dminv.resize((size_t)9 * total_pt);
+  H.pt_vol.resize(total_pt);
+  H.pt_info.resize(total_pt);
+  H.halo.resize(H.hb[n_parts]);
+  H.halo_src.resize(H.hb[n_parts]);
+  H.lcsr.resize((size_t)cp[Nn]);
+  // a node's local list has its global list's length, in node order
+  H.lcsr_ptr.assign(m->csr_ptr.begin(), m->csr_ptr.end());
+  parallel_items(n_parts, workers, [&](int p, int w) {
+    Scratch& S = scratch(w);
+    const int n_own = nb[p + 1] - nb[p];
+    const std::vector<int>& T = tl[p];
+    const std::vector<int>& Hh = hl[p];
+    for (int i = nb[p]; i < nb[p + 1]; ++i) S.node[i] = i - nb[p];
+    for (size_t j = 0; j < Hh.size(); ++j) S.node[Hh[j]] = n_own + (int)j;
+    const int e0 = H.tb[p];
+    for (size_t k = 0; k < T.size(); ++k) {
+      const int t = T[k], e = e0 + (int)k;
+      S.tet[t] = (int)k;
       int ln[4];
       int mn = Nn;
       for (int a = 0; a < 4; ++a) {
-        ln[a] = local_of_node[m->tets_new[4 * t + a]];
-        mn = std::min(mn, m->tets_new[4 * t + a]);
+        const int g = tn[4 * (size_t)t + a];
+        ln[a] = S.node[g];
+        mn = std::min(mn, g);
       }
-      pt_nodes.push_back(make_ushort4((unsigned short)ln[0], (unsigned short)ln[1], (unsigned short)ln[2],
-                                      (unsigned short)ln[3]));
-      for (int k9 = 0; k9 < 9; ++k9) pt_dminv_aos.push_back(m->dminv[9 * (size_t)t + k9]);
-      pt_vol.push_back(m->vol[t]);
-      const int owner = part_of[mn] == p ? 1 : 0;
-      pt_info.push_back(m->mat[t] | (owner << 16));
+      H.pt_nodes[e] = make_ushort4((unsigned short)ln[0], (unsigned short)ln[1], (unsigned short)ln[2],
+                                   (unsigned short)ln[3]);
+      for (int k9 = 0; k9 < 9; ++k9) H.pt_dminv[(size_t)k9 * total_pt + e] = m->dminv[9 * (size_t)t + k9];
+      H.pt_vol[e] = m->vol[t];
+      // a tet belongs to the part owning its smallest node
+      const int owner = (mn >= nb[p] && mn < nb[p + 1]) ? 1 : 0;
+      H.pt_info[e] = m->mat[t] | (owner << 16);
     }
-    for (int i = nb[p]; i < nb[p + 1]; ++i) {
-      lcsr_ptr[i] = (int)lcsr.size();
-      for (int j = m->csr_ptr[i]; j < m->csr_ptr[i + 1]; ++j) {
-        const int t = m->csr_ent[j] >> 2, corner = m->csr_ent[j] & 3;
-        lcsr.push_back(((unsigned)local_of_tet[t] << 2) | (unsigned)corner);
-      }
+    for (int i = nb[p]; i < nb[p + 1]; ++i)
+      for (int j = cp[i]; j < cp[i + 1]; ++j)
+        H.lcsr[j] = ((unsigned)S.tet[ce[j] >> 2] << 2) | (unsigned)(ce[j] & 3);
+    for (size_t j = 0; j < Hh.size(); ++j) {
+      const int g = Hh[j];
+      const int q = (int)(std::upper_bound(nb.begin(), nb.end(), g) - nb.begin()) - 1;
+      H.halo[H.hb[p] + j] = g;
+      H.halo_src[H.hb[p] + j] = ((unsigned)q << 16) | (unsigned)(g - nb[q]);
     }
-    for (int t : tl) local_of_tet[t] = -1;
-    for (int g : hl) local_of_node[g] = -1;
-    for (int i = nb[p]; i < nb[p + 1]; ++i) local_of_node[i] = -1;
-    for (int g : hl) {
-      const int q = part_of[g];
-      halo_src.push_back(((unsigned)q << 16) | (unsigned)(g - nb[q]));
-    }
-    halo.insert(halo.end(), hl.begin(), hl.end());
-    tb[p + 1] = (int)pt_nodes.size();
-    hb[p + 1] = (int)halo.size();
-    max_own = std::max(max_own, n_own);
-    max_loc = std::max(max_loc, n_loc);
-    max_pt = std::max(max_pt, (int)tl.size());
-  }
-  lcsr_ptr[Nn] = (int)lcsr.size();
-  hp.mark("parts");
-  const int total_pt = (int)pt_nodes.size();
-  std::vector<double> pt_dminv((size_t)9 * total_pt);
-  for (int e = 0; e < total_pt; ++e)
-    for (int k = 0; k < 9; ++k) pt_dminv[(size_t)k * total_pt + e] = pt_dminv_aos[(size_t)9 * e + k];
-  int max_lcsr = 0;
-  for (int p = 0; p < n_parts; ++p) max_lcsr = std::max(max_lcsr, lcsr_ptr[nb[p + 1]] - lcsr_ptr[nb[p]]);
+    for (int t : T) S.tet[t] = -1;
+    for (int g : Hh) S.node[g] = -1;
+    for (int i = nb[p]; i < nb[p + 1]; ++i) S.node[i] = -1;
+  });
+  hp.mark("fill");
+  hp.print("partition plan");
+  return FEM_OK;
+}
 
+// Host plan and device upload of a partition (one allocation, one copy).
+// Fills the partition fields of D (the mesh-wide fields are copied from
+// m->dev) and dims; the device block goes to o (freed first), its bytes to by.
+int build_partition(fem_mesh* m, int n_parts, int node_cap, MeshDev& D, PartDims& dims, std::vector<void*>& o,
+                    size_t& by) {
+  PartPlan H;
+  int rc = plan_partition(m, n_parts, node_cap, H);
+  if (rc != FEM_OK) return rc;
+  HostPhases hp;
   for (void* q : o) cudaFree(q);
   o.clear();
   m->bytes -= by;
   by = 0;
-  cudaStream_t s = m->stream;
-  int *d_nb, *d_tb, *d_hb, *d_halo, *d_info, *d_lcsr_ptr;
-  unsigned* d_hsrc;
-  ushort4* d_ptn;
-  double *d_dminv, *d_vol;
-  unsigned* d_lcsr;
-  CUDA_TRY(upload(&d_nb, nb, s, o, by), "upload");
-  CUDA_TRY(upload(&d_tb, tb, s, o, by), "upload");
-  CUDA_TRY(upload(&d_hb, hb, s, o, by), "upload");
-  CUDA_TRY(upload(&d_halo, halo, s, o, by), "upload");
-  CUDA_TRY(upload(&d_hsrc, halo_src, s, o, by), "upload");
-  CUDA_TRY(upload(&d_ptn, pt_nodes, s, o, by), "upload");
-  CUDA_TRY(upload(&d_dminv, pt_dminv, s, o, by), "upload");
-  CUDA_TRY(upload(&d_vol, pt_vol, s, o, by), "upload");
-  CUDA_TRY(upload(&d_info, pt_info, s, o, by), "upload");
-  CUDA_TRY(upload(&d_lcsr_ptr, lcsr_ptr, s, o, by), "upload");
-  CUDA_TRY(upload(&d_lcsr, lcsr, s, o, by), "upload");
-  m->bytes += by;
   D = m->dev;   // mesh-wide fields (sizes, X, masks, penalty, materials)
+  DeviceArena A;
+  A.upload(&D.part_node_begin, H.nb);
+  A.upload(&D.part_tet_begin, H.tb);
+  A.upload(&D.part_halo_begin, H.hb);
+  A.upload(&D.halo_nodes, H.halo);
+  A.upload(&D.halo_src, H.halo_src);
+  A.upload(&D.pt_nodes, H.pt_nodes);
+  A.upload(&D.pt_dminv, H.pt_dminv);
+  A.upload(&D.pt_vol, H.pt_vol);
+  A.upload(&D.pt_info, H.pt_info);
+  A.upload(&D.lcsr_ptr, H.lcsr_ptr);
+  A.upload(&D.lcsr, H.lcsr);
+  CUDA_TRY(A.commit(m->stream, o, by), "partition upload");
+  m->bytes += by;
   D.n_parts = n_parts;
-  D.total_pt = total_pt;
-  D.max_own = max_own;
-  D.max_loc = max_loc;
-  D.max_pt = max_pt;
-  D.max_lcsr = max_lcsr;
+  D.total_pt = H.total_pt;
+  D.max_own = H.max_own;
+  D.max_loc = H.max_loc;
+  D.max_pt = H.max_pt;
+  D.max_lcsr = H.max_lcsr;
   D.resident = 0;
-  D.part_node_begin = d_nb;
-  D.part_tet_begin = d_tb;
-  D.part_halo_begin = d_hb;
-  D.halo_nodes = d_halo;
-  D.halo_src = d_hsrc;
-  D.pt_nodes = d_ptn;
-  D.pt_dminv = d_dminv;
-  D.pt_vol = d_vol;
-  D.pt_info = d_info;
-  D.lcsr_ptr = d_lcsr_ptr;
-  D.lcsr = d_lcsr;
-  dims = PartDims{max_own, max_loc, max_pt, max_lcsr};
-  CUDA_TRY(cudaStreamSynchronize(s), "partition upload");
+  dims = PartDims{H.max_own, H.max_loc, H.max_pt, H.max_lcsr};
+  // the arena's staging buffer is released on return: the copy must be done
+  CUDA_TRY(cudaStreamSynchronize(m->stream), "partition upload");
   hp.mark("upload");
   hp.print("partition");
   return FEM_OK;
@@ -500,10 +622,12 @@ int build_partitions(fem_mesh* m, int n_parts) {
   unsigned long long* d_slot = nullptr;
   unsigned char* d_scr = nullptr;
   {
-    cudaError_t e = alloc(&d_tan, (size_t)kTanVec * D.total_pt, o, by);
-    if (e == cudaSuccess) e = alloc(&d_part, (size_t)2 * n_parts * kRed, o, by);
-    if (e == cudaSuccess) e = alloc(&d_slot, (size_t)12 * n_parts + 2, o, by);
-    if (e == cudaSuccess && L.gbytes > 0) e = alloc(&d_scr, (size_t)L.gbytes * n_parts, o, by);
+    DeviceArena ar;
+    ar.add(&d_tan, (size_t)kTanVec * D.total_pt);
+    ar.add(&d_part, (size_t)2 * n_parts * kRed);
+    ar.add(&d_slot, (size_t)12 * n_parts + 2);
+    if (L.gbytes > 0) ar.add(&d_scr, (size_t)L.gbytes * n_parts);
+    const cudaError_t e = ar.commit(m->stream, o, by);
     m->bytes += by - added;
     added = by;
     if (e != cudaSuccess) return drop(cuda_fail(e, "alloc partition workspace"));
@@ -629,14 +753,26 @@ void fem_destroy_mesh(fem_mesh* m) {
   delete m;
 }
 
-int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
-                    const int32_t* tet_material, const fem_material* materials, int32_t n_materials,
-                    const int32_t* fixed_nodes, int64_t n_fixed, const uint8_t* fixed_mask,
-                    void* cuda_stream, fem_mesh** out) {
-  g_err.clear();
+}  // extern "C"
+
+namespace {
+
+// Host arrays of a mesh that go to the device once (prepare_mesh).
+struct MeshHostArrays {
+  std::vector<double> X, kbase, lame, vol_lumped;
+  std::vector<int> mat_model;
+};
+
+// Host half of fem_create_mesh: validates the inputs, precomputes the per-tet
+// reference data (Dm^-1, V), renumbers nodes along a Morton curve and tets by
+// their smallest node, builds the node->tet lists, the boundary faces and
+// lumped nodal areas, the mean edge length and the penalty base per node.
+// Fills m's host fields and A; makes no CUDA call.
+int prepare_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
+                 const int32_t* tet_material, const fem_material* materials, int32_t n_materials,
+                 const int32_t* fixed_nodes, int64_t n_fixed, const uint8_t* fixed_mask, fem_mesh* m,
+                 MeshHostArrays& A) {
   HostPhases hp;
-  if (!out) return fail(FEM_ERR_ARG, "out is NULL");
-  *out = nullptr;
   if (!nodes || !tets || !materials) return fail(FEM_ERR_ARG, "nodes, tets and materials must be non-NULL");
   if (n_nodes < 4 || n_nodes > (1 << 30)) return fail(FEM_ERR_ARG, "n_nodes=%lld out of range", (long long)n_nodes);
   if (n_tets < 1 || n_tets > (1 << 28)) return fail(FEM_ERR_ARG, "n_tets=%lld out of range", (long long)n_tets);
@@ -708,25 +844,12 @@ int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, i
     vol_old[t] = V;
   }
   hp.mark("validate+Dm");
-  // ---------------------------------------------------------------- device
-  int device = 0;
-  {
-    cudaError_t e = cudaGetDevice(&device);
-    if (e != cudaSuccess) return cuda_fail(e, "no CUDA device");
-  }
-  fem_mesh* m = new fem_mesh();
-  m->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
-  m->device = device;
   m->n_nodes = n_nodes;
   m->n_tets = n_tets;
   m->n_fixed = n_fixed;
   m->fixed_nodes.assign(fixed_nodes, fixed_nodes + n_fixed);
   m->fixed_bits.resize(n_fixed);
   for (int64_t j = 0; j < n_fixed; ++j) m->fixed_bits[j] = fixed_mask ? fixed_mask[j] : 7;
-  auto bail = [&](int code) {
-    fem_destroy_mesh(m);
-    return code;
-  };
   // Morton renumbering of nodes
   double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
   for (int i = 0; i < Nn; ++i)
@@ -751,14 +874,20 @@ int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, i
     m->perm[i] = key[i].second;
     iperm[key[i].second] = i;
   }
-  // tets in new numbering, sorted by smallest node
-  std::vector<std::pair<int, int>> tkey(Nt);
-  for (int t = 0; t < Nt; ++t) {
-    int mn = Nn;
-    for (int a = 0; a < 4; ++a) mn = std::min(mn, iperm[tets[4 * t + a]]);
-    tkey[t] = {mn, t};
+  // tets in new numbering, ordered by smallest node and then by caller index
+  // (a counting sort: stable in t)
+  std::vector<int> tsorted(Nt);
+  {
+    std::vector<int> tmin(Nt), pos(Nn + 1, 0);
+    for (int t = 0; t < Nt; ++t) {
+      int mn = Nn;
+      for (int a = 0; a < 4; ++a) mn = std::min(mn, iperm[tets[4 * t + a]]);
+      tmin[t] = mn;
+      pos[mn + 1]++;
+    }
+    for (int i = 0; i < Nn; ++i) pos[i + 1] += pos[i];
+    for (int t = 0; t < Nt; ++t) tsorted[pos[tmin[t]]++] = t;
   }
-  std::sort(tkey.begin(), tkey.end());
   hp.mark("order");
   m->tets_new.resize(4 * (size_t)Nt);
   m->dminv.resize(9 * (size_t)Nt);
@@ -766,7 +895,7 @@ int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, i
   m->mat.resize(Nt);
   m->tet_perm.resize(Nt);
   for (int t = 0; t < Nt; ++t) {
-    const int to = tkey[t].second;
+    const int to = tsorted[t];
     m->tet_perm[t] = to;
     for (int a = 0; a < 4; ++a) m->tets_new[4 * (size_t)t + a] = iperm[tets[4 * to + a]];
     for (int k = 0; k < 9; ++k) m->dminv[9 * (size_t)t + k] = dminv_old[9 * (size_t)to + k];
@@ -784,6 +913,7 @@ int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, i
     for (int t = 0; t < Nt; ++t)
       for (int a = 0; a < 4; ++a) m->csr_ent[fill[m->tets_new[4 * (size_t)t + a]]++] = (t << 2) | a;
   }
+  hp.mark("csr");
   // X, mask in new order
   std::vector<double> X(3 * (size_t)Nn);
   m->node_mask.resize(Nn);
@@ -827,32 +957,41 @@ int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, i
           fkey[fill[a]++] = ((uint64_t)(unsigned)b << 32) | (uint64_t)(unsigned)c;
         }
     }
-    for (int a = 0; a < Nn; ++a) {
-      uint64_t* lo = fkey.data() + fptr[a];
-      uint64_t* hi = fkey.data() + fptr[a + 1];
-      std::sort(lo, hi);
-      for (uint64_t* q = lo; q < hi;) {
-        uint64_t* r = q + 1;
-        while (r < hi && *r == *q) ++r;
-        if (r - q == 1) {
-          const int b = (int)(*q >> 32), c = (int)(*q & 0xffffffffu);
-          const double* pa = &X[3 * (size_t)a];
-          const double* pb = &X[3 * (size_t)b];
-          const double* pc = &X[3 * (size_t)c];
-          const double e1[3] = {pb[0] - pa[0], pb[1] - pa[1], pb[2] - pa[2]};
-          const double e2[3] = {pc[0] - pa[0], pc[1] - pa[1], pc[2] - pa[2]};
-          const double cr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
-                                e1[0] * e2[1] - e1[1] * e2[0]};
-          const double A = 0.5 * std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
-          for (const int w : {a, b, c}) {
-            area[w] += A / 3.0;
-            on_boundary[w] = 1;
-          }
+    // buckets sorted and scanned in parallel over fixed node chunks; the
+    // boundary faces are then accumulated in node order
+    const int n_chunks = std::min(Nn, 64);
+    std::vector<std::vector<std::array<int, 3>>> bfaces(n_chunks);
+    parallel_items(n_chunks, host_workers(Nn, Nt), [&](int ch, int) {
+      const int a0 = (int)((int64_t)Nn * ch / n_chunks), a1 = (int)((int64_t)Nn * (ch + 1) / n_chunks);
+      for (int a = a0; a < a1; ++a) {
+        uint64_t* lo = fkey.data() + fptr[a];
+        uint64_t* hi = fkey.data() + fptr[a + 1];
+        std::sort(lo, hi);
+        for (uint64_t* q = lo; q < hi;) {
+          uint64_t* r = q + 1;
+          while (r < hi && *r == *q) ++r;
+          if (r - q == 1) bfaces[ch].push_back({a, (int)(*q >> 32), (int)(*q & 0xffffffffu)});
+          q = r;
         }
-        q = r;
       }
-    }
+    });
+    for (const auto& list : bfaces)
+      for (const auto& f : list) {
+        const double* pa = &X[3 * (size_t)f[0]];
+        const double* pb = &X[3 * (size_t)f[1]];
+        const double* pc = &X[3 * (size_t)f[2]];
+        const double e1[3] = {pb[0] - pa[0], pb[1] - pa[1], pb[2] - pa[2]};
+        const double e2[3] = {pc[0] - pa[0], pc[1] - pa[1], pc[2] - pa[2]};
+        const double cr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                              e1[0] * e2[1] - e1[1] * e2[0]};
+        const double A = 0.5 * std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+        for (const int w : f) {
+          area[w] += A / 3.0;
+          on_boundary[w] = 1;
+        }
+      }
   }
+  hp.mark("faces");
   double lsum = 0.0;
   size_t n_edges = 0;
   {
@@ -873,6 +1012,7 @@ int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, i
       }
   }
   m->h_bar = lsum / (double)n_edges;
+  hp.mark("edges");
   std::vector<double> Emax(Nn, 0.0);
   double Eglob = 0.0;
   for (int t = 0; t < Nt; ++t) {
@@ -900,61 +1040,88 @@ int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, i
     lame[2 * k + 1] = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
   }
   hp.mark("topology");
-  // uploads
-  cudaStream_t s = m->stream;
-  double *d_X, *d_kbase, *d_lame, *d_vl;
-  int* d_model;
-  unsigned char* d_mask;
-  {
-    cudaError_t e;
-    if ((e = upload(&d_X, X, s, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "upload X"));
-    if ((e = upload(&d_kbase, kbase, s, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "upload k"));
-    if ((e = upload(&d_lame, lame, s, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "upload lame"));
-    if ((e = upload(&d_vl, vol_lumped, s, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "upload mass"));
-    if ((e = upload(&d_model, mat_model, s, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "upload model"));
-    if ((e = upload(&d_mask, m->node_mask, s, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "upload mask"));
-    if ((e = upload(&m->d_perm, m->perm, s, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "upload perm"));
-    WorkDev& W = m->work;
-    if ((e = alloc(&W.u, 3 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
-    if ((e = alloc(&W.R, 3 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
-    if ((e = alloc(&W.uprev, 3 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
-    if ((e = alloc(&W.vel, 3 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
-    if ((e = alloc(&W.fric, 4 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
-    if ((e = alloc(&W.vpub, 6 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
-    if ((e = alloc(&W.dpub, (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
-    unsigned long long* d_bar;
-    if ((e = alloc(&d_bar, 2, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
-    W.barrier = d_bar;
-    W.abort_flag = reinterpret_cast<int*>(d_bar + 1);
-    if ((e = alloc(&W.out_R, 3 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
-    W.out_y = W.out_R;
-    if ((e = alloc(&W.out_fc, 3 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
-    double* d_inp;
-    if ((e = alloc(&d_inp, 3 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
-    W.in_p = d_inp;
-    if ((e = alloc(&m->d_stage, 3 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
-    if ((e = alloc(&W.step_force, 3 * (size_t)kMaxSteps, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
-    if ((e = alloc(&W.stats, 1, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
-    if ((e = alloc(&m->d_depths, (size_t)kMaxSteps, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
-    if ((e = alloc(&m->d_presc, 3 * (size_t)Nn, m->owned, m->bytes)) != cudaSuccess) return bail(cuda_fail(e, "alloc"));
-    if ((e = cudaMemsetAsync(W.u, 0, 3 * sizeof(double) * Nn, s)) != cudaSuccess) return bail(cuda_fail(e, "memset"));
-    if ((e = cudaMemsetAsync(W.vpub, 0, 6 * sizeof(unsigned long long) * Nn, s)) != cudaSuccess) return bail(cuda_fail(e, "memset"));
-    if ((e = cudaMemsetAsync(W.dpub, 0, sizeof(float4) * Nn, s)) != cudaSuccess) return bail(cuda_fail(e, "memset"));
-    W.u_presc = m->d_presc;
+  hp.print("prepare");
+  A.X = std::move(X);
+  A.kbase = std::move(kbase);
+  A.lame = std::move(lame);
+  A.vol_lumped = std::move(vol_lumped);
+  A.mat_model = std::move(mat_model);
+  return FEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
+                    const int32_t* tet_material, const fem_material* materials, int32_t n_materials,
+                    const int32_t* fixed_nodes, int64_t n_fixed, const uint8_t* fixed_mask,
+                    void* cuda_stream, fem_mesh** out) {
+  g_err.clear();
+  if (!out) return fail(FEM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  fem_mesh* m = new fem_mesh();
+  MeshHostArrays A;
+  int rc = prepare_mesh(nodes, n_nodes, tets, n_tets, tet_material, materials, n_materials, fixed_nodes, n_fixed,
+                        fixed_mask, m, A);
+  if (rc != FEM_OK) {
+    delete m;
+    return rc;
   }
+  HostPhases hp;
+  auto bail = [&](int code) {
+    fem_destroy_mesh(m);
+    return code;
+  };
+  {
+    cudaError_t e = cudaGetDevice(&m->device);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "no CUDA device"));
+  }
+  m->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  const size_t Nn = (size_t)n_nodes;
   MeshDev& D = m->dev;
-  D.n_nodes = Nn;
-  D.n_tets = Nt;
+  WorkDev& W = m->work;
+  unsigned long long* d_bar = nullptr;
+  double* d_inp = nullptr;
+  {
+    DeviceArena ar;
+    ar.upload(&D.X, A.X);
+    ar.upload(&D.kbase, A.kbase);
+    ar.upload(&D.lame, A.lame);
+    ar.upload(&D.vol_lumped, A.vol_lumped);
+    ar.upload(&D.mat_model, A.mat_model);
+    ar.upload(&D.fixmask, m->node_mask);
+    ar.upload(&m->d_perm, m->perm);
+    ar.add(&W.u, 3 * Nn, true);
+    ar.add(&W.R, 3 * Nn);
+    ar.add(&W.uprev, 3 * Nn);
+    ar.add(&W.vel, 3 * Nn);
+    ar.add(&W.fric, 4 * Nn);
+    ar.add(&W.vpub, 6 * Nn, true);
+    ar.add(&W.dpub, Nn, true);
+    ar.add(&d_bar, 2);
+    ar.add(&W.out_R, 3 * Nn);
+    ar.add(&W.out_fc, 3 * Nn);
+    ar.add(&d_inp, 3 * Nn);
+    ar.add(&m->d_stage, 3 * Nn);
+    ar.add(&W.step_force, 3 * (size_t)kMaxSteps);
+    ar.add(&W.stats, 1);
+    ar.add(&m->d_depths, (size_t)kMaxSteps);
+    ar.add(&m->d_presc, 3 * Nn);
+    cudaError_t e = ar.commit(m->stream, m->owned, m->bytes);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "mesh upload"));
+  }
+  W.barrier = d_bar;
+  W.abort_flag = reinterpret_cast<int*>(d_bar + 1);
+  W.out_y = W.out_R;
+  W.in_p = d_inp;
+  W.u_presc = m->d_presc;
+  D.n_nodes = (int)n_nodes;
+  D.n_tets = (int)n_tets;
   D.n_materials = n_materials;
   D.scale_floor = m->scale_floor;
-  D.X = d_X;
-  D.fixmask = d_mask;
-  D.kbase = d_kbase;
-  D.lame = d_lame;
-  D.vol_lumped = d_vl;
-  D.mat_model = d_model;
   hp.mark("upload");
-  int rc = build_partitions(m, default_parts(m));
+  rc = build_partitions(m, default_parts(m));
   if (rc != FEM_OK) return bail(rc);
   hp.mark("partition");
   hp.print("create");
@@ -1292,12 +1459,24 @@ int fem_element_stress(fem_mesh* m, const double* u, double* out_cauchy, double*
       t4[t] = make_int4(m->tets_new[4 * t], m->tets_new[4 * t + 1], m->tets_new[4 * t + 2], m->tets_new[4 * t + 3]);
       for (int k = 0; k < 9; ++k) dm[(size_t)k * Nt + t] = m->dminv[9 * t + k];
     }
-    CUDA_TRY(upload(&m->d_stress_tets, t4, s, m->owned, m->bytes), "upload");
-    CUDA_TRY(upload(&m->d_stress_dminv, dm, s, m->owned, m->bytes), "upload");
-    CUDA_TRY(upload(&m->d_stress_mat, m->mat, s, m->owned, m->bytes), "upload");
-    CUDA_TRY(upload(&m->d_tet_perm, m->tet_perm, s, m->owned, m->bytes), "upload");
-    CUDA_TRY(alloc(&m->d_stress_u, 3 * (size_t)m->n_nodes, m->owned, m->bytes), "alloc");
-    CUDA_TRY(alloc(&m->d_stress_out, 7 * Nt, m->owned, m->bytes), "alloc");
+    int4* d_t = nullptr;
+    double *d_dm = nullptr, *d_u = nullptr, *d_out = nullptr;
+    int *d_mat = nullptr, *d_tp = nullptr;
+    DeviceArena ar;
+    ar.upload(&d_t, t4);
+    ar.upload(&d_dm, dm);
+    ar.upload(&d_mat, m->mat);
+    ar.upload(&d_tp, m->tet_perm);
+    ar.add(&d_u, 3 * (size_t)m->n_nodes);
+    ar.add(&d_out, 7 * Nt);
+    CUDA_TRY(ar.commit(s, m->owned, m->bytes), "stress upload");
+    // published only once every array is in place
+    m->d_stress_tets = d_t;
+    m->d_stress_dminv = d_dm;
+    m->d_stress_mat = d_mat;
+    m->d_tet_perm = d_tp;
+    m->d_stress_u = d_u;
+    m->d_stress_out = d_out;
   }
   int rc = copy_in_nodes(m, u, m->d_stress_u);
   if (rc) return rc;
