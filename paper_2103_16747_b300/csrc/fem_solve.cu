@@ -720,10 +720,13 @@ __device__ bool load_halo_tagged(Ctx& C, const MeshDev& M, const WorkDev& W, int
 // Thread 0 stores the CTA's FP32-pair dot products (red_df[0..2]) and
 // arrives on the PCG counter with release semantics (the stores are visible
 // to whoever observes the arrival).
-__device__ void write_cg_slot(Ctx& C, const WorkDev& W, int ep) {
+// pub: the number of this publication (1, 2, ...). Consecutive publications
+// alternate between the two slot sets: a part writes publication k + 2 only
+// after every part has arrived at k + 1, that is, after every part has read k.
+__device__ void write_cg_slot(Ctx& C, const WorkDev& W, unsigned long long pub) {
   if (threadIdx.x == 0) {
     const float2* rd = C.st->red_df;
-    float4* dst = reinterpret_cast<float4*>(W.cgslot + ((size_t)(ep & 1) * C.nparts + C.part) * 6);
+    float4* dst = reinterpret_cast<float4*>(W.cgslot + ((size_t)(pub & 1) * C.nparts + C.part) * 6);
     dst[0] = make_float4(rd[0].x, rd[0].y, rd[1].x, rd[1].y);
     dst[1] = make_float4(rd[2].x, rd[2].y, 0.f, 0.f);
     unsigned long long* cnt = W.cgslot + (size_t)2 * C.nparts * 6;
@@ -740,8 +743,7 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
 // Thread 0 waits (bounded, acquire) until all parts arrived n_pub times; then
 // warp 0 sums the three values over the parts in a fixed order (identical in
 // every CTA) into red_df.
-__device__ bool reduce_cg_slots(Ctx& C, const WorkDev& W, int ep, unsigned long long n_pub,
-                                unsigned long long limit) {
+__device__ bool reduce_cg_slots(Ctx& C, const WorkDev& W, unsigned long long n_pub, unsigned long long limit) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int P = C.nparts;
   if (threadIdx.x == 0) {
@@ -758,7 +760,7 @@ __device__ bool reduce_cg_slots(Ctx& C, const WorkDev& W, int ep, unsigned long 
   __syncthreads();
   if (C.st->flag) return false;
   if (warp == 0) {
-    const float4* base = reinterpret_cast<const float4*>(W.cgslot + (size_t)(ep & 1) * P * 6);
+    const float4* base = reinterpret_cast<const float4*>(W.cgslot + (size_t)(n_pub & 1) * P * 6);
     constexpr int kMaxPer = 8;   // up to 256 CTAs, all loads in flight together
     float4 a4[kMaxPer], b4[kMaxPer];
 #pragma unroll
@@ -972,9 +974,9 @@ __device__ bool pcg(Ctx& C, const MeshDev& M, const WorkDev& W, const SolveParam
     if constexpr (CL) {
       reduce_cluster(C, ep);
     } else {
-      write_cg_slot(C, W, ep);
+      write_cg_slot(C, W, n_pub + 1);
       ++n_pub;
-      if (!reduce_cg_slots(C, W, ep, n_pub, P.timeout_ns)) return false;
+      if (!reduce_cg_slots(C, W, n_pub, P.timeout_ns)) return false;
     }
     tock(C, PH_CG_REDUCE, t);
     // scalars: every thread evaluates the same FP32 recurrences from the same
