@@ -149,7 +149,7 @@ class DeviceArena {
 
 // Host half of a partition (plan_partition): the cut and the per-part arrays.
 struct PartPlan {
-  std::vector<int> nb, tb, hb, halo, pt_info, lcsr_ptr;
+  std::vector<int> nb, tb, hb, ob, halo, pt_info, pt_tet, pt_own, lcsr_ptr;
   std::vector<unsigned> halo_src, lcsr;
   std::vector<ushort4> pt_nodes;
   std::vector<double> pt_dminv, pt_vol;   // pt_dminv: [9][total_pt]
@@ -335,6 +335,43 @@ int plan_partition(const fem_mesh* m, int n_parts, int node_cap, PartPlan& H) {
     return fail(FEM_ERR_TOO_LARGE, "part %d has %d local nodes (max 65534)", p,
                 (nb[p + 1] - nb[p]) + (int)hl[p].size());
   }
+  // tet owners (the evaluation pass computes each tet once, in its owner part,
+  // and the other parts holding it read its corner forces): a tet whose nodes
+  // all lie in one part belongs to that part; the others go, in a scattered
+  // order, to the least-loaded part among those owning one of their nodes
+  // (ties to the lower part id), which evens the owned counts out
+  std::vector<int> owner(Nt);
+  {
+    std::vector<int> part_of(Nn), load(n_parts, 0), shared;
+    for (int p = 0; p < n_parts; ++p)
+      for (int i = nb[p]; i < nb[p + 1]; ++i) part_of[i] = p;
+    for (int t = 0; t < Nt; ++t) {
+      const int q0 = part_of[tn[4 * (size_t)t]];
+      bool same = true;
+      for (int a = 1; a < 4; ++a) same = same && part_of[tn[4 * (size_t)t + a]] == q0;
+      if (same) {
+        owner[t] = q0;
+        ++load[q0];
+      } else {
+        shared.push_back(t);
+      }
+    }
+    // j -> j * k mod n permutes [0, n): k is a prime above any tet count
+    const uint64_t k = 2654435761ull, ns = shared.size();
+    for (uint64_t j = 0; j < ns; ++j) {
+      const int t = shared[(j * k) % ns];
+      int best = -1;
+      for (int a = 0; a < 4; ++a) {
+        const int q = part_of[tn[4 * (size_t)t + a]];
+        if (best < 0 || load[q] < load[best] || (load[q] == load[best] && q < best)) best = q;
+      }
+      owner[t] = best;
+      ++load[best];
+    }
+    H.ob.assign(n_parts + 1, 0);
+    for (int p = 0; p < n_parts; ++p) H.ob[p + 1] = H.ob[p] + load[p];
+    H.pt_own.resize(Nt);
+  }
   H.tb.assign(n_parts + 1, 0);
   H.hb.assign(n_parts + 1, 0);
   H.max_own = H.max_loc = H.max_pt = H.max_lcsr = 0;
@@ -353,6 +390,7 @@ int plan_partition(const fem_mesh* m, int n_parts, int node_cap, PartPlan& H) {
   H.pt_dminv.resize((size_t)9 * total_pt);
   H.pt_vol.resize(total_pt);
   H.pt_info.resize(total_pt);
+  H.pt_tet.resize(total_pt);
   H.halo.resize(H.hb[n_parts]);
   H.halo_src.resize(H.hb[n_parts]);
   H.lcsr.resize((size_t)cp[Nn]);
@@ -366,23 +404,20 @@ int plan_partition(const fem_mesh* m, int n_parts, int node_cap, PartPlan& H) {
     for (int i = nb[p]; i < nb[p + 1]; ++i) S.node[i] = i - nb[p];
     for (size_t j = 0; j < Hh.size(); ++j) S.node[Hh[j]] = n_own + (int)j;
     const int e0 = H.tb[p];
+    int n_mine = 0;
     for (size_t k = 0; k < T.size(); ++k) {
       const int t = T[k], e = e0 + (int)k;
       S.tet[t] = (int)k;
       int ln[4];
-      int mn = Nn;
-      for (int a = 0; a < 4; ++a) {
-        const int g = tn[4 * (size_t)t + a];
-        ln[a] = S.node[g];
-        mn = std::min(mn, g);
-      }
+      for (int a = 0; a < 4; ++a) ln[a] = S.node[tn[4 * (size_t)t + a]];
       H.pt_nodes[e] = make_ushort4((unsigned short)ln[0], (unsigned short)ln[1], (unsigned short)ln[2],
                                    (unsigned short)ln[3]);
       for (int k9 = 0; k9 < 9; ++k9) H.pt_dminv[(size_t)k9 * total_pt + e] = m->dminv[9 * (size_t)t + k9];
       H.pt_vol[e] = m->vol[t];
-      // a tet belongs to the part owning its smallest node
-      const int owner = (mn >= nb[p] && mn < nb[p + 1]) ? 1 : 0;
-      H.pt_info[e] = m->mat[t] | (owner << 16);
+      H.pt_tet[e] = t;
+      const int mine = owner[t] == p ? 1 : 0;
+      H.pt_info[e] = m->mat[t] | (mine << 16);
+      if (mine) H.pt_own[H.ob[p] + n_mine++] = (int)k;
     }
     for (int i = nb[p]; i < nb[p + 1]; ++i)
       for (int j = cp[i]; j < cp[i + 1]; ++j)
@@ -426,6 +461,9 @@ int build_partition(fem_mesh* m, int n_parts, int node_cap, MeshDev& D, PartDims
   A.upload(&D.pt_dminv, H.pt_dminv);
   A.upload(&D.pt_vol, H.pt_vol);
   A.upload(&D.pt_info, H.pt_info);
+  A.upload(&D.pt_tet, H.pt_tet);
+  A.upload(&D.part_own_begin, H.ob);
+  A.upload(&D.pt_own, H.pt_own);
   A.upload(&D.lcsr_ptr, H.lcsr_ptr);
   A.upload(&D.lcsr, H.lcsr);
   CUDA_TRY(A.commit(m->stream, o, by), "partition upload");
@@ -1097,6 +1135,7 @@ int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, i
     ar.add(&W.uprev, 3 * Nn);
     ar.add(&W.vel, 3 * Nn);
     ar.add(&W.fric, 4 * Nn);
+    ar.add(&W.tet_f, 12 * (size_t)n_tets);
     ar.add(&W.vpub, 6 * Nn, true);
     ar.add(&W.dpub, Nn, true);
     ar.add(&d_bar, 2);
@@ -1397,6 +1436,7 @@ int fem_eval_residual_noalloc(fem_mesh* m, const double* u, int32_t step, const 
   W.out_fc = reinterpret_cast<double*>(b + off_fc);
   W.R = W.out_R;
   W.tangent = m->work.tangent;   // not read by the evaluation
+  W.tet_f = m->work.tet_f;       // the mesh's own per-tet force scratch
   if (m->layout.gbytes > 0) {
     W.cta_scratch = b + off_cta;
     W.cta_stride = m->layout.gbytes;

@@ -325,6 +325,7 @@ int fem_batch_create(fem_mesh* const* meshes, const int32_t* n_steps, int32_t n,
     S.uprev = take(24 * max_nodes);
     S.vel = take(24 * max_nodes);
     S.fric = take(32 * max_nodes);
+    S.tet_f = take(96 * (size_t)max_tets);
     S.tangent = take(L.tan >= 0 ? 16 : 16 * (size_t)kTanVec * max_pt);
     S.cta = take((size_t)L.gbytes * max_parts);
     S.cta_stride = L.gbytes;

@@ -40,7 +40,11 @@ struct MeshDev {
   const ushort4* pt_nodes;          // [total_pt] local node ids of each part tet
   const double* pt_dminv;           // [9][total_pt] Dm^-1, row-major entries, SoA
   const double* pt_vol;             // [total_pt]
-  const int* pt_info;               // [total_pt] material | (energy-owner flag << 16)
+  const int* pt_info;               // [total_pt] material | (owner flag << 16)
+  const int* pt_tet;                // [total_pt] mesh tet id (ordered by smallest node) of each part tet
+  const int* part_own_begin;        // [P+1] part c evaluates its part tets pt_own[begin[c] .. begin[c+1])
+  const int* pt_own;                // [n_tets] local part-tet indices, ascending per part; every mesh tet
+                                    // is listed once, in one part holding it (its owner)
   const int* lcsr_ptr;              // [n_nodes+1] per owned node (global id)
   const unsigned* lcsr;             // (local part-tet index << 2) | corner, sorted
   const double* X;                  // [3*n_nodes]
@@ -73,6 +77,8 @@ struct WorkDev {
   double* uprev;                    // [3*n_nodes] converged displacement of the previous load step
   double* vel;                      // [3*n_nodes] velocity (dynamic stepping; null when quasi-static)
   double* fric;                     // [4*n_nodes] friction state of the load step: normal, normal force
+  double* tet_f;                    // [12][n_tets] corner forces of the last evaluation, written by the
+                                    // tet's owner part
   const double* u_presc;            // [3*n_nodes] prescribed values (or null)
   unsigned long long* vpub;         // [2][n_nodes][3] published PCG vector, (epoch, FP32) words
   float4* dpub;                     // [n_nodes] published Newton direction
@@ -155,7 +161,7 @@ struct SlotScratch {
   long long ctrl;                   // group engine: barrier counter, abort word, job word (u64 each)
   long long vpub, cgslot, partials; // group engine: as in WorkDev
   long long dpub, tangent, R, uprev, cta;   // offsets inside a slot
-  long long vel, fric;
+  long long vel, fric, tet_f;
   long long cta_stride;             // per-CTA bytes of the cta region
 };
 

@@ -450,7 +450,7 @@ int fem_server_create(fem_mesh* const* meshes, int32_t n_meshes, int32_t max_ste
   if (std::all_of(big.begin(), big.end(), [](char b) { return b != 0; })) big.assign(n_meshes, 0);
   std::vector<const MeshDev*> part(n_meshes);
   PartDims dims{0, 0, 0, 0};
-  size_t max_nodes = 0, max_pt = 0;
+  size_t max_nodes = 0, max_pt = 0, max_tets = 0;
   for (int i = 0; i < n_meshes; ++i) {
     if (big[i]) continue;
     const PartDims* pd = nullptr;
@@ -461,6 +461,7 @@ int fem_server_create(fem_mesh* const* meshes, int32_t n_meshes, int32_t max_ste
     dims.max_pt = std::max(dims.max_pt, pd->max_pt);
     dims.max_lcsr = std::max(dims.max_lcsr, pd->max_lcsr);
     max_nodes = std::max(max_nodes, (size_t)meshes[i]->n_nodes);
+    max_tets = std::max(max_tets, (size_t)meshes[i]->n_tets);
     max_pt = std::max(max_pt, (size_t)part[i]->total_pt);
   }
   int static_smem = 0, per_sm = 0;
@@ -552,6 +553,7 @@ int fem_server_create(fem_mesh* const* meshes, int32_t n_meshes, int32_t max_ste
     S.uprev = take(24 * max_nodes);
     S.vel = take(24 * max_nodes);
     S.fric = take(32 * max_nodes);
+    S.tet_f = take(96 * max_tets);
     S.tangent = take(L.tan >= 0 ? 16 : 16 * (size_t)kTanVec * max_pt);
     S.cta = take((size_t)L.gbytes * max_parts);
     S.cta_stride = L.gbytes;

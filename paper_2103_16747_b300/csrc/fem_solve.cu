@@ -403,6 +403,25 @@ __device__ __forceinline__ void friction_lag_node(Ctx& C, const SolveParams& P, 
   C.fric[4 * i + 3] = fn;
 }
 
+// FP64 corner forces, energy and det F of part tet t at the local positions ut.
+__device__ __forceinline__ void eval_part_tet(const Ctx& C, const MeshDev& M, int t, double f[4][3],
+                                              double& energy, double& J) {
+  const int e = C.t0 + t;
+  const ushort4 ln = C.ptn[t];
+  const int li[4] = {ln.x, ln.y, ln.z, ln.w};
+  double uu[4][3];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) uu[a][k] = C.ut[3 * li[a] + k];
+  double Dm[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Dm[k] = M.pt_dminv[(size_t)k * M.total_pt + e];
+  const int mat = M.pt_info[e] & 0xffff;
+  const double mu = M.lame[2 * mat], lam = M.lame[2 * mat + 1];
+  elem_eval_f64(uu, Dm, M.pt_vol[e], mu, lam, M.mat_model[mat], f, energy, J);
+}
+
 // FP64 energy, residual R = dPi/du and contact at ut = u + alpha*dx. Leaves
 // the owned residual in C.R (unmasked), contact forces in C.fc, the contact
 // Gauss-Newton vectors in C.hc, and the sums over all parts in red_out.
@@ -422,31 +441,40 @@ __device__ bool eval_pass(Ctx& C, const MeshDev& M, const WorkDev& W, const Solv
   if (!single) reset_cursors(C, 3);
   __syncthreads();
   double e_el = 0.0, bad = 0.0;
+  // Owner computes: each tet is evaluated once, by its owner (one of the
+  // parts holding it, chosen on the host to even the owned counts out). Its
+  // corner forces go to tet_f by mesh tet id (and straight into the staging
+  // chunk when the part is one chunk); after one sync of all parts every part
+  // stages the forces of its other tets from their owners. A part evaluating
+  // a halo tet itself would get the same values from the same inputs: the
+  // sums do not depend on the partition.
+  const int ob0 = M.part_own_begin[C.part];
+  const int n_ot = M.part_own_begin[C.part + 1] - ob0;
+  const size_t nT = (size_t)M.n_tets;
+  for (int j = threadIdx.x; j < n_ot; j += blockDim.x) {
+    const int t = M.pt_own[ob0 + j];
+    double f[4][3], energy, J;
+    eval_part_tet(C, M, t, f, energy, J);
+    if (!(J > 0.0) || !isfinite(energy)) bad += 1.0;
+    e_el += energy;
+    double* dst = W.tet_f + (size_t)M.pt_tet[C.t0 + t];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        dst[(3 * a + k) * nT] = f[a][k];
+        if (single) C.chunkd[(3 * a + k) * CH + t] = f[a][k];
+      }
+  }
+  __syncthreads();
+  if (!sync_parts<CL>(C, gb)) return false;
   for (int c0 = 0; c0 < C.n_pt; c0 += CH) {
     const int c1 = min(c0 + CH, C.n_pt);
     for (int t = c0 + threadIdx.x; t < c1; t += blockDim.x) {
-      const int e = C.t0 + t;
-      const ushort4 ln = C.ptn[t];
-      const int li[4] = {ln.x, ln.y, ln.z, ln.w};
-      double uu[4][3];
+      if (single && (M.pt_info[C.t0 + t] >> 16)) continue;   // owned: staged above
+      const double* src = W.tet_f + (size_t)M.pt_tet[C.t0 + t];
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) uu[a][k] = C.ut[3 * li[a] + k];
-      double Dm[9];
-#pragma unroll
-      for (int k = 0; k < 9; ++k) Dm[k] = M.pt_dminv[(size_t)k * M.total_pt + e];
-      const int info = M.pt_info[e];
-      const int mat = info & 0xffff;
-      const double mu = M.lame[2 * mat], lam = M.lame[2 * mat + 1];
-      double f[4][3], energy, J;
-      elem_eval_f64(uu, Dm, M.pt_vol[e], mu, lam, M.mat_model[mat], f, energy, J);
-      if (!(J > 0.0) || !isfinite(energy)) bad += 1.0;
-      if (info >> 16) e_el += energy;
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) C.chunkd[(3 * a + k) * CH + (t - c0)] = f[a][k];
+      for (int q = 0; q < 12; ++q) C.chunkd[q * CH + (t - c0)] = __ldcg(src + q * nT);
     }
     __syncthreads();
     gather_chunk<3, double>(C, CH, C.chunkd, c0, C.R, single);
@@ -1476,6 +1504,7 @@ __global__ void __launch_bounds__(kGroupBlock, 1) cluster_kernel(const BatchJob*
       w.uprev = reinterpret_cast<double*>(sb + S.uprev);
       w.vel = reinterpret_cast<double*>(sb + S.vel);
       w.fric = reinterpret_cast<double*>(sb + S.fric);
+      w.tet_f = reinterpret_cast<double*>(sb + S.tet_f);
       w.dpub = reinterpret_cast<float4*>(sb + S.dpub);
       w.tangent = reinterpret_cast<float4*>(sb + S.tangent);
       w.out_fc = J->out_fc;
@@ -1571,6 +1600,7 @@ __global__ void __launch_bounds__(kGroupBlock, 1) group_kernel(GroupRun R, SlotS
       w.uprev = reinterpret_cast<double*>(sb + S.uprev);
       w.vel = reinterpret_cast<double*>(sb + S.vel);
       w.fric = reinterpret_cast<double*>(sb + S.fric);
+      w.tet_f = reinterpret_cast<double*>(sb + S.tet_f);
       w.vpub = reinterpret_cast<unsigned long long*>(sb + S.vpub);
       w.dpub = reinterpret_cast<float4*>(sb + S.dpub);
       w.tangent = reinterpret_cast<float4*>(sb + S.tangent);
