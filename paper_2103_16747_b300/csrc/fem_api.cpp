@@ -18,6 +18,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <thread>
@@ -88,13 +89,30 @@ uint64_t spread_bits(uint64_t v) {
   return v;
 }
 
+// Pinned staging for host-to-device uploads, shared by every mesh of the
+// process and used under its mutex: allocated on first use, grown to the
+// largest upload up to kMaxPinnedStage (larger uploads stage through pageable
+// memory), and kept for the life of the process, so that creating a mesh does
+// not pay a page-locked allocation each time.
+constexpr size_t kMaxPinnedStage = (size_t)256 << 20;
+struct PinnedStage {
+  std::mutex mu;
+  unsigned char* buf = nullptr;
+  size_t cap = 0;
+};
+PinnedStage& pinned_stage() {
+  static PinnedStage* s = new PinnedStage();   // never destroyed: no teardown-order issue with the runtime
+  return *s;
+}
+
 // One device allocation for a set of arrays. add() records an array's length
 // and, optionally, host contents to upload or a zero fill; commit() allocates
 // the total once (each array 256-byte aligned, uploaded arrays first), points
 // every array into the block, copies all uploaded contents with one
-// host-to-device copy through a pageable staging buffer (the call returns once
-// the buffer is staged) and zero-fills the rest that asked for it. The block's
-// base pointer goes to `owned`, its size to `bytes`.
+// host-to-device copy through the pinned staging buffer (waiting for it, so the
+// buffer can be reused) or, for very large uploads, a pageable one, and
+// zero-fills the rest that asked for it. The block's base pointer goes to
+// `owned`, its size to `bytes`.
 class DeviceArena {
  public:
   template <typename P>
@@ -102,8 +120,8 @@ class DeviceArena {
     items_.push_back({reinterpret_cast<void**>(const_cast<std::remove_const_t<P>**>(dst)),
                       std::max<size_t>(count, 1) * sizeof(P), 0, nullptr, zero});
   }
-  template <typename P, typename T>
-  void upload(P** dst, const std::vector<T>& h) {
+  template <typename P, typename T, typename A>
+  void upload(P** dst, const std::vector<T, A>& h) {
     static_assert(std::is_same<std::remove_const_t<P>, T>::value, "pointer and vector types differ");
     items_.push_back({reinterpret_cast<void**>(const_cast<T**>(dst)), std::max<size_t>(h.size(), 1) * sizeof(T),
                       h.size() * sizeof(T), h.data(), false});
@@ -124,10 +142,31 @@ class DeviceArena {
     bytes += std::max<size_t>(off, 256);
     for (Item& it : items_) *it.dst = base + it.off;
     if (up_end > 0) {
-      std::vector<unsigned char> stage(up_end);
-      for (const Item& it : items_)
-        if (it.src && it.copy) std::memcpy(stage.data() + it.off, it.src, it.copy);
-      e = cudaMemcpyAsync(base, stage.data(), up_end, cudaMemcpyHostToDevice, s);
+      PinnedStage& P = pinned_stage();
+      std::lock_guard<std::mutex> lock(P.mu);
+      if (up_end <= kMaxPinnedStage && P.cap < up_end) {
+        if (P.buf) cudaFreeHost(P.buf);
+        P.buf = nullptr;
+        P.cap = 0;
+        const size_t want = std::min(kMaxPinnedStage, std::max(up_end + up_end / 2, (size_t)8 << 20));
+        if (cudaHostAlloc(reinterpret_cast<void**>(&P.buf), want, cudaHostAllocPortable) == cudaSuccess) {
+          P.cap = want;
+        } else {
+          P.buf = nullptr;
+          cudaGetLastError();   // no pinned buffer: stage through pageable memory
+        }
+      }
+      if (P.cap >= up_end) {
+        for (const Item& it : items_)
+          if (it.src && it.copy) std::memcpy(P.buf + it.off, it.src, it.copy);
+        e = cudaMemcpyAsync(base, P.buf, up_end, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      } else {
+        std::vector<unsigned char> stage(up_end);
+        for (const Item& it : items_)
+          if (it.src && it.copy) std::memcpy(stage.data() + it.off, it.src, it.copy);
+        e = cudaMemcpyAsync(base, stage.data(), up_end, cudaMemcpyHostToDevice, s);
+      }
       if (e != cudaSuccess) return e;
     }
     for (const Item& it : items_)
@@ -147,12 +186,37 @@ class DeviceArena {
   std::vector<Item> items_;
 };
 
+// An allocator that default-initialises: resize() leaves trivial elements
+// unwritten. The partition arrays are written in full by the parallel fill,
+// so zeroing them first would only add a serial pass over fresh pages.
+template <typename T>
+struct NoInit : std::allocator<T> {
+  template <typename U>
+  struct rebind {
+    using other = NoInit<U>;
+  };
+  NoInit() = default;
+  template <typename U>
+  NoInit(const NoInit<U>&) noexcept {}
+  template <typename U>
+  void construct(U* p) noexcept(std::is_nothrow_default_constructible<U>::value) {
+    ::new (static_cast<void*>(p)) U;
+  }
+  template <typename U, typename... A>
+  void construct(U* p, A&&... a) {
+    ::new (static_cast<void*>(p)) U(std::forward<A>(a)...);
+  }
+};
+template <typename T>
+using RawVec = std::vector<T, NoInit<T>>;
+
 // Host half of a partition (plan_partition): the cut and the per-part arrays.
 struct PartPlan {
-  std::vector<int> nb, tb, hb, ob, halo, pt_info, pt_tet, pt_own, lcsr_ptr;
-  std::vector<unsigned> halo_src, lcsr;
-  std::vector<ushort4> pt_nodes;
-  std::vector<double> pt_dminv, pt_vol;   // pt_dminv: [9][total_pt]
+  std::vector<int> nb, tb, hb, ob, lcsr_ptr;
+  RawVec<int> halo, pt_info, pt_tet, pt_own;
+  RawVec<unsigned> halo_src, lcsr;
+  RawVec<ushort4> pt_nodes;
+  RawVec<double> pt_dminv, pt_vol;   // pt_dminv: [9][total_pt]
   int total_pt = 0, max_own = 0, max_loc = 0, max_pt = 0, max_lcsr = 0;
 };
 
@@ -844,43 +908,58 @@ int prepare_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, int6
     if (bits > 7u) return fail(FEM_ERR_ARG, "fixed_mask[%lld]=%u (bits 0-2 only)", (long long)j, bits);
     mask_old[v] |= (unsigned char)bits;
   }
-  // reference shape matrices, volumes (caller order)
+  // reference shape matrices, volumes (caller order), on host threads over
+  // fixed tet chunks; the first degenerate tet in caller order is reported
   std::vector<double> dminv_old((size_t)9 * Nt), vol_old(Nt);
-  for (int t = 0; t < Nt; ++t) {
-    const double* x0 = nodes + 3 * (size_t)tets[4 * t];
-    double Dm[9];
-    double lmax = 0.0;
-    for (int c = 0; c < 3; ++c) {
-      const double* xc = nodes + 3 * (size_t)tets[4 * t + c + 1];
-      for (int i = 0; i < 3; ++i) Dm[3 * i + c] = xc[i] - x0[i];
-    }
-    for (int a = 0; a < 4; ++a)
-      for (int b = a + 1; b < 4; ++b) {
-        const double* xa = nodes + 3 * (size_t)tets[4 * t + a];
-        const double* xb = nodes + 3 * (size_t)tets[4 * t + b];
-        const double l = std::sqrt((xa[0] - xb[0]) * (xa[0] - xb[0]) + (xa[1] - xb[1]) * (xa[1] - xb[1]) +
-                                   (xa[2] - xb[2]) * (xa[2] - xb[2]));
-        lmax = std::max(lmax, l);
+  const int workers = host_workers(Nn, Nt);
+  const int n_tchunks = std::min(Nt, 64);
+  std::vector<int> bad_tet(n_tchunks, -1);
+  std::vector<double> bad_vol(n_tchunks, 0.0);
+  parallel_items(n_tchunks, workers, [&](int ch, int) {
+    const int ta = (int)((int64_t)Nt * ch / n_tchunks), tb = (int)((int64_t)Nt * (ch + 1) / n_tchunks);
+    for (int t = ta; t < tb; ++t) {
+      const double* x0 = nodes + 3 * (size_t)tets[4 * t];
+      double Dm[9];
+      double lmax = 0.0;
+      for (int c = 0; c < 3; ++c) {
+        const double* xc = nodes + 3 * (size_t)tets[4 * t + c + 1];
+        for (int i = 0; i < 3; ++i) Dm[3 * i + c] = xc[i] - x0[i];
       }
-    const double c00 = Dm[4] * Dm[8] - Dm[5] * Dm[7], c01 = Dm[5] * Dm[6] - Dm[3] * Dm[8],
-                 c02 = Dm[3] * Dm[7] - Dm[4] * Dm[6];
-    const double det = Dm[0] * c00 + Dm[1] * c01 + Dm[2] * c02;
-    const double V = det / 6.0;
-    if (!(V > 1e-12 * lmax * lmax * lmax))
-      return fail(FEM_ERR_DEGENERATE_TET, "tet %d has volume %.3e (%s)", t, V, V < 0 ? "inverted" : "degenerate");
-    const double id = 1.0 / det;
-    double* o = dminv_old.data() + 9 * (size_t)t;
-    o[0] = c00 * id;
-    o[1] = (Dm[2] * Dm[7] - Dm[1] * Dm[8]) * id;
-    o[2] = (Dm[1] * Dm[5] - Dm[2] * Dm[4]) * id;
-    o[3] = c01 * id;
-    o[4] = (Dm[0] * Dm[8] - Dm[2] * Dm[6]) * id;
-    o[5] = (Dm[2] * Dm[3] - Dm[0] * Dm[5]) * id;
-    o[6] = c02 * id;
-    o[7] = (Dm[1] * Dm[6] - Dm[0] * Dm[7]) * id;
-    o[8] = (Dm[0] * Dm[4] - Dm[1] * Dm[3]) * id;
-    vol_old[t] = V;
-  }
+      for (int a = 0; a < 4; ++a)
+        for (int b = a + 1; b < 4; ++b) {
+          const double* xa = nodes + 3 * (size_t)tets[4 * t + a];
+          const double* xb = nodes + 3 * (size_t)tets[4 * t + b];
+          const double l = std::sqrt((xa[0] - xb[0]) * (xa[0] - xb[0]) + (xa[1] - xb[1]) * (xa[1] - xb[1]) +
+                                     (xa[2] - xb[2]) * (xa[2] - xb[2]));
+          lmax = std::max(lmax, l);
+        }
+      const double c00 = Dm[4] * Dm[8] - Dm[5] * Dm[7], c01 = Dm[5] * Dm[6] - Dm[3] * Dm[8],
+                   c02 = Dm[3] * Dm[7] - Dm[4] * Dm[6];
+      const double det = Dm[0] * c00 + Dm[1] * c01 + Dm[2] * c02;
+      const double V = det / 6.0;
+      if (!(V > 1e-12 * lmax * lmax * lmax)) {
+        bad_tet[ch] = t;
+        bad_vol[ch] = V;
+        return;
+      }
+      const double id = 1.0 / det;
+      double* o = dminv_old.data() + 9 * (size_t)t;
+      o[0] = c00 * id;
+      o[1] = (Dm[2] * Dm[7] - Dm[1] * Dm[8]) * id;
+      o[2] = (Dm[1] * Dm[5] - Dm[2] * Dm[4]) * id;
+      o[3] = c01 * id;
+      o[4] = (Dm[0] * Dm[8] - Dm[2] * Dm[6]) * id;
+      o[5] = (Dm[2] * Dm[3] - Dm[0] * Dm[5]) * id;
+      o[6] = c02 * id;
+      o[7] = (Dm[1] * Dm[6] - Dm[0] * Dm[7]) * id;
+      o[8] = (Dm[0] * Dm[4] - Dm[1] * Dm[3]) * id;
+      vol_old[t] = V;
+    }
+  });
+  for (int ch = 0; ch < n_tchunks; ++ch)
+    if (bad_tet[ch] >= 0)
+      return fail(FEM_ERR_DEGENERATE_TET, "tet %d has volume %.3e (%s)", bad_tet[ch], bad_vol[ch],
+                  bad_vol[ch] < 0 ? "inverted" : "degenerate");
   hp.mark("validate+Dm");
   m->n_nodes = n_nodes;
   m->n_tets = n_tets;
@@ -932,14 +1011,17 @@ int prepare_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, int6
   m->vol.resize(Nt);
   m->mat.resize(Nt);
   m->tet_perm.resize(Nt);
-  for (int t = 0; t < Nt; ++t) {
-    const int to = tsorted[t];
-    m->tet_perm[t] = to;
-    for (int a = 0; a < 4; ++a) m->tets_new[4 * (size_t)t + a] = iperm[tets[4 * to + a]];
-    for (int k = 0; k < 9; ++k) m->dminv[9 * (size_t)t + k] = dminv_old[9 * (size_t)to + k];
-    m->vol[t] = vol_old[to];
-    m->mat[t] = tet_material ? tet_material[to] : 0;
-  }
+  parallel_items(n_tchunks, workers, [&](int ch, int) {
+    const int ta = (int)((int64_t)Nt * ch / n_tchunks), tb = (int)((int64_t)Nt * (ch + 1) / n_tchunks);
+    for (int t = ta; t < tb; ++t) {
+      const int to = tsorted[t];
+      m->tet_perm[t] = to;
+      for (int a = 0; a < 4; ++a) m->tets_new[4 * (size_t)t + a] = iperm[tets[4 * to + a]];
+      for (int k = 0; k < 9; ++k) m->dminv[9 * (size_t)t + k] = dminv_old[9 * (size_t)to + k];
+      m->vol[t] = vol_old[to];
+      m->mat[t] = tet_material ? tet_material[to] : 0;
+    }
+  });
   // node -> (tet, corner) CSR, ordered by tet
   m->csr_ptr.assign(Nn + 1, 0);
   for (int t = 0; t < Nt; ++t)
@@ -978,22 +1060,26 @@ int prepare_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, int6
       if (b > c) std::swap(b, c);
       if (a > b) std::swap(a, b);
     };
-    for (int t = 0; t < Nt; ++t)
-      for (int f = 0; f < 4; ++f) {
-        int a, b, c;
-        sorted3(t, f, a, b, c);
-        fptr[a + 1]++;
-      }
+    // each face's smallest vertex and the key of the other two, on host
+    // threads; then a counting scatter into buckets by smallest vertex
+    std::vector<int> fa(4 * (size_t)Nt);
+    std::vector<uint64_t> fk(4 * (size_t)Nt);
+    parallel_items(n_tchunks, workers, [&](int ch, int) {
+      const int ta = (int)((int64_t)Nt * ch / n_tchunks), tb = (int)((int64_t)Nt * (ch + 1) / n_tchunks);
+      for (int t = ta; t < tb; ++t)
+        for (int f = 0; f < 4; ++f) {
+          int a, b, c;
+          sorted3(t, f, a, b, c);
+          fa[4 * (size_t)t + f] = a;
+          fk[4 * (size_t)t + f] = ((uint64_t)(unsigned)b << 32) | (uint64_t)(unsigned)c;
+        }
+    });
+    for (size_t q = 0; q < fa.size(); ++q) fptr[fa[q] + 1]++;
     for (int i = 0; i < Nn; ++i) fptr[i + 1] += fptr[i];
     std::vector<uint64_t> fkey(4 * (size_t)Nt);
     {
       std::vector<int> fill(fptr.begin(), fptr.end() - 1);
-      for (int t = 0; t < Nt; ++t)
-        for (int f = 0; f < 4; ++f) {
-          int a, b, c;
-          sorted3(t, f, a, b, c);
-          fkey[fill[a]++] = ((uint64_t)(unsigned)b << 32) | (uint64_t)(unsigned)c;
-        }
+      for (size_t q = 0; q < fa.size(); ++q) fkey[fill[fa[q]]++] = fk[q];
     }
     // buckets sorted and scanned in parallel over fixed node chunks; the
     // boundary faces are then accumulated in node order
@@ -1030,24 +1116,36 @@ int prepare_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, int6
       }
   }
   hp.mark("faces");
+  // edge lengths over fixed node chunks on host threads (a stamp array per
+  // worker: the stamp is the node id), summed in node order afterwards
   double lsum = 0.0;
   size_t n_edges = 0;
   {
-    std::vector<int> stamp(Nn, -1);
-    for (int p = 0; p < Nn; ++p)
-      for (int j = m->csr_ptr[p]; j < m->csr_ptr[p + 1]; ++j) {
-        const int t = m->csr_ent[j] >> 2;
-        for (int k = 0; k < 4; ++k) {
-          const int q = m->tets_new[4 * (size_t)t + k];
-          if (q <= p || stamp[q] == p) continue;
-          stamp[q] = p;
-          const double* a = &X[3 * (size_t)p];
-          const double* b = &X[3 * (size_t)q];
-          lsum += std::sqrt((a[0] - b[0]) * (a[0] - b[0]) + (a[1] - b[1]) * (a[1] - b[1]) +
-                            (a[2] - b[2]) * (a[2] - b[2]));
-          ++n_edges;
+    const int n_chunks = std::min(Nn, 64);
+    std::vector<std::vector<double>> lens(n_chunks);
+    std::vector<std::vector<int>> stamps(workers);
+    parallel_items(n_chunks, workers, [&](int ch, int w) {
+      std::vector<int>& stamp = stamps[w];
+      if (stamp.empty()) stamp.assign(Nn, -1);
+      const int pa = (int)((int64_t)Nn * ch / n_chunks), pb = (int)((int64_t)Nn * (ch + 1) / n_chunks);
+      for (int p = pa; p < pb; ++p)
+        for (int j = m->csr_ptr[p]; j < m->csr_ptr[p + 1]; ++j) {
+          const int t = m->csr_ent[j] >> 2;
+          for (int k = 0; k < 4; ++k) {
+            const int q = m->tets_new[4 * (size_t)t + k];
+            if (q <= p || stamp[q] == p) continue;
+            stamp[q] = p;
+            const double* a = &X[3 * (size_t)p];
+            const double* b = &X[3 * (size_t)q];
+            lens[ch].push_back(std::sqrt((a[0] - b[0]) * (a[0] - b[0]) + (a[1] - b[1]) * (a[1] - b[1]) +
+                                         (a[2] - b[2]) * (a[2] - b[2])));
+          }
         }
-      }
+    });
+    for (const auto& l : lens) {
+      for (const double v : l) lsum += v;
+      n_edges += l.size();
+    }
   }
   m->h_bar = lsum / (double)n_edges;
   hp.mark("edges");
