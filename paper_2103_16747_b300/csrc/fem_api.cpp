@@ -20,6 +20,7 @@
 #include <cstring>
 #include <mutex>
 #include <numeric>
+#include <set>
 #include <string>
 #include <thread>
 #include <type_traits>
@@ -342,7 +343,7 @@ int cut_node_range(const fem_mesh* m, int n_parts, int node_cap, std::vector<int
 // the halo ascending), local node->tet lists, and the halo tables. The parts
 // are independent: their lists are found in parallel, then each part fills
 // its own slices at offsets from prefix sums.
-int plan_partition(const fem_mesh* m, int n_parts, int node_cap, PartPlan& H) {
+int plan_partition(const fem_mesh* m, int n_parts, int node_cap, PartPlan& H, int max_workers = 0) {
   HostPhases hp;
   const int Nn = (int)m->n_nodes, Nt = (int)m->n_tets;
   int rc = cut_node_range(m, n_parts, node_cap, H.nb);
@@ -352,7 +353,7 @@ int plan_partition(const fem_mesh* m, int n_parts, int node_cap, PartPlan& H) {
   const int* cp = m->csr_ptr.data();
   const int* ce = m->csr_ent.data();
   const int* tn = m->tets_new.data();
-  const int workers = host_workers(Nn, Nt);
+  const int workers = max_workers > 0 ? std::min(max_workers, host_workers(Nn, Nt)) : host_workers(Nn, Nt);
   struct Scratch {
     std::vector<int> tet, node;   // -1 between parts
   };
@@ -501,14 +502,11 @@ int plan_partition(const fem_mesh* m, int n_parts, int node_cap, PartPlan& H) {
   return FEM_OK;
 }
 
-// Host plan and device upload of a partition (one allocation, one copy).
-// Fills the partition fields of D (the mesh-wide fields are copied from
-// m->dev) and dims; the device block goes to o (freed first), its bytes to by.
-int build_partition(fem_mesh* m, int n_parts, int node_cap, MeshDev& D, PartDims& dims, std::vector<void*>& o,
-                    size_t& by) {
-  PartPlan H;
-  int rc = plan_partition(m, n_parts, node_cap, H);
-  if (rc != FEM_OK) return rc;
+// Device upload of a planned partition (one allocation, one copy). Fills the
+// partition fields of D (the mesh-wide fields are copied from m->dev) and
+// dims; the device block goes to o (freed first), its bytes to by.
+int upload_partition(fem_mesh* m, const PartPlan& H, int n_parts, MeshDev& D, PartDims& dims,
+                     std::vector<void*>& o, size_t& by) {
   HostPhases hp;
   for (void* q : o) cudaFree(q);
   o.clear();
@@ -545,6 +543,15 @@ int build_partition(fem_mesh* m, int n_parts, int node_cap, MeshDev& D, PartDims
   hp.mark("upload");
   hp.print("partition");
   return FEM_OK;
+}
+
+// Host plan and device upload of a partition.
+int build_partition(fem_mesh* m, int n_parts, int node_cap, MeshDev& D, PartDims& dims, std::vector<void*>& o,
+                    size_t& by) {
+  PartPlan H;
+  const int rc = plan_partition(m, n_parts, node_cap, H);
+  if (rc != FEM_OK) return rc;
+  return upload_partition(m, H, n_parts, D, dims, o, by);
 }
 
 }  // namespace
@@ -769,6 +776,52 @@ int batch_partition(fem_mesh* m, int parts, const MeshDev** dev, const PartDims*
   }
   *dev = &it->second.dev;
   *dims = &it->second.dims;
+  return FEM_OK;
+}
+
+
+// Plans the batch partitions of several solves at once, one mesh per host
+// thread, in waves of up to 16 (bounding the host memory of the plans), and
+// uploads each wave in order; pairs already cached or repeated in the list are
+// done once. batch_partition then finds them in the cache.
+int prefetch_batch_partitions(fem_mesh* const* meshes, const int* parts, int n) {
+  std::vector<std::pair<fem_mesh*, int>> todo;
+  {
+    std::set<std::pair<fem_mesh*, int>> seen;
+    for (int i = 0; i < n; ++i) {
+      if (!meshes[i] || meshes[i]->batch_parts.count(parts[i])) continue;
+      if (seen.insert({meshes[i], parts[i]}).second) todo.push_back({meshes[i], parts[i]});
+    }
+  }
+  if (todo.size() < 2) return FEM_OK;
+  const int wave = (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
+  for (size_t w0 = 0; w0 < todo.size(); w0 += wave) {
+    const int nw = (int)std::min<size_t>(wave, todo.size() - w0);
+    std::vector<PartPlan> plans(nw);
+    std::vector<int> rcs(nw, FEM_OK);
+    std::vector<std::string> errs(nw);
+    parallel_items(nw, nw, [&](int k, int) {
+      rcs[k] = plan_partition(todo[w0 + k].first, todo[w0 + k].second, kGroupBlock / 3, plans[k], 1);
+      if (rcs[k] != FEM_OK) errs[k] = last_error();   // the message is the worker thread's
+    });
+    for (int k = 0; k < nw; ++k)
+      if (rcs[k] != FEM_OK) {
+        last_error() = errs[k];
+        return rcs[k];
+      }
+    for (int k = 0; k < nw; ++k) {
+      fem_mesh* m = todo[w0 + k].first;
+      fem_mesh::BatchPart bp;
+      const int rc = upload_partition(m, plans[k], todo[w0 + k].second, bp.dev, bp.dims, bp.owned, bp.bytes);
+      if (rc != FEM_OK) {
+        for (void* q : bp.owned) cudaFree(q);
+        m->bytes -= bp.bytes;
+        return rc;
+      }
+      m->batch_parts.emplace(todo[w0 + k].second, std::move(bp));
+      plans[k] = PartPlan();   // release its host arrays early
+    }
+  }
   return FEM_OK;
 }
 

@@ -178,6 +178,8 @@ int fem_batch_create(fem_mesh* const* meshes, const int32_t* n_steps, int32_t n,
       return fail(FEM_ERR_ARG, "a mesh of %lld nodes cannot be cut into %d parts", (long long)meshes[i]->n_nodes,
                   job_parts[i]);
   // partitions (one per mesh and part count) and the layout covering them all
+  rc = prefetch_batch_partitions(meshes, job_parts.data(), n);
+  if (rc) return rc;
   std::vector<const MeshDev*> job_part(n);
   PartDims dims{0, 0, 0, 0};
   size_t max_nodes = 0, max_pt = 0;

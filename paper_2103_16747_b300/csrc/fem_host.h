@@ -84,6 +84,10 @@ bool common_options_valid(const fem_options& o);
 int smem_budget(const fem_mesh* m, int static_smem);
 // The mesh's partition into `parts` parts for batched solves (built on first use).
 int batch_partition(fem_mesh* m, int parts, const fem::MeshDev** dev, const fem::PartDims** dims);
+// Plans and uploads the batch partitions of n solves (meshes[i] cut into
+// parts[i]) on host threads, one mesh per thread; batch_partition then finds
+// them cached.
+int prefetch_batch_partitions(fem_mesh* const* meshes, const int* parts, int n);
 int validate_indenter(int shape, const double pose[12], const double* params, const double dir[3],
                       const double* depth_schedule, int32_t n_steps);
 

@@ -448,6 +448,17 @@ int fem_server_create(fem_mesh* const* meshes, int32_t n_meshes, int32_t max_ste
     big[i] = (int64_t)64 * T < meshes[i]->n_tets ? 1 : 0;
   }
   if (std::all_of(big.begin(), big.end(), [](char b) { return b != 0; })) big.assign(n_meshes, 0);
+  {
+    std::vector<fem_mesh*> small;
+    std::vector<int> small_parts;
+    for (int i = 0; i < n_meshes; ++i)
+      if (!big[i]) {
+        small.push_back(meshes[i]);
+        small_parts.push_back(parts[i]);
+      }
+    const int rc = prefetch_batch_partitions(small.data(), small_parts.data(), (int)small.size());
+    if (rc) return rc;
+  }
   std::vector<const MeshDev*> part(n_meshes);
   PartDims dims{0, 0, 0, 0};
   size_t max_nodes = 0, max_pt = 0, max_tets = 0;
