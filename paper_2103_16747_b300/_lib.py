@@ -44,7 +44,7 @@ PHASES = ("eval", "tangent", "pcg_init", "pcg_reduce", "pcg_matvec", "pcg_update
 EXPORTS = ("fem_default_options", "fem_create_mesh", "fem_set_indenter", "fem_set_dirichlet_values",
            "fem_solve", "fem_solve_batch", "fem_destroy_mesh", "fem_last_error", "fem_mesh_info_get", "fem_repartition",
            "fem_eval_residual", "fem_eval_residual_noalloc", "fem_apply_tangent",
-           "fem_debug_barrier_timeout", "fem_debug_reciprocals", "fem_batch_create", "fem_batch_run", "fem_batch_info_get",
+           "fem_debug_barrier_timeout", "fem_debug_reciprocals", "fem_debug_plan_check", "fem_batch_create", "fem_batch_run", "fem_batch_info_get",
            "fem_batch_destroy", "fem_batch_tune", "fem_server_create", "fem_server_start", "fem_server_submit",
            "fem_server_result", "fem_server_stop", "fem_server_info_get", "fem_server_destroy",
            "fem_element_stress")
@@ -135,6 +135,8 @@ def _load():
         "fem_apply_tangent": (C.c_int, [P, P, C.c_int32, C.POINTER(fem_options), P, P]),
         "fem_debug_barrier_timeout": (C.c_int, [C.c_double]),
         "fem_debug_reciprocals": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+        "fem_debug_plan_check": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                           C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p]),
         "fem_batch_create": (C.c_int, [P, P, C.c_int32, C.POINTER(fem_options), C.POINTER(P)]),
         "fem_batch_run": (C.c_int, [P, P, C.c_double, P, P, P]),
         "fem_batch_info_get": (C.c_int, [P, C.POINTER(fem_batch_info)]),
@@ -469,6 +471,28 @@ def fem_apply_tangent(mesh, u, step, p, out_y, opt=None):
 
 def fem_debug_barrier_timeout(timeout_s):
     return lib.fem_debug_barrier_timeout(float(timeout_s))
+
+
+def fem_debug_plan_check(nodes, tets, tet_material, materials, fixed_nodes, n_parts):
+    """Host-only check of mesh preparation and partitioning (no CUDA call): a
+    dict with the fields of fem_debug_plan_check's out[8]."""
+    keep = []
+    nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+    tets = np.ascontiguousarray(tets, dtype=np.int32)
+    mats = np.asarray(materials, dtype=np.float64)
+    mats = mats.reshape(-1, mats.shape[-1] if mats.ndim == 2 else 2)
+    model = mats[:, 2].astype(np.int32) if mats.shape[1] > 2 else np.zeros(len(mats), dtype=np.int32)
+    mat_arr = (fem_material * len(mats))(*[fem_material(float(e), float(n), int(md), 0)
+                                            for (e, n), md in zip(mats[:, :2], model)])
+    fixed = np.ascontiguousarray(fixed_nodes if fixed_nodes is not None else [], dtype=np.int32)
+    out = np.zeros(8, dtype=np.int64)
+    _check(lib.fem_debug_plan_check(_ptr(nodes, np.float64, keep), nodes.shape[0], _ptr(tets, np.int32, keep),
+                                    tets.shape[0], _ptr(tet_material, np.int32, keep), C.cast(mat_arr, C.c_void_p),
+                                    len(mats), _ptr(fixed, np.int32, keep) if len(fixed) else None, len(fixed),
+                                    int(n_parts), C.c_void_p(out.ctypes.data)))
+    keys = ("identical", "owners_valid", "max_owned", "min_owned", "max_part_tets", "workers", "max_owned_nodes",
+            "lists_ascending")
+    return dict(zip(keys, (int(v) for v in out)))
 
 
 def fem_debug_reciprocals(x):

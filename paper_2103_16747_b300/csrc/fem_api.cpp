@@ -1708,6 +1708,60 @@ int fem_debug_barrier_timeout(double timeout_s) {
   return FEM_OK;
 }
 
+int fem_debug_plan_check(const double* nodes, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
+                         const int32_t* tet_material, const fem_material* materials, int32_t n_materials,
+                         const int32_t* fixed_nodes, int64_t n_fixed, int32_t n_parts, int64_t out[8]) {
+  g_err.clear();
+  if (!out) return fail(FEM_ERR_ARG, "out is NULL");
+  fem_mesh m;
+  MeshHostArrays A;
+  int rc = prepare_mesh(nodes, n_nodes, tets, n_tets, tet_material, materials, n_materials, fixed_nodes, n_fixed,
+                        nullptr, &m, A);
+  if (rc != FEM_OK) return rc;
+  if (n_parts < 1 || n_parts > 256 || n_parts > n_nodes) return fail(FEM_ERR_ARG, "n_parts=%d out of range", n_parts);
+  PartPlan H, H1;
+  if ((rc = plan_partition(&m, n_parts, kSolveBlock / 3, H)) != FEM_OK) return rc;
+  if ((rc = plan_partition(&m, n_parts, kSolveBlock / 3, H1, 1)) != FEM_OK) return rc;
+  auto same = [](const auto& a, const auto& b) {
+    return a.size() == b.size() && (a.empty() || std::memcmp(a.data(), b.data(), a.size() * sizeof(a[0])) == 0);
+  };
+  out[0] = same(H.nb, H1.nb) && same(H.tb, H1.tb) && same(H.hb, H1.hb) && same(H.ob, H1.ob) && same(H.halo, H1.halo) &&
+           same(H.halo_src, H1.halo_src) && same(H.pt_nodes, H1.pt_nodes) && same(H.pt_dminv, H1.pt_dminv) &&
+           same(H.pt_vol, H1.pt_vol) && same(H.pt_info, H1.pt_info) && same(H.pt_tet, H1.pt_tet) &&
+           same(H.pt_own, H1.pt_own) && same(H.lcsr_ptr, H1.lcsr_ptr) && same(H.lcsr, H1.lcsr);
+  const int Nt = (int)n_tets;
+  bool valid = (int)H.pt_own.size() == Nt && H.ob[n_parts] == Nt;
+  bool ascending = true;
+  std::vector<int> seen(Nt, 0);
+  int64_t mx = 0, mn = INT64_MAX;
+  for (int p = 0; p < n_parts && valid; ++p) {
+    const int n_pt = H.tb[p + 1] - H.tb[p], c = H.ob[p + 1] - H.ob[p];
+    mx = std::max<int64_t>(mx, c);
+    mn = std::min<int64_t>(mn, c);
+    int flags = 0, prev = -1;
+    for (int e = H.tb[p]; e < H.tb[p + 1]; ++e) flags += (H.pt_info[e] >> 16) & 1;
+    valid = valid && flags == c;
+    for (int j = H.ob[p]; j < H.ob[p + 1] && valid; ++j) {
+      const int k = H.pt_own[j];
+      valid = k > prev && k < n_pt && ((H.pt_info[H.tb[p] + k] >> 16) & 1);
+      prev = k;
+      if (valid) ++seen[H.pt_tet[H.tb[p] + k]];
+    }
+    for (int i = H.nb[p]; i < H.nb[p + 1]; ++i)
+      for (int j = H.lcsr_ptr[i] + 1; j < H.lcsr_ptr[i + 1]; ++j)
+        ascending = ascending && (H.lcsr[j] >> 2) > (H.lcsr[j - 1] >> 2);
+  }
+  for (int t = 0; t < Nt && valid; ++t) valid = seen[t] == 1;
+  out[1] = valid ? 1 : 0;
+  out[2] = mx;
+  out[3] = mn == INT64_MAX ? 0 : mn;
+  out[4] = H.max_pt;
+  out[5] = host_workers(n_nodes, n_tets);
+  out[6] = H.max_own;
+  out[7] = ascending ? 1 : 0;
+  return FEM_OK;
+}
+
 int fem_debug_reciprocals(const double* x, int64_t n, double* out_rcp, double* out_rsqrt) {
   g_err.clear();
   if (!x || !out_rcp || n < 1 || n > (1 << 28)) return fail(FEM_ERR_ARG, "x, out_rcp and 1 <= n required");

@@ -104,3 +104,36 @@ def test_no_device_is_an_error_not_a_fallback():
     with pytest.raises(L.FemError) as ei:
         L.fem_create_mesh(m.nodes, m.tets, m.tet_material, m.materials, m.fixed_nodes)
     assert ei.value.code == L.FEM_ERR_CUDA
+
+
+@pytest.mark.parametrize("workload,n_parts", [("cube", 7), ("cube", 37), ("fingertip", 148), ("fingertip", 37),
+                                              ("fingertip", 1)])
+def test_host_plan_is_thread_independent_and_owners_are_balanced(workload, n_parts):
+    """Mesh preparation and partition plan on the host, without a GPU: the plan
+    on host threads equals the one-thread plan; every tet is evaluated by exactly
+    one part that holds it; owned counts stay within a few tets of the mean
+    (the owner of a tet is not simply the part of its smallest node); node->tet
+    lists are ascending in local tet index (the chunked gathers rely on it)."""
+    from paper_2103_16747_b300 import _lib as L
+    m = W.cube_mesh(8) if workload == "cube" else W.fingertip_sphere()[0]
+    r = L.fem_debug_plan_check(m.nodes, m.tets, m.tet_material, m.materials, m.fixed_nodes, n_parts)
+    assert r["identical"] == 1 and r["owners_valid"] == 1 and r["lists_ascending"] == 1
+    mean = len(m.tets) / n_parts
+    assert r["max_owned"] <= 1.05 * mean + 8
+    assert r["max_part_tets"] >= r["max_owned"]
+    if workload == "fingertip" and n_parts == 148:
+        # the single-solve kernel's gathers take one thread per owned node component
+        assert r["max_owned_nodes"] <= 256 // 3
+        # halo tets make a part's list well longer than its owned share
+        assert r["max_part_tets"] > 1.5 * r["max_owned"]
+
+
+def test_host_plan_check_reports_bad_input():
+    from paper_2103_16747_b300 import _lib as L
+    m = W.cube_mesh(2)
+    tets = m.tets.copy()
+    tets[0, [1, 2]] = tets[0, [2, 1]]   # inverted
+    with pytest.raises(RuntimeError):
+        L.fem_debug_plan_check(m.nodes, tets, m.tet_material, m.materials, m.fixed_nodes, 2)
+    with pytest.raises(RuntimeError):
+        L.fem_debug_plan_check(m.nodes, m.tets, m.tet_material, m.materials, m.fixed_nodes, 0)
