@@ -515,13 +515,13 @@ int fem_debug_reciprocals(const double* x, int64_t n, double* out_rcp, double* o
 /*
  * Host-only self-check of mesh preparation and partitioning (no CUDA call, so
  * it runs without a GPU): validates and prepares the mesh as fem_create_mesh
- * does, plans an n_parts partition for CTAs of the solve kernel, once on the
- * host threads and once on one thread, and fills out[8]:
+ * does, plans an n_parts partition for CTAs of the solve kernel, once on 8 host
+ * threads (whatever the mesh size) and once on one thread, and fills out[8]:
  *   out[0] 1 if the two plans are identical, out[1] 1 if the evaluation owner
  *   lists are valid (every tet listed exactly once, by a part holding it, with
  *   its owner flag set), out[2]/out[3] the largest/smallest owned tet count of
  *   a part, out[4] the largest part tet count (owned plus halo), out[5] the
- *   host threads used, out[6] the largest owned node count, out[7] 1 if every
+ *   host threads of the first plan (8), out[6] the largest owned node count, out[7] 1 if every
  *   part's local node->tet lists are ascending in local tet index within a
  *   node (the order the chunked gathers need).
  * Arguments as fem_create_mesh (fixed_mask may be NULL). Errors: those of

@@ -248,11 +248,12 @@ void parallel_items(int n, int workers, F&& f) {
   for (auto& t : th) t.join();
 }
 
-// Host threads for the per-part work of a mesh: none below ~20k tets (a
-// thread start costs about what a small mesh's whole pass does), at most 16,
-// and per-worker scratch (one int per node and per tet) kept under 256 MB.
+// Host threads for the per-tet and per-part work of a mesh: none below 100k
+// tets (measured on a shared GPU host, starting the threads cost as much as
+// the 39k-tet fingertip's passes save), at most 16, and per-worker scratch (one
+// int per node and per tet) kept under 256 MB.
 int host_workers(int64_t Nn, int64_t Nt) {
-  if (Nt < 20000) return 1;
+  if (Nt < 100000) return 1;
   const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
   const int64_t by_mem = std::max<int64_t>(1, (int64_t)(256 << 20) / (4 * (Nn + Nt)));
   return (int)std::min<int64_t>({(int64_t)hw, 16, by_mem});
@@ -343,6 +344,8 @@ int cut_node_range(const fem_mesh* m, int n_parts, int node_cap, std::vector<int
 // the halo ascending), local node->tet lists, and the halo tables. The parts
 // are independent: their lists are found in parallel, then each part fills
 // its own slices at offsets from prefix sums.
+// max_workers > 0: exactly that many host threads (at most 16), whatever the
+// mesh size; 0: host_workers().
 int plan_partition(const fem_mesh* m, int n_parts, int node_cap, PartPlan& H, int max_workers = 0) {
   HostPhases hp;
   const int Nn = (int)m->n_nodes, Nt = (int)m->n_tets;
@@ -353,7 +356,7 @@ int plan_partition(const fem_mesh* m, int n_parts, int node_cap, PartPlan& H, in
   const int* cp = m->csr_ptr.data();
   const int* ce = m->csr_ent.data();
   const int* tn = m->tets_new.data();
-  const int workers = max_workers > 0 ? std::min(max_workers, host_workers(Nn, Nt)) : host_workers(Nn, Nt);
+  const int workers = max_workers > 0 ? std::min(max_workers, 16) : host_workers(Nn, Nt);
   struct Scratch {
     std::vector<int> tet, node;   // -1 between parts
   };
@@ -1720,7 +1723,7 @@ int fem_debug_plan_check(const double* nodes, int64_t n_nodes, const int32_t* te
   if (rc != FEM_OK) return rc;
   if (n_parts < 1 || n_parts > 256 || n_parts > n_nodes) return fail(FEM_ERR_ARG, "n_parts=%d out of range", n_parts);
   PartPlan H, H1;
-  if ((rc = plan_partition(&m, n_parts, kSolveBlock / 3, H)) != FEM_OK) return rc;
+  if ((rc = plan_partition(&m, n_parts, kSolveBlock / 3, H, 8)) != FEM_OK) return rc;
   if ((rc = plan_partition(&m, n_parts, kSolveBlock / 3, H1, 1)) != FEM_OK) return rc;
   auto same = [](const auto& a, const auto& b) {
     return a.size() == b.size() && (a.empty() || std::memcmp(a.data(), b.data(), a.size() * sizeof(a[0])) == 0);
@@ -1756,7 +1759,7 @@ int fem_debug_plan_check(const double* nodes, int64_t n_nodes, const int32_t* te
   out[2] = mx;
   out[3] = mn == INT64_MAX ? 0 : mn;
   out[4] = H.max_pt;
-  out[5] = host_workers(n_nodes, n_tets);
+  out[5] = 8;
   out[6] = H.max_own;
   out[7] = ascending ? 1 : 0;
   return FEM_OK;
