@@ -147,13 +147,15 @@ def test_friction_passes_match_oracle(F, n_parts):
     assert np.array_equal(a["u"], b["u"]) and a["stats"].newton_iters == b["stats"].newton_iters
 
 
-def test_batch_friction_passes_match_oracle(F):
+@pytest.mark.parametrize("engine", [(1, 2), (2, 2)])
+def test_batch_friction_passes_match_oracle(F, engine):
+    """Friction passes in the CTA-group engine and in thread-block clusters."""
     mu, passes = 0.783, 4
     m, ind = _dragged_plane()
     ref = Problem(m, ind, mu_f=mu, friction_passes=passes).solve(tol=1e-10)
     h = F.fem_create_mesh(m.nodes, m.tets, m.tet_material, m.materials, m.fixed_nodes)
     opt = _opt(F, mu, passes)
-    opt.batch_engine, opt.batch_parts = 1, 2
+    opt.batch_engine, opt.batch_parts = engine
     out = [np.zeros((m.n_nodes, 3)) for _ in range(2)]
     frc = [np.zeros((ind.n_steps, 3)) for _ in range(2)]
     rc, st = F.fem_solve_batch([h, h], [ind, ind], 1e-6, opt, out, frc)

@@ -127,19 +127,23 @@ def test_server_whole_gpu_passes_for_large_meshes(F):
         F.fem_destroy_mesh(h)
 
 
-@pytest.mark.parametrize("physics", ["dynamic", "friction", "corotational"])
+@pytest.mark.parametrize("physics", ["dynamic", "friction", "friction_passes", "corotational"])
 def test_server_physics_options_match_oracle(F, physics):
     """The served path runs every physics option: dynamic stepping, Coulomb
-    friction and the co-rotational law, each against the FP64 oracle."""
+    friction (one and several passes per load step) and the co-rotational
+    law, each against the FP64 oracle."""
     m, ind = W.cube_sphere()
     opt = F.fem_default_options()
     kw = {}
     if physics == "dynamic":
         opt.dt, opt.density = 1e-3, 1.0
         kw = {"dt": 1e-3, "density": 1.0}
-    elif physics == "friction":
+    elif physics in ("friction", "friction_passes"):
         opt.mu_f = 0.783
         kw = {"mu_f": 0.783}
+        if physics == "friction_passes":
+            opt.friction_passes = 3
+            kw["friction_passes"] = 3
     else:
         m = W.with_model(m, 1)
     ref = Problem(m, ind, **kw).solve(tol=1e-10)
@@ -152,7 +156,7 @@ def test_server_physics_options_match_oracle(F, physics):
     rc, u, f, st, _ = srv.result(rid, m.n_nodes, ind.n_steps, wait_ms=60000)
     assert rc == F.FEM_OK
     assert np.linalg.norm(u - ref.u) / np.linalg.norm(ref.u) <= 1e-4
-    k0 = 1 if physics == "friction" else 0
+    k0 = 1 if physics.startswith("friction") else 0
     for k in range(k0, ind.n_steps):
         assert np.linalg.norm(f[k] - ref.step_force[k]) / np.linalg.norm(ref.step_force[k]) <= 1e-3
     assert srv.stop() == 0
