@@ -45,7 +45,7 @@ extern "C" {
 #define FEM_ERR_ARG            -1   /* bad pointer, size, index or option */
 #define FEM_ERR_DEGENERATE_TET -2   /* tet volume <= 1e-12 * (longest edge)^3, or inverted */
 #define FEM_ERR_NONFINITE      -3   /* NaN/Inf in an input or in the FP64 residual */
-#define FEM_ERR_OOM            -4   /* device allocation failed */
+#define FEM_ERR_OOM            -4   /* device or host allocation failed */
 #define FEM_ERR_NOT_CONVERGED  -5   /* a load step hit max_newton or the line search failed;
                                        outputs hold the last iterate, stats are filled */
 #define FEM_ERR_TIMEOUT        -6   /* a bounded device wait (grid barrier) expired */

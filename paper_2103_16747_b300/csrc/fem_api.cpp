@@ -18,6 +18,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <exception>
 #include <mutex>
 #include <numeric>
 #include <set>
@@ -230,11 +231,21 @@ namespace {
 // index, for per-worker scratch); the calling thread is worker 0. Items are
 // taken from a shared counter, so the assignment varies but every item runs
 // exactly once; if a thread cannot be started its items run on the others.
+// An exception thrown by f on any thread stops the remaining items and is
+// rethrown on the calling thread after every thread has joined.
 template <typename F>
 void parallel_items(int n, int workers, F&& f) {
   std::atomic<int> next{0};
+  std::exception_ptr err;
+  std::mutex err_mu;
   auto run = [&](int w) {
-    for (int p; (p = next.fetch_add(1, std::memory_order_relaxed)) < n;) f(p, w);
+    try {
+      for (int p; (p = next.fetch_add(1, std::memory_order_relaxed)) < n;) f(p, w);
+    } catch (...) {
+      std::lock_guard<std::mutex> lock(err_mu);
+      if (!err) err = std::current_exception();
+      next.store(n);
+    }
   };
   std::vector<std::thread> th;
   for (int w = 1; w < workers; ++w) {
@@ -246,6 +257,7 @@ void parallel_items(int n, int workers, F&& f) {
   }
   run(0);
   for (auto& t : th) t.join();
+  if (err) std::rethrow_exception(err);
 }
 
 // Host threads for the per-tet and per-part work of a mesh: none below 100k
@@ -1245,7 +1257,7 @@ int prepare_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, int6
 
 extern "C" {
 
-int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
+static int fem_create_mesh_body(const double* nodes, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
                     const int32_t* tet_material, const fem_material* materials, int32_t n_materials,
                     const int32_t* fixed_nodes, int64_t n_fixed, const uint8_t* fixed_mask,
                     void* cuda_stream, fem_mesh** out) {
@@ -1322,13 +1334,27 @@ int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, i
   return FEM_OK;
 }
 
-int fem_repartition(fem_mesh* m, int32_t n_parts) {
+int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
+                    const int32_t* tet_material, const fem_material* materials, int32_t n_materials,
+                    const int32_t* fixed_nodes, int64_t n_fixed, const uint8_t* fixed_mask,
+                    void* cuda_stream, fem_mesh** out) {
+  return guarded([&] {
+    return fem_create_mesh_body(nodes, n_nodes, tets, n_tets, tet_material, materials, n_materials, fixed_nodes,
+                                n_fixed, fixed_mask, cuda_stream, out);
+  });
+}
+
+static int fem_repartition_body(fem_mesh* m, int32_t n_parts) {
   if (!m) return fail(FEM_ERR_ARG, "mesh is NULL");
   if (n_parts < 1) return fail(FEM_ERR_ARG, "n_parts=%d", n_parts);
   return build_partitions(m, n_parts);
 }
 
-int fem_mesh_info_get(const fem_mesh* m, fem_mesh_info* info) {
+int fem_repartition(fem_mesh* m, int32_t n_parts) {
+  return guarded([&] { return fem_repartition_body(m, n_parts); });
+}
+
+static int fem_mesh_info_get_body(const fem_mesh* m, fem_mesh_info* info) {
   if (!m || !info) return fail(FEM_ERR_ARG, "NULL argument");
   info->n_nodes = m->n_nodes;
   info->n_tets = m->n_tets;
@@ -1346,8 +1372,12 @@ int fem_mesh_info_get(const fem_mesh* m, fem_mesh_info* info) {
   return FEM_OK;
 }
 
+int fem_mesh_info_get(const fem_mesh* m, fem_mesh_info* info) {
+  return guarded([&] { return fem_mesh_info_get_body(m, info); });
+}
 
-int fem_set_indenter(fem_mesh* m, int shape, const double pose[12], const double* params, const double dir[3],
+
+static int fem_set_indenter_body(fem_mesh* m, int shape, const double pose[12], const double* params, const double dir[3],
                      const double* depth_schedule, int32_t n_steps) {
   if (!m) return fail(FEM_ERR_ARG, "NULL argument");
   if (!pose || !depth_schedule) return fail(FEM_ERR_ARG, "NULL argument");
@@ -1373,7 +1403,12 @@ int fem_set_indenter(fem_mesh* m, int shape, const double pose[12], const double
   return FEM_OK;
 }
 
-int fem_set_dirichlet_values(fem_mesh* m, const double* values) {
+int fem_set_indenter(fem_mesh* m, int shape, const double pose[12], const double* params, const double dir[3],
+                     const double* depth_schedule, int32_t n_steps) {
+  return guarded([&] { return fem_set_indenter_body(m, shape, pose, params, dir, depth_schedule, n_steps); });
+}
+
+static int fem_set_dirichlet_values_body(fem_mesh* m, const double* values) {
   if (!m) return fail(FEM_ERR_ARG, "mesh is NULL");
   if (!values) {
     m->has_presc = false;
@@ -1395,6 +1430,10 @@ int fem_set_dirichlet_values(fem_mesh* m, const double* values) {
   CUDA_TRY(cudaStreamSynchronize(m->stream), "upload prescribed values");
   m->has_presc = true;
   return FEM_OK;
+}
+
+int fem_set_dirichlet_values(fem_mesh* m, const double* values) {
+  return guarded([&] { return fem_set_dirichlet_values_body(m, values); });
 }
 
 static int fill_params(fem_mesh* m, const fem_options* opt, int mode, int steps, int step, double tol,
@@ -1464,7 +1503,7 @@ static int copy_in_nodes(fem_mesh* m, const double* in, double* d_dst) {
   return FEM_OK;
 }
 
-int fem_solve(fem_mesh* m, int32_t load_steps, double tol, const fem_options* opt, double* out_disp,
+static int fem_solve_body(fem_mesh* m, int32_t load_steps, double tol, const fem_options* opt, double* out_disp,
               double* out_contact_force, double* out_nodal_contact, fem_stats* stats) {
   g_err.clear();
   if (!m) return fail(FEM_ERR_ARG, "mesh is NULL");
@@ -1524,7 +1563,14 @@ int fem_solve(fem_mesh* m, int32_t load_steps, double tol, const fem_options* op
   return code;
 }
 
-int fem_eval_residual(fem_mesh* m, const double* u, int32_t step, const fem_options* opt, double* out_R,
+int fem_solve(fem_mesh* m, int32_t load_steps, double tol, const fem_options* opt, double* out_disp,
+              double* out_contact_force, double* out_nodal_contact, fem_stats* stats) {
+  return guarded([&] {
+    return fem_solve_body(m, load_steps, tol, opt, out_disp, out_contact_force, out_nodal_contact, stats);
+  });
+}
+
+static int fem_eval_residual_body(fem_mesh* m, const double* u, int32_t step, const fem_options* opt, double* out_R,
                       double* out_fc, double* out_energy) {
   g_err.clear();
   if (!m || !u || !out_R) return fail(FEM_ERR_ARG, "NULL argument");
@@ -1549,11 +1595,16 @@ int fem_eval_residual(fem_mesh* m, const double* u, int32_t step, const fem_opti
   return FEM_OK;
 }
 
+int fem_eval_residual(fem_mesh* m, const double* u, int32_t step, const fem_options* opt, double* out_R,
+                      double* out_fc, double* out_energy) {
+  return guarded([&] { return fem_eval_residual_body(m, u, step, opt, out_R, out_fc, out_energy); });
+}
+
 // Same evaluation as fem_eval_residual, with every buffer the call needs
 // besides the mesh taken from the library's fixed device scratch block
 // (noalloc_scratch): no cudaMalloc, cudaFree or allocating call. The block is
 // shared by all calls in the process, so calls that overlap on the GPU race.
-int fem_eval_residual_noalloc(fem_mesh* m, const double* u, int32_t step, const fem_options* opt,
+static int fem_eval_residual_noalloc_body(fem_mesh* m, const double* u, int32_t step, const fem_options* opt,
                               double* out_R, double* out_fc, double* out_energy) {
   g_err.clear();
   if (!m || !u || !out_R) return fail(FEM_ERR_ARG, "NULL argument");
@@ -1623,7 +1674,12 @@ int fem_eval_residual_noalloc(fem_mesh* m, const double* u, int32_t step, const 
   return FEM_OK;
 }
 
-int fem_apply_tangent(fem_mesh* m, const double* u, int32_t step, const fem_options* opt, const double* p,
+int fem_eval_residual_noalloc(fem_mesh* m, const double* u, int32_t step, const fem_options* opt,
+                              double* out_R, double* out_fc, double* out_energy) {
+  return guarded([&] { return fem_eval_residual_noalloc_body(m, u, step, opt, out_R, out_fc, out_energy); });
+}
+
+static int fem_apply_tangent_body(fem_mesh* m, const double* u, int32_t step, const fem_options* opt, const double* p,
                       double* out_y) {
   g_err.clear();
   if (!m || !u || !p || !out_y) return fail(FEM_ERR_ARG, "NULL argument");
@@ -1641,7 +1697,12 @@ int fem_apply_tangent(fem_mesh* m, const double* u, int32_t step, const fem_opti
   return FEM_OK;
 }
 
-int fem_element_stress(fem_mesh* m, const double* u, double* out_cauchy, double* out_von_mises) {
+int fem_apply_tangent(fem_mesh* m, const double* u, int32_t step, const fem_options* opt, const double* p,
+                      double* out_y) {
+  return guarded([&] { return fem_apply_tangent_body(m, u, step, opt, p, out_y); });
+}
+
+static int fem_element_stress_body(fem_mesh* m, const double* u, double* out_cauchy, double* out_von_mises) {
   g_err.clear();
   if (!m || !u || !out_cauchy) return fail(FEM_ERR_ARG, "NULL argument");
   const size_t Nt = (size_t)m->n_tets;
@@ -1686,7 +1747,11 @@ int fem_element_stress(fem_mesh* m, const double* u, double* out_cauchy, double*
   return FEM_OK;
 }
 
-int fem_debug_barrier_timeout(double timeout_s) {
+int fem_element_stress(fem_mesh* m, const double* u, double* out_cauchy, double* out_von_mises) {
+  return guarded([&] { return fem_element_stress_body(m, u, out_cauchy, out_von_mises); });
+}
+
+static int fem_debug_barrier_timeout_body(double timeout_s) {
   g_err.clear();
   if (!(timeout_s > 0) || timeout_s > 10) return fail(FEM_ERR_ARG, "timeout_s must be in (0, 10]");
   unsigned long long* d = nullptr;
@@ -1711,7 +1776,11 @@ int fem_debug_barrier_timeout(double timeout_s) {
   return FEM_OK;
 }
 
-int fem_debug_plan_check(const double* nodes, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
+int fem_debug_barrier_timeout(double timeout_s) {
+  return guarded([&] { return fem_debug_barrier_timeout_body(timeout_s); });
+}
+
+static int fem_debug_plan_check_body(const double* nodes, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
                          const int32_t* tet_material, const fem_material* materials, int32_t n_materials,
                          const int32_t* fixed_nodes, int64_t n_fixed, int32_t n_parts, int64_t out[8]) {
   g_err.clear();
@@ -1765,7 +1834,16 @@ int fem_debug_plan_check(const double* nodes, int64_t n_nodes, const int32_t* te
   return FEM_OK;
 }
 
-int fem_debug_reciprocals(const double* x, int64_t n, double* out_rcp, double* out_rsqrt) {
+int fem_debug_plan_check(const double* nodes, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
+                         const int32_t* tet_material, const fem_material* materials, int32_t n_materials,
+                         const int32_t* fixed_nodes, int64_t n_fixed, int32_t n_parts, int64_t out[8]) {
+  return guarded([&] {
+    return fem_debug_plan_check_body(nodes, n_nodes, tets, n_tets, tet_material, materials, n_materials, fixed_nodes,
+                                     n_fixed, n_parts, out);
+  });
+}
+
+static int fem_debug_reciprocals_body(const double* x, int64_t n, double* out_rcp, double* out_rsqrt) {
   g_err.clear();
   if (!x || !out_rcp || n < 1 || n > (1 << 28)) return fail(FEM_ERR_ARG, "x, out_rcp and 1 <= n required");
   double* d = nullptr;
@@ -1780,6 +1858,10 @@ int fem_debug_reciprocals(const double* x, int64_t n, double* out_rcp, double* o
   cudaFree(d);
   if (e != cudaSuccess) return cuda_fail(e, "reciprocals");
   return FEM_OK;
+}
+
+int fem_debug_reciprocals(const double* x, int64_t n, double* out_rcp, double* out_rsqrt) {
+  return guarded([&] { return fem_debug_reciprocals_body(x, n, out_rcp, out_rsqrt); });
 }
 
 }  // extern "C"

@@ -125,7 +125,7 @@ cudaError_t enqueue(fem_batch* b) {
 
 extern "C" {
 
-int fem_batch_create(fem_mesh* const* meshes, const int32_t* n_steps, int32_t n, const fem_options* opt,
+static int fem_batch_create_body(fem_mesh* const* meshes, const int32_t* n_steps, int32_t n, const fem_options* opt,
                      fem_batch** out) {
   last_error().clear();
   if (!meshes || !n_steps || !out || n < 1) return fail(FEM_ERR_ARG, "meshes, n_steps, out and n >= 1 required");
@@ -453,7 +453,12 @@ int fem_batch_create(fem_mesh* const* meshes, const int32_t* n_steps, int32_t n,
   return FEM_OK;
 }
 
-int fem_batch_run(fem_batch* b, const fem_indenter* ind, double tol, double* const* out_disp,
+int fem_batch_create(fem_mesh* const* meshes, const int32_t* n_steps, int32_t n, const fem_options* opt,
+                     fem_batch** out) {
+  return guarded([&] { return fem_batch_create_body(meshes, n_steps, n, opt, out); });
+}
+
+static int fem_batch_run_body(fem_batch* b, const fem_indenter* ind, double tol, double* const* out_disp,
                   double* const* out_contact_force, fem_stats* stats) {
   last_error().clear();
   if (!b || !ind || !out_disp) return fail(FEM_ERR_ARG, "batch, indenters and out_disp required");
@@ -539,12 +544,17 @@ int fem_batch_run(fem_batch* b, const fem_indenter* ind, double tol, double* con
   return code;
 }
 
+int fem_batch_run(fem_batch* b, const fem_indenter* ind, double tol, double* const* out_disp,
+                  double* const* out_contact_force, fem_stats* stats) {
+  return guarded([&] { return fem_batch_run_body(b, ind, tol, out_disp, out_contact_force, stats); });
+}
+
 void fem_batch_destroy(fem_batch* b) {
   if (b) cudaStreamSynchronize(b->s);
   release(b);
 }
 
-int fem_batch_info_get(const fem_batch* b, fem_batch_info* info) {
+static int fem_batch_info_get_body(const fem_batch* b, fem_batch_info* info) {
   if (!b || !info) return fail(FEM_ERR_ARG, "NULL argument");
   info->engine = b->clusters ? FEM_BATCH_CLUSTERS : FEM_BATCH_GROUPS;
   info->parts = b->parts;
@@ -557,6 +567,10 @@ int fem_batch_info_get(const fem_batch* b, fem_batch_info* info) {
   return FEM_OK;
 }
 
+int fem_batch_info_get(const fem_batch* b, fem_batch_info* info) {
+  return guarded([&] { return fem_batch_info_get_body(b, info); });
+}
+
 // Autotuner of the slot shape. Each candidate is planned for the same jobs
 // truncated to their first proxy_steps load steps and timed on one run; the
 // candidate with the most solves per second wins. Candidates: CTA groups in
@@ -565,7 +579,7 @@ int fem_batch_info_get(const fem_batch* b, fem_batch_info* info) {
 // CTAs.
 // Candidates that do not fit the device, or need more parts than a mesh has
 // nodes, are skipped.
-int fem_batch_tune(fem_mesh* const* meshes, const fem_indenter* ind, int32_t n, double tol, const fem_options* opt,
+static int fem_batch_tune_body(fem_mesh* const* meshes, const fem_indenter* ind, int32_t n, double tol, const fem_options* opt,
                    int32_t proxy_steps, fem_options* out_opt, fem_tune_report* report) {
   last_error().clear();
   if (!meshes || !ind || !out_opt || n < 1) return fail(FEM_ERR_ARG, "meshes, indenters, out_opt and n >= 1 required");
@@ -645,7 +659,12 @@ int fem_batch_tune(fem_mesh* const* meshes, const fem_indenter* ind, int32_t n, 
   return FEM_OK;
 }
 
-int fem_solve_batch(fem_mesh* const* meshes, const fem_indenter* ind, int32_t n, double tol,
+int fem_batch_tune(fem_mesh* const* meshes, const fem_indenter* ind, int32_t n, double tol, const fem_options* opt,
+                   int32_t proxy_steps, fem_options* out_opt, fem_tune_report* report) {
+  return guarded([&] { return fem_batch_tune_body(meshes, ind, n, tol, opt, proxy_steps, out_opt, report); });
+}
+
+static int fem_solve_batch_body(fem_mesh* const* meshes, const fem_indenter* ind, int32_t n, double tol,
                     const fem_options* opt, double* const* out_disp, double* const* out_contact_force,
                     fem_stats* stats) {
   last_error().clear();
@@ -681,6 +700,12 @@ int fem_solve_batch(fem_mesh* const* meshes, const fem_indenter* ind, int32_t n,
   fem_batch_destroy(b);
   if (rc) last_error() = msg;
   return rc;
+}
+
+int fem_solve_batch(fem_mesh* const* meshes, const fem_indenter* ind, int32_t n, double tol,
+                    const fem_options* opt, double* const* out_disp, double* const* out_contact_force,
+                    fem_stats* stats) {
+  return guarded([&] { return fem_solve_batch_body(meshes, ind, n, tol, opt, out_disp, out_contact_force, stats); });
 }
 
 }  // extern "C"

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 
 #include <map>
+#include <new>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
@@ -93,6 +95,26 @@ int validate_indenter(int shape, const double pose[12], const double* params, co
 
 }  // namespace host
 }  // namespace fem
+
+// Exported entry points run their bodies through guarded(): no C++ exception
+// crosses the C ABI. A failed host allocation becomes FEM_ERR_OOM, any other
+// exception FEM_ERR_ARG with its message.
+template <typename F>
+int guarded(F&& f) noexcept {
+  try {
+    return f();
+  } catch (const std::bad_alloc&) {
+    return fem::host::fail(FEM_ERR_OOM, "host memory allocation failed");
+  } catch (const std::exception& e) {
+    try {
+      return fem::host::fail(FEM_ERR_ARG, "internal error: %s", e.what());
+    } catch (...) {
+      return FEM_ERR_ARG;
+    }
+  } catch (...) {
+    return FEM_ERR_ARG;
+  }
+}
 
 #define CUDA_TRY(call, what)                                            \
   do {                                                                  \

@@ -410,7 +410,7 @@ void dispatcher(fem_server* v) {
 
 extern "C" {
 
-int fem_server_create(fem_mesh* const* meshes, int32_t n_meshes, int32_t max_steps, const fem_options* opt,
+static int fem_server_create_body(fem_mesh* const* meshes, int32_t n_meshes, int32_t max_steps, const fem_options* opt,
                       int64_t result_bytes, fem_server** out) {
   last_error().clear();
   if (!meshes || n_meshes < 1 || !out || max_steps < 1 || max_steps > FEM_MAX_STEPS)
@@ -647,7 +647,12 @@ int fem_server_create(fem_mesh* const* meshes, int32_t n_meshes, int32_t max_ste
   return FEM_OK;
 }
 
-int fem_server_start(fem_server* v, double max_seconds) {
+int fem_server_create(fem_mesh* const* meshes, int32_t n_meshes, int32_t max_steps, const fem_options* opt,
+                      int64_t result_bytes, fem_server** out) {
+  return guarded([&] { return fem_server_create_body(meshes, n_meshes, max_steps, opt, result_bytes, out); });
+}
+
+static int fem_server_start_body(fem_server* v, double max_seconds) {
   last_error().clear();
   if (!v) return fail(FEM_ERR_ARG, "server is NULL");
   if (!(max_seconds > 0) || max_seconds > 3600) return fail(FEM_ERR_ARG, "max_seconds must be in (0, 3600]");
@@ -664,7 +669,11 @@ int fem_server_start(fem_server* v, double max_seconds) {
   return FEM_OK;
 }
 
-int fem_server_submit(fem_server* v, int32_t mesh, const fem_indenter* ind, double tol, int64_t* id) {
+int fem_server_start(fem_server* v, double max_seconds) {
+  return guarded([&] { return fem_server_start_body(v, max_seconds); });
+}
+
+static int fem_server_submit_body(fem_server* v, int32_t mesh, const fem_indenter* ind, double tol, int64_t* id) {
   last_error().clear();
   if (!v || !ind || !id) return fail(FEM_ERR_ARG, "NULL argument");
   if (mesh < 0 || mesh >= (int)v->meshes.size()) return fail(FEM_ERR_ARG, "mesh index %d out of range", mesh);
@@ -695,7 +704,11 @@ int fem_server_submit(fem_server* v, int32_t mesh, const fem_indenter* ind, doub
   return FEM_OK;
 }
 
-int fem_server_result(fem_server* v, int64_t id, int32_t wait_ms, double* out_disp, double* out_contact_force,
+int fem_server_submit(fem_server* v, int32_t mesh, const fem_indenter* ind, double tol, int64_t* id) {
+  return guarded([&] { return fem_server_submit_body(v, mesh, ind, tol, id); });
+}
+
+static int fem_server_result_body(fem_server* v, int64_t id, int32_t wait_ms, double* out_disp, double* out_contact_force,
                       fem_stats* stats, double* times) {
   last_error().clear();
   if (!v) return fail(FEM_ERR_ARG, "server is NULL");
@@ -723,7 +736,12 @@ int fem_server_result(fem_server* v, int64_t id, int32_t wait_ms, double* out_di
   return FEM_OK;
 }
 
-int fem_server_stop(fem_server* v) {
+int fem_server_result(fem_server* v, int64_t id, int32_t wait_ms, double* out_disp, double* out_contact_force,
+                      fem_stats* stats, double* times) {
+  return guarded([&] { return fem_server_result_body(v, id, wait_ms, out_disp, out_contact_force, stats, times); });
+}
+
+static int fem_server_stop_body(fem_server* v) {
   last_error().clear();
   if (!v) return fail(FEM_ERR_ARG, "server is NULL");
   {
@@ -772,7 +790,11 @@ int fem_server_stop(fem_server* v) {
   return FEM_OK;
 }
 
-int fem_server_info_get(const fem_server* v, fem_server_info* info) {
+int fem_server_stop(fem_server* v) {
+  return guarded([&] { return fem_server_stop_body(v); });
+}
+
+static int fem_server_info_get_body(const fem_server* v, fem_server_info* info) {
   if (!v || !info) return fail(FEM_ERR_ARG, "NULL argument");
   memset(info, 0, sizeof(*info));
   info->n_classes = (int32_t)v->class_parts.size();
@@ -787,6 +809,10 @@ int fem_server_info_get(const fem_server* v, fem_server_info* info) {
   info->rejected = v->rejected;
   info->workspace_bytes = (int64_t)v->ws_bytes;
   return FEM_OK;
+}
+
+int fem_server_info_get(const fem_server* v, fem_server_info* info) {
+  return guarded([&] { return fem_server_info_get_body(v, info); });
 }
 
 void fem_server_destroy(fem_server* v) {
