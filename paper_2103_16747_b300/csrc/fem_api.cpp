@@ -7,10 +7,12 @@
 // CTA of the solve kernel and uploads everything once. fem_solve then runs the
 // whole solve in one cooperative kernel launch and copies the outputs out.
 #include <cuda_runtime.h>
+#include <unistd.h>
 
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <condition_variable>
 #include <climits>
 #include <array>
 #include <cmath>
@@ -19,6 +21,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <exception>
+#include <functional>
 #include <mutex>
 #include <numeric>
 #include <set>
@@ -227,18 +230,93 @@ struct PartPlan {
 
 namespace {
 
+// Process-wide pool of host worker threads for parallel_items, started on
+// first use and reused, so that a parallel pass pays a wake-up rather than a
+// thread start. One job at a time: a caller that finds the pool busy (another
+// host thread's job, or a nested call) gets false and runs its items itself;
+// so does a forked child (the parent's threads do not exist there, and a lock
+// copied mid-operation could never be released). Never destroyed: its threads
+// wait on a condition variable until the process exits.
+class HostPool {
+ public:
+  static HostPool& get() {
+    static HostPool* pool = new HostPool();
+    return *pool;
+  }
+  // Runs fn(w) on `workers` - 1 pool threads (w = 1, 2, ...) and on the
+  // calling thread (w = 0); returns once every call has returned.
+  bool run(int workers, const std::function<void(int)>& fn) {
+    if (getpid() != pid_) return false;
+    std::unique_lock<std::mutex> job(job_mu_, std::try_to_lock);
+    if (!job.owns_lock()) return false;
+    while (n_threads_ < std::min(workers - 1, kMaxHelpers)) {
+      try {
+        std::thread([this, id = n_threads_ + 1] { loop(id); }).detach();
+      } catch (...) {
+        break;
+      }
+      ++n_threads_;
+    }
+    const int helpers = std::min(workers - 1, n_threads_);
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      fn_ = &fn;
+      helpers_ = helpers;
+      pending_ = helpers;
+      ++generation_;
+    }
+    cv_.notify_all();
+    fn(0);
+    std::unique_lock<std::mutex> lk(mu_);
+    done_cv_.wait(lk, [&] { return pending_ == 0; });
+    fn_ = nullptr;
+    return true;
+  }
+
+ private:
+  static constexpr int kMaxHelpers = 15;
+  HostPool() : pid_(getpid()) {}
+  void loop(int id) {
+    uint64_t seen = 0;
+    for (;;) {
+      const std::function<void(int)>* fn = nullptr;
+      {
+        std::unique_lock<std::mutex> lk(mu_);
+        cv_.wait(lk, [&] { return generation_ != seen; });
+        seen = generation_;
+        if (id > helpers_) continue;   // not one of this job's helpers
+        fn = fn_;
+      }
+      (*fn)(id);
+      std::lock_guard<std::mutex> lk(mu_);
+      if (--pending_ == 0) done_cv_.notify_one();
+    }
+  }
+  std::mutex job_mu_, mu_;
+  std::condition_variable cv_, done_cv_;
+  const std::function<void(int)>* fn_ = nullptr;
+  int n_threads_ = 0, helpers_ = 0, pending_ = 0;
+  uint64_t generation_ = 0;
+  const pid_t pid_;
+};
+
 // Runs f(p, w) for p in [0, n) on up to `workers` threads (w = the worker's
-// index, for per-worker scratch); the calling thread is worker 0. Items are
-// taken from a shared counter, so the assignment varies but every item runs
-// exactly once; if a thread cannot be started its items run on the others.
-// An exception thrown by f on any thread stops the remaining items and is
-// rethrown on the calling thread after every thread has joined.
+// index, for per-worker scratch); the calling thread is worker 0, the others
+// come from the host pool. Items are taken from a shared counter, so the
+// assignment varies but every item runs exactly once. An exception thrown by
+// f stops the remaining items and is rethrown on the calling thread once all
+// workers are done.
 template <typename F>
 void parallel_items(int n, int workers, F&& f) {
+  workers = std::min(workers, n);
+  if (workers <= 1) {
+    for (int p = 0; p < n; ++p) f(p, 0);
+    return;
+  }
   std::atomic<int> next{0};
   std::exception_ptr err;
   std::mutex err_mu;
-  auto run = [&](int w) {
+  const std::function<void(int)> run = [&](int w) {
     try {
       for (int p; (p = next.fetch_add(1, std::memory_order_relaxed)) < n;) f(p, w);
     } catch (...) {
@@ -247,25 +325,15 @@ void parallel_items(int n, int workers, F&& f) {
       next.store(n);
     }
   };
-  std::vector<std::thread> th;
-  for (int w = 1; w < workers; ++w) {
-    try {
-      th.emplace_back(run, w);
-    } catch (...) {
-      break;
-    }
-  }
-  run(0);
-  for (auto& t : th) t.join();
+  if (!HostPool::get().run(workers, run)) run(0);   // pool busy: all items here
   if (err) std::rethrow_exception(err);
 }
 
-// Host threads for the per-tet and per-part work of a mesh: none below 100k
-// tets (measured on a shared GPU host, starting the threads cost as much as
-// the 39k-tet fingertip's passes save), at most 16, and per-worker scratch (one
-// int per node and per tet) kept under 256 MB.
+// Host threads for the per-tet and per-part work of a mesh: none below 20k
+// tets (a pass there takes about what waking the pool does), at most 16, and
+// per-worker scratch (one int per node and per tet) kept under 256 MB.
 int host_workers(int64_t Nn, int64_t Nt) {
-  if (Nt < 100000) return 1;
+  if (Nt < 20000) return 1;
   const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
   const int64_t by_mem = std::max<int64_t>(1, (int64_t)(256 << 20) / (4 * (Nn + Nt)));
   return (int)std::min<int64_t>({(int64_t)hw, 16, by_mem});

@@ -137,3 +137,35 @@ def test_host_plan_check_reports_bad_input():
         L.fem_debug_plan_check(m.nodes, tets, m.tet_material, m.materials, m.fixed_nodes, 2)
     with pytest.raises(RuntimeError):
         L.fem_debug_plan_check(m.nodes, m.tets, m.tet_material, m.materials, m.fixed_nodes, 0)
+
+
+def test_host_plan_from_concurrent_threads_and_a_forked_child():
+    """The host worker pool serves one job at a time: concurrent callers (ctypes
+    releases the GIL) run their items on their own thread and still get the
+    same plan; a forked child runs without the parent's pool threads."""
+    import os
+    import threading
+    from paper_2103_16747_b300 import _lib as L
+    m = W.fingertip_sphere()[0]
+    args = (m.nodes, m.tets, m.tet_material, m.materials, m.fixed_nodes, 148)
+    ref = L.fem_debug_plan_check(*args)
+    out = [None] * 6
+
+    def work(k):
+        out[k] = [L.fem_debug_plan_check(*args) for _ in range(3)]
+    ts = [threading.Thread(target=work, args=(k,)) for k in range(6)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert all(r == ref for rs in out for r in rs)
+    if hasattr(os, "fork"):
+        import warnings
+        with warnings.catch_warnings():
+            warnings.simplefilter("ignore", DeprecationWarning)
+            pid = os.fork()
+        if pid == 0:
+            r = L.fem_debug_plan_check(*args)
+            os._exit(0 if r == ref else 1)
+        _, status = os.waitpid(pid, 0)
+        assert os.WIFEXITED(status) and os.WEXITSTATUS(status) == 0
