@@ -198,7 +198,10 @@ static int fem_batch_create_body(fem_mesh* const* meshes, const int32_t* n_steps
   int static_smem = 0;
   if (clusters) CUDA_TRY(cluster_kernel_attrs(max_parts, 0, &static_smem, nullptr), "cluster kernel attributes");
   else CUDA_TRY(group_kernel_attrs(0, &static_smem, nullptr), "group kernel attributes");
-  const SmemLayout L = plan_layout(dims, smem_budget(meshes[0], static_smem));
+  SmemLayout L = plan_layout(dims, smem_budget(meshes[0], static_smem));
+  // the batched engines store the tangent as FP16 with a per-tet scale: half
+  // the bytes each tangent product streams; the single path keeps FP32
+  L.tan16 = 1;
   if (L.total < 0)
     return fail(FEM_ERR_TOO_LARGE, "a part of %d owned / %d local nodes does not fit one CTA", dims.max_own,
                 dims.max_loc);

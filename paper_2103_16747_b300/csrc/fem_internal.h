@@ -128,6 +128,9 @@ struct SmemLayout {
   int acc, x, r, ucg, w, s, p, minv, hc, mask, cursor, ut, cd, mh2, hf;
   int tan, ptn, lptr, lcsr;                       // resident part data, or -1: read from global memory
   int chunk_tets;                                 // part tets per chunk of the evaluation passes
+  int tan16;                                      // 1: the tangent is stored as FP16 with a per-tet
+                                                  // scale (the batched engines, whatever the placement,
+                                                  // so a job's bits do not depend on the launch layout)
   int total;                                      // dynamic shared bytes
   int gbytes;                                     // global scratch bytes per CTA
 };

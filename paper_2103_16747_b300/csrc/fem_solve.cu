@@ -37,6 +37,8 @@
 
 #include <mutex>
 
+#include <cuda_fp16.h>
+
 #include "fem_internal.h"
 #include "fem_math.cuh"
 
@@ -146,6 +148,7 @@ struct Ctx {
   float4* lm;
   float4* tan;            // part tangent, element (g, t) at tan[g * tan_stride + t]
   int tan_stride;
+  bool tan16;             // tangent as FP16 with a per-tet scale: 4 words of 8 halves per tet
   const ushort4* ptn;     // part tet local node ids, index t
   const int* lptr;        // owned node i: entries lcsr[lptr[i] .. lptr[i+1])
   const unsigned* lcsr;   // (local tet << 2) | corner, sorted by local tet
@@ -576,9 +579,34 @@ __device__ void tangent_pass(Ctx& C, const MeshDev& M, int mode) {
       tangent_build(F, (float)M.lame[2 * mat], (float)M.lame[2 * mat + 1], (float)M.pt_vol[e], Dm,
                     mode, M.mat_model[mat], T, dg);
       T[30] = 0.f; T[31] = 0.f;
+      if (C.tan16) {
+        // FP16, each value over the tet's largest magnitude (so any stiffness
+        // fits), 8 halves per 16-byte word; the scale in the last word
+        float mx = 0.f;
 #pragma unroll
-      for (int g = 0; g < kTanVec; ++g)
-        C.tan[(size_t)g * C.tan_stride + t] = make_float4(T[4 * g], T[4 * g + 1], T[4 * g + 2], T[4 * g + 3]);
+        for (int k = 0; k < 30; ++k) mx = fmaxf(mx, fabsf(T[k]));
+        const float inv = mx > 0.f ? 1.f / mx : 0.f;
+        uint4* t16 = reinterpret_cast<uint4*>(C.tan);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          unsigned w[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int k = 8 * g + 2 * q;
+            if (k < 30) {
+              const __half2 h = __floats2half2_rn(T[k] * inv, T[k + 1] * inv);
+              w[q] = *reinterpret_cast<const unsigned*>(&h);
+            } else {
+              w[q] = __float_as_uint(mx);
+            }
+          }
+          t16[(size_t)g * C.tan_stride + t] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+      } else {
+#pragma unroll
+        for (int g = 0; g < kTanVec; ++g)
+          C.tan[(size_t)g * C.tan_stride + t] = make_float4(T[4 * g], T[4 * g + 1], T[4 * g + 2], T[4 * g + 3]);
+      }
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -625,10 +653,32 @@ __device__ void matvec_pass(Ctx& C, const MeshDev& M, long long* tp = nullptr) {
     for (int t = c0 + threadIdx.x; t < c1; t += blockDim.x) {
       const ushort4 ln = C.ptn[t];
       float T[32];
+      if (C.tan16) {
+        const uint4* t16 = reinterpret_cast<const uint4*>(C.tan);
+        uint4 v[4];
 #pragma unroll
-      for (int g = 0; g < kTanVec; ++g) {
-        const float4 v = C.tan[(size_t)g * C.tan_stride + t];
-        T[4 * g] = v.x; T[4 * g + 1] = v.y; T[4 * g + 2] = v.z; T[4 * g + 3] = v.w;
+        for (int g = 0; g < 4; ++g) v[g] = t16[(size_t)g * C.tan_stride + t];
+        const float sc = __uint_as_float(v[3].w);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          const unsigned w[4] = {v[g].x, v[g].y, v[g].z, v[g].w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int k = 8 * g + 2 * q;
+            if (k < 30) {
+              const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[q]));
+              T[k] = f.x * sc;
+              T[k + 1] = f.y * sc;
+            }
+          }
+        }
+        T[30] = 0.f; T[31] = 0.f;
+      } else {
+#pragma unroll
+        for (int g = 0; g < kTanVec; ++g) {
+          const float4 v = C.tan[(size_t)g * C.tan_stride + t];
+          T[4 * g] = v.x; T[4 * g + 1] = v.y; T[4 * g + 2] = v.z; T[4 * g + 3] = v.w;
+        }
       }
       float p[4][3];
       const int li[4] = {ln.x, ln.y, ln.z, ln.w};
@@ -1160,6 +1210,7 @@ __device__ void setup_ctx(Ctx& C, const MeshDev& M, const WorkDev& W, const Smem
     C.tan = W.tangent + C.t0;
     C.tan_stride = M.total_pt;
   }
+  C.tan16 = L.tan16 != 0;
   for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {

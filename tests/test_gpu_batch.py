@@ -58,6 +58,25 @@ def test_batch_cube_matches_oracle(F, engine):
 
 
 @pytest.mark.parametrize("engine", ENGINES)
+def test_batch_fp16_tangent_holds_for_any_stiffness(F, engine):
+    """The batched engines store the tangent in FP16 with a per-tet scale. The
+    penalty stiffness scales with E, so the displacements of the cube do not
+    depend on E: the cube at E = 1e9 (tangent entries far above FP16's range
+    unscaled) and at E = 1e3 must both match the oracle at E = 1e6."""
+    m6, ind = W.cube_sphere()
+    ref = Problem(m6, ind).solve(tol=1e-10)
+    for E in (1.0e3, 1.0e9):
+        m = W.cube_mesh(8, E=E, nu=0.3)
+        h = F.fem_create_mesh(m.nodes, m.tets, m.tet_material, m.materials, m.fixed_nodes)
+        rc, out, frc, st = _batch(F, [m], [h], [ind], engine=engine)
+        F.fem_destroy_mesh(h)
+        assert rc == 0 and st[0].residual <= 1e-6 * st[0].scale
+        assert rel(out[0], ref.u) <= 1e-4
+        # forces scale with E
+        assert rel(frc[0][-1] * (1.0e6 / E), ref.step_force[-1]) <= 1e-3
+
+
+@pytest.mark.parametrize("engine", ENGINES)
 def test_batch_fingertip_matches_golden_and_is_mix_independent(F, engine):
     g = np.load(os.path.join(HERE, "golden", "fingertip_sphere_oracle.npz"))
     m, ind = W.fingertip_sphere()
