@@ -107,7 +107,7 @@ def test_no_device_is_an_error_not_a_fallback():
 
 
 @pytest.mark.parametrize("workload,n_parts", [("cube", 7), ("cube", 37), ("fingertip", 148), ("fingertip", 37),
-                                              ("fingertip", 1)])
+                                              ("fingertip", 1), ("large", 148), ("large", 64)])
 def test_host_plan_is_thread_independent_and_owners_are_balanced(workload, n_parts):
     """Mesh preparation and partition plan on the host, without a GPU: the plan
     on host threads equals the one-thread plan; every tet is evaluated by exactly
@@ -115,7 +115,12 @@ def test_host_plan_is_thread_independent_and_owners_are_balanced(workload, n_par
     (the owner of a tet is not simply the part of its smallest node); node->tet
     lists are ascending in local tet index (the chunked gathers rely on it)."""
     from paper_2103_16747_b300 import _lib as L
-    m = W.cube_mesh(8) if workload == "cube" else W.fingertip_sphere()[0]
+    if workload == "cube":
+        m = W.cube_mesh(8)
+    elif workload == "fingertip":
+        m = W.fingertip_sphere()[0]
+    else:   # the largest fingertip of the uneven batch: R = 9 mm, about 204k tets
+        m = W.fingertip_mesh(R=9.0, h=W.fingertip_for_tets(2e5, 9.0))
     r = L.fem_debug_plan_check(m.nodes, m.tets, m.tet_material, m.materials, m.fixed_nodes, n_parts)
     assert r["identical"] == 1 and r["owners_valid"] == 1 and r["lists_ascending"] == 1
     mean = len(m.tets) / n_parts
