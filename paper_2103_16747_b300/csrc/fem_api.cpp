@@ -1264,6 +1264,7 @@ int prepare_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, int6
       std::vector<int>& stamp = stamps[w];
       if (stamp.empty()) stamp.assign(Nn, -1);
       const int pa = (int)((int64_t)Nn * ch / n_chunks), pb = (int)((int64_t)Nn * (ch + 1) / n_chunks);
+      lens[ch].reserve((size_t)8 * (pb - pa));   // about 7 edges per node start at it in a tet mesh
       for (int p = pa; p < pb; ++p)
         for (int j = m->csr_ptr[p]; j < m->csr_ptr[p + 1]; ++j) {
           const int t = m->csr_ent[j] >> 2;
