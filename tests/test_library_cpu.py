@@ -174,3 +174,36 @@ def test_host_plan_from_concurrent_threads_and_a_forked_child():
             os._exit(0 if r == ref else 1)
         _, status = os.waitpid(pid, 0)
         assert os.WIFEXITED(status) and os.WEXITSTATUS(status) == 0
+
+
+def test_ctypes_structures_match_the_c_header(tmp_path):
+    """Every structure the binding declares has the size and field offsets of
+    the C header's (a mismatch would hand the library shifted options). The
+    offsets come from a small C program compiled against include/fem.h."""
+    import shutil
+    import subprocess
+    from paper_2103_16747_b300 import _lib as L
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    here = os.path.dirname(os.path.abspath(__file__))
+    include = os.path.join(os.path.dirname(here), "include")
+    structs = [v for v in vars(L).values()
+               if isinstance(v, type) and issubclass(v, ctypes.Structure) and v.__name__.startswith("fem_")]
+    assert len(structs) >= 8
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "fem.h"', 'int main(void) {']
+    for st in structs:
+        lines.append(f'  printf("{st.__name__} sizeof %zu\\n", sizeof({st.__name__}));')
+        for name, _ in st._fields_:
+            lines.append(f'  printf("{st.__name__} {name} %zu\\n", offsetof({st.__name__}, {name}));')
+    lines += ['  return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", include, str(src), "-o", str(exe)], check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for st in structs:
+        assert got[(st.__name__, "sizeof")] == ctypes.sizeof(st), st.__name__
+        for name, _ in st._fields_:
+            assert got[(st.__name__, name)] == getattr(st, name).offset, (st.__name__, name)
