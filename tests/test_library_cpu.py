@@ -207,3 +207,22 @@ def test_ctypes_structures_match_the_c_header(tmp_path):
         assert got[(st.__name__, "sizeof")] == ctypes.sizeof(st), st.__name__
         for name, _ in st._fields_:
             assert got[(st.__name__, name)] == getattr(st, name).offset, (st.__name__, name)
+
+
+def test_binding_signatures_match_the_header():
+    """Each function the header declares is bound with as many arguments as it
+    takes and with its return kind (int status, void, or a C string)."""
+    import ctypes
+    from paper_2103_16747_b300 import _lib as L
+    here = os.path.dirname(os.path.abspath(__file__))
+    text = open(os.path.join(os.path.dirname(here), "include", "fem.h")).read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    decls = re.findall(r"^\s*(int|void|const char\s*\*)\s*(fem_\w+)\s*\(([^;]*?)\)\s*;", text, flags=re.M | re.S)
+    assert len(decls) >= 25
+    for ret, name, params in decls:
+        params = params.strip()
+        n = 0 if params in ("", "void") else params.count(",") + 1
+        f = getattr(L.lib, name)
+        assert len(f.argtypes) == n, (name, len(f.argtypes), n)
+        want = {"int": ctypes.c_int, "void": None}.get(ret.replace(" ", ""), ctypes.c_char_p)
+        assert f.restype == want, (name, f.restype, want)
