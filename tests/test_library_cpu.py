@@ -226,3 +226,27 @@ def test_binding_signatures_match_the_header():
         assert len(f.argtypes) == n, (name, len(f.argtypes), n)
         want = {"int": ctypes.c_int, "void": None}.get(ret.replace(" ", ""), ctypes.c_char_p)
         assert f.restype == want, (name, f.restype, want)
+
+
+def test_product_and_oracle_share_no_code():
+    """The CUDA path and the oracle are independent: no product module imports
+    the oracle, no oracle module imports the product, and the product's C/CUDA
+    sources include nothing from the oracle. Importing the product leaves the
+    oracle unloaded."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    pkg = os.path.join(root, "paper_2103_16747_b300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle\b|#include\s+\"[^\"]*oracle", text, re.M), f
+    for dirpath, _, files in os.walk(os.path.join(root, "oracle")):
+        for f in files:
+            if f.endswith(".py"):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(from|import)\s+paper_2103_16747_b300\b", text, re.M), f
+    code = "import sys, paper_2103_16747_b300; print(any(m == 'oracle' or m.startswith('oracle.') for m in sys.modules))"
+    out = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, check=True)
+    assert out.stdout.strip() == "False"
