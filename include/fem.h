@@ -123,13 +123,14 @@ typedef struct {
     double  friction_eps;     /* smoothing slip of f0, relative to the mesh's mean    */
                               /* edge length (default 0.01): below it a node sticks   */
                               /* elastically, above it it slides with force mu_f fn   */
-    int32_t friction_passes;  /* solves per load step with friction, 1..64 (default  */
-                              /* 1): after each converged solve the normal forces and */
-                              /* normals are frozen again at the current state, with  */
-                              /* the indenter at the step's own pose (the slip still  */
-                              /* counts from the step's start). The passes converge   */
-                              /* to friction that uses the step's own normal forces;  */
-                              /* newton_iters counts the iterations of all passes     */
+    int32_t friction_passes;  /* solves per load step with friction, 1..64          */
+                              /* (default 1). After each converged solve the normal   */
+                              /* forces and normals are frozen again at the current   */
+                              /* state, with the indenter at the step's own pose (the */
+                              /* slip still counts from the step's start). The passes */
+                              /* converge to friction that uses the step's own normal */
+                              /* forces; newton_iters counts the iterations of all    */
+                              /* passes                                                */
 } fem_options;
 
 /* engines of fem_solve_batch */

@@ -276,3 +276,23 @@ def test_bench_reference_line_keeps_the_contract():
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_documented_option_defaults_are_the_defaults():
+    """Every numeric "(default N)" in the header's fem_options comments is what
+    fem_default_options sets."""
+    from paper_2103_16747_b300 import _lib as L
+    here = os.path.dirname(os.path.abspath(__file__))
+    text = open(os.path.join(os.path.dirname(here), "include", "fem.h")).read()
+    body = text[:text.index("} fem_options;")]
+    body = body[body.rindex("typedef struct {"):]
+    fields = list(re.finditer(r"^\s*(?:double|int32_t|int64_t)\s+(\w+);", body, re.M))
+    o = L.fem_default_options()
+    checked = 0
+    for k, f in enumerate(fields):
+        end = fields[k + 1].start() if k + 1 < len(fields) else len(body)
+        m = re.search(r"default\s+(-?\d[\d.]*(?:e[-+]?\d+)?)", body[f.start():end])
+        if m:
+            assert getattr(o, f.group(1)) == pytest.approx(float(m.group(1)), rel=1e-12), f.group(1)
+            checked += 1
+    assert checked >= 12
