@@ -13,11 +13,16 @@ load steps):
   fingertip_sphere_friction_oracle.npz quasi-static with Coulomb friction
                                        mu_f = FRICTION_MU (the paper's calibrated
                                        coefficient)
+  fingertip_cylinder_oracle.npz        quasi-static, one cylinder draw of the
+                                       random-indentation workload (r 3.2 mm,
+                                       axis normal to the approach, 1.57 mm)
+  fingertip_box_edge_oracle.npz        quasi-static, one box-edge draw (20 mm
+                                       cube, faces at +-45 deg, 1.90 mm)
 
 Calls only ``oracle/`` and the seeded input generators; the GPU parity tests
 compare against the stored arrays because the full oracle solve takes minutes.
 Run from the repository root:
-    python tests/golden/make_golden.py [static|dynamic|corot|friction]
+    python tests/golden/make_golden.py [static|dynamic|corot|friction|cylinder|box]
 """
 import hashlib
 import os
@@ -57,6 +62,10 @@ def main(kind="static"):
     elif kind == "friction":
         r = Problem(mesh, ind, mu_f=FRICTION_MU).solve(tol=1e-10)
         name = "fingertip_sphere_friction_oracle.npz"
+    elif kind in ("cylinder", "box"):
+        mesh, ind = W.fingertip_shape_draw(W.CYLINDER if kind == "cylinder" else W.BOX)
+        r = Problem(mesh, ind).solve(tol=1e-10)
+        name = f"fingertip_{'cylinder' if kind == 'cylinder' else 'box_edge'}_oracle.npz"
     elif kind == "corot":
         mesh, ind = W.fingertip_calibrated()
         r = Problem(mesh, ind).solve(tol=1e-10)
@@ -73,5 +82,5 @@ def main(kind="static"):
 
 
 if __name__ == "__main__":
-    for k in (sys.argv[1:] or ["static", "dynamic", "corot", "friction"]):
+    for k in (sys.argv[1:] or ["static", "dynamic", "corot", "friction", "cylinder", "box"]):
         main(k)

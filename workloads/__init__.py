@@ -31,6 +31,7 @@ import math
 import numpy as np
 
 from .indenters import (BOX, CYLINDER, PLANE, SHAPE_NAMES, SPHERE, Indenter,  # noqa: F401
+                        cube_box_edge_indenter, cube_cylinder_indenter,
                         cube_sphere_indenter, draw_indentations, entry_times,
                         fingertip_sphere_indentation, linear_schedule,
                         place_at_contact, plane_indenter)
@@ -66,6 +67,33 @@ def fingertip_sphere(seed: int = SEED_BASE + 1):
     """The single-fingertip sphere indentation."""
     mesh = fingertip_mesh()
     return mesh, fingertip_sphere_indentation(mesh, seed=seed)
+
+
+def cube_cylinder():
+    """Unit cube with a cylinder pressed across the top face (axis normal to the
+    approach)."""
+    return cube_mesh(8), place_at_contact(cube_cylinder_indenter(), cube_mesh(8).nodes)
+
+
+def cube_box_edge():
+    """Unit cube with the edge of a box pressed into the top face (faces at
+    +-45 degrees to the approach)."""
+    return cube_mesh(8), place_at_contact(cube_box_edge_indenter(), cube_mesh(8).nodes)
+
+
+def fingertip_shape_draw(shape: int, seed: int = SEED_BASE + 5, min_depth: float = 1.5):
+    """The fingertip with the first random indentation (the draws of
+    ``fingertip_draws``, from ``seed``) of the given shape that goes at least
+    ``min_depth`` mm deep: a fixed cylinder or box-edge case of the random-draw
+    workload."""
+    mesh = fingertip_mesh()
+    rng = np.random.Generator(np.random.PCG64(seed))
+    for _ in range(1000):
+        from .indenters import draw_indentation
+        ind = draw_indentation(mesh, rng)
+        if ind.shape == shape and ind.depth_schedule[-1] >= min_depth:
+            return mesh, ind
+    raise RuntimeError("no draw of that shape")
 
 
 def fingertip_draws(n: int = 256, seed: int = SEED_BASE + 2, n_steps: int = 20):

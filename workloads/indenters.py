@@ -157,6 +157,38 @@ def cube_sphere_indenter(radius: float = 0.3, depth: float = 0.05, n_steps: int 
                     np.array([0.0, 0.0, -1.0]), linear_schedule(depth, n_steps))
 
 
+def cube_cylinder_indenter(radius: float = 0.3, depth: float = 0.05, n_steps: int = 10,
+                           yaw_deg: float = 20.0, offset: float = 0.03) -> Indenter:
+    """Infinite cylinder lying across the top face of the unit cube, axis
+    horizontal (perpendicular to the approach -z) and turned ``yaw_deg`` from the
+    x axis, line of contact shifted ``offset`` off the face centre; placed at
+    initial contact with the top face and pressed along -z."""
+    yaw = math.radians(yaw_deg)
+    axis = np.array([math.cos(yaw), math.sin(yaw), 0.0])
+    across = np.array([-math.sin(yaw), math.cos(yaw), 0.0])
+    c = np.array([0.5, 0.5, 1.0 + radius]) + offset * across
+    ind = Indenter(CYLINDER, c, _frame_from_axis(axis), np.array([radius, 0.0, 0.0]),
+                   np.array([0.0, 0.0, -1.0]), linear_schedule(depth, n_steps))
+    return ind
+
+
+def cube_box_edge_indenter(half: float = 0.3, depth: float = 0.05, n_steps: int = 10,
+                           yaw_deg: float = 15.0, offset: float = 0.03) -> Indenter:
+    """Cube of half extent ``half`` presenting one edge to the top face of the
+    unit cube: the edge is horizontal (turned ``yaw_deg`` from the x axis), the
+    two faces meeting there lie at +-45 degrees to the approach -z, and the edge
+    is shifted ``offset`` off the face centre. Nodes pressed under the edge fall
+    on both sides of the box's medial plane through the edge."""
+    yaw = math.radians(yaw_deg)
+    edge = np.array([math.cos(yaw), math.sin(yaw), 0.0])
+    a = np.array([0.0, 0.0, -1.0])
+    w = np.cross(a, edge)
+    rot = np.stack([(a + w) / math.sqrt(2.0), (a - w) / math.sqrt(2.0), edge], axis=1)
+    across = np.array([-math.sin(yaw), math.cos(yaw), 0.0])
+    centre = np.array([0.5, 0.5, 1.0 + half * math.sqrt(2.0)]) + offset * across
+    return Indenter(BOX, centre, rot, np.array([half, half, half]), a, linear_schedule(depth, n_steps))
+
+
 def plane_indenter(height: float, depth: float, n_steps: int) -> Indenter:
     """Rigid plane whose face sits at z=height, outward normal -z, pushed along -z."""
     R = np.array([[1.0, 0, 0], [0, -1.0, 0], [0, 0, -1.0]])   # third column = -z
