@@ -21,7 +21,7 @@ from __future__ import annotations
 import math
 
 import numpy as np
-from scipy.optimize import fsolve
+from scipy.optimize import brentq
 
 
 def lame(E, nu):
@@ -29,19 +29,37 @@ def lame(E, nu):
 
 
 def uniaxial_plane(delta, E, nu, h_bar, c_kappa):
-    """(lz, lt, P_zz) of the rollers + rigid plane problem at plate travel delta."""
+    """(lz, lt, P_zz) of the rollers + rigid plane problem at plate travel delta.
+
+    Two nested bracketed roots. For a given lz, the traction-free lateral faces
+    fix lt: mu (lt^2 - 1) + lam (2 ln lt + ln lz) = 0 (lt P_xx = 0), strictly
+    increasing in lt. The plate then fixes lz: lz - (1 - delta) + P_zz h_bar /
+    (c_kappa E) = 0, negative at lz = 1 - delta (compression) and equal to delta
+    at lz = 1 (no strain). Both equations' residuals are asserted."""
     mu, lam = lame(E, nu)
+    if delta == 0.0:
+        return 1.0, 1.0, 0.0
 
-    def eqs(v):
-        lz, lt = v
+    def lateral(lz):
+        return brentq(lambda lt: mu * (lt * lt - 1.0) + lam * (2.0 * math.log(lt) + math.log(lz)),
+                      1e-3, 10.0, xtol=1e-15, rtol=4 * np.finfo(float).eps, maxiter=500)
+
+    def pzz_of(lz):
+        lt = lateral(lz)
         lnJ = math.log(lt * lt * lz)
-        pxx = mu * (lt - 1 / lt) + lam * lnJ / lt
-        pzz = mu * (lz - 1 / lz) + lam * lnJ / lz
-        return [pxx / E, lz - (1 - delta) + pzz * h_bar / (c_kappa * E)]
+        return mu * (lz - 1 / lz) + lam * lnJ / lz
 
-    lz, lt = fsolve(eqs, [1 - delta, 1 + nu * delta], xtol=1e-14)
+    def plate(lz):
+        return lz - (1.0 - delta) + pzz_of(lz) * h_bar / (c_kappa * E)
+
+    lo, hi = (1.0 - delta, 1.0) if delta > 0 else (1.0, 1.0 - delta)
+    lz = brentq(plate, lo, hi, xtol=1e-15, rtol=4 * np.finfo(float).eps, maxiter=500)
+    lt = lateral(lz)
     lnJ = math.log(lt * lt * lz)
+    pxx = mu * (lt - 1 / lt) + lam * lnJ / lt
     pzz = mu * (lz - 1 / lz) + lam * lnJ / lz
+    assert abs(pxx) <= 1e-9 * E, pxx
+    assert abs(lz - (1.0 - delta) + pzz * h_bar / (c_kappa * E)) <= 1e-13, lz
     return float(lz), float(lt), float(pzz)
 
 
