@@ -131,6 +131,15 @@ typedef struct {
                               /* converge to friction that uses the step's own normal */
                               /* forces; newton_iters counts the iterations of all    */
                               /* passes                                                */
+    int32_t tangent_fp16;     /* stored element tangent of the batched engines and the*/
+                              /* request server: 0 = FP32, 30 floats per tet, as the  */
+                              /* single-solve path (default 0); 1 = FP16, each value  */
+                              /* over the tet's largest magnitude, with that scale in */
+                              /* FP32 (64 bytes per tet instead of 128: half the bytes */
+                              /* each tangent product streams; the tangent then      */
+                              /* carries ~5e-4 relative rounding, which changes the   */
+                              /* PCG path, not the FP64-residual stop). fem_solve and */
+                              /* the single-pass diagnostics always use FP32          */
 } fem_options;
 
 /* engines of fem_solve_batch */
@@ -471,15 +480,24 @@ int fem_eval_residual(fem_mesh* mesh, const double* u, int32_t step, const fem_o
  * allocate device memory once they are running: a real-time control loop with
  * a no-allocation rule after start-up, a host application that hands out all
  * device memory from its own pool, or a process already at its memory budget.
- *   - Limit: the block must hold 4 x 3 doubles per node plus per-part
- *     reduction slots, i.e. up to about 87,000 nodes; larger meshes return
- *     FEM_ERR_TOO_LARGE with the sizes in the message.
- *   - The first call on each device looks up the block's device address (with
- *     that device current) and caches it; make that first call before any
- *     stream capture.
+ *   - Limit: the block must hold 4 x 3 doubles per node, the per-part
+ *     reduction slots and, for meshes whose parts do not fit in shared memory,
+ *     the per-CTA arrays placed in global memory; about 87,000 nodes is the
+ *     upper bound (reached when the parts fit on chip), and the real limit
+ *     depends on the mesh's partition layout. Larger meshes return
+ *     FEM_ERR_TOO_LARGE with the sizes and the node limit for that layout in
+ *     the message.
+ *   - The call runs on the mesh's device (made current for the call, the
+ *     caller's current device restored afterwards). The first call on each
+ *     device looks up the block's device address (with that device current)
+ *     and caches it; make that first call before any stream capture.
  *   - All calls share the one block and each call overwrites it (the words that
  *     must start at zero are cleared at the start of every call). Calls that can
  *     overlap on the GPU (other streams, other host threads) race: serialise them.
+ *   - The call also reuses the mesh's own per-tet force scratch, the one that
+ *     fem_solve, fem_eval_residual and fem_apply_tangent use: it must not
+ *     overlap any of those on the same mesh from another host thread (calls on
+ *     the mesh's stream from one thread are ordered and safe).
  */
 int fem_eval_residual_noalloc(fem_mesh* mesh, const double* u, int32_t step, const fem_options* opt,
                               double* out_R, double* out_fc, double* out_energy);

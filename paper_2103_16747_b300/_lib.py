@@ -61,7 +61,8 @@ class fem_options(C.Structure):
                 ("barrier_timeout_s", C.c_double), ("batch_engine", C.c_int32), ("batch_parts", C.c_int32),
                 ("batch_tets_per_cta", C.c_int32), ("precond_degree", C.c_int32),
                 ("precond_ratio", C.c_double), ("dt", C.c_double), ("density", C.c_double),
-                ("mu_f", C.c_double), ("friction_eps", C.c_double), ("friction_passes", C.c_int32)]
+                ("mu_f", C.c_double), ("friction_eps", C.c_double), ("friction_passes", C.c_int32),
+                ("tangent_fp16", C.c_int32)]
 
 
 class fem_stats(C.Structure):

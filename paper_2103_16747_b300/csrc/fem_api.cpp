@@ -677,7 +677,7 @@ bool common_options_valid(const fem_options& o) {
          o.barrier_timeout_s > 0 && o.precond_degree >= 1 && o.precond_degree <= 8 && o.precond_ratio > 1.0 &&
          o.dt >= 0.0 && std::isfinite(o.dt) && (o.dt == 0.0 || (o.density > 0.0 && std::isfinite(o.density))) &&
          o.mu_f >= 0.0 && std::isfinite(o.mu_f) && o.friction_eps > 0.0 && std::isfinite(o.friction_eps) &&
-         o.friction_passes >= 1 && o.friction_passes <= 64;
+         o.friction_passes >= 1 && o.friction_passes <= 64 && (o.tangent_fp16 == 0 || o.tangent_fp16 == 1);
 }
 
 SmemLayout plan_layout(const PartDims& d, int budget) {
@@ -978,6 +978,7 @@ void fem_default_options(fem_options* opt) {
   opt->mu_f = 0.0;
   opt->friction_eps = 0.01;
   opt->friction_passes = 1;
+  opt->tangent_fp16 = 0;
 }
 
 const char* fem_last_error(void) { return g_err.c_str(); }
@@ -1691,14 +1692,32 @@ static int fem_eval_residual_noalloc_body(fem_mesh* m, const double* u, int32_t 
   const size_t off_fc = off_R + a256(node_bytes);
   const size_t off_stage = off_fc + a256(node_bytes);
   const size_t off_cta = off_stage + a256(node_bytes);
-  const size_t need = off_cta + (size_t)m->layout.gbytes * m->dev.n_parts;
-  if (need > kNoAllocScratchBytes)
+  const size_t cta_bytes = (size_t)m->layout.gbytes * m->dev.n_parts;
+  const size_t need = off_cta + cta_bytes;
+  if (need > kNoAllocScratchBytes) {
+    // the most nodes this mesh's partition layout leaves room for: four node
+    // arrays of 24 B per node (each rounded up to 256 B) after the fixed words
+    // and reduction slots, before the per-CTA arrays that did not fit on chip
+    const size_t fixed = off_u + cta_bytes;
+    const size_t max_nodes = fixed + 4 * 256 < kNoAllocScratchBytes
+                                 ? (kNoAllocScratchBytes - fixed - 4 * 255) / (4 * 3 * sizeof(double))
+                                 : 0;
     return fail(FEM_ERR_TOO_LARGE,
-                "fem_eval_residual_noalloc: mesh needs %zu B of scratch, the fixed block holds %zu B "
-                "(about %zu nodes at most)",
-                need, (size_t)kNoAllocScratchBytes, (size_t)(kNoAllocScratchBytes - off_u) / (4 * 3 * sizeof(double)));
+                "fem_eval_residual_noalloc: mesh of %lld nodes needs %zu B of scratch (%zu B of it per-CTA "
+                "arrays of %d parts), the fixed block holds %zu B: at most %zu nodes with this partition layout",
+                (long long)m->n_nodes, need, cta_bytes, m->dev.n_parts, (size_t)kNoAllocScratchBytes, max_nodes);
+  }
+  // the block and the launches belong to the mesh's device: make it current
+  // for the call and restore the caller's device afterwards
+  int prev_dev = 0;
+  CUDA_TRY(cudaGetDevice(&prev_dev), "current device");
+  if (prev_dev != m->device) CUDA_TRY(cudaSetDevice(m->device), "mesh device");
+  struct Restore {
+    int dev, prev;
+    ~Restore() { if (prev != dev) cudaSetDevice(prev); }
+  } restore{m->device, prev_dev};
   void* base = nullptr;
-  CUDA_TRY(noalloc_scratch(&base), "scratch address lookup");
+  CUDA_TRY(noalloc_scratch(m->device, &base), "scratch address lookup");
   unsigned char* b = static_cast<unsigned char*>(base);
   WorkDev W{};
   W.barrier = reinterpret_cast<unsigned long long*>(b);

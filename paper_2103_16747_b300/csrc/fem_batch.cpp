@@ -199,9 +199,11 @@ static int fem_batch_create_body(fem_mesh* const* meshes, const int32_t* n_steps
   if (clusters) CUDA_TRY(cluster_kernel_attrs(max_parts, 0, &static_smem, nullptr), "cluster kernel attributes");
   else CUDA_TRY(group_kernel_attrs(0, &static_smem, nullptr), "group kernel attributes");
   SmemLayout L = plan_layout(dims, smem_budget(meshes[0], static_smem));
-  // the batched engines store the tangent as FP16 with a per-tet scale: half
-  // the bytes each tangent product streams; the single path keeps FP32
-  L.tan16 = 1;
+  // stored tangent: FP32 (default), or FP16 with a per-tet scale (half the
+  // bytes each tangent product streams) when the options ask for it. The
+  // format is the engine's choice for every job of the launch, not the
+  // layout's, so a job's bits do not depend on the other jobs.
+  L.tan16 = o.tangent_fp16 ? 1 : 0;
   if (L.total < 0)
     return fail(FEM_ERR_TOO_LARGE, "a part of %d owned / %d local nodes does not fit one CTA", dims.max_own,
                 dims.max_loc);

@@ -222,6 +222,8 @@ cudaError_t launch_stress(const int4* tets, const double* dminv, const int* mat,
 // Fixed scratch block for fem_eval_residual_noalloc (fem_solve.cu).
 constexpr size_t kNoAllocScratchBytes = 8u << 20;
 constexpr int kMaxDevices = 64;
-cudaError_t noalloc_scratch(void** ptr);
+// Device address of the block on `device` (looked up with that device current
+// on first use, then cached).
+cudaError_t noalloc_scratch(int device, void** ptr);
 
 }  // namespace fem

@@ -1869,24 +1869,29 @@ unsigned long long device_clock_ns() {
 // module's own device memory, present on every GPU that loads this library
 // until the process exits. Host code must not use the symbol itself as a
 // device address; noalloc_scratch() looks the real address up once per
-// device (with that device current) and caches it.
+// device, with that device current, and caches it.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-cudaError_t noalloc_scratch(void** ptr) {
+cudaError_t noalloc_scratch(int device, void** ptr) {
   static std::mutex mu;
   static void* cache[kMaxDevices] = {};
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(mu);
-  if (!cache[dev]) {
+  if (!cache[device]) {
+    int prev = 0;
+    cudaError_t e = cudaGetDevice(&prev);
+    if (e != cudaSuccess) return e;
+    if (prev != device && (e = cudaSetDevice(device)) != cudaSuccess) return e;
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (prev != device) {
+      const cudaError_t e2 = cudaSetDevice(prev);
+      if (e == cudaSuccess) e = e2;
+    }
     if (e != cudaSuccess) return e;
-    cache[dev] = p;
+    cache[device] = p;
   }
-  *ptr = cache[dev];
+  *ptr = cache[device];
   return cudaSuccess;
 }
 

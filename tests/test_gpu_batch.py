@@ -30,10 +30,11 @@ def rel(a, b):
 ENGINES = [(1, 0), (2, 0)]        # (FEM_BATCH_GROUPS, automatic parts), (FEM_BATCH_CLUSTERS, automatic)
 
 
-def _batch(F, meshes, handles, inds, tol=1e-6, max_newton=None, engine=(1, 0)):
+def _batch(F, meshes, handles, inds, tol=1e-6, max_newton=None, engine=(1, 0), fp16=False):
     out = [np.zeros((m.n_nodes, 3)) for m in meshes]
     frc = [np.zeros((d.n_steps, 3)) for d in inds]
     opt = F.fem_default_options()
+    opt.tangent_fp16 = int(fp16)
     if max_newton is not None:
         opt.max_newton = max_newton
     opt.batch_engine, opt.batch_parts = engine
@@ -59,16 +60,16 @@ def test_batch_cube_matches_oracle(F, engine):
 
 @pytest.mark.parametrize("engine", ENGINES)
 def test_batch_fp16_tangent_holds_for_any_stiffness(F, engine):
-    """The batched engines store the tangent in FP16 with a per-tet scale. The
-    penalty stiffness scales with E, so the displacements of the cube do not
-    depend on E: the cube at E = 1e9 (tangent entries far above FP16's range
-    unscaled) and at E = 1e3 must both match the oracle at E = 1e6."""
+    """With tangent_fp16 the batched engines store the tangent in FP16 with a
+    per-tet scale. The penalty stiffness scales with E, so the displacements of
+    the cube do not depend on E: the cube at E = 1e9 (tangent entries far above
+    FP16's range unscaled) and at E = 1e3 must both match the oracle at E = 1e6."""
     m6, ind = W.cube_sphere()
     ref = Problem(m6, ind).solve(tol=1e-10)
     for E in (1.0e3, 1.0e9):
         m = W.cube_mesh(8, E=E, nu=0.3)
         h = F.fem_create_mesh(m.nodes, m.tets, m.tet_material, m.materials, m.fixed_nodes)
-        rc, out, frc, st = _batch(F, [m], [h], [ind], engine=engine)
+        rc, out, frc, st = _batch(F, [m], [h], [ind], engine=engine, fp16=True)
         F.fem_destroy_mesh(h)
         assert rc == 0 and st[0].residual <= 1e-6 * st[0].scale
         assert rel(out[0], ref.u) <= 1e-4

@@ -32,13 +32,14 @@ def test_default_options():
     assert o.precond_degree == 5 and o.precond_ratio == 120.0
     assert o.dt == 0.0 and o.density == 1.1e-9
     assert o.mu_f == 0.0 and o.friction_eps == 0.01 and o.friction_passes == 1
+    assert o.tangent_fp16 == 0
 
 
 @pytest.mark.parametrize("field,value", [("batch_engine", 3), ("batch_parts", -1), ("batch_parts", 300),
                                          ("tangent", 7), ("max_cg", 0), ("precond_degree", 0),
                                          ("precond_degree", 9), ("precond_ratio", 1.0),
                                          ("dt", -1e-4), ("dt", float("inf")), ("friction_passes", 0),
-                                         ("friction_passes", 65)])
+                                         ("friction_passes", 65), ("tangent_fp16", 2), ("tangent_fp16", -1)])
 def test_batch_options_are_checked_before_any_device_call(field, value):
     """Invalid options are rejected on the host (no mesh is touched)."""
     from paper_2103_16747_b300 import _lib as L
