@@ -58,7 +58,7 @@ def _active_state(name, cube_refs, seed):
     m, ind, r = cube_refs[name]
     rng = np.random.default_rng(seed)
     p = Problem(m, ind)
-    u = r.u + 0.02 * np.abs(r.u).max() * rng.standard_normal(r.u.shape)
+    u = r.u + 0.005 * np.abs(r.u).max() * rng.standard_normal(r.u.shape)
     u[p.fixed] = 0.0
     phi, n, _ = contact.sdf(ind.shape, p.origin_at(ind.n_steps), ind.rotation, ind.params, m.nodes + u)
     act = (phi < 0) & (p.k > 0)

@@ -172,7 +172,7 @@ def cube_cylinder_indenter(radius: float = 0.3, depth: float = 0.05, n_steps: in
     return ind
 
 
-def cube_box_edge_indenter(half: float = 0.3, depth: float = 0.05, n_steps: int = 10,
+def cube_box_edge_indenter(half: float = 0.3, depth: float = 0.12, n_steps: int = 10,
                            yaw_deg: float = 15.0, offset: float = 0.03) -> Indenter:
     """Cube of half extent ``half`` presenting one edge to the top face of the
     unit cube: the edge is horizontal (turned ``yaw_deg`` from the x axis), the
