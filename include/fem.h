@@ -512,6 +512,19 @@ int fem_apply_tangent(fem_mesh* mesh, const double* u, int32_t step, const fem_o
                       const double* p, double* out_y);
 
 /*
+ * Self-check of the PCG's dot products (Sec. III-A's Newton solver needs the
+ * inner linear solves; these are their reductions): (r,u), (w,u) and (r,r)
+ * over the free DOFs of the mesh, with r, u, w [n_nodes*3] (host or device,
+ * caller node order) rounded to FP32 as the PCG holds its vectors, summed by
+ * the same device code as every PCG iteration of fem_solve: error-free FP32
+ * products, compensated FP32-pair sums per CTA and over the CTAs in a fixed
+ * order. out[3] receives the three sums (each pair's hi + lo as a double). The
+ * mesh's evaluation buffers are overwritten. Errors: FEM_ERR_ARG, FEM_ERR_CUDA,
+ * FEM_ERR_TIMEOUT.
+ */
+int fem_debug_pcg_dots(fem_mesh* mesh, const double* r, const double* u, const double* w, double out[3]);
+
+/*
  * Failure-detection check: launch the solve kernel's grid barrier with one CTA
  * that never arrives, bounded by timeout_s (e.g. 0.05). The waiting CTAs give
  * up, set the device error word and return; the call returns FEM_ERR_TIMEOUT

@@ -44,7 +44,7 @@ PHASES = ("eval", "tangent", "pcg_init", "pcg_reduce", "pcg_matvec", "pcg_update
 EXPORTS = ("fem_default_options", "fem_create_mesh", "fem_set_indenter", "fem_set_dirichlet_values",
            "fem_solve", "fem_solve_batch", "fem_destroy_mesh", "fem_last_error", "fem_mesh_info_get", "fem_repartition",
            "fem_eval_residual", "fem_eval_residual_noalloc", "fem_apply_tangent",
-           "fem_debug_barrier_timeout", "fem_debug_reciprocals", "fem_debug_plan_check", "fem_batch_create", "fem_batch_run", "fem_batch_info_get",
+           "fem_debug_barrier_timeout", "fem_debug_pcg_dots", "fem_debug_reciprocals", "fem_debug_plan_check", "fem_batch_create", "fem_batch_run", "fem_batch_info_get",
            "fem_batch_destroy", "fem_batch_tune", "fem_server_create", "fem_server_start", "fem_server_submit",
            "fem_server_result", "fem_server_stop", "fem_server_info_get", "fem_server_destroy",
            "fem_element_stress")
@@ -135,6 +135,7 @@ def _load():
         "fem_eval_residual_noalloc": (C.c_int, [P, P, C.c_int32, C.POINTER(fem_options), P, P, P]),
         "fem_apply_tangent": (C.c_int, [P, P, C.c_int32, C.POINTER(fem_options), P, P]),
         "fem_debug_barrier_timeout": (C.c_int, [C.c_double]),
+        "fem_debug_pcg_dots": (C.c_int, [P, P, P, P, P]),
         "fem_debug_reciprocals": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
         "fem_debug_plan_check": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
                                            C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p]),
@@ -468,6 +469,15 @@ def fem_apply_tangent(mesh, u, step, p, out_y, opt=None):
     return _check(lib.fem_apply_tangent(mesh, _ptr(u, np.float64, keep), int(step),
                                         C.byref(opt) if opt is not None else None,
                                         _ptr(p, np.float64, keep), _out_ptr(out_y, np.float64, keep)))
+
+
+def fem_debug_pcg_dots(mesh, r, u, w):
+    """(r,u), (w,u), (r,r) over the free DOFs as the PCG's reductions form them."""
+    keep = []
+    out = np.zeros(3)
+    _check(lib.fem_debug_pcg_dots(mesh, _ptr(r, np.float64, keep), _ptr(u, np.float64, keep),
+                                  _ptr(w, np.float64, keep), C.c_void_p(out.ctypes.data)))
+    return out
 
 
 def fem_debug_barrier_timeout(timeout_s):

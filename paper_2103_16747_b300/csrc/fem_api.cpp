@@ -1839,6 +1839,27 @@ int fem_element_stress(fem_mesh* m, const double* u, double* out_cauchy, double*
   return guarded([&] { return fem_element_stress_body(m, u, out_cauchy, out_von_mises); });
 }
 
+static int fem_debug_pcg_dots_body(fem_mesh* m, const double* r, const double* u, const double* w, double* out) {
+  g_err.clear();
+  if (!m || !r || !u || !w || !out) return fail(FEM_ERR_ARG, "NULL argument");
+  SolveParams P;
+  int rc = fill_params(m, nullptr, MODE_DOT, 1, 0, 1e-6, P);
+  if (rc) return rc;
+  WorkDev W = m->work;
+  if ((rc = copy_in_nodes(m, r, const_cast<double*>(W.in_p)))) return rc;
+  if ((rc = copy_in_nodes(m, u, W.u))) return rc;
+  if ((rc = copy_in_nodes(m, w, W.R))) return rc;
+  StatsDev hst;
+  if ((rc = run_kernel(m, W, P, nullptr, &hst))) return rc;
+  CUDA_TRY(cudaMemcpyAsync(out, W.out_y, 3 * sizeof(double), cudaMemcpyDefault, m->stream), "output copy");
+  CUDA_TRY(cudaStreamSynchronize(m->stream), "output copy");
+  return FEM_OK;
+}
+
+int fem_debug_pcg_dots(fem_mesh* m, const double* r, const double* u, const double* w, double out[3]) {
+  return guarded([&] { return fem_debug_pcg_dots_body(m, r, u, w, out); });
+}
+
 static int fem_debug_barrier_timeout_body(double timeout_s) {
   g_err.clear();
   if (!(timeout_s > 0) || timeout_s > 10) return fail(FEM_ERR_ARG, "timeout_s must be in (0, 10]");

@@ -16,7 +16,7 @@ constexpr int kRed = 12;          // doubles per CTA reduction slot
 constexpr int kMaxSteps = 256;
 constexpr int kTanVec = 8;        // float4 groups of the stored per-tet tangent
 
-enum Mode : int { MODE_SOLVE = 0, MODE_EVAL = 1, MODE_APPLY = 2, MODE_BARRIER_TEST = 3 };
+enum Mode : int { MODE_SOLVE = 0, MODE_EVAL = 1, MODE_APPLY = 2, MODE_BARRIER_TEST = 3, MODE_DOT = 4 };
 
 enum Status : int {
   ST_OK = 0, ST_NOT_CONVERGED = 1, ST_LINESEARCH = 2, ST_NONFINITE = 3, ST_TIMEOUT = 4,

@@ -638,6 +638,13 @@ __device__ __forceinline__ DF df_add(DF a, DF b) {
 
 __device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
 
+// a * b exactly, as an FP32 pair: the rounded product and its rounding error
+// (fma computes a b - p without intermediate rounding).
+__device__ __forceinline__ DF two_prod(float a, float b) {
+  const float p = a * b;
+  return DF{p, fmaf(a, b, -p)};
+}
+
 __device__ __forceinline__ DF df_mul(DF a, DF b) {
   const float p = a.hi * b.hi;
   float e = fmaf(a.hi, b.hi, -p);

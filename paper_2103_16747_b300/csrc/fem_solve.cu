@@ -186,16 +186,16 @@ __device__ __forceinline__ bool sync_parts(Ctx& C, Barrier& gb) {
   }
 }
 
-// Deterministic CTA reduction of NV per-thread FP32 values into C.st->red_df:
-// two-sum tree in a fixed order.
+// Deterministic CTA reduction of NV per-thread FP32-pair values into
+// C.st->red_df: two-sum tree in a fixed order.
 template <int NV>
-__device__ void block_reduce_df(Ctx& C, const float* v, int active_warps) {
+__device__ void block_reduce_df(Ctx& C, const DF* v, int active_warps) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float2* red = reinterpret_cast<float2*>(C.red);
   if (warp < active_warps) {
     DF a[NV];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) a[k] = DF{v[k], 0.f};
+    for (int k = 0; k < NV; ++k) a[k] = v[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
@@ -335,6 +335,21 @@ __device__ __forceinline__ void gather_chunk(Ctx& C, int CH, const T* buf, int c
 
 __device__ __forceinline__ void reset_cursors(Ctx& C, int nv) {
   for (int idx = threadIdx.x; idx < C.n_own * nv; idx += blockDim.x) C.cursor[idx] = C.lptr[idx / nv];
+}
+
+// One owned node's terms of the PCG dot products (r,u), (w,u) and (r,r),
+// accumulated with error-free products: each FP32 product goes into the
+// thread's FP32 pair together with its rounding error, so the per-thread sums,
+// and with the compensated CTA and grid sums the whole dot product, carry about
+// 44 significant bits relative to the sum of |terms| (FP64-class accuracy
+// without B300's narrow FP64 pipe).
+__device__ __forceinline__ void dot_terms(DF acc[3], const float r[3], const float u[3], const float w[3]) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    acc[0] = df_add(acc[0], two_prod(r[k], u[k]));
+    acc[1] = df_add(acc[1], two_prod(w[k], u[k]));
+    acc[2] = df_add(acc[2], two_prod(r[k], r[k]));
+  }
 }
 
 // Indices of the reduced values of an evaluation pass.
@@ -1033,20 +1048,18 @@ __device__ bool pcg(Ctx& C, const MeshDev& M, const WorkDev& W, const SolveParam
     tock(C, PH_CG_BARRIER, t);
     matvec_pass(C, M, &t);   // w = A u (u in C.lm)
     ++products;
-    float v[3] = {0.f, 0.f, 0.f};
+    DF v[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
       const float4 u4 = C.lm[i];
       const float uu[3] = {u4.x, u4.y, u4.z};
-      float w[3];
+      float w[3], rr3[3];
       finish_product(C, i, uu, w);
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         C.w[3 * i + k] = w[k];
-        const float rk = C.r[3 * i + k];
-        v[0] += rk * uu[k];
-        v[1] += w[k] * uu[k];
-        v[2] += rk * rk;
+        rr3[k] = C.r[3 * i + k];
       }
+      dot_terms(v, rr3, uu, w);
     }
     block_reduce_df<3>(C, v, active_warps);
     if constexpr (CL) {
@@ -1474,6 +1487,35 @@ __global__ void __launch_bounds__(kSolveBlock, 1) solve_kernel(MeshDev M, WorkDe
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
   StatsDev* st = W.stats;
 
+  if (P.mode == MODE_DOT) {
+    // self-check of the PCG reductions: r (in_p), u (u) and w (R) rounded to
+    // FP32 and masked like the PCG's vectors, the three dot products summed by
+    // the PCG's own code, the pair sums written to out_y[0..2]
+    const int active_warps = min((C.n_own + 31) / 32, (int)(blockDim.x >> 5));
+    DF v[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    for (int i = threadIdx.x; i < C.n_own; i += blockDim.x) {
+      const unsigned mk = C.mask[i];
+      float r3[3], u3[3], w3[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const size_t j = 3 * (size_t)(C.node0 + i) + k;
+        const bool fx = (mk & (1u << k)) != 0;
+        r3[k] = fx ? 0.f : (float)W.in_p[j];
+        u3[k] = fx ? 0.f : (float)W.u[j];
+        w3[k] = fx ? 0.f : (float)W.R[j];
+      }
+      dot_terms(v, r3, u3, w3);
+    }
+    block_reduce_df<3>(C, v, active_warps);
+    write_cg_slot(C, W, 1);
+    if (!reduce_cg_slots(C, W, 1, P.timeout_ns)) return;
+    if (leader) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) W.out_y[k] = (double)S.red_df[k].x + (double)S.red_df[k].y;
+      st->status = ST_OK;
+    }
+    return;
+  }
   if (P.mode == MODE_EVAL || P.mode == MODE_APPLY) {
     double org[3];
     const double d = P.step > 0 ? P.depths[P.step - 1] : 0.0;
