@@ -1,40 +1,37 @@
 """Benchmark of the quasi-static tet-FEM indentation solve on B300.
 
-Default workload (--workload fingertip): one step = one complete indentation
-solve (all 20 load steps: FP64 residual, FP32 tangent, block-Jacobi PCG in
-Chronopoulos-Gear form, line search) of the single-fingertip sphere workload:
-a two-layer half-capsule fingertip (R = 7 mm, L = 40 mm, 38,880 tets / 8,740
-nodes) pressed 2 mm by a sphere of radius 4 mm in 20 load steps, to a
-relative residual of 1e-6. The mesh is resident on the device when the timed
-region starts; outputs go to device buffers. The end-to-end figure goes
-through the same public C ABI from host arrays (mesh upload, indenter, solve,
-host outputs, release) every step.
+Default workload (--workload batch): one step = 256 random indentations of the
+single-fingertip mesh (two-layer half-capsule, R = 7 mm, L = 40 mm, 38,880 tets
+/ 8,740 nodes; sphere r 2-6 / cylinder r 1-4 / 20 mm box edge, tilt <= 30 deg,
+depth 0.5-3 mm, 20 load steps each) to a relative residual of 1e-6, in one
+replayed CUDA graph of the persistent batched kernel (fem_batch_run), slot
+shape from the autotuner, FP32 stored tangent. Meshes and workspace are
+resident when the timed region starts; outputs go to device buffers. Beside it
+the line carries the plain path (one fem_solve launch per indentation) on the
+same draws, the end-to-end figure through the public one-shot call from pinned
+host arrays, the roofline of the batched kernel and the oracle on the host
+cores.
 
-Batched workloads print their own line:
-  --workload batch   one step = 256 random indentations of that fingertip
-                     (sphere / cylinder / box edge, tilt <= 30 deg, depth
-                     0.5-3 mm) in one replayed CUDA graph of the persistent
-                     batched kernel (fem_batch_run).
-  --workload uneven  one step = 64 fingertips of uneven size (R 5-10 mm,
-                     5k-200k tets log-uniform), one random indentation each,
-                     in one launch; the slot shape comes from fem_batch_tune.
-  --workload dynamic the fingertip solve as 20 backward-Euler time steps of
-                     1e-4 s (the paper's implicit time step) from rest, with
-                     the lumped mass of a 1100 kg/m^3 body; same line format.
-  --workload calibrated  the same solve on the paper's calibrated model: one
-                     co-rotational shell, E=1.55 MPa, nu=0.316.
-  --workload friction    the fingertip solve with Coulomb friction mu=0.783.
-  --workload serve   Poisson streams of requests over a resident pool of 16
-                     fingertip meshes (5k-200k tets) through the request
-                     server (continuous batching), one session per offered
-                     rate; latency p50/p99 and throughput beside the plain
-                     one-solve-per-launch path on the same arrival trace.
+Other workloads print the same kind of line:
+  --workload fingertip   one step = the single sphere indentation of that
+                         fingertip (2 mm, r = 4 mm, 20 load steps), fem_solve.
+  --workload dynamic     the same as 20 backward-Euler time steps of 1e-4 s from
+                         rest (lumped mass, 1100 kg/m^3).
+  --workload calibrated  the same on the paper's calibrated model: one
+                         co-rotational shell, E = 1.55 MPa, nu = 0.316.
+  --workload friction    the same with Coulomb friction mu = 0.783.
+  --workload uneven      one step = 64 fingertips of uneven size (R 5-10 mm,
+                         5k-200k tets log-uniform), one random indentation each.
+  --workload serve       Poisson streams of requests over a resident pool of 16
+                         fingertip meshes through the request server (continuous
+                         batching), one session per offered rate, and the plain
+                         one-solve-per-request path run on the same arrival trace.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference]
-                    [--workload fingertip|dynamic|calibrated|friction|batch|uneven|serve]
+                    [--workload batch|fingertip|dynamic|calibrated|friction|uneven|serve]
 
 Multi-GPU runs (torchrun) are independent replicas: every rank solves its own
-indentation, no collectives on the data path (weak scaling).
+draws, no collectives on the data path (weak scaling).
 """
 from __future__ import annotations
 
@@ -56,24 +53,23 @@ sys.path.insert(0, ROOT)
 METRIC = "indentation solves/s at residual 1e-6; kernel HBM GB/s vs peak; p50/p99 latency"
 UNIT = "solves/s"
 TOL = 1e-6
+DTYPE = "f32 (tangent, PCG vectors) + f64 (residual, energy, line search, displacement)"
 WORKLOAD = ("fingertip_sphere: two-layer half-capsule fingertip R=7 mm L=40 mm (1 mm skin "
             "E=1.5 MPa nu=0.45 over 2 mm inner E=0.2 MPa nu=0.48, core fixed), 38880 tets / "
             "8740 nodes; sphere r=4 mm pressed 2 mm normal to a seeded skin point in 20 load steps")
 DYN_DT, DYN_DENSITY = 1e-4, 1.1e-9     # s; t/mm^3 (1100 kg/m^3)
 FRICTION_MU = 0.783                    # the paper's calibrated Coulomb coefficient
-# single-solve variants of the fingertip workload: description, oracle
-# arguments, stored oracle solution (its Newton count extrapolates the CPU leg)
 VARIANTS = {
-    "fingertip": (WORKLOAD, {}, "fingertip_sphere_oracle.npz"),
+    "fingertip": (WORKLOAD, {}),
     "dynamic": (WORKLOAD + f"; dynamic: each load step one backward-Euler time step of {DYN_DT:g} s from "
-                f"rest, lumped mass of density {DYN_DENSITY:g} t/mm^3",
-                {"dt": DYN_DT, "density": DYN_DENSITY}, "fingertip_sphere_dynamic_oracle.npz"),
+                f"rest, lumped mass of density {DYN_DENSITY:g} t/mm^3", {"dt": DYN_DT, "density": DYN_DENSITY}),
     "calibrated": ("fingertip_calibrated: the same geometry and load as one co-rotational linear-elastic shell "
-                   "(E=1.55 MPa, nu=0.316, the paper's calibrated parameters) over the fixed core",
-                   {}, "fingertip_calibrated_oracle.npz"),
+                   "(E=1.55 MPa, nu=0.316, the paper's calibrated parameters) over the fixed core", {}),
     "friction": (WORKLOAD + f"; lagged smoothed Coulomb friction mu={FRICTION_MU} (slip smoothing 0.01 h_bar)",
-                 {"mu_f": FRICTION_MU}, "fingertip_sphere_friction_oracle.npz"),
+                 {"mu_f": FRICTION_MU}),
 }
+BATCH_MAX_NEWTON = 200   # deep random draws need more Newton steps in their last load steps
+L2_NOTE = "flushed between timed steps (256 MiB write, L2 is 126 MB)"
 
 
 def variant_case(name, seed=None):
@@ -90,6 +86,24 @@ def variant_options(F, name):
     elif name == "friction":
         opt.mu_f = FRICTION_MU
     return opt
+
+
+def batch_jobs(workload, n, rank):
+    """(meshes, draws, description) of a batched workload; rank r draws its own."""
+    import workloads as W
+    if workload == "batch":
+        mesh, _ = W.fingertip_sphere()
+        draws = W.draw_indentations(mesh, n, seed=1002 + 1000 * rank)
+        return [mesh] * len(draws), draws, (
+            f"batch: {len(draws)} random indentations (sphere r 2-6 / cylinder r 1-4 / 20 mm box edge, "
+            f"tilt <= 30 deg, depth 0.5-3 mm, 20 load steps) of the fingertip of the single-solve "
+            f"workload ({mesh.n_tets} tets / {mesh.n_nodes} nodes), one replayed CUDA graph per step")
+    jobs = W.uneven_fingertips(n, seed=1003 + 1000 * rank)
+    meshes = [m for m, _ in jobs]
+    return meshes, [d for _, d in jobs], (
+        f"uneven: {len(jobs)} fingertips R 5-10 mm, {min(m.n_tets for m in meshes)}-"
+        f"{max(m.n_tets for m in meshes)} tets (log-uniform 5k-200k, {sum(m.n_tets for m in meshes)} "
+        f"total), one random indentation each, one launch per step")
 
 
 def replica_seed(rank: int) -> int:
@@ -175,27 +189,54 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def algorithmic_bytes(n_tets, n_nodes, products, newton_iters, evals):
-    """Per-launch algorithmic bytes of the solve kernel.
+# ------------------------------------------------------------ roofline accounting
+#
+# Two accountings of the bytes a solve moves, both from the iteration counts the
+# library reports (fem_stats): products = tangent products (PCG iterations and
+# preconditioner steps), newton = Newton iterations (each builds the tangent),
+# evals = FP64 evaluation passes (one per Newton iteration, one per line-search
+# halving, one per load step).
 
-    Stored-tangent accounting of the indentation problem (FP32 = 4 B): per
-    element-tangent product (each PCG iteration and each Chebyshev step of the
-    preconditioner) 264 B/tet + 160 B/node (tangent 45 floats + Dm^-1 9 floats,
-    tet ids, CSR, p read / y write, fused vector updates); per Newton iteration
-    464 B/tet + 48 B/node extra (u read, tangent write, FP64 forces, CSR); per
-    line-search energy pass 60 B/tet."""
-    return (products * (264 * n_tets + 160 * n_nodes) + newton_iters * (464 * n_tets + 48 * n_nodes)
+def stored_tangent_bytes(n_tets, n_nodes, products, newton, evals):
+    """The indentation problem's reference accounting with a stored 45-float
+    FP32 tangent: per product 264 B/tet + 160 B/node (tangent 45 floats + Dm^-1
+    9 floats, tet ids, node->tet lists, p read / y write, fused vector updates);
+    per Newton iteration 464 B/tet + 48 B/node (u read, tangent write, FP64
+    forces, lists); per energy pass 60 B/tet."""
+    return (products * (264 * n_tets + 160 * n_nodes) + newton * (464 * n_tets + 48 * n_nodes)
             + evals * 60 * n_tets)
 
 
-def compact_bytes(n_tets, n_nodes, products, newton_iters, evals):
-    """The same, for this library's compressed tangent (30 floats + ushort4 local
-    ids per tet, node vectors in shared memory): per tangent product 128 B/tet
-    read + 32 B/node published/loaded; per Newton iteration the FP64 pass (Dm^-1
-    72 B, V 8 B, ids 8 B, info 4 B) + tangent write 128 B; per energy pass
-    92 B/tet."""
-    return (products * (128 * n_tets + 32 * n_nodes) + newton_iters * (220 * n_tets + 48 * n_nodes)
-            + evals * 92 * n_tets)
+def own_bytes(n_tets, n_nodes, products, newton, evals, tan_bytes):
+    """This library's own bytes. Per tangent product: the stored tangent
+    (tan_bytes per tet: 30 floats in 8 float4 = 128 B, or 64 B in FP16), local
+    node ids 8 B and four node->tet entries 16 B per tet; per node the published
+    vector (12 B), its halo read (12 B) and the accumulator (8 B). Per Newton
+    iteration (tangent build): Dm^-1 72 B, volume 8 B, ids 8 B, material 4 B
+    per tet read, the tangent written, 48 B per node. Per evaluation pass: the
+    same 92 B per tet read, 96 B of FP64 corner forces written by the tet's
+    owner and 96 B read back, 48 B per node (u read, residual and contact
+    written)."""
+    return (products * ((tan_bytes + 24) * n_tets + 32 * n_nodes)
+            + newton * ((92 + tan_bytes) * n_tets + 48 * n_nodes)
+            + evals * (284 * n_tets + 48 * n_nodes))
+
+
+def product_bytes(n_tets, n_nodes, tan_bytes):
+    return (tan_bytes + 24) * n_tets + 32 * n_nodes
+
+
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+
+
+def flops_per_solve(n_tets, n_nodes, products, newton):
+    """FP32 work of the hot path: ~300 flop/tet + ~40 flop/node per tangent
+    product, ~600 flop/tet per Newton iteration (tangent build)."""
+    return products * (300 * n_tets + 40 * n_nodes) + newton * 600 * n_tets
+
+
+def evals_of(st, n_steps):
+    return st.newton_iters + st.backtracks + n_steps
 
 
 # device-side sources of the profiled kernels and of the shared-memory layout
@@ -214,9 +255,9 @@ def source_digest():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(summary="solve_kernel_fingertip_sphere.md", key="traffic_bytes_per_launch"):
-    """DRAM bytes (per launch, or per solve) from a committed ncu summary, or
-    None if the kernel sources changed since that capture."""
+def profiled_value(summary, key):
+    """A figure from a committed ncu summary, or None if the kernel sources
+    changed since that capture."""
     path = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(path):
         return None
@@ -233,99 +274,136 @@ def profiled_traffic(summary="solve_kernel_fingertip_sphere.md", key="traffic_by
         return None
 
 
-def _oracle_steps(job):
-    """One worker of cpu_oracle_batch_rate: the oracle's first load steps of
-    one solve, timed (run in a spawned process)."""
-    mesh, ind, n_load_steps = job
+def phase_fractions(rows, peak, time_ms):
+    """Per-phase bandwidth: rows = [(bytes, share of the kernel time)]; the
+    phase time is share x time_ms."""
+    out = {}
+    for name, (b, share) in rows.items():
+        t = share * time_ms / 1000.0
+        gbs = b / t / 1e9 if t > 0 else None
+        out[name] = {"bytes": b, "time_ms": share * time_ms, "achieved_GBs": gbs,
+                     "frac": (gbs / peak) if gbs else None}
+    return out
+
+
+# ------------------------------------------------------------ CPU oracle legs
+
+def _oracle_sample(job):
+    """One worker of the oracle legs: the oracle as it stands on the first
+    load steps of one solve (Problem set-up included), timed."""
+    mesh, ind, n_load_steps, kwargs = job
     from oracle import Problem
     t0 = time.perf_counter()
-    r = Problem(mesh, ind).solve(tol=1e-10, load_steps=n_load_steps)
+    r = Problem(mesh, ind, **kwargs).solve(tol=1e-10, load_steps=n_load_steps)
     return time.perf_counter() - t0, int(np.sum(r.newton_iters[:n_load_steps]))
 
 
-def cpu_oracle_batch_rate(meshes, draws, n_jobs=16, n_load_steps=2):
-    """The oracle as it stands on independent solves, one process per solve
-    across the host cores (spawned, so no process inherits a CUDA context):
-    the first n_load_steps of n_jobs seeded solves, extrapolated to the full
-    load schedule by load steps."""
-    import multiprocessing as mp
-    cores = os.cpu_count() or 1
-    jobs = [(meshes[i], draws[i], n_load_steps) for i in range(min(n_jobs, len(draws)))]
-    t0 = time.perf_counter()
-    with mp.get_context("spawn").Pool(processes=min(cores, len(jobs))) as pool:
-        res = pool.map(_oracle_steps, jobs)
-    wall = time.perf_counter() - t0
-    full = [t * d.n_steps / n_load_steps for (t, _), d in zip(res, draws)]
-    # throughput of a pool of min(cores, jobs) workers running such solves back to back
-    workers = min(cores, len(jobs))
-    value = workers / (sum(full) / len(full))
-    return {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
-            "sample": (f"{len(jobs)} of the step's solves, load steps 1-{n_load_steps} each ({sum(n for _, n in res)} "
-                       f"Newton iterations, {wall:.1f} s wall on {workers} processes), extrapolated to their full "
-                       f"schedules by load steps; one spawned process per solve, nproc {cores}")}
+def _one_thread_per_worker():
+    """Pool initializer: one BLAS thread per worker process (one process per
+    core; SuperLU itself is single-threaded)."""
+    try:
+        from threadpoolctl import threadpool_limits
+        threadpool_limits(1)
+    except Exception:
+        pass
 
 
-def cpu_oracle_rate(mesh, ind, n_load_steps, variant="fingertip"):
-    """Time the oracle (as it stands) on the first n_load_steps of the same
-    solve and extrapolate to a full solve by Newton iterations, using the
-    oracle's Newton count for the full solve stored in tests/golden."""
+class OraclePool:
+    """Spawned worker processes for the oracle (spawned, so no worker inherits
+    a CUDA context); one solve sample per worker at a time."""
+
+    def __init__(self, n):
+        import multiprocessing as mp
+        self.n = max(1, int(n))
+        init = _one_thread_per_worker if self.n > 1 else None
+        self.pool = mp.get_context("spawn").Pool(processes=self.n, initializer=init)
+
+    def run(self, jobs):
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_sample, jobs, chunksize=1)
+        return time.perf_counter() - t0, res
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def blas_threads():
     try:
         from threadpoolctl import threadpool_info
-    except ImportError:                     # not installed on every host
-        def threadpool_info():
-            return [{"num_threads": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))}]
-    from oracle import Problem
-    _, kwargs, golden = VARIANTS[variant]
-    p = Problem(mesh, ind, **kwargs)
-    t0 = time.perf_counter()
-    r = p.solve(tol=1e-10, load_steps=n_load_steps)
-    dt = time.perf_counter() - t0
-    its = int(np.sum(r.newton_iters[:n_load_steps]))
-    full_its = None
-    g = os.path.join(ROOT, "tests", "golden", golden)
-    if os.path.exists(g):
-        full_its = int(np.sum(np.load(g)["newton_iters"]))
-    per_it = dt / max(its, 1)
-    est = per_it * (full_its if full_its else its * ind.n_steps / n_load_steps)
-    threads = max([t.get("num_threads", 1) for t in threadpool_info()] or [1])
-    return {"value": 1.0 / est, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": (f"load steps 1-{n_load_steps} of 20 of the same solve ({its} Newton iterations, "
-                       f"{dt:.1f} s), extrapolated by the oracle's {full_its} Newton iterations for the "
-                       f"full solve; scipy SuperLU is single-threaded, BLAS pool {threads} threads, "
-                       f"nproc {os.cpu_count()}"),
-            "seconds": dt}
+        return max([t.get("num_threads", 1) for t in threadpool_info()] or [1])
+    except Exception:
+        return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
+
+def oracle_sample_rate(pool, meshes, draws, picks, n_load_steps, kwargs=None):
+    """Solves/s of the oracle on a bounded sample: load steps 1..n_load_steps
+    of each picked solve, all picks at once on the pool. The sample's share of
+    a full solve is n_load_steps / K (K load steps per solve), so the rate is
+    (picks x n_load_steps / K) / wall. Later load steps take more Newton
+    iterations than the first ones, so this overstates the oracle's rate."""
+    jobs = [(meshes[k], draws[k], n_load_steps, kwargs or {}) for k in picks]
+    wall, res = pool.run(jobs)
+    solves = sum(n_load_steps / draws[k].n_steps for k in picks)
+    return solves / wall, wall, sum(n for _, n in res)
+
+
+def cpu_baseline_line(value, cores, sample):
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+
+# ------------------------------------------------------------ reference arm
 
 def run_reference(args, rank, world):
-    """The oracle as it stands on the host cores (rank 0 only)."""
+    """The oracle as it stands on the host cores (rank 0 only); every step is a
+    bounded sample of the same workload, timed as it runs."""
     if rank != 0:
         return
-    variant = args.workload if args.workload in VARIANTS else "fingertip"
-    mesh, ind = variant_case(variant)
-    for _ in range(args.warmup):
-        cpu_oracle_rate(mesh, ind, 1, variant)
-    times, rates = [], []
-    cores = 1
-    for _ in range(args.steps):
-        r = cpu_oracle_rate(mesh, ind, 1, variant)
-        times.append(r["seconds"])
-        rates.append(r["value"])
-        cores = r["cores"]
-    value = float(args.steps / sum(1.0 / v for v in rates))
+    cores = os.cpu_count() or 1
+    if args.workload in VARIANTS:
+        mesh, ind = variant_case(args.workload)
+        meshes, draws, desc, kwargs = [mesh], [ind], VARIANTS[args.workload][0], VARIANTS[args.workload][1]
+        width = 1
+    elif args.workload in ("batch", "uneven"):
+        meshes, draws, desc = batch_jobs(args.workload, args.n_solves, 0)
+        # the oracle's direct solve is for meshes up to the fingertip's size
+        keep = [k for k, m in enumerate(meshes) if m.n_tets <= 40000]
+        meshes, draws = [meshes[k] for k in keep], [draws[k] for k in keep]
+        kwargs = {}
+        width = min(cores, 16, len(draws))
+    else:
+        print(json.dumps({"impl": "reference", "unavailable": "the serving workload has no CPU reference: "
+                          "its comparison is the plain one-solve-per-request GPU path"}), flush=True)
+        return
+    pool = OraclePool(width)
+    walls, solves_done, newton = [], 0.0, 0
+    for step in range(args.warmup + args.steps):
+        picks = [(step * width + j) % len(draws) for j in range(width)]
+        rate, wall, its = oracle_sample_rate(pool, meshes, draws, picks, 1, kwargs)
+        if step >= args.warmup:
+            walls.append(wall)
+            solves_done += rate * wall
+            newton += its
+    pool.close()
+    value = solves_done / sum(walls)
+    sample = (f"each step: load step 1 of {draws[0].n_steps} of {width} solve(s) of the workload at once "
+              f"({width} spawned process(es), set-up included; steps rotate through the draws), scaled to "
+              f"full solves by load steps ({newton} Newton iterations in the timed steps); scipy SuperLU is "
+              f"single-threaded, BLAS {'1 thread per process' if width > 1 else f'pool {blas_threads()} threads'}, "
+              f"nproc {cores}")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * statistics.mean(walls),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": VARIANTS[variant][0], "tol": TOL},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "each step: load step 1 of 20 of the solve, extrapolated by "
-                                       "Newton iterations to a full solve"},
+            "data": "synthetic", "config": {"workload": desc, "tol": TOL},
+            "cpu_baseline": cpu_baseline_line(value, width, sample),
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def run_cuda(args, rank, world, local):
+# ------------------------------------------------------------ single solve (C1 and variants)
+
+def run_single(args, rank, world, local):
     import torch
-    import workloads as W
     import paper_2103_16747_b300 as F
 
     torch.cuda.set_device(local)
@@ -350,7 +428,7 @@ def run_cuda(args, rank, world, local):
         return F.fem_solve(solver.handle, ind.n_steps, TOL, opt, d_u, d_f, d_fc)[1]
 
     for _ in range(max(args.warmup, 0)):
-        st = solve_once()
+        solve_once()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -395,39 +473,52 @@ def run_cuda(args, rank, world, local):
             e2e_times.append(t1 - t0)
     e2e_total = max_over_ranks(sum(e2e_times), world, dev)
 
-    # roofline of the dominant kernel (the persistent solve kernel)
+    # roofline of the dominant kernel (the persistent solve kernel), own bytes
     s0 = stats[-1]
-    evals = s0.newton_iters + s0.backtracks + ind.n_steps
+    ev_n = evals_of(s0, ind.n_steps)
     kms = statistics.mean(kernel_ms)
-    alg = algorithmic_bytes(mesh.n_tets, n, s0.tangent_products, s0.newton_iters, evals)
-    cmp_b = compact_bytes(mesh.n_tets, n, s0.tangent_products, s0.newton_iters, evals)
     peak, peak_kind = peaks()
-    achieved = alg / (kms / 1000.0) / 1e9
-    # the committed capture is of the default variant
-    traffic = profiled_traffic() if variant == "fingertip" else None
+    own = own_bytes(mesh.n_tets, n, s0.tangent_products, s0.newton_iters, ev_n, 128)
+    stored = stored_tangent_bytes(mesh.n_tets, n, s0.tangent_products, s0.newton_iters, ev_n)
+    achieved = own / (kms / 1000.0) / 1e9
+    ph = {name: s0.phase_ms[k] / max(s0.phase_ms[7], 1e-30) for k, name in enumerate(F.PHASES)}
+    phases = phase_fractions({
+        "tangent_product": (s0.tangent_products * product_bytes(mesh.n_tets, n, 128),
+                            ph["product_element"] + ph["product_gather"]),
+        "element_eval": (ev_n * (284 * mesh.n_tets + 48 * n), ph["eval"]),
+        "tangent_build": (s0.newton_iters * ((92 + 128) * mesh.n_tets + 48 * n), ph["tangent"])}, peak, kms)
+    traffic = (profiled_value("solve_kernel_fingertip_sphere.md", "traffic_bytes_per_launch")
+               if variant == "fingertip" else None)
     lat = sorted(step_ms)
-    p = lambda q: lat[min(len(lat) - 1, int(math.ceil(q * len(lat))) - 1)]   # noqa: E731
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total * 1000.0 / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (tangent, PCG vectors) + f64 (residual, "
-            "energy, reductions, displacement)", "data": "synthetic",
-            "config": {"workload": VARIANTS[variant][0], "tol": TOL, "n_parts": info.n_parts,
-                       "l2": "flushed between timed steps (256 MiB write, L2 is 126 MB)",
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE, "data": "synthetic",
+            "config": {"workload": VARIANTS[variant][0], "tol": TOL, "n_parts": info.n_parts, "l2": L2_NOTE,
                        "replicas": world, "newton_iters": s0.newton_iters, "cg_iters": s0.cg_iters,
                        "tangent_products": s0.tangent_products, "backtracks": s0.backtracks,
                        "preconditioner": f"Chebyshev degree {opt.precond_degree} on block-Jacobi, "
                                          f"interval [4/{opt.precond_ratio:g}, 4]"},
-            "latency_ms": {"p50": p(0.5), "p99": p(0.99)},
+            "latency_ms": {"p50": percentile(lat, 0.5), "p99": percentile(lat, 0.99)},
             "e2e": {"value": world * args.steps / e2e_total, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": 3 * args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": "solve_kernel",
-                         "kernel_ms": kms, "algorithmic_bytes": alg, "peak_kind": peak_kind,
-                         "compact_accounting_GBs": cmp_b / (kms / 1000.0) / 1e9},
+                         "kernel_ms": kms, "algorithmic_bytes": own, "accounting": "own (FP32 30-float tangent)",
+                         "peak_kind": peak_kind, "phases": phases,
+                         "stored_tangent_accounting": {"bytes": stored,
+                                                       "achieved": stored / (kms / 1000.0) / 1e9,
+                                                       "frac": stored / (kms / 1000.0) / 1e9 / peak}},
             "clocks": clk.summary()}
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = {k: v for k, v in cpu_oracle_rate(mesh, ind, 2, variant).items() if k != "seconds"}
+        pool = OraclePool(1)
+        rate, wall, its = oracle_sample_rate(pool, [mesh], [ind], [0], 2, VARIANTS[variant][1])
+        pool.close()
+        line["cpu_baseline"] = cpu_baseline_line(
+            rate, 1, f"load steps 1-2 of {ind.n_steps} of the same solve (set-up included, {its} Newton "
+                     f"iterations, {wall:.1f} s), scaled to a full solve by load steps (later steps take more "
+                     f"Newton iterations: this overstates the oracle's rate); scipy SuperLU single-threaded, "
+                     f"nproc {os.cpu_count()}")
     if rank == 0:
         print(json.dumps(line), flush=True)
     solver.close()
@@ -435,19 +526,10 @@ def run_cuda(args, rank, world, local):
         torch.distributed.destroy_process_group()
 
 
-FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
-
-
-def flops_per_solve(n_tets, n_nodes, products, newton_iters):
-    """FP32 work of the hot path: ~300 flop/tet + ~40 flop/node per tangent
-    product, ~600 flop/tet per Newton iteration (tangent build)."""
-    return products * (300 * n_tets + 40 * n_nodes) + newton_iters * 600 * n_tets
-
+# ------------------------------------------------------------ batched solves (C2, C3)
 
 def run_batch(args, rank, world, local):
-    """Batched workloads: many independent solves per step in one launch."""
     import torch
-    import workloads as W
     import paper_2103_16747_b300 as F
 
     torch.cuda.set_device(local)
@@ -456,28 +538,16 @@ def run_batch(args, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     opt = F.fem_default_options()
-    opt.max_newton = 200            # deep random draws need more Newton steps in their last load steps
-    if args.workload == "batch":
-        mesh, _ = W.fingertip_sphere()
-        draws = W.draw_indentations(mesh, args.n_solves, seed=1002 + 1000 * rank)
-        meshes = [mesh] * len(draws)
-        workload = (f"batch: {len(draws)} random indentations (sphere r 2-6 / cylinder r 1-4 / 20 mm box edge, "
-                    f"tilt <= 30 deg, depth 0.5-3 mm, 20 load steps) of the fingertip of the single-solve "
-                    f"workload ({mesh.n_tets} tets / {mesh.n_nodes} nodes), one replayed CUDA graph per step")
-    else:
-        jobs = W.uneven_fingertips(args.n_solves, seed=1003 + 1000 * rank)
-        meshes = [m for m, _ in jobs]
-        draws = [d for _, d in jobs]
-        workload = (f"uneven: {len(draws)} fingertips R 5-10 mm, {min(m.n_tets for m in meshes)}-"
-                    f"{max(m.n_tets for m in meshes)} tets (log-uniform 5k-200k, {sum(m.n_tets for m in meshes)} "
-                    f"total), one random indentation each, one launch per step")
+    opt.max_newton = BATCH_MAX_NEWTON
+    opt.tangent_fp16 = 1 if args.fp16_tangent else 0
+    tan_bytes = 64 if args.fp16_tangent else 128
+    meshes, draws, workload = batch_jobs(args.workload, args.n_solves, rank)
     uniq = {id(m): m for m in meshes}
     handles = {k: F.fem_create_mesh(m.nodes, m.tets, m.tet_material, m.materials, m.fixed_nodes)
                for k, m in uniq.items()}
     hs = [handles[id(m)] for m in meshes]
-    # both batched workloads take their slot shape from the autotuner, unless
-    # a fixed group size is asked for (profiling: then the plan's launches are
-    # the only ones)
+    # slot shape from the autotuner, unless a fixed group size is asked for
+    # (profiling: then the plan's launches are the only ones)
     t0 = time.perf_counter()
     if args.batch_parts:
         opt.batch_engine, opt.batch_parts = F.FEM_BATCH_GROUPS, args.batch_parts
@@ -500,37 +570,58 @@ def run_batch(args, rank, world, local):
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    step_s, stats = [], None
+    step_dev_ms, step_wall, stats = [], [], None
     with ClockSampler(local) as clk:
         for k in range(args.steps):
-            flush.fill_(float(k))
+            flush.fill_(float(k))                     # evict L2 between timed steps
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             rc, stats = plan.run(draws, TOL, outs, frcs, check=False)
             torch.cuda.synchronize()
-            step_s.append(time.perf_counter() - t0)
-    kernel_ms = stats[0].kernel_ms
-    total = max_over_ranks(sum(step_s), world, dev)
+            step_wall.append(time.perf_counter() - t0)
+            # device time of the replayed graph (CUDA events on the plan's stream
+            # around the launch: workspace reset, uploads, persistent kernel, reorder)
+            step_dev_ms.append(stats[0].kernel_ms)
+    total = max_over_ranks(sum(step_dev_ms) / 1000.0, world, dev)
     n = len(draws)
     value = world * n * args.steps / total
     ok = sum(1 for s_ in stats if s_.status == 0)
-    alg = sum(algorithmic_bytes(m.n_tets, m.n_nodes, s_.tangent_products, s_.newton_iters,
-                                s_.newton_iters + s_.backtracks + d.n_steps)
-              for m, s_, d in zip(meshes, stats, draws))
-    flops = sum(flops_per_solve(m.n_tets, m.n_nodes, s_.tangent_products, s_.newton_iters)
-                for m, s_ in zip(meshes, stats))
+    kms = statistics.mean(step_dev_ms)
     peak, peak_kind = peaks()
-    achieved = alg / (kernel_ms / 1000.0) / 1e9
-    # the plain one-solve-per-launch path (fem_solve, one cooperative launch
-    # per solve) on every draw of the step, kernel time
-    single_s = 0.0
+    per = [(m, s_, d, evals_of(s_, d.n_steps)) for m, s_, d in zip(meshes, stats, draws)]
+    own = sum(own_bytes(m.n_tets, m.n_nodes, s_.tangent_products, s_.newton_iters, e, tan_bytes)
+              for m, s_, d, e in per)
+    stored = sum(stored_tangent_bytes(m.n_tets, m.n_nodes, s_.tangent_products, s_.newton_iters, e)
+                 for m, s_, d, e in per)
+    flops = sum(flops_per_solve(m.n_tets, m.n_nodes, s_.tangent_products, s_.newton_iters) for m, s_, d, e in per)
+    achieved = own / (kms / 1000.0) / 1e9
+    # per-phase bandwidth: each solve reports the shares of its own time spent
+    # in each phase (clock of its part 0); groups run side by side for the whole
+    # launch, so a phase's share of the launch is the product-weighted mean share
+    wsum = sum(s_.tangent_products for _, s_, _, _ in per) or 1
+
+    def share(*names):
+        idx = [F.PHASES.index(x) for x in names]
+        return sum(s_.tangent_products * sum(s_.phase_ms[i] for i in idx) for _, s_, _, _ in per) / wsum
+
+    phases = phase_fractions({
+        "tangent_product": (sum(s_.tangent_products * product_bytes(m.n_tets, m.n_nodes, tan_bytes)
+                                for m, s_, _, _ in per), share("product_element", "product_gather")),
+        "element_eval": (sum(e * (284 * m.n_tets + 48 * m.n_nodes) for m, s_, _, e in per), share("eval")),
+        "tangent_build": (sum(s_.newton_iters * ((92 + tan_bytes) * m.n_tets + 48 * m.n_nodes)
+                              for m, s_, _, _ in per), share("tangent"))}, peak, kms)
+    # the plain one-solve-per-launch path (fem_solve: one cooperative launch
+    # per solve, all SMs) on every draw of the step, kernel time
+    single_s, single_ok = 0.0, 0
     for i in range(n):
         s1 = F.IndentationSolver(meshes[i])
         s1.set_indenter(draws[i])
         r = s1.solve(TOL, opt, check=False)
         single_s += r["stats"].kernel_ms / 1000.0
+        single_ok += int(r["rc"] == 0)
         s1.close()
-    # end to end: public one-shot call from host arrays (meshes uploaded every step)
+    # end to end: the public one-shot call from pinned host arrays, meshes
+    # uploaded, the plan built and released inside every step
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()   # noqa: E731
     h_out = [torch.zeros((m.n_nodes, 3), dtype=torch.float64).pin_memory() for m in meshes]
     h_frc = [torch.zeros((d.n_steps, 3), dtype=torch.float64).pin_memory() for d in draws]
@@ -539,8 +630,9 @@ def run_batch(args, rank, world, local):
     d2h = sum(o.numel() * 8 for o in h_out) + sum(f.numel() * 8 for f in h_frc)
     h_in = {k: (pin(m.nodes), pin(m.tets.astype(np.int32)), pin(m.tet_material.astype(np.int32)),
                 pin(m.fixed_nodes.astype(np.int32))) for k, m in uniq.items()}
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
     e2e_s = 0.0
-    for _ in range(args.steps):
+    for _ in range(e2e_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         eh = {k: F.fem_create_mesh(h_in[k][0], h_in[k][1], h_in[k][2], m.materials, h_in[k][3])
@@ -551,39 +643,58 @@ def run_batch(args, rank, world, local):
         e2e_s += time.perf_counter() - t0
     e2e_s = max_over_ranks(e2e_s, world, dev)
     # DRAM traffic from the committed capture of the same slot shape (uniform
-    # 37-CTA groups on this fingertip, 8 solves), scaled by the solves of the
-    # launch; None for other shapes or changed sources
+    # 37-CTA groups on this fingertip, 8 solves, FP32 tangent), scaled by the
+    # solves of the launch; None for other shapes or changed sources
     traffic = None
-    if args.workload == "batch" and info.engine == 1 and info.parts == 37:
-        per_solve = profiled_traffic("group_kernel_fingertip_batch.md", "traffic_bytes_per_solve")
+    if args.workload == "batch" and info.engine == 1 and info.parts == 37 and not args.fp16_tangent:
+        per_solve = profiled_value("group_kernel_fingertip_batch.md", "traffic_bytes_per_solve")
         traffic = per_solve * n if per_solve is not None else None
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total * 1000.0 / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 (tangent, PCG vectors) + f64 (residual, energy, reductions, displacement)",
-            "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE, "data": "synthetic",
             "config": {"workload": workload, "tol": TOL, "solves_per_step": n, "converged": ok,
+                       "tangent_storage": "fp16 (per-tet scale)" if args.fp16_tangent else "fp32",
+                       "max_newton_per_step": BATCH_MAX_NEWTON,
                        "engine": {1: "cta_groups", 2: "clusters"}[info.engine], "ctas_per_solve": info.parts,
                        "slots": info.slots, "graph": bool(info.graph), "resident_tangent": bool(info.resident_tangent),
                        "cg_iters_total": sum(s_.cg_iters for s_ in stats),
                        "newton_iters_total": sum(s_.newton_iters for s_ in stats),
-                       "l2": "flushed between timed steps (256 MiB write, L2 is 126 MB)", "autotune": tune},
-            "single_path_same_draws": {"value": n / single_s, "unit": UNIT, "solves": n,
-                                       "note": "fem_solve (one cooperative launch per solve) on every draw "
-                                               "of the step, sum of kernel times"},
-            "e2e": {"value": world * n * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": int(d2h)},
+                       "tangent_products_total": sum(s_.tangent_products for s_ in stats),
+                       "wall_ms_per_step": 1000.0 * statistics.mean(step_wall),
+                       "l2": L2_NOTE, "autotune": tune},
+            "plain_path_same_draws": {"value": n / single_s, "unit": UNIT, "solves": n, "converged": single_ok,
+                                      "note": "fem_solve (one cooperative launch on all SMs per solve) on every "
+                                              "draw of the step, same options and tolerance, sum of kernel times"},
+            "e2e": {"value": world * n * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h), "steps": e2e_steps,
+                    "note": "fem_create_mesh from pinned host arrays, fem_solve_batch (plan, graph, run, release) "
+                            "with pinned host outputs, fem_destroy_mesh, every step"},
+            # per step: the persistent kernel (once per phase of the plan; one
+            # phase here) and one reorder kernel per solve
             "gpu_launches": (1 + n) * args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "group_kernel" if info.engine == 1 else "cluster_kernel",
-                         "kernel_ms": kernel_ms, "algorithmic_bytes": alg, "peak_kind": peak_kind,
-                         "fp32_tflops": flops / (kernel_ms / 1000.0) / 1e12, "fp32_peak_tflops": FP32_PEAK_TFLOPS},
+                         "kernel_ms": kms, "algorithmic_bytes": own,
+                         "accounting": f"own ({'FP16' if args.fp16_tangent else 'FP32'} tangent, {tan_bytes} B/tet)",
+                         "peak_kind": peak_kind, "phases": phases,
+                         "stored_tangent_accounting": {"bytes": stored,
+                                                       "achieved": stored / (kms / 1000.0) / 1e9,
+                                                       "frac": stored / (kms / 1000.0) / 1e9 / peak},
+                         "fp32_tflops": flops / (kms / 1000.0) / 1e12, "fp32_peak_tflops": FP32_PEAK_TFLOPS},
             "clocks": clk.summary()}
     if rank == 0 and not args.no_cpu_baseline:
-        # the oracle's direct solve is for meshes up to the fingertip's size
         small = [k for k, m in enumerate(meshes) if m.n_tets <= 40000]
-        line["cpu_baseline"] = cpu_oracle_batch_rate([meshes[k] for k in small], [draws[k] for k in small])
+        width = min(os.cpu_count() or 1, 16, len(small))
+        pool = OraclePool(width)
+        picks = small[:width]
+        rate, wall, its = oracle_sample_rate(pool, meshes, draws, picks, 2)
+        pool.close()
+        line["cpu_baseline"] = cpu_baseline_line(
+            rate, width, f"load steps 1-2 of {width} of the step's solves (meshes up to 40k tets) at once, one "
+                         f"spawned process each, set-up included ({its} Newton iterations, {wall:.1f} s wall), "
+                         f"scaled to full solves by load steps (later steps take more Newton iterations: this "
+                         f"overstates the oracle's rate); SuperLU single-threaded, nproc {os.cpu_count()}")
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()
@@ -600,32 +711,28 @@ def percentile(xs, q):
     return xs[min(len(xs) - 1, max(0, int(math.ceil(q * len(xs))) - 1))]
 
 
+# ------------------------------------------------------------ serving (C4)
+
 def run_serve(args, rank, world, local):
-    """Request server under Poisson arrivals (one session per offered rate)."""
+    """Request server under Poisson arrivals (one session per offered rate),
+    then the plain path on the same arrival trace: one fem_solve per request,
+    in arrival order, each started once it has arrived and the GPU is free."""
     import torch
     import workloads as W
     import paper_2103_16747_b300 as F
 
     torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
     jobs = W.uneven_fingertips(16, seed=1004 + 1000 * rank)
     pool = [m for m, _ in jobs]
     kinds = [(k, d) for k, m in enumerate(pool) for d in W.draw_indentations(m, 4, seed=2000 + k)]
     handles = [F.fem_create_mesh(m.nodes, m.tets, m.tet_material, m.materials, m.fixed_nodes) for m in pool]
     opt = F.fem_default_options()
-    opt.max_newton = 200
+    opt.max_newton = BATCH_MAX_NEWTON
     sopt = F.fem_default_options()
-    sopt.max_newton = 200
+    sopt.max_newton = BATCH_MAX_NEWTON
     sopt.batch_parts = args.serve_class_cap
     if args.serve_tets_per_cta:
         sopt.batch_tets_per_cta = args.serve_tets_per_cta
-    # the plain path: one fem_solve (cooperative launch) per request kind, kernel time
-    t_plain = []
-    for k, d in kinds:
-        s1 = F.IndentationSolver(pool[k])
-        s1.set_indenter(d)
-        t_plain.append(s1.solve(TOL, opt, check=False)["stats"].kernel_ms / 1000.0)
-        s1.close()
     srv = F.FemServer(handles, 20, sopt, result_bytes=1 << 30)
     info = srv.info()
     rng = np.random.Generator(np.random.PCG64(1004 + 1000 * rank))
@@ -661,34 +768,28 @@ def run_serve(args, rank, world, local):
                 t_first = tm[0] if t_first is None else min(t_first, tm[0])
                 t_last = tm[2] if t_last is None else max(t_last, tm[2])
             srv.stop()
-            done = len(lat)
-            # the plain path on the same trace: one GPU worker, FIFO, each
-            # request taking its kind's measured fem_solve time
-            fin, plain_lat = 0.0, []
-            for a, p_ in zip(arrivals, picks):
-                fin = max(fin, a) + t_plain[p_]
-                plain_lat.append(1000.0 * (fin - a))
+            # the plain path on the same trace, run for real: one GPU worker,
+            # requests in arrival order, each fem_solve on the pool's resident mesh
+            plain = plain_path_on_trace(F, handles, pool, kinds, arrivals, picks, opt,
+                                        args.serve_seconds + args.drain_seconds)
             sessions.append({
-                "offered_per_s": rate, "requests": int(len(arrivals)), "rejected": rejected, "completed": done,
-                "converged": int(ok), "throughput": done / (t_last - t_first) if done > 1 else None,
-                "p50_ms": percentile(lat, 0.5), "p99_ms": percentile(lat, 0.99),
-                "plain_path": {"throughput": len(arrivals) / fin if fin > 0 else None,
-                               "p50_ms": percentile(plain_lat, 0.5), "p99_ms": percentile(plain_lat, 0.99)}})
+                "offered_per_s": rate, "requests": int(len(arrivals)), "rejected": rejected,
+                "completed": len(lat), "converged": int(ok),
+                "throughput": len(lat) / (t_last - t_first) if len(lat) > 1 else None,
+                "p50_ms": percentile(lat, 0.5), "p99_ms": percentile(lat, 0.99), "plain_path": plain})
             print(json.dumps({"session": sessions[-1]}), file=sys.stderr, flush=True)
     best = max((x["throughput"] or 0.0) for x in sessions)
     line = {"metric": METRIC, "value": best, "unit": UNIT, "n_gpus": world, "steps": len(sessions), "warmup": 0,
             "ms_per_step": 1000.0 * args.serve_seconds, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None,
-            "dtype": "f32 (tangent, PCG vectors) + f64 (residual, energy, reductions, displacement)",
-            "data": "synthetic",
+            "vs_baseline": None, "dtype": DTYPE, "data": "synthetic",
             "config": {"workload": (f"serve: Poisson requests over a resident pool of 16 fingertips "
                                     f"({min(m.n_tets for m in pool)}-{max(m.n_tets for m in pool)} tets), "
                                     f"4 random indentations per mesh, {args.serve_seconds:.0f} s per offered rate"),
                        "tol": TOL, "tets_per_cta_target": sopt.batch_tets_per_cta,
                        "size_classes": list(info.class_parts[:info.n_classes]),
                        "groups": list(info.class_groups[:info.n_classes]), "result_slots": info.result_slots,
-                       "plain_path": "fem_solve per request in arrival order, measured kernel time per request kind "
-                                     "(queueing simulated on the same trace)"},
+                       "plain_path": "fem_solve per request in arrival order on the same trace, run on the GPU "
+                                     "(latency = completion - arrival)"},
             "sessions": sessions,
             "latency_ms": {"p50": sessions[0]["p50_ms"], "p99": sessions[0]["p99_ms"],
                            "at_offered_per_s": sessions[0]["offered_per_s"]},
@@ -700,18 +801,45 @@ def run_serve(args, rank, world, local):
         F.fem_destroy_mesh(h_)
 
 
+def plain_path_on_trace(F, handles, pool, kinds, arrivals, picks, opt, limit_s):
+    """One fem_solve per request on the trace, in arrival order, in real time."""
+    lat, done, t_end = [], 0, None
+    t0 = time.perf_counter()
+    outs = {k: np.zeros((m.n_nodes, 3)) for k, m in enumerate(pool)}
+    frc = np.zeros((20, 3))
+    for a, p_ in zip(arrivals, picks):
+        now = time.perf_counter() - t0
+        if now > limit_s:
+            break
+        if now < a:
+            time.sleep(a - now)
+        k, d = kinds[p_]
+        F.fem_set_indenter(handles[k], d.shape, d.pose, np.asarray(d.params), d.direction, d.depth_schedule)
+        F.fem_solve(handles[k], d.n_steps, TOL, opt, outs[k], frc[:d.n_steps], None, check=False)
+        t_end = time.perf_counter() - t0
+        lat.append(1000.0 * (t_end - a))
+        done += 1
+    first = float(arrivals[0]) if len(arrivals) else 0.0
+    return {"completed": done, "throughput": done / (t_end - first) if done > 1 and t_end > first else None,
+            "p50_ms": percentile(lat, 0.5), "p99_ms": percentile(lat, 0.99)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["fingertip", "dynamic", "calibrated", "friction", "batch", "uneven",
-                                           "serve"], default="fingertip")
+    ap.add_argument("--workload", choices=["batch", "fingertip", "dynamic", "calibrated", "friction", "uneven",
+                                           "serve"], default="batch")
+    ap.add_argument("--fp16-tangent", action="store_true",
+                    help="batched workloads: store the tangent in FP16 with a per-tet scale")
+    ap.add_argument("--e2e-steps", type=int, default=3,
+                    help="batched workloads: end-to-end steps timed (at most --steps)")
     ap.add_argument("--rates", type=float, nargs="+", default=[1.0, 2.0, 4.0, 8.0, 16.0],
                     help="offered request rates (req/s) of the serve workload")
-    ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--drain-seconds", type=float, default=90.0)
     ap.add_argument("--serve-class-cap", type=int, default=64,
                     help="largest CTA group of the request server (power of two)")
@@ -724,12 +852,12 @@ def main():
                     help="solves per step of the batched workloads (default 256 / 64)")
     args = ap.parse_args()
     if args.n_solves is None:
-        args.n_solves = 256 if args.workload == "batch" else 64
+        args.n_solves = 64 if args.workload == "uneven" else 256
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
     elif args.workload in VARIANTS:
-        run_cuda(args, rank, world, local)
+        run_single(args, rank, world, local)
     elif args.workload == "serve":
         run_serve(args, rank, world, local)
     else:

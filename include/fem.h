@@ -162,11 +162,15 @@ typedef struct {
     double  kernel_ms;                      /* device time of the solve kernel          */
     int32_t exact_newton_iters;             /* Newton iterations on the exact tangent   */
     double  phase_ms[10];                   /* kernel time split (CTA 0 clock shares):
-                                               eval, tangent, pcg init, pcg reduce+halo,
-                                               pcg tangent product, pcg vector update,
-                                               pcg grid barrier, total, pcg scalars,
-                                               pcg gather. fem_solve_batch: fractions
-                                               of that solve's own time instead        */
+                                               eval (FP64 residual and energy passes),
+                                               tangent (build + block-Jacobi), pcg init,
+                                               pcg dot reductions, tangent products'
+                                               element part (PCG and preconditioner),
+                                               pcg and preconditioner vector updates,
+                                               halo exchange waits, total, pcg scalars,
+                                               tangent products' node gathers.
+                                               fem_solve_batch: fractions of that
+                                               solve's own time instead                */
     double  phase_max_ms[10];               /* the same phases, largest over CTAs       */
     double  phase_min_ms[10];               /* the same phases, smallest over CTAs      */
                                             /* (both 0 in fem_solve_batch)              */

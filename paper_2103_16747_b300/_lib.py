@@ -37,8 +37,8 @@ FEM_SPHERE, FEM_CYLINDER, FEM_BOX, FEM_PLANE = 0, 1, 2, 3
 FEM_MAX_STEPS = 256
 FEM_TANGENT_PROJECTED, FEM_TANGENT_EXACT, FEM_TANGENT_ADAPTIVE, FEM_TANGENT_ABS = 0, 1, 2, 3
 FEM_BATCH_AUTO, FEM_BATCH_GROUPS, FEM_BATCH_CLUSTERS = 0, 1, 2
-PHASES = ("eval", "tangent", "pcg_init", "pcg_reduce", "pcg_matvec", "pcg_update", "pcg_barrier", "total",
-          "pcg_scalar", "pcg_gather")
+PHASES = ("eval", "tangent", "pcg_init", "pcg_reduce", "product_element", "vector_update", "halo_wait", "total",
+          "pcg_scalar", "product_gather")
 
 # Every symbol include/fem.h declares.
 EXPORTS = ("fem_default_options", "fem_create_mesh", "fem_set_indenter", "fem_set_dirichlet_values",

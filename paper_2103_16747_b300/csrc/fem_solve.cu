@@ -956,9 +956,12 @@ __device__ __forceinline__ bool exchange_halo(Ctx& C, const MeshDev& M, const Wo
 // whenever the top bounds the spectrum (the clamped element tangents satisfy
 // K_e <= 4 blockdiag(K_e), and the exact tangent lies below the clamped one).
 // Leaves u in C.ucg and C.lm (owned) and publishes it at a new epoch.
+// tp: phase timer of the caller (thread 0 of the timing CTA): the products'
+// element and gather parts and the halo waits go to their own phases, the
+// vector updates to PH_CG_UPDATE.
 template <bool CL>
 __device__ bool apply_precond(Ctx& C, const MeshDev& M, const WorkDev& W, const SolveParams& P, int& ep,
-                              long long& products) {
+                              long long& products, long long* tp) {
   const int deg = P.cheb_deg > 1 ? P.cheb_deg : 1;
   const float theta = P.cheb_theta, delta = P.cheb_delta;
   const float sigma = deg > 1 ? theta / delta : 1.f;
@@ -981,8 +984,10 @@ __device__ bool apply_precond(Ctx& C, const MeshDev& M, const WorkDev& W, const 
     if constexpr (!CL) publish_node(C, M, W, i, z, ep);
   }
   for (int j = 1; j < deg; ++j) {
+    tock(C, PH_CG_UPDATE, *tp);
     if (!exchange_halo<CL>(C, M, W, ep, P.timeout_ns)) return false;
-    matvec_pass(C, M);   // acc = element tangent applied to z
+    tock(C, PH_CG_BARRIER, *tp);
+    matvec_pass(C, M, tp);   // acc = element tangent applied to z
     ++products;
     // the owners overwrite their shared z below: every peer has read it
     if constexpr (CL) cluster_sync();
@@ -1038,7 +1043,7 @@ __device__ bool pcg(Ctx& C, const MeshDev& M, const WorkDev& W, const SolveParam
     }
   }
   __syncthreads();
-  if (!apply_precond<CL>(C, M, W, P, ep, products)) return false;
+  if (!apply_precond<CL>(C, M, W, P, ep, products, &t)) return false;
   tock(C, PH_CG_INIT, t);
   float gamma_prev = 1.f, alpha_prev = 1.f, rr0 = 0.f;
   const float eta2 = (float)(eta * eta), abs2 = (float)(abs_tol * abs_tol);
@@ -1123,7 +1128,7 @@ __device__ bool pcg(Ctx& C, const MeshDev& M, const WorkDev& W, const SolveParam
     // the peers read the shared u of this iteration before the reduction
     // barrier above, so the preconditioner may overwrite it now
     __syncthreads();
-    if (!apply_precond<CL>(C, M, W, P, ep, products)) return false;
+    if (!apply_precond<CL>(C, M, W, P, ep, products, &t)) return false;
     tock(C, PH_CG_UPDATE, t);
   }
   iters = it;
