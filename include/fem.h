@@ -179,6 +179,11 @@ typedef struct {
     double  residual_per_step[FEM_MAX_STEPS];
     int64_t tangent_products;               /* element-tangent products (PCG and     */
                                             /* preconditioner) of the whole solve    */
+    double  step_end_ms[FEM_MAX_STEPS];     /* device time from the solve's start to */
+                                            /* the end of each load step (global     */
+                                            /* timer of the solve's first CTA): the  */
+                                            /* per-step timeline inside the one      */
+                                            /* persistent launch                     */
 } fem_stats;
 
 typedef struct {

@@ -74,7 +74,8 @@ class fem_stats(C.Structure):
                 ("phase_min_ms", C.c_double * 10),
                 ("newton_per_step", C.c_int32 * FEM_MAX_STEPS),
                 ("cg_per_step", C.c_int32 * FEM_MAX_STEPS),
-                ("residual_per_step", C.c_double * FEM_MAX_STEPS), ("tangent_products", C.c_int64)]
+                ("residual_per_step", C.c_double * FEM_MAX_STEPS), ("tangent_products", C.c_int64),
+                ("step_end_ms", C.c_double * FEM_MAX_STEPS)]
 
 
 class fem_indenter(C.Structure):

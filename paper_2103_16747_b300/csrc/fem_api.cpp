@@ -1620,6 +1620,7 @@ static int fem_solve_body(fem_mesh* m, int32_t load_steps, double tol, const fem
       stats->newton_per_step[k] = hst.newton_per_step[k];
       stats->cg_per_step[k] = hst.cg_per_step[k];
       stats->residual_per_step[k] = hst.residual_per_step[k];
+      stats->step_end_ms[k] = hst.step_end_ms[k];
     }
   }
   int code = FEM_OK;

@@ -543,6 +543,7 @@ static int fem_batch_run_body(fem_batch* b, const fem_indenter* ind, double tol,
         st.newton_per_step[k] = h.newton_per_step[k];
         st.cg_per_step[k] = h.cg_per_step[k];
         st.residual_per_step[k] = h.residual_per_step[k];
+        st.step_end_ms[k] = h.step_end_ms[k];
       }
     }
   }

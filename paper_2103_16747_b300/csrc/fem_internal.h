@@ -69,6 +69,8 @@ struct StatsDev {
   int newton_per_step[kMaxSteps];
   int cg_per_step[kMaxSteps];
   double residual_per_step[kMaxSteps];
+  double step_end_ms[kMaxSteps];    // globaltimer of the leader at the end of each load step, from the
+                                    // solve's start
 };
 
 struct WorkDev {

@@ -252,6 +252,7 @@ void finish(fem_server* v, int slot) {
     st.newton_per_step[k] = h.newton_per_step[k];
     st.cg_per_step[k] = h.cg_per_step[k];
     st.residual_per_step[k] = h.residual_per_step[k];
+    st.step_end_ms[k] = h.step_end_ms[k];
   }
   q.t_done = now_s();
   st.kernel_ms = 1000.0 * (q.t_done - q.t_admit);

@@ -1256,6 +1256,7 @@ template <bool CL>
 __device__ bool solve_body(Ctx& C, const MeshDev& M, const WorkDev& W, const SolveParams& P, Barrier& gb, int& ep,
                            unsigned long long& n_pub) {
   const long long t_start = tick(C);
+  const unsigned long long ns_start = (C.part == 0 && threadIdx.x == 0) ? global_ns() : 0ull;
   Bufs bf{0};
   StatsDev* st = W.stats;
   const bool leader = C.part == 0 && threadIdx.x == 0;
@@ -1439,6 +1440,7 @@ __device__ bool solve_body(Ctx& C, const MeshDev& M, const WorkDev& W, const Sol
       st->newton_per_step[step - 1] = it;
       st->cg_per_step[step - 1] = cg_step;
       st->residual_per_step[step - 1] = rn;
+      st->step_end_ms[step - 1] = 1e-6 * (double)(global_ns() - ns_start);
       W.step_force[3 * (step - 1)] = fs[0];
       W.step_force[3 * (step - 1) + 1] = fs[1];
       W.step_force[3 * (step - 1) + 2] = fs[2];
