@@ -53,6 +53,10 @@ extern "C" {
 #define FEM_ERR_BUSY           -9   /* request server: not running, or its admission queue is full */
 #define FEM_PENDING             1   /* request server: the request has not finished yet */
 #define FEM_ERR_TOO_LARGE      -8   /* mesh does not fit the single-solve kernel */
+#define FEM_ERR_CHECK         -10   /* checked build (FEM_CHECKED) only: a kernel found an index
+                                       of the mesh's device arrays out of range, or a NaN/Inf
+                                       element force or stored tangent; the access was skipped,
+                                       outputs are not to be trusted, the message names the check */
 
 /* ---------------------------------------------------------------- shapes */
 #define FEM_SPHERE   0   /* params[0] = radius; centre = pose origin                  */
@@ -441,6 +445,18 @@ void fem_destroy_mesh(fem_mesh* mesh);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char* fem_last_error(void);
+
+/*
+ * 1 if this library was built with FEM_CHECKED, else 0. The checked build
+ * (libfem_b300_checked.so; the Python binding loads it when the environment
+ * sets FEM_B300_CHECKED=1) bounds every index its kernels read from the mesh's
+ * device arrays and checks element forces and stored tangents for NaN/Inf; a
+ * failed check skips the access and the entry point that ran the kernel
+ * returns FEM_ERR_CHECK (fem_solve, the diagnostics, fem_batch_run,
+ * fem_solve_batch; the request server reports it from fem_server_stop). It
+ * stands in for a memory checker: the production build contains none of it.
+ */
+int fem_build_checked(void);
 
 /* Sizes and derived constants of a mesh (partitioning, shared memory, h_bar). */
 int fem_mesh_info_get(const fem_mesh* mesh, fem_mesh_info* info);

@@ -14,7 +14,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libfem_b300.so")
+# FEM_B300_CHECKED=1 selects the checked build (bounds- and NaN-checked kernels)
+LIB_PATH = os.path.join(_HERE, "libfem_b300_checked.so" if os.environ.get("FEM_B300_CHECKED") == "1"
+                        else "libfem_b300.so")
 
 FEM_OK = 0
 FEM_MODEL_NEO_HOOKEAN = 0
@@ -27,11 +29,12 @@ FEM_ERR_NOT_CONVERGED = -5
 FEM_ERR_TIMEOUT = -6
 FEM_ERR_CUDA = -7
 FEM_ERR_TOO_LARGE = -8
+FEM_ERR_CHECK = -10
 FEM_ERR_BUSY = -9
 FEM_PENDING = 1
 ERR_NAMES = {0: "FEM_OK", -1: "FEM_ERR_ARG", -2: "FEM_ERR_DEGENERATE_TET", -3: "FEM_ERR_NONFINITE",
              -4: "FEM_ERR_OOM", -5: "FEM_ERR_NOT_CONVERGED", -6: "FEM_ERR_TIMEOUT", -7: "FEM_ERR_CUDA",
-             -8: "FEM_ERR_TOO_LARGE", -9: "FEM_ERR_BUSY", 1: "FEM_PENDING"}
+             -8: "FEM_ERR_TOO_LARGE", -9: "FEM_ERR_BUSY", -10: "FEM_ERR_CHECK", 1: "FEM_PENDING"}
 
 FEM_SPHERE, FEM_CYLINDER, FEM_BOX, FEM_PLANE = 0, 1, 2, 3
 FEM_MAX_STEPS = 256
@@ -42,7 +45,8 @@ PHASES = ("eval", "tangent", "pcg_init", "pcg_reduce", "product_element", "vecto
 
 # Every symbol include/fem.h declares.
 EXPORTS = ("fem_default_options", "fem_create_mesh", "fem_set_indenter", "fem_set_dirichlet_values",
-           "fem_solve", "fem_solve_batch", "fem_destroy_mesh", "fem_last_error", "fem_mesh_info_get", "fem_repartition",
+           "fem_solve", "fem_solve_batch", "fem_destroy_mesh", "fem_last_error", "fem_build_checked",
+           "fem_mesh_info_get", "fem_repartition",
            "fem_eval_residual", "fem_eval_residual_noalloc", "fem_apply_tangent",
            "fem_debug_barrier_timeout", "fem_debug_pcg_dots", "fem_debug_reciprocals", "fem_debug_plan_check", "fem_batch_create", "fem_batch_run", "fem_batch_info_get",
            "fem_batch_destroy", "fem_batch_tune", "fem_server_create", "fem_server_start", "fem_server_submit",
@@ -130,6 +134,7 @@ def _load():
         "fem_solve_batch": (C.c_int, [P, P, C.c_int32, C.c_double, C.POINTER(fem_options), P, P, P]),
         "fem_destroy_mesh": (None, [P]),
         "fem_last_error": (C.c_char_p, []),
+        "fem_build_checked": (C.c_int, []),
         "fem_mesh_info_get": (C.c_int, [P, C.POINTER(fem_mesh_info)]),
         "fem_repartition": (C.c_int, [P, C.c_int32]),
         "fem_eval_residual": (C.c_int, [P, P, C.c_int32, C.POINTER(fem_options), P, P, P]),

@@ -52,6 +52,24 @@ int fail(int code, const char* fmt, ...) {
   return code;
 }
 
+int check_status(const char* where) {
+  if (!kCheckedBuild) return FEM_OK;
+  unsigned flags = 0;
+  long long value = 0;
+  const cudaError_t e = take_check_word(&flags, &value);
+  if (e != cudaSuccess) return cuda_fail(e, "check word");
+  if (!flags) return FEM_OK;
+  static const char* names[] = {"local node id", "node->tet list entry", "halo node", "mesh tet id",
+                                "owner list entry", "material id", "non-finite element value"};
+  std::string what;
+  for (int b = 0; b < 7; ++b)
+    if (flags & (1u << b)) {
+      if (!what.empty()) what += ", ";
+      what += names[b];
+    }
+  return fail(FEM_ERR_CHECK, "%s: kernel checks failed (%s; first value %lld)", where, what.c_str(), value);
+}
+
 int cuda_fail(cudaError_t e, const char* what) {
   if (e == cudaErrorMemoryAllocation)
     return fail(FEM_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
@@ -983,6 +1001,8 @@ void fem_default_options(fem_options* opt) {
 
 const char* fem_last_error(void) { return g_err.c_str(); }
 
+int fem_build_checked(void) { return kCheckedBuild ? 1 : 0; }
+
 void fem_destroy_mesh(fem_mesh* m) {
   if (!m) return;
   for (void* q : m->part_owned) cudaFree(q);
@@ -1555,7 +1575,7 @@ static int run_kernel(fem_mesh* m, const WorkDev& W, const SolveParams& P, float
   CUDA_TRY(cudaMemcpyAsync(&abort_flag, m->work.abort_flag, sizeof(int), cudaMemcpyDeviceToHost, s), "flag copy");
   CUDA_TRY(cudaStreamSynchronize(s), "solve kernel");
   if (abort_flag) return fail(FEM_ERR_TIMEOUT, "a grid barrier wait exceeded its bound");
-  return FEM_OK;
+  return check_status("solve kernel");
 }
 
 static int copy_out_nodes(fem_mesh* m, const double* d_src, double* out) {
@@ -1755,6 +1775,7 @@ static int fem_eval_residual_noalloc_body(fem_mesh* m, const double* u, int32_t 
   }
   CUDA_TRY(cudaStreamSynchronize(s), "evaluation");
   if (abort_flag) return fail(FEM_ERR_TIMEOUT, "a grid barrier wait exceeded its bound");
+  if ((rc = check_status("evaluation kernel"))) return rc;
   if (out_energy) {
     out_energy[0] = hst.elastic;
     out_energy[1] = hst.contact_energy;

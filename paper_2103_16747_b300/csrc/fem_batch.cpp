@@ -508,6 +508,7 @@ static int fem_batch_run_body(fem_batch* b, const fem_indenter* ind, double tol,
                                cudaMemcpyDefault, s), "output");
   }
   CUDA_TRY(cudaStreamSynchronize(s), "batch");
+  if (int crc = check_status("batched kernel")) return crc;
   float ms = 0.f;
   cudaEventElapsedTime(&ms, b->ev0, b->ev1);
   int code = FEM_OK;

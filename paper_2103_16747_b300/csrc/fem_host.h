@@ -75,6 +75,10 @@ namespace host {
 std::string& last_error();                 // this thread's message (fem_last_error)
 int fail(int code, const char* fmt, ...);  // sets the message, returns code
 int cuda_fail(cudaError_t e, const char* what);
+// FEM_CHECKED build: FEM_ERR_CHECK with the failed checks named if a kernel
+// check fired since the last call (the word is cleared); FEM_OK otherwise and
+// always in the production build. Call after the launches have completed.
+int check_status(const char* where);
 SmemLayout plan_layout(const PartDims& d, int budget);
 void set_precond(const fem_options& o, SolveParams& P);
 // Time stepping (inv_dt = 1/dt, density; dt = 0: quasi-static) and friction

@@ -18,6 +18,23 @@ constexpr int kTanVec = 8;        // float4 groups of the stored per-tet tangent
 
 enum Mode : int { MODE_SOLVE = 0, MODE_EVAL = 1, MODE_APPLY = 2, MODE_BARRIER_TEST = 3, MODE_DOT = 4 };
 
+// Check word bits of the FEM_CHECKED build (which kind of index or value failed).
+enum CheckBit : unsigned {
+  CHK_LOCAL = 1u,        // local node id of a part tet >= the part's local nodes
+  CHK_CSR = 2u,          // node->tet list entry outside the part's tets (or the chunk)
+  CHK_HALO = 4u,         // halo node id or halo source outside the mesh / the cluster
+  CHK_TET = 8u,          // mesh tet id of a part tet >= n_tets
+  CHK_OWNER = 16u,       // owner-list entry outside the part's tets
+  CHK_MATERIAL = 32u,    // material id >= n_materials
+  CHK_NONFINITE = 64u,   // NaN/Inf in element forces (valid tets) or in a stored tangent
+};
+
+#ifdef FEM_CHECKED
+constexpr bool kCheckedBuild = true;
+#else
+constexpr bool kCheckedBuild = false;
+#endif
+
 enum Status : int {
   ST_OK = 0, ST_NOT_CONVERGED = 1, ST_LINESEARCH = 2, ST_NONFINITE = 3, ST_TIMEOUT = 4,
 };
@@ -220,6 +237,10 @@ cudaError_t launch_reciprocals(const double* x, int n, double* rcp, double* rsq,
 cudaError_t launch_stress(const int4* tets, const double* dminv, const int* mat, const double* lame,
                           const int* mat_model, const double* u, const int* tet_perm, int n_tets, double* sig,
                           double* vm, cudaStream_t s);
+
+// Checked build: read and clear the module's check word (the flags and the
+// first failing value); the production build reports 0 (fem_solve.cu).
+cudaError_t take_check_word(unsigned* flags, long long* value);
 
 // Fixed scratch block for fem_eval_residual_noalloc (fem_solve.cu).
 constexpr size_t kNoAllocScratchBytes = 8u << 20;

@@ -793,7 +793,7 @@ static int fem_server_stop_body(fem_server* v) {
   v->pending.clear();
   v->cv.notify_all();
   if (e != cudaSuccess) return cuda_fail(e, "server kernel");
-  return FEM_OK;
+  return check_status("server kernel");
 }
 
 int fem_server_stop(fem_server* v) {

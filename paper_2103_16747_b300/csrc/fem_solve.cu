@@ -160,6 +160,33 @@ struct Ctx {
   long long cyc[PH_N];
 };
 
+// ------------------------------------------------------------ checked build
+// Built with FEM_CHECKED, the kernels bound every index they read from the
+// mesh's device arrays (local node ids of a part tet, node->tet list entries,
+// halo node ids and sources, part-tet and owner lists, material ids) before
+// using it, and check the element forces and stored tangents for NaN/Inf. A
+// failed check sets a bit of the module's check word (the first failing value
+// is kept beside it) and the access goes to index 0 instead, so a corrupt
+// input becomes an error status the host reports (FEM_ERR_CHECK), never an
+// out-of-bounds access. The production build compiles none of this.
+#ifdef FEM_CHECKED
+__device__ unsigned int g_check_flags;
+__device__ long long g_check_value;
+__device__ __noinline__ int check_fail(long long v, unsigned bit) {
+  if (atomicOr(&g_check_flags, bit) == 0u) g_check_value = v;
+  return 0;
+}
+__device__ __forceinline__ int chk(int v, int n, unsigned bit) {
+  return (unsigned)v < (unsigned)n ? v : check_fail(v, bit);
+}
+__device__ __forceinline__ void chk_finite(double x, unsigned bit) {
+  if (!isfinite(x)) check_fail(0, bit);
+}
+#else
+__device__ __forceinline__ int chk(int v, int, unsigned) { return v; }
+__device__ __forceinline__ void chk_finite(double, unsigned) {}
+#endif
+
 __device__ __forceinline__ long long tick(const Ctx& C) { return C.timer ? clock64() : 0ll; }
 __device__ __forceinline__ void tock(Ctx& C, int ph, long long& t) {
   if (C.timer) {
@@ -170,7 +197,7 @@ __device__ __forceinline__ void tock(Ctx& C, int ph, long long& t) {
 }
 
 __device__ __forceinline__ int local_to_global(const Ctx& C, const MeshDev& M, int l) {
-  return l < C.n_own ? C.node0 + l : M.halo_nodes[C.halo0 + l - C.n_own];
+  return l < C.n_own ? C.node0 + l : chk(M.halo_nodes[C.halo0 + l - C.n_own], M.n_nodes, CHK_HALO);
 }
 
 // Newton-level synchronisation of all parts; global-memory writes before it
@@ -272,7 +299,7 @@ __device__ void load_local_positions(Ctx& C, const MeshDev& M, const WorkDev& W,
       a0 = C.u[3 * l]; a1 = C.u[3 * l + 1]; a2 = C.u[3 * l + 2];
       d0 = C.x[3 * l]; d1 = C.x[3 * l + 1]; d2 = C.x[3 * l + 2];
     } else {
-      const int g = M.halo_nodes[C.halo0 + l - C.n_own];
+      const int g = chk(M.halo_nodes[C.halo0 + l - C.n_own], M.n_nodes, CHK_HALO);
       a0 = __ldcg(W.u + 3 * g); a1 = __ldcg(W.u + 3 * g + 1); a2 = __ldcg(W.u + 3 * g + 2);
       if (alpha != 0.0) {   // the direction array exists only where a step is taken
         const float4 d = __ldcg(W.dpub + g);
@@ -309,7 +336,7 @@ __device__ __forceinline__ void gather_chunk(Ctx& C, int CH, const T* buf, int c
 #pragma unroll 4
       for (int j = j0; j < j1; ++j) {
         const unsigned e = C.lcsr[j];
-        s += col[(int)(e & 3u) * NV * CH + (int)(e >> 2)];
+        s += col[(int)(e & 3u) * NV * CH + chk((int)(e >> 2), C.n_pt, CHK_CSR)];
       }
       acc[idx] = s;
     }
@@ -325,7 +352,7 @@ __device__ __forceinline__ void gather_chunk(Ctx& C, int CH, const T* buf, int c
       const unsigned e = C.lcsr[j];
       const int lt = (int)(e >> 2);
       if (lt >= c1) break;
-      s += buf[((int)(e & 3u) * NV + k) * CH + (lt - c0)];
+      s += buf[((int)(e & 3u) * NV + k) * CH + chk(lt - c0, CH, CHK_CSR)];
       ++j;
     }
     acc[idx] = s;
@@ -426,7 +453,8 @@ __device__ __forceinline__ void eval_part_tet(const Ctx& C, const MeshDev& M, in
                                               double& energy, double& J) {
   const int e = C.t0 + t;
   const ushort4 ln = C.ptn[t];
-  const int li[4] = {ln.x, ln.y, ln.z, ln.w};
+  const int li[4] = {chk(ln.x, C.n_loc, CHK_LOCAL), chk(ln.y, C.n_loc, CHK_LOCAL), chk(ln.z, C.n_loc, CHK_LOCAL),
+                     chk(ln.w, C.n_loc, CHK_LOCAL)};
   double uu[4][3];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -435,9 +463,19 @@ __device__ __forceinline__ void eval_part_tet(const Ctx& C, const MeshDev& M, in
   double Dm[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) Dm[k] = M.pt_dminv[(size_t)k * M.total_pt + e];
-  const int mat = M.pt_info[e] & 0xffff;
+  const int mat = chk(M.pt_info[e] & 0xffff, M.n_materials, CHK_MATERIAL);
   const double mu = M.lame[2 * mat], lam = M.lame[2 * mat + 1];
   elem_eval_f64(uu, Dm, M.pt_vol[e], mu, lam, M.mat_model[mat], f, energy, J);
+#ifdef FEM_CHECKED
+  // an inverted tet (finite J <= 0) is a state the line search rejects, not an
+  // error; anything else must give finite forces
+  if (!(J <= 0.0)) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) chk_finite(f[a][k], CHK_NONFINITE);
+  }
+#endif
 }
 
 // FP64 energy, residual R = dPi/du and contact at ut = u + alpha*dx. Leaves
@@ -470,12 +508,12 @@ __device__ bool eval_pass(Ctx& C, const MeshDev& M, const WorkDev& W, const Solv
   const int n_ot = M.part_own_begin[C.part + 1] - ob0;
   const size_t nT = (size_t)M.n_tets;
   for (int j = threadIdx.x; j < n_ot; j += blockDim.x) {
-    const int t = M.pt_own[ob0 + j];
+    const int t = chk(M.pt_own[ob0 + j], C.n_pt, CHK_OWNER);
     double f[4][3], energy, J;
     eval_part_tet(C, M, t, f, energy, J);
     if (!(J > 0.0) || !isfinite(energy)) bad += 1.0;
     e_el += energy;
-    double* dst = W.tet_f + (size_t)M.pt_tet[C.t0 + t];
+    double* dst = W.tet_f + (size_t)chk(M.pt_tet[C.t0 + t], M.n_tets, CHK_TET);
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -490,7 +528,7 @@ __device__ bool eval_pass(Ctx& C, const MeshDev& M, const WorkDev& W, const Solv
     const int c1 = min(c0 + CH, C.n_pt);
     for (int t = c0 + threadIdx.x; t < c1; t += blockDim.x) {
       if (single && (M.pt_info[C.t0 + t] >> 16)) continue;   // owned: staged above
-      const double* src = W.tet_f + (size_t)M.pt_tet[C.t0 + t];
+      const double* src = W.tet_f + (size_t)chk(M.pt_tet[C.t0 + t], M.n_tets, CHK_TET);
 #pragma unroll
       for (int q = 0; q < 12; ++q) C.chunkd[q * CH + (t - c0)] = __ldcg(src + q * nT);
     }
@@ -573,7 +611,8 @@ __device__ void tangent_pass(Ctx& C, const MeshDev& M, int mode) {
     for (int t = c0 + threadIdx.x; t < c1; t += blockDim.x) {
       const int e = C.t0 + t;
       const ushort4 ln = C.ptn[t];
-      const int li[4] = {ln.x, ln.y, ln.z, ln.w};
+      const int li[4] = {chk(ln.x, C.n_loc, CHK_LOCAL), chk(ln.y, C.n_loc, CHK_LOCAL),
+                         chk(ln.z, C.n_loc, CHK_LOCAL), chk(ln.w, C.n_loc, CHK_LOCAL)};
       float Ds[3][3];
 #pragma unroll
       for (int c = 0; c < 3; ++c)
@@ -588,12 +627,16 @@ __device__ void tangent_pass(Ctx& C, const MeshDev& M, int mode) {
 #pragma unroll
         for (int j = 0; j < 3; ++j)
           F[3 * i + j] = (i == j ? 1.f : 0.f) + Ds[i][0] * Dm[j] + Ds[i][1] * Dm[3 + j] + Ds[i][2] * Dm[6 + j];
-      const int mat = M.pt_info[e] & 0xffff;
+      const int mat = chk(M.pt_info[e] & 0xffff, M.n_materials, CHK_MATERIAL);
       float T[32];
       float dg[4][6];
       tangent_build(F, (float)M.lame[2 * mat], (float)M.lame[2 * mat + 1], (float)M.pt_vol[e], Dm,
                     mode, M.mat_model[mat], T, dg);
       T[30] = 0.f; T[31] = 0.f;
+#ifdef FEM_CHECKED
+#pragma unroll
+      for (int k = 0; k < 30; ++k) chk_finite(T[k], CHK_NONFINITE);
+#endif
       if (C.tan16) {
         // FP16, each value over the tet's largest magnitude (so any stiffness
         // fits), 8 halves per 16-byte word; the scale in the last word
@@ -696,7 +739,8 @@ __device__ void matvec_pass(Ctx& C, const MeshDev& M, long long* tp = nullptr) {
         }
       }
       float p[4][3];
-      const int li[4] = {ln.x, ln.y, ln.z, ln.w};
+      const int li[4] = {chk(ln.x, C.n_loc, CHK_LOCAL), chk(ln.y, C.n_loc, CHK_LOCAL),
+                         chk(ln.z, C.n_loc, CHK_LOCAL), chk(ln.w, C.n_loc, CHK_LOCAL)};
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
         const float4 q = C.lm[li[a]];
@@ -794,7 +838,7 @@ __device__ bool load_halo_tagged(Ctx& C, const MeshDev& M, const WorkDev& W, int
   const unsigned long long* src = W.vpub + (size_t)(ep & 1) * M.n_nodes * 3;
   int failed = 0;
   for (int l = C.n_own + threadIdx.x; l < C.n_loc && !failed; l += blockDim.x) {
-    const unsigned long long* q = src + (size_t)M.halo_nodes[C.halo0 + l - C.n_own] * 3;
+    const unsigned long long* q = src + (size_t)chk(M.halo_nodes[C.halo0 + l - C.n_own], M.n_nodes, CHK_HALO) * 3;
     unsigned long long a, b, c, t0 = 0;
     unsigned it = 0;
     for (;;) {
@@ -891,11 +935,12 @@ __device__ bool reduce_cg_slots(Ctx& C, const WorkDev& W, unsigned long long n_p
 // memory after the barrier that follows every part's update. An owner writes
 // its entries again only after the next reduction barrier, which every reader
 // reaches after its reads.
-__device__ void load_halo_cluster(Ctx& C) {
+__device__ void load_halo_cluster(Ctx& C, const MeshDev& M) {
   cluster_sync();
   for (int l = C.n_own + threadIdx.x; l < C.n_loc; l += blockDim.x) {
     const unsigned src = C.hsrc[l - C.n_own];
-    C.lm[l] = peer(C.lm, src >> 16)[src & 0xffffu];
+    C.lm[l] = peer(C.lm, (unsigned)chk((int)(src >> 16), C.nparts, CHK_HALO))[chk((int)(src & 0xffffu), M.max_own,
+                                                                                  CHK_HALO)];
   }
   __syncthreads();
 }
@@ -940,7 +985,7 @@ template <bool CL>
 __device__ __forceinline__ bool exchange_halo(Ctx& C, const MeshDev& M, const WorkDev& W, int ep,
                                               unsigned long long limit) {
   if constexpr (CL) {
-    load_halo_cluster(C);
+    load_halo_cluster(C, M);
     return true;
   } else {
     return load_halo_tagged(C, M, W, ep, limit);
@@ -1920,6 +1965,22 @@ unsigned long long device_clock_ns() {
 // device address; noalloc_scratch() looks the real address up once per
 // device, with that device current, and caches it.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+cudaError_t take_check_word(unsigned* flags, long long* value) {
+  *flags = 0;
+  *value = 0;
+#ifdef FEM_CHECKED
+  cudaError_t e = cudaMemcpyFromSymbol(flags, g_check_flags, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemcpyFromSymbol(value, g_check_value, sizeof(long long));
+  if (e == cudaSuccess && *flags) {
+    const unsigned zero = 0;
+    e = cudaMemcpyToSymbol(g_check_flags, &zero, sizeof(zero));
+  }
+  return e;
+#else
+  return cudaSuccess;
+#endif
+}
 
 cudaError_t noalloc_scratch(int device, void** ptr) {
   static std::mutex mu;
