@@ -174,6 +174,11 @@ def fem_last_error() -> str:
     return lib.fem_last_error().decode()
 
 
+def fem_build_checked() -> int:
+    """1 for the FEM_CHECKED build (bounds- and NaN-checked kernels), else 0."""
+    return int(lib.fem_build_checked())
+
+
 def _check(rc):
     if rc != FEM_OK:
         raise FemError(rc, fem_last_error())

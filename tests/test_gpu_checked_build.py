@@ -45,7 +45,8 @@ for name, (m, ind, ck) in cases.items():
     opt = F.fem_default_options()
     opt.c_kappa = ck
     r = s.solve(1e-8 if name != "cube" else 1e-6, opt, check=False)
-    ref = Problem(m, ind, c_kappa=ck).solve(tol=1e-12)
+    ref = Problem(m, ind, c_kappa=ck).solve(tol=1e-12 if name == "one_tet" else 1e-10)
+    assert ref.converged, name
     out[name] = {"rc": int(r["rc"]), "rel_u": rel(r["u"], ref.u), "msg": F.fem_last_error()}
     s.close()
 # both batched engines on two cube jobs
