@@ -760,6 +760,14 @@ SmemLayout plan_layout(const PartDims& d, int budget) {
       L.hf = g | kInGlobal;
       g = align_up(g + 24 * d.max_own, 16);
     }
+    // indenter-curvature blocks of the contact Hessian: read only by products
+    // on the exact tangent, placed on the same terms
+    if (fits(24 * d.max_own)) {
+      L.hx = take(24 * d.max_own);
+    } else {
+      L.hx = g | kInGlobal;
+      g = align_up(g + 24 * d.max_own, 16);
+    }
     L.ptn = place_opt(8 * d.max_pt);
     const int lptr_bytes = align_up(4 * (d.max_own + 1), 16);
     if (fits(lptr_bytes + 4 * d.max_lcsr)) {

@@ -144,7 +144,7 @@ __host__ __device__ inline int align_up(int v, int a) { return (v + a - 1) / a *
 
 struct SmemLayout {
   int lm, red, chunk;                             // always shared
-  int acc, x, r, ucg, w, s, p, minv, hc, mask, cursor, ut, cd, mh2, hf;
+  int acc, x, r, ucg, w, s, p, minv, hc, mask, cursor, ut, cd, mh2, hf, hx;
   int tan, ptn, lptr, lcsr;                       // resident part data, or -1: read from global memory
   int chunk_tets;                                 // part tets per chunk of the evaluation passes
   int tan16;                                      // 1: the tangent is stored as FP16 with a per-tet

@@ -619,6 +619,40 @@ __device__ __forceinline__ void indenter_sdf(int shape, const double o[3], const
   for (int i = 0; i < 3; ++i) n[i] = R[3 * i] * nl[0] + R[3 * i + 1] * nl[1] + R[3 * i + 2] * nl[2];
 }
 
+// Curvature part of the penalty Hessian of a node inside the indenter (phi <
+// 0): k phi grad^2 phi, symmetric 3x3 as (xx xy xz yy yz zz). The Gauss-Newton
+// part k n n^T is applied separately. grad^2 phi is (I - n n^T) / rho for the
+// sphere and (I - a a^T - n n^T) / rho for the cylinder, rho the distance to
+// the centre / the axis; the box's and the plane's faces are flat (a node
+// inside the box is nearest to a face: no curvature). With phi < 0 the block
+// is negative semidefinite: it softens the contact across the normal, which
+// Gauss-Newton leaves out. Out of line: it runs only for penetrating nodes,
+// and inlined it would take registers from the whole solve kernel.
+static __device__ __noinline__ void indenter_curvature(int shape, const double* o, const double* R,
+                                                       const double* x, const double* n, double kphi,
+                                                       float* out) {
+#pragma unroll
+  for (int k = 0; k < 6; ++k) out[k] = 0.f;
+  if (shape != 0 && shape != 1) return;
+  double d[3] = {x[0] - o[0], x[1] - o[1], x[2] - o[2]};
+  const double ax[3] = {R[2], R[5], R[8]};
+  if (shape == 1) {
+    const double t = d[0] * ax[0] + d[1] * ax[1] + d[2] * ax[2];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d[k] -= t * ax[k];
+  }
+  const double rho = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  if (!(rho > 0.0)) return;
+  const double c = kphi / rho;
+  const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    double v = (ia[k] == ib[k] ? 1.0 : 0.0) - n[ia[k]] * n[ib[k]];
+    if (shape == 1) v -= ax[ia[k]] * ax[ib[k]];
+    out[k] = (float)(c * v);
+  }
+}
+
 // ------------------------------------------------------------------ FP32 pairs
 // Compensated FP32 pair ("double-float", two-sum): about 44 significant bits
 // from FP32 adds only. Used inside a CTA, where FP64 instructions would run on

@@ -141,6 +141,8 @@ struct Ctx {
   const double *X, *kb, *vl;
   float* mh2;                   // owned nodes: lumped mass / dt^2 (0 when quasi-static)
   float* hf;                    // owned nodes: friction Hessian block (xx xy xz yy yz zz)
+  float* hx;                    // owned nodes: indenter-curvature block of the contact Hessian
+  bool curv_on;                 // products include hx (exact tangent)
   bool fric_on;                 // friction in this solve
   double dc[3];                 // indenter translation over the current load step
   double *ut, *chunkd, *red;
@@ -559,6 +561,7 @@ __device__ bool eval_pass(Ctx& C, const MeshDev& M, const WorkDev& W, const Solv
     const double kp = C.kb[i] * P.c_kappa;
     double fcv[3] = {0.0, 0.0, 0.0};
     float h[3] = {0.f, 0.f, 0.f};
+    bool curved = false;
     if (kp > 0.0) {
       const double xx[3] = {C.X[3 * i] + C.ut[3 * i], C.X[3 * i + 1] + C.ut[3 * i + 1],
                             C.X[3 * i + 2] + C.ut[3 * i + 2]};
@@ -575,7 +578,13 @@ __device__ bool eval_pass(Ctx& C, const MeshDev& M, const WorkDev& W, const Solv
         v[EV_ACTIVE] += 1.0;
         const float sk = (float)sqrt(kp);
         h[0] = sk * (float)n[0]; h[1] = sk * (float)n[1]; h[2] = sk * (float)n[2];
+        indenter_curvature(P.shape, org, P.R, xx, n, kp * phi, C.hx + 6 * i);
+        curved = true;
       }
+    }
+    if (!curved) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) C.hx[6 * i + k] = 0.f;
     }
     if (C.fric_on) v[EV_CONTACT] += friction_node(C, P, i, fcv);
 #pragma unroll
@@ -767,8 +776,9 @@ __device__ __forceinline__ void apply_minv(const float* mi, const float v[3], fl
   out[2] = mi[2] * v[0] + mi[4] * v[1] + mi[5] * v[2];
 }
 
-// Contact Gauss-Newton term, lumped mass / dt^2 (dynamic stepping), friction
-// block and Dirichlet mask on the owned product.
+// Contact Gauss-Newton term (plus, on the exact tangent, the indenter's
+// curvature term), lumped mass / dt^2 (dynamic stepping), friction block and
+// Dirichlet mask on the owned product.
 __device__ __forceinline__ void finish_product(const Ctx& C, int i, const float v[3], float out[3]) {
   const float h0 = C.hc[3 * i], h1 = C.hc[3 * i + 1], h2 = C.hc[3 * i + 2];
   const float hv = h0 * v[0] + h1 * v[1] + h2 * v[2];
@@ -782,6 +792,12 @@ __device__ __forceinline__ void finish_product(const Ctx& C, int i, const float 
     a0 += f[0] * v[0] + f[1] * v[1] + f[2] * v[2];
     a1 += f[1] * v[0] + f[3] * v[1] + f[4] * v[2];
     a2 += f[2] * v[0] + f[4] * v[1] + f[5] * v[2];
+  }
+  if (C.curv_on) {
+    const float* q = C.hx + 6 * i;
+    a0 += q[0] * v[0] + q[1] * v[1] + q[2] * v[2];
+    a1 += q[1] * v[0] + q[3] * v[1] + q[4] * v[2];
+    a2 += q[2] * v[0] + q[4] * v[1] + q[5] * v[2];
   }
   out[0] = (mk & 1u) ? 0.f : a0;
   out[1] = (mk & 2u) ? 0.f : a1;
@@ -1238,6 +1254,8 @@ __device__ void setup_ctx(Ctx& C, const MeshDev& M, const WorkDev& W, const Smem
   C.cd = reinterpret_cast<float*>(at(L.cd));
   C.mh2 = reinterpret_cast<float*>(at(L.mh2));
   C.hf = reinterpret_cast<float*>(at(L.hf));
+  C.hx = reinterpret_cast<float*>(at(L.hx));
+  C.curv_on = false;
   C.mask = at(L.mask);
   C.cursor = reinterpret_cast<int*>(at(L.cursor));
   C.hsrc = M.halo_src + C.halo0;
@@ -1388,7 +1406,12 @@ __device__ bool solve_body(Ctx& C, const MeshDev& M, const WorkDev& W, const Sol
     int it = 0, it_pass0 = 0, pass = 1, cg_step = 0;
     bool ok = false;
     bool use_exact = P.tangent_mode == 1;
-    bool exact_banned = false;
+    // adaptive tangent: after the exact tangent fails (negative curvature, a
+    // shortened or failed line search) the projected one is used for ban_len
+    // iterations (doubling with each failure in the step) before exact is
+    // tried again
+    int exact_retry = 0, ban_len = 4;
+    int slow = 0;   // consecutive projected steps that cut the residual less than 2x
     for (;;) {
       if (!isfinite(rn)) { status = ST_NONFINITE; break; }
       if (rn <= P.tol * scale) {
@@ -1413,13 +1436,16 @@ __device__ bool solve_body(Ctx& C, const MeshDev& M, const WorkDev& W, const Sol
         rn_prev = rn;
         rn_step0 = rn;
         use_exact = P.tangent_mode == 1;
-        exact_banned = false;
+        exact_retry = it;
+        ban_len = 4;
+        slow = 0;
         continue;
       }
       if (it - it_pass0 >= P.max_newton) { status = ST_NOT_CONVERGED; break; }
       const int mode = P.tangent_mode == 3 ? 3 : (use_exact ? 1 : 0);
       long long t = tick(C);
       tangent_pass(C, M, mode);
+      C.curv_on = mode == 1;   // exact tangent: exact contact Hessian too
       tock(C, PH_TANGENT, t);
       double eta = P.cg_rtol_max;
       if (it > 0) {
@@ -1445,7 +1471,11 @@ __device__ bool solve_body(Ctx& C, const MeshDev& M, const WorkDev& W, const Sol
         }
         const double et = red_out[EV_ELASTIC] + red_out[EV_CONTACT];
         const bool valid = red_out[EV_BAD] == 0.0 && isfinite(et) && isfinite(red_out[EV_RR]);
-        if (valid && (rn <= 1e-3 * scale || et <= energy + 1e-4 * alpha * slope)) {
+        // near the solution (residual below 1e-3 scale) energy differences sit
+        // at roundoff and full steps are taken; a step on the exact tangent,
+        // which can be indefinite there, must in addition lower the residual
+        const bool near = rn <= 1e-3 * scale && (mode != 1 || red_out[EV_RR] < rn * rn);
+        if (valid && (near || et <= energy + 1e-4 * alpha * slope)) {
           accepted = true;
           energy = et;
           break;
@@ -1458,7 +1488,9 @@ __device__ bool solve_body(Ctx& C, const MeshDev& M, const WorkDev& W, const Sol
         if (mode != 1) { status = ST_LINESEARCH; break; }
         // exact tangent failed: restore the state at u and continue projected
         use_exact = false;
-        exact_banned = true;
+        exact_retry = it + ban_len;
+        ban_len *= 2;
+        slow = 0;
         if (!eval_pass<CL>(C, M, W, P, gb, bf, 0.0, org, false)) return false;
         continue;
       }
@@ -1469,13 +1501,22 @@ __device__ bool solve_body(Ctx& C, const MeshDev& M, const WorkDev& W, const Sol
       fs[0] = red_out[EV_FX]; fs[1] = red_out[EV_FY]; fs[2] = red_out[EV_FZ];
       active = (int)red_out[EV_ACTIVE];
       if (P.tangent_mode == 2) {
-        // exact tangent once the step is in its asymptotic regime; back to the
-        // projected one for the rest of the step if it misbehaves
+        // exact tangent (element and contact) once the step is in its
+        // asymptotic regime, or once the projected tangent stalls: its
+        // Gauss-Newton contact block leaves out the indenter's curvature, and
+        // under a small, deeply pressed cylinder that alone can slow Newton to
+        // a crawl. Back to the projected one for a while if exact misbehaves.
         if (use_exact && (neg_curv || alpha < 1.0)) {
           use_exact = false;
-          exact_banned = true;
-        } else if (!use_exact && !exact_banned && rn <= 1e-2 * rn_step0) {
-          use_exact = true;
+          exact_retry = it + ban_len;
+          ban_len *= 2;
+          slow = 0;
+        } else if (!use_exact) {
+          slow = rn > 0.5 * rn_prev ? slow + 1 : 0;
+          if (it >= exact_retry && (rn <= 1e-2 * rn_step0 || slow >= 3)) {
+            use_exact = true;
+            slow = 0;
+          }
         }
       }
     }
@@ -1587,6 +1628,7 @@ __global__ void __launch_bounds__(kSolveBlock, 1) solve_kernel(MeshDev M, WorkDe
       return;
     }
     tangent_pass(C, M, P.tangent_mode == 2 ? 0 : P.tangent_mode);
+    C.curv_on = P.tangent_mode == 1;
     for (int l = threadIdx.x; l < C.n_loc; l += blockDim.x) {
       const int g = local_to_global(C, M, l);
       const unsigned mk = M.fixmask[g];
