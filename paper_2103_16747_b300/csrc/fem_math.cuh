@@ -623,34 +623,32 @@ __device__ __forceinline__ void indenter_sdf(int shape, const double o[3], const
 // 0): k phi grad^2 phi, symmetric 3x3 as (xx xy xz yy yz zz). The Gauss-Newton
 // part k n n^T is applied separately. grad^2 phi is (I - n n^T) / rho for the
 // sphere and (I - a a^T - n n^T) / rho for the cylinder, rho the distance to
-// the centre / the axis; the box's and the plane's faces are flat (a node
+// the centre / the axis a; the box's and the plane's faces are flat (a node
 // inside the box is nearest to a face: no curvature). With phi < 0 the block
 // is negative semidefinite: it softens the contact across the normal, which
-// Gauss-Newton leaves out. Out of line: it runs only for penetrating nodes,
+// Gauss-Newton leaves out. d = x - centre, n = grad phi, kphi = k phi.
+// Out of line, with its inputs by value: it runs only for penetrating nodes,
 // and inlined it would take registers from the whole solve kernel.
-static __device__ __noinline__ void indenter_curvature(int shape, const double* o, const double* R,
-                                                       const double* x, const double* n, double kphi,
-                                                       float* out) {
+static __device__ __noinline__ void indenter_curvature(int shape, double d0, double d1, double d2, double a0,
+                                                       double a1, double a2, double n0, double n1, double n2,
+                                                       double kphi, float* out) {
 #pragma unroll
   for (int k = 0; k < 6; ++k) out[k] = 0.f;
   if (shape != 0 && shape != 1) return;
-  double d[3] = {x[0] - o[0], x[1] - o[1], x[2] - o[2]};
-  const double ax[3] = {R[2], R[5], R[8]};
   if (shape == 1) {
-    const double t = d[0] * ax[0] + d[1] * ax[1] + d[2] * ax[2];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) d[k] -= t * ax[k];
+    const double t = d0 * a0 + d1 * a1 + d2 * a2;
+    d0 -= t * a0; d1 -= t * a1; d2 -= t * a2;
   }
-  const double rho = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  const double rho = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
   if (!(rho > 0.0)) return;
   const double c = kphi / rho;
-  const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
-#pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    double v = (ia[k] == ib[k] ? 1.0 : 0.0) - n[ia[k]] * n[ib[k]];
-    if (shape == 1) v -= ax[ia[k]] * ax[ib[k]];
-    out[k] = (float)(c * v);
-  }
+  const double cyl = shape == 1 ? 1.0 : 0.0;
+  out[0] = (float)(c * (1.0 - n0 * n0 - cyl * a0 * a0));
+  out[1] = (float)(c * (-n0 * n1 - cyl * a0 * a1));
+  out[2] = (float)(c * (-n0 * n2 - cyl * a0 * a2));
+  out[3] = (float)(c * (1.0 - n1 * n1 - cyl * a1 * a1));
+  out[4] = (float)(c * (-n1 * n2 - cyl * a1 * a2));
+  out[5] = (float)(c * (1.0 - n2 * n2 - cyl * a2 * a2));
 }
 
 // ------------------------------------------------------------------ FP32 pairs

@@ -578,7 +578,8 @@ __device__ bool eval_pass(Ctx& C, const MeshDev& M, const WorkDev& W, const Solv
         v[EV_ACTIVE] += 1.0;
         const float sk = (float)sqrt(kp);
         h[0] = sk * (float)n[0]; h[1] = sk * (float)n[1]; h[2] = sk * (float)n[2];
-        indenter_curvature(P.shape, org, P.R, xx, n, kp * phi, C.hx + 6 * i);
+        indenter_curvature(P.shape, xx[0] - org[0], xx[1] - org[1], xx[2] - org[2], P.R[2], P.R[5], P.R[8], n[0],
+                           n[1], n[2], kp * phi, C.hx + 6 * i);
         curved = true;
       }
     }
