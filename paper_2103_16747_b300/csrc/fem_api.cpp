@@ -1364,6 +1364,7 @@ static int fem_create_mesh_body(const double* nodes, int64_t n_nodes, const int3
   *out = nullptr;
   fem_mesh* m = new fem_mesh();
   MeshHostArrays A;
+  fem::NvtxRange nvtx_prep("prepare_mesh");
   int rc = prepare_mesh(nodes, n_nodes, tets, n_tets, tet_material, materials, n_materials, fixed_nodes, n_fixed,
                         fixed_mask, m, A);
   if (rc != FEM_OK) {
@@ -1424,7 +1425,10 @@ static int fem_create_mesh_body(const double* nodes, int64_t n_nodes, const int3
   D.n_materials = n_materials;
   D.scale_floor = m->scale_floor;
   hp.mark("upload");
-  rc = build_partitions(m, default_parts(m));
+  {
+    fem::NvtxRange nvtx_part("partition and layout");
+    rc = build_partitions(m, default_parts(m));
+  }
   if (rc != FEM_OK) return bail(rc);
   hp.mark("partition");
   hp.print("create");
@@ -1436,6 +1440,7 @@ int fem_create_mesh(const double* nodes, int64_t n_nodes, const int32_t* tets, i
                     const int32_t* tet_material, const fem_material* materials, int32_t n_materials,
                     const int32_t* fixed_nodes, int64_t n_fixed, const uint8_t* fixed_mask,
                     void* cuda_stream, fem_mesh** out) {
+  fem::NvtxRange nvtx_("fem_create_mesh");
   return guarded([&] {
     return fem_create_mesh_body(nodes, n_nodes, tets, n_tets, tet_material, materials, n_materials, fixed_nodes,
                                 n_fixed, fixed_mask, cuda_stream, out);
@@ -1449,6 +1454,7 @@ static int fem_repartition_body(fem_mesh* m, int32_t n_parts) {
 }
 
 int fem_repartition(fem_mesh* m, int32_t n_parts) {
+  fem::NvtxRange nvtx_("fem_repartition");
   return guarded([&] { return fem_repartition_body(m, n_parts); });
 }
 
@@ -1471,6 +1477,7 @@ static int fem_mesh_info_get_body(const fem_mesh* m, fem_mesh_info* info) {
 }
 
 int fem_mesh_info_get(const fem_mesh* m, fem_mesh_info* info) {
+  fem::NvtxRange nvtx_("fem_mesh_info_get");
   return guarded([&] { return fem_mesh_info_get_body(m, info); });
 }
 
@@ -1503,6 +1510,7 @@ static int fem_set_indenter_body(fem_mesh* m, int shape, const double pose[12], 
 
 int fem_set_indenter(fem_mesh* m, int shape, const double pose[12], const double* params, const double dir[3],
                      const double* depth_schedule, int32_t n_steps) {
+  fem::NvtxRange nvtx_("fem_set_indenter");
   return guarded([&] { return fem_set_indenter_body(m, shape, pose, params, dir, depth_schedule, n_steps); });
 }
 
@@ -1531,6 +1539,7 @@ static int fem_set_dirichlet_values_body(fem_mesh* m, const double* values) {
 }
 
 int fem_set_dirichlet_values(fem_mesh* m, const double* values) {
+  fem::NvtxRange nvtx_("fem_set_dirichlet_values");
   return guarded([&] { return fem_set_dirichlet_values_body(m, values); });
 }
 
@@ -1577,6 +1586,7 @@ static int run_kernel(fem_mesh* m, const WorkDev& W, const SolveParams& P, float
            "reset published vectors");
   CUDA_TRY(cudaMemsetAsync(m->work.stats, 0, sizeof(StatsDev), s), "reset stats");
   CUDA_TRY(cudaMemsetAsync(m->work.stats->cycles_min, 0x7f, sizeof(long long) * PH_N, s), "reset stats");
+  fem::NvtxRange nvtx_("solve kernel");
   CUDA_TRY(launch_solve(m->dev, W, P, m->layout, s, ms), "solve kernel launch");
   int abort_flag = 0;
   CUDA_TRY(cudaMemcpyAsync(hst, m->work.stats, sizeof(StatsDev), cudaMemcpyDeviceToHost, s), "stats copy");
@@ -1664,6 +1674,7 @@ static int fem_solve_body(fem_mesh* m, int32_t load_steps, double tol, const fem
 
 int fem_solve(fem_mesh* m, int32_t load_steps, double tol, const fem_options* opt, double* out_disp,
               double* out_contact_force, double* out_nodal_contact, fem_stats* stats) {
+  fem::NvtxRange nvtx_("fem_solve");
   return guarded([&] {
     return fem_solve_body(m, load_steps, tol, opt, out_disp, out_contact_force, out_nodal_contact, stats);
   });
@@ -1696,6 +1707,7 @@ static int fem_eval_residual_body(fem_mesh* m, const double* u, int32_t step, co
 
 int fem_eval_residual(fem_mesh* m, const double* u, int32_t step, const fem_options* opt, double* out_R,
                       double* out_fc, double* out_energy) {
+  fem::NvtxRange nvtx_("fem_eval_residual");
   return guarded([&] { return fem_eval_residual_body(m, u, step, opt, out_R, out_fc, out_energy); });
 }
 
@@ -1794,6 +1806,7 @@ static int fem_eval_residual_noalloc_body(fem_mesh* m, const double* u, int32_t 
 
 int fem_eval_residual_noalloc(fem_mesh* m, const double* u, int32_t step, const fem_options* opt,
                               double* out_R, double* out_fc, double* out_energy) {
+  fem::NvtxRange nvtx_("fem_eval_residual_noalloc");
   return guarded([&] { return fem_eval_residual_noalloc_body(m, u, step, opt, out_R, out_fc, out_energy); });
 }
 
@@ -1817,6 +1830,7 @@ static int fem_apply_tangent_body(fem_mesh* m, const double* u, int32_t step, co
 
 int fem_apply_tangent(fem_mesh* m, const double* u, int32_t step, const fem_options* opt, const double* p,
                       double* out_y) {
+  fem::NvtxRange nvtx_("fem_apply_tangent");
   return guarded([&] { return fem_apply_tangent_body(m, u, step, opt, p, out_y); });
 }
 
@@ -1866,6 +1880,7 @@ static int fem_element_stress_body(fem_mesh* m, const double* u, double* out_cau
 }
 
 int fem_element_stress(fem_mesh* m, const double* u, double* out_cauchy, double* out_von_mises) {
+  fem::NvtxRange nvtx_("fem_element_stress");
   return guarded([&] { return fem_element_stress_body(m, u, out_cauchy, out_von_mises); });
 }
 
@@ -1887,6 +1902,7 @@ static int fem_debug_pcg_dots_body(fem_mesh* m, const double* r, const double* u
 }
 
 int fem_debug_pcg_dots(fem_mesh* m, const double* r, const double* u, const double* w, double out[3]) {
+  fem::NvtxRange nvtx_("fem_debug_pcg_dots");
   return guarded([&] { return fem_debug_pcg_dots_body(m, r, u, w, out); });
 }
 
@@ -1916,6 +1932,7 @@ static int fem_debug_barrier_timeout_body(double timeout_s) {
 }
 
 int fem_debug_barrier_timeout(double timeout_s) {
+  fem::NvtxRange nvtx_("fem_debug_barrier_timeout");
   return guarded([&] { return fem_debug_barrier_timeout_body(timeout_s); });
 }
 
@@ -1976,6 +1993,7 @@ static int fem_debug_plan_check_body(const double* nodes, int64_t n_nodes, const
 int fem_debug_plan_check(const double* nodes, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
                          const int32_t* tet_material, const fem_material* materials, int32_t n_materials,
                          const int32_t* fixed_nodes, int64_t n_fixed, int32_t n_parts, int64_t out[8]) {
+  fem::NvtxRange nvtx_("fem_debug_plan_check");
   return guarded([&] {
     return fem_debug_plan_check_body(nodes, n_nodes, tets, n_tets, tet_material, materials, n_materials, fixed_nodes,
                                      n_fixed, n_parts, out);
@@ -2000,6 +2018,7 @@ static int fem_debug_reciprocals_body(const double* x, int64_t n, double* out_rc
 }
 
 int fem_debug_reciprocals(const double* x, int64_t n, double* out_rcp, double* out_rsqrt) {
+  fem::NvtxRange nvtx_("fem_debug_reciprocals");
   return guarded([&] { return fem_debug_reciprocals_body(x, n, out_rcp, out_rsqrt); });
 }
 

@@ -460,6 +460,7 @@ static int fem_batch_create_body(fem_mesh* const* meshes, const int32_t* n_steps
 
 int fem_batch_create(fem_mesh* const* meshes, const int32_t* n_steps, int32_t n, const fem_options* opt,
                      fem_batch** out) {
+  fem::NvtxRange nvtx_("fem_batch_create");
   return guarded([&] { return fem_batch_create_body(meshes, n_steps, n, opt, out); });
 }
 
@@ -497,6 +498,7 @@ static int fem_batch_run_body(fem_batch* b, const fem_indenter* ind, double tol,
   CUDA_TRY(cudaEventRecord(b->ready, b->caller), "order after the caller's stream");
   CUDA_TRY(cudaStreamWaitEvent(s, b->ready, 0), "order after the caller's stream");
   CUDA_TRY(cudaEventRecord(b->ev0, s), "event");
+  fem::NvtxRange nvtx_run("graph replay");
   if (b->exec) CUDA_TRY(cudaGraphLaunch(b->exec, s), "batch graph");
   else CUDA_TRY(enqueue(b), "batch launch");
   CUDA_TRY(cudaEventRecord(b->ev1, s), "event");
@@ -553,6 +555,7 @@ static int fem_batch_run_body(fem_batch* b, const fem_indenter* ind, double tol,
 
 int fem_batch_run(fem_batch* b, const fem_indenter* ind, double tol, double* const* out_disp,
                   double* const* out_contact_force, fem_stats* stats) {
+  fem::NvtxRange nvtx_("fem_batch_run");
   return guarded([&] { return fem_batch_run_body(b, ind, tol, out_disp, out_contact_force, stats); });
 }
 
@@ -575,6 +578,7 @@ static int fem_batch_info_get_body(const fem_batch* b, fem_batch_info* info) {
 }
 
 int fem_batch_info_get(const fem_batch* b, fem_batch_info* info) {
+  fem::NvtxRange nvtx_("fem_batch_info_get");
   return guarded([&] { return fem_batch_info_get_body(b, info); });
 }
 
@@ -668,6 +672,7 @@ static int fem_batch_tune_body(fem_mesh* const* meshes, const fem_indenter* ind,
 
 int fem_batch_tune(fem_mesh* const* meshes, const fem_indenter* ind, int32_t n, double tol, const fem_options* opt,
                    int32_t proxy_steps, fem_options* out_opt, fem_tune_report* report) {
+  fem::NvtxRange nvtx_("fem_batch_tune");
   return guarded([&] { return fem_batch_tune_body(meshes, ind, n, tol, opt, proxy_steps, out_opt, report); });
 }
 
@@ -712,6 +717,7 @@ static int fem_solve_batch_body(fem_mesh* const* meshes, const fem_indenter* ind
 int fem_solve_batch(fem_mesh* const* meshes, const fem_indenter* ind, int32_t n, double tol,
                     const fem_options* opt, double* const* out_disp, double* const* out_contact_force,
                     fem_stats* stats) {
+  fem::NvtxRange nvtx_("fem_solve_batch");
   return guarded([&] { return fem_solve_batch_body(meshes, ind, n, tol, opt, out_disp, out_contact_force, stats); });
 }
 

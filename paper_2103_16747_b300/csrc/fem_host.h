@@ -65,7 +65,22 @@ struct fem_mesh {
   double* d_stress_out = nullptr;   // [7 Nt]: sigma (6 per tet), von Mises
 };
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace fem {
+
+// NVTX range over a host-side phase of a library call (mesh preparation,
+// partitioning, uploads, launches, graph replays, the server's admissions and
+// whole-GPU passes), visible on an Nsight Systems timeline; a no-op without a
+// profiler attached. The device-side timeline of a persistent solve (load
+// steps, Newton iterations, PCG phases) cannot carry host ranges: it comes back
+// as fem_stats.step_end_ms and the phase split.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 cudaError_t launch_permute(const double* src, double* dst, const int* perm, int n, bool to_caller,
                            cudaStream_t s);

@@ -380,6 +380,7 @@ void dispatcher(fem_server* v) {
             if (it == v->pending.end() || v->stopping) break;
             const int64_t id = *it;
             v->pending.erase(it);
+            fem::NvtxRange nvtx_big("whole-GPU pass");
             run_big(v, lk, id);
           }
           v->draining = false;
@@ -394,6 +395,7 @@ void dispatcher(fem_server* v) {
           if (k == n_slots) break;
           const int64_t id = *it;
           it = v->pending.erase(it);
+          fem::NvtxRange nvtx_admit("admit");
           if (!admit(v, k, v->reqs[id])) {
             v->reqs[id].rc = FEM_ERR_CUDA;
             v->reqs[id].state = 2;
@@ -655,6 +657,7 @@ static int fem_server_create_body(fem_mesh* const* meshes, int32_t n_meshes, int
 
 int fem_server_create(fem_mesh* const* meshes, int32_t n_meshes, int32_t max_steps, const fem_options* opt,
                       int64_t result_bytes, fem_server** out) {
+  fem::NvtxRange nvtx_("fem_server_create");
   return guarded([&] { return fem_server_create_body(meshes, n_meshes, max_steps, opt, result_bytes, out); });
 }
 
@@ -676,6 +679,7 @@ static int fem_server_start_body(fem_server* v, double max_seconds) {
 }
 
 int fem_server_start(fem_server* v, double max_seconds) {
+  fem::NvtxRange nvtx_("fem_server_start");
   return guarded([&] { return fem_server_start_body(v, max_seconds); });
 }
 
@@ -711,6 +715,7 @@ static int fem_server_submit_body(fem_server* v, int32_t mesh, const fem_indente
 }
 
 int fem_server_submit(fem_server* v, int32_t mesh, const fem_indenter* ind, double tol, int64_t* id) {
+  fem::NvtxRange nvtx_("fem_server_submit");
   return guarded([&] { return fem_server_submit_body(v, mesh, ind, tol, id); });
 }
 
@@ -744,6 +749,7 @@ static int fem_server_result_body(fem_server* v, int64_t id, int32_t wait_ms, do
 
 int fem_server_result(fem_server* v, int64_t id, int32_t wait_ms, double* out_disp, double* out_contact_force,
                       fem_stats* stats, double* times) {
+  fem::NvtxRange nvtx_("fem_server_result");
   return guarded([&] { return fem_server_result_body(v, id, wait_ms, out_disp, out_contact_force, stats, times); });
 }
 
@@ -797,6 +803,7 @@ static int fem_server_stop_body(fem_server* v) {
 }
 
 int fem_server_stop(fem_server* v) {
+  fem::NvtxRange nvtx_("fem_server_stop");
   return guarded([&] { return fem_server_stop_body(v); });
 }
 
@@ -818,6 +825,7 @@ static int fem_server_info_get_body(const fem_server* v, fem_server_info* info) 
 }
 
 int fem_server_info_get(const fem_server* v, fem_server_info* info) {
+  fem::NvtxRange nvtx_("fem_server_info_get");
   return guarded([&] { return fem_server_info_get_body(v, info); });
 }
 
