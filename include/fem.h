@@ -274,6 +274,33 @@ int fem_solve(fem_mesh* mesh, int32_t load_steps, double tol, const fem_options*
               double* out_disp, double* out_contact_force, double* out_nodal_contact,
               fem_stats* stats);
 
+/*
+ * Checkpoint and resume: solve load steps first_step..last_step (1-based,
+ * inclusive) of the schedule set by fem_set_indenter, starting from a saved
+ * state. The state of a solve after load step k is the pair of converged
+ * displacements (u_k, u_{k-1}): the secant predictor of step k+1 and, for
+ * dt > 0, the velocity (u_k - u_{k-1}) / dt come from it, and friction is
+ * frozen from u_k. A solve split into ranges, each resumed from the state the
+ * previous one returned, gives bitwise the results of one fem_solve.
+ *   u0, u0_prev    [n_nodes*3] u_{first_step-1} and u_{first_step-2} (caller
+ *                  node order, host or device). Both NULL for first_step = 1
+ *                  (from rest); u0_prev NULL means u0_prev = u0.
+ *   out_disp       [n_nodes*3] u of the last solved step (as fem_solve).
+ *   out_prev_disp  [n_nodes*3] u of the step before it, or NULL: with out_disp
+ *                  the state to resume the next range from.
+ *   out_contact_force [n_steps*3] of the whole schedule; rows of steps outside
+ *                  the range are zero. out_nodal_contact and stats as fem_solve
+ *                  (steps_done is the last converged step of the schedule; the
+ *                  per-step arrays are filled for the range's steps).
+ * The saved state is the caller's; nothing persists in the mesh between calls
+ * but the mesh itself. Errors: FEM_ERR_ARG (range outside the schedule, a range
+ * after step 1 without u0) and those of fem_solve.
+ */
+int fem_solve_range(fem_mesh* mesh, int32_t first_step, int32_t last_step, const double* u0,
+                    const double* u0_prev, double tol, const fem_options* opt, double* out_disp,
+                    double* out_prev_disp, double* out_contact_force, double* out_nodal_contact,
+                    fem_stats* stats);
+
 /* One indenter of a batched solve (same meaning as fem_set_indenter's arguments). */
 typedef struct {
     int32_t       shape;            /* FEM_SPHERE / FEM_CYLINDER / FEM_BOX / FEM_PLANE      */

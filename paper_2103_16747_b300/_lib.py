@@ -45,7 +45,7 @@ PHASES = ("eval", "tangent", "pcg_init", "pcg_reduce", "product_element", "vecto
 
 # Every symbol include/fem.h declares.
 EXPORTS = ("fem_default_options", "fem_create_mesh", "fem_set_indenter", "fem_set_dirichlet_values",
-           "fem_solve", "fem_solve_batch", "fem_destroy_mesh", "fem_last_error", "fem_build_checked",
+           "fem_solve", "fem_solve_range", "fem_solve_batch", "fem_destroy_mesh", "fem_last_error", "fem_build_checked",
            "fem_mesh_info_get", "fem_repartition",
            "fem_eval_residual", "fem_eval_residual_noalloc", "fem_apply_tangent",
            "fem_debug_barrier_timeout", "fem_debug_pcg_dots", "fem_debug_reciprocals", "fem_debug_plan_check", "fem_batch_create", "fem_batch_run", "fem_batch_info_get",
@@ -132,6 +132,8 @@ def _load():
         "fem_solve": (C.c_int, [P, C.c_int32, C.c_double, C.POINTER(fem_options), P, P, P,
                                 C.POINTER(fem_stats)]),
         "fem_solve_batch": (C.c_int, [P, P, C.c_int32, C.c_double, C.POINTER(fem_options), P, P, P]),
+        "fem_solve_range": (C.c_int, [P, C.c_int32, C.c_int32, P, P, C.c_double, C.POINTER(fem_options), P, P, P, P,
+                                      C.POINTER(fem_stats)]),
         "fem_destroy_mesh": (None, [P]),
         "fem_last_error": (C.c_char_p, []),
         "fem_build_checked": (C.c_int, []),
@@ -266,6 +268,23 @@ def fem_solve(mesh, load_steps, tol, opt=None, out_disp=None, out_contact_force=
     rc = lib.fem_solve(mesh, int(load_steps), float(tol), C.byref(opt) if opt is not None else None,
                        _out_ptr(out_disp, np.float64, keep), _out_ptr(out_contact_force, np.float64, keep),
                        _out_ptr(out_nodal_contact, np.float64, keep), C.byref(st))
+    if check:
+        _check(rc)
+    return rc, st
+
+
+def fem_solve_range(mesh, first_step, last_step, tol, opt=None, u0=None, u0_prev=None, out_disp=None,
+                    out_prev_disp=None, out_contact_force=None, out_nodal_contact=None, check=True):
+    """Load steps first_step..last_step from the saved state (u0, u0_prev);
+    returns (rc, fem_stats). (out_disp, out_prev_disp) is the state to resume
+    the next range from."""
+    keep = []
+    st = fem_stats()
+    rc = lib.fem_solve_range(mesh, int(first_step), int(last_step), _ptr(u0, np.float64, keep),
+                             _ptr(u0_prev, np.float64, keep), float(tol), C.byref(opt) if opt is not None else None,
+                             _out_ptr(out_disp, np.float64, keep), _out_ptr(out_prev_disp, np.float64, keep),
+                             _out_ptr(out_contact_force, np.float64, keep),
+                             _out_ptr(out_nodal_contact, np.float64, keep), C.byref(st))
     if check:
         _check(rc)
     return rc, st

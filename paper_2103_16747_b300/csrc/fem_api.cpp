@@ -1611,27 +1611,36 @@ static int copy_in_nodes(fem_mesh* m, const double* in, double* d_dst) {
   return FEM_OK;
 }
 
-static int fem_solve_body(fem_mesh* m, int32_t load_steps, double tol, const fem_options* opt, double* out_disp,
-              double* out_contact_force, double* out_nodal_contact, fem_stats* stats) {
-  g_err.clear();
-  if (!m) return fail(FEM_ERR_ARG, "mesh is NULL");
-  if (!m->has_indenter) return fail(FEM_ERR_ARG, "fem_set_indenter was not called");
-  if (load_steps == 0) load_steps = m->n_steps;
-  if (load_steps != m->n_steps) return fail(FEM_ERR_ARG, "load_steps=%d but the schedule has %d", load_steps, m->n_steps);
+// Load steps first..last of the mesh's schedule from the state (u0, uprev0):
+// the converged displacements of steps first-1 and first-2 (NULL: zero, the
+// schedule's start; uprev0 NULL with u0 given: no increment). fem_solve is the
+// whole schedule from rest.
+static int solve_steps(fem_mesh* m, int32_t first, int32_t last, const double* u0, const double* uprev0, double tol,
+                       const fem_options* opt, double* out_disp, double* out_prev_disp, double* out_contact_force,
+                       double* out_nodal_contact, fem_stats* stats) {
   if (!(tol > 0) || !std::isfinite(tol)) return fail(FEM_ERR_ARG, "tol must be > 0");
   SolveParams P;
-  int rc = fill_params(m, opt, MODE_SOLVE, load_steps, 0, tol, P);
+  int rc = fill_params(m, opt, MODE_SOLVE, m->n_steps, 0, tol, P);
   if (rc) return rc;
-  CUDA_TRY(cudaMemsetAsync(m->work.u, 0, 3 * sizeof(double) * m->n_nodes, m->stream), "reset u");
+  P.first_step = first;
+  P.last_step = last;
+  if (u0) {
+    P.keep_state = 1;
+    if ((rc = copy_in_nodes(m, u0, m->work.u))) return rc;
+    if ((rc = copy_in_nodes(m, uprev0 ? uprev0 : u0, m->work.uprev))) return rc;
+  } else {
+    CUDA_TRY(cudaMemsetAsync(m->work.u, 0, 3 * sizeof(double) * m->n_nodes, m->stream), "reset u");
+  }
   CUDA_TRY(cudaMemsetAsync(m->work.step_force, 0, 3 * sizeof(double) * kMaxSteps, m->stream), "reset forces");
   StatsDev hst;
   float ms = 0.f;
   rc = run_kernel(m, m->work, P, &ms, &hst);
   if (rc) return rc;
   if ((rc = copy_out_nodes(m, m->work.u, out_disp))) return rc;
+  if ((rc = copy_out_nodes(m, m->work.uprev, out_prev_disp))) return rc;
   if ((rc = copy_out_nodes(m, m->work.out_fc, out_nodal_contact))) return rc;
   if (out_contact_force)
-    CUDA_TRY(cudaMemcpyAsync(out_contact_force, m->work.step_force, 3 * sizeof(double) * load_steps,
+    CUDA_TRY(cudaMemcpyAsync(out_contact_force, m->work.step_force, 3 * sizeof(double) * m->n_steps,
                              cudaMemcpyDefault, m->stream), "force copy");
   CUDA_TRY(cudaStreamSynchronize(m->stream), "output copy");
   if (stats) {
@@ -1654,7 +1663,7 @@ static int fem_solve_body(fem_mesh* m, int32_t load_steps, double tol, const fem
       stats->phase_max_ms[k] = tot > 0 ? ms * (double)hst.cycles_max[k] / tot : 0.0;
       stats->phase_min_ms[k] = tot > 0 ? ms * (double)hst.cycles_min[k] / tot : 0.0;
     }
-    for (int k = 0; k < load_steps; ++k) {
+    for (int k = first - 1; k < last; ++k) {
       stats->newton_per_step[k] = hst.newton_per_step[k];
       stats->cg_per_step[k] = hst.cg_per_step[k];
       stats->residual_per_step[k] = hst.residual_per_step[k];
@@ -1672,11 +1681,46 @@ static int fem_solve_body(fem_mesh* m, int32_t load_steps, double tol, const fem
   return code;
 }
 
+static int fem_solve_body(fem_mesh* m, int32_t load_steps, double tol, const fem_options* opt, double* out_disp,
+              double* out_contact_force, double* out_nodal_contact, fem_stats* stats) {
+  g_err.clear();
+  if (!m) return fail(FEM_ERR_ARG, "mesh is NULL");
+  if (!m->has_indenter) return fail(FEM_ERR_ARG, "fem_set_indenter was not called");
+  if (load_steps == 0) load_steps = m->n_steps;
+  if (load_steps != m->n_steps) return fail(FEM_ERR_ARG, "load_steps=%d but the schedule has %d", load_steps, m->n_steps);
+  return solve_steps(m, 1, load_steps, nullptr, nullptr, tol, opt, out_disp, nullptr, out_contact_force,
+                     out_nodal_contact, stats);
+}
+
 int fem_solve(fem_mesh* m, int32_t load_steps, double tol, const fem_options* opt, double* out_disp,
               double* out_contact_force, double* out_nodal_contact, fem_stats* stats) {
   fem::NvtxRange nvtx_("fem_solve");
   return guarded([&] {
     return fem_solve_body(m, load_steps, tol, opt, out_disp, out_contact_force, out_nodal_contact, stats);
+  });
+}
+
+static int fem_solve_range_body(fem_mesh* m, int32_t first_step, int32_t last_step, const double* u0,
+                                const double* u0_prev, double tol, const fem_options* opt, double* out_disp,
+                                double* out_prev_disp, double* out_contact_force, double* out_nodal_contact,
+                                fem_stats* stats) {
+  g_err.clear();
+  if (!m) return fail(FEM_ERR_ARG, "mesh is NULL");
+  if (!m->has_indenter) return fail(FEM_ERR_ARG, "fem_set_indenter was not called");
+  if (first_step < 1 || last_step < first_step || last_step > m->n_steps)
+    return fail(FEM_ERR_ARG, "steps %d..%d outside the schedule 1..%d", first_step, last_step, m->n_steps);
+  if (first_step > 1 && !u0) return fail(FEM_ERR_ARG, "a range after step 1 needs the state u0");
+  return solve_steps(m, first_step, last_step, u0, u0_prev, tol, opt, out_disp, out_prev_disp, out_contact_force,
+                     out_nodal_contact, stats);
+}
+
+int fem_solve_range(fem_mesh* m, int32_t first_step, int32_t last_step, const double* u0, const double* u0_prev,
+                    double tol, const fem_options* opt, double* out_disp, double* out_prev_disp,
+                    double* out_contact_force, double* out_nodal_contact, fem_stats* stats) {
+  fem::NvtxRange nvtx_("fem_solve_range");
+  return guarded([&] {
+    return fem_solve_range_body(m, first_step, last_step, u0, u0_prev, tol, opt, out_disp, out_prev_disp,
+                                out_contact_force, out_nodal_contact, stats);
   });
 }
 

@@ -119,6 +119,8 @@ struct WorkDev {
 
 struct SolveParams {
   int mode, n_steps, step, tangent_mode, has_presc;
+  int first_step, last_step;        // solve load steps first..last of the n_steps (0: 1 and n_steps)
+  int keep_state;                   // 1: u and uprev hold a saved state (u of step first-1 and of first-2)
   int init_zero;                    // 1: the solve starts from u = 0 it writes itself (served jobs)
   int cheb_deg;                     // preconditioner: 1 = block-Jacobi, d > 1 = Chebyshev of degree d on it
   float cheb_theta, cheb_delta;     // centre and half-width of the Chebyshev interval

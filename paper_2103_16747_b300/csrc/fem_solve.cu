@@ -1216,7 +1216,7 @@ __device__ void accept_state(Ctx& C) {
 // gscr: this CTA's region of the global scratch (arrays placed there by L).
 __device__ void setup_ctx(Ctx& C, const MeshDev& M, const WorkDev& W, const SmemLayout& L, unsigned char* smem,
                           unsigned char* gscr, Statics* st, int part, int nparts, bool zero_u = false,
-                          double mass_scale = 0.0) {
+                          double mass_scale = 0.0, bool keep_uprev = false) {
   auto at = [&](int off) -> unsigned char* { return (off & kInGlobal) ? gscr + (off & ~kInGlobal) : smem + off; };
   C.part = part;
   C.nparts = nparts;
@@ -1298,7 +1298,7 @@ __device__ void setup_ctx(Ctx& C, const MeshDev& M, const WorkDev& W, const Smem
     for (int k = 0; k < 3; ++k) {
       C.x[3 * i + k] = 0.f;
       if (zero_u) C.u[3 * i + k] = 0.0;
-      if (C.uprev) C.uprev[3 * i + k] = C.u[3 * i + k];
+      if (C.uprev && !keep_uprev) C.uprev[3 * i + k] = C.u[3 * i + k];
     }
     C.mask[i] = M.fixmask[C.node0 + i];
     C.mh2[i] = (float)(mass_scale * C.vl[i]);
@@ -1330,8 +1330,11 @@ __device__ bool solve_body(Ctx& C, const MeshDev& M, const WorkDev& W, const Sol
   long long products = 0;
   double rn = 0.0, scale = 1.0, energy = 0.0;
   C.fric_on = P.mu_f > 0.0 && C.fric != nullptr;
-  int steps_done = 0;
-  for (int step = 1; step <= P.n_steps; ++step) {
+  // a range of the schedule resumes from the saved state in u and uprev
+  const int first = P.first_step > 0 ? P.first_step : 1;
+  const int last = P.last_step > 0 ? P.last_step : P.n_steps;
+  int steps_done = first - 1;
+  for (int step = first; step <= last; ++step) {
     double org[3];
     // schedules of served jobs are rewritten between jobs: read past L1
     const double dk = __ldcg(P.depths + step - 1);
@@ -1576,7 +1579,8 @@ __global__ void __launch_bounds__(kSolveBlock, 1) solve_kernel(MeshDev M, WorkDe
   }
   Ctx C;
   unsigned char* gscr = W.cta_scratch ? W.cta_scratch + (size_t)blockIdx.x * W.cta_stride : nullptr;
-  setup_ctx(C, M, W, L, smem, gscr, &S, blockIdx.x, gridDim.x, false, P.density * P.inv_dt * P.inv_dt);
+  setup_ctx(C, M, W, L, smem, gscr, &S, blockIdx.x, gridDim.x, false, P.density * P.inv_dt * P.inv_dt,
+            P.keep_state != 0);
   Barrier gb{W.barrier, W.abort_flag, 0ull, P.timeout_ns, gridDim.x};
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
   StatsDev* st = W.stats;
