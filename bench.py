@@ -837,15 +837,16 @@ def main():
                     help="batched workloads: store the tangent in FP16 with a per-tet scale")
     ap.add_argument("--e2e-steps", type=int, default=3,
                     help="batched workloads: end-to-end steps timed (at most --steps)")
-    ap.add_argument("--rates", type=float, nargs="+", default=[1.0, 2.0, 4.0, 8.0, 16.0],
+    ap.add_argument("--rates", type=float, nargs="+", default=[2.0, 8.0, 16.0, 32.0],
                     help="offered request rates (req/s) of the serve workload")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--drain-seconds", type=float, default=90.0)
     ap.add_argument("--serve-class-cap", type=int, default=64,
                     help="largest CTA group of the request server (power of two)")
-    ap.add_argument("--serve-tets-per-cta", type=int, default=650,
-                    help="size-class target of the request server (0: the library default, 1300); "
-                         "650 gives larger groups per request than batches use")
+    ap.add_argument("--serve-tets-per-cta", type=int, default=0,
+                    help="size-class target of the request server (0: the library default, 1300 tets per CTA; "
+                         "smaller targets give each request a larger group but send more meshes to whole-GPU "
+                         "passes)")
     ap.add_argument("--batch-parts", type=int, default=0,
                     help="batched workloads: uniform CTA groups of this size instead of the autotuner")
     ap.add_argument("--n-solves", type=int, default=None,
