@@ -68,7 +68,7 @@ VARIANTS = {
     "friction": (WORKLOAD + f"; lagged smoothed Coulomb friction mu={FRICTION_MU} (slip smoothing 0.01 h_bar)",
                  {"mu_f": FRICTION_MU}),
 }
-BATCH_MAX_NEWTON = 200   # deep random draws need more Newton steps in their last load steps
+BATCH_MAX_NEWTON = 400   # the deepest random draws need up to ~370 Newton steps at their hardest load step
 L2_NOTE = "flushed between timed steps (256 MiB write, L2 is 126 MB)"
 
 
