@@ -413,15 +413,20 @@ int fem_batch_tune(fem_mesh* const* meshes, const fem_indenter* indenters, int32
  * their requests waits, the persistent launch finishes the solves it holds and
  * leaves, the waiting large requests run one after another with the
  * single-solve kernel on all SMs (fem_solve on the pool's handle, which the
- * caller must not use meanwhile), and the persistent launch resumes. A
- * request's result is bitwise independent of the others (its partition
- * depends only on its mesh).
+ * caller must not use meanwhile), and the persistent launch resumes. Solves
+ * running when a whole-GPU pass is due leave at their next load-step boundary
+ * and resume after the pass from their own state (the converged displacements
+ * of their last two steps, kept in their result slot), so the pass waits one
+ * load step, not the rest of every running solve. A request's result is
+ * bitwise independent of the others and of any suspension (its partition
+ * depends only on its mesh; a resumed solve continues bitwise as if it had not
+ * been interrupted).
  */
 typedef struct fem_server fem_server;
 
 /* meshes: the resident pool (handles stay owned by the caller and must outlive
  * the server); max_steps: most load steps of any request; result_bytes: device
- * memory for results in flight (one result slot ~ 48 B per node of the largest
+ * memory for results in flight (one result slot ~ 72 B per node of the largest
  * mesh + 32 B per step; at least one slot per group). Errors: FEM_ERR_ARG,
  * FEM_ERR_TOO_LARGE, FEM_ERR_OOM, FEM_ERR_CUDA. */
 int fem_server_create(fem_mesh* const* meshes, int32_t n_meshes, int32_t max_steps, const fem_options* opt,
@@ -458,6 +463,9 @@ typedef struct {
     int32_t result_slots;           /* requests in flight at most         */
     int64_t admitted, completed, rejected;
     int64_t workspace_bytes;
+    int64_t suspended;              /* times a running solve left between load */
+                                    /* steps for a whole-GPU pass and resumed   */
+                                    /* after it                                 */
 } fem_server_info;
 int fem_server_info_get(const fem_server* server, fem_server_info* info);
 

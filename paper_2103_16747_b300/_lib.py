@@ -109,7 +109,8 @@ class fem_tune_report(C.Structure):
 class fem_server_info(C.Structure):
     _fields_ = [("n_classes", C.c_int32), ("class_parts", C.c_int32 * 8), ("class_groups", C.c_int32 * 8),
                 ("n_ctas", C.c_int32), ("result_slots", C.c_int32), ("admitted", C.c_int64),
-                ("completed", C.c_int64), ("rejected", C.c_int64), ("workspace_bytes", C.c_int64)]
+                ("completed", C.c_int64), ("rejected", C.c_int64), ("workspace_bytes", C.c_int64),
+                ("suspended", C.c_int64)]
 
 
 class FemError(RuntimeError):

@@ -323,7 +323,7 @@ static int fem_batch_create_body(fem_mesh* const* meshes, const int32_t* n_steps
   {
     long long o2 = 0;
     auto take = [&](size_t bytes) { const long long at = o2; o2 += (long long)a256(bytes); return at; };
-    S.ctrl = take(3 * sizeof(unsigned long long));
+    S.ctrl = take(4 * sizeof(unsigned long long));
     S.cgslot = take(sizeof(unsigned long long) * (12 * (size_t)max_parts + 2));
     S.vpub = clusters ? 0 : take(48 * max_nodes);
     S.partials = clusters ? 0 : take(16 * (size_t)max_parts * kRed);

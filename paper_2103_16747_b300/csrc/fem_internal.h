@@ -37,6 +37,7 @@ constexpr bool kCheckedBuild = false;
 
 enum Status : int {
   ST_OK = 0, ST_NOT_CONVERGED = 1, ST_LINESEARCH = 2, ST_NONFINITE = 3, ST_TIMEOUT = 4,
+  ST_SUSPENDED = 5,   // a served solve left between load steps (resumes at resume_step)
 };
 
 // Read-only mesh data, renumbered (Morton node order) and partitioned: part c
@@ -88,6 +89,8 @@ struct StatsDev {
   double residual_per_step[kMaxSteps];
   double step_end_ms[kMaxSteps];    // globaltimer of the leader at the end of each load step, from the
                                     // solve's start
+  unsigned long long t0_ns;         // globaltimer at the solve's start (kept across suspensions)
+  int resume_step;                  // ST_SUSPENDED: the load step the solve resumes at
 };
 
 struct WorkDev {
@@ -115,12 +118,16 @@ struct WorkDev {
   const double* in_p;               // [3*n_nodes] (MODE_APPLY)
   double* step_force;               // [3*K]
   StatsDev* stats;
+  int* yield_word;                  // served jobs: the group's decision to leave between load steps
 };
 
 struct SolveParams {
   int mode, n_steps, step, tangent_mode, has_presc;
   int first_step, last_step;        // solve load steps first..last of the n_steps (0: 1 and n_steps)
   int keep_state;                   // 1: u and uprev hold a saved state (u of step first-1 and of first-2)
+  int resume;                       // 1: the job's statistics hold its earlier load steps (add to them)
+  const volatile int* yield;        // served jobs: host flag asking running solves to leave between
+                                    // load steps (null: never)
   int init_zero;                    // 1: the solve starts from u = 0 it writes itself (served jobs)
   int cheb_deg;                     // preconditioner: 1 = block-Jacobi, d > 1 = Chebyshev of degree d on it
   float cheb_theta, cheb_delta;     // centre and half-width of the Chebyshev interval
@@ -174,6 +181,8 @@ struct BatchJob {
   MeshDev mesh;                     // partition into exactly as many parts as a slot has CTAs
   SolveParams prm;
   double* u;                        // [3 Nn] zero on entry; displacement on exit
+  double* uprev;                    // [3 Nn] the job's own u of the previous load step (served jobs, so a
+                                    // suspended solve keeps its state), or null: the group's scratch
   double* out_fc;                   // [3 Nn] nodal contact force on exit
   double* step_force;               // [3 K]
   StatsDev* stats;                  // status ST_TIMEOUT on entry: overwritten when the solve ends
@@ -182,7 +191,8 @@ struct BatchJob {
 struct SlotScratch {
   unsigned char* base;              // slot s at base + s * stride
   long long stride;
-  long long ctrl;                   // group engine: barrier counter, abort word, job word (u64 each)
+  long long ctrl;                   // group engine: barrier counter, abort word, job word, yield decision
+                                    // (u64 each)
   long long vpub, cgslot, partials; // group engine: as in WorkDev
   long long dpub, tangent, R, uprev, cta;   // offsets inside a slot
   long long vel, fric, tet_f;

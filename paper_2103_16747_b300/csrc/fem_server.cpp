@@ -97,6 +97,8 @@ struct fem_server {
   int* h_tail = nullptr;            // [classes]
   int* h_done = nullptr;            // [n_slots]
   int* h_stop = nullptr;
+  int* h_yield = nullptr;           // running solves leave between load steps (a whole-GPU pass waits)
+  const int* d_yield = nullptr;     // its device address
   BatchJob* h_job = nullptr;        // staging of one job entry
   double* h_dep = nullptr;          // staging of one schedule
   StatsDev* h_st0 = nullptr;        // initial statistics
@@ -116,7 +118,7 @@ struct fem_server {
   bool big_busy = false;            // the dispatcher is running a whole-GPU solve
   double session_end = 0.0;         // host clock at which the session ends
   std::vector<char> big;            // per mesh: served in whole-GPU passes
-  int64_t admitted = 0, completed = 0, rejected = 0;
+  int64_t admitted = 0, completed = 0, rejected = 0, suspended = 0;
 };
 
 namespace {
@@ -129,7 +131,8 @@ void server_release(fem_server* v) {
     if (s.h_force) cudaFreeHost(s.h_force);
     if (s.h_stats) cudaFreeHost(s.h_stats);
   }
-  for (void* p : {(void*)v->h_ids, (void*)v->h_tail, (void*)v->h_done, (void*)v->h_stop, (void*)v->h_job,
+  for (void* p : {(void*)v->h_ids, (void*)v->h_tail, (void*)v->h_done, (void*)v->h_stop, (void*)v->h_yield,
+                  (void*)v->h_job,
                   (void*)v->h_dep, (void*)v->h_st0})
     if (p) cudaFreeHost(p);
   if (v->ws) cudaFree(v->ws);
@@ -143,15 +146,17 @@ double* slot_ptr(fem_server* v, int slot, size_t off) {
   return reinterpret_cast<double*>(v->ws + v->res_off + (size_t)slot * v->res_stride + off);
 }
 
-// result-slot layout: u, out_fc, step forces, statistics, schedule
+// result-slot layout: u, u of the previous load step, out_fc, step forces,
+// statistics, schedule
 struct ResLayout {
-  size_t u, fc, force, stats, depths, stride;
+  size_t u, uprev, fc, force, stats, depths, stride;
 };
 ResLayout res_layout(size_t max_nodes, int max_steps) {
   ResLayout r;
   size_t o = 0;
   auto take = [&](size_t b) { const size_t at = o; o += a256s(b); return at; };
   r.u = take(24 * max_nodes);
+  r.uprev = take(24 * max_nodes);
   r.fc = take(24 * max_nodes);
   r.force = take(24 * (size_t)max_steps);
   r.stats = take(sizeof(StatsDev));
@@ -169,6 +174,7 @@ bool admit(fem_server* v, int slot, Request& q) {
   memset(&J, 0, sizeof(J));
   J.mesh = *v->mesh_part[q.mesh];
   J.u = slot_ptr(v, slot, R.u);
+  J.uprev = slot_ptr(v, slot, R.uprev);
   J.out_fc = slot_ptr(v, slot, R.fc);
   J.step_force = slot_ptr(v, slot, R.force);
   J.stats = reinterpret_cast<StatsDev*>(slot_ptr(v, slot, R.stats));
@@ -185,6 +191,7 @@ bool admit(fem_server* v, int slot, Request& q) {
   P.cg_rtol_min = v->o.cg_rtol_min;
   P.timeout_ns = (unsigned long long)(v->o.barrier_timeout_s * 1e9);
   P.init_zero = 1;
+  P.yield = v->d_yield;
   set_precond(v->o, P);
   set_physics(v->o, m->h_bar, P);
   P.shape = q.ind.shape;
@@ -278,6 +285,7 @@ int launch_persistent(fem_server* v) {
     v->h_ids[(size_t)c * n_slots + pos % n_slots] = k;
     v->h_tail[c] = pos + 1;
   }
+  __atomic_store_n(v->h_yield, 0, __ATOMIC_RELEASE);
   __atomic_store_n(v->h_stop, 0, __ATOMIC_RELEASE);
   const unsigned long long t0 = device_clock_ns();
   if (!t0) return fail(FEM_ERR_CUDA, "could not read the device clock");
@@ -327,7 +335,14 @@ bool retire(fem_server* v, bool wait) {
   bool worked = false;
   for (int k = 0; k < n_slots; ++k) {
     Slot& s = v->slots[k];
-    if (s.state == SLOT_RUNNING && __atomic_load_n(&v->h_done[k], __ATOMIC_ACQUIRE)) {
+    const int done = s.state == SLOT_RUNNING ? __atomic_load_n(&v->h_done[k], __ATOMIC_ACQUIRE) : 0;
+    if (done == 2) {
+      // suspended between load steps: the slot stays running and is published
+      // again when the persistent launch resumes
+      __atomic_store_n(&v->h_done[k], 0, __ATOMIC_RELAXED);
+      ++v->suspended;
+      worked = true;
+    } else if (done) {
       __atomic_store_n(&v->h_done[k], 0, __ATOMIC_RELAXED);
       const fem_mesh* m = v->meshes[v->reqs[s.req].mesh];
       cudaMemcpyAsync(s.h_u, slot_ptr(v, k, R.u), 24 * (size_t)m->n_nodes, cudaMemcpyDeviceToHost, v->cs);
@@ -361,7 +376,10 @@ void dispatcher(fem_server* v) {
         const bool big_waiting = std::any_of(v->pending.begin(), v->pending.end(),
                                              [&](int64_t id) { return v->big[v->reqs[id].mesh] != 0; });
         if (v->kernel_live && big_waiting && !v->draining) {
-          __atomic_store_n(v->h_stop, 1, __ATOMIC_RELEASE);   // idle groups leave, busy ones finish first
+          // idle groups leave at once, busy ones at their next load step (their
+          // solves resume after the whole-GPU pass)
+          __atomic_store_n(v->h_yield, 1, __ATOMIC_RELEASE);
+          __atomic_store_n(v->h_stop, 1, __ATOMIC_RELEASE);
           v->draining = true;
           worked = true;
         }
@@ -563,7 +581,7 @@ static int fem_server_create_body(fem_mesh* const* meshes, int32_t n_meshes, int
   {
     long long o2 = 0;
     auto take = [&](size_t bytes) { const long long at = o2; o2 += (long long)a256s(bytes); return at; };
-    S.ctrl = take(3 * sizeof(unsigned long long));
+    S.ctrl = take(4 * sizeof(unsigned long long));
     S.cgslot = take(sizeof(unsigned long long) * (12 * (size_t)max_parts + 2));
     S.vpub = take(48 * max_nodes);
     S.partials = take(16 * (size_t)max_parts * kRed);
@@ -594,6 +612,7 @@ static int fem_server_create_body(fem_mesh* const* meshes, int32_t n_meshes, int
   if ((rc = pinned(reinterpret_cast<void**>(&v->h_tail), sizeof(int) * C, cudaHostAllocMapped))) return rc;
   if ((rc = pinned(reinterpret_cast<void**>(&v->h_done), sizeof(int) * n_slots, cudaHostAllocMapped))) return rc;
   if ((rc = pinned(reinterpret_cast<void**>(&v->h_stop), sizeof(int), cudaHostAllocMapped))) return rc;
+  if ((rc = pinned(reinterpret_cast<void**>(&v->h_yield), sizeof(int), cudaHostAllocMapped))) return rc;
   if ((rc = pinned(reinterpret_cast<void**>(&v->h_job), sizeof(BatchJob), cudaHostAllocDefault))) return rc;
   if ((rc = pinned(reinterpret_cast<void**>(&v->h_dep), 8 * (size_t)max_steps, cudaHostAllocDefault))) return rc;
   if ((rc = pinned(reinterpret_cast<void**>(&v->h_st0), sizeof(StatsDev), cudaHostAllocDefault))) return rc;
@@ -601,6 +620,7 @@ static int fem_server_create_body(fem_mesh* const* meshes, int32_t n_meshes, int
   memset(v->h_tail, 0, sizeof(int) * C);
   memset(v->h_done, 0, sizeof(int) * n_slots);
   *v->h_stop = 0;
+  *v->h_yield = 0;
   memset(v->h_st0, 0, sizeof(StatsDev));
   v->h_st0->status = ST_TIMEOUT;
   for (int k = 0; k < PH_N; ++k) v->h_st0->cycles_min[k] = LLONG_MAX;
@@ -625,6 +645,11 @@ static int fem_server_create_body(fem_mesh* const* meshes, int32_t n_meshes, int
   if ((rc = cu(cudaHostGetDevicePointer(reinterpret_cast<void**>(&d_tail), v->h_tail, 0), "mapped"))) return rc;
   if ((rc = cu(cudaHostGetDevicePointer(reinterpret_cast<void**>(&d_done), v->h_done, 0), "mapped"))) return rc;
   if ((rc = cu(cudaHostGetDevicePointer(reinterpret_cast<void**>(&d_stop), v->h_stop, 0), "mapped"))) return rc;
+  {
+    int* d_yield = nullptr;
+    if ((rc = cu(cudaHostGetDevicePointer(reinterpret_cast<void**>(&d_yield), v->h_yield, 0), "mapped"))) return rc;
+    v->d_yield = d_yield;
+  }
   std::vector<JobQueue> queues(C);
   for (int c = 0; c < C; ++c) {
     queues[c].head = reinterpret_cast<int*>(v->ws + v->heads_off) + c;
@@ -820,6 +845,7 @@ static int fem_server_info_get_body(const fem_server* v, fem_server_info* info) 
   info->admitted = v->admitted;
   info->completed = v->completed;
   info->rejected = v->rejected;
+  info->suspended = v->suspended;
   info->workspace_bytes = (int64_t)v->ws_bytes;
   return FEM_OK;
 }

@@ -60,6 +60,13 @@ __device__ __forceinline__ int ld_volatile_i32(const int* p) {
   return *reinterpret_cast<const volatile int*>(p);
 }
 
+// A word of pinned host memory the host writes (release) while the kernel runs.
+__device__ __forceinline__ int ld_acquire_sys_i32(const volatile int* p) {
+  int v;
+  asm volatile("ld.acquire.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 // ------------------------------------------------------------ cluster helpers
 __device__ __forceinline__ unsigned cluster_rank() {
   unsigned r;
@@ -1320,14 +1327,30 @@ template <bool CL>
 __device__ bool solve_body(Ctx& C, const MeshDev& M, const WorkDev& W, const SolveParams& P, Barrier& gb, int& ep,
                            unsigned long long& n_pub) {
   const long long t_start = tick(C);
-  const unsigned long long ns_start = (C.part == 0 && threadIdx.x == 0) ? global_ns() : 0ull;
   Bufs bf{0};
   StatsDev* st = W.stats;
   const bool leader = C.part == 0 && threadIdx.x == 0;
+  // a resumed served solve adds to the statistics and the clock of its earlier steps
+  unsigned long long ns_start = 0ull;
+  if (leader) {
+    if (P.resume) {
+      ns_start = st->t0_ns;
+    } else {
+      ns_start = global_ns();
+      st->t0_ns = ns_start;
+    }
+  }
   const double* red_out = C.st->red_out;
   int status = ST_OK;
   int newton_total = 0, cg_total = 0, bt_total = 0, exact_total = 0;
   long long products = 0;
+  if (P.resume) {
+    newton_total = __ldcg(&st->newton_total);
+    cg_total = __ldcg(&st->cg_total);
+    bt_total = __ldcg(&st->backtracks_total);
+    exact_total = __ldcg(&st->exact_newton);
+    products = __ldcg(&st->products);
+  }
   double rn = 0.0, scale = 1.0, energy = 0.0;
   C.fric_on = P.mu_f > 0.0 && C.fric != nullptr;
   // a range of the schedule resumes from the saved state in u and uprev
@@ -1335,6 +1358,19 @@ __device__ bool solve_body(Ctx& C, const MeshDev& M, const WorkDev& W, const Sol
   const int last = P.last_step > 0 ? P.last_step : P.n_steps;
   int steps_done = first - 1;
   for (int step = first; step <= last; ++step) {
+    if (P.yield && step > first) {
+      // served solve: the host may ask for the GPU (a whole-GPU pass). Part 0
+      // reads the request and every part takes its decision after one sync;
+      // the state (u, u of the previous step) stays in the job's own arrays
+      if (leader) *reinterpret_cast<volatile int*>(W.yield_word) = ld_acquire_sys_i32(P.yield) ? step : 0;
+      if (!sync_parts<CL>(C, gb)) return false;
+      const int ys = ld_volatile_i32(W.yield_word);
+      if (ys) {
+        status = ST_SUSPENDED;
+        if (leader) st->resume_step = ys;
+        break;
+      }
+    }
     double org[3];
     // schedules of served jobs are rewritten between jobs: read past L1
     const double dk = __ldcg(P.depths + step - 1);
@@ -1557,7 +1593,7 @@ __device__ bool solve_body(Ctx& C, const MeshDev& M, const WorkDev& W, const Sol
     C.cyc[PH_TOTAL] = clock64() - t_start;
     if (leader) {
 #pragma unroll
-      for (int k = 0; k < PH_N; ++k) st->cycles[k] = C.cyc[k];
+      for (int k = 0; k < PH_N; ++k) st->cycles[k] = (P.resume ? st->cycles[k] : 0ll) + C.cyc[k];
     }
 #pragma unroll
     for (int k = 0; k < PH_N; ++k) {
@@ -1722,11 +1758,6 @@ __global__ void __launch_bounds__(kGroupBlock, 1) cluster_kernel(const BatchJob*
 // expires marks its job and leaves; in the served form a group also leaves
 // when the host sets the stop word or the deadline passes while it waits for
 // work.
-__device__ __forceinline__ int ld_acquire_sys_i32(const volatile int* p) {
-  int v;
-  asm volatile("ld.acquire.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
 
 __device__ int next_job(const GroupRun& R, const JobQueue& q) {
   if (!q.tail) {
@@ -1789,7 +1820,11 @@ __global__ void __launch_bounds__(kGroupBlock, 1) group_kernel(GroupRun R, SlotS
       WorkDev w{};
       w.u = reinterpret_cast<double*>(__ldcg(reinterpret_cast<const unsigned long long*>(&J->u)));
       w.R = reinterpret_cast<double*>(sb + S.R);
-      w.uprev = reinterpret_cast<double*>(sb + S.uprev);
+      // served jobs keep u of the previous load step in their own array, so a
+      // solve that leaves between load steps can resume in another group
+      double* own_prev = reinterpret_cast<double*>(__ldcg(reinterpret_cast<const unsigned long long*>(&J->uprev)));
+      w.uprev = own_prev ? own_prev : reinterpret_cast<double*>(sb + S.uprev);
+      w.yield_word = reinterpret_cast<int*>(ctrl + 3);
       w.vel = reinterpret_cast<double*>(sb + S.vel);
       w.fric = reinterpret_cast<double*>(sb + S.fric);
       w.tet_f = reinterpret_cast<double*>(sb + S.tet_f);
@@ -1808,15 +1843,26 @@ __global__ void __launch_bounds__(kGroupBlock, 1) group_kernel(GroupRun R, SlotS
     __syncthreads();
     Ctx C;
     setup_ctx(C, sM, sW, L, smem, gscr, &ST, part, G.parts, sP.init_zero != 0,
-              sP.density * sP.inv_dt * sP.inv_dt);
+              sP.density * sP.inv_dt * sP.inv_dt, sP.keep_state != 0);
     const bool solved = solve_body<false>(C, sM, sW, sP, gb, ep, n_pub);
     if (!solved && part == 0 && threadIdx.x == 0) sW.stats->status = ST_TIMEOUT;
     if (R.done) {
       // every part's outputs are written before part 0 reports the job done
+      // (1), or suspended between load steps (2): then the job entry is set to
+      // resume at its next load step from its own state, in a later launch
       if (solved && !grid_sync(gb, &ST.flag)) return;
       if (part == 0 && threadIdx.x == 0) {
+        int word = 1;
+        if (solved && sW.stats->status == ST_SUSPENDED) {
+          SolveParams* jp = const_cast<SolveParams*>(&J->prm);
+          jp->first_step = sW.stats->resume_step;
+          jp->keep_state = 1;
+          jp->init_zero = 0;
+          jp->resume = 1;
+          word = 2;
+        }
         __threadfence_system();
-        R.done[j] = 1;
+        R.done[j] = word;
       }
     }
     if (!solved) return;

@@ -1,6 +1,7 @@
 """Request server (continuous batching) on the GPU: a request's result is
-bitwise the same alone and inside a burst of mixed requests, matches the FP64
-oracle, and requests submitted after stop are rejected."""
+bitwise the same alone and inside a burst of mixed requests (also when it is
+suspended for a whole-GPU pass and resumed), matches the FP64 oracle, and
+requests submitted after stop are rejected."""
 import numpy as np
 import pytest
 
@@ -121,6 +122,58 @@ def test_server_whole_gpu_passes_for_large_meshes(F):
         else:
             rc_ref, u_ref, f_ref = ref[(k, j)]
             assert r[0] == rc_ref and np.array_equal(r[1], u_ref) and np.array_equal(r[2], f_ref), (k, j)
+    assert srv.stop() == 0
+    srv.close()
+    for h in handles:
+        F.fem_destroy_mesh(h)
+
+
+def test_running_solves_yield_to_a_whole_gpu_pass(F):
+    """A whole-GPU pass waits one load step, not the rest of the running
+    solves: they leave between load steps and resume after the pass from their
+    own state. Each resumed request gives bitwise the result it gives served
+    alone, the large request bitwise that of a direct fem_solve."""
+    tip, tip_ind = W.fingertip_sphere()
+    big = W.fingertip_mesh(R=8.0, h=0.75)       # 81,408 tets: beyond 64 x 700
+    pool = [tip, big]
+    assert big.n_tets > 64 * 700 > tip.n_tets
+    handles = [F.fem_create_mesh(m.nodes, m.tets, m.tet_material, m.materials, m.fixed_nodes) for m in pool]
+    small = W.draw_indentations(tip, 4, seed=411)
+    big_ind = W.draw_indentations(big, 1, seed=412)[0]
+    opt = F.fem_default_options()
+    opt.max_newton = 400
+    opt.batch_tets_per_cta = 700
+    s = F.IndentationSolver(big)
+    s.set_indenter(big_ind)
+    ref_big = s.solve(1e-6, opt, check=False)
+    s.close()
+    srv = F.FemServer(handles, 20, opt, result_bytes=256 << 20)
+    srv.start(300.0)
+    alone = []
+    for d in small:
+        rc, rid = srv.submit(0, d, 1e-6)
+        assert rc == 0
+        alone.append(srv.result(rid, tip.n_nodes, 20, wait_ms=200000))
+    assert srv.info().suspended == 0
+    # the small requests start, then the large one arrives while they run
+    ids = []
+    for d in small:
+        rc, rid = srv.submit(0, d, 1e-6)
+        assert rc == 0
+        ids.append(rid)
+    import time
+    time.sleep(0.02)
+    rc, rid_big = srv.submit(1, big_ind, 1e-6)
+    assert rc == 0
+    for rid, a in zip(ids, alone):
+        r = srv.result(rid, tip.n_nodes, 20, wait_ms=200000)
+        assert r[0] == a[0] and np.array_equal(r[1], a[1]) and np.array_equal(r[2], a[2])
+    rb = srv.result(rid_big, big.n_nodes, 20, wait_ms=200000)
+    assert rb[0] == ref_big["rc"] and np.array_equal(rb[1], ref_big["u"])
+    assert np.array_equal(rb[2], ref_big["step_force"])
+    info = srv.info()
+    print(f"suspended solves: {info.suspended}")
+    assert info.suspended >= 1
     assert srv.stop() == 0
     srv.close()
     for h in handles:
