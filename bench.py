@@ -735,8 +735,26 @@ def run_serve(args, rank, world, local):
         sopt.batch_tets_per_cta = args.serve_tets_per_cta
     srv = F.FemServer(handles, 20, sopt, result_bytes=1 << 30)
     info = srv.info()
+    # each mesh's class as the server forms it (CTAs per solve; beyond 64 x
+    # the tets-per-CTA target, the large- or huge-mesh group), to break
+    # latencies down
+    T = sopt.batch_tets_per_cta if sopt.batch_tets_per_cta > 0 else 1300
+    p_large = info.class_parts[info.large_class] if info.large_class >= 0 else 0
+    p_huge = info.class_parts[info.huge_class] if info.huge_class >= 0 else 0
+    label = {}
+    for k, m in enumerate(pool):
+        p = 1
+        while p < min(args.serve_class_cap, 64) and p * T < m.n_tets and 2 * p <= m.n_nodes:
+            p *= 2
+        if m.n_tets <= 64 * T:
+            label[k] = f"{p:02d}_ctas"
+        elif p_large and m.n_tets <= p_large * T:
+            label[k] = f"large_{p_large}_ctas"
+        else:
+            label[k] = f"huge_{p_huge}_ctas"
     rng = np.random.Generator(np.random.PCG64(1004 + 1000 * rank))
     sessions = []
+    prev_launches, prev_suspended = info.launches, info.suspended
     with ClockSampler(local) as clk:
         for rate in args.rates:
             n_req = int(rng.poisson(rate * args.serve_seconds))
@@ -756,7 +774,7 @@ def run_serve(args, rank, world, local):
                     ids.append((rid, p_))
                 else:
                     rejected += 1
-            lat, ok, t_first, t_last = [], 0, None, None
+            lat, ok, t_first, t_last, by = [], 0, None, None, {}
             for rid, p_ in ids:
                 k, d = kinds[p_]
                 left = max(1, int(1000 * (t0 + args.serve_seconds + args.drain_seconds - time.perf_counter())))
@@ -764,19 +782,29 @@ def run_serve(args, rank, world, local):
                 if rc == F.FEM_PENDING:
                     continue
                 lat.append(1000.0 * (tm[2] - tm[0]))
+                by.setdefault(label[k], []).append(lat[-1])
                 ok += rc == 0
                 t_first = tm[0] if t_first is None else min(t_first, tm[0])
                 t_last = tm[2] if t_last is None else max(t_last, tm[2])
             srv.stop()
+            after = srv.info()
+            launches, suspended = after.launches - prev_launches, after.suspended - prev_suspended
+            prev_launches, prev_suspended = after.launches, after.suspended
             # the plain path on the same trace, run for real: one GPU worker,
             # requests in arrival order, each fem_solve on the pool's resident mesh
-            plain = plain_path_on_trace(F, handles, pool, kinds, arrivals, picks, opt,
-                                        args.serve_seconds + args.drain_seconds)
+            plain, plain_lat = plain_path_on_trace(F, handles, pool, kinds, arrivals, picks, opt,
+                                                   args.serve_seconds + args.drain_seconds)
+            plain_by = {}
+            for p_, x in zip(picks, plain_lat):
+                plain_by.setdefault(label[kinds[p_][0]], []).append(x)
+            plain["by_class"] = class_latencies(plain_by)
             sessions.append({
                 "offered_per_s": rate, "requests": int(len(arrivals)), "rejected": rejected,
                 "completed": len(lat), "converged": int(ok),
                 "throughput": len(lat) / (t_last - t_first) if len(lat) > 1 else None,
-                "p50_ms": percentile(lat, 0.5), "p99_ms": percentile(lat, 0.99), "plain_path": plain})
+                "p50_ms": percentile(lat, 0.5), "p99_ms": percentile(lat, 0.99),
+                "by_class": class_latencies(by), "launches": launches, "suspended_solves": suspended,
+                "plain_path": plain})
             print(json.dumps({"session": sessions[-1]}), file=sys.stderr, flush=True)
     best = max((x["throughput"] or 0.0) for x in sessions)
     line = {"metric": METRIC, "value": best, "unit": UNIT, "n_gpus": world, "steps": len(sessions), "warmup": 0,
@@ -787,13 +815,19 @@ def run_serve(args, rank, world, local):
                                     f"4 random indentations per mesh, {args.serve_seconds:.0f} s per offered rate"),
                        "tol": TOL, "tets_per_cta_target": sopt.batch_tets_per_cta,
                        "size_classes": list(info.class_parts[:info.n_classes]),
-                       "groups": list(info.class_groups[:info.n_classes]), "result_slots": info.result_slots,
+                       "groups": list(info.class_groups[:info.n_classes]),
+                       "launch_shapes": [{"ctas": info.shape_ctas[k],
+                                          "groups": list(info.shape_groups[k][:info.n_classes])}
+                                         for k in range(info.n_shapes)],
+                       "result_slots": info.result_slots,
                        "plain_path": "fem_solve per request in arrival order on the same trace, run on the GPU "
                                      "(latency = completion - arrival)"},
             "sessions": sessions,
             "latency_ms": {"p50": sessions[0]["p50_ms"], "p99": sessions[0]["p99_ms"],
                            "at_offered_per_s": sessions[0]["offered_per_s"]},
-            "gpu_launches": len(sessions), "clocks": clk.summary()}
+            # one persistent launch per session and one per change of launch
+            # shape (the plain-path comparison is not counted)
+            "gpu_launches": sum(x["launches"] for x in sessions), "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     srv.close()
@@ -820,8 +854,14 @@ def plain_path_on_trace(F, handles, pool, kinds, arrivals, picks, opt, limit_s):
         lat.append(1000.0 * (t_end - a))
         done += 1
     first = float(arrivals[0]) if len(arrivals) else 0.0
-    return {"completed": done, "throughput": done / (t_end - first) if done > 1 and t_end > first else None,
-            "p50_ms": percentile(lat, 0.5), "p99_ms": percentile(lat, 0.99)}
+    return ({"completed": done, "throughput": done / (t_end - first) if done > 1 and t_end > first else None,
+             "p50_ms": percentile(lat, 0.5), "p99_ms": percentile(lat, 0.99)}, lat)
+
+
+def class_latencies(by):
+    """Latency percentiles per size class (label -> latencies in ms)."""
+    return {k: {"n": len(v), "p50_ms": percentile(v, 0.5), "p99_ms": percentile(v, 0.99), "max_ms": max(v)}
+            for k, v in sorted(by.items())}
 
 
 def main():

@@ -409,18 +409,22 @@ int fem_batch_tune(fem_mesh* const* meshes, const fem_indenter* indenters, int32
  * requests while result memory is free, publishes them to the GPU through
  * pinned host memory and collects the results; a request that arrives while
  * others run starts as soon as a group of its class is idle. Meshes with more
- * than 64 x batch_tets_per_cta tets are served in whole-GPU passes: when one of
- * their requests waits, the persistent launch finishes the solves it holds and
- * leaves, the waiting large requests run one after another with the
- * single-solve kernel on all SMs (fem_solve on the pool's handle, which the
- * caller must not use meanwhile), and the persistent launch resumes. Solves
- * running when a whole-GPU pass is due leave at their next load-step boundary
- * and resume after the pass from their own state (the converged displacements
- * of their last two steps, kept in their result slot), so the pass waits one
- * load step, not the rest of every running solve. A request's result is
- * bitwise independent of the others and of any suspension (its partition
- * depends only on its mesh; a resumed solve continues bitwise as if it had not
- * been interrupted).
+ * than 64 x batch_tets_per_cta tets are served by other launch shapes of the
+ * persistent kernel. Shape 1 keeps as many groups of the largest size class as
+ * leave at least half of the SMs and makes one group of the other SMs for the
+ * "large" meshes, those whose parts at that count stay within
+ * batch_tets_per_cta tets; shape 2 is one group of every SM for the larger
+ * ("huge") meshes; each such mesh is always cut into its group's number of
+ * parts. The host changes the shape first come, first served: when the oldest
+ * unfinished request the live shape does not serve is older than every
+ * unfinished request that only the live shape (of the two) serves, the running
+ * solves leave at their next load-step boundary, the kernel is relaunched in
+ * the shape that serves the waiting request, and the suspended solves resume
+ * from their own state (the converged displacements of their last two steps,
+ * kept in their result slot); it returns to shape 0 once nothing needs the
+ * other shape. A request's result is bitwise independent of the others, of
+ * the shape it ran in and of any suspension (its partition depends only on its
+ * mesh; a resumed solve continues bitwise as if it had not been interrupted).
  */
 typedef struct fem_server fem_server;
 
@@ -464,8 +468,15 @@ typedef struct {
     int64_t admitted, completed, rejected;
     int64_t workspace_bytes;
     int64_t suspended;              /* times a running solve left between load */
-                                    /* steps for a whole-GPU pass and resumed   */
-                                    /* after it                                 */
+                                    /* steps for a change of launch shape and   */
+                                    /* resumed after it                         */
+    int64_t launches;               /* persistent launches: the first of each  */
+                                    /* session and one per change of shape      */
+    int32_t large_class;            /* class of the large meshes, -1 if none    */
+    int32_t huge_class;             /* class of the huge meshes, -1 if none     */
+    int32_t n_shapes;               /* launch shapes (1-3)                      */
+    int32_t shape_ctas[3];          /* CTAs of each shape's launch              */
+    int32_t shape_groups[3][8];     /* groups per class in each shape           */
 } fem_server_info;
 int fem_server_info_get(const fem_server* server, fem_server_info* info);
 

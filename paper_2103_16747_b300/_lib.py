@@ -110,7 +110,9 @@ class fem_server_info(C.Structure):
     _fields_ = [("n_classes", C.c_int32), ("class_parts", C.c_int32 * 8), ("class_groups", C.c_int32 * 8),
                 ("n_ctas", C.c_int32), ("result_slots", C.c_int32), ("admitted", C.c_int64),
                 ("completed", C.c_int64), ("rejected", C.c_int64), ("workspace_bytes", C.c_int64),
-                ("suspended", C.c_int64)]
+                ("suspended", C.c_int64), ("launches", C.c_int64), ("large_class", C.c_int32),
+                ("huge_class", C.c_int32), ("n_shapes", C.c_int32), ("shape_ctas", C.c_int32 * 3),
+                ("shape_groups", (C.c_int32 * 8) * 3)]
 
 
 class FemError(RuntimeError):

@@ -75,6 +75,16 @@ struct Slot {
 
 }  // namespace
 
+// One launch shape of the persistent kernel: its shared-memory layout, its
+// groups (tables on the device) and which class rings its groups take.
+struct LaunchShape {
+  SmemLayout L{};
+  GroupRun run{};
+  int n_ctas = 0, n_groups = 0;
+  unsigned char* tab = nullptr;     // device: groups, CTA -> group, queues
+  std::vector<int> class_groups;    // groups per class (0: the class waits)
+};
+
 struct fem_server {
   int device = 0;
   cudaStream_t ks = nullptr, cs = nullptr;   // kernel stream, copy stream
@@ -83,21 +93,27 @@ struct fem_server {
   std::vector<fem_mesh*> meshes;
   std::vector<int> mesh_class;
   std::vector<const MeshDev*> mesh_part;
-  std::vector<int> class_parts, class_groups;
-  SmemLayout L{};
+  std::vector<int> class_parts;
+  // shape 0 serves the size classes; with meshes beyond the largest class
+  // in the pool, shape 1 keeps groups of the largest class and gives the other
+  // SMs to one group for the large meshes, and shape 2 is one group of every
+  // SM for the huge ones (either may be absent)
+  LaunchShape shape[3];
+  int n_shapes = 1;
+  int large_class = -1, huge_class = -1;
+  int cur = 0;                      // shape of the live (or next) launch
+  int next = 0;                     // shape to launch once the live one has drained
+  double shape_t0 = 0.0;            // host time of the live launch
   SlotScratch S{};
-  GroupRun run{};
-  int n_ctas = 0, n_groups = 0;
   unsigned char* ws = nullptr;      // group scratch, queue heads, job table, result slots
   size_t ws_bytes = 0, groups_bytes = 0, heads_off = 0, jobs_off = 0, res_off = 0, res_stride = 0;
-  unsigned char* tab = nullptr;     // device: groups, CTA -> group, queues
   size_t max_nodes = 0;
   // pinned host memory the GPU reads or writes
   int* h_ids = nullptr;             // [classes][n_slots] rings
   int* h_tail = nullptr;            // [classes]
   int* h_done = nullptr;            // [n_slots]
   int* h_stop = nullptr;
-  int* h_yield = nullptr;           // running solves leave between load steps (a whole-GPU pass waits)
+  int* h_yield = nullptr;           // running solves leave between load steps (the launch shape changes)
   const int* d_yield = nullptr;     // its device address
   BatchJob* h_job = nullptr;        // staging of one job entry
   double* h_dep = nullptr;          // staging of one schedule
@@ -113,12 +129,11 @@ struct fem_server {
   std::atomic<bool> quit{false};
   bool running = false;             // a session is open (start .. stop)
   bool kernel_live = false;         // the persistent launch is on the device
-  bool draining = false;            // stop word set for a whole-GPU pass
+  bool draining = false;            // stop and yield words set for a change of launch shape
   bool stopping = false;
-  bool big_busy = false;            // the dispatcher is running a whole-GPU solve
   double session_end = 0.0;         // host clock at which the session ends
-  std::vector<char> big;            // per mesh: served in whole-GPU passes
-  int64_t admitted = 0, completed = 0, rejected = 0, suspended = 0;
+  std::vector<char> big;            // per mesh: beyond the largest size class
+  int64_t admitted = 0, completed = 0, rejected = 0, suspended = 0, launches = 0;
 };
 
 namespace {
@@ -136,7 +151,8 @@ void server_release(fem_server* v) {
                   (void*)v->h_dep, (void*)v->h_st0})
     if (p) cudaFreeHost(p);
   if (v->ws) cudaFree(v->ws);
-  if (v->tab) cudaFree(v->tab);
+  for (LaunchShape& sh : v->shape)
+    if (sh.tab) cudaFree(sh.tab);
   if (v->ks) cudaStreamDestroy(v->ks);
   if (v->cs) cudaStreamDestroy(v->cs);
   delete v;
@@ -269,18 +285,23 @@ void finish(fem_server* v, int slot) {
   s.req = -1;
 }
 
-// Launch (or relaunch) the persistent kernel for the rest of the session;
-// requests already in result slots but not run are published again from the
-// start of their rings. Caller holds the lock.
+// Launch (or relaunch) the persistent kernel, in shape v->cur, for the rest
+// of the session. Requests in result slots that have not finished (queued,
+// or suspended between load steps) are published again, in arrival order,
+// from the start of their rings. Caller holds the lock.
 int launch_persistent(fem_server* v) {
   const double left = v->session_end - now_s();
   if (left <= 0.0) return FEM_OK;
+  LaunchShape& sh = v->shape[v->cur];
   CUDA_TRY(cudaMemsetAsync(v->ws, 0, v->jobs_off, v->ks), "reset");   // group counters, queue heads
   for (size_t c = 0; c < v->class_parts.size(); ++c) v->h_tail[c] = 0;
   const int n_slots = (int)v->slots.size();
-  for (int k = 0; k < n_slots; ++k) {
-    if (v->slots[k].state != SLOT_RUNNING) continue;
-    const int c = v->mesh_class[v->reqs[v->slots[k].req].mesh];
+  std::vector<std::pair<int64_t, int>> live;
+  for (int k = 0; k < n_slots; ++k)
+    if (v->slots[k].state == SLOT_RUNNING) live.emplace_back(v->slots[k].req, k);
+  std::sort(live.begin(), live.end());
+  for (const auto& [id, k] : live) {
+    const int c = v->mesh_class[v->reqs[id].mesh];
     const int pos = v->h_tail[c];
     v->h_ids[(size_t)c * n_slots + pos % n_slots] = k;
     v->h_tail[c] = pos + 1;
@@ -289,41 +310,13 @@ int launch_persistent(fem_server* v) {
   __atomic_store_n(v->h_stop, 0, __ATOMIC_RELEASE);
   const unsigned long long t0 = device_clock_ns();
   if (!t0) return fail(FEM_ERR_CUDA, "could not read the device clock");
-  v->run.deadline_ns = t0 + (unsigned long long)(left * 1e9);
-  CUDA_TRY(launch_groups(v->run, v->S, v->L, v->n_ctas, v->ks, nullptr), "server kernel");
+  sh.run.deadline_ns = t0 + (unsigned long long)(left * 1e9);
+  CUDA_TRY(launch_groups(sh.run, v->S, sh.L, sh.n_ctas, v->ks, nullptr), "server kernel");
   v->kernel_live = true;
   v->draining = false;
+  v->shape_t0 = now_s();
+  ++v->launches;
   return FEM_OK;
-}
-
-// One large request on all SMs (the single-solve kernel); the lock is
-// released while it runs.
-void run_big(fem_server* v, std::unique_lock<std::mutex>& lk, int64_t id) {
-  Request& q0 = v->reqs[id];
-  fem_mesh* m = v->meshes[q0.mesh];
-  const fem_indenter ind = q0.ind;
-  const std::vector<double> depths = q0.depths;
-  const double tol = q0.tol;
-  std::vector<double> u(3 * (size_t)m->n_nodes), force(3 * (size_t)ind.n_steps);
-  q0.state = 1;
-  q0.t_admit = now_s();
-  v->big_busy = true;
-  lk.unlock();
-  fem_stats st;
-  memset(&st, 0, sizeof(st));
-  int rc = fem_set_indenter(m, ind.shape, ind.pose, ind.params, ind.dir, depths.data(), ind.n_steps);
-  if (rc == FEM_OK) rc = fem_solve(m, ind.n_steps, tol, &v->o, u.data(), force.data(), nullptr, &st);
-  lk.lock();
-  v->big_busy = false;
-  Request& q = v->reqs[id];
-  q.u = std::move(u);
-  q.force = std::move(force);
-  q.stats = st;
-  q.rc = rc;
-  q.t_done = now_s();
-  q.state = 2;
-  ++v->admitted;
-  ++v->completed;
 }
 
 // Start the copy-out of every solve the kernel reported done and finish the
@@ -364,6 +357,48 @@ bool retire(fem_server* v, bool wait) {
   return worked;
 }
 
+// The launch shape the unfinished requests ask for (request ids grow with
+// submission, so the smallest id is the oldest request). A request of a class
+// the live shape does not serve waits in its ring. Let o be the oldest such
+// request and t the first shape serving its class: the kernel changes to t
+// when o is older than every unfinished request of the classes the live shape
+// serves and t does not (first come, first served between the shapes), or at
+// once when there are none. The largest size class is served by shapes 0 and
+// 1 and asks for no change between them; once no unfinished request needs
+// the live shape more than shape 0, the kernel returns to shape 0, whose
+// groups serve every size class.
+int wanted_shape(const fem_server* v) {
+  if (v->n_shapes < 2) return 0;
+  const int cur = v->cur;
+  auto serves = [&](int sh, int c) { return v->shape[sh].class_groups[c] > 0; };
+  std::vector<int64_t> ids;
+  ids.reserve(v->pending.size() + v->slots.size());
+  for (int64_t id : v->pending) ids.push_back(id);
+  for (const Slot& s : v->slots)
+    if (s.state == SLOT_RUNNING) ids.push_back(s.req);
+  int64_t o = INT64_MAX;
+  int t = cur;
+  bool needs_cur = false;
+  for (int64_t id : ids) {
+    const int c = v->mesh_class[v->reqs.at(id).mesh];
+    if (serves(cur, c)) {
+      needs_cur |= !serves(0, c);
+      continue;
+    }
+    if (id < o) {
+      o = id;
+      t = 0;
+      while (t < v->n_shapes && !serves(t, c)) ++t;
+    }
+  }
+  if (o == INT64_MAX) return cur != 0 && !needs_cur ? 0 : cur;
+  for (int64_t id : ids) {
+    const int c = v->mesh_class[v->reqs.at(id).mesh];
+    if (serves(cur, c) && !serves(t, c) && id < o) return cur;
+  }
+  return t;
+}
+
 void dispatcher(fem_server* v) {
   cudaSetDevice(v->device);
   const int n_slots = (int)v->slots.size();
@@ -373,51 +408,44 @@ void dispatcher(fem_server* v) {
       std::unique_lock<std::mutex> lk(v->mu);
       worked |= retire(v, false);
       if (v->running && !v->stopping) {
-        const bool big_waiting = std::any_of(v->pending.begin(), v->pending.end(),
-                                             [&](int64_t id) { return v->big[v->reqs[id].mesh] != 0; });
-        if (v->kernel_live && big_waiting && !v->draining) {
-          // idle groups leave at once, busy ones at their next load step (their
-          // solves resume after the whole-GPU pass)
-          __atomic_store_n(v->h_yield, 1, __ATOMIC_RELEASE);
-          __atomic_store_n(v->h_stop, 1, __ATOMIC_RELEASE);
-          v->draining = true;
-          worked = true;
-        }
-        if (v->kernel_live && cudaStreamQuery(v->ks) != cudaErrorNotReady) {
-          v->kernel_live = false;   // drained (or the session deadline passed)
-          // done words set after this iteration's first pass: retire them now,
-          // before any relaunch republishes the solves that were not run
-          retire(v, true);
-          worked = true;
-        }
-        if (!v->kernel_live && v->draining) {
-          // whole-GPU pass: every waiting large request, in arrival order
-          for (;;) {
-            auto it = std::find_if(v->pending.begin(), v->pending.end(),
-                                   [&](int64_t id) { return v->big[v->reqs[id].mesh] != 0; });
-            if (it == v->pending.end() || v->stopping) break;
-            const int64_t id = *it;
-            v->pending.erase(it);
-            fem::NvtxRange nvtx_big("whole-GPU pass");
-            run_big(v, lk, id);
-          }
-          v->draining = false;
-          if (!v->stopping && launch_persistent(v) != FEM_OK) v->stopping = true;
-          worked = true;
-        }
-        // small requests into free result slots while the persistent launch serves
-        for (auto it = v->pending.begin(); it != v->pending.end() && v->kernel_live && !v->draining;) {
-          if (v->big[v->reqs[*it].mesh]) { ++it; continue; }
+        // every waiting request into a free result slot, in arrival order (a
+        // request of a class the live shape does not serve waits in its ring)
+        while (!v->pending.empty()) {
           int k = 0;
           while (k < n_slots && v->slots[k].state != SLOT_FREE) ++k;
           if (k == n_slots) break;
-          const int64_t id = *it;
-          it = v->pending.erase(it);
+          const int64_t id = v->pending.front();
+          v->pending.pop_front();
           fem::NvtxRange nvtx_admit("admit");
           if (!admit(v, k, v->reqs[id])) {
             v->reqs[id].rc = FEM_ERR_CUDA;
             v->reqs[id].state = 2;
           }
+          worked = true;
+        }
+        if (v->kernel_live && !v->draining) {
+          const int want = wanted_shape(v);
+          if (want != v->cur) {
+            // idle groups leave at once, busy ones at their next load step
+            // (their solves resume in the next launch, from their own state)
+            __atomic_store_n(v->h_yield, 1, __ATOMIC_RELEASE);
+            __atomic_store_n(v->h_stop, 1, __ATOMIC_RELEASE);
+            v->draining = true;
+            v->next = want;
+            worked = true;
+          }
+        }
+        if (v->kernel_live && cudaStreamQuery(v->ks) != cudaErrorNotReady) {
+          v->kernel_live = false;   // drained (or the session deadline passed)
+          // done words set after this iteration's first pass: retire them now,
+          // before the relaunch republishes the solves that did not finish
+          retire(v, true);
+          worked = true;
+        }
+        if (!v->kernel_live && v->draining) {
+          v->cur = v->next;
+          fem::NvtxRange nvtx_launch(v->cur ? "launch: large-mesh shape" : "launch: size-class shape");
+          if (launch_persistent(v) != FEM_OK) v->stopping = true;
           worked = true;
         }
       }
@@ -465,10 +493,11 @@ static int fem_server_create_body(fem_mesh* const* meshes, int32_t n_meshes, int
     int p = 1;
     while (p < pcap && (int64_t)p * T < meshes[i]->n_tets && 2 * p <= meshes[i]->n_nodes) p *= 2;
     parts[i] = std::min(p, n_sm);
-    // too large for the largest class: whole-GPU passes
+    // too large for the largest class: the large-mesh group of launch shape 1
     big[i] = (int64_t)64 * T < meshes[i]->n_tets ? 1 : 0;
   }
   if (std::all_of(big.begin(), big.end(), [](char b) { return b != 0; })) big.assign(n_meshes, 0);
+  const bool any_big = std::any_of(big.begin(), big.end(), [](char b) { return b != 0; });
   {
     std::vector<fem_mesh*> small;
     std::vector<int> small_parts;
@@ -481,24 +510,28 @@ static int fem_server_create_body(fem_mesh* const* meshes, int32_t n_meshes, int
     if (rc) return rc;
   }
   std::vector<const MeshDev*> part(n_meshes);
+  std::vector<const PartDims*> pdims(n_meshes);
+  auto widen = [](PartDims& d, const PartDims& e) {
+    d.max_own = std::max(d.max_own, e.max_own);
+    d.max_loc = std::max(d.max_loc, e.max_loc);
+    d.max_pt = std::max(d.max_pt, e.max_pt);
+    d.max_lcsr = std::max(d.max_lcsr, e.max_lcsr);
+  };
   PartDims dims{0, 0, 0, 0};
   size_t max_nodes = 0, max_pt = 0, max_tets = 0;
   for (int i = 0; i < n_meshes; ++i) {
-    if (big[i]) continue;
-    const PartDims* pd = nullptr;
-    int rc = batch_partition(meshes[i], parts[i], &part[i], &pd);
-    if (rc) return rc;
-    dims.max_own = std::max(dims.max_own, pd->max_own);
-    dims.max_loc = std::max(dims.max_loc, pd->max_loc);
-    dims.max_pt = std::max(dims.max_pt, pd->max_pt);
-    dims.max_lcsr = std::max(dims.max_lcsr, pd->max_lcsr);
     max_nodes = std::max(max_nodes, (size_t)meshes[i]->n_nodes);
     max_tets = std::max(max_tets, (size_t)meshes[i]->n_tets);
+    if (big[i]) continue;
+    int rc = batch_partition(meshes[i], parts[i], &part[i], &pdims[i]);
+    if (rc) return rc;
+    widen(dims, *pdims[i]);
     max_pt = std::max(max_pt, (size_t)part[i]->total_pt);
   }
   int static_smem = 0, per_sm = 0;
   CUDA_TRY(group_kernel_attrs(0, &static_smem, nullptr), "group kernel attributes");
-  SmemLayout L = plan_layout(dims, smem_budget(meshes[0], static_smem));
+  const int budget = smem_budget(meshes[0], static_smem);
+  SmemLayout L = plan_layout(dims, budget);
   // stored tangent: FP32 (default), or FP16 with a per-tet scale (half the
   // bytes each tangent product streams) when the options ask for it. The
   // format is the engine's choice for every job of the launch, not the
@@ -507,13 +540,10 @@ static int fem_server_create_body(fem_mesh* const* meshes, int32_t n_meshes, int
   if (L.total < 0) return fail(FEM_ERR_TOO_LARGE, "a part does not fit one CTA");
   CUDA_TRY(group_kernel_attrs(L.total, nullptr, &per_sm), "group occupancy");
   const int cap = per_sm * n_sm;
-  std::vector<int> class_parts, mesh_class(n_meshes);
+  std::vector<int> class_parts, mesh_class(n_meshes, -1);
   std::vector<double> class_work;
   for (int i = 0; i < n_meshes; ++i) {
-    if (big[i]) {
-      mesh_class[i] = -1;
-      continue;
-    }
+    if (big[i]) continue;
     int c = (int)(std::find(class_parts.begin(), class_parts.end(), parts[i]) - class_parts.begin());
     if (c == (int)class_parts.size()) {
       class_parts.push_back(parts[i]);
@@ -525,14 +555,10 @@ static int fem_server_create_body(fem_mesh* const* meshes, int32_t n_meshes, int
   }
   const int C = (int)class_parts.size();
   int used = 0;
-  double W = 0.0;
-  for (int c = 0; c < C; ++c) {
-    used += class_parts[c];
-    W += class_work[c];
-  }
+  for (int c = 0; c < C; ++c) used += class_parts[c];
   if (used > cap) return fail(FEM_ERR_TOO_LARGE, "the size classes need %d co-resident CTAs of %d", used, cap);
-  // one group per class, then one more group at a time to the class with the
-  // most work per CTA that still fits
+  // launch shape 0: one group per class, then one more group at a time to the
+  // class with the most work per CTA that still fits
   std::vector<int> class_groups(C, 1);
   for (;;) {
     int best = -1;
@@ -546,16 +572,105 @@ static int fem_server_create_body(fem_mesh* const* meshes, int32_t n_meshes, int
     ++class_groups[best];
     used += class_parts[best];
   }
-  int n_groups = 0, max_parts = 0;
-  for (int c = 0; c < C; ++c) {
-    n_groups += class_groups[c];
-    max_parts = std::max(max_parts, class_parts[c]);
+  // launch shapes for the meshes beyond the largest class (more than 64 x
+  // batch_tets_per_cta tets). Shape 1: the largest class keeps as many of its
+  // groups as leave at least half of the SMs, and the other SMs form one group
+  // for the "large" meshes, those whose parts at that count stay within
+  // batch_tets_per_cta tets. Shape 2: one group of every SM for the larger
+  // ("huge") meshes. A mesh is always cut into its group's number of parts,
+  // so its result does not depend on what else runs.
+  struct ShapePlan {
+    SmemLayout L{};
+    std::vector<int> groups;
+    int n_groups = 0;
+  };
+  std::vector<ShapePlan> plans(1);
+  plans[0].L = L;
+  plans[0].groups = class_groups;
+  int large_class = -1, huge_class = -1;
+  if (any_big) {
+    const int c_max = (int)(std::max_element(class_parts.begin(), class_parts.end()) - class_parts.begin());
+    const int keep = std::min(class_groups[c_max], (n_sm / 2) / class_parts[c_max]);
+    int p_large = n_sm - keep * class_parts[c_max], p_huge = n_sm;
+    std::vector<char> huge(n_meshes, 0);
+    for (int i = 0; i < n_meshes; ++i) {
+      if (!big[i]) continue;
+      huge[i] = keep == 0 || (int64_t)p_large * T < meshes[i]->n_tets ? 1 : 0;
+      int& p = huge[i] ? p_huge : p_large;
+      p = std::min<int>(p, (int)(meshes[i]->n_nodes / 2));
+    }
+    std::vector<fem_mesh*> bm;
+    std::vector<int> bp;
+    for (int i = 0; i < n_meshes; ++i)
+      if (big[i]) {
+        bm.push_back(meshes[i]);
+        bp.push_back(huge[i] ? p_huge : p_large);
+      }
+    int rc = prefetch_batch_partitions(bm.data(), bp.data(), (int)bm.size());
+    if (rc) return rc;
+    PartDims d_large{0, 0, 0, 0}, d_huge{0, 0, 0, 0};
+    bool any_large = false, any_huge = false;
+    for (int i = 0; i < n_meshes; ++i) {
+      if (!big[i]) continue;
+      if ((rc = batch_partition(meshes[i], huge[i] ? p_huge : p_large, &part[i], &pdims[i]))) return rc;
+      max_pt = std::max(max_pt, (size_t)part[i]->total_pt);
+      widen(huge[i] ? d_huge : d_large, *pdims[i]);
+      (huge[i] ? any_huge : any_large) = true;
+    }
+    if (any_large) {
+      for (int i = 0; i < n_meshes; ++i)
+        if (!big[i] && mesh_class[i] == c_max) widen(d_large, *pdims[i]);
+      large_class = (int)class_parts.size();
+      class_parts.push_back(p_large);
+    }
+    if (any_huge) {
+      huge_class = (int)class_parts.size();
+      class_parts.push_back(p_huge);
+    }
+    for (int i = 0; i < n_meshes; ++i)
+      if (big[i]) mesh_class[i] = huge[i] ? huge_class : large_class;
+    const int nc = (int)class_parts.size();
+    plans[0].groups.resize(nc, 0);
+    auto add_shape = [&](const PartDims& d, std::vector<int> groups, const char* what) {
+      ShapePlan sp;
+      sp.L = plan_layout(d, budget);
+      sp.L.tan16 = L.tan16;
+      if (sp.L.total < 0) return fail(FEM_ERR_TOO_LARGE, "a part of a %s mesh does not fit one CTA", what);
+      int ps = 0;
+      CUDA_TRY(group_kernel_attrs(sp.L.total, nullptr, &ps), "group occupancy");
+      int ctas = 0;
+      for (int c = 0; c < nc; ++c) ctas += groups[c] * class_parts[c];
+      if (ctas > ps * n_sm)
+        return fail(FEM_ERR_TOO_LARGE, "the %s-mesh launch shape needs %d co-resident CTAs of %d", what, ctas,
+                    ps * n_sm);
+      sp.groups = std::move(groups);
+      plans.push_back(std::move(sp));
+      return (int)FEM_OK;
+    };
+    if (any_large) {
+      std::vector<int> g(nc, 0);
+      g[c_max] = keep;
+      g[large_class] = 1;
+      if ((rc = add_shape(d_large, g, "large"))) return rc;
+    }
+    if (any_huge) {
+      std::vector<int> g(nc, 0);
+      g[huge_class] = 1;
+      if ((rc = add_shape(d_huge, g, "huge"))) return rc;
+    }
   }
+  const int n_classes = (int)class_parts.size();
+  int max_groups = 0, max_parts = 0;
+  for (ShapePlan& sp : plans) {
+    for (int c = 0; c < n_classes; ++c) sp.n_groups += sp.groups[c];
+    max_groups = std::max(max_groups, sp.n_groups);
+  }
+  for (int c = 0; c < n_classes; ++c) max_parts = std::max(max_parts, class_parts[c]);
   const ResLayout RL = res_layout(max_nodes, max_steps);
   int n_slots = (int)std::min<int64_t>(4096, std::max<int64_t>(result_bytes / (int64_t)RL.stride, 0));
-  if (n_slots < n_groups)
+  if (n_slots < max_groups)
     return fail(FEM_ERR_ARG, "result_bytes holds %d result slots, the server needs at least %d (%zu B each)", n_slots,
-                n_groups, RL.stride);
+                max_groups, RL.stride);
 
   fem_server* v = new fem_server();
   v->device = meshes[0]->device;
@@ -566,9 +681,14 @@ static int fem_server_create_body(fem_mesh* const* meshes, int32_t n_meshes, int
   v->big = big;
   v->mesh_part = part;
   v->class_parts = class_parts;
-  v->class_groups = class_groups;
-  v->L = L;
-  v->n_groups = n_groups;
+  v->n_shapes = (int)plans.size();
+  for (int k = 0; k < v->n_shapes; ++k) {
+    v->shape[k].L = plans[k].L;
+    v->shape[k].class_groups = plans[k].groups;
+    v->shape[k].n_groups = plans[k].n_groups;
+  }
+  v->large_class = large_class;
+  v->huge_class = huge_class;
   v->max_nodes = max_nodes;
   v->max_pending = std::max(64, 4 * n_slots);
   auto bail = [&](int code) { server_release(v); return code; };
@@ -591,12 +711,18 @@ static int fem_server_create_body(fem_mesh* const* meshes, int32_t n_meshes, int
     S.vel = take(24 * max_nodes);
     S.fric = take(32 * max_nodes);
     S.tet_f = take(96 * max_tets);
-    S.tangent = take(L.tan >= 0 ? 16 : 16 * (size_t)kTanVec * max_pt);
-    S.cta = take((size_t)L.gbytes * max_parts);
-    S.cta_stride = L.gbytes;
+    bool streamed = false;
+    int gbytes = 0;
+    for (const ShapePlan& sp : plans) {
+      streamed |= sp.L.tan < 0;
+      gbytes = std::max(gbytes, sp.L.gbytes);
+    }
+    S.tangent = take(streamed ? 16 * (size_t)kTanVec * max_pt : 16);
+    S.cta = take((size_t)gbytes * max_parts);
+    S.cta_stride = gbytes;
     S.stride = o2;
   }
-  v->groups_bytes = (size_t)S.stride * n_groups;
+  v->groups_bytes = (size_t)S.stride * max_groups;
   v->heads_off = v->groups_bytes;
   v->jobs_off = v->heads_off + 256;
   v->res_off = v->jobs_off + a256s(sizeof(BatchJob) * n_slots);
@@ -608,16 +734,16 @@ static int fem_server_create_body(fem_mesh* const* meshes, int32_t n_meshes, int
   auto pinned = [&](void** p, size_t bytes, unsigned flags) {
     return cu(cudaHostAlloc(p, bytes, flags), "pinned host memory");
   };
-  if ((rc = pinned(reinterpret_cast<void**>(&v->h_ids), sizeof(int) * C * n_slots, cudaHostAllocMapped))) return rc;
-  if ((rc = pinned(reinterpret_cast<void**>(&v->h_tail), sizeof(int) * C, cudaHostAllocMapped))) return rc;
+  if ((rc = pinned(reinterpret_cast<void**>(&v->h_ids), sizeof(int) * n_classes * n_slots, cudaHostAllocMapped))) return rc;
+  if ((rc = pinned(reinterpret_cast<void**>(&v->h_tail), sizeof(int) * n_classes, cudaHostAllocMapped))) return rc;
   if ((rc = pinned(reinterpret_cast<void**>(&v->h_done), sizeof(int) * n_slots, cudaHostAllocMapped))) return rc;
   if ((rc = pinned(reinterpret_cast<void**>(&v->h_stop), sizeof(int), cudaHostAllocMapped))) return rc;
   if ((rc = pinned(reinterpret_cast<void**>(&v->h_yield), sizeof(int), cudaHostAllocMapped))) return rc;
   if ((rc = pinned(reinterpret_cast<void**>(&v->h_job), sizeof(BatchJob), cudaHostAllocDefault))) return rc;
   if ((rc = pinned(reinterpret_cast<void**>(&v->h_dep), 8 * (size_t)max_steps, cudaHostAllocDefault))) return rc;
   if ((rc = pinned(reinterpret_cast<void**>(&v->h_st0), sizeof(StatsDev), cudaHostAllocDefault))) return rc;
-  memset(v->h_ids, 0, sizeof(int) * C * n_slots);
-  memset(v->h_tail, 0, sizeof(int) * C);
+  memset(v->h_ids, 0, sizeof(int) * n_classes * n_slots);
+  memset(v->h_tail, 0, sizeof(int) * n_classes);
   memset(v->h_done, 0, sizeof(int) * n_slots);
   *v->h_stop = 0;
   *v->h_yield = 0;
@@ -631,15 +757,8 @@ static int fem_server_create_body(fem_mesh* const* meshes, int32_t n_meshes, int
     if ((rc = pinned(reinterpret_cast<void**>(&s.h_force), 24 * (size_t)max_steps, cudaHostAllocDefault))) return rc;
     if ((rc = pinned(reinterpret_cast<void**>(&s.h_stats), sizeof(StatsDev), cudaHostAllocDefault))) return rc;
   }
-  // static tables: groups, CTA -> group, queues (rings in mapped host memory)
-  std::vector<GroupDesc> groups;
-  std::vector<int> gmap;
-  for (int c = 0; c < C; ++c)
-    for (int g = 0; g < class_groups[c]; ++g) {
-      groups.push_back(GroupDesc{(int)gmap.size(), class_parts[c], c});
-      for (int k = 0; k < class_parts[c]; ++k) gmap.push_back((int)groups.size() - 1);
-    }
-  v->n_ctas = (int)gmap.size();
+  // device tables of each launch shape: groups, CTA -> group, queues (the
+  // rings live in mapped host memory and are shared by the shapes)
   int *d_ids = nullptr, *d_tail = nullptr, *d_done = nullptr, *d_stop = nullptr;
   if ((rc = cu(cudaHostGetDevicePointer(reinterpret_cast<void**>(&d_ids), v->h_ids, 0), "mapped"))) return rc;
   if ((rc = cu(cudaHostGetDevicePointer(reinterpret_cast<void**>(&d_tail), v->h_tail, 0), "mapped"))) return rc;
@@ -650,31 +769,43 @@ static int fem_server_create_body(fem_mesh* const* meshes, int32_t n_meshes, int
     if ((rc = cu(cudaHostGetDevicePointer(reinterpret_cast<void**>(&d_yield), v->h_yield, 0), "mapped"))) return rc;
     v->d_yield = d_yield;
   }
-  std::vector<JobQueue> queues(C);
-  for (int c = 0; c < C; ++c) {
+  std::vector<JobQueue> queues(n_classes);
+  for (int c = 0; c < n_classes; ++c) {
     queues[c].head = reinterpret_cast<int*>(v->ws + v->heads_off) + c;
     queues[c].ids = d_ids + (size_t)c * n_slots;
     queues[c].n = 0;
     queues[c].cap = n_slots;
     queues[c].tail = d_tail + c;
   }
-  const size_t o_groups = 0, o_gmap = a256s(sizeof(GroupDesc) * groups.size()),
-               o_queues = o_gmap + a256s(sizeof(int) * gmap.size()), tab_bytes = o_queues + a256s(sizeof(JobQueue) * C);
-  if ((rc = cu(cudaMalloc(reinterpret_cast<void**>(&v->tab), tab_bytes), "server tables"))) return rc;
-  if ((rc = cu(cudaMemcpy(v->tab + o_groups, groups.data(), sizeof(GroupDesc) * groups.size(), cudaMemcpyHostToDevice),
-               "server tables"))) return rc;
-  if ((rc = cu(cudaMemcpy(v->tab + o_gmap, gmap.data(), sizeof(int) * gmap.size(), cudaMemcpyHostToDevice),
-               "server tables"))) return rc;
-  if ((rc = cu(cudaMemcpy(v->tab + o_queues, queues.data(), sizeof(JobQueue) * C, cudaMemcpyHostToDevice),
-               "server tables"))) return rc;
-  GroupRun& R = v->run;
-  R.jobs = reinterpret_cast<const BatchJob*>(v->ws + v->jobs_off);
-  R.groups = reinterpret_cast<const GroupDesc*>(v->tab + o_groups);
-  R.group_of_cta = reinterpret_cast<const int*>(v->tab + o_gmap);
-  R.queues = reinterpret_cast<const JobQueue*>(v->tab + o_queues);
-  R.timeout_ns = (unsigned long long)(o.barrier_timeout_s * 1e9);
-  R.stop = d_stop;
-  R.done = d_done;
+  for (int sidx = 0; sidx < v->n_shapes; ++sidx) {
+    LaunchShape& sh = v->shape[sidx];
+    std::vector<GroupDesc> groups;
+    std::vector<int> gmap;
+    for (int c = 0; c < n_classes; ++c)
+      for (int g = 0; g < sh.class_groups[c]; ++g) {
+        groups.push_back(GroupDesc{(int)gmap.size(), class_parts[c], c});
+        for (int k = 0; k < class_parts[c]; ++k) gmap.push_back((int)groups.size() - 1);
+      }
+    sh.n_ctas = (int)gmap.size();
+    const size_t o_groups = 0, o_gmap = a256s(sizeof(GroupDesc) * groups.size()),
+                 o_queues = o_gmap + a256s(sizeof(int) * gmap.size()),
+                 tab_bytes = o_queues + a256s(sizeof(JobQueue) * n_classes);
+    if ((rc = cu(cudaMalloc(reinterpret_cast<void**>(&sh.tab), tab_bytes), "server tables"))) return rc;
+    if ((rc = cu(cudaMemcpy(sh.tab + o_groups, groups.data(), sizeof(GroupDesc) * groups.size(),
+                            cudaMemcpyHostToDevice), "server tables"))) return rc;
+    if ((rc = cu(cudaMemcpy(sh.tab + o_gmap, gmap.data(), sizeof(int) * gmap.size(), cudaMemcpyHostToDevice),
+                 "server tables"))) return rc;
+    if ((rc = cu(cudaMemcpy(sh.tab + o_queues, queues.data(), sizeof(JobQueue) * n_classes, cudaMemcpyHostToDevice),
+                 "server tables"))) return rc;
+    GroupRun& R = sh.run;
+    R.jobs = reinterpret_cast<const BatchJob*>(v->ws + v->jobs_off);
+    R.groups = reinterpret_cast<const GroupDesc*>(sh.tab + o_groups);
+    R.group_of_cta = reinterpret_cast<const int*>(sh.tab + o_gmap);
+    R.queues = reinterpret_cast<const JobQueue*>(sh.tab + o_queues);
+    R.timeout_ns = (unsigned long long)(o.barrier_timeout_s * 1e9);
+    R.stop = d_stop;
+    R.done = d_done;
+  }
   v->th = std::thread(dispatcher, v);
   *out = v;
   return FEM_OK;
@@ -784,17 +915,15 @@ static int fem_server_stop_body(fem_server* v) {
   {
     std::unique_lock<std::mutex> lk(v->mu);
     if (!v->running) return FEM_OK;
-    v->stopping = true;   // no further whole-GPU pass or relaunch
+    v->stopping = true;   // no further relaunch
     __atomic_store_n(v->h_stop, 1, __ATOMIC_RELEASE);
   }
-  // groups finish the solve they hold, then leave; a whole-GPU solve in
-  // progress finishes too
+  // groups finish the solve they hold, then leave
   const cudaError_t e = cudaStreamSynchronize(v->ks);
-  for (int k = 0; k < 600000; ++k) {   // bounded: 10 min for a running whole-GPU solve
+  for (int k = 0; k < 600000; ++k) {   // bounded: 10 min for the last copies
     bool busy = false;
     {
       std::unique_lock<std::mutex> lk(v->mu);
-      busy = v->big_busy;
       for (size_t j = 0; j < v->slots.size(); ++j)
         busy |= v->slots[j].state == SLOT_COPYING ||
                 (v->slots[j].state == SLOT_RUNNING && __atomic_load_n(&v->h_done[j], __ATOMIC_ACQUIRE));
@@ -836,11 +965,17 @@ static int fem_server_info_get_body(const fem_server* v, fem_server_info* info) 
   if (!v || !info) return fail(FEM_ERR_ARG, "NULL argument");
   memset(info, 0, sizeof(*info));
   info->n_classes = (int32_t)v->class_parts.size();
+  info->large_class = v->large_class;
+  info->huge_class = v->huge_class;
+  info->n_shapes = v->n_shapes;
   for (size_t c = 0; c < v->class_parts.size() && c < 8; ++c) {
     info->class_parts[c] = v->class_parts[c];
-    info->class_groups[c] = v->class_groups[c];
+    info->class_groups[c] = v->shape[0].class_groups[c];
+    for (int k = 0; k < v->n_shapes; ++k) info->shape_groups[k][c] = v->shape[k].class_groups[c];
   }
-  info->n_ctas = v->n_ctas;
+  info->n_ctas = v->shape[0].n_ctas;
+  for (int k = 0; k < v->n_shapes; ++k) info->shape_ctas[k] = v->shape[k].n_ctas;
+  info->launches = v->launches;
   info->result_slots = (int32_t)v->slots.size();
   info->admitted = v->admitted;
   info->completed = v->completed;

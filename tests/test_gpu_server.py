@@ -1,6 +1,6 @@
 """Request server (continuous batching) on the GPU: a request's result is
 bitwise the same alone and inside a burst of mixed requests (also when it is
-suspended for a whole-GPU pass and resumed), matches the FP64 oracle, and
+suspended for a change of launch shape and resumed), matches the FP64 oracle, and
 requests submitted after stop are rejected."""
 import numpy as np
 import pytest
@@ -77,29 +77,50 @@ def test_server_alone_equals_mix_and_matches_oracle(F):
         F.fem_destroy_mesh(h)
 
 
-def test_server_whole_gpu_passes_for_large_meshes(F):
+def _batch_reference(F, mesh, handle, draws, opt, parts):
+    """The batched group engine on one mesh cut into `parts` parts: the same
+    partition and kernel as the server's large-mesh group."""
+    bo = F.fem_options.from_buffer_copy(opt)
+    bo.batch_engine, bo.batch_parts = 1, parts
+    out = []
+    for d in draws:
+        u = [np.zeros((mesh.n_nodes, 3))]
+        f = [np.zeros((d.n_steps, 3))]
+        rc, _ = F.fem_solve_batch([handle], [d], 1e-6, bo, u, f, check=False)
+        out.append((rc, u[0], f[0]))
+    return out
+
+
+def test_server_large_meshes_in_their_own_launch_shape(F):
     """Meshes too large for a 64-CTA class (here: more than 64 x 100 tets)
-    are served in whole-GPU passes between runs of the persistent launch: a
-    large request's result equals a direct fem_solve, a small one's result
-    equals the same request served alone."""
+    are served by other launch shapes of the persistent kernel: the large
+    ones (parts of at most 100 tets on the SMs the largest class leaves) by
+    one group beside that class's groups, the huge ones by one group of every
+    SM. A large or huge request's result equals the batched engine's on the
+    same number of parts, a small one's result equals the same request served
+    alone."""
     cube, cube_ind = W.cube_sphere()
-    pool = [cube] + [m for m, _ in W.uneven_fingertips(2, seed=21, tet_min=8e3, tet_max=1.2e4)]
+    pool = [cube] + [m for m, _ in W.uneven_fingertips(3, seed=21, tet_min=6.6e3, tet_max=1.2e4)]
     assert all(m.n_tets > 6400 for m in pool[1:])
     handles = [F.fem_create_mesh(m.nodes, m.tets, m.tet_material, m.materials, m.fixed_nodes) for m in pool]
     draws = {k: W.draw_indentations(pool[k], 2, seed=300 + k) for k in range(1, len(pool))}
     opt = F.fem_default_options()
     opt.max_newton = 200
     opt.batch_tets_per_cta = 100
-    # direct single solves of the large requests (reference)
+    srv = F.FemServer(handles, 20, opt, result_bytes=32 << 20)
+    info = srv.info()
+    assert info.n_shapes == 3 and info.large_class >= 0 and info.huge_class >= 0
+    lc, hc = info.large_class, info.huge_class
+    p_large, p_huge = info.class_parts[lc], info.class_parts[hc]
+    assert p_large * 100 < 9216 and p_large * 100 >= 8208
+    assert info.class_groups[lc] == 0 and info.shape_groups[1][lc] == 1 and info.shape_groups[2][hc] == 1
+    assert info.shape_ctas[1] == p_large + sum(info.class_parts[c] * info.shape_groups[1][c] for c in range(lc))
+    assert info.shape_ctas[2] == p_huge
+    parts_of = {k: (p_huge if pool[k].n_tets > p_large * 100 else p_large) for k in range(1, len(pool))}
     ref = {}
     for k in range(1, len(pool)):
-        for j, d in enumerate(draws[k]):
-            s = F.IndentationSolver(pool[k])
-            s.set_indenter(d)
-            r = s.solve(1e-6, opt, check=False)
-            ref[(k, j)] = (r["rc"], r["u"], r["step_force"])
-            s.close()
-    srv = F.FemServer(handles, 20, opt, result_bytes=32 << 20)
+        for j, r in enumerate(_batch_reference(F, pool[k], handles[k], draws[k], opt, parts_of[k])):
+            ref[(k, j)] = r
     srv.start(120.0)
     rc, rid = srv.submit(0, cube_ind, 1e-6)
     alone = srv.result(rid, cube.n_nodes, 10, wait_ms=100000)
@@ -122,58 +143,65 @@ def test_server_whole_gpu_passes_for_large_meshes(F):
         else:
             rc_ref, u_ref, f_ref = ref[(k, j)]
             assert r[0] == rc_ref and np.array_equal(r[1], u_ref) and np.array_equal(r[2], f_ref), (k, j)
+    info = srv.info()
+    print(f"launches {info.launches}, suspended {info.suspended}, parts large {p_large} huge {p_huge}")
+    assert info.launches >= 3
     assert srv.stop() == 0
     srv.close()
     for h in handles:
         F.fem_destroy_mesh(h)
 
 
-def test_running_solves_yield_to_a_whole_gpu_pass(F):
-    """A whole-GPU pass waits one load step, not the rest of the running
-    solves: they leave between load steps and resume after the pass from their
-    own state. Each resumed request gives bitwise the result it gives served
-    alone, the large request bitwise that of a direct fem_solve."""
+def test_running_solves_yield_to_the_large_mesh_shape(F):
+    """A change of launch shape waits one load step, not the rest of the
+    running solves: they leave between load steps and resume in the next
+    launch from their own state. A short request A (4 load steps) and a long
+    one C run on the two groups of the fingertip's class, and a huge request B
+    that arrived between them asks for the other shape: when A is done, B is
+    older than C, so C leaves mid-solve and resumes after B. Each request
+    gives bitwise the result it gives served alone, B bitwise that of the
+    batched engine on the huge-mesh group's part count."""
+    import dataclasses
+    import time
     tip, tip_ind = W.fingertip_sphere()
     big = W.fingertip_mesh(R=8.0, h=0.75)       # 81,408 tets: beyond 64 x 700
     pool = [tip, big]
     assert big.n_tets > 64 * 700 > tip.n_tets
     handles = [F.fem_create_mesh(m.nodes, m.tets, m.tet_material, m.materials, m.fixed_nodes) for m in pool]
-    small = W.draw_indentations(tip, 4, seed=411)
+    d_a, d_c = W.draw_indentations(tip, 2, seed=411)
+    d_a = dataclasses.replace(d_a, depth_schedule=d_a.depth_schedule[:4].copy())
     big_ind = W.draw_indentations(big, 1, seed=412)[0]
     opt = F.fem_default_options()
     opt.max_newton = 400
     opt.batch_tets_per_cta = 700
-    s = F.IndentationSolver(big)
-    s.set_indenter(big_ind)
-    ref_big = s.solve(1e-6, opt, check=False)
-    s.close()
     srv = F.FemServer(handles, 20, opt, result_bytes=256 << 20)
+    info = srv.info()
+    big_class = max(info.large_class, info.huge_class)
+    assert info.n_shapes == 2 and big_class == 1 and info.class_groups[0] == 2
+    ref_big = _batch_reference(F, big, handles[1], [big_ind], opt, info.class_parts[big_class])[0]
     srv.start(300.0)
     alone = []
-    for d in small:
+    for d in (d_a, d_c):
         rc, rid = srv.submit(0, d, 1e-6)
         assert rc == 0
-        alone.append(srv.result(rid, tip.n_nodes, 20, wait_ms=200000))
+        alone.append(srv.result(rid, tip.n_nodes, d.n_steps, wait_ms=200000))
     assert srv.info().suspended == 0
-    # the small requests start, then the large one arrives while they run
-    ids = []
-    for d in small:
-        rc, rid = srv.submit(0, d, 1e-6)
-        assert rc == 0
-        ids.append(rid)
-    import time
-    time.sleep(0.02)
+    launches0 = srv.info().launches
+    rc, rid_a = srv.submit(0, d_a, 1e-6)
+    time.sleep(0.005)
     rc, rid_big = srv.submit(1, big_ind, 1e-6)
+    rc, rid_c = srv.submit(0, d_c, 1e-6)
     assert rc == 0
-    for rid, a in zip(ids, alone):
-        r = srv.result(rid, tip.n_nodes, 20, wait_ms=200000)
+    for rid, d, a in ((rid_a, d_a, alone[0]), (rid_c, d_c, alone[1])):
+        r = srv.result(rid, tip.n_nodes, d.n_steps, wait_ms=200000)
         assert r[0] == a[0] and np.array_equal(r[1], a[1]) and np.array_equal(r[2], a[2])
     rb = srv.result(rid_big, big.n_nodes, 20, wait_ms=200000)
-    assert rb[0] == ref_big["rc"] and np.array_equal(rb[1], ref_big["u"])
-    assert np.array_equal(rb[2], ref_big["step_force"])
+    assert rb[0] == ref_big[0] and np.array_equal(rb[1], ref_big[1])
+    assert np.array_equal(rb[2], ref_big[2])
     info = srv.info()
-    print(f"suspended solves: {info.suspended}")
+    print(f"suspended solves: {info.suspended}, launches {info.launches - launches0}")
     assert info.suspended >= 1
+    assert info.launches - launches0 >= 2
     assert srv.stop() == 0
     srv.close()
     for h in handles:
