@@ -634,6 +634,24 @@ int fem_debug_plan_check(const double* nodes, int64_t n_nodes, const int32_t* te
                          const int32_t* tet_material, const fem_material* materials, int32_t n_materials,
                          const int32_t* fixed_nodes, int64_t n_fixed, int32_t n_parts, int64_t out[8]);
 
+/*
+ * Host-only check of the request server's choice of launch shape (no CUDA
+ * call; the paper has no counterpart: it is the server's scheduling rule).
+ * shape_groups [n_shapes * n_classes]: groups of class c in shape s at
+ * [s * n_classes + c] (> 0: the shape serves the class); cur: the live shape;
+ * request_ids / request_classes [n_requests]: the unfinished requests (ids
+ * grow with submission). Writes the shape the server would run next to
+ * *out_shape: with o the oldest request the live shape does not serve and t
+ * the first shape serving o's class, t when o is older than every request of
+ * the classes cur serves and t does not (or there is none); with no such o,
+ * shape 0 when cur != 0 and every unfinished request's class is served by
+ * shape 0, else cur. Errors: FEM_ERR_ARG (1-3 shapes, 1-8 classes, every class
+ * served by some shape, classes in range, cur in range).
+ */
+int fem_debug_pick_shape(int32_t n_shapes, int32_t n_classes, const int32_t* shape_groups, int32_t cur,
+                         const int64_t* request_ids, const int32_t* request_classes, int32_t n_requests,
+                         int32_t* out_shape);
+
 #ifdef __cplusplus
 }
 #endif

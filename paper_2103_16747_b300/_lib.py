@@ -48,7 +48,7 @@ EXPORTS = ("fem_default_options", "fem_create_mesh", "fem_set_indenter", "fem_se
            "fem_solve", "fem_solve_range", "fem_solve_batch", "fem_destroy_mesh", "fem_last_error", "fem_build_checked",
            "fem_mesh_info_get", "fem_repartition",
            "fem_eval_residual", "fem_eval_residual_noalloc", "fem_apply_tangent",
-           "fem_debug_barrier_timeout", "fem_debug_pcg_dots", "fem_debug_reciprocals", "fem_debug_plan_check", "fem_batch_create", "fem_batch_run", "fem_batch_info_get",
+           "fem_debug_barrier_timeout", "fem_debug_pcg_dots", "fem_debug_reciprocals", "fem_debug_plan_check", "fem_debug_pick_shape", "fem_batch_create", "fem_batch_run", "fem_batch_info_get",
            "fem_batch_destroy", "fem_batch_tune", "fem_server_create", "fem_server_start", "fem_server_submit",
            "fem_server_result", "fem_server_stop", "fem_server_info_get", "fem_server_destroy",
            "fem_element_stress")
@@ -150,6 +150,8 @@ def _load():
         "fem_debug_reciprocals": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
         "fem_debug_plan_check": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
                                            C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p]),
+        "fem_debug_pick_shape": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                                           C.c_int32, C.c_void_p]),
         "fem_batch_create": (C.c_int, [P, P, C.c_int32, C.POINTER(fem_options), C.POINTER(P)]),
         "fem_batch_run": (C.c_int, [P, P, C.c_double, P, P, P]),
         "fem_batch_info_get": (C.c_int, [P, C.POINTER(fem_batch_info)]),
@@ -537,6 +539,20 @@ def fem_debug_plan_check(nodes, tets, tet_material, materials, fixed_nodes, n_pa
     keys = ("identical", "owners_valid", "max_owned", "min_owned", "max_part_tets", "workers", "max_owned_nodes",
             "lists_ascending")
     return dict(zip(keys, (int(v) for v in out)))
+
+
+def fem_debug_pick_shape(shape_groups, cur, requests):
+    """The request server's next launch shape (host rule, no CUDA call).
+    shape_groups: [n_shapes][n_classes] groups per class in each shape;
+    cur: the live shape; requests: (id, class) of the unfinished requests."""
+    g = np.ascontiguousarray(shape_groups, dtype=np.int32)
+    ids = np.ascontiguousarray([r[0] for r in requests], dtype=np.int64)
+    cls = np.ascontiguousarray([r[1] for r in requests], dtype=np.int32)
+    out = C.c_int32(-1)
+    _check(lib.fem_debug_pick_shape(g.shape[0], g.shape[1], C.c_void_p(g.ctypes.data), int(cur),
+                                    C.c_void_p(ids.ctypes.data) if len(ids) else None,
+                                    C.c_void_p(cls.ctypes.data) if len(cls) else None, len(ids), C.byref(out)))
+    return out.value
 
 
 def fem_debug_reciprocals(x):

@@ -358,45 +358,58 @@ bool retire(fem_server* v, bool wait) {
 }
 
 // The launch shape the unfinished requests ask for (request ids grow with
-// submission, so the smallest id is the oldest request). A request of a class
-// the live shape does not serve waits in its ring. Let o be the oldest such
-// request and t the first shape serving its class: the kernel changes to t
-// when o is older than every unfinished request of the classes the live shape
-// serves and t does not (first come, first served between the shapes), or at
-// once when there are none. The largest size class is served by shapes 0 and
-// 1 and asks for no change between them; once no unfinished request needs
-// the live shape more than shape 0, the kernel returns to shape 0, whose
-// groups serve every size class.
-int wanted_shape(const fem_server* v) {
-  if (v->n_shapes < 2) return 0;
-  const int cur = v->cur;
-  auto serves = [&](int sh, int c) { return v->shape[sh].class_groups[c] > 0; };
-  std::vector<int64_t> ids;
-  ids.reserve(v->pending.size() + v->slots.size());
-  for (int64_t id : v->pending) ids.push_back(id);
-  for (const Slot& s : v->slots)
-    if (s.state == SLOT_RUNNING) ids.push_back(s.req);
+// submission, so the smallest id is the oldest request). groups[s * n_classes
+// + c] > 0 when shape s serves class c. A request of a class the live shape
+// does not serve waits in its ring. Let o be the oldest such request and t the
+// first shape serving its class: the kernel changes to t when o is older than
+// every unfinished request of the classes the live shape serves and t does not
+// (first come, first served between the shapes), or at once when there are
+// none. The largest size class is served by shapes 0 and 1 and asks for no
+// change between them; once no unfinished request needs the live shape more
+// than shape 0, the kernel returns to shape 0, whose groups serve every size
+// class.
+int pick_shape(int n_shapes, int n_classes, const int* groups, int cur, const int64_t* ids, const int* cls, int n) {
+  if (n_shapes < 2) return 0;
+  auto serves = [&](int sh, int c) { return groups[(size_t)sh * n_classes + c] > 0; };
   int64_t o = INT64_MAX;
   int t = cur;
   bool needs_cur = false;
-  for (int64_t id : ids) {
-    const int c = v->mesh_class[v->reqs.at(id).mesh];
+  for (int r = 0; r < n; ++r) {
+    const int c = cls[r];
     if (serves(cur, c)) {
       needs_cur |= !serves(0, c);
       continue;
     }
-    if (id < o) {
-      o = id;
+    if (ids[r] < o) {
+      o = ids[r];
       t = 0;
-      while (t < v->n_shapes && !serves(t, c)) ++t;
+      while (t < n_shapes && !serves(t, c)) ++t;
     }
   }
   if (o == INT64_MAX) return cur != 0 && !needs_cur ? 0 : cur;
-  for (int64_t id : ids) {
-    const int c = v->mesh_class[v->reqs.at(id).mesh];
-    if (serves(cur, c) && !serves(t, c) && id < o) return cur;
-  }
+  for (int r = 0; r < n; ++r)
+    if (serves(cur, cls[r]) && !serves(t, cls[r]) && ids[r] < o) return cur;
   return t;
+}
+
+int wanted_shape(const fem_server* v) {
+  if (v->n_shapes < 2) return 0;
+  const int nc = (int)v->class_parts.size();
+  std::vector<int> groups((size_t)v->n_shapes * nc);
+  for (int sh = 0; sh < v->n_shapes; ++sh)
+    for (int c = 0; c < nc; ++c) groups[(size_t)sh * nc + c] = v->shape[sh].class_groups[c];
+  std::vector<int64_t> ids;
+  std::vector<int> cls;
+  ids.reserve(v->pending.size() + v->slots.size());
+  cls.reserve(v->pending.size() + v->slots.size());
+  auto add = [&](int64_t id) {
+    ids.push_back(id);
+    cls.push_back(v->mesh_class[v->reqs.at(id).mesh]);
+  };
+  for (int64_t id : v->pending) add(id);
+  for (const Slot& s : v->slots)
+    if (s.state == SLOT_RUNNING) add(s.req);
+  return pick_shape(v->n_shapes, nc, groups.data(), v->cur, ids.data(), cls.data(), (int)ids.size());
 }
 
 void dispatcher(fem_server* v) {
@@ -988,6 +1001,25 @@ static int fem_server_info_get_body(const fem_server* v, fem_server_info* info) 
 int fem_server_info_get(const fem_server* v, fem_server_info* info) {
   fem::NvtxRange nvtx_("fem_server_info_get");
   return guarded([&] { return fem_server_info_get_body(v, info); });
+}
+
+int fem_debug_pick_shape(int32_t n_shapes, int32_t n_classes, const int32_t* shape_groups, int32_t cur,
+                         const int64_t* request_ids, const int32_t* request_classes, int32_t n_requests,
+                         int32_t* out_shape) {
+  last_error().clear();
+  if (n_shapes < 1 || n_shapes > 3 || n_classes < 1 || n_classes > 8 || !shape_groups || !out_shape ||
+      cur < 0 || cur >= n_shapes || n_requests < 0 || (n_requests > 0 && (!request_ids || !request_classes)))
+    return fail(FEM_ERR_ARG, "invalid arguments");
+  for (int c = 0; c < n_classes; ++c) {
+    bool served = false;
+    for (int sh = 0; sh < n_shapes; ++sh) served |= shape_groups[sh * n_classes + c] > 0;
+    if (!served) return fail(FEM_ERR_ARG, "class %d is served by no shape", c);
+  }
+  for (int r = 0; r < n_requests; ++r)
+    if (request_classes[r] < 0 || request_classes[r] >= n_classes)
+      return fail(FEM_ERR_ARG, "request %d: class out of range", r);
+  *out_shape = pick_shape(n_shapes, n_classes, shape_groups, cur, request_ids, request_classes, n_requests);
+  return FEM_OK;
 }
 
 void fem_server_destroy(fem_server* v) {
