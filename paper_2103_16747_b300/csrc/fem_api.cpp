@@ -366,6 +366,8 @@ int host_workers(int64_t Nn, int64_t Nt) {
 // component: a part over CTA size / 3 nodes needs a second pass and holds up
 // every CTA at the next sync); it applies only where the average part stays
 // well below it.
+constexpr double kNodeCost = 0.25;   // cost of an owned node, in tets
+
 int cut_node_range(const fem_mesh* m, int n_parts, int node_cap, std::vector<int>& nb) {
   const int Nn = (int)m->n_nodes, Nt = (int)m->n_tets;
   if (node_cap > 0 && (double)Nn > 0.8 * (double)node_cap * n_parts) node_cap = 0;
@@ -397,7 +399,7 @@ int cut_node_range(const fem_mesh* m, int n_parts, int node_cap, std::vector<int
         fresh += stamp[t] != id;
         stamp[t] = id;
       }
-      double add = 0.25 + fresh;
+      double add = kNodeCost + fresh;
       if ((cost > 0.0 && cost + add > target) || (node_cap > 0 && nodes == node_cap)) {
         if (cuts && parts < n_parts) (*cuts)[parts] = i;
         ++parts;
@@ -405,7 +407,7 @@ int cut_node_range(const fem_mesh* m, int n_parts, int node_cap, std::vector<int
         id = fresh_id();
         cost = 0.0;
         nodes = 0;
-        add = 0.25 + (j1 - j0);   // the new part has seen none of these tets
+        add = kNodeCost + (j1 - j0);   // the new part has seen none of these tets
         for (int j = j0; j < j1; ++j) stamp[ce[j] >> 2] = id;
       }
       cost += add;
@@ -419,7 +421,7 @@ int cut_node_range(const fem_mesh* m, int n_parts, int node_cap, std::vector<int
   // when its top already gives at most n_parts ranges.
   double lo = 1.0, hi = 8.0 * (double)Nt + Nn;
   {
-    const double low = ((double)Nt + 0.25 * Nn) / n_parts;
+    const double low = ((double)Nt + kNodeCost * Nn) / n_parts;
     if (sweep(8.0 * low, nullptr) <= n_parts) {
       lo = std::max(1.0, low - 1.0);
       hi = 8.0 * low;
