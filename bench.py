@@ -885,8 +885,8 @@ def main():
                     help="largest CTA group of the request server (power of two)")
     ap.add_argument("--serve-tets-per-cta", type=int, default=0,
                     help="size-class target of the request server (0: the library default, 1300 tets per CTA; "
-                         "smaller targets give each request a larger group but send more meshes to whole-GPU "
-                         "passes)")
+                         "smaller targets give each request a larger group but send more meshes to the "
+                         "large- and huge-mesh launch shapes)")
     ap.add_argument("--batch-parts", type=int, default=0,
                     help="batched workloads: uniform CTA groups of this size instead of the autotuner")
     ap.add_argument("--n-solves", type=int, default=None,

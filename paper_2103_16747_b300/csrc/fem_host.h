@@ -71,7 +71,7 @@ namespace fem {
 
 // NVTX range over a host-side phase of a library call (mesh preparation,
 // partitioning, uploads, launches, graph replays, the server's admissions and
-// whole-GPU passes), visible on an Nsight Systems timeline; a no-op without a
+// launches per shape), visible on an Nsight Systems timeline; a no-op without a
 // profiler attached. The device-side timeline of a persistent solve (load
 // steps, Newton iterations, PCG phases) cannot carry host ranges: it comes back
 // as fem_stats.step_end_ms and the phase split.

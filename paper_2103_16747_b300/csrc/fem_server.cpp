@@ -15,11 +15,13 @@
 // others run is picked up by the first idle group of its class.
 //
 // Meshes too large for a class of at most 64 CTAs (more than 64 x
-// batch_tets_per_cta tets) are served in whole-GPU passes: when one of their
-// requests waits, the dispatcher stops admitting, lets the persistent launch
-// finish the solves it holds and leave, runs the waiting large requests one
-// after another with the single-solve kernel on all SMs, and launches the
-// persistent kernel again (republishing the queued small requests).
+// batch_tets_per_cta tets) are served by other launch shapes of the same
+// kernel: shape 1 keeps groups of the largest class and gives the other SMs to
+// one group for the "large" meshes, shape 2 is one group of every SM for the
+// "huge" ones. The dispatcher changes the shape first come, first served
+// (pick_shape): running solves leave at their next load step with their state
+// in their result slot, the kernel is relaunched in the other shape, and the
+// suspended solves resume in the next launch that serves their class.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -132,7 +134,6 @@ struct fem_server {
   bool draining = false;            // stop and yield words set for a change of launch shape
   bool stopping = false;
   double session_end = 0.0;         // host clock at which the session ends
-  std::vector<char> big;            // per mesh: beyond the largest size class
   int64_t admitted = 0, completed = 0, rejected = 0, suspended = 0, launches = 0;
 };
 
@@ -691,7 +692,6 @@ static int fem_server_create_body(fem_mesh* const* meshes, int32_t n_meshes, int
   v->max_steps = max_steps;
   v->meshes.assign(meshes, meshes + n_meshes);
   v->mesh_class = mesh_class;
-  v->big = big;
   v->mesh_part = part;
   v->class_parts = class_parts;
   v->n_shapes = (int)plans.size();
