@@ -243,3 +243,56 @@ def test_server_physics_options_match_oracle(F, physics):
     assert srv.stop() == 0
     srv.close()
     F.fem_destroy_mesh(h)
+
+
+def test_stop_while_shapes_change_returns_every_request(F):
+    """Stop while the server changes launch shapes (large, huge and small
+    requests interleaved, so solves are being suspended and resumed): stop
+    returns, every request comes back finished or FEM_ERR_TIMEOUT (not run, or
+    suspended when the session closed), none stays pending, and a finished
+    small request equals the same request served alone."""
+    import time
+    cube, cube_ind = W.cube_sphere()
+    pool = [cube] + [m for m, _ in W.uneven_fingertips(3, seed=21, tet_min=6.6e3, tet_max=1.2e4)]
+    handles = [F.fem_create_mesh(m.nodes, m.tets, m.tet_material, m.materials, m.fixed_nodes) for m in pool]
+    draws = {k: W.draw_indentations(pool[k], 2, seed=500 + k) for k in range(1, len(pool))}
+    opt = F.fem_default_options()
+    opt.max_newton = 200
+    opt.batch_tets_per_cta = 100
+    srv = F.FemServer(handles, 20, opt, result_bytes=32 << 20)
+    assert srv.info().n_shapes == 3
+    srv.start(120.0)
+    rc, rid = srv.submit(0, cube_ind, 1e-6)
+    alone = srv.result(rid, cube.n_nodes, 10, wait_ms=100000)
+    assert alone[0] == 0
+    launches0 = srv.info().launches
+    ids = []
+    for rep in range(3):
+        for k in range(1, len(pool)):
+            for d in draws[k]:
+                rc, rid = srv.submit(k, d, 1e-6)
+                assert rc == 0
+                ids.append((rid, k))
+        rc, rid = srv.submit(0, cube_ind, 1e-6)
+        assert rc == 0
+        ids.append((rid, 0))
+    time.sleep(0.3)
+    t0 = time.perf_counter()
+    assert srv.stop() == 0
+    assert time.perf_counter() - t0 < 60.0
+    seen = {}
+    for rid, k in ids:
+        n_steps = 10 if k == 0 else 20
+        r = srv.result(rid, pool[k].n_nodes, n_steps, wait_ms=0)
+        assert r[0] in (F.FEM_OK, F.FEM_ERR_NOT_CONVERGED, F.FEM_ERR_TIMEOUT), r[0]
+        seen[r[0]] = seen.get(r[0], 0) + 1
+        if k == 0 and r[0] == F.FEM_OK:
+            assert np.array_equal(r[1], alone[1]) and np.array_equal(r[2], alone[2])
+    info = srv.info()
+    print(f"statuses {seen}, launches {info.launches - launches0}, suspended {info.suspended}")
+    assert info.launches - launches0 >= 2
+    rc, _ = srv.submit(0, cube_ind, 1e-6)
+    assert rc == F.FEM_ERR_BUSY
+    srv.close()
+    for h in handles:
+        F.fem_destroy_mesh(h)
