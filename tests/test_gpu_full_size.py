@@ -1,0 +1,71 @@
+"""Parity at full size: the three largest meshes of the 64-mesh uneven workload
+(175k-186k tets, the largest the benchmarks run), in the launch configuration
+its benchmark times (size classes at 1,000 tets per CTA, which puts each of
+these meshes on every SM) and on the single-solve path. The oracle cannot
+solve these meshes in test time, so each answer is checked through properties
+that hold at any size: the oracle's own FP64 residual at the GPU displacement
+is within the solve tolerance of its scale at the last load step, and the
+GPU's last-step resultant contact force equals the oracle's resultant
+(Sec. III-A: nodal contact forces summed) at that displacement."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import Problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2103_16747_b300 as F
+    return F
+
+
+@pytest.fixture(scope="module")
+def largest():
+    jobs = W.uneven_fingertips(64, seed=1003)
+    order = np.argsort([-m.n_tets for m, _ in jobs])[:3]
+    return [jobs[k] for k in order]
+
+
+def _certify(m, d, u, force):
+    p = Problem(m, d)
+    rn, scale, _ = p.residual_norm(u, d.n_steps)
+    assert rn <= 1e-6 * scale, (rn, scale)
+    _, fc = p.gradient(u, d.n_steps)
+    ref = fc.sum(axis=0)
+    assert np.linalg.norm(force - ref) <= 1e-8 * np.linalg.norm(ref), (force, ref)
+
+
+def test_largest_uneven_meshes_batched_and_single(F, largest):
+    assert min(m.n_tets for m, _ in largest) > 170000
+    meshes = [m for m, _ in largest]
+    inds = [d for _, d in largest]
+    handles = [F.fem_create_mesh(m.nodes, m.tets, m.tet_material, m.materials, m.fixed_nodes) for m in meshes]
+    opt = F.fem_default_options()
+    opt.max_newton = 400
+    opt.batch_engine, opt.batch_parts, opt.batch_tets_per_cta = 1, 0, 1000
+    out = [np.zeros((m.n_nodes, 3)) for m in meshes]
+    frc = [np.zeros((d.n_steps, 3)) for d in inds]
+    rc, st = F.fem_solve_batch(handles, inds, 1e-6, opt, out, frc, check=False)
+    assert rc == 0, [s.status for s in st]
+    for k, (m, d) in enumerate(largest):
+        assert st[k].steps_done == d.n_steps and st[k].residual <= 1e-6 * st[k].scale
+        _certify(m, d, out[k], frc[k][-1])
+    # the single-solve path on the same meshes (its own partition of 148 parts)
+    for k, (m, d) in enumerate(largest):
+        F.fem_set_indenter(handles[k], d.shape, d.pose, np.asarray(d.params), d.direction, d.depth_schedule)
+        u = np.zeros((m.n_nodes, 3))
+        f = np.zeros((d.n_steps, 3))
+        rc1, s1 = F.fem_solve(handles[k], d.n_steps, 1e-6, opt, u, f, None, check=False)
+        assert rc1 == 0 and s1.steps_done == d.n_steps
+        _certify(m, d, u, f[-1])
+        # two converged answers of the same problem: within the conditioning
+        # of the tangent times the residual tolerance of each other
+        assert np.linalg.norm(u - out[k]) <= 1e-3 * np.linalg.norm(out[k])
+    for h in handles:
+        F.fem_destroy_mesh(h)
