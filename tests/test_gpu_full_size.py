@@ -1,8 +1,9 @@
-"""Parity at full size: the three largest meshes of the 64-mesh uneven workload
-(175k-186k tets, the largest the benchmarks run), in the launch configuration
-its benchmark times (size classes at 1,000 tets per CTA, which puts each of
-these meshes on every SM) and on the single-solve path. The oracle cannot
-solve these meshes in test time, so each answer is checked through properties
+"""Parity at full size, in the launch configurations the benchmarks time: the
+256 random fingertip indentations of the batched workload (groups of 37 CTAs),
+and the three largest meshes of the 64-mesh uneven workload (175k-186k tets,
+the largest the benchmarks run; size classes at 1,000 tets per CTA, which puts
+each of them on every SM) also on the single-solve path. The oracle cannot
+solve all of these in test time, so each answer is checked through properties
 that hold at any size: the oracle's own FP64 residual at the GPU displacement
 is within the solve tolerance of its scale at the last load step, and the
 GPU's last-step resultant contact force equals the oracle's resultant
@@ -69,3 +70,30 @@ def test_largest_uneven_meshes_batched_and_single(F, largest):
         assert np.linalg.norm(u - out[k]) <= 1e-3 * np.linalg.norm(out[k])
     for h in handles:
         F.fem_destroy_mesh(h)
+
+
+def test_fingertip_256_draws_in_the_benchmark_slot_shape(F):
+    """The 256 random indentations of the batched fingertip workload, in the
+    slot shape its benchmark times (groups of 37 CTAs, FP32 tangent, at most
+    400 Newton iterations per load step): every solve converges, every 8th
+    draw and the two hardest (62, 176) are certified by the oracle's residual
+    and resultant force, and a draw alone gives bitwise its result in the
+    256-solve mix."""
+    m, _ = W.fingertip_sphere()
+    draws = W.draw_indentations(m, 256, seed=1002)
+    h = F.fem_create_mesh(m.nodes, m.tets, m.tet_material, m.materials, m.fixed_nodes)
+    opt = F.fem_default_options()
+    opt.max_newton = 400
+    opt.batch_engine, opt.batch_parts = 1, 37
+    out = [np.zeros((m.n_nodes, 3)) for _ in draws]
+    frc = [np.zeros((d.n_steps, 3)) for d in draws]
+    rc, st = F.fem_solve_batch([h] * len(draws), draws, 1e-6, opt, out, frc, check=False)
+    assert rc == 0, [k for k, s in enumerate(st) if s.status != 0]
+    assert all(s.steps_done == 20 and s.residual <= 1e-6 * s.scale for s in st)
+    for k in sorted(set(range(0, 256, 8)) | {62, 176}):
+        _certify(m, draws[k], out[k], frc[k][-1])
+    u1 = [np.zeros((m.n_nodes, 3))]
+    f1 = [np.zeros((20, 3))]
+    rc1, _ = F.fem_solve_batch([h], [draws[62]], 1e-6, opt, u1, f1, check=False)
+    assert rc1 == 0 and np.array_equal(u1[0], out[62]) and np.array_equal(f1[0], frc[62])
+    F.fem_destroy_mesh(h)
