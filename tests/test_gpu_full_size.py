@@ -1,8 +1,9 @@
 """Parity at full size, in the launch configurations the benchmarks time: the
 256 random fingertip indentations of the batched workload (groups of 37 CTAs),
-and the three largest meshes of the 64-mesh uneven workload (175k-186k tets,
-the largest the benchmarks run; size classes at 1,000 tets per CTA, which puts
-each of them on every SM) also on the single-solve path. The oracle cannot
+the three largest meshes of the 64-mesh uneven workload (175k-186k tets, the
+largest the benchmarks run; size classes at 1,000 tets per CTA, which puts each
+of them on every SM) also on the single-solve path, and the request server on
+the serving workload's 16-mesh pool in all three launch shapes. The oracle cannot
 solve all of these in test time, so each answer is checked through properties
 that hold at any size: the oracle's own FP64 residual at the GPU displacement
 is within the solve tolerance of its scale at the last load step, and the
@@ -97,3 +98,34 @@ def test_fingertip_256_draws_in_the_benchmark_slot_shape(F):
     rc1, _ = F.fem_solve_batch([h], [draws[62]], 1e-6, opt, u1, f1, check=False)
     assert rc1 == 0 and np.array_equal(u1[0], out[62]) and np.array_equal(f1[0], frc[62])
     F.fem_destroy_mesh(h)
+
+
+def test_request_server_on_the_serving_pool(F):
+    """The request server on the serving workload's pool (16 fingertips of
+    6k-168k tets, the default 1,300 tets per CTA: size classes, the large-mesh
+    group beside the 64-CTA class, and the whole-GPU group for the largest),
+    one request per mesh submitted at once: every result converges and is
+    certified by the oracle's residual and resultant force."""
+    jobs = W.uneven_fingertips(16, seed=1004)
+    pool = [m for m, _ in jobs]
+    handles = [F.fem_create_mesh(m.nodes, m.tets, m.tet_material, m.materials, m.fixed_nodes) for m in pool]
+    opt = F.fem_default_options()
+    opt.max_newton = 400
+    srv = F.FemServer(handles, 20, opt, result_bytes=1 << 30)
+    info = srv.info()
+    assert info.n_shapes == 3
+    draws = [W.draw_indentations(m, 4, seed=2000 + k)[0] for k, m in enumerate(pool)]
+    srv.start(300.0)
+    ids = []
+    for k, d in enumerate(draws):
+        rc, rid = srv.submit(k, d, 1e-6)
+        assert rc == 0
+        ids.append(rid)
+    for k, rid in enumerate(ids):
+        rc, u, f, st, _ = srv.result(rid, pool[k].n_nodes, 20, wait_ms=200000)
+        assert rc == 0 and st.steps_done == 20, (k, rc)
+        _certify(pool[k], draws[k], u, f[-1])
+    assert srv.stop() == 0
+    srv.close()
+    for h in handles:
+        F.fem_destroy_mesh(h)
