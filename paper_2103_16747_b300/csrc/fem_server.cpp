@@ -292,7 +292,10 @@ void finish(fem_server* v, int slot) {
 // from the start of their rings. Caller holds the lock.
 int launch_persistent(fem_server* v) {
   const double left = v->session_end - now_s();
-  if (left <= 0.0) return FEM_OK;
+  if (left <= 0.0) {
+    v->draining = false;   // the session is over: no relaunch, nothing left to drain
+    return FEM_OK;
+  }
   LaunchShape& sh = v->shape[v->cur];
   CUDA_TRY(cudaMemsetAsync(v->ws, 0, v->jobs_off, v->ks), "reset");   // group counters, queue heads
   for (size_t c = 0; c < v->class_parts.size(); ++c) v->h_tail[c] = 0;
