@@ -69,6 +69,7 @@ enum SlotState { SLOT_FREE = 0, SLOT_RUNNING, SLOT_COPYING };
 struct Slot {
   int state = SLOT_FREE;
   int64_t req = -1;
+  int cls = -1;                     // size class of the request it holds
   cudaEvent_t ev = nullptr;
   double* h_u = nullptr;            // pinned staging
   double* h_force = nullptr;
@@ -237,6 +238,7 @@ bool admit(fem_server* v, int slot, Request& q) {
   __atomic_store_n(&v->h_tail[c], pos + 1, __ATOMIC_RELEASE);
   v->slots[slot].state = SLOT_RUNNING;
   v->slots[slot].req = q.id;
+  v->slots[slot].cls = c;
   q.state = 1;
   q.t_admit = now_s();
   ++v->admitted;
@@ -406,13 +408,15 @@ int wanted_shape(const fem_server* v) {
   std::vector<int> cls;
   ids.reserve(v->pending.size() + v->slots.size());
   cls.reserve(v->pending.size() + v->slots.size());
-  auto add = [&](int64_t id) {
+  for (int64_t id : v->pending) {
     ids.push_back(id);
     cls.push_back(v->mesh_class[v->reqs.at(id).mesh]);
-  };
-  for (int64_t id : v->pending) add(id);
+  }
   for (const Slot& s : v->slots)
-    if (s.state == SLOT_RUNNING) add(s.req);
+    if (s.state == SLOT_RUNNING) {
+      ids.push_back(s.req);
+      cls.push_back(s.cls);
+    }
   return pick_shape(v->n_shapes, nc, groups.data(), v->cur, ids.data(), cls.data(), (int)ids.size());
 }
 
@@ -461,7 +465,9 @@ void dispatcher(fem_server* v) {
         }
         if (!v->kernel_live && v->draining) {
           v->cur = v->next;
-          fem::NvtxRange nvtx_launch(v->cur ? "launch: large-mesh shape" : "launch: size-class shape");
+          static const char* const kShapeName[3] = {"launch: size-class shape", "launch: large-mesh shape",
+                                                    "launch: huge-mesh shape"};
+          fem::NvtxRange nvtx_launch(kShapeName[v->large_class >= 0 || v->cur == 0 ? v->cur : 2]);
           if (launch_persistent(v) != FEM_OK) v->stopping = true;
           worked = true;
         }
